@@ -1,0 +1,576 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test checks the oracle against a fact the paper or the mathematics
+fixes: closed forms (a single Gaussian on the optical axis), an independent
+projection (scipy rotations + a numerically differentiated pinhole),
+brute-force per-pixel compositing, invariants (transmittance, occlusion,
+permutation, mask == deletion, rigid motion), and central finite
+differences for every gradient (scene parameters, codebooks, mask logits
+through the straight-through estimator, camera pose, ICP).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.linalg import expm
+from scipy.spatial.transform import Rotation
+
+from oracle import oracle as O
+from paper_2403_11247_b300 import synth
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# ---------------------------------------------------------------------------
+# helpers (input construction only)
+# ---------------------------------------------------------------------------
+
+def raw_scene(mu, logscale, quat, op_logit, rgb, mask=None):
+    n = len(mu)
+    groups = {
+        "logscale": synth.Group(3, raw=np.asarray(logscale, np.float32).reshape(n, 3)),
+        "rot": synth.Group(4, raw=np.asarray(quat, np.float32).reshape(n, 4)),
+        "opacity": synth.Group(1, raw=np.asarray(op_logit, np.float32).reshape(n, 1)),
+        "rgb": synth.Group(3, raw=np.asarray(rgb, np.float32).reshape(n, 3)),
+    }
+    return synth.Scene(np.asarray(mu, np.float32).reshape(n, 3), np.ones((n, 3), np.float32),
+                       np.zeros((n, 1, 3), np.float32), groups,
+                       None if mask is None else np.asarray(mask, np.float32), 0.5)
+
+
+def cam(fx, fy, cx, cy, w, h, T=None):
+    return synth.camera(fx, fy, cx, cy, w, h, synth.identity_pose() if T is None else T)
+
+
+def sigma2d_independent(mu, scales, quat_wxyz, c, dil):
+    """Sigma' from an independent route: scipy rotation (x,y,z,w order),
+    Sigma as a sum over principal axes, and the Jacobian of the full pinhole
+    map x -> pi(W x + t) taken by central differences."""
+    q = np.asarray(quat_wxyz, np.float64)
+    Rg = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    Sig = sum(scales[k] ** 2 * np.outer(Rg[:, k], Rg[:, k]) for k in range(3))
+    T = np.asarray(c.T_cw, np.float64)
+
+    def pi(x):
+        p = T[:, :3] @ x + T[:, 3]
+        return np.array([c.fx * p[0] / p[2] + c.cx, c.fy * p[1] / p[2] + c.cy])
+
+    h = 1e-5
+    Jw = np.zeros((2, 3))
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        Jw[:, k] = (pi(mu + e) - pi(mu - e)) / (2 * h)
+    return Jw @ Sig @ Jw.T + dil * np.eye(2), pi(mu)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 14 decode
+# ---------------------------------------------------------------------------
+
+def test_rvq_single_stage_is_table_lookup():
+    rng = np.random.default_rng(0)
+    cb = rng.normal(size=(1, 64, 4))
+    idx = rng.integers(0, 64, size=(1, 500), dtype=np.uint8)
+    out = O.rvq_decode(cb, idx)
+    assert np.array_equal(out, cb[0][idx[0]])
+
+
+def test_rvq_stage_sum_recovers_index_digits():
+    # C^s[k] = k * 256^-s: the decoded sum is the index digits in base 256
+    L, K = 3, 256
+    cb = np.zeros((L, K, 1))
+    for s in range(L):
+        cb[s, :, 0] = np.arange(K) * 256.0 ** (-s)
+    rng = np.random.default_rng(1)
+    idx = rng.integers(0, K, size=(L, 1000), dtype=np.uint8)
+    v = O.rvq_decode(cb, idx)[:, 0]
+    for s in range(L):
+        digit = np.floor(v).astype(np.int64)
+        assert np.array_equal(digit, idx[s])
+        v = (v - digit) * 256.0
+
+
+def test_rvq_matches_gather_sum():
+    rng = np.random.default_rng(2)
+    cb = rng.normal(size=(4, 48, 3))
+    idx = rng.integers(0, 48, size=(4, 333), dtype=np.uint8)
+    ref = sum(cb[s][idx[s]] for s in range(4))
+    assert np.allclose(O.rvq_decode(cb, idx), ref, rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 2-3 projection
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dil", [0.0, 0.3])
+def test_projection_on_axis_closed_form(dil):
+    sx, sy, sz, z = 0.11, 0.07, 0.05, 2.5
+    sc = raw_scene([[0, 0, z]], [np.log([sx, sy, sz])], [[1, 0, 0, 0]], [0.0], [[0.5, 0.5, 0.5]])
+    c = cam(300.0, 250.0, 31.5, 23.5, 64, 48)
+    o = O.Oracle(sc, [c], params=dict(dilation=dil))
+    proj, b32, _ = o.projection()
+    A = (300.0 * sx / z) ** 2 + dil
+    Cc = (250.0 * sy / z) ** 2 + dil
+    assert proj[0, 10] == 1
+    assert np.allclose(proj[0, 3:6], [1 / A, 0.0, 1 / Cc], rtol=1e-6, atol=1e-12)
+    assert np.allclose(proj[0, 0:3], [31.5, 23.5, z], rtol=1e-6)
+    assert proj[0, 11] == math.ceil(3 * math.sqrt(max(A, Cc)))
+
+
+def test_projection_rotated_matches_independent_route():
+    rng = np.random.default_rng(3)
+    n = 40
+    q = synth.random_quats(rng, n)
+    mu = np.stack([rng.uniform(-0.5, 0.5, n), rng.uniform(-0.4, 0.4, n), rng.uniform(2, 4, n)], 1)
+    ls = rng.uniform(-3.5, -2.0, (n, 3))
+    sc = raw_scene(mu, ls, q, np.zeros(n), np.full((n, 3), 0.5))
+    T = synth.perturb_pose(synth.identity_pose(), rng, 10.0, 0.1).astype(np.float32)
+    c = cam(120.0, 110.0, 63.5, 47.5, 128, 96, T)
+    o = O.Oracle(sc, [c], params=dict(jacobian_clamp=0, dilation=0.3))
+    proj, _, _ = o.projection()
+    checked = 0
+    for i in range(n):
+        if proj[i, 10] != 1:
+            continue
+        S2, uv = sigma2d_independent(mu[i].astype(np.float32).astype(np.float64), np.exp(ls[i].astype(np.float32).astype(np.float64)),
+                                     q[i].astype(np.float32), c, 0.3)
+        a, b, cc = proj[i, 3:6]
+        conic_inv = np.linalg.inv(np.array([[a, b], [b, cc]]))
+        assert np.allclose(conic_inv, S2, rtol=2e-7, atol=1e-9)
+        assert np.allclose(proj[i, 0:2], uv, rtol=1e-10)
+        checked += 1
+    assert checked > 20
+
+
+def test_fp32_binning_expressions_bit_exact():
+    """u32, v32, z32 follow the stated FP32 expression order exactly."""
+    sc = synth.room_scene(n_anchors=3000)
+    c = synth.room_camera(320, 180, 160.0)
+    o = O.Oracle(sc, [c])
+    _, b32, _ = o.projection()
+    f = np.float32
+    a = np.arange(sc.n) // sc.k
+    i = np.arange(sc.n) % sc.k
+    mu = sc.anchor_xyz[a] + (sc.offsets[a, i] * sc.anchor_l[a])
+    T = c.T_cw
+    p = [((T[r, 0] * mu[:, 0] + T[r, 1] * mu[:, 1]) + T[r, 2] * mu[:, 2]) + T[r, 3] for r in range(3)]
+    z = p[2]
+    front = z > f(c.near)
+    thr = O.mask_threshold(sc.mask_eps)
+    front &= sc.mask_logit > thr
+    u = (f(c.fx) * p[0]) / z + f(c.cx)
+    v = (f(c.fy) * p[1]) / z + f(c.cy)
+    assert u.dtype == np.float32 and front.sum() > 1000
+    assert np.array_equal(b32[front, 0].view(np.uint32), u[front].view(np.uint32))
+    assert np.array_equal(b32[front, 1].view(np.uint32), v[front].view(np.uint32))
+    assert np.array_equal(b32[front, 2].view(np.uint32), z[front].view(np.uint32))
+
+
+# ---------------------------------------------------------------------------
+# Eq. 16-18 compositing
+# ---------------------------------------------------------------------------
+
+def test_single_gaussian_closed_form():
+    mu = np.array([0.05, -0.03, 2.0])
+    ls = np.log([0.08, 0.05, 0.06])
+    q = np.array([0.9, 0.2, -0.3, 0.1])
+    q /= np.linalg.norm(q)
+    ol, rgb = 0.7, np.array([0.2, 0.6, 0.9])
+    sc = raw_scene([mu], [ls], [q], [ol], [rgb])
+    c = cam(100.0, 100.0, 15.5, 15.5, 32, 32)
+    o = O.Oracle(sc, [c], params=dict(jacobian_clamp=0))
+    out = o.forward()
+    mu32 = mu.astype(np.float32).astype(np.float64)
+    S2, uv = sigma2d_independent(mu32, np.exp(ls.astype(np.float32).astype(np.float64)), q.astype(np.float32), c, 0.3)
+    conic = np.linalg.inv(S2)
+    lam = np.linalg.eigvalsh(S2).max()
+    r = math.ceil(3 * math.sqrt(lam))
+    _, b32, _ = o.projection()
+    u32, v32 = b32[0, 0], b32[0, 1]
+    x0, x1 = max(0, math.floor((u32 - np.float32(r)) / 16)), min(2, math.floor((u32 + np.float32(r)) / 16) + 1)
+    y0, y1 = max(0, math.floor((v32 - np.float32(r)) / 16)), min(2, math.floor((v32 + np.float32(r)) / 16) + 1)
+    opac = 1 / (1 + math.exp(-np.float32(ol)))
+    z = (np.asarray(c.T_cw, np.float64)[:, :3] @ mu32 + np.asarray(c.T_cw, np.float64)[:, 3])[2]
+    C = out["C"].reshape(3, 32, 32)
+    for py in range(32):
+        for px in range(32):
+            d = np.array([uv[0] - px, uv[1] - py])
+            al = min(0.99, opac * math.exp(-0.5 * d @ conic @ d))
+            inside = x0 <= px // 16 < x1 and y0 <= py // 16 < y1
+            if al < 1 / 255 or not inside:
+                al = 0.0
+            assert abs(out["S"][py * 32 + px] - al) < 1e-9
+            assert abs(out["D"][py * 32 + px] - z * al) < 1e-9
+            assert np.allclose(C[:, py, px], rgb.astype(np.float32) * al, atol=1e-9)
+    assert out["S"].max() > 0.3
+
+
+def test_compositing_invariants_tiny_scene():
+    sc = synth.tiny_scene()
+    c = synth.tiny_camera()
+    o = O.Oracle(sc, [c])
+    out = o.forward()
+    S, T = out["S"], out["T_final"]
+    assert S.min() >= 0 and S.max() < 1
+    assert np.allclose(S, 1 - T, atol=1e-12)
+    rgb_max = sc.groups["rgb"].raw.max(0)
+    C = out["C"].reshape(3, -1)
+    for ch in range(3):
+        assert np.all(C[ch] <= rgb_max[ch] * S + 1e-12)
+    proj, _, _ = o.projection()
+    zmax = proj[proj[:, 10] == 1, 2].max()
+    assert np.all(out["D"] <= zmax * S + 1e-12)
+    assert out["evaluated"] == out["n_eval"].sum()
+    assert np.all(out["n_contrib"] <= out["n_eval"])
+
+
+def test_opaque_front_pair_occludes_everything_behind():
+    rng = np.random.default_rng(5)
+    front_mu = [[0.0, 0.0, 1.0], [0.001, 0.0, 1.05]]
+    n_b = 200
+    back_mu = np.stack([rng.uniform(-0.3, 0.3, n_b), rng.uniform(-0.3, 0.3, n_b), rng.uniform(2, 4, n_b)], 1)
+    mu = np.concatenate([front_mu, back_mu])
+    n = len(mu)
+    ls = np.concatenate([np.full((2, 3), np.log(1.0)), rng.uniform(-3, -2, (n_b, 3))])
+    q = np.concatenate([[[1, 0, 0, 0]] * 2, synth.random_quats(rng, n_b)])
+    ol = np.concatenate([[12.0, 12.0], rng.normal(size=n_b)])
+    rgb = rng.uniform(size=(n, 3))
+    c = cam(50.0, 50.0, 15.5, 15.5, 32, 32)
+    full = O.Oracle(raw_scene(mu, ls, q, ol, rgb), [c]).forward()
+    front = O.Oracle(raw_scene(mu[:2], ls[:2], q[:2], ol[:2], rgb[:2]), [c]).forward()
+    # centre pixels: both front Gaussians at alpha = 0.99, so transmittance
+    # reaches 1e-4 and nothing behind may contribute
+    for py in range(12, 20):
+        for px in range(12, 20):
+            i = py * 32 + px
+            assert abs(front["S"][i] - 0.9999) < 1e-12
+            assert full["S"][i] == front["S"][i] and full["D"][i] == front["D"][i]
+    assert np.abs(full["S"] - front["S"]).max() > 1e-4  # away from the centre the back does show
+
+
+def test_permutation_invariance():
+    sc = synth.tiny_scene(seed=11, n=600)
+    c = synth.tiny_camera()
+    perm = np.random.default_rng(6).permutation(sc.n)
+    g = {k: synth.Group(v.dim, raw=v.raw[perm]) for k, v in sc.groups.items()}
+    sp = synth.Scene(sc.anchor_xyz[perm], sc.anchor_l[perm], sc.offsets[perm], g)
+    a = O.Oracle(sc, [c]).forward()
+    b = O.Oracle(sp, [c]).forward()
+    for k in ("C", "D", "S", "n_eval"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_mask_equals_deletion():
+    sc = synth.box_scene(21, 800, frac_masked=0.3)
+    c = synth.tiny_camera()
+    keep = sc.mask_logit > O.mask_threshold(sc.mask_eps)
+    assert 0 < keep.sum() < sc.n
+    g = {k: synth.Group(v.dim, raw=v.raw[keep]) for k, v in sc.groups.items()}
+    sd = synth.Scene(sc.anchor_xyz[keep], sc.anchor_l[keep], sc.offsets[keep], g)
+    a = O.Oracle(sc, [c]).forward()
+    b = O.Oracle(sd, [c]).forward()
+    for k in ("C", "D", "S"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_rigid_motion_invariance():
+    sc = synth.tiny_scene(seed=12, n=500)
+    c = synth.tiny_camera()
+    Rg = Rotation.from_rotvec([0.3, -0.2, 0.5])
+    tg = np.array([0.4, -0.7, 1.1])
+    mu2 = Rg.apply(sc.anchor_xyz.astype(np.float64)) + tg
+    qr = sc.groups["rot"].raw.astype(np.float64)
+    q2 = (Rg * Rotation.from_quat(qr[:, [1, 2, 3, 0]])).as_quat()[:, [3, 0, 1, 2]]
+    g = dict(sc.groups)
+    g["rot"] = synth.Group(4, raw=q2.astype(np.float32))
+    s2 = synth.Scene(mu2.astype(np.float32), sc.anchor_l, sc.offsets, g)
+    T = np.asarray(c.T_cw, np.float64)
+    Rm = Rg.as_matrix()
+    T2 = np.zeros((3, 4))
+    T2[:, :3] = T[:, :3] @ Rm.T
+    T2[:, 3] = T[:, 3] - T[:, :3] @ Rm.T @ tg
+    c2 = synth.camera(c.fx, c.fy, c.cx, c.cy, c.width, c.height, T2)
+    # float32 inputs differ by rounding only: compare in FP64 with the moved
+    # arrays passed exactly (overrides), flags excluded
+    a = O.Oracle(sc, [c]).forward()
+    b = O.Oracle(s2, [c2], overrides=dict(anchor_xyz=mu2, raw_rot=q2, T_cw=[T2])).forward()
+    ok = (a["flags"] == 0) & (b["flags"] == 0)
+    assert ok.mean() > 0.99
+    dS = np.abs(a["S"] - b["S"])[ok]
+    # membership (FP32 rects) may flip only for a Gaussian exactly at a tile edge
+    assert (dS > 1e-7).mean() < 2e-3
+    assert np.median(dS) < 1e-12
+
+
+def test_brute_force_per_pixel_compositing():
+    """Per pixel: sort every Gaussian whose rect holds the pixel's tile by
+    (FP32 depth, index) and composite directly; no tiles, no lists."""
+    rng = np.random.default_rng(7)
+    n = 50
+    mu = np.stack([rng.uniform(-0.4, 0.4, n), rng.uniform(-0.4, 0.4, n), rng.uniform(1, 3, n)], 1)
+    sc = raw_scene(mu, rng.uniform(-3.5, -2.2, (n, 3)), synth.random_quats(rng, n), rng.normal(size=n),
+                   rng.uniform(size=(n, 3)))
+    c = cam(40.0, 40.0, 15.5, 15.5, 32, 32)
+    o = O.Oracle(sc, [c])
+    out = o.forward()
+    proj, b32, _ = o.projection()
+    zbits = b32[:, 2].view(np.uint32)
+    for py in range(32):
+        for px in range(32):
+            tx, ty = px // 16, py // 16
+            cand = [i for i in range(n) if proj[i, 10] == 1 and proj[i, 12] <= tx < proj[i, 14]
+                    and proj[i, 13] <= ty < proj[i, 15]]
+            cand.sort(key=lambda i: (int(zbits[i]), i))
+            T, Cacc, D, S = 1.0, np.zeros(3), 0.0, 0.0
+            for i in cand:
+                dx, dy = proj[i, 0] - px, proj[i, 1] - py
+                a, b, cc = proj[i, 3:6]
+                pw = -0.5 * (a * dx * dx + cc * dy * dy) - b * dx * dy
+                if pw > 0:
+                    continue
+                al = min(0.99, proj[i, 6] * math.exp(pw))
+                if al < 1 / 255:
+                    continue
+                if T * (1 - al) < 1e-4:
+                    break
+                Cacc += proj[i, 7:10] * al * T
+                D += proj[i, 2] * al * T
+                S += al * T
+                T *= 1 - al
+            k = py * 32 + px
+            assert abs(out["S"][k] - S) < 1e-12 and abs(out["D"][k] - D) < 1e-12
+            assert np.allclose(out["C"].reshape(3, -1)[:, k], Cacc, atol=1e-12)
+
+
+def test_bins_are_lexicographic_tile_depth_index():
+    sc = synth.tiny_scene()
+    c = synth.tiny_camera()
+    o = O.Oracle(sc, [c])
+    proj, b32, _ = o.projection()
+    ts, lst = o.bins()
+    zb = b32[:, 2].view(np.uint32).astype(np.int64)
+    keys, zs, ns = [], [], []
+    for i in np.nonzero(proj[:, 10] == 1)[0]:
+        x0, y0, x1, y1 = proj[i, 12:16].astype(int)
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                keys.append(ty * 4 + tx)
+                zs.append(zb[i])
+                ns.append(i)
+    order = np.lexsort((ns, zs, keys))
+    assert np.array_equal(np.asarray(ns)[order], lst)
+    assert np.array_equal(np.bincount(np.asarray(keys), minlength=12), np.diff(ts))
+
+
+# ---------------------------------------------------------------------------
+# backward: central finite differences in FP64
+# ---------------------------------------------------------------------------
+
+def fd_scene(coded: bool, seed: int, with_mask: bool = False):
+    rng = np.random.default_rng(seed)
+    na, k = 3, 2
+    xyz = np.stack([rng.uniform(-0.1, 0.1, na), rng.uniform(-0.1, 0.1, na), [1.6, 2.2, 2.9]], 1).astype(np.float32)
+    l = rng.uniform(0.5, 1.5, (na, 3)).astype(np.float32)
+    off = rng.normal(0, 0.06, (na, k, 3)).astype(np.float32)
+    n = na * k
+    if coded:
+        L, K = 2, 4
+        groups = {}
+        for name, d in synth.GROUP_DIMS.items():
+            cb = rng.normal(0, 0.3, (L, K, d)).astype(np.float32)
+            if name == "logscale":
+                cb[0] += -2.4
+            if name == "rot":
+                cb[0, :, 0] += 1.5
+            if name == "rgb":
+                cb[0] += 0.5
+            groups[name] = synth.Group(d, codebook=cb, idx=rng.integers(0, K, (L, n), dtype=np.uint8))
+    else:
+        groups = {
+            "logscale": synth.Group(3, raw=rng.uniform(-2.6, -2.2, (n, 3)).astype(np.float32)),
+            "rot": synth.Group(4, raw=synth.random_quats(rng, n).astype(np.float32)),
+            "opacity": synth.Group(1, raw=rng.normal(0, 0.7, (n, 1)).astype(np.float32)),
+            "rgb": synth.Group(3, raw=rng.uniform(0, 1, (n, 3)).astype(np.float32)),
+        }
+    mask = None
+    if with_mask:
+        mask = rng.uniform(1, 3, n).astype(np.float32)
+        mask[1] = -2.0
+    return synth.Scene(xyz, l, off, groups, mask, 0.5)
+
+
+def fd_cams(n_views, off_screen=False):
+    cams = []
+    rng = np.random.default_rng(40)
+    for v in range(n_views):
+        T = synth.perturb_pose(synth.identity_pose(), rng, 3.0, 0.03) if v else synth.identity_pose()
+        cams.append(cam(40.0, 40.0, 7.5, 7.5, 16, 16, T))
+    return cams
+
+
+def _arrays(scene):
+    arr = dict(anchor_xyz=scene.anchor_xyz, anchor_l=scene.anchor_l, offsets=scene.offsets)
+    for name, g in scene.groups.items():
+        arr[("cb_" if g.coded else "raw_") + name] = g.codebook if g.coded else g.raw
+    return {k: np.asarray(v, np.float64) for k, v in arr.items()}
+
+
+def _objective(scene, cams, ups, overrides):
+    o = O.Oracle(scene, cams, overrides=overrides)
+    f = o.forward()
+    assert not np.any(f["flags"]), "finite differences crossed a threshold"
+    return float(ups[0] @ f["C"] + ups[1] @ f["D"] + ups[2] @ f["S"])
+
+
+def _fd_check(scene, cams, names=None, h=1e-6, rtol=2e-5):
+    o = O.Oracle(scene, cams)
+    f = o.forward()
+    assert f["S"].max() > 0.5 and not np.any(f["flags"])
+    ups = synth.upstream_grads(99, o.n_pixels, scale=o.n_pixels)
+    ups = [u.astype(np.float64) for u in ups]
+    grads = o.backward(*ups)
+    base = _arrays(scene)
+    key = {"anchor_xyz": "anchor_xyz", "anchor_l": "anchor_l", "offsets": "offsets"}
+    for name in (names or base):
+        arr = base[name]
+        g = grads[key[name]] if name in key else grads[name.split("_", 1)[1]]
+        assert g.shape == arr.shape, name
+        fd = np.zeros(arr.size)
+        for j in range(arr.size):
+            hp = h * max(1.0, abs(arr.flat[j]))
+            a1 = arr.copy(); a1.flat[j] += hp
+            a2 = arr.copy(); a2.flat[j] -= hp
+            fd[j] = (_objective(scene, cams, ups, {name: a1}) - _objective(scene, cams, ups, {name: a2})) / (2 * hp)
+        scale = max(1e-6, np.abs(fd).max())
+        assert np.abs(fd - g.ravel()).max() <= rtol * scale, (name, fd, g.ravel())
+    return o, ups, grads
+
+
+@pytest.mark.parametrize("coded", [False, True])
+def test_fd_scene_parameters(coded):
+    sc = fd_scene(coded, seed=31 if coded else 30)
+    _fd_check(sc, fd_cams(1))
+
+
+def test_fd_two_views_and_pose():
+    sc = fd_scene(False, seed=32)
+    cams = fd_cams(2)
+    o, ups, grads = _fd_check(sc, cams, names=["anchor_xyz", "raw_rot", "raw_logscale"])
+    h = 1e-6
+    for v in range(2):
+        T0 = np.eye(4)
+        T0[:3, :] = np.asarray(cams[v].T_cw, np.float64)
+        for k in range(6):
+            xi = np.zeros(6)
+            xi[k] = h
+            Ts = []
+            for sgn in (1, -1):
+                X = np.zeros((4, 4))
+                rho, phi = sgn * xi[:3], sgn * xi[3:]
+                X[:3, :3] = [[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]]
+                X[:3, 3] = rho
+                Tv = [np.asarray(c.T_cw, np.float64) for c in cams]
+                Tv[v] = (expm(X) @ T0)[:3, :]
+                Ts.append(_objective(sc, cams, ups, {"T_cw": Tv}))
+            fd = (Ts[0] - Ts[1]) / (2 * h)
+            assert abs(fd - grads["pose"][v, k]) <= 2e-5 * max(1e-6, np.abs(grads["pose"][v]).max()), (v, k)
+
+
+def test_fd_jacobian_clamp_branch():
+    """A Gaussian whose centre lies off screen beyond the clamp still reaches
+    the image; the clamped Jacobian's derivative is exact on that branch."""
+    mu = [[-0.45, 0.0, 1.5], [0.02, 0.03, 2.0]]
+    sc = raw_scene(mu, [np.log([0.25, 0.2, 0.2]), np.log([0.06, 0.05, 0.07])],
+                   [[0.9, 0.1, 0.3, -0.2], [1, 0, 0, 0]], [2.0, 0.3], [[0.9, 0.1, 0.2], [0.1, 0.8, 0.3]])
+    cams = [cam(40.0, 40.0, 7.5, 7.5, 16, 16)]
+    o = O.Oracle(sc, cams)
+    proj, _, _ = o.projection()
+    assert proj[0, 10] == 1 and -0.45 / 1.5 < -1.3 * 8 / 40  # clamped in x
+    _fd_check(sc, cams, names=["anchor_xyz", "raw_logscale", "raw_rot"])
+
+
+def test_fd_mask_straight_through():
+    """Eq. 11-12: with hat s = M s and hat alpha = M alpha, the estimator is
+    dL/dm = dL/dM * sigmoid'(m) at M = 1; dL/dM is checked by differencing a
+    continuous multiplier M on s and alpha."""
+    sc = fd_scene(False, seed=33, with_mask=True)
+    cams = fd_cams(1)
+    o = O.Oracle(sc, cams)
+    ups = [u.astype(np.float64) for u in synth.upstream_grads(98, o.n_pixels, scale=o.n_pixels)]
+    grads = o.backward(*ups)
+    base = _arrays(sc)
+    h = 1e-6
+    keep = sc.mask_logit > O.mask_threshold(0.5)
+    assert not keep[1] and grads["mask_logit"][1] == 0.0
+    for n in np.nonzero(keep)[0]:
+        vals = []
+        for M in (1 + h, 1 - h):
+            ls = base["raw_logscale"].copy()
+            ls[n] += math.log(M)
+            op = base["raw_opacity"].copy()
+            a = M / (1 + math.exp(-op[n, 0]))
+            op[n, 0] = math.log(a / (1 - a))
+            vals.append(_objective(sc, cams, ups, {"raw_logscale": ls, "raw_opacity": op}))
+        dM = (vals[0] - vals[1]) / (2 * h)
+        sm = 1 / (1 + math.exp(-float(sc.mask_logit[n])))
+        assert abs(dM * sm * (1 - sm) - grads["mask_logit"][n]) <= 1e-6 * max(1e-3, abs(dM)), n
+
+
+def test_icp_closed_form_identity_pose():
+    rng = np.random.default_rng(8)
+    n = 30
+    mu = rng.normal(0, 1, (n, 3)) + [0, 0, 3]
+    sc = raw_scene(mu, np.full((n, 3), -3.0), [[1, 0, 0, 0]] * n, np.zeros(n), np.full((n, 3), 0.5))
+    c = cam(50, 50, 32, 24, 64, 48)
+    q, w = synth.icp_targets(9, 1, n)
+    loss, dpose = O.Oracle(sc, [c]).icp(q, w)
+    m = mu.astype(np.float32).astype(np.float64)
+    r = m - q[0]
+    assert np.isclose(loss[0], np.sum(w[0][:, None] * r * r), rtol=1e-12)
+    g = 2 * w[0][:, None] * r
+    assert np.allclose(dpose[0, :3], g.sum(0), rtol=1e-12)
+    assert np.allclose(dpose[0, 3:], np.cross(m, g).sum(0), rtol=1e-10, atol=1e-12)
+
+
+def test_icp_pose_gradient_fd():
+    rng = np.random.default_rng(10)
+    n = 20
+    mu = rng.normal(0, 1, (n, 3)) + [0, 0, 3]
+    sc = raw_scene(mu, np.full((n, 3), -3.0), [[1, 0, 0, 0]] * n, np.zeros(n), np.full((n, 3), 0.5))
+    T = synth.perturb_pose(synth.identity_pose(), rng, 5.0, 0.1)
+    c = cam(50, 50, 32, 24, 64, 48, T)
+    q, w = synth.icp_targets(11, 1, n)
+    _, dpose = O.Oracle(sc, [c]).icp(q, w)
+    T0 = np.eye(4)
+    T0[:3] = np.asarray(c.T_cw, np.float64)
+    h = 1e-6
+    for k in range(6):
+        vals = []
+        for sgn in (1, -1):
+            xi = np.zeros(6)
+            xi[k] = sgn * h
+            X = np.zeros((4, 4))
+            X[:3, :3] = [[0, -xi[5], xi[4]], [xi[5], 0, -xi[3]], [-xi[4], xi[3], 0]]
+            X[:3, 3] = xi[:3]
+            Tn = (expm(X) @ T0)[:3]
+            vals.append(O.Oracle(sc, [c], overrides=dict(T_cw=[Tn])).icp(q, w)[0][0])
+        assert abs((vals[0] - vals[1]) / (2 * h) - dpose[0, k]) < 1e-5 * np.abs(dpose).max()
+
+
+def test_loss_l1_matches_definition():
+    rng = np.random.default_rng(12)
+    n = 500
+    C_, Ct = rng.uniform(size=3 * n), rng.uniform(size=3 * n)
+    D_, Dt = rng.uniform(0, 3, n), rng.uniform(0, 3, n)
+    Dt[::7] = 0.0
+    S_ = rng.uniform(size=n)
+    L, dC, dD = O.loss_l1(C_, D_, S_, Ct, Dt, 0.5)
+    valid = Dt > 0
+    ref = np.abs(C_ - Ct).mean() + 0.5 * np.abs(D_ - Dt)[valid].mean()
+    assert np.isclose(L, ref, rtol=1e-13)
+    assert np.allclose(dC, np.sign(C_ - Ct) / (3 * n))
+    assert np.allclose(dD, np.where(valid, 0.5 * np.sign(D_ - Dt) / valid.sum(), 0))
+    Lg, dCg, _ = O.loss_l1(C_, D_, S_, Ct, Dt, 0.5, gate=0.99)
+    gate = np.tile(S_ > 0.99, 3)
+    assert np.allclose(dCg, np.where(gate, np.sign(C_ - Ct) / (3 * n), 0))
