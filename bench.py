@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the mapping step of the voxelized compact 3D-Gaussian SLAM
+rasterizer: forward + backward iterations per second at 1200 x 680 with
+40,000 anchors x 8 = 320k Gaussians (RVQ-coded, 20% masked).
+
+One step = decode + project + bin + depth/tile sort + composite (forward),
+L1 colour + 0.5 L1 depth loss gradient, backward composite with transmittance
+recovered by division, chain rule to anchors / offsets / codebooks / mask
+logits, camera-pose twist gradient, and an Adam step on the map, all on the
+device, through the libvg C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (the step does not
+shard: no collective); value = steps of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd iters/s and Mpix/s at 1200x680, 300k Gaussians; served p50/p99 latency vs 1-at-a-time"
+WORKLOAD = ("mapping step fwd+bwd: 40,000 anchors x 8 = 320,000 Gaussians on a 0.05 m room grid (20% masked), "
+            "RVQ 4 groups x 3 stages x 64 codewords, 1200x680 fx=fy=600, L1 colour + 0.5 L1 depth vs a "
+            "jittered-camera render, Adam on anchors/offsets/l/codebooks/mask logits")
+W_IMG, H_IMG = 1200, 680
+FP32_PEAK_PER_SM_CLK = 128 * 2      # FP32 lanes x 2 FLOP (FMA) per SM per clock
+# algorithmic FP32 FLOPs per pair (FMA = 2), counted from the kernels' source
+FWD_FLOP_EVAL = 14        # offset, quadratic form, exp argument, opacity product, tests
+FWD_FLOP_BLEND = 12       # transmittance update, 4 FMA accumulations, silhouette
+BWD_FLOP_WALK = 14        # per walked pair: offset, quadratic form, exp argument, opacity product
+BWD_FLOP_BLEND = 49       # per blended pair: T recovery, dL/dalpha, colour/depth/opacity/conic/mean partials
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def env_dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        if which == "begin":
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        recs = []
+        for ts, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                recs.append(dict(ts=ts, sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        inside = [r for r in recs if self.t0 and self.t1 and self.t0 - 0.1 <= r["ts"] <= self.t1 + 0.1]
+        use = inside if inside else recs[-3:]
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        reasons = set()
+        for r in use:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in use), "sm_max_mhz": max(r["smax"] for r in use),
+                "reasons": sorted(reasons), "samples": len(use), "in_timed_region": bool(inside),
+                "power_w_max": max(r["power"] for r in use)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def build_workload(torch, V, synth):
+    scene = synth.room_scene()
+    cam = synth.room_camera()
+    tcam = synth.room_camera(pose_seed=7, jitter_deg=1.0, jitter_m=0.02)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tt = lambda a: torch.from_numpy(a).to(dev)
+    # map parameters live in torch tensors that the library borrows, so the
+    # Adam step updates them in place between iterations
+    dscene = synth.Scene(tt(scene.anchor_xyz), tt(scene.anchor_l), tt(scene.offsets),
+                         {k: synth.Group(g.dim, codebook=tt(g.codebook), idx=tt(g.idx)) for k, g in scene.groups.items()},
+                         tt(scene.mask_logit), scene.mask_eps)
+    sh = V.vg_scene_upload(dscene, V.VG_SCENE_BORROW)
+    ctx = V.vg_ctx_create(0)
+    params = V.default_params()
+    # target frame: a render at a jittered camera (fixed during the run)
+    Ct, Dt, _ = V.render_with_retry(sh, [tcam], params, ctx)
+    Ct, Dt = Ct.clone(), Dt.clone()
+    V.render_with_retry(sh, [cam], params, ctx)
+    pairs = V.vg_ctx_stats(ctx)["pairs"]
+    V.vg_ctx_reserve(ctx, int(pairs * 1.5) + 4096)
+    P = W_IMG * H_IMG
+    f32 = dict(dtype=torch.float32, device=dev)
+    bufs = dict(C=torch.empty(3 * P, **f32), D=torch.empty(P, **f32), S=torch.empty(P, **f32),
+                dC=torch.empty(3 * P, **f32), dD=torch.empty(P, **f32), loss=torch.empty(1, **f32),
+                dxi=torch.empty((1, 6), **f32), Ct=Ct, Dt=Dt)
+    grads = V.grads_like(sh)
+    plist = [dscene.anchor_xyz, dscene.anchor_l, dscene.offsets, dscene.mask_logit] + \
+            [dscene.groups[k].codebook for k in V.GROUPS]
+    glist = [grads["anchor_xyz"], grads["anchor_l"], grads["offsets"], grads["mask_logit"]] + \
+            [grads[k] for k in V.GROUPS]
+    ms = [torch.zeros_like(p) for p in plist]
+    vs = [torch.zeros_like(p) for p in plist]
+    step_dev = torch.ones(1, dtype=torch.int32, device=dev)
+    return dict(scene=scene, cam=cam, tcam=tcam, sh=sh, ctx=ctx, params=params, bufs=bufs, grads=grads,
+                plist=plist, glist=glist, ms=ms, vs=vs, step_dev=step_dev, P=P)
+
+
+def make_step(V, w):
+    b, sh, ctx, params, cams = w["bufs"], w["sh"], w["ctx"], w["params"], [w["cam"]]
+
+    def step():
+        V.vg_render_fwd(sh, cams, params, ctx, b["C"], b["D"], b["S"])
+        V.vg_loss_l1(1, w["P"], b["C"], b["D"], b["S"], b["Ct"], b["Dt"], 0.5, -1.0, ctx, dC=b["dC"], dD=b["dD"],
+                     loss=b["loss"])
+        V.vg_render_bwd(sh, cams, params, ctx, b["dC"], b["dD"], None, w["grads"])
+        V.vg_pose_grad(ctx, 1, dxi=b["dxi"])
+        V.vg_adam_step(w["plist"], w["glist"], w["ms"], w["vs"], 1e-4, step_dev=w["step_dev"])
+    return step
+
+
+# ---------------------------------------------------------------------------
+# the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_iteration(O, synth, scene, cam, tcam, threads, band_rows=None):
+    """One oracle fwd+bwd iteration (target render, forward, L1 loss,
+    backward) on a horizontal band of the image (full image if None);
+    returns the fraction of the image it covered."""
+    import numpy as np
+    if band_rows is not None and band_rows < cam.height:
+        y0 = (cam.height - band_rows) // 2
+        band = lambda c: synth.camera(c.fx, c.fy, c.cx, c.cy - y0, c.width, band_rows, c.T_cw, c.near)
+        cam, tcam = band(cam), band(tcam)
+    t = O.Oracle(scene, [tcam]).forward(threads=threads)
+    o = O.Oracle(scene, [cam])
+    f = o.forward(threads=threads)
+    _, dC, dD = O.loss_l1(f["C"], f["D"], f["S"], t["C"], t["D"], 0.5)
+    o.backward(dC, dD, np.zeros_like(f["S"]), threads=threads)
+    return cam.height / float(H_IMG)
+
+
+def cpu_baseline(O, synth, scene, cam, tcam, budget_s=15.0):
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    frac = oracle_iteration(O, synth, scene, cam, tcam, threads, band_rows=H_IMG // 8)
+    first = time.perf_counter() - t0
+    iters, work = 1, frac
+    while time.perf_counter() - t0 + first < budget_s:
+        work += oracle_iteration(O, synth, scene, cam, tcam, threads, band_rows=H_IMG // 8)
+        iters += 1
+    dt = time.perf_counter() - t0
+    return {"value": work / dt, "unit": "iters/s", "cores": threads, "kind": "oracle",
+            "sample": f"{iters} oracle fwd+bwd iterations on a {H_IMG // 8}-row band (1/8) of the 1200x680 image "
+                      f"(full 320k-Gaussian scene decoded and binned each time), scaled to full images; "
+                      f"{dt:.1f} s on {threads} OpenMP threads"}
+
+
+def run_reference(args):
+    rank, world, _ = env_dist()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2403_11247_b300 import synth
+    O.build()
+    scene = synth.room_scene()
+    cam = synth.room_camera()
+    tcam = synth.room_camera(pose_seed=7, jitter_deg=1.0, jitter_m=0.02)
+    threads = os.cpu_count() or 1
+    # size the per-step band so that warmup + steps end within ~3 minutes
+    t0 = time.perf_counter()
+    oracle_iteration(O, synth, scene, cam, tcam, threads, band_rows=H_IMG // 8)
+    per_band = time.perf_counter() - t0
+    total = max(1, args.steps + args.warmup)
+    rows = int(min(H_IMG, max(16, H_IMG // 8 * (150.0 / (total * per_band)))))
+    for _ in range(args.warmup):
+        oracle_iteration(O, synth, scene, cam, tcam, threads, band_rows=rows)
+    work = 0.0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        work += oracle_iteration(O, synth, scene, cam, tcam, threads, band_rows=rows)
+    dt = time.perf_counter() - t0
+    value = work / dt
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / max(1, args.steps),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample_rows": rows},
+           "cpu_baseline": {"value": value, "unit": "iters/s", "cores": threads, "kind": "oracle",
+                            "sample": f"each step: one oracle fwd+bwd on a {rows}-row band of the 1200x680 image, "
+                                      f"scaled to full images"},
+           "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    rank, world, local = env_dist()
+    import torch
+    from paper_2403_11247_b300 import build as B
+    from paper_2403_11247_b300 import synth
+    from paper_2403_11247_b300 import vg as V
+
+    B.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = build_workload(torch, V, synth)
+    step = make_step(V, w)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 126 MB L2
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    st = V.vg_check(w["ctx"])
+    if st != V.VG_OK:
+        raise RuntimeError(f"device status {V.STATUS_NAMES[st]} during warmup")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    V.vg_ctx_profile(w["ctx"], True)
+    V.vg_ctx_reset_counters(w["ctx"])
+    params_count = V.default_params(count_evals=1)
+    w["params"] = params_count
+    step = make_step(V, w)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = V.vg_launch_count()
+    sampler.mark("begin")
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    sampler.mark("end")
+    if dist:
+        dist.barrier()
+    launches = V.vg_launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    prof = V.vg_ctx_profile_read(w["ctx"])
+    V.vg_ctx_profile(w["ctx"], False)
+    stats = V.vg_ctx_stats(w["ctx"])
+    status = V.vg_check(w["ctx"])
+    clocks = sampler.stop()
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    if status != V.VG_OK:
+        raise RuntimeError(f"device status {V.STATUS_NAMES[status]} in the timed region: run invalid")
+
+    value = world * args.steps / (total_ms / 1000.0)
+    mpix = value * W_IMG * H_IMG / 1e6
+
+    # roofline of the dominant stage, timed with events on the launching stream
+    peaks, src = measured_peaks()
+    dom = max((s for s in prof if s != "memset"), key=lambda s: prof[s][0])
+    ms_dom, n_dom = prof[dom]
+    per_launch_s = ms_dom / 1000.0 / max(1, n_dom)
+    sm_mhz = peaks.get("sm_max_mhz", 2032.0)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    alu_peak = n_sm * FP32_PEAK_PER_SM_CLK * sm_mhz * 1e6 / 1e12   # TFLOP/s
+    K = max(1, args.steps)
+    if dom == "blend_bwd":
+        walked, blended = stats["bwd_pairs"] / K, stats["blended"] / K
+        flops = BWD_FLOP_WALK * walked + BWD_FLOP_BLEND * blended
+        roof = {"bound": "alu", "achieved": flops / per_launch_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                "traffic": None, "kernel": "blend_bwd_kernel",
+                "work": f"{walked:.4g} walked + {blended:.4g} blended pairs per launch"}
+    elif dom == "blend_fwd":
+        ev, blended = stats["evaluated"] / K, stats["blended"] / K
+        flops = FWD_FLOP_EVAL * ev + FWD_FLOP_BLEND * blended
+        roof = {"bound": "alu", "achieved": flops / per_launch_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                "traffic": None, "kernel": "blend_fwd_kernel",
+                "work": f"{ev:.4g} evaluated + {blended:.4g} blended pairs per launch"}
+    else:
+        n = 320000
+        byts = {"preprocess": 79 * n, "chain": 100 * n}.get(dom, 0)
+        roof = {"bound": "hbm", "achieved": byts / per_launch_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "traffic": None, "kernel": dom}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["peak_source"] = ("derived: %d SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz (max SM clock, %s peaks file)"
+                           % (n_sm, sm_mhz, src)) if roof["bound"] == "alu" else f"{src} hbm_gbs"
+    roof["ms_per_launch"] = per_launch_s * 1000.0
+
+    # end to end through the public API: the target frame goes up from pinned
+    # host memory each step, the loss and the pose gradient come back
+    e2e = None
+    if True:
+        b = w["bufs"]
+        Ct_h = b["Ct"].cpu().pin_memory()
+        Dt_h = b["Dt"].cpu().pin_memory()
+        out_h = torch.empty(7, dtype=torch.float32).pin_memory()
+        w["params"] = V.default_params()
+        step = make_step(V, w)
+        n_e2e = max(3, min(args.steps, 200))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            b["Ct"].copy_(Ct_h, non_blocking=True)
+            b["Dt"].copy_(Dt_h, non_blocking=True)
+            step()
+            out_h[0:1].copy_(b["loss"], non_blocking=True)
+            out_h[1:7].copy_(b["dxi"].view(-1), non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": world * n_e2e / dt, "unit": "iters/s", "h2d_bytes_per_step": Ct_h.numel() * 4 + Dt_h.numel() * 4,
+               "d2h_bytes_per_step": 7 * 4, "steps": n_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        cpu = cpu_baseline(O, synth, w["scene"], w["cam"], w["tcam"])
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MB write, outside the step events)",
+                           "parallelism": f"replicas x{world}", "pairs_per_step": stats["pairs"]},
+                "mpix_per_s": mpix, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "launches_per_step": launches / max(1, args.steps), "clocks": clocks,
+                "stages_ms_per_step": {k: v[0] / K for k, v in prof.items()},
+                "p50_step_ms": statistics.median(step_ms), "p99_step_ms": sorted(step_ms)[int(0.99 * (len(step_ms) - 1))]}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,321 @@
+/*
+ * vg.h -- C ABI of libvg, a B300 (sm_103a) differentiable tile rasterizer for
+ * voxel-anchored, residual-codebook-coded, mask-pruned 3D Gaussians
+ * (Deng et al., "Voxelized 3D Gaussian Representation for Dense Visual SLAM
+ * on Embedded Vision System").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Pointers.  Unless a parameter says "host", every array argument is a DEVICE
+ *   pointer of the current CUDA device, allocated and owned by the caller.
+ *   libvg owns only what it allocates itself: a vg_scene made by
+ *   vg_scene_upload with VG_SCENE_COPY and a vg_ctx; each is released by its
+ *   _free call.
+ * Layout.  Float arrays are IEEE FP32, little-endian, dense, row-major (C
+ *   order).  Images of a multi-view call are per-view planar blocks laid end to
+ *   end in view order: view v owns pixels [pb_v, pb_v + W_v*H_v), pb_v the sum
+ *   of W*H over earlier views; colour holds three planes per view
+ *   (C + 3*pb_v: R plane, G plane, B plane, each H_v rows of W_v), depth and
+ *   silhouette one plane.  With equal sizes this is [B][3][H][W] and [B][H][W].
+ * Streams.  Every call enqueues its work on the given stream and returns
+ *   without synchronising, except vg_scene_upload (which synchronises its
+ *   stream before returning) and vg_check / vg_ctx_stats (which synchronise
+ *   the stream to read device status).
+ * Errors.  Argument errors are detected on the host before anything is
+ *   enqueued and return VG_ERR_INVALID_ARG.  A failed CUDA call returns
+ *   VG_ERR_CUDA.  Conditions found on the device (the pair buffer of the ctx
+ *   too small, a bounded wait that ran out) set a flag in the ctx and leave the
+ *   outputs of that call undefined; the next vg_check returns VG_ERR_CAPACITY
+ *   or VG_ERR_TIMEOUT and clears the flag.  vg_last_error() gives a message for
+ *   the calling thread's last non-OK status.
+ * Threads.  One vg_ctx per stream; a vg_scene may be shared by calls on
+ *   several streams as long as nothing writes it meanwhile.
+ */
+#ifndef VG_H
+#define VG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* vg_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    VG_OK = 0,
+    VG_ERR_INVALID_ARG = 1,
+    VG_ERR_OOM = 2,
+    VG_ERR_CUDA = 3,
+    VG_ERR_CAPACITY = 4,
+    VG_ERR_TIMEOUT = 5,
+    VG_ERR_UNIMPLEMENTED = 6
+} vg_status;
+
+#define VG_TILE 16          /* tile side in pixels (the only supported value) */
+#define VG_MAX_VIEWS 64     /* views per launch */
+#define VG_MAX_CODEWORDS 256 /* 1-byte indices */
+
+/* Pinhole camera.  T_cw: row-major 3x4 world->camera transform [R | t];
+ * camera x right, y down, z forward.  A point projects to
+ * u = fx * x / z + cx, v = fy * y / z + cy (pixel (px, py) is sampled at
+ * integer coordinates).  Gaussians with camera depth z <= near_plane are
+ * culled. */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float T_cw[12];
+    float near_plane;
+} vg_camera;
+
+/* One attribute group of the Gaussians (Sec. "Residual Codebook
+ * Quantization", Eq. 14 first line: the attribute of Gaussian n is the sum,
+ * over stages s = 0..L-1 in order, of codebook[s][idx[s][n]]; 1-byte indices).
+ * stages == 0 selects raw per-Gaussian values instead.
+ *   dim        values per Gaussian (log-scale 3, quaternion 4, opacity 1, RGB 3)
+ *   stages     L (0 = raw)
+ *   codewords  K, 1..256
+ *   codebook   [L][K][dim] FP32
+ *   idx        [L][N] uint8, stage-major
+ *   raw        [N][dim] FP32 when stages == 0 */
+typedef struct {
+    int32_t dim;
+    int32_t stages;
+    int32_t codewords;
+    const float* codebook;
+    const uint8_t* idx;
+    const float* raw;
+} vg_attr_group;
+
+/* Scene (Sec. "Voxel-Anchored 3D Gaussian Representation", Eq. 7): anchors
+ * with position x_a, scaling factor l and k offsets O_i; Gaussian n = a*k + i
+ * sits at mu_n = x_a + O_i * l (element-wise).  Attributes: log-scale
+ * (scale = exp), quaternion (w, x, y, z; normalised before use), opacity
+ * logit (opacity = sigmoid), RGB (used as is).  Online mask (Eq. 11-12):
+ * Gaussian n is kept iff sigmoid(mask_logit[n]) > mask_eps, evaluated as
+ * mask_logit[n] > logit(mask_eps) rounded to FP32; a removed Gaussian renders
+ * exactly as if deleted.  mask_logit may be NULL (all kept). */
+typedef struct {
+    int64_t n_anchors;
+    int32_t k;
+    const float* anchor_xyz; /* [Na][3] */
+    const float* anchor_l;   /* [Na][3] */
+    const float* offsets;    /* [Na][k][3] */
+    vg_attr_group logscale, rot, opacity, rgb;
+    const float* mask_logit; /* [N] or NULL */
+    float mask_eps;
+} vg_scene_desc;
+
+/* Per-pixel compositing constants (readings of Eq. 16-18; the paper leaves
+ * them open):
+ *   alpha(p) = min(alpha_max, o * exp(-1/2 d^T Sigma'^-1 d)), d = (u,v) - p;
+ *   a Gaussian with alpha < alpha_min, or with positive exponent, is skipped;
+ *   compositing stops before a Gaussian that would bring transmittance below
+ *   t_min (that Gaussian is not blended);
+ *   Sigma' gets `dilation` px^2 added to its diagonal;
+ *   radius r = ceil(sigma_cull * sqrt(lambda_max(Sigma'))), tile rect
+ *   [floor((u-r)/16), floor((u+r)/16)+1) x [same for v], clipped to the image;
+ *   with jacobian_clamp, x/z and y/z inside the projection Jacobian are
+ *   clamped to +-clamp_factor * (W/2)/fx and +-clamp_factor * (H/2)/fy.
+ * batch: Gaussians staged per shared-memory batch in the blend kernels
+ *   (0 = default 256).
+ * pose_dev: optional DEVICE array [n_views][12] read instead of the
+ *   cameras' T_cw (lets a captured CUDA graph follow poses updated on the
+ *   device).  count_evals: accumulate evaluated (pixel, Gaussian) pairs into
+ *   the ctx counter (vg_ctx_stats). */
+typedef struct {
+    int32_t tile;
+    int32_t batch;
+    float alpha_max, alpha_min, t_min, dilation, sigma_cull, clamp_factor;
+    int32_t jacobian_clamp;
+    int32_t count_evals;
+    const float* pose_dev;
+} vg_render_params;
+
+/* Gradient outputs of vg_render_bwd (DEVICE pointers, caller-allocated; each
+ * may be NULL to skip it; every non-NULL array is fully overwritten):
+ *   anchor_xyz [Na][3], anchor_l [Na][3], offsets [Na][k][3];
+ *   per attribute group: [L][K][dim] codebook gradient for a coded group,
+ *   [N][dim] for a raw group; mask_logit [N] (straight-through estimator of
+ *   Eq. 11: dL/dm = (sum_j dL/ds_j s_j + dL/do o) sigmoid'(m) for kept
+ *   Gaussians, 0 for removed ones). */
+typedef struct {
+    float* anchor_xyz;
+    float* anchor_l;
+    float* offsets;
+    float* logscale;
+    float* rot;
+    float* opacity;
+    float* rgb;
+    float* mask_logit;
+} vg_scene_grads;
+
+/* Device counters of a ctx, read by vg_ctx_stats. */
+typedef struct {
+    int64_t pairs;          /* (Gaussian, tile) pairs of the last forward */
+    int64_t pair_capacity;  /* current pair buffer size */
+    int64_t visible;        /* (view, Gaussian) slots that reached a tile */
+    int64_t evaluated;      /* forward: (pixel, Gaussian) pairs examined, accumulated while count_evals */
+    int64_t blended;        /* forward: pairs blended, accumulated while count_evals */
+    int64_t bwd_pairs;      /* backward: pairs walked (sum of per-pixel list lengths), while count_evals */
+    uint32_t flags;         /* bit0 bounded wait ran out, bit1 pair overflow */
+} vg_stats;
+
+typedef struct vg_scene vg_scene;
+typedef struct vg_ctx vg_ctx;
+
+#define VG_SCENE_COPY 0   /* copy every array (host or device source) into libvg-owned device memory */
+#define VG_SCENE_BORROW 1 /* keep the caller's device pointers; values may change between calls */
+
+/* Make a device-resident scene from `desc` (a HOST struct).  COPY: arrays may
+ * be host or device pointers; they are copied, and the call synchronises
+ * `stream` before returning.  BORROW: arrays must be device pointers that stay
+ * valid until vg_scene_free; the caller may update their values in place
+ * (e.g. an optimiser step) but not their sizes or index arrays.  Both forms
+ * build, once, the per-stage codeword-to-Gaussian lists used to reduce
+ * codebook gradients.  Errors: VG_ERR_INVALID_ARG (null or inconsistent
+ * sizes, k < 1, K > 256, dims other than 3/4/1/3), VG_ERR_OOM, VG_ERR_CUDA. */
+vg_status vg_scene_upload(const vg_scene_desc* desc, int32_t flags, vg_stream stream, vg_scene** out);
+vg_status vg_scene_free(vg_scene* scene);
+/* Number of Gaussians (n_anchors * k). */
+int64_t vg_scene_size(const vg_scene* scene);
+
+/* Workspace for the render calls: per-(view, Gaussian) records, sort
+ * buffers, per-pixel state kept from forward to backward, device counters.
+ * Sizes are hints; slot, pixel and tile buffers grow on demand (outside
+ * stream capture), the pair buffer grows only through vg_ctx_reserve. */
+vg_status vg_ctx_create(int64_t pair_capacity, vg_ctx** out);
+vg_status vg_ctx_free(vg_ctx* ctx);
+/* Grow the pair buffer to at least `pair_capacity` (no-op if large enough). */
+vg_status vg_ctx_reserve(vg_ctx* ctx, int64_t pair_capacity);
+/* Synchronise `stream`, read the counters into *out (may be NULL), return
+ * VG_ERR_CAPACITY / VG_ERR_TIMEOUT if a device flag is set (and clear it),
+ * else VG_OK. */
+vg_status vg_check(vg_ctx* ctx, vg_stream stream);
+vg_status vg_ctx_stats(vg_ctx* ctx, vg_stream stream, vg_stats* out);
+/* Zero the evaluated / blended / backward pair counters (enqueued). */
+vg_status vg_ctx_reset_counters(vg_ctx* ctx, vg_stream stream);
+
+/* Per-stage timing with CUDA events recorded on the launching stream around
+ * every kernel a render / loss / pose call enqueues.  vg_ctx_profile(ctx, 1)
+ * clears the records and starts recording, 0 stops.  vg_ctx_profile_read
+ * synchronises `stream` and writes, for each stage id s < VG_STAGE_COUNT,
+ * ms_total[s] (sum of event-to-event durations) and launches[s]. */
+enum {
+    VG_STAGE_PREPROCESS = 0, VG_STAGE_DEPTH_SORT, VG_STAGE_DUPLICATE, VG_STAGE_TILE_SORT, VG_STAGE_RANGES,
+    VG_STAGE_BLEND_FWD, VG_STAGE_LOSS, VG_STAGE_BLEND_BWD, VG_STAGE_CHAIN, VG_STAGE_CODEBOOK, VG_STAGE_POSE,
+    VG_STAGE_MEMSET, VG_STAGE_COUNT
+};
+vg_status vg_ctx_profile(vg_ctx* ctx, int32_t enable);
+vg_status vg_ctx_profile_read(vg_ctx* ctx, vg_stream stream, double* ms_total, int64_t* launches);
+
+/* Read-only view of an intermediate workspace array, for inspection and
+ * tests.  Valid after the call that fills it and until the next render call
+ * on the ctx; the ctx keeps ownership.  *ptr gets the device address and
+ * *bytes the number of valid bytes (pair arrays: capacity bytes; the valid
+ * count is vg_stats.pairs).
+ *   VG_BUF_XY         float2 [slots]  projected mean (u, v)   (slot = view*N + n)
+ *   VG_BUF_CONIC      float4 [slots]  inverse 2D covariance a, b, c and opacity
+ *   VG_BUF_RGBD       float4 [slots]  r, g, b, camera depth
+ *   VG_BUF_RECT       uint2  [slots]  tile rect x0|y0<<16, x1|y1<<16
+ *   VG_BUF_NTILES     uint32 [slots]  tiles touched (0 = culled)
+ *   VG_BUF_PAIR_KEYS  uint32 [pairs]  sorted global tile ids
+ *   VG_BUF_PAIR_VALS  uint32 [pairs]  slot of each sorted pair
+ *   VG_BUF_RANGES     uint2  [tiles]  [start, end) of each tile's list
+ *   VG_BUF_T_FINAL    float  [pixels] transmittance after compositing
+ *   VG_BUF_N_CONTRIB  uint32 [pixels] list position + 1 of the last blended Gaussian
+ *   VG_BUF_G2D        float  [slots][10] du dv da db dc dopacity dr dg db ddepth */
+enum {
+    VG_BUF_XY = 0, VG_BUF_CONIC, VG_BUF_RGBD, VG_BUF_RECT, VG_BUF_NTILES, VG_BUF_PAIR_KEYS, VG_BUF_PAIR_VALS,
+    VG_BUF_RANGES, VG_BUF_T_FINAL, VG_BUF_N_CONTRIB, VG_BUF_G2D
+};
+vg_status vg_ctx_buffer(const vg_ctx* ctx, int32_t which, const void** ptr, int64_t* bytes);
+
+/* Eq. 14, first line, standalone: out[n][c] = sum_s codebook[s][idx[s][n]][c]
+ * summed in stage order, for n < n_items.  `group` is a HOST struct with
+ * device arrays; out is [n_items][dim].  A raw group (stages == 0) is copied. */
+vg_status vg_rvq_decode(const vg_attr_group* group, int64_t n_items, float* out, vg_stream stream);
+
+/* Forward render of n_views (1..64) cameras (HOST array) of one scene in one
+ * launch sequence: decode (Eq. 7, 11-12, 14) and project (Eq. 2-3) every
+ * Gaussian for every view, bin (Gaussian, tile) pairs and order each tile's
+ * list by (FP32 depth, Gaussian index), composite front to back (Eq. 16-18):
+ *   C(p) = sum_i c_i a_i T_i,  D(p) = sum_i z_i a_i T_i,  S(p) = sum_i a_i T_i,
+ *   T_i = prod_{j<i} (1 - a_j), background 0.
+ * C, D, S: output images (layout above); D is not normalised by S.  The ctx
+ * keeps what vg_render_bwd needs (final transmittance, last contributor per
+ * pixel, the sorted lists); do not reuse the ctx for another forward before
+ * the matching backward. */
+vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views, const vg_render_params* params,
+                        vg_ctx* ctx, float* C, float* D, float* S, vg_stream stream);
+
+/* Backward of the last vg_render_fwd on this ctx (same scene, cameras,
+ * params) for upstream images dC, dD, dS (same layout as C, D, S; any may be
+ * NULL = zero).  Per-pixel transmittance is recovered back to front from the
+ * final transmittance by division, not stored per step.  Writes the scene
+ * gradients (*grads, HOST struct of device pointers) and keeps per-view pose
+ * partial sums in the ctx for vg_pose_grad. */
+vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views, const vg_render_params* params,
+                        vg_ctx* ctx, const float* dC, const float* dD, const float* dS,
+                        const vg_scene_grads* grads, vg_stream stream);
+
+/* Camera pose gradients of the last vg_render_bwd, for the left
+ * perturbation T_cw <- exp(xi^) T_cw, xi = (rho, phi): dxi [n_views][6]
+ * (rho then phi).  Optional ICP term (Eq. 20): with icp_q [n_views][N][3]
+ * (camera-frame targets) and icp_w [n_views][N] (weights, 0 = none), adds
+ * the gradient of sum_n w_n |R mu_n + t - q_n|^2 over kept Gaussians and
+ * writes that loss per view to icp_loss [n_views] (may be NULL).  Pass
+ * icp_q = NULL to skip it. */
+vg_status vg_pose_grad(vg_ctx* ctx, int32_t n_views, const float* icp_q, const float* icp_w,
+                       float* dxi, float* icp_loss, vg_stream stream);
+
+/* Upstream gradients of L = mean|C - Ct| + w_depth * mean_{Dt>0}|D - Dt| over
+ * n_views views of n_pix pixels each (C, Ct: [n_views][3][n_pix]; D, Dt, S:
+ * [n_views][n_pix]); with gate >= 0 only pixels with S > gate contribute
+ * (Eq. 21), normalisers unchanged.  Writes dC, dD (dS is zeroed if non-NULL)
+ * and the loss value to loss[0] (device float).  sign(0) = 0. */
+vg_status vg_loss_l1(int32_t n_views, int64_t n_pix, const float* C, const float* D, const float* S,
+                     const float* Ct, const float* Dt, float w_depth, float gate,
+                     float* dC, float* dD, float* dS, float* loss, vg_ctx* ctx, vg_stream stream);
+
+/* One Adam step (Kingma & Ba) on up to 16 FP32 arrays in one launch:
+ *   m = b1 m + (1-b1) g ; v = b2 v + (1-b2) g^2 ;
+ *   p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+ * `tensors` is a HOST array of n_tensors records of device pointers (m and v
+ * caller-allocated, zero before the first step).  The step number t comes
+ * from step_dev[0] when step_dev is non-NULL (then incremented on the device,
+ * so a captured graph advances it on every replay), else from step_host. */
+typedef struct {
+    float* param;
+    const float* grad;
+    float* m;
+    float* v;
+    int64_t n;
+} vg_adam_tensor;
+vg_status vg_adam_step(const vg_adam_tensor* tensors, int32_t n_tensors, float lr, float beta1, float beta2, float eps,
+                       int32_t* step_dev, int32_t step_host, vg_stream stream);
+
+/* Adam step on camera poses from their twist gradients dxi [n_views][6]
+ * (rho, phi for the left perturbation exp(xi^) T_cw): the Adam direction d
+ * (scaled by lr_trans for rho and lr_rot for phi) moves each pose to
+ * T_cw <- exp(-d^) T_cw.  pose [n_views][12] row-major 3x4, m and v
+ * [n_views][6] (zero before the first step); step as in vg_adam_step. */
+vg_status vg_pose_step(int32_t n_views, float* pose, const float* dxi, float* m, float* v, float lr_rot,
+                       float lr_trans, float beta1, float beta2, float eps, int32_t* step_dev, int32_t step_host,
+                       vg_stream stream);
+
+/* Number of CUDA kernels libvg has enqueued in this process (host count). */
+int64_t vg_launch_count(void);
+
+/* Message for the calling thread's last non-OK status ("" if none). */
+const char* vg_last_error(void);
+
+/* Default compositing constants (alpha_max 0.99, alpha_min 1/255, t_min 1e-4,
+ * dilation 0.3, sigma_cull 3, clamp_factor 1.3, jacobian_clamp 1, tile 16). */
+vg_render_params vg_default_params(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VG_H */

@@ -93,7 +93,7 @@ def _p(a: Optional[np.ndarray]):
 
 def default_params(**kw) -> Dict[str, float]:
     p = dict(alpha_max=0.99, alpha_min=1.0 / 255.0, t_min=1e-4, dilation=0.3, sigma_cull=3.0,
-             clamp_factor=1.3, jacobian_clamp=1, tile=16, r_band=2e-5, decision_band=1e-5)
+             clamp_factor=1.3, jacobian_clamp=1, tile=16, r_band=5e-6, decision_band=1e-5)
     p.update(kw)
     return p
 

@@ -1,0 +1,791 @@
+// vg_api.cu -- the extern "C" boundary of libvg (declared in include/vg.h):
+// argument checks, ownership of scenes and workspaces, and the launch
+// sequence of each call.  Nothing here synchronises the stream except
+// vg_scene_upload, vg_check and vg_ctx_stats.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vg.h"
+#include "vg_internal.h"
+
+using namespace vgk;
+
+#include <atomic>
+
+namespace vgk {
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace vgk
+
+namespace {
+
+thread_local std::string g_err;
+
+vg_status fail(vg_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define VG_CUDA(expr)                                                                                   \
+    do {                                                                                                \
+        cudaError_t e_ = (expr);                                                                        \
+        if (e_ != cudaSuccess) return fail(VG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // grow to at least b bytes (contents are not kept)
+    vg_status ensure(size_t b, cudaStream_t st, const char* what) {
+        if (b == 0) b = 16;
+        if (b <= bytes) return VG_OK;
+        if (capturing(st))
+            return fail(VG_ERR_CAPACITY, std::string("workspace buffer '") + what +
+                                             "' must grow, which cannot happen during stream capture; run once "
+                                             "outside capture first");
+        release();
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? VG_ERR_OOM : VG_ERR_CUDA,
+                        std::string("cudaMalloc(") + what + "): " + cudaGetErrorString(e));
+        }
+        bytes = b;
+        return VG_OK;
+    }
+    template <class T>
+    T* as() const { return (T*)p; }
+};
+
+#define VG_TRY(expr)                     \
+    do {                                 \
+        vg_status s_ = (expr);           \
+        if (s_ != VG_OK) return s_;      \
+    } while (0)
+
+constexpr int GDIMS[4] = {3, 4, 1, 3};
+
+// run `expr` (a launch returning cudaError_t) bracketed by profiling events
+#define VG_STAGE(id, expr)                                                     \
+    do {                                                                       \
+        cudaEvent_t e0_ = nullptr;                                             \
+        if (prof_on) {                                                         \
+            e0_ = ctx->prof.get();                                             \
+            if (e0_) cudaEventRecord(e0_, st);                                 \
+        }                                                                      \
+        VG_CUDA(expr);                                                         \
+        if (prof_on && e0_) {                                                  \
+            cudaEvent_t e1_ = ctx->prof.get();                                 \
+            if (e1_) {                                                         \
+                cudaEventRecord(e1_, st);                                      \
+                if (ctx->prof.recs.size() < 200000) ctx->prof.recs.push_back({(id), e0_, e1_}); \
+            }                                                                  \
+        }                                                                      \
+    } while (0)
+const char* GNAMES[4] = {"logscale", "rot", "opacity", "rgb"};
+
+}  // namespace
+
+struct vg_scene {
+    SceneDev dev{};
+    bool owned = false;
+    std::vector<void*> owned_ptrs;
+    DevBuf perm[4], seg[4];
+    ~vg_scene() {
+        for (void* p : owned_ptrs) cudaFree(p);
+    }
+};
+
+// CUDA events around each stage, harvested on demand
+struct StageProfiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    struct Rec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    cudaEvent_t get() {
+        if (used < pool.size()) return pool[used++];
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        pool.push_back(e);
+        ++used;
+        return e;
+    }
+    void reset() {
+        recs.clear();
+        used = 0;
+    }
+    ~StageProfiler() {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+};
+
+struct vg_ctx {
+    StageProfiler prof;
+    int64_t pair_cap = 0;
+    DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, Tfin, ncontrib, lookback,
+        scratch, state, dattr, pose_part, icp_part, loss_scratch;
+    int final_pair = 0;
+    bool have_fwd = false, have_bwd = false;
+    Views views{};
+    int64_t fwd_N = -1;
+    const vg_scene* fwd_scene = nullptr;
+    int pose_blocks = 0;
+    SceneDev bwd_scene{};
+};
+
+extern "C" {
+
+const char* vg_last_error(void) { return g_err.c_str(); }
+
+int64_t vg_launch_count(void) { return (int64_t)g_launches.load(); }
+
+vg_render_params vg_default_params(void) {
+    vg_render_params p;
+    std::memset(&p, 0, sizeof(p));
+    p.tile = VG_TILE;
+    p.batch = 0;
+    p.alpha_max = 0.99f;
+    p.alpha_min = 1.0f / 255.0f;
+    p.t_min = 1e-4f;
+    p.dilation = 0.3f;
+    p.sigma_cull = 3.0f;
+    p.clamp_factor = 1.3f;
+    p.jacobian_clamp = 1;
+    p.count_evals = 0;
+    p.pose_dev = nullptr;
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// scenes
+// ---------------------------------------------------------------------------
+
+static vg_status check_group(const vg_attr_group& g, int gi, int64_t N) {
+    if (g.dim != GDIMS[gi])
+        return fail(VG_ERR_INVALID_ARG, std::string("group ") + GNAMES[gi] + ": dim must be " + std::to_string(GDIMS[gi]));
+    if (g.stages < 0) return fail(VG_ERR_INVALID_ARG, std::string("group ") + GNAMES[gi] + ": stages < 0");
+    if (g.stages > 0) {
+        if (g.codewords < 1 || g.codewords > VG_MAX_CODEWORDS)
+            return fail(VG_ERR_INVALID_ARG, std::string("group ") + GNAMES[gi] + ": codewords must be in 1..256");
+        if (!g.codebook || (N > 0 && !g.idx))
+            return fail(VG_ERR_INVALID_ARG, std::string("group ") + GNAMES[gi] + ": null codebook or idx");
+    } else if (N > 0 && !g.raw) {
+        return fail(VG_ERR_INVALID_ARG, std::string("group ") + GNAMES[gi] + ": null raw array");
+    }
+    return VG_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+vg_status vg_scene_upload(const vg_scene_desc* d, int32_t flags, vg_stream stream, vg_scene** out) {
+    if (!d || !out) return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: null argument");
+    *out = nullptr;
+    if (flags != VG_SCENE_COPY && flags != VG_SCENE_BORROW) return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: bad flags");
+    if (d->n_anchors < 0 || d->k < 1) return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: n_anchors < 0 or k < 1");
+    const int64_t N = d->n_anchors * (int64_t)d->k;
+    if (N >= (int64_t)1 << 30) return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: more than 2^30 Gaussians");
+    if (d->n_anchors > 0 && (!d->anchor_xyz || !d->anchor_l || !d->offsets))
+        return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: null anchor array");
+    const vg_attr_group* gr[4] = {&d->logscale, &d->rot, &d->opacity, &d->rgb};
+    for (int gi = 0; gi < 4; ++gi) VG_TRY(check_group(*gr[gi], gi, N));
+    if (d->mask_logit && !(d->mask_eps > 0.f && d->mask_eps < 1.f))
+        return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: mask_eps must be in (0, 1)");
+    cudaStream_t st = (cudaStream_t)stream;
+
+    vg_scene* sc = new vg_scene();
+    SceneDev& S = sc->dev;
+    S.n_anchors = d->n_anchors;
+    S.k = d->k;
+    S.N = N;
+    S.mask_thr = d->mask_logit ? (float)std::log((double)d->mask_eps / (1.0 - (double)d->mask_eps)) : 0.f;
+
+    auto fin = [&](vg_status s) {
+        if (s != VG_OK) delete sc;
+        return s;
+    };
+    if (flags == VG_SCENE_BORROW) {
+        sc->owned = false;
+        const void* ptrs[] = {d->anchor_xyz, d->anchor_l, d->offsets, d->mask_logit};
+        for (const void* p : ptrs)
+            if (p && !is_device_ptr(p)) return fin(fail(VG_ERR_INVALID_ARG, "VG_SCENE_BORROW needs device pointers"));
+        S.xyz = d->anchor_xyz;
+        S.l = d->anchor_l;
+        S.off = d->offsets;
+        S.mask = d->mask_logit;
+        for (int gi = 0; gi < 4; ++gi) {
+            const vg_attr_group& g = *gr[gi];
+            S.L[gi] = g.stages;
+            S.K[gi] = g.stages > 0 ? g.codewords : 0;
+            S.cb[gi] = g.stages > 0 ? g.codebook : nullptr;
+            S.idx[gi] = g.stages > 0 ? g.idx : nullptr;
+            S.raw[gi] = g.stages > 0 ? nullptr : g.raw;
+            const void* gp[] = {S.cb[gi], S.idx[gi], S.raw[gi]};
+            for (const void* p : gp)
+                if (p && !is_device_ptr(p)) return fin(fail(VG_ERR_INVALID_ARG, "VG_SCENE_BORROW needs device pointers"));
+        }
+    } else {
+        sc->owned = true;
+        auto copy = [&](const void* src, size_t bytes, const void** dst) -> vg_status {
+            *dst = nullptr;
+            if (!src || bytes == 0) return VG_OK;
+            void* p = nullptr;
+            cudaError_t e = cudaMalloc(&p, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(e == cudaErrorMemoryAllocation ? VG_ERR_OOM : VG_ERR_CUDA, "vg_scene_upload: cudaMalloc");
+            }
+            sc->owned_ptrs.push_back(p);
+            VG_CUDA(cudaMemcpyAsync(p, src, bytes, cudaMemcpyDefault, st));
+            *dst = p;
+            return VG_OK;
+        };
+        const size_t Na = (size_t)d->n_anchors;
+        VG_TRY(fin(copy(d->anchor_xyz, Na * 3 * 4, (const void**)&S.xyz)));
+        VG_TRY(fin(copy(d->anchor_l, Na * 3 * 4, (const void**)&S.l)));
+        VG_TRY(fin(copy(d->offsets, (size_t)N * 3 * 4, (const void**)&S.off)));
+        VG_TRY(fin(copy(d->mask_logit, (size_t)N * 4, (const void**)&S.mask)));
+        for (int gi = 0; gi < 4; ++gi) {
+            const vg_attr_group& g = *gr[gi];
+            S.L[gi] = g.stages;
+            S.K[gi] = g.stages > 0 ? g.codewords : 0;
+            if (g.stages > 0) {
+                VG_TRY(fin(copy(g.codebook, (size_t)g.stages * g.codewords * g.dim * 4, (const void**)&S.cb[gi])));
+                VG_TRY(fin(copy(g.idx, (size_t)g.stages * N, (const void**)&S.idx[gi])));
+                S.raw[gi] = nullptr;
+            } else {
+                VG_TRY(fin(copy(g.raw, (size_t)N * g.dim * 4, (const void**)&S.raw[gi])));
+                S.cb[gi] = nullptr;
+                S.idx[gi] = nullptr;
+            }
+        }
+    }
+
+    // per-stage codeword -> Gaussian lists for the codebook-gradient reduction:
+    // one stable 8-bit radix pass of Gaussian ids keyed by their index byte
+    bool any_coded = false;
+    for (int gi = 0; gi < 4; ++gi) any_coded |= (S.L[gi] > 0 && N > 0);
+    if (any_coded) {
+        DevBuf keys, keys_out, hist, lb, state;
+        const int64_t parts = ceil_div(N, SORT_TILE);
+        VG_TRY(fin(keys.ensure((size_t)N * 4, st, "keys")));
+        VG_TRY(fin(keys_out.ensure((size_t)N * 4, st, "keys_out")));
+        VG_TRY(fin(hist.ensure(256 * 4 * 2, st, "hist")));
+        VG_TRY(fin(lb.ensure((size_t)parts * 256 * 8, st, "lookback")));
+        VG_TRY(fin(state.ensure(ST_WORDS * 4, st, "state")));
+        VG_CUDA(cudaMemsetAsync(lb.p, 0, lb.bytes, st));
+        VG_CUDA(cudaMemsetAsync(state.p, 0, state.bytes, st));
+        uint32_t epoch_off = 1;
+        for (int gi = 0; gi < 4; ++gi) {
+            if (S.L[gi] <= 0) continue;
+            const int L = S.L[gi], K = S.K[gi];
+            VG_TRY(fin(sc->perm[gi].ensure((size_t)L * N * 4, st, "perm")));
+            VG_TRY(fin(sc->seg[gi].ensure((size_t)L * (K + 1) * 4, st, "seg")));
+            for (int s = 0; s < L; ++s) {
+                uint32_t* h = hist.as<uint32_t>();
+                VG_CUDA(cudaMemsetAsync(h, 0, 256 * 4 * 2, st));
+                VG_CUDA(launch_idx_to_keys(S.idx[gi] + (int64_t)s * N, N, keys.as<uint32_t>(), st));
+                VG_CUDA(launch_hist(keys.as<uint32_t>(), N, 1, h, st));
+                VG_CUDA(launch_sort_pass(keys.as<uint32_t>(), nullptr, keys_out.as<uint32_t>(),
+                                         sc->perm[gi].as<uint32_t>() + (int64_t)s * N, nullptr, (uint32_t)N, 0, h,
+                                         lb.as<unsigned long long>(), h + 256, state.as<uint32_t>(), epoch_off++,
+                                         state.as<uint32_t>() + ST_ERR, sort_pass_grid((uint32_t)N), st));
+                VG_CUDA(launch_seg_from_hist(h, K, sc->seg[gi].as<uint32_t>() + (int64_t)s * (K + 1), st));
+            }
+        }
+        VG_CUDA(cudaStreamSynchronize(st));
+    } else {
+        VG_CUDA(cudaStreamSynchronize(st));
+    }
+    *out = sc;
+    return VG_OK;
+}
+
+vg_status vg_scene_free(vg_scene* scene) {
+    if (!scene) return fail(VG_ERR_INVALID_ARG, "vg_scene_free: null scene");
+    delete scene;
+    return VG_OK;
+}
+
+int64_t vg_scene_size(const vg_scene* scene) { return scene ? scene->dev.N : -1; }
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+
+vg_status vg_ctx_create(int64_t pair_capacity, vg_ctx** out) {
+    if (!out || pair_capacity < 0) return fail(VG_ERR_INVALID_ARG, "vg_ctx_create: bad argument");
+    *out = nullptr;
+    vg_ctx* c = new vg_ctx();
+    vg_status s = c->state.ensure(ST_WORDS * 4, nullptr, "state");
+    if (s == VG_OK) s = c->scratch.ensure(SCR_WORDS * 4, nullptr, "scratch");
+    if (s == VG_OK) s = c->loss_scratch.ensure(16, nullptr, "loss");
+    if (s != VG_OK) {
+        delete c;
+        return s;
+    }
+    if (cudaMemset(c->state.p, 0, c->state.bytes) != cudaSuccess) {
+        delete c;
+        return fail(VG_ERR_CUDA, "vg_ctx_create: cudaMemset");
+    }
+    if (pair_capacity > 0) {
+        s = vg_ctx_reserve(c, pair_capacity);
+        if (s != VG_OK) {
+            delete c;
+            return s;
+        }
+    }
+    *out = c;
+    return VG_OK;
+}
+
+vg_status vg_ctx_free(vg_ctx* ctx) {
+    if (!ctx) return fail(VG_ERR_INVALID_ARG, "vg_ctx_free: null ctx");
+    delete ctx;
+    return VG_OK;
+}
+
+vg_status vg_ctx_reserve(vg_ctx* ctx, int64_t cap) {
+    if (!ctx || cap < 0) return fail(VG_ERR_INVALID_ARG, "vg_ctx_reserve: bad argument");
+    if (cap >= ((int64_t)1 << 30)) return fail(VG_ERR_INVALID_ARG, "vg_ctx_reserve: capacity must be below 2^30 pairs");
+    if (cap <= ctx->pair_cap) return VG_OK;
+    for (int b = 0; b < 2; ++b) {
+        VG_TRY(ctx->pkey[b].ensure((size_t)cap * 4, nullptr, "pair keys"));
+        VG_TRY(ctx->pval[b].ensure((size_t)cap * 4, nullptr, "pair values"));
+    }
+    ctx->pair_cap = cap;
+    return VG_OK;
+}
+
+vg_status vg_ctx_stats(vg_ctx* ctx, vg_stream stream, vg_stats* out) {
+    if (!ctx) return fail(VG_ERR_INVALID_ARG, "vg_ctx_stats: null ctx");
+    cudaStream_t st = (cudaStream_t)stream;
+    VG_CUDA(cudaStreamSynchronize(st));
+    uint32_t state[ST_WORDS];
+    uint32_t scr[SCR_WORDS];
+    VG_CUDA(cudaMemcpy(state, ctx->state.p, sizeof(state), cudaMemcpyDeviceToHost));
+    VG_CUDA(cudaMemcpy(scr, ctx->scratch.p, sizeof(scr), cudaMemcpyDeviceToHost));
+    if (out) {
+        out->pairs = scr[SCR_PAIRS];
+        out->pair_capacity = ctx->pair_cap;
+        out->visible = scr[SCR_NVIS];
+        unsigned long long ev, bl, bw;
+        std::memcpy(&ev, state + ST_EVALS, 8);
+        std::memcpy(&bl, state + ST_BLENDED, 8);
+        std::memcpy(&bw, state + ST_BWD, 8);
+        out->evaluated = (int64_t)ev;
+        out->blended = (int64_t)bl;
+        out->bwd_pairs = (int64_t)bw;
+        out->flags = state[ST_ERR];
+    }
+    return VG_OK;
+}
+
+vg_status vg_check(vg_ctx* ctx, vg_stream stream) {
+    if (!ctx) return fail(VG_ERR_INVALID_ARG, "vg_check: null ctx");
+    vg_stats s;
+    VG_TRY(vg_ctx_stats(ctx, stream, &s));
+    if (s.flags) {
+        VG_CUDA(cudaMemset(ctx->state.as<uint32_t>() + ST_ERR, 0, 4));
+        if (s.flags & ERR_WAIT) return fail(VG_ERR_TIMEOUT, "a bounded device wait ran out");
+        return fail(VG_ERR_CAPACITY, "pair buffer too small: " + std::to_string(s.pairs) + " pairs needed, capacity " +
+                                         std::to_string(s.pair_capacity));
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(VG_ERR_CUDA, cudaGetErrorString(e));
+    return VG_OK;
+}
+
+vg_status vg_ctx_reset_counters(vg_ctx* ctx, vg_stream stream) {
+    if (!ctx) return fail(VG_ERR_INVALID_ARG, "vg_ctx_reset_counters: null ctx");
+    VG_CUDA(cudaMemsetAsync(ctx->state.as<uint32_t>() + ST_EVALS, 0, 24, (cudaStream_t)stream));
+    return VG_OK;
+}
+
+vg_status vg_ctx_profile(vg_ctx* ctx, int32_t enable) {
+    if (!ctx) return fail(VG_ERR_INVALID_ARG, "vg_ctx_profile: null ctx");
+    ctx->prof.reset();
+    ctx->prof.on = enable != 0;
+    return VG_OK;
+}
+
+vg_status vg_ctx_profile_read(vg_ctx* ctx, vg_stream stream, double* ms_total, int64_t* launches) {
+    if (!ctx || !ms_total || !launches) return fail(VG_ERR_INVALID_ARG, "vg_ctx_profile_read: null argument");
+    VG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    for (int i = 0; i < VG_STAGE_COUNT; ++i) {
+        ms_total[i] = 0.0;
+        launches[i] = 0;
+    }
+    for (const auto& r : ctx->prof.recs) {
+        float ms = 0.f;
+        VG_CUDA(cudaEventSynchronize(r.b));
+        VG_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        ms_total[r.stage] += ms;
+        launches[r.stage] += 1;
+    }
+    return VG_OK;
+}
+
+vg_status vg_ctx_buffer(const vg_ctx* ctx, int32_t which, const void** ptr, int64_t* bytes) {
+    if (!ctx || !ptr || !bytes) return fail(VG_ERR_INVALID_ARG, "vg_ctx_buffer: null argument");
+    const DevBuf* b = nullptr;
+    switch (which) {
+        case VG_BUF_XY: b = &ctx->xy; break;
+        case VG_BUF_CONIC: b = &ctx->conic_o; break;
+        case VG_BUF_RGBD: b = &ctx->rgbd; break;
+        case VG_BUF_RECT: b = &ctx->rect; break;
+        case VG_BUF_NTILES: b = &ctx->ntiles; break;
+        case VG_BUF_PAIR_KEYS: b = &ctx->pkey[ctx->final_pair]; break;
+        case VG_BUF_PAIR_VALS: b = &ctx->pval[ctx->final_pair]; break;
+        case VG_BUF_RANGES: b = &ctx->ranges; break;
+        case VG_BUF_T_FINAL: b = &ctx->Tfin; break;
+        case VG_BUF_N_CONTRIB: b = &ctx->ncontrib; break;
+        case VG_BUF_G2D: b = &ctx->g2d; break;
+        default: return fail(VG_ERR_INVALID_ARG, "vg_ctx_buffer: unknown buffer id");
+    }
+    *ptr = b->p;
+    *bytes = (int64_t)b->bytes;
+    return VG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// decode
+// ---------------------------------------------------------------------------
+
+vg_status vg_rvq_decode(const vg_attr_group* g, int64_t n, float* out, vg_stream stream) {
+    if (!g || !out || n < 0) return fail(VG_ERR_INVALID_ARG, "vg_rvq_decode: null argument or n < 0");
+    if (g->dim < 1) return fail(VG_ERR_INVALID_ARG, "vg_rvq_decode: dim < 1");
+    if (g->stages > 0) {
+        if (g->codewords < 1 || g->codewords > VG_MAX_CODEWORDS)
+            return fail(VG_ERR_INVALID_ARG, "vg_rvq_decode: codewords must be in 1..256");
+        if (!g->codebook || (n > 0 && !g->idx)) return fail(VG_ERR_INVALID_ARG, "vg_rvq_decode: null codebook or idx");
+    } else if (g->stages < 0 || (n > 0 && !g->raw)) {
+        return fail(VG_ERR_INVALID_ARG, "vg_rvq_decode: raw group needs raw values");
+    }
+    VG_CUDA(launch_rvq_decode(g->dim, g->stages, g->codewords, g->codebook, g->idx, g->raw, n, out, (cudaStream_t)stream));
+    return VG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// render
+// ---------------------------------------------------------------------------
+
+static vg_status build_views(const vg_camera* cams, int32_t n_views, const vg_render_params* p, Views* V, Consts* cs,
+                             int64_t* pixels) {
+    if (!cams || !p) return fail(VG_ERR_INVALID_ARG, "null cameras or params");
+    if (n_views < 1 || n_views > VG_MAX_VIEWS) return fail(VG_ERR_INVALID_ARG, "n_views must be in 1..64");
+    if (p->tile != VG_TILE) return fail(VG_ERR_INVALID_ARG, "params.tile must be 16");
+    if (!(p->alpha_max > 0.f && p->alpha_max < 1.f) || !(p->alpha_min >= 0.f) || !(p->t_min >= 0.f) ||
+        !(p->dilation >= 0.f) || !(p->sigma_cull > 0.f) || !(p->clamp_factor > 0.f))
+        return fail(VG_ERR_INVALID_ARG, "render params out of range");
+    std::memset(V, 0, sizeof(*V));
+    V->n = n_views;
+    V->pose_dev = p->pose_dev;
+    int64_t tb = 0, pb = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const vg_camera& c = cams[v];
+        if (c.width < 1 || c.height < 1 || c.width > 65535 * VG_TILE || c.height > 65535 * VG_TILE)
+            return fail(VG_ERR_INVALID_ARG, "camera size out of range");
+        if (!(c.fx > 0.f && c.fy > 0.f) || !(c.near_plane > 0.f))
+            return fail(VG_ERR_INVALID_ARG, "camera focal lengths and near plane must be positive");
+        ViewInfo& vi = V->v[v];
+        vi.fx = c.fx;
+        vi.fy = c.fy;
+        vi.cx = c.cx;
+        vi.cy = c.cy;
+        std::memcpy(vi.T, c.T_cw, sizeof(vi.T));
+        vi.near_plane = c.near_plane;
+        vi.limx = p->clamp_factor * (0.5f * c.width / c.fx);
+        vi.limy = p->clamp_factor * (0.5f * c.height / c.fy);
+        vi.W = c.width;
+        vi.H = c.height;
+        vi.tiles_x = (c.width + VG_TILE - 1) / VG_TILE;
+        vi.tiles_y = (c.height + VG_TILE - 1) / VG_TILE;
+        vi.tile_base = (int32_t)tb;
+        vi.pix_base = pb;
+        tb += (int64_t)vi.tiles_x * vi.tiles_y;
+        pb += (int64_t)c.width * c.height;
+    }
+    if (tb >= ((int64_t)1 << 24)) return fail(VG_ERR_INVALID_ARG, "too many tiles in one call");
+    V->total_tiles = (int32_t)tb;
+    cs->alpha_max = p->alpha_max;
+    cs->alpha_min = p->alpha_min;
+    cs->t_min = p->t_min;
+    cs->dilation = p->dilation;
+    cs->sigma_cull = p->sigma_cull;
+    cs->jacobian_clamp = p->jacobian_clamp;
+    *pixels = pb;
+    return VG_OK;
+}
+
+static int tile_passes_for(int total_tiles) {
+    int bits = 1;
+    while ((1 << bits) < total_tiles) ++bits;
+    return (bits + 7) / 8;
+}
+
+vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views, const vg_render_params* params,
+                        vg_ctx* ctx, float* C, float* D, float* S, vg_stream stream) {
+    if (!scene || !ctx || !C || !D || !S) return fail(VG_ERR_INVALID_ARG, "vg_render_fwd: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    Views V;
+    Consts cs;
+    int64_t pixels = 0;
+    VG_TRY(build_views(cams, n_views, params, &V, &cs, &pixels));
+    const SceneDev& sd = scene->dev;
+    const int64_t N = sd.N;
+    const int64_t slots = N * n_views;
+    if (slots >= ((int64_t)1 << 30)) return fail(VG_ERR_INVALID_ARG, "vg_render_fwd: views x Gaussians >= 2^30");
+    if (ctx->pair_cap < 1) VG_TRY(vg_ctx_reserve(ctx, std::max<int64_t>(1024, slots * 8)));
+
+    VG_TRY(ctx->xy.ensure(slots * 8, st, "xy"));
+    VG_TRY(ctx->conic_o.ensure(slots * 16, st, "conic"));
+    VG_TRY(ctx->rgbd.ensure(slots * 16, st, "rgbd"));
+    VG_TRY(ctx->rect.ensure(slots * 8, st, "rect"));
+    VG_TRY(ctx->ntiles.ensure(slots * 4, st, "ntiles"));
+    for (int b = 0; b < 2; ++b) {
+        VG_TRY(ctx->dkey[b].ensure(slots * 4, st, "depth keys"));
+        VG_TRY(ctx->dval[b].ensure(slots * 4, st, "depth values"));
+    }
+    VG_TRY(ctx->ranges.ensure((size_t)V.total_tiles * 8, st, "ranges"));
+    VG_TRY(ctx->Tfin.ensure(pixels * 4, st, "T_final"));
+    VG_TRY(ctx->ncontrib.ensure(pixels * 4, st, "n_contrib"));
+    const int64_t lb_parts = std::max(ceil_div(slots, SORT_TILE), ceil_div(ctx->pair_cap, SORT_TILE));
+    const int64_t lb_entries = std::max(lb_parts * 256, ceil_div(slots, DUP_TILE));
+    if (ctx->lookback.bytes < (size_t)lb_entries * 8) {
+        VG_TRY(ctx->lookback.ensure(lb_entries * 8, st, "lookback"));
+        VG_CUDA(cudaMemsetAsync(ctx->lookback.p, 0, ctx->lookback.bytes, st));
+    }
+
+    uint32_t* scr = ctx->scratch.as<uint32_t>();
+    uint32_t* state = ctx->state.as<uint32_t>();
+    uint32_t* err = state + ST_ERR;
+    unsigned long long* lb = ctx->lookback.as<unsigned long long>();
+    const bool prof_on = ctx->prof.on && !capturing(st);
+    VG_STAGE(VG_STAGE_MEMSET, cudaMemsetAsync(scr, 0, SCR_WORDS * 4, st));
+    VG_STAGE(VG_STAGE_PREPROCESS,
+             launch_preprocess(sd, V, cs, ctx->xy.as<float2>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
+                               ctx->rect.as<uint2>(), ctx->ntiles.as<uint32_t>(), ctx->dkey[0].as<uint32_t>(), scr,
+                               state, st));
+    // depth order of all slots (culled slots carry key 0xffffffff and sort last)
+    const int dgrid = sort_pass_grid((uint32_t)slots);
+    VG_STAGE(VG_STAGE_DEPTH_SORT, ([&]() -> cudaError_t {
+                 for (int p = 0; p < 4; ++p) {
+                     const int i = p & 1, o = i ^ 1;
+                     cudaError_t e = launch_sort_pass(
+                         ctx->dkey[i].as<uint32_t>(), p == 0 ? nullptr : ctx->dval[i].as<uint32_t>(),
+                         ctx->dkey[o].as<uint32_t>(), ctx->dval[o].as<uint32_t>(), nullptr, (uint32_t)slots, 8 * p,
+                         scr + SCR_DEPTH_HIST + 256 * p, lb, scr + SCR_CNT_DEPTH + p, state, (uint32_t)p, err, dgrid, st);
+                     if (e != cudaSuccess) return e;
+                 }
+                 return cudaSuccess;
+             })());
+    // pairs in depth order, then stable by tile
+    const int tp = tile_passes_for(V.total_tiles);
+    const uint32_t cap = (uint32_t)ctx->pair_cap;
+    VG_STAGE(VG_STAGE_DUPLICATE,
+             launch_duplicate(ctx->dval[0].as<uint32_t>(), scr + SCR_NVIS, ctx->ntiles.as<uint32_t>(),
+                              ctx->rect.as<uint2>(), N, V, ctx->pkey[0].as<uint32_t>(), ctx->pval[0].as<uint32_t>(), cap,
+                              scr, tp, lb, state, 4u, err, slots, st));
+    const int tgrid = sort_pass_grid(cap);
+    VG_STAGE(VG_STAGE_TILE_SORT, ([&]() -> cudaError_t {
+                 for (int p = 0; p < tp; ++p) {
+                     const int i = p & 1, o = i ^ 1;
+                     cudaError_t e = launch_sort_pass(
+                         ctx->pkey[i].as<uint32_t>(), ctx->pval[i].as<uint32_t>(), ctx->pkey[o].as<uint32_t>(),
+                         ctx->pval[o].as<uint32_t>(), scr + SCR_PAIRS, cap, 8 * p, scr + SCR_TILE_HIST + 256 * p, lb,
+                         scr + SCR_CNT_TILE + p, state, 5u + (uint32_t)p, err, tgrid, st);
+                     if (e != cudaSuccess) return e;
+                 }
+                 return cudaSuccess;
+             })());
+    const int fin = tp & 1;
+    ctx->final_pair = fin;
+    VG_STAGE(VG_STAGE_RANGES, launch_ranges(ctx->pkey[fin].as<uint32_t>(), scr + SCR_PAIRS, cap, V.total_tiles,
+                                            ctx->ranges.as<uint2>(), st));
+    VG_STAGE(VG_STAGE_BLEND_FWD,
+             launch_blend_fwd(V, cs, params->batch, ctx->ranges.as<uint2>(), ctx->pval[fin].as<uint32_t>(),
+                              ctx->xy.as<float2>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(), C, D, S,
+                              ctx->Tfin.as<float>(), ctx->ncontrib.as<uint32_t>(),
+                              (unsigned long long*)(state + ST_EVALS), (unsigned long long*)(state + ST_BLENDED),
+                              params->count_evals, st));
+    ctx->views = V;
+    ctx->fwd_N = N;
+    ctx->fwd_scene = scene;
+    ctx->have_fwd = true;
+    return VG_OK;
+}
+
+static bool same_views(const Views& a, const Views& b) {
+    if (a.n != b.n || a.total_tiles != b.total_tiles) return false;
+    for (int v = 0; v < a.n; ++v)
+        if (a.v[v].W != b.v[v].W || a.v[v].H != b.v[v].H) return false;
+    return true;
+}
+
+vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views, const vg_render_params* params,
+                        vg_ctx* ctx, const float* dC, const float* dD, const float* dS, const vg_scene_grads* grads,
+                        vg_stream stream) {
+    if (!scene || !ctx || !grads) return fail(VG_ERR_INVALID_ARG, "vg_render_bwd: null argument");
+    if (!ctx->have_fwd || ctx->fwd_scene != scene)
+        return fail(VG_ERR_INVALID_ARG, "vg_render_bwd: no matching vg_render_fwd on this ctx");
+    cudaStream_t st = (cudaStream_t)stream;
+    Views V;
+    Consts cs;
+    int64_t pixels = 0;
+    VG_TRY(build_views(cams, n_views, params, &V, &cs, &pixels));
+    if (!same_views(V, ctx->views)) return fail(VG_ERR_INVALID_ARG, "vg_render_bwd: cameras differ from the forward");
+    const SceneDev& sd = scene->dev;
+    const int64_t N = sd.N, slots = N * n_views;
+    VG_TRY(ctx->g2d.ensure(slots * G2D_STRIDE * 4, st, "g2d"));
+    const int nb = chain_blocks(N);
+    VG_TRY(ctx->pose_part.ensure((size_t)n_views * nb * 6 * 4, st, "pose partials"));
+    bool need_attr = false;
+    float* gptr[4] = {grads->logscale, grads->rot, grads->opacity, grads->rgb};
+    for (int gi = 0; gi < 4; ++gi) need_attr |= (sd.L[gi] > 0 && gptr[gi]);
+    if (need_attr) VG_TRY(ctx->dattr.ensure(N * ATTR_STRIDE * 4, st, "attribute grads"));
+
+    const bool prof_on = ctx->prof.on && !capturing(st);
+    VG_STAGE(VG_STAGE_MEMSET, cudaMemsetAsync(ctx->g2d.p, 0, slots * G2D_STRIDE * 4, st));
+    VG_STAGE(VG_STAGE_BLEND_BWD,
+             launch_blend_bwd(V, cs, params->batch, ctx->ranges.as<uint2>(), ctx->pval[ctx->final_pair].as<uint32_t>(),
+                              ctx->xy.as<float2>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
+                              ctx->Tfin.as<float>(), ctx->ncontrib.as<uint32_t>(), dC, dD, dS, ctx->g2d.as<float>(),
+                              (unsigned long long*)(ctx->state.as<uint32_t>() + ST_BWD), params->count_evals, st));
+    if ((32 % sd.k) != 0) {
+        if (grads->anchor_xyz) VG_CUDA(cudaMemsetAsync(grads->anchor_xyz, 0, sd.n_anchors * 12, st));
+        if (grads->anchor_l) VG_CUDA(cudaMemsetAsync(grads->anchor_l, 0, sd.n_anchors * 12, st));
+    }
+    float* raws[4];
+    for (int gi = 0; gi < 4; ++gi) raws[gi] = sd.L[gi] > 0 ? nullptr : gptr[gi];
+    if (N > 0) {
+        VG_STAGE(VG_STAGE_CHAIN,
+                 launch_chain(sd, V, cs, ctx->g2d.as<float>(), need_attr ? ctx->dattr.as<float>() : nullptr, raws[0],
+                              raws[1], raws[2], raws[3], grads->anchor_xyz, grads->anchor_l, grads->offsets,
+                              grads->mask_logit, ctx->pose_part.as<float>(), &ctx->pose_blocks, st));
+    } else {
+        VG_CUDA(cudaMemsetAsync(ctx->pose_part.p, 0, (size_t)n_views * nb * 6 * 4, st));
+        ctx->pose_blocks = nb;
+    }
+    for (int gi = 0; gi < 4; ++gi) {
+        if (sd.L[gi] <= 0 || !gptr[gi]) continue;
+        const size_t bytes = (size_t)sd.L[gi] * sd.K[gi] * GDIMS[gi] * 4;
+        if (N == 0) {
+            VG_CUDA(cudaMemsetAsync(gptr[gi], 0, bytes, st));
+            continue;
+        }
+        VG_STAGE(VG_STAGE_CODEBOOK,
+                 launch_codebook_reduce(gi, sd.L[gi], sd.K[gi], GDIMS[gi], scene->perm[gi].as<uint32_t>(),
+                                        scene->seg[gi].as<uint32_t>(), N, ctx->dattr.as<float>(), gptr[gi], st));
+    }
+    ctx->bwd_scene = sd;
+    ctx->views = V;
+    ctx->have_bwd = true;
+    return VG_OK;
+}
+
+vg_status vg_pose_grad(vg_ctx* ctx, int32_t n_views, const float* icp_q, const float* icp_w, float* dxi,
+                       float* icp_loss, vg_stream stream) {
+    if (!ctx || !dxi) return fail(VG_ERR_INVALID_ARG, "vg_pose_grad: null argument");
+    if (!ctx->have_bwd) return fail(VG_ERR_INVALID_ARG, "vg_pose_grad: no vg_render_bwd on this ctx");
+    if (n_views != ctx->views.n) return fail(VG_ERR_INVALID_ARG, "vg_pose_grad: n_views differs from the backward");
+    if (icp_q && !icp_w) return fail(VG_ERR_INVALID_ARG, "vg_pose_grad: icp_q without icp_w");
+    cudaStream_t st = (cudaStream_t)stream;
+    const SceneDev& sd = ctx->bwd_scene;
+    const float* icp_part = nullptr;
+    int nbi = 0;
+    const bool prof_on = ctx->prof.on && !capturing(st);
+    if (icp_q) {
+        nbi = icp_blocks(sd.N);
+        VG_TRY(ctx->icp_part.ensure((size_t)n_views * nbi * 7 * 4, st, "icp partials"));
+        VG_STAGE(VG_STAGE_POSE, launch_icp(sd, ctx->views, icp_q, icp_w, ctx->icp_part.as<float>(), nbi, st));
+        icp_part = ctx->icp_part.as<float>();
+    } else if (icp_loss) {
+        VG_CUDA(cudaMemsetAsync(icp_loss, 0, (size_t)n_views * 4, st));
+    }
+    VG_STAGE(VG_STAGE_POSE, launch_pose_final(n_views, ctx->pose_part.as<float>(), ctx->pose_blocks, icp_part, nbi,
+                                              dxi, icp_q ? icp_loss : nullptr, st));
+    return VG_OK;
+}
+
+vg_status vg_loss_l1(int32_t n_views, int64_t n_pix, const float* C, const float* D, const float* S, const float* Ct,
+                     const float* Dt, float w_depth, float gate, float* dC, float* dD, float* dS, float* loss,
+                     vg_ctx* ctx, vg_stream stream) {
+    if (!ctx || !C || !D || !Ct || !Dt || !dC || !dD || !loss || n_views < 1 || n_pix < 1)
+        return fail(VG_ERR_INVALID_ARG, "vg_loss_l1: null argument or empty size");
+    if (gate >= 0.f && !S) return fail(VG_ERR_INVALID_ARG, "vg_loss_l1: gate needs S");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool prof_on = ctx->prof.on && !capturing(st);
+    VG_CUDA(cudaMemsetAsync(ctx->loss_scratch.p, 0, 16, st));
+    VG_CUDA(cudaMemsetAsync(loss, 0, 4, st));
+    if (dS) VG_CUDA(cudaMemsetAsync(dS, 0, (size_t)n_views * n_pix * 4, st));
+    VG_STAGE(VG_STAGE_LOSS, launch_loss_l1(n_views, n_pix, C, D, S, Ct, Dt, w_depth, gate, dC, dD, loss,
+                                           ctx->loss_scratch.as<uint32_t>(), st));
+    return VG_OK;
+}
+
+vg_status vg_adam_step(const vg_adam_tensor* tensors, int32_t n, float lr, float beta1, float beta2, float eps,
+                       int32_t* step_dev, int32_t step_host, vg_stream stream) {
+    if (!tensors || n < 1 || n > 16) return fail(VG_ERR_INVALID_ARG, "vg_adam_step: need 1..16 tensors");
+    if (!step_dev && step_host < 1) return fail(VG_ERR_INVALID_ARG, "vg_adam_step: step must be >= 1");
+    float* p[16];
+    const float* g[16];
+    float* m[16];
+    float* v[16];
+    int64_t size[16];
+    for (int i = 0; i < n; ++i) {
+        const vg_adam_tensor& t = tensors[i];
+        if (t.n < 0 || (t.n > 0 && (!t.param || !t.grad || !t.m || !t.v)))
+            return fail(VG_ERR_INVALID_ARG, "vg_adam_step: null array or negative size");
+        p[i] = t.param;
+        g[i] = t.grad;
+        m[i] = t.m;
+        v[i] = t.v;
+        size[i] = t.n;
+    }
+    VG_CUDA(launch_adam(n, p, g, m, v, size, lr, beta1, beta2, eps, step_dev, step_host, (cudaStream_t)stream));
+    return VG_OK;
+}
+
+vg_status vg_pose_step(int32_t n_views, float* pose, const float* dxi, float* m, float* v, float lr_rot, float lr_trans,
+                       float beta1, float beta2, float eps, int32_t* step_dev, int32_t step_host, vg_stream stream) {
+    if (n_views < 1 || !pose || !dxi || !m || !v) return fail(VG_ERR_INVALID_ARG, "vg_pose_step: null argument");
+    if (!step_dev && step_host < 1) return fail(VG_ERR_INVALID_ARG, "vg_pose_step: step must be >= 1");
+    VG_CUDA(launch_pose_step(n_views, pose, dxi, m, v, lr_rot, lr_trans, beta1, beta2, eps, step_dev, step_host,
+                             (cudaStream_t)stream));
+    return VG_OK;
+}
+
+}  // extern "C"

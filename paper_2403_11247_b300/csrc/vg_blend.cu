@@ -1,0 +1,311 @@
+// vg_blend.cu -- per-tile front-to-back compositing (Eq. 16-18) and its
+// reverse mode.
+//
+// Forward, per pixel p over its tile's list in (depth, index) order:
+//   power = -1/2 d^T conic d (d = uv - p), skipped if > 0
+//   alpha = min(alpha_max, o e^power), skipped if < alpha_min
+//   stop (Gaussian not blended) if T (1 - alpha) < t_min
+//   C += c alpha T, D += z alpha T, S += alpha T, T *= (1 - alpha)
+// Keeps the final T and the list position + 1 of the last blended Gaussian.
+//
+// Backward walks each pixel's list back to front from that position and
+// recovers T_i = T_{i+1} / (1 - alpha_i) from the final T (no per-step
+// storage).  With w_i = g . (r, g, b, z, 1)_i for the upstream pixel gradient
+// g and B_i = sum_{j > i} w_j alpha_j T_j,
+//   dL/dalpha_i = T_i w_i - B_i / (1 - alpha_i).
+// Lanes of a warp hold different pixels of the same Gaussian: their ten
+// per-Gaussian partials are reduced with a transposing butterfly (17
+// shuffles) before four lanes issue the global atomics.
+#include "vg_internal.h"
+
+namespace vgk {
+
+constexpr int BLEND_BATCH = 256;
+
+template <int PPT>
+__global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
+    const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pvals,
+    const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
+    float* __restrict__ C, float* __restrict__ D, float* __restrict__ S, float* __restrict__ Tfin,
+    uint32_t* __restrict__ ncontrib, unsigned long long* evals, unsigned long long* blended, int count_evals) {
+    constexpr int NT = TILE_PIX / PPT;
+    __shared__ float2 s_xy[BLEND_BATCH];
+    __shared__ float4 s_co[BLEND_BATCH];
+    __shared__ float4 s_cd[BLEND_BATCH];
+
+    const int gt = blockIdx.x;
+    const int v = view_of_tile(V, gt);
+    const ViewInfo& vi = V.v[v];
+    const int t = gt - vi.tile_base;
+    const int tx = t % vi.tiles_x, ty = t / vi.tiles_x;
+
+    int px[PPT], py[PPT];
+    bool done[PPT];
+    float T[PPT], acc[PPT][5];
+    uint32_t last[PPT], ne[PPT], nb[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int pi = threadIdx.x + k * NT;
+        px[k] = tx * TILE + (pi & (TILE - 1));
+        py[k] = ty * TILE + pi / TILE;
+        done[k] = !(px[k] < vi.W && py[k] < vi.H);
+        T[k] = 1.f;
+        last[k] = 0;
+        ne[k] = 0;
+        nb[k] = 0;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) acc[k][c] = 0.f;
+    }
+    const uint2 rg = ranges[gt];
+    for (uint32_t b = rg.x; b < rg.y; b += BLEND_BATCH) {
+        int alldone = 1;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) alldone &= (int)done[k];
+        if (__syncthreads_count(alldone) == NT) break;
+        for (int i = threadIdx.x; i < BLEND_BATCH; i += NT) {
+            const uint32_t j = b + i;
+            if (j < rg.y) {
+                const uint32_t s = pvals[j];
+                s_xy[i] = xy[s];
+                s_co[i] = conic_o[s];
+                s_cd[i] = rgbd[s];
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)min((uint32_t)BLEND_BATCH, rg.y - b);
+        for (int i = 0; i < cnt; ++i) {
+            const float2 g = s_xy[i];
+            const float4 co = s_co[i];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (done[k]) continue;
+                ++ne[k];
+                const float dx = g.x - (float)px[k], dy = g.y - (float)py[k];
+                const float power = gauss_power(co.x, co.y, co.z, dx, dy);
+                if (power > 0.f) continue;
+                const float alpha = fminf(cs.alpha_max, __fmul_rn(co.w, __expf(power)));
+                if (alpha < cs.alpha_min) continue;
+                const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
+                if (Tn < cs.t_min) {
+                    done[k] = true;
+                    continue;
+                }
+                const float4 cd = s_cd[i];
+                const float w = alpha * T[k];
+                acc[k][0] = fmaf(cd.x, w, acc[k][0]);
+                acc[k][1] = fmaf(cd.y, w, acc[k][1]);
+                acc[k][2] = fmaf(cd.z, w, acc[k][2]);
+                acc[k][3] = fmaf(cd.w, w, acc[k][3]);
+                acc[k][4] += w;
+                T[k] = Tn;
+                last[k] = b - rg.x + i + 1;
+                ++nb[k];
+            }
+        }
+    }
+    const int64_t HW = (int64_t)vi.W * vi.H;
+    uint32_t ev = 0, bl = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (!(px[k] < vi.W && py[k] < vi.H)) continue;
+        const int64_t i = (int64_t)py[k] * vi.W + px[k];
+        const int64_t pb = vi.pix_base;
+        C[3 * pb + i] = acc[k][0];
+        C[3 * pb + HW + i] = acc[k][1];
+        C[3 * pb + 2 * HW + i] = acc[k][2];
+        D[pb + i] = acc[k][3];
+        S[pb + i] = acc[k][4];
+        Tfin[pb + i] = T[k];
+        ncontrib[pb + i] = last[k];
+        ev += ne[k];
+        bl += nb[k];
+    }
+    if (count_evals) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ev += __shfl_xor_sync(0xffffffffu, ev, o);
+            bl += __shfl_xor_sync(0xffffffffu, bl, o);
+        }
+        if ((threadIdx.x & 31) == 0 && ev) atomicAdd(evals, (unsigned long long)ev);
+        if ((threadIdx.x & 31) == 0 && bl) atomicAdd(blended, (unsigned long long)bl);
+    }
+}
+
+// transposing butterfly: ten per-lane values summed over the warp; lanes 0, 8,
+// 16, 24 end up holding values {0,1,2}, {3,4}, {5,6,7}, {8,9} and add them to dst
+__device__ __forceinline__ void warp_reduce_add10(const float v[10], float* dst) {
+    const int lane = threadIdx.x & 31;
+    const bool h16 = (lane & 16) != 0;
+    float a[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float send = h16 ? v[k] : v[k + 5];
+        const float keep = h16 ? v[k + 5] : v[k];
+        a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    const bool h8 = (lane & 8) != 0;
+    float b0 = (h8 ? a[3] : a[0]) + __shfl_xor_sync(0xffffffffu, h8 ? a[0] : a[3], 8);
+    float b1 = (h8 ? a[4] : a[1]) + __shfl_xor_sync(0xffffffffu, h8 ? a[1] : a[4], 8);
+    float b2 = (h8 ? 0.f : a[2]) + __shfl_xor_sync(0xffffffffu, h8 ? a[2] : 0.f, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+        b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+    }
+    if ((lane & 7) == 0) {
+        const int base = (h16 ? 5 : 0) + (h8 ? 3 : 0);
+        atomicAdd(dst + base, b0);
+        atomicAdd(dst + base + 1, b1);
+        if (!h8) atomicAdd(dst + base + 2, b2);
+    }
+}
+
+template <int PPT>
+__global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
+    const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pvals,
+    const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
+    const float* __restrict__ Tfin, const uint32_t* __restrict__ ncontrib, const float* __restrict__ dC,
+    const float* __restrict__ dD, const float* __restrict__ dS, float* __restrict__ g2d,
+    unsigned long long* bwd_pairs, int count) {
+    constexpr int NT = TILE_PIX / PPT;
+    __shared__ float2 s_xy[BLEND_BATCH];
+    __shared__ float4 s_co[BLEND_BATCH];
+    __shared__ float4 s_cd[BLEND_BATCH];
+    __shared__ uint32_t s_slot[BLEND_BATCH];
+    __shared__ uint32_t s_max;
+
+    const int gt = blockIdx.x;
+    const int v = view_of_tile(V, gt);
+    const ViewInfo& vi = V.v[v];
+    const int t = gt - vi.tile_base;
+    const int tx = t % vi.tiles_x, ty = t / vi.tiles_x;
+    const int64_t HW = (int64_t)vi.W * vi.H, pb = vi.pix_base;
+
+    int px[PPT], py[PPT];
+    uint32_t nc[PPT];
+    float T[PPT], Bk[PPT], gp[PPT][5];
+    uint32_t mymax = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int pi = threadIdx.x + k * NT;
+        px[k] = tx * TILE + (pi & (TILE - 1));
+        py[k] = ty * TILE + pi / TILE;
+        const bool inside = px[k] < vi.W && py[k] < vi.H;
+        const int64_t i = (int64_t)py[k] * vi.W + px[k];
+        nc[k] = inside ? ncontrib[pb + i] : 0u;
+        T[k] = inside ? Tfin[pb + i] : 1.f;
+        Bk[k] = 0.f;
+        gp[k][0] = (inside && dC) ? dC[3 * pb + i] : 0.f;
+        gp[k][1] = (inside && dC) ? dC[3 * pb + HW + i] : 0.f;
+        gp[k][2] = (inside && dC) ? dC[3 * pb + 2 * HW + i] : 0.f;
+        gp[k][3] = (inside && dD) ? dD[pb + i] : 0.f;
+        gp[k][4] = (inside && dS) ? dS[pb + i] : 0.f;
+        mymax = max(mymax, nc[k]);
+    }
+    if (count) {
+        uint32_t walked = 0;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) walked += nc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) walked += __shfl_xor_sync(0xffffffffu, walked, o);
+        if ((threadIdx.x & 31) == 0 && walked) atomicAdd(bwd_pairs, (unsigned long long)walked);
+    }
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_max, mymax);
+    __syncthreads();
+    const uint2 rg = ranges[gt];
+    const uint32_t end = rg.x + min(s_max, rg.y - rg.x);
+
+    for (uint32_t bend = end; bend > rg.x;) {
+        const uint32_t bstart = (bend - rg.x > (uint32_t)BLEND_BATCH) ? bend - BLEND_BATCH : rg.x;
+        __syncthreads();
+        for (int i = threadIdx.x; i < (int)(bend - bstart); i += NT) {
+            const uint32_t s = pvals[bstart + i];
+            s_slot[i] = s;
+            s_xy[i] = xy[s];
+            s_co[i] = conic_o[s];
+            s_cd[i] = rgbd[s];
+        }
+        __syncthreads();
+        for (int i = (int)(bend - bstart) - 1; i >= 0; --i) {
+            const uint32_t jl = bstart - rg.x + (uint32_t)i;
+            const float2 g = s_xy[i];
+            const float4 co = s_co[i];
+            const float4 cd = s_cd[i];
+            float vals[10];
+#pragma unroll
+            for (int c = 0; c < 10; ++c) vals[c] = 0.f;
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (jl >= nc[k]) continue;
+                const float dx = g.x - (float)px[k], dy = g.y - (float)py[k];
+                const float power = gauss_power(co.x, co.y, co.z, dx, dy);
+                if (power > 0.f) continue;
+                const float G = __expf(power);
+                const float x = __fmul_rn(co.w, G);
+                const float alpha = fminf(cs.alpha_max, x);
+                if (alpha < cs.alpha_min) continue;
+                const float inv = 1.f / (1.f - alpha);
+                T[k] *= inv;  // transmittance in front of this Gaussian
+                const float w = gp[k][0] * cd.x + gp[k][1] * cd.y + gp[k][2] * cd.z + gp[k][3] * cd.w + gp[k][4];
+                const float dA = T[k] * w - Bk[k] * inv;
+                const float wt = alpha * T[k];
+                Bk[k] = fmaf(w, wt, Bk[k]);
+                vals[6] = fmaf(wt, gp[k][0], vals[6]);
+                vals[7] = fmaf(wt, gp[k][1], vals[7]);
+                vals[8] = fmaf(wt, gp[k][2], vals[8]);
+                vals[9] = fmaf(wt, gp[k][3], vals[9]);
+                if (x <= cs.alpha_max) {
+                    const float dp = alpha * dA;
+                    vals[5] = fmaf(G, dA, vals[5]);
+                    vals[0] -= dp * (co.x * dx + co.y * dy);
+                    vals[1] -= dp * (co.y * dx + co.z * dy);
+                    vals[2] -= 0.5f * dp * dx * dx;
+                    vals[3] -= dp * dx * dy;
+                    vals[4] -= 0.5f * dp * dy * dy;
+                }
+                any = true;
+            }
+            if (__any_sync(0xffffffffu, any)) warp_reduce_add10(vals, g2d + (int64_t)s_slot[i] * G2D_STRIDE);
+        }
+        bend = bstart;
+    }
+}
+
+static int default_ppt() { return 1; }
+
+cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int /*batch*/, const uint2* ranges, const uint32_t* pvals,
+                             const float2* xy, const float4* conic_o, const float4* rgbd, float* C, float* D, float* S,
+                             float* Tfin, uint32_t* ncontrib, unsigned long long* evals, unsigned long long* blended,
+                             int count_evals, cudaStream_t st) {
+    if (V.total_tiles <= 0) return cudaSuccess;
+    count_launches(1);
+    switch (default_ppt()) {
+        case 2:
+            blend_fwd_kernel<2><<<V.total_tiles, TILE_PIX / 2, 0, st>>>(V, cs, ranges, pvals, xy, conic_o, rgbd, C, D, S,
+                                                                        Tfin, ncontrib, evals, blended, count_evals);
+            break;
+        default:
+            blend_fwd_kernel<1><<<V.total_tiles, TILE_PIX, 0, st>>>(V, cs, ranges, pvals, xy, conic_o, rgbd, C, D, S,
+                                                                    Tfin, ncontrib, evals, blended, count_evals);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int /*batch*/, const uint2* ranges, const uint32_t* pvals,
+                             const float2* xy, const float4* conic_o, const float4* rgbd, const float* Tfin,
+                             const uint32_t* ncontrib, const float* dC, const float* dD, const float* dS, float* g2d,
+                             unsigned long long* bwd_pairs, int count, cudaStream_t st) {
+    if (V.total_tiles <= 0) return cudaSuccess;
+    count_launches(1);
+    blend_bwd_kernel<4><<<V.total_tiles, TILE_PIX / 4, 0, st>>>(V, cs, ranges, pvals, xy, conic_o, rgbd, Tfin, ncontrib,
+                                                                dC, dD, dS, g2d, bwd_pairs, count);
+    return cudaGetLastError();
+}
+
+}  // namespace vgk

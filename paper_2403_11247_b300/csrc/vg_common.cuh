@@ -1,0 +1,184 @@
+// vg_common.cuh -- device-side types and helpers shared by the libvg kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vg.h"
+
+namespace vgk {
+
+constexpr int TILE = VG_TILE;
+constexpr int TILE_PIX = TILE * TILE;
+
+// device status bits (vg_stats.flags)
+constexpr uint32_t ERR_WAIT = 1u;      // a bounded spin ran out
+constexpr uint32_t ERR_OVERFLOW = 2u;  // pair buffer too small
+
+// a bounded spin gives up after this many polls (~1 s of L2 round trips)
+constexpr uint32_t SPIN_LIMIT = 1u << 21;
+
+constexpr int RADIUS_MAX = 1 << 20;
+
+// Per-view launch constants.  Passed by value as a __grid_constant__ kernel
+// parameter so that a captured graph keeps them; poses may instead come from
+// device memory (pose_dev) for graphs that update poses on the device.
+struct ViewInfo {
+    float fx, fy, cx, cy;
+    float T[12];
+    float near_plane;
+    float limx, limy;
+    int32_t W, H, tiles_x, tiles_y;
+    int32_t tile_base;
+    int64_t pix_base;
+};
+
+struct Views {
+    int32_t n;
+    int32_t total_tiles;
+    const float* pose_dev;
+    ViewInfo v[VG_MAX_VIEWS];
+};
+
+struct Consts {
+    float alpha_max, alpha_min, t_min, dilation, sigma_cull;
+    int32_t jacobian_clamp;
+};
+
+// Scene arrays as the kernels see them (device pointers).
+struct SceneDev {
+    int64_t n_anchors;
+    int32_t k;
+    int64_t N;
+    const float* xyz;
+    const float* l;
+    const float* off;
+    int32_t L[4], K[4];
+    const float* cb[4];
+    const uint8_t* idx[4];
+    const float* raw[4];
+    const float* mask;
+    float mask_thr;
+};
+
+// attribute group dims and their offsets in the packed 11-float attribute
+// gradient record: log-scale 0..2, quaternion 3..6, opacity 7, rgb 8..10
+__host__ __device__ constexpr int gdim(int g) { return g == 0 ? 3 : (g == 1 ? 4 : (g == 2 ? 1 : 3)); }
+__host__ __device__ constexpr int goff(int g) { return g == 0 ? 0 : (g == 1 ? 3 : (g == 2 ? 7 : 8)); }
+constexpr int ATTR_STRIDE = 11;
+constexpr int G2D_STRIDE = 10;  // du dv da db dc dopacity dr dg db ddepth
+
+__device__ __forceinline__ int view_of_tile(const Views& V, int gt) {
+    int lo = 0, hi = V.n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (V.v[mid].tile_base <= gt) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void view_pose(const Views& V, int v, float T[12]) {
+    if (V.pose_dev) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) T[i] = __ldg(V.pose_dev + v * 12 + i);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) T[i] = V.v[v].T[i];
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void decode_attr(const SceneDev& S, int g, int64_t n, float* out) {
+    if (S.L[g] > 0) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) out[c] = 0.f;
+        const int K = S.K[g];
+        for (int s = 0; s < S.L[g]; ++s) {
+            int k = __ldg(S.idx[g] + (int64_t)s * S.N + n);
+            const float* w = S.cb[g] + ((int64_t)s * K + k) * D;
+#pragma unroll
+            for (int c = 0; c < D; ++c) out[c] += __ldg(w + c);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < D; ++c) out[c] = __ldg(S.raw[g] + n * D + c);
+    }
+}
+
+// Eq. 7 with the binning rounding: mu_c = xa_c + (O_c * l_c), no FMA
+__device__ __forceinline__ void anchor_mean(const SceneDev& S, int64_t n, float mu[3]) {
+    int64_t a = n / S.k;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float xa = __ldg(S.xyz + a * 3 + c);
+        float o = __ldg(S.off + n * 3 + c);
+        float l = __ldg(S.l + a * 3 + c);
+        mu[c] = __fadd_rn(xa, __fmul_rn(o, l));
+    }
+}
+
+// camera-space point with the binning rounding: ((W0 m0 + W1 m1) + W2 m2) + t
+__device__ __forceinline__ void cam_point(const float T[12], const float mu[3], float p[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float e0 = __fmul_rn(T[r * 4 + 0], mu[0]);
+        float e1 = __fmul_rn(T[r * 4 + 1], mu[1]);
+        float e2 = __fmul_rn(T[r * 4 + 2], mu[2]);
+        p[r] = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), e2), T[r * 4 + 3]);
+    }
+}
+
+__device__ __forceinline__ void quat_rot(const float q[4], float R[3][3]) {
+    float w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = 1.f - 2.f * (y * y + z * z); R[0][1] = 2.f * (x * y - w * z);       R[0][2] = 2.f * (x * z + w * y);
+    R[1][0] = 2.f * (x * y + w * z);       R[1][1] = 1.f - 2.f * (x * x + z * z); R[1][2] = 2.f * (y * z - w * x);
+    R[2][0] = 2.f * (x * z - w * y);       R[2][1] = 2.f * (y * z + w * x);       R[2][2] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Exponent of the 2D Gaussian, -1/2 (a dx^2 + c dy^2) - b dx dy, with every
+// rounding spelled out so the forward and backward kernels decide alike.
+__device__ __forceinline__ float gauss_power(float a, float b, float c, float dx, float dy) {
+    float q = __fmaf_rn(__fmul_rn(a, dx), dx, __fmul_rn(__fmul_rn(c, dy), dy));
+    float bxy = __fmul_rn(__fmul_rn(b, dx), dy);
+    return __fmaf_rn(-0.5f, q, -bxy);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) { return *(const volatile uint32_t*)p; }
+__device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) { *(volatile uint32_t*)p = v; }
+__device__ __forceinline__ unsigned long long ld_volatile64(const unsigned long long* p) {
+    return *(const volatile unsigned long long*)p;
+}
+__device__ __forceinline__ void st_volatile64(unsigned long long* p, unsigned long long v) {
+    *(volatile unsigned long long*)p = v;
+}
+
+// exclusive scan over a 256-thread block; returns the block total in *total
+__device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t x, uint32_t* s_tmp /*[8]*/, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_tmp[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        uint32_t t = s_tmp[w];
+        wpre += (w < warp) ? t : 0u;
+        tot += t;
+    }
+    __syncthreads();
+    *total = tot;
+    return wpre + inc - x;
+}
+
+}  // namespace vgk

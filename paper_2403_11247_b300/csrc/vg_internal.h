@@ -1,0 +1,105 @@
+// vg_internal.h -- host-side launchers of the libvg kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vg_common.cuh"
+
+namespace vgk {
+
+// per-forward scratch words (zeroed by one memset per forward)
+constexpr int SCR_DEPTH_HIST = 0;      // [4][256]
+constexpr int SCR_TILE_HIST = 1024;    // [3][256]
+constexpr int SCR_NVIS = 1792;
+constexpr int SCR_PAIRS = 1793;
+constexpr int SCR_CNT_DEPTH = 1794;    // 4 pass counters
+constexpr int SCR_CNT_DUP = 1798;
+constexpr int SCR_CNT_TILE = 1799;     // 3 pass counters
+constexpr int SCR_LOSS_VALID = 1802;
+constexpr int SCR_WORDS = 1808;
+
+// persistent state words
+constexpr int ST_EPOCH = 0;
+constexpr int ST_ERR = 1;
+constexpr int ST_EVALS = 2;    // u64 at words 2..3: evaluated (pixel, Gaussian) pairs, forward
+constexpr int ST_BLENDED = 4;  // u64 at words 4..5: blended pairs, forward
+constexpr int ST_BWD = 6;      // u64 at words 6..7: pairs walked by the backward
+constexpr int ST_WORDS = 8;
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 8;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int DUP_THREADS = 256;
+constexpr int DUP_ITEMS = 4;
+constexpr int DUP_TILE = DUP_THREADS * DUP_ITEMS;
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// kernels enqueued by this library in this process (host-side count)
+void count_launches(int n);
+
+// preprocess.cu
+cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& cs, float2* xy, float4* conic_o,
+                              float4* rgbd, uint2* rect, uint32_t* ntiles, uint32_t* dkey, uint32_t* scratch,
+                              uint32_t* state, cudaStream_t st);
+cudaError_t launch_rvq_decode(int dim, int L, int K, const float* cb, const uint8_t* idx, const float* raw,
+                              int64_t n, float* out, cudaStream_t st);
+
+// sort.cu
+// One stable LSD pass on 8-bit digit (key >> shift) & 255 of u32 keys with u32
+// values (vals_in NULL: value = index).  n = min(*n_dev, n_cap) if n_dev, else n_cap.
+cudaError_t launch_sort_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                             uint32_t* vals_out, const uint32_t* n_dev, uint32_t n_cap, int shift,
+                             const uint32_t* hist, unsigned long long* lookback, uint32_t* counter,
+                             const uint32_t* state, uint32_t epoch_offset, uint32_t* err, int grid,
+                             cudaStream_t st);
+int sort_pass_grid(uint32_t n_cap);
+cudaError_t launch_hist(const uint32_t* keys, int64_t n, int passes, uint32_t* hist, cudaStream_t st);
+cudaError_t launch_duplicate(const uint32_t* sorted_slots, const uint32_t* scratch_nvis, const uint32_t* ntiles,
+                             const uint2* rect, int64_t N, const Views& V, uint32_t* pkeys, uint32_t* pvals,
+                             uint32_t cap, uint32_t* scratch, int tile_passes, unsigned long long* lookback,
+                             const uint32_t* state, uint32_t epoch_offset, uint32_t* err, int64_t max_slots,
+                             cudaStream_t st);
+cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* pairs_dev, uint32_t cap, int n_tiles, uint2* ranges,
+                          cudaStream_t st);
+cudaError_t launch_epoch_bump(uint32_t* state, uint32_t by, cudaStream_t st);
+
+// blend.cu
+cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int batch, const uint2* ranges, const uint32_t* pvals,
+                             const float2* xy, const float4* conic_o, const float4* rgbd, float* C, float* D,
+                             float* S, float* Tfin, uint32_t* ncontrib, unsigned long long* evals,
+                             unsigned long long* blended, int count_evals, cudaStream_t st);
+cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int batch, const uint2* ranges, const uint32_t* pvals,
+                             const float2* xy, const float4* conic_o, const float4* rgbd, const float* Tfin,
+                             const uint32_t* ncontrib, const float* dC, const float* dD, const float* dS,
+                             float* g2d, unsigned long long* bwd_pairs, int count, cudaStream_t st);
+
+// grad.cu
+cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, const float* g2d, float* dattr,
+                         float* raw_grad0, float* raw_grad1, float* raw_grad2, float* raw_grad3, float* d_xyz,
+                         float* d_l, float* d_off, float* d_mask, float* pose_part, int* n_blocks_out,
+                         cudaStream_t st);
+int chain_blocks(int64_t N);
+cudaError_t launch_codebook_reduce(int g, int L, int K, int dim, const uint32_t* perm, const uint32_t* seg,
+                                   int64_t N, const float* dattr, float* d_cb, cudaStream_t st);
+cudaError_t launch_seg_from_hist(const uint32_t* hist, int K, uint32_t* seg, cudaStream_t st);
+cudaError_t launch_icp(const SceneDev& S, const Views& V, const float* q, const float* w, float* part, int n_blocks,
+                       cudaStream_t st);
+int icp_blocks(int64_t N);
+cudaError_t launch_pose_final(int n_views, const float* pose_part, int n_pose_blocks, const float* icp_part,
+                              int n_icp_blocks, float* dxi, float* icp_loss, cudaStream_t st);
+cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const float* D, const float* S,
+                           const float* Ct, const float* Dt, float w_depth, float gate, float* dC, float* dD,
+                           float* loss, uint32_t* valid_count, cudaStream_t st);
+cudaError_t launch_idx_to_keys(const uint8_t* idx, int64_t n, uint32_t* keys, cudaStream_t st);
+
+// optim.cu
+cudaError_t launch_adam(int n, float* const* p, const float* const* g, float* const* m, float* const* v,
+                        const int64_t* size, float lr, float b1, float b2, float eps, int32_t* step_dev,
+                        int32_t step_host, cudaStream_t st);
+cudaError_t launch_pose_step(int n_views, float* pose, const float* dxi, float* m, float* v, float lr_rot,
+                             float lr_trans, float b1, float b2, float eps, int32_t* step_dev, int32_t step_host,
+                             cudaStream_t st);
+
+}  // namespace vgk

@@ -1,0 +1,149 @@
+// vg_optim.cu -- on-device optimiser steps for map parameters (Adam over up
+// to 16 arrays in one launch) and camera poses (Adam on the pose twist, then
+// the pose moves by the SE(3) exponential of the step, left-multiplied).
+#include "vg_internal.h"
+
+namespace vgk {
+
+struct AdamPack {
+    int32_t n;
+    float* p[16];
+    const float* g[16];
+    float* m[16];
+    float* v[16];
+    int64_t size[16];
+    int64_t block_start[17];
+};
+
+__global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamPack A, float lr, float b1, float b2,
+                                                   float eps, const int32_t* step_dev, int32_t step_host) {
+    int t = 0;
+    while (t + 1 < A.n && (int64_t)blockIdx.x >= A.block_start[t + 1]) ++t;
+    const int32_t step = step_dev ? step_dev[0] : step_host;
+    const float bc1 = 1.f - powf(b1, (float)step);
+    const float bc2 = 1.f - powf(b2, (float)step);
+    const float step_size = lr / bc1;
+    const float inv_sqrt_bc2 = rsqrtf(bc2);
+    const int64_t i = ((int64_t)blockIdx.x - A.block_start[t]) * 256 + threadIdx.x;
+    if (i >= A.size[t]) return;
+    const float g = A.g[t][i];
+    const float m = b1 * A.m[t][i] + (1.f - b1) * g;
+    const float v = b2 * A.v[t][i] + (1.f - b2) * g * g;
+    A.m[t][i] = m;
+    A.v[t][i] = v;
+    A.p[t][i] -= step_size * m / (sqrtf(v) * inv_sqrt_bc2 + eps);
+}
+
+__global__ void step_increment_kernel(int32_t* step_dev) { step_dev[0] += 1; }
+
+cudaError_t launch_adam(int n, float* const* p, const float* const* g, float* const* m, float* const* v,
+                        const int64_t* size, float lr, float b1, float b2, float eps, int32_t* step_dev,
+                        int32_t step_host, cudaStream_t st) {
+    AdamPack A;
+    A.n = n;
+    int64_t blocks = 0;
+    for (int i = 0; i < n; ++i) {
+        A.p[i] = p[i];
+        A.g[i] = g[i];
+        A.m[i] = m[i];
+        A.v[i] = v[i];
+        A.size[i] = size[i];
+        A.block_start[i] = blocks;
+        blocks += ceil_div(size[i], 256);
+    }
+    A.block_start[n] = blocks;
+    if (blocks > 0) {
+        count_launches(1);
+        adam_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, lr, b1, b2, eps, step_dev, step_host);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (step_dev) {
+        count_launches(1);
+        step_increment_kernel<<<1, 1, 0, st>>>(step_dev);
+    }
+    return cudaGetLastError();
+}
+
+// SE(3) exponential of xi = (rho, phi): R = exp([phi]x) (Rodrigues),
+// t = V rho with V = I + (1 - cos a)/a^2 [phi]x + (a - sin a)/a^3 [phi]x^2
+__device__ void se3_exp(const float xi[6], float R[3][3], float t[3]) {
+    const float px = xi[3], py = xi[4], pz = xi[5];
+    const float a2 = px * px + py * py + pz * pz;
+    const float a = sqrtf(a2);
+    float A, B, Cc;
+    if (a < 1e-4f) {
+        A = 1.f - a2 / 6.f;
+        B = 0.5f - a2 / 24.f;
+        Cc = 1.f / 6.f - a2 / 120.f;
+    } else {
+        A = sinf(a) / a;
+        B = (1.f - cosf(a)) / a2;
+        Cc = (a - sinf(a)) / (a2 * a);
+    }
+    const float K[3][3] = {{0.f, -pz, py}, {pz, 0.f, -px}, {-py, px, 0.f}};
+    float K2[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) K2[r][c] = K[r][0] * K[0][c] + K[r][1] * K[1][c] + K[r][2] * K[2][c];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            const float I = r == c ? 1.f : 0.f;
+            R[r][c] = I + A * K[r][c] + B * K2[r][c];
+        }
+    for (int r = 0; r < 3; ++r) {
+        float acc = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            const float I = r == c ? 1.f : 0.f;
+            acc += (I + B * K[r][c] + Cc * K2[r][c]) * xi[c];
+        }
+        t[r] = acc;
+    }
+}
+
+__global__ void pose_step_kernel(int n_views, float* pose, const float* dxi, float* m, float* v, float lr_rot,
+                                 float lr_trans, float b1, float b2, float eps, const int32_t* step_dev,
+                                 int32_t step_host) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_views) return;
+    const int32_t step = step_dev ? step_dev[0] : step_host;
+    const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
+    float d[6];
+    for (int c = 0; c < 6; ++c) {
+        const float g = dxi[w * 6 + c];
+        const float mm = b1 * m[w * 6 + c] + (1.f - b1) * g;
+        const float vv = b2 * v[w * 6 + c] + (1.f - b2) * g * g;
+        m[w * 6 + c] = mm;
+        v[w * 6 + c] = vv;
+        const float lr = c < 3 ? lr_trans : lr_rot;
+        d[c] = -lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+    }
+    float R[3][3], t[3];
+    se3_exp(d, R, t);
+    float* T = pose + w * 12;
+    float out[12];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 4; ++c) {
+            float acc = R[r][0] * T[0 * 4 + c] + R[r][1] * T[1 * 4 + c] + R[r][2] * T[2 * 4 + c];
+            if (c == 3) acc += t[r];
+            out[r * 4 + c] = acc;
+        }
+    }
+    for (int i = 0; i < 12; ++i) T[i] = out[i];
+}
+
+cudaError_t launch_pose_step(int n_views, float* pose, const float* dxi, float* m, float* v, float lr_rot,
+                             float lr_trans, float b1, float b2, float eps, int32_t* step_dev, int32_t step_host,
+                             cudaStream_t st) {
+    count_launches(1);
+    pose_step_kernel<<<(unsigned)ceil_div(n_views, 64), 64, 0, st>>>(n_views, pose, dxi, m, v, lr_rot, lr_trans, b1,
+                                                                      b2, eps, step_dev, step_host);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (step_dev) {
+        count_launches(1);
+        step_increment_kernel<<<1, 1, 0, st>>>(step_dev);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace vgk

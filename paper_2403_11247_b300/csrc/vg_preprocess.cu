@@ -1,0 +1,197 @@
+// vg_preprocess.cu -- fused decode + mask + projection of every (view, Gaussian)
+// slot, and the standalone residual-codebook decode.
+//
+// Decode follows Eq. 7 (mu = x_a + O_i * l), Eq. 14 first line (attribute =
+// sum over stages of the indexed codewords) and Eq. 11-12 (a Gaussian whose
+// mask is off is removed).  Projection follows Eq. 2 (Sigma = R S S^T R^T)
+// and Eq. 3 (Sigma' = J W Sigma W^T J^T, plus a low-pass dilation).
+#include "vg_internal.h"
+
+namespace vgk {
+
+__global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __grid_constant__ Views V, Consts cs,
+                                                         float2* __restrict__ xy, float4* __restrict__ conic_o,
+                                                         float4* __restrict__ rgbd, uint2* __restrict__ rect,
+                                                         uint32_t* __restrict__ ntiles, uint32_t* __restrict__ dkey,
+                                                         uint32_t* __restrict__ scratch, uint32_t* state) {
+    __shared__ uint32_t s_hist[4 * 256];
+    __shared__ uint32_t s_cnt[2];
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_hist[i] = 0;
+    if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) state[ST_EPOCH] += 16u;  // fresh lookback epochs for this forward
+    __syncthreads();
+
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = n < S.N;
+    uint32_t n_vis = 0, n_inv = 0;
+    if (live) {
+        float mu[3], ls[3], q[4], ol, rgb[3];
+        anchor_mean(S, n, mu);
+        decode_attr<3>(S, 0, n, ls);
+        decode_attr<4>(S, 1, n, q);
+        decode_attr<1>(S, 2, n, &ol);
+        decode_attr<3>(S, 3, n, rgb);
+        bool active = S.mask ? (__ldg(S.mask + n) > S.mask_thr) : true;
+        float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+        active = active && (qq > 0.f);
+        float Sig[6] = {0, 0, 0, 0, 0, 0};  // xx xy xz yy yz zz
+        float opac = 0.f;
+        if (active) {
+            float qn_inv = 1.f / sqrtf(qq);
+            float qn[4] = {q[0] * qn_inv, q[1] * qn_inv, q[2] * qn_inv, q[3] * qn_inv};
+            float R[3][3];
+            quat_rot(qn, R);
+            float s2[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float s = expf(ls[c]);
+                s2[c] = s * s;
+            }
+            Sig[0] = R[0][0] * R[0][0] * s2[0] + R[0][1] * R[0][1] * s2[1] + R[0][2] * R[0][2] * s2[2];
+            Sig[1] = R[0][0] * R[1][0] * s2[0] + R[0][1] * R[1][1] * s2[1] + R[0][2] * R[1][2] * s2[2];
+            Sig[2] = R[0][0] * R[2][0] * s2[0] + R[0][1] * R[2][1] * s2[1] + R[0][2] * R[2][2] * s2[2];
+            Sig[3] = R[1][0] * R[1][0] * s2[0] + R[1][1] * R[1][1] * s2[1] + R[1][2] * R[1][2] * s2[2];
+            Sig[4] = R[1][0] * R[2][0] * s2[0] + R[1][1] * R[2][1] * s2[1] + R[1][2] * R[2][2] * s2[2];
+            Sig[5] = R[2][0] * R[2][0] * s2[0] + R[2][1] * R[2][1] * s2[1] + R[2][2] * R[2][2] * s2[2];
+            opac = 1.f / (1.f + expf(-ol));
+        }
+        for (int v = 0; v < V.n; ++v) {
+            const int64_t slot = (int64_t)v * S.N + n;
+            const ViewInfo& vi = V.v[v];
+            bool ok = active;
+            float p[3] = {0, 0, 1};
+            float u = 0, vv = 0;
+            uint32_t cnt = 0;
+            int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+            float a = 0, b = 0, c = 0;
+            if (ok) {
+                float T[12];
+                view_pose(V, v, T);
+                cam_point(T, mu, p);
+                const float z = p[2];
+                ok = z > vi.near_plane;
+                if (ok) {
+                    u = __fadd_rn(__fdiv_rn(__fmul_rn(vi.fx, p[0]), z), vi.cx);
+                    vv = __fadd_rn(__fdiv_rn(__fmul_rn(vi.fy, p[1]), z), vi.cy);
+                    float txz = p[0] / z, tyz = p[1] / z;
+                    if (cs.jacobian_clamp) {
+                        txz = fminf(fmaxf(txz, -vi.limx), vi.limx);
+                        tyz = fminf(fmaxf(tyz, -vi.limy), vi.limy);
+                    }
+                    const float J00 = vi.fx / z, J02 = -vi.fx * txz / z;
+                    const float J11 = vi.fy / z, J12 = -vi.fy * tyz / z;
+                    // Sc = W Sigma W^T
+                    float W[3][3] = {{T[0], T[1], T[2]}, {T[4], T[5], T[6]}, {T[8], T[9], T[10]}};
+                    float Sm[3][3] = {{Sig[0], Sig[1], Sig[2]}, {Sig[1], Sig[3], Sig[4]}, {Sig[2], Sig[4], Sig[5]}};
+                    float T1[3][3], Sc[3][3];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc)
+                            T1[r][cc] = W[r][0] * Sm[0][cc] + W[r][1] * Sm[1][cc] + W[r][2] * Sm[2][cc];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc)
+                            Sc[r][cc] = T1[r][0] * W[cc][0] + T1[r][1] * W[cc][1] + T1[r][2] * W[cc][2];
+                    const float A = J00 * J00 * Sc[0][0] + 2.f * J00 * J02 * Sc[0][2] + J02 * J02 * Sc[2][2] + cs.dilation;
+                    const float B = J00 * J11 * Sc[0][1] + J00 * J12 * Sc[0][2] + J02 * J11 * Sc[1][2] + J02 * J12 * Sc[2][2];
+                    const float C = J11 * J11 * Sc[1][1] + 2.f * J11 * J12 * Sc[1][2] + J12 * J12 * Sc[2][2] + cs.dilation;
+                    const float det = A * C - B * B;
+                    ok = det > 0.f;
+                    if (ok) {
+                        const float inv = 1.f / det;
+                        a = C * inv;
+                        b = -B * inv;
+                        c = A * inv;
+                        const float mid = 0.5f * (A + C);
+                        const float lam = mid + sqrtf(fmaxf(0.f, mid * mid - det));
+                        float rr = cs.sigma_cull * sqrtf(lam);
+                        int radius = (rr < (float)RADIUS_MAX) ? (int)ceilf(rr) : RADIUS_MAX;
+                        const float rf = (float)radius;
+                        const float fx0 = floorf(__fdiv_rn(__fsub_rn(u, rf), (float)TILE));
+                        const float fx1 = floorf(__fdiv_rn(__fadd_rn(u, rf), (float)TILE)) + 1.f;
+                        const float fy0 = floorf(__fdiv_rn(__fsub_rn(vv, rf), (float)TILE));
+                        const float fy1 = floorf(__fdiv_rn(__fadd_rn(vv, rf), (float)TILE)) + 1.f;
+                        x0 = (int)fminf(fmaxf(fx0, 0.f), (float)vi.tiles_x);
+                        x1 = (int)fminf(fmaxf(fx1, 0.f), (float)vi.tiles_x);
+                        y0 = (int)fminf(fmaxf(fy0, 0.f), (float)vi.tiles_y);
+                        y1 = (int)fminf(fmaxf(fy1, 0.f), (float)vi.tiles_y);
+                        ok = (x1 > x0) && (y1 > y0);
+                        cnt = ok ? (uint32_t)((x1 - x0) * (y1 - y0)) : 0u;
+                    }
+                }
+            }
+            if (ok) {
+                xy[slot] = make_float2(u, vv);
+                conic_o[slot] = make_float4(a, b, c, opac);
+                rgbd[slot] = make_float4(rgb[0], rgb[1], rgb[2], p[2]);
+                rect[slot] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+                ntiles[slot] = cnt;
+                const uint32_t key = __float_as_uint(p[2]);
+                dkey[slot] = key;
+#pragma unroll
+                for (int pass = 0; pass < 4; ++pass) atomicAdd(&s_hist[pass * 256 + ((key >> (8 * pass)) & 255u)], 1u);
+                ++n_vis;
+            } else {
+                ntiles[slot] = 0u;
+                dkey[slot] = 0xffffffffu;
+                ++n_inv;
+            }
+        }
+    }
+    if (n_inv) {
+#pragma unroll
+        for (int pass = 0; pass < 4; ++pass) atomicAdd(&s_hist[pass * 256 + 255], n_inv);
+    }
+    if (n_vis) atomicAdd(&s_cnt[0], n_vis);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+        uint32_t h = s_hist[i];
+        if (h) atomicAdd(scratch + SCR_DEPTH_HIST + i, h);
+    }
+    if (threadIdx.x == 0 && s_cnt[0]) atomicAdd(scratch + SCR_NVIS, s_cnt[0]);
+}
+
+cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& cs, float2* xy, float4* conic_o,
+                              float4* rgbd, uint2* rect, uint32_t* ntiles, uint32_t* dkey, uint32_t* scratch,
+                              uint32_t* state, cudaStream_t st) {
+    int64_t blocks = ceil_div(S.N > 0 ? S.N : 1, 256);
+    count_launches(1);
+    preprocess_kernel<<<(unsigned)blocks, 256, 0, st>>>(S, V, cs, xy, conic_o, rgbd, rect, ntiles, dkey, scratch, state);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// standalone residual-codebook decode: one thread per output element
+// ---------------------------------------------------------------------------
+__global__ void rvq_decode_kernel(int dim, int L, int K, const float* __restrict__ cb, const uint8_t* __restrict__ idx,
+                                  const float* __restrict__ raw, int64_t n, float* __restrict__ out) {
+    const int64_t total = n * dim;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        if (L == 0) {
+            out[e] = raw[e];
+            continue;
+        }
+        const int64_t i = e / dim;
+        const int c = (int)(e - i * dim);
+        float acc = 0.f;
+        for (int s = 0; s < L; ++s) {
+            int k = __ldg(idx + (int64_t)s * n + i);
+            acc += __ldg(cb + ((int64_t)s * K + k) * dim + c);
+        }
+        out[e] = acc;
+    }
+}
+
+cudaError_t launch_rvq_decode(int dim, int L, int K, const float* cb, const uint8_t* idx, const float* raw, int64_t n,
+                              float* out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = ceil_div(n * dim, 256);
+    if (blocks > 148 * 32) blocks = 148 * 32;
+    count_launches(1);
+    rvq_decode_kernel<<<(unsigned)blocks, 256, 0, st>>>(dim, L, K, cb, idx, raw, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace vgk

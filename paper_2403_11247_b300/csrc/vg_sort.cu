@@ -1,0 +1,320 @@
+// vg_sort.cu -- tile binning: an in-house onesweep LSD radix sort (one kernel
+// per 8-bit digit, decoupled look-back across partitions, digit histograms
+// computed up front by the producer kernels), the fused scan + duplicate
+// kernel that emits (tile, Gaussian) pairs in depth order, and per-tile ranges.
+//
+// Order produced: every tile's list ascending by (FP32 depth bits, slot
+// index).  The depth sort is a stable sort of slot ids by depth key (ties keep
+// slot order); pairs are then emitted in that order and stably sorted by tile
+// key, so within a tile the depth order survives.
+//
+// Look-back entries are 64-bit: [epoch:32][flag:2][count:30].  The epoch comes
+// from device memory (bumped once per forward), so entries left by earlier
+// sorts never look ready and no memset of the look-back arrays is needed.
+// Every wait on another partition is bounded (SPIN_LIMIT polls); on timeout
+// the kernel sets ERR_WAIT and carries on with a zero count.
+#include "vg_internal.h"
+
+namespace vgk {
+
+constexpr unsigned long long LB_AGG = 1ull << 30;
+constexpr unsigned long long LB_INC = 2ull << 30;
+constexpr unsigned long long LB_COUNT = (1ull << 30) - 1;
+
+__device__ __forceinline__ unsigned long long lb_make(uint32_t epoch, unsigned long long flag, uint32_t count) {
+    return ((unsigned long long)epoch << 32) | flag | (unsigned long long)count;
+}
+
+// Walk back from partition pid-1, summing counts until an inclusive prefix.
+__device__ __forceinline__ uint32_t lookback_walk(const unsigned long long* lb, int stride, int col, uint32_t pid,
+                                                  uint32_t epoch, uint32_t* err) {
+    uint32_t excl = 0;
+    int64_t j = (int64_t)pid - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+        unsigned long long s = ld_volatile64(lb + j * stride + col);
+        if ((uint32_t)(s >> 32) != epoch || (s & (LB_AGG | LB_INC)) == 0) {
+            if (++spins > SPIN_LIMIT) {
+                atomicOr(err, ERR_WAIT);
+                break;
+            }
+            continue;
+        }
+        excl += (uint32_t)(s & LB_COUNT);
+        if (s & LB_INC) break;
+        --j;
+    }
+    return excl;
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) onesweep_pass_kernel(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, const uint32_t* n_dev, uint32_t n_cap, int shift, const uint32_t* __restrict__ hist,
+    unsigned long long* lookback, uint32_t* counter, const uint32_t* state, uint32_t epoch_offset, uint32_t* err) {
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_whist[8][256];
+    __shared__ uint32_t s_bpre[256];
+    __shared__ uint32_t s_gout[256];
+    __shared__ uint32_t s_keys[SORT_TILE];
+    __shared__ uint32_t s_vals[SORT_TILE];
+    __shared__ uint32_t s_tmp[8];
+    __shared__ uint32_t s_pid;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t n = n_dev ? min(*n_dev, n_cap) : n_cap;
+    const uint32_t nparts = (n + SORT_TILE - 1) / SORT_TILE;
+    const uint32_t epoch = state[ST_EPOCH] + epoch_offset;
+    uint32_t tot;
+    s_base[tid] = block_excl_scan_256(hist[tid], s_tmp, &tot);
+    const uint32_t lt = lanemask_lt();
+
+    for (;;) {
+        if (tid == 0) s_pid = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t pid = s_pid;
+        if (pid >= nparts) break;
+        for (int i = lane; i < 256; i += 32) s_whist[warp][i] = 0;
+        __syncwarp();
+        const uint32_t base = pid * SORT_TILE + warp * (32 * SORT_ITEMS);
+        uint32_t key[SORT_ITEMS], val[SORT_ITEMS], rank[SORT_ITEMS];
+#pragma unroll
+        for (int i = 0; i < SORT_ITEMS; ++i) {
+            const uint32_t idx = base + i * 32 + lane;
+            const bool valid = idx < n;
+            key[i] = valid ? keys_in[idx] : 0u;
+            val[i] = valid ? (vals_in ? vals_in[idx] : idx) : 0u;
+            const uint32_t d = valid ? ((key[i] >> shift) & 255u) : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const int leader = __ffs(peers) - 1;
+            uint32_t cnt = 0;
+            if (valid && lane == leader) {
+                cnt = s_whist[warp][d];
+                s_whist[warp][d] = cnt + __popc(peers);
+            }
+            cnt = __shfl_sync(0xffffffffu, cnt, leader);
+            rank[i] = cnt + __popc(peers & lt);
+            __syncwarp();
+        }
+        __syncthreads();
+        // per digit (thread = digit): warp-exclusive prefix and partition total
+        uint32_t total = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            uint32_t c = s_whist[w][tid];
+            s_whist[w][tid] = total;
+            total += c;
+        }
+        unsigned long long* lb = lookback;
+        st_volatile64(lb + (int64_t)pid * 256 + tid, lb_make(epoch, pid == 0 ? LB_INC : LB_AGG, total));
+        uint32_t btot;
+        s_bpre[tid] = block_excl_scan_256(total, s_tmp, &btot);
+        uint32_t excl = 0;
+        if (pid > 0) {
+            excl = lookback_walk(lb, 256, tid, pid, epoch, err);
+            st_volatile64(lb + (int64_t)pid * 256 + tid, lb_make(epoch, LB_INC, excl + total));
+        }
+        s_gout[tid] = s_base[tid] + excl;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < SORT_ITEMS; ++i) {
+            const uint32_t idx = base + i * 32 + lane;
+            if (idx < n) {
+                const uint32_t d = (key[i] >> shift) & 255u;
+                const uint32_t pos = s_bpre[d] + s_whist[warp][d] + rank[i];
+                s_keys[pos] = key[i];
+                s_vals[pos] = val[i];
+            }
+        }
+        __syncthreads();
+        const uint32_t nvalid = min((uint32_t)SORT_TILE, n - pid * SORT_TILE);
+        for (uint32_t j = tid; j < nvalid; j += SORT_THREADS) {
+            const uint32_t k = s_keys[j];
+            const uint32_t d = (k >> shift) & 255u;
+            const uint32_t g = s_gout[d] + (j - s_bpre[d]);
+            keys_out[g] = k;
+            vals_out[g] = s_vals[j];
+        }
+        __syncthreads();
+    }
+}
+
+int sort_pass_grid(uint32_t n_cap) {
+    static int max_grid = 0;
+    if (!max_grid) {
+        int dev = 0, sms = 148, per = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, onesweep_pass_kernel, SORT_THREADS, 0);
+        max_grid = sms * (per > 0 ? per : 1);
+    }
+    int64_t parts = ceil_div((int64_t)n_cap, SORT_TILE);
+    if (parts < 1) parts = 1;
+    return (int)(parts < max_grid ? parts : max_grid);
+}
+
+cudaError_t launch_sort_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
+                             const uint32_t* n_dev, uint32_t n_cap, int shift, const uint32_t* hist,
+                             unsigned long long* lookback, uint32_t* counter, const uint32_t* state,
+                             uint32_t epoch_offset, uint32_t* err, int grid, cudaStream_t st) {
+    count_launches(1);
+    onesweep_pass_kernel<<<grid, SORT_THREADS, 0, st>>>(keys_in, vals_in, keys_out, vals_out, n_dev, n_cap, shift, hist,
+                                                        lookback, counter, state, epoch_offset, err);
+    return cudaGetLastError();
+}
+
+// digit histograms of u32 keys for `passes` 8-bit digits (hist must be zeroed)
+__global__ void hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int passes, uint32_t* hist) {
+    __shared__ uint32_t s[4 * 256];
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s[i] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&s[p * 256 + ((k >> (8 * p)) & 255u)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
+        if (s[i]) atomicAdd(hist + i, s[i]);
+}
+
+cudaError_t launch_hist(const uint32_t* keys, int64_t n, int passes, uint32_t* hist, cudaStream_t st) {
+    int64_t blocks = ceil_div(n > 0 ? n : 1, 1024);
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    count_launches(1);
+    hist_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys, n, passes, hist);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// scan of tile counts in depth order + pair emission (persistent partitions)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
+    const uint32_t* __restrict__ sorted_slots, const uint32_t* __restrict__ ntiles, const uint2* __restrict__ rect,
+    int64_t N, const __grid_constant__ Views V, uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals, uint32_t cap,
+    uint32_t* scratch, int tile_passes, unsigned long long* lookback, const uint32_t* state, uint32_t epoch_offset,
+    uint32_t* err) {
+    __shared__ uint32_t s_hist[3 * 256];
+    __shared__ uint32_t s_tmp[8];
+    __shared__ uint32_t s_pid;
+    __shared__ uint32_t s_excl;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 3 * 256; i += DUP_THREADS) s_hist[i] = 0;
+    const uint32_t nvis = scratch[SCR_NVIS];
+    const uint32_t nparts = (nvis + DUP_TILE - 1) / DUP_TILE;
+    const uint32_t epoch = state[ST_EPOCH] + epoch_offset;
+    uint32_t* counter = scratch + SCR_CNT_DUP;
+    __syncthreads();
+    for (;;) {
+        if (tid == 0) s_pid = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t pid = s_pid;
+        if (pid >= nparts) break;
+        uint32_t slot[DUP_ITEMS], cnt[DUP_ITEMS];
+        uint32_t local = 0;
+#pragma unroll
+        for (int i = 0; i < DUP_ITEMS; ++i) {
+            const uint32_t pos = pid * DUP_TILE + tid * DUP_ITEMS + i;
+            slot[i] = pos < nvis ? sorted_slots[pos] : 0u;
+            cnt[i] = pos < nvis ? ntiles[slot[i]] : 0u;
+            local += cnt[i];
+        }
+        uint32_t agg;
+        uint32_t pre = block_excl_scan_256(local, s_tmp, &agg);
+        if (tid == 0) {
+            st_volatile64(lookback + pid, lb_make(epoch, pid == 0 ? LB_INC : LB_AGG, agg));
+            uint32_t excl = 0;
+            if (pid > 0) {
+                excl = lookback_walk(lookback, 1, 0, pid, epoch, err);
+                st_volatile64(lookback + pid, lb_make(epoch, LB_INC, excl + agg));
+            }
+            s_excl = excl;
+            if (pid == nparts - 1) {
+                scratch[SCR_PAIRS] = excl + agg;
+                if (excl + agg > cap) atomicOr(err, ERR_OVERFLOW);
+            }
+        }
+        __syncthreads();
+        uint32_t off = s_excl + pre;
+#pragma unroll
+        for (int i = 0; i < DUP_ITEMS; ++i) {
+            if (!cnt[i]) continue;
+            const uint32_t s = slot[i];
+            const int v = (int)(s / (uint64_t)N);
+            const uint2 r = rect[s];
+            const int x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff, y1 = r.y >> 16;
+            const int tbase = V.v[v].tile_base, tx = V.v[v].tiles_x;
+            for (int ty = y0; ty < y1; ++ty)
+                for (int txi = x0; txi < x1; ++txi) {
+                    if (off < cap) {
+                        const uint32_t key = (uint32_t)(tbase + ty * tx + txi);
+                        pkeys[off] = key;
+                        pvals[off] = s;
+                        for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 255u)], 1u);
+                    }
+                    ++off;
+                }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int i = tid; i < tile_passes * 256; i += DUP_THREADS) {
+        const uint32_t h = s_hist[i];
+        if (h) atomicAdd(scratch + SCR_TILE_HIST + i, h);
+    }
+}
+
+cudaError_t launch_duplicate(const uint32_t* sorted_slots, const uint32_t* /*scratch_nvis*/, const uint32_t* ntiles,
+                             const uint2* rect, int64_t N, const Views& V, uint32_t* pkeys, uint32_t* pvals, uint32_t cap,
+                             uint32_t* scratch, int tile_passes, unsigned long long* lookback, const uint32_t* state,
+                             uint32_t epoch_offset, uint32_t* err, int64_t max_slots, cudaStream_t st) {
+    static int max_grid = 0;
+    if (!max_grid) {
+        int dev = 0, sms = 148, per = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, duplicate_kernel, DUP_THREADS, 0);
+        max_grid = sms * (per > 0 ? per : 1);
+    }
+    int64_t parts = ceil_div(max_slots > 0 ? max_slots : 1, DUP_TILE);
+    int grid = (int)(parts < max_grid ? parts : max_grid);
+    count_launches(1);
+    duplicate_kernel<<<grid, DUP_THREADS, 0, st>>>(sorted_slots, ntiles, rect, N, V, pkeys, pvals, cap, scratch,
+                                                   tile_passes, lookback, state, epoch_offset, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// per-tile [start, end) of the sorted pair keys by binary search
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* keys, uint32_t n, uint32_t x) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (keys[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* pairs_dev, uint32_t cap, int n_tiles,
+                              uint2* __restrict__ ranges) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const uint32_t n = min(*pairs_dev, cap);
+    ranges[t] = make_uint2(lower_bound_u32(keys, n, (uint32_t)t), lower_bound_u32(keys, n, (uint32_t)t + 1u));
+}
+
+cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* pairs_dev, uint32_t cap, int n_tiles, uint2* ranges,
+                          cudaStream_t st) {
+    count_launches(1);
+    ranges_kernel<<<(unsigned)ceil_div(n_tiles, 256), 256, 0, st>>>(keys, pairs_dev, cap, n_tiles, ranges);
+    return cudaGetLastError();
+}
+
+__global__ void epoch_bump_kernel(uint32_t* state, uint32_t by) { state[ST_EPOCH] += by; }
+
+cudaError_t launch_epoch_bump(uint32_t* state, uint32_t by, cudaStream_t st) {
+    count_launches(1);
+    epoch_bump_kernel<<<1, 1, 0, st>>>(state, by);
+    return cudaGetLastError();
+}
+
+}  // namespace vgk

@@ -1,0 +1,486 @@
+"""Thin ctypes binding of libvg (include/vg.h), one Python function per C call
+and with the same name.  Argument marshalling only: every step of the render
+path runs in the CUDA library; there is no CPU fallback.  PyTorch provides
+device memory and streams.
+
+Tensors passed in must be contiguous CUDA tensors of the stated dtype; host
+numpy arrays are accepted only where the C call accepts host memory
+(vg_scene_upload with VG_SCENE_COPY).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libvg.so")
+
+VG_OK, VG_ERR_INVALID_ARG, VG_ERR_OOM, VG_ERR_CUDA, VG_ERR_CAPACITY, VG_ERR_TIMEOUT, VG_ERR_UNIMPLEMENTED = range(7)
+STATUS_NAMES = ["VG_OK", "VG_ERR_INVALID_ARG", "VG_ERR_OOM", "VG_ERR_CUDA", "VG_ERR_CAPACITY", "VG_ERR_TIMEOUT",
+                "VG_ERR_UNIMPLEMENTED"]
+VG_SCENE_COPY, VG_SCENE_BORROW = 0, 1
+VG_MAX_VIEWS = 64
+GROUPS = ("logscale", "rot", "opacity", "rgb")
+GDIM = {"logscale": 3, "rot": 4, "opacity": 1, "rgb": 3}
+
+
+class VgError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class vg_camera(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32), ("T_cw", C.c_float * 12), ("near_plane", C.c_float)]
+
+
+class vg_attr_group(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("stages", C.c_int32), ("codewords", C.c_int32),
+                ("codebook", C.c_void_p), ("idx", C.c_void_p), ("raw", C.c_void_p)]
+
+
+class vg_scene_desc(C.Structure):
+    _fields_ = [("n_anchors", C.c_int64), ("k", C.c_int32),
+                ("anchor_xyz", C.c_void_p), ("anchor_l", C.c_void_p), ("offsets", C.c_void_p),
+                ("logscale", vg_attr_group), ("rot", vg_attr_group), ("opacity", vg_attr_group), ("rgb", vg_attr_group),
+                ("mask_logit", C.c_void_p), ("mask_eps", C.c_float)]
+
+
+class vg_render_params(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("batch", C.c_int32),
+                ("alpha_max", C.c_float), ("alpha_min", C.c_float), ("t_min", C.c_float), ("dilation", C.c_float),
+                ("sigma_cull", C.c_float), ("clamp_factor", C.c_float),
+                ("jacobian_clamp", C.c_int32), ("count_evals", C.c_int32), ("pose_dev", C.c_void_p)]
+
+
+class vg_scene_grads(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("anchor_xyz", "anchor_l", "offsets", "logscale", "rot", "opacity", "rgb",
+                                          "mask_logit")]
+
+
+class vg_stats(C.Structure):
+    _fields_ = [("pairs", C.c_int64), ("pair_capacity", C.c_int64), ("visible", C.c_int64),
+                ("evaluated", C.c_int64), ("blended", C.c_int64), ("bwd_pairs", C.c_int64), ("flags", C.c_uint32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libvg.so.  Raises if it has not been built: there is no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libvg.so not found at {LIB_PATH}; build it with paper_2403_11247_b300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+        sig = {
+            "vg_scene_upload": [P, I32, P, P],
+            "vg_scene_free": [P],
+            "vg_ctx_create": [I64, P],
+            "vg_ctx_free": [P],
+            "vg_ctx_reserve": [P, I64],
+            "vg_check": [P, P],
+            "vg_ctx_stats": [P, P, P],
+            "vg_ctx_reset_counters": [P, P],
+            "vg_ctx_buffer": [P, I32, P, P],
+            "vg_ctx_profile": [P, I32],
+            "vg_ctx_profile_read": [P, P, P, P],
+            "vg_rvq_decode": [P, I64, P, P],
+            "vg_render_fwd": [P, P, I32, P, P, P, P, P, P],
+            "vg_render_bwd": [P, P, I32, P, P, P, P, P, P, P],
+            "vg_pose_grad": [P, I32, P, P, P, P, P],
+            "vg_loss_l1": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P, P],
+            "vg_adam_step": [P, I32, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
+            "vg_pose_step": [I32, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.vg_last_error.restype = C.c_char_p
+        L.vg_last_error.argtypes = []
+        L.vg_default_params.restype = vg_render_params
+        L.vg_default_params.argtypes = []
+        L.vg_launch_count.restype = C.c_int64
+        L.vg_launch_count.argtypes = []
+        L.vg_scene_size.restype = C.c_int64
+        L.vg_scene_size.argtypes = [P]
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != VG_OK:
+        raise VgError(status, where, lib().vg_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        raise TypeError("a device tensor is required here, not a numpy array")
+    if not t.is_cuda:
+        raise TypeError("a CUDA tensor is required")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _host_or_dev_ptr(a):
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data, a
+    return _ptr(a), a
+
+
+def default_params(**kw) -> vg_render_params:
+    p = lib().vg_default_params()
+    for k, v in kw.items():
+        if k == "pose_dev":
+            p.pose_dev = _ptr(v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def cameras(cams: Sequence) -> C.Array:
+    arr = (vg_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i].fx, arr[i].fy, arr[i].cx, arr[i].cy = c.fx, c.fy, c.cx, c.cy
+        arr[i].width, arr[i].height = c.width, c.height
+        T = np.asarray(c.T_cw, np.float32).reshape(12)
+        for j in range(12):
+            arr[i].T_cw[j] = float(T[j])
+        arr[i].near_plane = c.near
+    return arr
+
+
+# ---------------------------------------------------------------------------
+# scenes and workspaces
+# ---------------------------------------------------------------------------
+
+class SceneHandle:
+    """An owned vg_scene; keeps borrowed tensors alive."""
+
+    def __init__(self, handle: int, keep, n: int, n_anchors: int, k: int, coded: Dict[str, tuple], masked: bool):
+        self.handle = handle
+        self._keep = keep
+        self.n = n
+        self.n_anchors = n_anchors
+        self.k = k
+        self.coded = coded          # group -> (L, K) for coded groups
+        self.masked = masked
+
+    def free(self):
+        if self.handle:
+            _check(lib().vg_scene_free(self.handle), "vg_scene_free")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def vg_scene_upload(scene, flags: int = VG_SCENE_COPY, stream=None) -> SceneHandle:
+    """``scene``: a synth.Scene (numpy host arrays, COPY) or any object with the
+    same attributes holding CUDA tensors (COPY or BORROW)."""
+    desc = vg_scene_desc()
+    keep = []
+
+    def put(a):
+        p, ref = _host_or_dev_ptr(a)
+        if ref is not None:
+            keep.append(ref)
+        return p
+
+    desc.n_anchors = int(scene.anchor_xyz.shape[0])
+    desc.k = int(scene.offsets.shape[1])
+    desc.anchor_xyz = put(scene.anchor_xyz)
+    desc.anchor_l = put(scene.anchor_l)
+    desc.offsets = put(scene.offsets)
+    coded = {}
+    for name in GROUPS:
+        g = scene.groups[name]
+        grp = getattr(desc, name)
+        grp.dim = GDIM[name]
+        if g.codebook is not None:
+            grp.stages, grp.codewords = int(g.codebook.shape[0]), int(g.codebook.shape[1])
+            grp.codebook = put(g.codebook)
+            grp.idx = put(g.idx)
+            grp.raw = None
+            coded[name] = (grp.stages, grp.codewords)
+        else:
+            grp.stages, grp.codewords = 0, 0
+            grp.raw = put(g.raw)
+    desc.mask_logit = put(scene.mask_logit)
+    desc.mask_eps = float(scene.mask_eps)
+    h = C.c_void_p()
+    _check(lib().vg_scene_upload(C.byref(desc), flags, _stream(stream), C.byref(h)), "vg_scene_upload")
+    n = desc.n_anchors * desc.k
+    return SceneHandle(h.value, keep if flags == VG_SCENE_BORROW else None, n, desc.n_anchors, desc.k, coded,
+                       scene.mask_logit is not None)
+
+
+class CtxHandle:
+    def __init__(self, handle: int):
+        self.handle = handle
+        self.views = None
+
+    def free(self):
+        if self.handle:
+            _check(lib().vg_ctx_free(self.handle), "vg_ctx_free")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def vg_ctx_create(pair_capacity: int = 0) -> CtxHandle:
+    h = C.c_void_p()
+    _check(lib().vg_ctx_create(int(pair_capacity), C.byref(h)), "vg_ctx_create")
+    return CtxHandle(h.value)
+
+
+def vg_ctx_reserve(ctx: CtxHandle, pair_capacity: int):
+    _check(lib().vg_ctx_reserve(ctx.handle, int(pair_capacity)), "vg_ctx_reserve")
+
+
+def vg_ctx_stats(ctx: CtxHandle, stream=None) -> Dict[str, int]:
+    s = vg_stats()
+    _check(lib().vg_ctx_stats(ctx.handle, _stream(stream), C.byref(s)), "vg_ctx_stats")
+    return dict(pairs=s.pairs, pair_capacity=s.pair_capacity, visible=s.visible, evaluated=s.evaluated,
+                blended=s.blended, bwd_pairs=s.bwd_pairs, flags=s.flags)
+
+
+def vg_check(ctx: CtxHandle, stream=None) -> int:
+    """Returns the status code (VG_OK, VG_ERR_CAPACITY, ...) without raising."""
+    return lib().vg_check(ctx.handle, _stream(stream))
+
+
+def vg_ctx_reset_counters(ctx: CtxHandle, stream=None):
+    _check(lib().vg_ctx_reset_counters(ctx.handle, _stream(stream)), "vg_ctx_reset_counters")
+
+
+# ---------------------------------------------------------------------------
+# compute calls
+# ---------------------------------------------------------------------------
+
+def vg_rvq_decode(codebook, idx, out=None, stream=None):
+    """codebook [L,K,d] f32 CUDA, idx [L,n] u8 CUDA -> out [n,d] f32."""
+    torch = _torch()
+    L, K, d = codebook.shape
+    n = idx.shape[1]
+    if out is None:
+        out = torch.empty((n, d), dtype=torch.float32, device=codebook.device)
+    g = vg_attr_group(int(d), int(L), int(K), _ptr(codebook), _ptr(idx), None)
+    _check(lib().vg_rvq_decode(C.byref(g), int(n), _ptr(out), _stream(stream)), "vg_rvq_decode")
+    return out
+
+
+def image_sizes(cams):
+    return [c.width * c.height for c in cams]
+
+
+def vg_render_fwd(scene: SceneHandle, cams, params: Optional[vg_render_params], ctx: CtxHandle,
+                  C_=None, D=None, S=None, stream=None):
+    """Returns flat (C [3*P], D [P], S [P]) CUDA tensors (per-view planar blocks)."""
+    torch = _torch()
+    P = sum(image_sizes(cams))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if C_ is None:
+        C_ = torch.empty(3 * P, dtype=torch.float32, device=dev)
+    if D is None:
+        D = torch.empty(P, dtype=torch.float32, device=dev)
+    if S is None:
+        S = torch.empty(P, dtype=torch.float32, device=dev)
+    p = params if params is not None else default_params()
+    cc = cameras(cams)
+    _check(lib().vg_render_fwd(scene.handle, cc, len(cams), C.byref(p), ctx.handle, _ptr(C_), _ptr(D), _ptr(S),
+                               _stream(stream)), "vg_render_fwd")
+    return C_, D, S
+
+
+def grads_like(scene: SceneHandle, device=None, mask=True):
+    """Allocate a full set of gradient tensors for ``scene``."""
+    torch = _torch()
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    f = dict(dtype=torch.float32, device=dev)
+    g = dict(anchor_xyz=torch.empty((scene.n_anchors, 3), **f), anchor_l=torch.empty((scene.n_anchors, 3), **f),
+             offsets=torch.empty((scene.n_anchors, scene.k, 3), **f))
+    for name in GROUPS:
+        if name in scene.coded:
+            L, K = scene.coded[name]
+            g[name] = torch.empty((L, K, GDIM[name]), **f)
+        else:
+            g[name] = torch.empty((scene.n, GDIM[name]), **f)
+    if mask and scene.masked:
+        g["mask_logit"] = torch.empty(scene.n, **f)
+    return g
+
+
+def vg_render_bwd(scene: SceneHandle, cams, params: Optional[vg_render_params], ctx: CtxHandle,
+                  dC=None, dD=None, dS=None, grads: Optional[Dict] = None, stream=None):
+    if grads is None:
+        grads = grads_like(scene)
+    sg = vg_scene_grads()
+    for name, _ in vg_scene_grads._fields_:
+        setattr(sg, name, _ptr(grads.get(name)))
+    p = params if params is not None else default_params()
+    cc = cameras(cams)
+    _check(lib().vg_render_bwd(scene.handle, cc, len(cams), C.byref(p), ctx.handle, _ptr(dC), _ptr(dD), _ptr(dS),
+                               C.byref(sg), _stream(stream)), "vg_render_bwd")
+    return grads
+
+
+def vg_pose_grad(ctx: CtxHandle, n_views: int, icp_q=None, icp_w=None, dxi=None, icp_loss=None, stream=None):
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if dxi is None:
+        dxi = torch.empty((n_views, 6), dtype=torch.float32, device=dev)
+    if icp_q is not None and icp_loss is None:
+        icp_loss = torch.empty(n_views, dtype=torch.float32, device=dev)
+    _check(lib().vg_pose_grad(ctx.handle, int(n_views), _ptr(icp_q), _ptr(icp_w), _ptr(dxi), _ptr(icp_loss),
+                              _stream(stream)), "vg_pose_grad")
+    return dxi, icp_loss
+
+
+def vg_loss_l1(n_views: int, n_pix: int, C_, D, S, Ct, Dt, w_depth: float, gate: float, ctx: CtxHandle,
+               dC=None, dD=None, dS=None, loss=None, stream=None):
+    torch = _torch()
+    if dC is None:
+        dC = torch.empty_like(C_)
+    if dD is None:
+        dD = torch.empty_like(D)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=C_.device)
+    _check(lib().vg_loss_l1(int(n_views), int(n_pix), _ptr(C_), _ptr(D), _ptr(S), _ptr(Ct), _ptr(Dt), float(w_depth),
+                            float(gate), _ptr(dC), _ptr(dD), _ptr(dS), _ptr(loss), ctx.handle, _stream(stream)),
+           "vg_loss_l1")
+    return dC, dD, dS, loss
+
+
+VG_BUF = dict(xy=0, conic=1, rgbd=2, rect=3, ntiles=4, pair_keys=5, pair_vals=6, ranges=7, t_final=8, n_contrib=9,
+              g2d=10)
+_BUF_DTYPE = dict(xy=("float32", 2), conic=("float32", 4), rgbd=("float32", 4), rect=("uint32", 2),
+                  ntiles=("uint32", 1), pair_keys=("uint32", 1), pair_vals=("uint32", 1), ranges=("uint32", 2),
+                  t_final=("float32", 1), n_contrib=("uint32", 1), g2d=("float32", 10))
+
+
+def vg_ctx_buffer(ctx: CtxHandle, which: str, count: int, stream=None) -> np.ndarray:
+    """Copy ``count`` records of an intermediate workspace array to the host
+    (synchronises the stream)."""
+    torch = _torch()
+    ptr, nbytes = C.c_void_p(), C.c_int64()
+    _check(lib().vg_ctx_buffer(ctx.handle, VG_BUF[which], C.byref(ptr), C.byref(nbytes)), "vg_ctx_buffer")
+    dt, width = _BUF_DTYPE[which]
+    rec = np.dtype(dt).itemsize * width
+    if count * rec > nbytes.value:
+        raise ValueError(f"{which}: {count} records exceed the buffer ({nbytes.value} bytes)")
+    out = np.empty(count * width, dtype=dt)
+    (torch.cuda.current_stream() if stream is None else stream).synchronize()
+    if count:
+        res = _cudart().cudaMemcpy(C.c_void_p(out.ctypes.data), ptr, C.c_size_t(count * rec), 2)  # device -> host
+        if int(res) != 0:
+            raise RuntimeError(f"cudaMemcpy failed: {res}")
+    return out.reshape(count, width) if width > 1 else out
+
+
+_cudart_lib = None
+
+
+def _cudart():
+    global _cudart_lib
+    if _cudart_lib is None:
+        _cudart_lib = C.CDLL("libcudart.so.13")
+        _cudart_lib.cudaMemcpy.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
+        _cudart_lib.cudaMemcpy.restype = C.c_int
+    return _cudart_lib
+
+
+class vg_adam_tensor(C.Structure):
+    _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p), ("n", C.c_int64)]
+
+
+def vg_adam_step(params, grads, ms, vs, lr, beta1=0.9, beta2=0.999, eps=1e-15, step_dev=None, step_host=0,
+                 stream=None):
+    """Adam over lists of equally-shaped CUDA tensors (one launch)."""
+    n = len(params)
+    arr = (vg_adam_tensor * n)()
+    for i in range(n):
+        arr[i].param, arr[i].grad = _ptr(params[i]), _ptr(grads[i])
+        arr[i].m, arr[i].v, arr[i].n = _ptr(ms[i]), _ptr(vs[i]), params[i].numel()
+    _check(lib().vg_adam_step(arr, n, lr, beta1, beta2, eps, _ptr(step_dev), int(step_host), _stream(stream)),
+           "vg_adam_step")
+
+
+def vg_pose_step(pose, dxi, m, v, lr_rot, lr_trans, beta1=0.9, beta2=0.999, eps=1e-15, step_dev=None, step_host=0,
+                 stream=None):
+    _check(lib().vg_pose_step(int(pose.shape[0]), _ptr(pose), _ptr(dxi), _ptr(m), _ptr(v), lr_rot, lr_trans, beta1,
+                              beta2, eps, _ptr(step_dev), int(step_host), _stream(stream)), "vg_pose_step")
+
+
+STAGES = ("preprocess", "depth_sort", "duplicate", "tile_sort", "ranges", "blend_fwd", "loss", "blend_bwd", "chain",
+          "codebook", "pose", "memset")
+
+
+def vg_ctx_profile(ctx: CtxHandle, enable: bool):
+    _check(lib().vg_ctx_profile(ctx.handle, 1 if enable else 0), "vg_ctx_profile")
+
+
+def vg_ctx_profile_read(ctx: CtxHandle, stream=None) -> Dict[str, tuple]:
+    """{stage: (total ms, launches)} since profiling was enabled."""
+    ms = (C.c_double * len(STAGES))()
+    n = (C.c_int64 * len(STAGES))()
+    _check(lib().vg_ctx_profile_read(ctx.handle, _stream(stream), ms, n), "vg_ctx_profile_read")
+    return {s: (ms[i], n[i]) for i, s in enumerate(STAGES)}
+
+
+def vg_launch_count() -> int:
+    return int(lib().vg_launch_count())
+
+
+def exported_symbols():
+    return ["vg_scene_upload", "vg_scene_free", "vg_scene_size", "vg_ctx_create", "vg_ctx_free", "vg_ctx_reserve",
+            "vg_check", "vg_ctx_stats", "vg_ctx_reset_counters", "vg_ctx_buffer", "vg_ctx_profile",
+            "vg_ctx_profile_read", "vg_adam_step", "vg_pose_step", "vg_rvq_decode", "vg_render_fwd",
+            "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_last_error", "vg_default_params", "vg_launch_count"]
+
+
+def render_with_retry(scene: SceneHandle, cams, params, ctx: CtxHandle, stream=None, max_tries: int = 4):
+    """Forward, and if the pair buffer overflowed, grow it and render again
+    (the overflowed outputs are discarded).  Synchronises the stream."""
+    for _ in range(max_tries):
+        out = vg_render_fwd(scene, cams, params, ctx, stream=stream)
+        st = vg_check(ctx, stream)
+        if st == VG_OK:
+            return out
+        if st != VG_ERR_CAPACITY:
+            _check(st, "vg_render_fwd")
+        need = vg_ctx_stats(ctx, stream)["pairs"]
+        vg_ctx_reserve(ctx, int(need * 1.25) + 1024)
+    raise VgError(VG_ERR_CAPACITY, "render_with_retry", "pair buffer kept overflowing")
