@@ -118,8 +118,10 @@ typedef struct {
  *   [floor((u-r)/16), floor((u+r)/16)+1) x [same for v], clipped to the image;
  *   with jacobian_clamp, x/z and y/z inside the projection Jacobian are
  *   clamped to +-clamp_factor * (W/2)/fx and +-clamp_factor * (H/2)/fy.
- * batch: Gaussians staged per shared-memory batch in the blend kernels
- *   (0 = default 256).
+ * batch: reserved, 0.
+ * ppt_fwd, ppt_bwd: pixels per thread in the forward / backward blend
+ *   kernels, 1, 2 or 4 (0 = default: 1 forward, 4 backward); a 16x16 tile is
+ *   one block of 256 / ppt threads.
  * pose_dev: optional DEVICE array [n_views][12] read instead of the
  *   cameras' T_cw (lets a captured CUDA graph follow poses updated on the
  *   device).  count_evals: accumulate evaluated (pixel, Gaussian) pairs into
@@ -131,6 +133,7 @@ typedef struct {
     int32_t jacobian_clamp;
     int32_t count_evals;
     const float* pose_dev;
+    int32_t ppt_fwd, ppt_bwd;
 } vg_render_params;
 
 /* Gradient outputs of vg_render_bwd (DEVICE pointers, caller-allocated; each
@@ -201,7 +204,10 @@ vg_status vg_ctx_reset_counters(vg_ctx* ctx, vg_stream stream);
  * every kernel a render / loss / pose call enqueues.  vg_ctx_profile(ctx, 1)
  * clears the records and starts recording, 0 stops.  vg_ctx_profile_read
  * synchronises `stream` and writes, for each stage id s < VG_STAGE_COUNT,
- * ms_total[s] (sum of event-to-event durations) and launches[s]. */
+ * ms_total[s] (sum of event-to-event durations) and launches[s].  Calls made
+ * during stream capture record their events as external event nodes of the
+ * graph; those records persist (until the ctx is freed) and report the most
+ * recent replay of the graph. */
 enum {
     VG_STAGE_PREPROCESS = 0, VG_STAGE_DEPTH_SORT, VG_STAGE_DUPLICATE, VG_STAGE_TILE_SORT, VG_STAGE_RANGES,
     VG_STAGE_BLEND_FWD, VG_STAGE_LOSS, VG_STAGE_BLEND_BWD, VG_STAGE_CHAIN, VG_STAGE_CODEBOOK, VG_STAGE_POSE,
@@ -215,7 +221,8 @@ vg_status vg_ctx_profile_read(vg_ctx* ctx, vg_stream stream, double* ms_total, i
  * on the ctx; the ctx keeps ownership.  *ptr gets the device address and
  * *bytes the number of valid bytes (pair arrays: capacity bytes; the valid
  * count is vg_stats.pairs).
- *   VG_BUF_XY         float2 [slots]  projected mean (u, v)   (slot = view*N + n)
+ *   VG_BUF_XY         float4 [slots]  projected mean (u, v) and the half extents of the
+ *                                     box where alpha can reach alpha_min (slot = view*N + n)
  *   VG_BUF_CONIC      float4 [slots]  inverse 2D covariance a, b, c and opacity
  *   VG_BUF_RGBD       float4 [slots]  r, g, b, camera depth
  *   VG_BUF_RECT       uint2  [slots]  tile rect x0|y0<<16, x1|y1<<16

@@ -9,6 +9,12 @@ Parameter defaults are the readings the method leaves open: per-pixel opacity
 cap 0.99, skip below 1/255, early stop when transmittance would fall below
 1e-4, 16x16 tiles, 3-sigma radius, 0.3 px^2 low-pass dilation, Jacobian clamp
 at 1.3x the half field of view, near plane 0.2 m.
+
+The flag bands mark pixels whose discrete decisions an FP32 evaluation may
+take the other way: alpha and the exponent carry ~5e-6 relative error in FP32
+(band 5e-5); transmittance after a run of high-alpha Gaussians carries up to
+~sum alpha/(1-alpha) x 1e-6 relative error, a few 1e-4 (band 2e-3); the radius
+3 sqrt(lambda_max) carries ~3e-7 (band 5e-6).
 """
 from __future__ import annotations
 
@@ -57,7 +63,7 @@ class _Params(C.Structure):
     _fields_ = [("alpha_max", C.c_double), ("alpha_min", C.c_double), ("t_min", C.c_double),
                 ("dilation", C.c_double), ("sigma_cull", C.c_double), ("clamp_factor", C.c_double),
                 ("jacobian_clamp", C.c_int), ("tile", C.c_int), ("r_band", C.c_double),
-                ("decision_band", C.c_double)]
+                ("decision_band", C.c_double), ("t_band", C.c_double)]
 
 
 _lib = None
@@ -93,7 +99,7 @@ def _p(a: Optional[np.ndarray]):
 
 def default_params(**kw) -> Dict[str, float]:
     p = dict(alpha_max=0.99, alpha_min=1.0 / 255.0, t_min=1e-4, dilation=0.3, sigma_cull=3.0,
-             clamp_factor=1.3, jacobian_clamp=1, tile=16, r_band=5e-6, decision_band=1e-5)
+             clamp_factor=1.3, jacobian_clamp=1, tile=16, r_band=5e-6, decision_band=5e-5, t_band=2e-3)
     p.update(kw)
     return p
 

@@ -498,7 +498,7 @@ static int walk_pixel(const orc_ctx* ctx, int v, int px, int py, step_t* steps,
         double alpha = capped ? prm->alpha_max : x;
         if (alpha < prm->alpha_min) continue;
         double Tn = T * (1.0 - alpha);
-        if (fabs(Tn - prm->t_min) <= band * prm->t_min) f |= 4;
+        if (fabs(Tn - prm->t_min) <= prm->t_band * prm->t_min) f |= 4;
         if (Tn < prm->t_min) break;
         double wgt = alpha * T;
         C0 += g->rgb[0] * wgt; C1 += g->rgb[1] * wgt; C2 += g->rgb[2] * wgt;

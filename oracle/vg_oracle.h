@@ -48,7 +48,8 @@ typedef struct {
     int jacobian_clamp;
     int tile;                            /* 16 */
     double r_band;                       /* relative band flagging a borderline radius */
-    double decision_band;                /* relative band flagging near-threshold decisions */
+    double decision_band;                /* relative band flagging near-threshold alpha / exponent decisions */
+    double t_band;                       /* relative band flagging a near-threshold transmittance stop */
 } orc_params;
 
 typedef struct orc_ctx orc_ctx;

@@ -87,22 +87,24 @@ struct DevBuf {
 
 constexpr int GDIMS[4] = {3, 4, 1, 3};
 
-// run `expr` (a launch returning cudaError_t) bracketed by profiling events
-#define VG_STAGE(id, expr)                                                     \
-    do {                                                                       \
-        cudaEvent_t e0_ = nullptr;                                             \
-        if (prof_on) {                                                         \
-            e0_ = ctx->prof.get();                                             \
-            if (e0_) cudaEventRecord(e0_, st);                                 \
-        }                                                                      \
-        VG_CUDA(expr);                                                         \
-        if (prof_on && e0_) {                                                  \
-            cudaEvent_t e1_ = ctx->prof.get();                                 \
-            if (e1_) {                                                         \
-                cudaEventRecord(e1_, st);                                      \
-                if (ctx->prof.recs.size() < 200000) ctx->prof.recs.push_back({(id), e0_, e1_}); \
-            }                                                                  \
-        }                                                                      \
+// run `expr` (a launch returning cudaError_t) bracketed by profiling events;
+// inside stream capture the events become external event nodes of the graph
+#define VG_STAGE(id, expr)                                                                          \
+    do {                                                                                            \
+        cudaEvent_t e0_ = nullptr;                                                                  \
+        if (prof_on) {                                                                              \
+            e0_ = prof_graph ? ctx->prof.get_graph() : ctx->prof.get();                             \
+            if (e0_) cudaEventRecordWithFlags(e0_, st, prof_graph ? cudaEventRecordExternal : 0);   \
+        }                                                                                           \
+        VG_CUDA(expr);                                                                              \
+        if (prof_on && e0_) {                                                                       \
+            cudaEvent_t e1_ = prof_graph ? ctx->prof.get_graph() : ctx->prof.get();                 \
+            if (e1_) {                                                                              \
+                cudaEventRecordWithFlags(e1_, st, prof_graph ? cudaEventRecordExternal : 0);        \
+                auto& v_ = prof_graph ? ctx->prof.graph_recs : ctx->prof.recs;                      \
+                if (v_.size() < 200000) v_.push_back({(id), e0_, e1_});                             \
+            }                                                                                       \
+        }                                                                                           \
     } while (0)
 const char* GNAMES[4] = {"logscale", "rot", "opacity", "rgb"};
 
@@ -128,6 +130,16 @@ struct StageProfiler {
         cudaEvent_t a, b;
     };
     std::vector<Rec> recs;
+    // records captured into CUDA graphs: their events are graph nodes, so they
+    // are never reused and always hold the latest replay's timestamps
+    std::vector<Rec> graph_recs;
+    std::vector<cudaEvent_t> graph_pool;
+    cudaEvent_t get_graph() {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        graph_pool.push_back(e);
+        return e;
+    }
     cudaEvent_t get() {
         if (used < pool.size()) return pool[used++];
         cudaEvent_t e = nullptr;
@@ -142,6 +154,7 @@ struct StageProfiler {
     }
     ~StageProfiler() {
         for (cudaEvent_t e : pool) cudaEventDestroy(e);
+        for (cudaEvent_t e : graph_pool) cudaEventDestroy(e);
     }
 };
 
@@ -448,12 +461,17 @@ vg_status vg_ctx_profile_read(vg_ctx* ctx, vg_stream stream, double* ms_total, i
         ms_total[i] = 0.0;
         launches[i] = 0;
     }
-    for (const auto& r : ctx->prof.recs) {
-        float ms = 0.f;
-        VG_CUDA(cudaEventSynchronize(r.b));
-        VG_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
-        ms_total[r.stage] += ms;
-        launches[r.stage] += 1;
+    for (const auto* list : {&ctx->prof.recs, &ctx->prof.graph_recs}) {
+        for (const auto& r : *list) {
+            float ms = 0.f;
+            VG_CUDA(cudaEventSynchronize(r.b));
+            if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+                cudaGetLastError();  // a graph record whose graph has not run yet
+                continue;
+            }
+            ms_total[r.stage] += ms;
+            launches[r.stage] += 1;
+        }
     }
     return VG_OK;
 }
@@ -485,7 +503,7 @@ vg_status vg_ctx_buffer(const vg_ctx* ctx, int32_t which, const void** ptr, int6
 // ---------------------------------------------------------------------------
 
 vg_status vg_rvq_decode(const vg_attr_group* g, int64_t n, float* out, vg_stream stream) {
-    if (!g || !out || n < 0) return fail(VG_ERR_INVALID_ARG, "vg_rvq_decode: null argument or n < 0");
+    if (!g || (n > 0 && !out) || n < 0) return fail(VG_ERR_INVALID_ARG, "vg_rvq_decode: null argument or n < 0");
     if (g->dim < 1) return fail(VG_ERR_INVALID_ARG, "vg_rvq_decode: dim < 1");
     if (g->stages > 0) {
         if (g->codewords < 1 || g->codewords > VG_MAX_CODEWORDS)
@@ -507,6 +525,10 @@ static vg_status build_views(const vg_camera* cams, int32_t n_views, const vg_re
     if (!cams || !p) return fail(VG_ERR_INVALID_ARG, "null cameras or params");
     if (n_views < 1 || n_views > VG_MAX_VIEWS) return fail(VG_ERR_INVALID_ARG, "n_views must be in 1..64");
     if (p->tile != VG_TILE) return fail(VG_ERR_INVALID_ARG, "params.tile must be 16");
+    if (p->ppt_fwd != 0 && p->ppt_fwd != 1 && p->ppt_fwd != 2 && p->ppt_fwd != 4)
+        return fail(VG_ERR_INVALID_ARG, "params.ppt_fwd must be 0, 1, 2 or 4");
+    if (p->ppt_bwd != 0 && p->ppt_bwd != 1 && p->ppt_bwd != 2 && p->ppt_bwd != 4)
+        return fail(VG_ERR_INVALID_ARG, "params.ppt_bwd must be 0, 1, 2 or 4");
     if (!(p->alpha_max > 0.f && p->alpha_max < 1.f) || !(p->alpha_min >= 0.f) || !(p->t_min >= 0.f) ||
         !(p->dilation >= 0.f) || !(p->sigma_cull > 0.f) || !(p->clamp_factor > 0.f))
         return fail(VG_ERR_INVALID_ARG, "render params out of range");
@@ -570,7 +592,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     if (slots >= ((int64_t)1 << 30)) return fail(VG_ERR_INVALID_ARG, "vg_render_fwd: views x Gaussians >= 2^30");
     if (ctx->pair_cap < 1) VG_TRY(vg_ctx_reserve(ctx, std::max<int64_t>(1024, slots * 8)));
 
-    VG_TRY(ctx->xy.ensure(slots * 8, st, "xy"));
+    VG_TRY(ctx->xy.ensure(slots * 16, st, "xy"));
     VG_TRY(ctx->conic_o.ensure(slots * 16, st, "conic"));
     VG_TRY(ctx->rgbd.ensure(slots * 16, st, "rgbd"));
     VG_TRY(ctx->rect.ensure(slots * 8, st, "rect"));
@@ -593,10 +615,11 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     uint32_t* state = ctx->state.as<uint32_t>();
     uint32_t* err = state + ST_ERR;
     unsigned long long* lb = ctx->lookback.as<unsigned long long>();
-    const bool prof_on = ctx->prof.on && !capturing(st);
+    const bool prof_graph = capturing(st);
+    const bool prof_on = ctx->prof.on;
     VG_STAGE(VG_STAGE_MEMSET, cudaMemsetAsync(scr, 0, SCR_WORDS * 4, st));
     VG_STAGE(VG_STAGE_PREPROCESS,
-             launch_preprocess(sd, V, cs, ctx->xy.as<float2>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
+             launch_preprocess(sd, V, cs, ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
                                ctx->rect.as<uint2>(), ctx->ntiles.as<uint32_t>(), ctx->dkey[0].as<uint32_t>(), scr,
                                state, st));
     // depth order of all slots (culled slots carry key 0xffffffff and sort last)
@@ -636,8 +659,8 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     VG_STAGE(VG_STAGE_RANGES, launch_ranges(ctx->pkey[fin].as<uint32_t>(), scr + SCR_PAIRS, cap, V.total_tiles,
                                             ctx->ranges.as<uint2>(), st));
     VG_STAGE(VG_STAGE_BLEND_FWD,
-             launch_blend_fwd(V, cs, params->batch, ctx->ranges.as<uint2>(), ctx->pval[fin].as<uint32_t>(),
-                              ctx->xy.as<float2>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(), C, D, S,
+             launch_blend_fwd(V, cs, params->ppt_fwd, ctx->ranges.as<uint2>(), ctx->pval[fin].as<uint32_t>(),
+                              ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(), C, D, S,
                               ctx->Tfin.as<float>(), ctx->ncontrib.as<uint32_t>(),
                               (unsigned long long*)(state + ST_EVALS), (unsigned long long*)(state + ST_BLENDED),
                               params->count_evals, st));
@@ -677,11 +700,12 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     for (int gi = 0; gi < 4; ++gi) need_attr |= (sd.L[gi] > 0 && gptr[gi]);
     if (need_attr) VG_TRY(ctx->dattr.ensure(N * ATTR_STRIDE * 4, st, "attribute grads"));
 
-    const bool prof_on = ctx->prof.on && !capturing(st);
+    const bool prof_graph = capturing(st);
+    const bool prof_on = ctx->prof.on;
     VG_STAGE(VG_STAGE_MEMSET, cudaMemsetAsync(ctx->g2d.p, 0, slots * G2D_STRIDE * 4, st));
     VG_STAGE(VG_STAGE_BLEND_BWD,
-             launch_blend_bwd(V, cs, params->batch, ctx->ranges.as<uint2>(), ctx->pval[ctx->final_pair].as<uint32_t>(),
-                              ctx->xy.as<float2>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
+             launch_blend_bwd(V, cs, params->ppt_bwd, ctx->ranges.as<uint2>(), ctx->pval[ctx->final_pair].as<uint32_t>(),
+                              ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
                               ctx->Tfin.as<float>(), ctx->ncontrib.as<uint32_t>(), dC, dD, dS, ctx->g2d.as<float>(),
                               (unsigned long long*)(ctx->state.as<uint32_t>() + ST_BWD), params->count_evals, st));
     if ((32 % sd.k) != 0) {
@@ -699,17 +723,25 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
         VG_CUDA(cudaMemsetAsync(ctx->pose_part.p, 0, (size_t)n_views * nb * 6 * 4, st));
         ctx->pose_blocks = nb;
     }
+    CodebookJobs jobs;
+    std::memset(&jobs, 0, sizeof(jobs));
     for (int gi = 0; gi < 4; ++gi) {
         if (sd.L[gi] <= 0 || !gptr[gi]) continue;
-        const size_t bytes = (size_t)sd.L[gi] * sd.K[gi] * GDIMS[gi] * 4;
         if (N == 0) {
-            VG_CUDA(cudaMemsetAsync(gptr[gi], 0, bytes, st));
+            VG_CUDA(cudaMemsetAsync(gptr[gi], 0, (size_t)sd.L[gi] * sd.K[gi] * GDIMS[gi] * 4, st));
             continue;
         }
-        VG_STAGE(VG_STAGE_CODEBOOK,
-                 launch_codebook_reduce(gi, sd.L[gi], sd.K[gi], GDIMS[gi], scene->perm[gi].as<uint32_t>(),
-                                        scene->seg[gi].as<uint32_t>(), N, ctx->dattr.as<float>(), gptr[gi], st));
+        const int j = jobs.n++;
+        jobs.K[j] = sd.K[gi];
+        jobs.dim[j] = GDIMS[gi];
+        jobs.off[j] = goff(gi);
+        jobs.perm[j] = scene->perm[gi].as<uint32_t>();
+        jobs.seg[j] = scene->seg[gi].as<uint32_t>();
+        jobs.out[j] = gptr[gi];
+        jobs.block_start[j + 1] = jobs.block_start[j] + sd.L[gi] * sd.K[gi];
     }
+    if (jobs.n > 0)
+        VG_STAGE(VG_STAGE_CODEBOOK, launch_codebook_reduce(jobs, N, ctx->dattr.as<float>(), st));
     ctx->bwd_scene = sd;
     ctx->views = V;
     ctx->have_bwd = true;
@@ -726,7 +758,8 @@ vg_status vg_pose_grad(vg_ctx* ctx, int32_t n_views, const float* icp_q, const f
     const SceneDev& sd = ctx->bwd_scene;
     const float* icp_part = nullptr;
     int nbi = 0;
-    const bool prof_on = ctx->prof.on && !capturing(st);
+    const bool prof_graph = capturing(st);
+    const bool prof_on = ctx->prof.on;
     if (icp_q) {
         nbi = icp_blocks(sd.N);
         VG_TRY(ctx->icp_part.ensure((size_t)n_views * nbi * 7 * 4, st, "icp partials"));
@@ -747,7 +780,8 @@ vg_status vg_loss_l1(int32_t n_views, int64_t n_pix, const float* C, const float
         return fail(VG_ERR_INVALID_ARG, "vg_loss_l1: null argument or empty size");
     if (gate >= 0.f && !S) return fail(VG_ERR_INVALID_ARG, "vg_loss_l1: gate needs S");
     cudaStream_t st = (cudaStream_t)stream;
-    const bool prof_on = ctx->prof.on && !capturing(st);
+    const bool prof_graph = capturing(st);
+    const bool prof_on = ctx->prof.on;
     VG_CUDA(cudaMemsetAsync(ctx->loss_scratch.p, 0, 16, st));
     VG_CUDA(cudaMemsetAsync(loss, 0, 4, st));
     if (dS) VG_CUDA(cudaMemsetAsync(dS, 0, (size_t)n_views * n_pix * 4, st));

@@ -13,8 +13,14 @@
 // storage).  With w_i = g . (r, g, b, z, 1)_i for the upstream pixel gradient
 // g and B_i = sum_{j > i} w_j alpha_j T_j,
 //   dL/dalpha_i = T_i w_i - B_i / (1 - alpha_i).
-// Lanes of a warp hold different pixels of the same Gaussian: their ten
-// per-Gaussian partials are reduced with a transposing butterfly (17
+//
+// Thread layout: a block is one 16x16 tile; with PPT pixels per thread a warp
+// owns a compact 16 x 2*PPT block of rows, so one test per (warp, Gaussian)
+// against the Gaussian's alpha >= alpha_min bounding box (half extents from
+// the preprocess, widened for FP32 rounding) skips Gaussians that every
+// pixel of the warp would skip anyway; the per-pixel decisions are unchanged.
+// In the backward, lanes of a warp hold different pixels of the same
+// Gaussian: their ten partials are reduced with a transposing butterfly (17
 // shuffles) before four lanes issue the global atomics.
 #include "vg_internal.h"
 
@@ -22,14 +28,28 @@ namespace vgk {
 
 constexpr int BLEND_BATCH = 256;
 
+// pixel (lx, ly) in the tile of pixel slot k of thread t for PPT pixels per thread
+template <int PPT>
+__device__ __forceinline__ void pixel_of(int t, int k, int& lx, int& ly) {
+    const int w = t >> 5, l = t & 31;
+    lx = l & 15;
+    ly = w * 2 * PPT + (l >> 4) + 2 * k;
+}
+
+// does the box [X0, X0+15] x [Y0, Y0+2*PPT-1] meet the Gaussian's alpha box?
+__device__ __forceinline__ bool warp_hits(const float4 g, float X0, float X1, float Y0, float Y1) {
+    const float cx = fminf(fmaxf(g.x, X0), X1), cy = fminf(fmaxf(g.y, Y0), Y1);
+    return fabsf(g.x - cx) <= g.z && fabsf(g.y - cy) <= g.w;
+}
+
 template <int PPT>
 __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pvals,
-    const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
+    const float4* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
     float* __restrict__ C, float* __restrict__ D, float* __restrict__ S, float* __restrict__ Tfin,
     uint32_t* __restrict__ ncontrib, unsigned long long* evals, unsigned long long* blended, int count_evals) {
     constexpr int NT = TILE_PIX / PPT;
-    __shared__ float2 s_xy[BLEND_BATCH];
+    __shared__ float4 s_xy[BLEND_BATCH];
     __shared__ float4 s_co[BLEND_BATCH];
     __shared__ float4 s_cd[BLEND_BATCH];
 
@@ -38,24 +58,29 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     const ViewInfo& vi = V.v[v];
     const int t = gt - vi.tile_base;
     const int tx = t % vi.tiles_x, ty = t / vi.tiles_x;
+    const int warp = threadIdx.x >> 5;
+    const float X0 = (float)(tx * TILE), X1 = X0 + (float)(TILE - 1);
+    const float Y0 = (float)(ty * TILE + warp * 2 * PPT), Y1 = Y0 + (float)(2 * PPT - 1);
 
     int px[PPT], py[PPT];
     bool done[PPT];
     float T[PPT], acc[PPT][5];
-    uint32_t last[PPT], ne[PPT], nb[PPT];
+    uint32_t last[PPT], stop_at[PPT], nb[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int pi = threadIdx.x + k * NT;
-        px[k] = tx * TILE + (pi & (TILE - 1));
-        py[k] = ty * TILE + pi / TILE;
+        int lx, ly;
+        pixel_of<PPT>(threadIdx.x, k, lx, ly);
+        px[k] = tx * TILE + lx;
+        py[k] = ty * TILE + ly;
         done[k] = !(px[k] < vi.W && py[k] < vi.H);
         T[k] = 1.f;
         last[k] = 0;
-        ne[k] = 0;
+        stop_at[k] = 0xffffffffu;
         nb[k] = 0;
 #pragma unroll
         for (int c = 0; c < 5; ++c) acc[k][c] = 0.f;
     }
+    const int lane = threadIdx.x & 31;
     const uint2 rg = ranges[gt];
     for (uint32_t b = rg.x; b < rg.y; b += BLEND_BATCH) {
         int alldone = 1;
@@ -73,33 +98,44 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)BLEND_BATCH, rg.y - b);
-        for (int i = 0; i < cnt; ++i) {
-            const float2 g = s_xy[i];
-            const float4 co = s_co[i];
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            int wdone = 1;
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                if (done[k]) continue;
-                ++ne[k];
-                const float dx = g.x - (float)px[k], dy = g.y - (float)py[k];
-                const float power = gauss_power(co.x, co.y, co.z, dx, dy);
-                if (power > 0.f) continue;
-                const float alpha = fminf(cs.alpha_max, __fmul_rn(co.w, __expf(power)));
-                if (alpha < cs.alpha_min) continue;
-                const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
-                if (Tn < cs.t_min) {
-                    done[k] = true;
-                    continue;
+            for (int k = 0; k < PPT; ++k) wdone &= (int)done[k];
+            if (__all_sync(0xffffffffu, wdone)) break;
+            // each lane tests one Gaussian of the chunk against the warp's pixels
+            const int il = c0 + lane;
+            uint32_t m = __ballot_sync(0xffffffffu, il < cnt && warp_hits(s_xy[il], X0, X1, Y0, Y1));
+            while (m) {
+                const int i = c0 + __ffs(m) - 1;
+                m &= m - 1;
+                const float4 g = s_xy[i];
+                const float4 co = s_co[i];
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    if (done[k]) continue;
+                    const float dx = g.x - (float)px[k], dy = g.y - (float)py[k];
+                    const float power = gauss_power(co.x, co.y, co.z, dx, dy);
+                    if (power > 0.f) continue;
+                    const float alpha = fminf(cs.alpha_max, __fmul_rn(co.w, __expf(power)));
+                    if (alpha < cs.alpha_min) continue;
+                    const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
+                    if (Tn < cs.t_min) {
+                        done[k] = true;
+                        stop_at[k] = b - rg.x + i;
+                        continue;
+                    }
+                    const float4 cd = s_cd[i];
+                    const float w = alpha * T[k];
+                    acc[k][0] = fmaf(cd.x, w, acc[k][0]);
+                    acc[k][1] = fmaf(cd.y, w, acc[k][1]);
+                    acc[k][2] = fmaf(cd.z, w, acc[k][2]);
+                    acc[k][3] = fmaf(cd.w, w, acc[k][3]);
+                    acc[k][4] += w;
+                    T[k] = Tn;
+                    last[k] = b - rg.x + i + 1;
+                    ++nb[k];
                 }
-                const float4 cd = s_cd[i];
-                const float w = alpha * T[k];
-                acc[k][0] = fmaf(cd.x, w, acc[k][0]);
-                acc[k][1] = fmaf(cd.y, w, acc[k][1]);
-                acc[k][2] = fmaf(cd.z, w, acc[k][2]);
-                acc[k][3] = fmaf(cd.w, w, acc[k][3]);
-                acc[k][4] += w;
-                T[k] = Tn;
-                last[k] = b - rg.x + i + 1;
-                ++nb[k];
             }
         }
     }
@@ -117,7 +153,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
         S[pb + i] = acc[k][4];
         Tfin[pb + i] = T[k];
         ncontrib[pb + i] = last[k];
-        ev += ne[k];
+        // examined list entries: up to and including the stopping one
+        ev += stop_at[k] != 0xffffffffu ? stop_at[k] + 1 : rg.y - rg.x;
         bl += nb[k];
     }
     if (count_evals) {
@@ -164,12 +201,12 @@ __device__ __forceinline__ void warp_reduce_add10(const float v[10], float* dst)
 template <int PPT>
 __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pvals,
-    const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
+    const float4* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
     const float* __restrict__ Tfin, const uint32_t* __restrict__ ncontrib, const float* __restrict__ dC,
     const float* __restrict__ dD, const float* __restrict__ dS, float* __restrict__ g2d,
     unsigned long long* bwd_pairs, int count) {
     constexpr int NT = TILE_PIX / PPT;
-    __shared__ float2 s_xy[BLEND_BATCH];
+    __shared__ float4 s_xy[BLEND_BATCH];
     __shared__ float4 s_co[BLEND_BATCH];
     __shared__ float4 s_cd[BLEND_BATCH];
     __shared__ uint32_t s_slot[BLEND_BATCH];
@@ -181,6 +218,9 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     const int t = gt - vi.tile_base;
     const int tx = t % vi.tiles_x, ty = t / vi.tiles_x;
     const int64_t HW = (int64_t)vi.W * vi.H, pb = vi.pix_base;
+    const int warp = threadIdx.x >> 5;
+    const float X0 = (float)(tx * TILE), X1 = X0 + (float)(TILE - 1);
+    const float Y0 = (float)(ty * TILE + warp * 2 * PPT), Y1 = Y0 + (float)(2 * PPT - 1);
 
     int px[PPT], py[PPT];
     uint32_t nc[PPT];
@@ -188,9 +228,10 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     uint32_t mymax = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int pi = threadIdx.x + k * NT;
-        px[k] = tx * TILE + (pi & (TILE - 1));
-        py[k] = ty * TILE + pi / TILE;
+        int lx, ly;
+        pixel_of<PPT>(threadIdx.x, k, lx, ly);
+        px[k] = tx * TILE + lx;
+        py[k] = ty * TILE + ly;
         const bool inside = px[k] < vi.W && py[k] < vi.H;
         const int64_t i = (int64_t)py[k] * vi.W + px[k];
         nc[k] = inside ? ncontrib[pb + i] : 0u;
@@ -219,6 +260,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     __syncthreads();
     const uint2 rg = ranges[gt];
     const uint32_t end = rg.x + min(s_max, rg.y - rg.x);
+    // largest list position this warp still needs
+    const uint32_t warp_max = mymax;
 
     for (uint32_t bend = end; bend > rg.x;) {
         const uint32_t bstart = (bend - rg.x > (uint32_t)BLEND_BATCH) ? bend - BLEND_BATCH : rg.x;
@@ -231,80 +274,94 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
             s_cd[i] = rgbd[s];
         }
         __syncthreads();
-        for (int i = (int)(bend - bstart) - 1; i >= 0; --i) {
-            const uint32_t jl = bstart - rg.x + (uint32_t)i;
-            const float2 g = s_xy[i];
-            const float4 co = s_co[i];
-            const float4 cd = s_cd[i];
-            float vals[10];
+        const int lane = threadIdx.x & 31;
+        for (int c1 = (int)(bend - bstart); c1 > 0; c1 -= 32) {
+            const int c0 = c1 > 32 ? c1 - 32 : 0;
+            // each lane tests one Gaussian of the chunk; hits are then walked
+            // back to front (highest set bit first)
+            const int il = c0 + lane;
+            const bool hit = il < c1 && (bstart - rg.x + (uint32_t)il) < warp_max &&
+                             warp_hits(s_xy[il], X0, X1, Y0, Y1);
+            uint32_t m = __ballot_sync(0xffffffffu, hit);
+            while (m) {
+                const int hb = 31 - __clz(m);
+                m &= ~(1u << hb);
+                const int i = c0 + hb;
+                const uint32_t jl = bstart - rg.x + (uint32_t)i;
+                const float4 g = s_xy[i];
+                const float4 co = s_co[i];
+                const float4 cd = s_cd[i];
+                float vals[10];
 #pragma unroll
-            for (int c = 0; c < 10; ++c) vals[c] = 0.f;
-            bool any = false;
+                for (int c = 0; c < 10; ++c) vals[c] = 0.f;
+                bool any = false;
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                if (jl >= nc[k]) continue;
-                const float dx = g.x - (float)px[k], dy = g.y - (float)py[k];
-                const float power = gauss_power(co.x, co.y, co.z, dx, dy);
-                if (power > 0.f) continue;
-                const float G = __expf(power);
-                const float x = __fmul_rn(co.w, G);
-                const float alpha = fminf(cs.alpha_max, x);
-                if (alpha < cs.alpha_min) continue;
-                const float inv = 1.f / (1.f - alpha);
-                T[k] *= inv;  // transmittance in front of this Gaussian
-                const float w = gp[k][0] * cd.x + gp[k][1] * cd.y + gp[k][2] * cd.z + gp[k][3] * cd.w + gp[k][4];
-                const float dA = T[k] * w - Bk[k] * inv;
-                const float wt = alpha * T[k];
-                Bk[k] = fmaf(w, wt, Bk[k]);
-                vals[6] = fmaf(wt, gp[k][0], vals[6]);
-                vals[7] = fmaf(wt, gp[k][1], vals[7]);
-                vals[8] = fmaf(wt, gp[k][2], vals[8]);
-                vals[9] = fmaf(wt, gp[k][3], vals[9]);
-                if (x <= cs.alpha_max) {
-                    const float dp = alpha * dA;
-                    vals[5] = fmaf(G, dA, vals[5]);
-                    vals[0] -= dp * (co.x * dx + co.y * dy);
-                    vals[1] -= dp * (co.y * dx + co.z * dy);
-                    vals[2] -= 0.5f * dp * dx * dx;
-                    vals[3] -= dp * dx * dy;
-                    vals[4] -= 0.5f * dp * dy * dy;
+                for (int k = 0; k < PPT; ++k) {
+                    if (jl >= nc[k]) continue;
+                    const float dx = g.x - (float)px[k], dy = g.y - (float)py[k];
+                    const float power = gauss_power(co.x, co.y, co.z, dx, dy);
+                    if (power > 0.f) continue;
+                    const float G = __expf(power);
+                    const float x = __fmul_rn(co.w, G);
+                    const float alpha = fminf(cs.alpha_max, x);
+                    if (alpha < cs.alpha_min) continue;
+                    const float inv = 1.f / (1.f - alpha);
+                    T[k] *= inv;  // transmittance in front of this Gaussian
+                    const float w = gp[k][0] * cd.x + gp[k][1] * cd.y + gp[k][2] * cd.z + gp[k][3] * cd.w + gp[k][4];
+                    const float dA = T[k] * w - Bk[k] * inv;
+                    const float wt = alpha * T[k];
+                    Bk[k] = fmaf(w, wt, Bk[k]);
+                    vals[6] = fmaf(wt, gp[k][0], vals[6]);
+                    vals[7] = fmaf(wt, gp[k][1], vals[7]);
+                    vals[8] = fmaf(wt, gp[k][2], vals[8]);
+                    vals[9] = fmaf(wt, gp[k][3], vals[9]);
+                    if (x <= cs.alpha_max) {
+                        const float dp = alpha * dA;
+                        vals[5] = fmaf(G, dA, vals[5]);
+                        vals[0] -= dp * (co.x * dx + co.y * dy);
+                        vals[1] -= dp * (co.y * dx + co.z * dy);
+                        vals[2] -= 0.5f * dp * dx * dx;
+                        vals[3] -= dp * dx * dy;
+                        vals[4] -= 0.5f * dp * dy * dy;
+                    }
+                    any = true;
                 }
-                any = true;
+                if (__any_sync(0xffffffffu, any)) warp_reduce_add10(vals, g2d + (int64_t)s_slot[i] * G2D_STRIDE);
             }
-            if (__any_sync(0xffffffffu, any)) warp_reduce_add10(vals, g2d + (int64_t)s_slot[i] * G2D_STRIDE);
         }
         bend = bstart;
     }
 }
 
-static int default_ppt() { return 1; }
-
-cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int /*batch*/, const uint2* ranges, const uint32_t* pvals,
-                             const float2* xy, const float4* conic_o, const float4* rgbd, float* C, float* D, float* S,
+cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* pvals,
+                             const float4* xy, const float4* conic_o, const float4* rgbd, float* C, float* D, float* S,
                              float* Tfin, uint32_t* ncontrib, unsigned long long* evals, unsigned long long* blended,
                              int count_evals, cudaStream_t st) {
     if (V.total_tiles <= 0) return cudaSuccess;
     count_launches(1);
-    switch (default_ppt()) {
-        case 2:
-            blend_fwd_kernel<2><<<V.total_tiles, TILE_PIX / 2, 0, st>>>(V, cs, ranges, pvals, xy, conic_o, rgbd, C, D, S,
-                                                                        Tfin, ncontrib, evals, blended, count_evals);
-            break;
-        default:
-            blend_fwd_kernel<1><<<V.total_tiles, TILE_PIX, 0, st>>>(V, cs, ranges, pvals, xy, conic_o, rgbd, C, D, S,
-                                                                    Tfin, ncontrib, evals, blended, count_evals);
-    }
+#define VG_FWD(P)                                                                                                   \
+    blend_fwd_kernel<P><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, pvals, xy, conic_o, rgbd, C, D, S, Tfin, \
+                                                                ncontrib, evals, blended, count_evals)
+    if (ppt == 4) VG_FWD(4);
+    else if (ppt == 2) VG_FWD(2);
+    else VG_FWD(1);
+#undef VG_FWD
     return cudaGetLastError();
 }
 
-cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int /*batch*/, const uint2* ranges, const uint32_t* pvals,
-                             const float2* xy, const float4* conic_o, const float4* rgbd, const float* Tfin,
+cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* pvals,
+                             const float4* xy, const float4* conic_o, const float4* rgbd, const float* Tfin,
                              const uint32_t* ncontrib, const float* dC, const float* dD, const float* dS, float* g2d,
                              unsigned long long* bwd_pairs, int count, cudaStream_t st) {
     if (V.total_tiles <= 0) return cudaSuccess;
     count_launches(1);
-    blend_bwd_kernel<4><<<V.total_tiles, TILE_PIX / 4, 0, st>>>(V, cs, ranges, pvals, xy, conic_o, rgbd, Tfin, ncontrib,
-                                                                dC, dD, dS, g2d, bwd_pairs, count);
+#define VG_BWD(P)                                                                                                    \
+    blend_bwd_kernel<P><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, pvals, xy, conic_o, rgbd, Tfin, ncontrib, \
+                                                                dC, dD, dS, g2d, bwd_pairs, count)
+    if (ppt == 1) VG_BWD(1);
+    else if (ppt == 2) VG_BWD(2);
+    else VG_BWD(4);
+#undef VG_BWD
     return cudaGetLastError();
 }
 

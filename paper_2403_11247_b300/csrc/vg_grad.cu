@@ -35,7 +35,17 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
     float mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, ol = 0, rgb[3];
     bool active = false;
     float R[3][3], s[3] = {1, 1, 1}, qn[4] = {1, 0, 0, 0}, qnorm = 1.f, Sig[3][3];
+    // most Gaussians reach no pixel of any view: their gradients are zero and
+    // they need no decode
+    bool touched = false;
     if (live) {
+        for (int v = 0; v < V.n && !touched; ++v) {
+            const float* gg = g2d + ((int64_t)v * S.N + n) * G2D_STRIDE;
+#pragma unroll
+            for (int c = 0; c < 10; ++c) touched |= gg[c] != 0.f;
+        }
+    }
+    if (live && touched) {
         anchor_mean(S, n, mu);
         decode_attr<3>(S, 0, n, ls);
         decode_attr<4>(S, 1, n, q);
@@ -299,28 +309,41 @@ cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, co
 // the attribute gradient of n, as a segmented sum over a per-stage
 // codeword-sorted Gaussian list (deterministic, no atomics)
 // ---------------------------------------------------------------------------
-__global__ void codebook_reduce_kernel(int g, int K, int dim, const uint32_t* __restrict__ perm,
-                                       const uint32_t* __restrict__ seg, int64_t N, const float* __restrict__ dattr,
-                                       float* __restrict__ d_cb) {
+__global__ void __launch_bounds__(256) codebook_reduce_kernel(const __grid_constant__ CodebookJobs J, int64_t N,
+                                                                const float* __restrict__ dattr) {
     __shared__ float s_tmp[8];
-    const int s = blockIdx.x / K, k = blockIdx.x % K;
-    const uint32_t b = seg[s * (K + 1) + k], e = seg[s * (K + 1) + k + 1];
+    int j = 0;
+    while (j + 1 < J.n && (int)blockIdx.x >= J.block_start[j + 1]) ++j;
+    const int local = blockIdx.x - J.block_start[j];
+    const int K = J.K[j], dim = J.dim[j], off = J.off[j];
+    const int s = local / K, k = local % K;
+    const uint32_t* perm = J.perm[j] + (int64_t)s * N;
+    const uint32_t b = J.seg[j][s * (K + 1) + k], e = J.seg[j][s * (K + 1) + k + 1];
     float acc[4] = {0, 0, 0, 0};
-    const int off = goff(g);
-    for (uint32_t j = b + threadIdx.x; j < e; j += blockDim.x) {
-        const uint32_t n = perm[(int64_t)s * N + j];
-        for (int c = 0; c < dim; ++c) acc[c] += dattr[(int64_t)n * ATTR_STRIDE + off + c];
+    // four independent gathers in flight per thread
+    uint32_t i = b + threadIdx.x;
+    for (; i + 3 * 256 < e; i += 4 * 256) {
+        uint32_t n4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) n4[u] = __ldg(perm + i + u * 256);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            for (int c = 0; c < dim; ++c) acc[c] += __ldg(dattr + (int64_t)n4[u] * ATTR_STRIDE + off + c);
+    }
+    for (; i < e; i += 256) {
+        const uint32_t n = __ldg(perm + i);
+        for (int c = 0; c < dim; ++c) acc[c] += __ldg(dattr + (int64_t)n * ATTR_STRIDE + off + c);
     }
     for (int c = 0; c < dim; ++c) {
         const float t = block_sum_256(acc[c], s_tmp);
-        if (threadIdx.x == 0) d_cb[((int64_t)s * K + k) * dim + c] = t;
+        if (threadIdx.x == 0) J.out[j][((int64_t)s * K + k) * dim + c] = t;
     }
 }
 
-cudaError_t launch_codebook_reduce(int g, int L, int K, int dim, const uint32_t* perm, const uint32_t* seg, int64_t N,
-                                   const float* dattr, float* d_cb, cudaStream_t st) {
+cudaError_t launch_codebook_reduce(const CodebookJobs& J, int64_t N, const float* dattr, cudaStream_t st) {
+    if (J.n == 0 || J.block_start[J.n] == 0) return cudaSuccess;
     count_launches(1);
-    codebook_reduce_kernel<<<L * K, 256, 0, st>>>(g, K, dim, perm, seg, N, dattr, d_cb);
+    codebook_reduce_kernel<<<J.block_start[J.n], 256, 0, st>>>(J, N, dattr);
     return cudaGetLastError();
 }
 

@@ -33,6 +33,7 @@ constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 constexpr int DUP_THREADS = 256;
 constexpr int DUP_ITEMS = 4;
 constexpr int DUP_TILE = DUP_THREADS * DUP_ITEMS;
+constexpr uint32_t DUP_SMALL = 16;  // rects up to this many tiles are emitted by one thread
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -40,7 +41,7 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 void count_launches(int n);
 
 // preprocess.cu
-cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& cs, float2* xy, float4* conic_o,
+cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& cs, float4* xy, float4* conic_o,
                               float4* rgbd, uint2* rect, uint32_t* ntiles, uint32_t* dkey, uint32_t* scratch,
                               uint32_t* state, cudaStream_t st);
 cudaError_t launch_rvq_decode(int dim, int L, int K, const float* cb, const uint8_t* idx, const float* raw,
@@ -66,12 +67,12 @@ cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* pairs_dev, uint3
 cudaError_t launch_epoch_bump(uint32_t* state, uint32_t by, cudaStream_t st);
 
 // blend.cu
-cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int batch, const uint2* ranges, const uint32_t* pvals,
-                             const float2* xy, const float4* conic_o, const float4* rgbd, float* C, float* D,
+cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* pvals,
+                             const float4* xy, const float4* conic_o, const float4* rgbd, float* C, float* D,
                              float* S, float* Tfin, uint32_t* ncontrib, unsigned long long* evals,
                              unsigned long long* blended, int count_evals, cudaStream_t st);
-cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int batch, const uint2* ranges, const uint32_t* pvals,
-                             const float2* xy, const float4* conic_o, const float4* rgbd, const float* Tfin,
+cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* pvals,
+                             const float4* xy, const float4* conic_o, const float4* rgbd, const float* Tfin,
                              const uint32_t* ncontrib, const float* dC, const float* dD, const float* dS,
                              float* g2d, unsigned long long* bwd_pairs, int count, cudaStream_t st);
 
@@ -81,8 +82,18 @@ cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, co
                          float* d_l, float* d_off, float* d_mask, float* pose_part, int* n_blocks_out,
                          cudaStream_t st);
 int chain_blocks(int64_t N);
-cudaError_t launch_codebook_reduce(int g, int L, int K, int dim, const uint32_t* perm, const uint32_t* seg,
-                                   int64_t N, const float* dattr, float* d_cb, cudaStream_t st);
+// codebook-gradient reductions of all coded groups in one launch: block
+// range [block_start[j], block_start[j+1]) serves group job j, one block per
+// (stage, codeword)
+struct CodebookJobs {
+    int32_t n;
+    int32_t K[4], dim[4], off[4];
+    const uint32_t* perm[4];
+    const uint32_t* seg[4];
+    float* out[4];
+    int32_t block_start[5];
+};
+cudaError_t launch_codebook_reduce(const CodebookJobs& J, int64_t N, const float* dattr, cudaStream_t st);
 cudaError_t launch_seg_from_hist(const uint32_t* hist, int K, uint32_t* seg, cudaStream_t st);
 cudaError_t launch_icp(const SceneDev& S, const Views& V, const float* q, const float* w, float* part, int n_blocks,
                        cudaStream_t st);

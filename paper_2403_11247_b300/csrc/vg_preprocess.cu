@@ -10,7 +10,7 @@
 namespace vgk {
 
 __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __grid_constant__ Views V, Consts cs,
-                                                         float2* __restrict__ xy, float4* __restrict__ conic_o,
+                                                         float4* __restrict__ xy, float4* __restrict__ conic_o,
                                                          float4* __restrict__ rgbd, uint2* __restrict__ rect,
                                                          uint32_t* __restrict__ ntiles, uint32_t* __restrict__ dkey,
                                                          uint32_t* __restrict__ scratch, uint32_t* state) {
@@ -23,19 +23,20 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
 
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = n < S.N;
-    uint32_t n_vis = 0, n_inv = 0;
+    uint32_t n_vis = 0;
+    float mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, ol = 0.f, rgb[3] = {0, 0, 0};
+    bool active = false;
+    float Sig[6] = {0, 0, 0, 0, 0, 0};  // xx xy xz yy yz zz
+    float opac = 0.f;
     if (live) {
-        float mu[3], ls[3], q[4], ol, rgb[3];
         anchor_mean(S, n, mu);
         decode_attr<3>(S, 0, n, ls);
         decode_attr<4>(S, 1, n, q);
         decode_attr<1>(S, 2, n, &ol);
         decode_attr<3>(S, 3, n, rgb);
-        bool active = S.mask ? (__ldg(S.mask + n) > S.mask_thr) : true;
+        active = S.mask ? (__ldg(S.mask + n) > S.mask_thr) : true;
         float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
         active = active && (qq > 0.f);
-        float Sig[6] = {0, 0, 0, 0, 0, 0};  // xx xy xz yy yz zz
-        float opac = 0.f;
         if (active) {
             float qn_inv = 1.f / sqrtf(qq);
             float qn[4] = {q[0] * qn_inv, q[1] * qn_inv, q[2] * qn_inv, q[3] * qn_inv};
@@ -55,7 +56,11 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
             Sig[5] = R[2][0] * R[2][0] * s2[0] + R[2][1] * R[2][1] * s2[1] + R[2][2] * R[2][2] * s2[2];
             opac = 1.f / (1.f + expf(-ol));
         }
-        for (int v = 0; v < V.n; ++v) {
+    }
+    const uint32_t live_mask = __ballot_sync(0xffffffffu, live);
+    for (int v = 0; v < V.n; ++v) {
+        uint32_t key = 0xffffffffu;  // culled slots sort last
+        if (live) {
             const int64_t slot = (int64_t)v * S.N + n;
             const ViewInfo& vi = V.v[v];
             bool ok = active;
@@ -63,7 +68,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
             float u = 0, vv = 0;
             uint32_t cnt = 0;
             int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-            float a = 0, b = 0, c = 0;
+            float a = 0, b = 0, c = 0, ex = -1.f, ey = -1.f;
             if (ok) {
                 float T[12];
                 view_pose(V, v, T);
@@ -104,6 +109,16 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
                         a = C * inv;
                         b = -B * inv;
                         c = A * inv;
+                        // half extents of the box holding every pixel with
+                        // o exp(-q/2) >= alpha_min, q = d^T conic d: the ellipse
+                        // q <= tau, tau = 2 ln(o / alpha_min), has half extents
+                        // sqrt(tau A), sqrt(tau C); widened so that FP32
+                        // rounding of a pixel's own test can never fall outside
+                        if (opac > cs.alpha_min) {
+                            const float tau = 2.f * logf(opac / cs.alpha_min) * 1.001f + 1e-3f;
+                            ex = sqrtf(tau * A) * 1.0001f + 1e-3f;
+                            ey = sqrtf(tau * C) * 1.0001f + 1e-3f;
+                        }
                         const float mid = 0.5f * (A + C);
                         const float lam = mid + sqrtf(fmaxf(0.f, mid * mid - det));
                         float rr = cs.sigma_cull * sqrtf(lam);
@@ -123,26 +138,28 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
                 }
             }
             if (ok) {
-                xy[slot] = make_float2(u, vv);
+                xy[slot] = make_float4(u, vv, ex, ey);
                 conic_o[slot] = make_float4(a, b, c, opac);
                 rgbd[slot] = make_float4(rgb[0], rgb[1], rgb[2], p[2]);
                 rect[slot] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
                 ntiles[slot] = cnt;
-                const uint32_t key = __float_as_uint(p[2]);
+                key = __float_as_uint(p[2]);
                 dkey[slot] = key;
-#pragma unroll
-                for (int pass = 0; pass < 4; ++pass) atomicAdd(&s_hist[pass * 256 + ((key >> (8 * pass)) & 255u)], 1u);
                 ++n_vis;
             } else {
                 ntiles[slot] = 0u;
                 dkey[slot] = 0xffffffffu;
-                ++n_inv;
             }
         }
-    }
-    if (n_inv) {
+        // depth-key digit histograms; most lanes share the high digits
+        if (live) {
 #pragma unroll
-        for (int pass = 0; pass < 4; ++pass) atomicAdd(&s_hist[pass * 256 + 255], n_inv);
+            for (int pass = 0; pass < 4; ++pass) {
+                const uint32_t b = (key >> (8 * pass)) & 255u;
+                const uint32_t peers = __match_any_sync(live_mask, b);
+                if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_hist[pass * 256 + b], (uint32_t)__popc(peers));
+            }
+        }
     }
     if (n_vis) atomicAdd(&s_cnt[0], n_vis);
     __syncthreads();
@@ -153,7 +170,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
     if (threadIdx.x == 0 && s_cnt[0]) atomicAdd(scratch + SCR_NVIS, s_cnt[0]);
 }
 
-cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& cs, float2* xy, float4* conic_o,
+cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& cs, float4* xy, float4* conic_o,
                               float4* rgbd, uint2* rect, uint32_t* ntiles, uint32_t* dkey, uint32_t* scratch,
                               uint32_t* state, cudaStream_t st) {
     int64_t blocks = ceil_div(S.N > 0 ? S.N : 1, 256);

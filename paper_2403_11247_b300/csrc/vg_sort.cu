@@ -26,25 +26,45 @@ __device__ __forceinline__ unsigned long long lb_make(uint32_t epoch, unsigned l
 }
 
 // Walk back from partition pid-1, summing counts until an inclusive prefix.
+// Eight predecessors are read per round (independent loads in flight), so a
+// chain of P partitions costs about P/8 L2 round trips instead of P.
+constexpr int LB_WINDOW = 8;
+
 __device__ __forceinline__ uint32_t lookback_walk(const unsigned long long* lb, int stride, int col, uint32_t pid,
                                                   uint32_t epoch, uint32_t* err) {
     uint32_t excl = 0;
     int64_t j = (int64_t)pid - 1;
     uint32_t spins = 0;
     while (j >= 0) {
-        unsigned long long s = ld_volatile64(lb + j * stride + col);
-        if ((uint32_t)(s >> 32) != epoch || (s & (LB_AGG | LB_INC)) == 0) {
-            if (++spins > SPIN_LIMIT) {
-                atomicOr(err, ERR_WAIT);
+        unsigned long long w[LB_WINDOW];
+#pragma unroll
+        for (int u = 0; u < LB_WINDOW; ++u) w[u] = (j - u >= 0) ? ld_volatile64(lb + (j - u) * stride + col) : 0ull;
+        int u = 0;
+        bool stop = false;
+        for (; u < LB_WINDOW && j - u >= 0; ++u) {
+            const unsigned long long s = w[u];
+            if ((uint32_t)(s >> 32) != epoch || (s & (LB_AGG | LB_INC)) == 0) break;  // not ready: re-read from here
+            excl += (uint32_t)(s & LB_COUNT);
+            if (s & LB_INC) {
+                stop = true;
                 break;
             }
-            continue;
         }
-        excl += (uint32_t)(s & LB_COUNT);
-        if (s & LB_INC) break;
-        --j;
+        if (stop) break;
+        if (u == 0 && ++spins > SPIN_LIMIT) {
+            atomicOr(err, ERR_WAIT);
+            break;
+        }
+        j -= u;
     }
     return excl;
+}
+
+// add 1 to bin b of a shared histogram; lanes of a warp adding to the same bin
+// are combined first (one atomic per distinct bin)
+__device__ __forceinline__ void hist_add_warp(uint32_t* h, uint32_t b, uint32_t active) {
+    const uint32_t peers = __match_any_sync(active, b);
+    if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicAdd(h + b, (uint32_t)__popc(peers));
 }
 
 __global__ void __launch_bounds__(SORT_THREADS) onesweep_pass_kernel(
@@ -233,25 +253,64 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
             }
         }
         __syncthreads();
-        uint32_t off = s_excl + pre;
+        // rects of up to DUP_SMALL tiles: the owning thread emits them; larger
+        // ones (a Gaussian close to the camera can cover thousands of tiles)
+        // are emitted by the whole warp, one tile per lane, coalesced
+        uint32_t item_off[DUP_ITEMS];
+        {
+            uint32_t off = s_excl + pre;
+#pragma unroll
+            for (int i = 0; i < DUP_ITEMS; ++i) {
+                item_off[i] = off;
+                off += cnt[i];
+            }
+        }
 #pragma unroll
         for (int i = 0; i < DUP_ITEMS; ++i) {
-            if (!cnt[i]) continue;
+            if (cnt[i] == 0 || cnt[i] > DUP_SMALL) continue;
             const uint32_t s = slot[i];
             const int v = (int)(s / (uint64_t)N);
             const uint2 r = rect[s];
             const int x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff, y1 = r.y >> 16;
-            const int tbase = V.v[v].tile_base, tx = V.v[v].tiles_x;
+            const int tbase = V.v[v].tile_base, tw = V.v[v].tiles_x;
+            uint32_t off = item_off[i];
             for (int ty = y0; ty < y1; ++ty)
-                for (int txi = x0; txi < x1; ++txi) {
-                    if (off < cap) {
-                        const uint32_t key = (uint32_t)(tbase + ty * tx + txi);
-                        pkeys[off] = key;
-                        pvals[off] = s;
-                        for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 255u)], 1u);
-                    }
-                    ++off;
+                for (int txi = x0; txi < x1; ++txi, ++off) {
+                    if (off >= cap) continue;
+                    const uint32_t key = (uint32_t)(tbase + ty * tw + txi);
+                    pkeys[off] = key;
+                    pvals[off] = s;
+                    for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 255u)], 1u);
                 }
+        }
+        const int lane = tid & 31;
+#pragma unroll
+        for (int i = 0; i < DUP_ITEMS; ++i) {
+            uint32_t big = __ballot_sync(0xffffffffu, cnt[i] > DUP_SMALL);
+            while (big) {
+                const int src = __ffs(big) - 1;
+                big &= big - 1;
+                const uint32_t s = __shfl_sync(0xffffffffu, slot[i], src);
+                const uint32_t o = __shfl_sync(0xffffffffu, item_off[i], src);
+                const uint32_t c = __shfl_sync(0xffffffffu, cnt[i], src);
+                const int v = (int)(s / (uint64_t)N);
+                const uint2 r = rect[s];
+                const int x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff;
+                const uint32_t w = (uint32_t)(x1 - x0);
+                const int tbase = V.v[v].tile_base, tw = V.v[v].tiles_x;
+                for (uint32_t e0 = 0; e0 < c; e0 += 32) {
+                    const uint32_t e = e0 + lane;
+                    const bool live = e < c && o + e < cap;
+                    const uint32_t active = __ballot_sync(0xffffffffu, live);
+                    if (!live) continue;
+                    const uint32_t ry = e / w, rx = e - ry * w;
+                    const uint32_t key = (uint32_t)(tbase + (y0 + (int)ry) * tw + x0 + (int)rx);
+                    pkeys[o + e] = key;
+                    pvals[o + e] = s;
+                    for (int p = 0; p < tile_passes; ++p)
+                        hist_add_warp(s_hist + p * 256, (key >> (8 * p)) & 255u, active);
+                }
+            }
         }
         __syncthreads();
     }

@@ -54,7 +54,8 @@ class vg_render_params(C.Structure):
     _fields_ = [("tile", C.c_int32), ("batch", C.c_int32),
                 ("alpha_max", C.c_float), ("alpha_min", C.c_float), ("t_min", C.c_float), ("dilation", C.c_float),
                 ("sigma_cull", C.c_float), ("clamp_factor", C.c_float),
-                ("jacobian_clamp", C.c_int32), ("count_evals", C.c_int32), ("pose_dev", C.c_void_p)]
+                ("jacobian_clamp", C.c_int32), ("count_evals", C.c_int32), ("pose_dev", C.c_void_p),
+                ("ppt_fwd", C.c_int32), ("ppt_bwd", C.c_int32)]
 
 
 class vg_scene_grads(C.Structure):
@@ -386,7 +387,7 @@ def vg_loss_l1(n_views: int, n_pix: int, C_, D, S, Ct, Dt, w_depth: float, gate:
 
 VG_BUF = dict(xy=0, conic=1, rgbd=2, rect=3, ntiles=4, pair_keys=5, pair_vals=6, ranges=7, t_final=8, n_contrib=9,
               g2d=10)
-_BUF_DTYPE = dict(xy=("float32", 2), conic=("float32", 4), rgbd=("float32", 4), rect=("uint32", 2),
+_BUF_DTYPE = dict(xy=("float32", 4), conic=("float32", 4), rgbd=("float32", 4), rect=("uint32", 2),
                   ntiles=("uint32", 1), pair_keys=("uint32", 1), pair_vals=("uint32", 1), ranges=("uint32", 2),
                   t_final=("float32", 1), n_contrib=("uint32", 1), g2d=("float32", 10))
 

@@ -14,7 +14,8 @@ from oracle import oracle as O
 from paper_2403_11247_b300 import synth
 from paper_2403_11247_b300 import vg as V
 
-from gpu_common import (assert_forward_parity, gpu_forward, grad_tolerance_check, oracle_params, to_np_grads)
+from gpu_common import (assert_forward_parity, gpu_forward, grad_tolerance_check, masked_upstream, oracle_params,
+                        to_np_grads)
 
 pytestmark = pytest.mark.gpu
 
@@ -164,8 +165,7 @@ def test_forward_is_deterministic(cuda):
 def backward_parity(scene, cams, label, seed=77, **pkw):
     torch = pytest.importorskip("torch")
     sh, ctx, params, o, f, g = assert_forward_parity(scene, cams, label, **pkw)
-    P = o.n_pixels
-    dC, dD, dS = synth.upstream_grads(seed, P, scale=P)
+    dC, dD, dS = masked_upstream(seed, f, cams)
     grads = V.vg_render_bwd(sh, cams, params, ctx, t(dC, torch), t(dD, torch), t(dS, torch))
     dxi, _ = V.vg_pose_grad(ctx, len(cams))
     gg = to_np_grads(grads)
@@ -179,6 +179,7 @@ def backward_parity(scene, cams, label, seed=77, **pkw):
         worst["mask"] = grad_tolerance_check(gg["mask_logit"], og["mask_logit"], label + ":mask_logit")
     for v in range(len(cams)):
         worst[f"pose{v}"] = grad_tolerance_check(dxi[v].cpu().numpy(), og["pose"][v], f"{label}:pose{v}")
+    print(label, "worst err/tol", {k: round(x, 3) for k, x in worst.items()})
     return worst
 
 
@@ -186,8 +187,10 @@ def test_backward_tiny_raw(cuda):
     backward_parity(synth.tiny_scene(), [synth.tiny_camera()], "bwd-tiny")
 
 
-def test_backward_room_rvq_mask(cuda):
-    backward_parity(small_room(), [small_room_cam(330, 190, 165.0)], "bwd-room")
+@pytest.mark.parametrize("ppt_fwd,ppt_bwd", [(1, 4), (2, 2), (4, 1)])
+def test_backward_room_rvq_mask(cuda, ppt_fwd, ppt_bwd):
+    backward_parity(small_room(), [small_room_cam(330, 190, 165.0)], f"bwd-room-{ppt_fwd}{ppt_bwd}",
+                    ppt_fwd=ppt_fwd, ppt_bwd=ppt_bwd)
 
 
 def test_backward_two_views(cuda):
@@ -205,8 +208,7 @@ def test_pose_grad_with_icp(cuda):
     sc = synth.tiny_scene(seed=9, n=1500)
     cams = synth.keyframe_cameras(n_views=3, width=64, height=48, f=50.0)
     sh, ctx, params, o, f, g = assert_forward_parity(sc, cams, "icp")
-    P = o.n_pixels
-    dC, dD, dS = synth.upstream_grads(5, P, scale=P)
+    dC, dD, dS = masked_upstream(5, f, cams)
     V.vg_render_bwd(sh, cams, params, ctx, t(dC, torch), t(dD, torch), t(dS, torch))
     q, w = synth.icp_targets(6, len(cams), sc.n)
     dxi, loss = V.vg_pose_grad(ctx, len(cams), t(q, torch), t(w, torch))
