@@ -162,7 +162,7 @@ struct vg_ctx {
     StageProfiler prof;
     int64_t pair_cap = 0;
     DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, Tfin, ncontrib, lookback,
-        scratch, state, dattr, pose_part, icp_part, loss_scratch;
+        scratch, state, dattr, pose_part, icp_part, loss_scratch, pair_off, blk_count, blk_base, touched;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
     Views views{};
@@ -597,6 +597,9 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     VG_TRY(ctx->rgbd.ensure(slots * 16, st, "rgbd"));
     VG_TRY(ctx->rect.ensure(slots * 8, st, "rect"));
     VG_TRY(ctx->ntiles.ensure(slots * 4, st, "ntiles"));
+    VG_TRY(ctx->pair_off.ensure(slots * 4, st, "pair offsets"));
+    VG_TRY(ctx->blk_count.ensure((size_t)preprocess_blocks(N) * 4, st, "block counts"));
+    VG_TRY(ctx->blk_base.ensure((size_t)preprocess_blocks(N) * 4, st, "block bases"));
     for (int b = 0; b < 2; ++b) {
         VG_TRY(ctx->dkey[b].ensure(slots * 4, st, "depth keys"));
         VG_TRY(ctx->dval[b].ensure(slots * 4, st, "depth values"));
@@ -620,17 +623,22 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     VG_STAGE(VG_STAGE_MEMSET, cudaMemsetAsync(scr, 0, SCR_WORDS * 4, st));
     VG_STAGE(VG_STAGE_PREPROCESS,
              launch_preprocess(sd, V, cs, ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
-                               ctx->rect.as<uint2>(), ctx->ntiles.as<uint32_t>(), ctx->dkey[0].as<uint32_t>(), scr,
-                               state, st));
-    // depth order of all slots (culled slots carry key 0xffffffff and sort last)
+                               ctx->rect.as<uint2>(), ctx->ntiles.as<uint32_t>(), ctx->dkey[1].as<uint32_t>(), scr,
+                               state, ctx->blk_count.as<uint32_t>(), st));
+    // depth order of the visible slots: order-preserving compaction, then a
+    // stable radix sort on the FP32 depth bits (ties keep Gaussian order)
     const int dgrid = sort_pass_grid((uint32_t)slots);
     VG_STAGE(VG_STAGE_DEPTH_SORT, ([&]() -> cudaError_t {
+                 cudaError_t e = launch_compact(V, N, ctx->dkey[1].as<uint32_t>(), ctx->blk_count.as<uint32_t>(),
+                                                ctx->blk_base.as<uint32_t>(), ctx->dkey[0].as<uint32_t>(),
+                                                ctx->dval[0].as<uint32_t>(), st);
+                 if (e != cudaSuccess) return e;
                  for (int p = 0; p < 4; ++p) {
                      const int i = p & 1, o = i ^ 1;
-                     cudaError_t e = launch_sort_pass(
-                         ctx->dkey[i].as<uint32_t>(), p == 0 ? nullptr : ctx->dval[i].as<uint32_t>(),
-                         ctx->dkey[o].as<uint32_t>(), ctx->dval[o].as<uint32_t>(), nullptr, (uint32_t)slots, 8 * p,
-                         scr + SCR_DEPTH_HIST + 256 * p, lb, scr + SCR_CNT_DEPTH + p, state, (uint32_t)p, err, dgrid, st);
+                     e = launch_sort_pass(ctx->dkey[i].as<uint32_t>(), ctx->dval[i].as<uint32_t>(),
+                                          ctx->dkey[o].as<uint32_t>(), ctx->dval[o].as<uint32_t>(), scr + SCR_NVIS,
+                                          (uint32_t)slots, 8 * p, scr + SCR_DEPTH_HIST + 256 * p, lb,
+                                          scr + SCR_CNT_DEPTH + p, state, (uint32_t)p, err, dgrid, st);
                      if (e != cudaSuccess) return e;
                  }
                  return cudaSuccess;
@@ -639,7 +647,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     const int tp = tile_passes_for(V.total_tiles);
     const uint32_t cap = (uint32_t)ctx->pair_cap;
     VG_STAGE(VG_STAGE_DUPLICATE,
-             launch_duplicate(ctx->dval[0].as<uint32_t>(), scr + SCR_NVIS, ctx->ntiles.as<uint32_t>(),
+             launch_duplicate(ctx->dval[0].as<uint32_t>(), ctx->pair_off.as<uint32_t>(), ctx->ntiles.as<uint32_t>(),
                               ctx->rect.as<uint2>(), N, V, ctx->pkey[0].as<uint32_t>(), ctx->pval[0].as<uint32_t>(), cap,
                               scr, tp, lb, state, 4u, err, slots, st));
     const int tgrid = sort_pass_grid(cap);
@@ -699,6 +707,7 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     float* gptr[4] = {grads->logscale, grads->rot, grads->opacity, grads->rgb};
     for (int gi = 0; gi < 4; ++gi) need_attr |= (sd.L[gi] > 0 && gptr[gi]);
     if (need_attr) VG_TRY(ctx->dattr.ensure(N * ATTR_STRIDE * 4, st, "attribute grads"));
+    VG_TRY(ctx->touched.ensure((size_t)ceil_div(N, 32) * 4 + 1024, st, "touched mask"));
 
     const bool prof_graph = capturing(st);
     const bool prof_on = ctx->prof.on;
@@ -718,7 +727,8 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
         VG_STAGE(VG_STAGE_CHAIN,
                  launch_chain(sd, V, cs, ctx->g2d.as<float>(), need_attr ? ctx->dattr.as<float>() : nullptr, raws[0],
                               raws[1], raws[2], raws[3], grads->anchor_xyz, grads->anchor_l, grads->offsets,
-                              grads->mask_logit, ctx->pose_part.as<float>(), &ctx->pose_blocks, st));
+                              grads->mask_logit, ctx->pose_part.as<float>(), ctx->touched.as<uint32_t>(),
+                              &ctx->pose_blocks, st));
     } else {
         VG_CUDA(cudaMemsetAsync(ctx->pose_part.p, 0, (size_t)n_views * nb * 6 * 4, st));
         ctx->pose_blocks = nb;
@@ -741,7 +751,8 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
         jobs.block_start[j + 1] = jobs.block_start[j] + sd.L[gi] * sd.K[gi];
     }
     if (jobs.n > 0)
-        VG_STAGE(VG_STAGE_CODEBOOK, launch_codebook_reduce(jobs, N, ctx->dattr.as<float>(), st));
+        VG_STAGE(VG_STAGE_CODEBOOK,
+                 launch_codebook_reduce(jobs, N, ctx->dattr.as<float>(), ctx->touched.as<uint32_t>(), st));
     ctx->bwd_scene = sd;
     ctx->views = V;
     ctx->have_bwd = true;

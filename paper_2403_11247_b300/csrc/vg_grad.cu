@@ -26,7 +26,8 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
                                                              const float* __restrict__ g2d, float* __restrict__ dattr,
                                                              float* raw0, float* raw1, float* raw2, float* raw3,
                                                              float* d_xyz, float* d_l, float* d_off, float* d_mask,
-                                                             float* __restrict__ pose_part) {
+                                                             float* __restrict__ pose_part,
+                                                             uint32_t* __restrict__ touched_mask) {
     __shared__ float s_red[8][6];
     const int64_t n = (int64_t)blockIdx.x * CHAIN_THREADS + threadIdx.x;
     const bool live = n < S.N;
@@ -44,6 +45,10 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
 #pragma unroll
             for (int c = 0; c < 10; ++c) touched |= gg[c] != 0.f;
         }
+    }
+    {
+        const uint32_t tm = __ballot_sync(0xffffffffu, live && touched);
+        if (lane == 0) touched_mask[n >> 5] = tm;
     }
     if (live && touched) {
         anchor_mean(S, n, mu);
@@ -239,7 +244,8 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
         for (int gi = 0; gi < 4; ++gi) {
             const int d = gdim(gi);
             if (S.L[gi] > 0) {
-                if (dattr)
+                // untouched Gaussians are skipped by the codebook reduction
+                if (dattr && touched)
                     for (int c = 0; c < d; ++c) dattr[n * ATTR_STRIDE + goff(gi) + c] = vals[gi][c];
             } else if (raws[gi]) {
                 for (int c = 0; c < d; ++c) raws[gi][n * d + c] = vals[gi][c];
@@ -295,12 +301,12 @@ int chain_blocks(int64_t N) { return (int)ceil_div(N > 0 ? N : 1, CHAIN_THREADS)
 
 cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, const float* g2d, float* dattr, float* r0,
                          float* r1, float* r2, float* r3, float* d_xyz, float* d_l, float* d_off, float* d_mask,
-                         float* pose_part, int* n_blocks_out, cudaStream_t st) {
+                         float* pose_part, uint32_t* touched, int* n_blocks_out, cudaStream_t st) {
     const int blocks = chain_blocks(S.N);
     if (n_blocks_out) *n_blocks_out = blocks;
     count_launches(1);
     chain_kernel<<<blocks, CHAIN_THREADS, 0, st>>>(S, V, cs, g2d, dattr, r0, r1, r2, r3, d_xyz, d_l, d_off, d_mask,
-                                                   pose_part);
+                                                   pose_part, touched);
     return cudaGetLastError();
 }
 
@@ -310,7 +316,8 @@ cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, co
 // codeword-sorted Gaussian list (deterministic, no atomics)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) codebook_reduce_kernel(const __grid_constant__ CodebookJobs J, int64_t N,
-                                                                const float* __restrict__ dattr) {
+                                                                const float* __restrict__ dattr,
+                                                                const uint32_t* __restrict__ touched) {
     __shared__ float s_tmp[8];
     int j = 0;
     while (j + 1 < J.n && (int)blockIdx.x >= J.block_start[j + 1]) ++j;
@@ -323,16 +330,20 @@ __global__ void __launch_bounds__(256) codebook_reduce_kernel(const __grid_const
     // four independent gathers in flight per thread
     uint32_t i = b + threadIdx.x;
     for (; i + 3 * 256 < e; i += 4 * 256) {
-        uint32_t n4[4];
+        uint32_t n4[4], t4[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) n4[u] = __ldg(perm + i + u * 256);
 #pragma unroll
+        for (int u = 0; u < 4; ++u) t4[u] = (__ldg(touched + (n4[u] >> 5)) >> (n4[u] & 31)) & 1u;
+#pragma unroll
         for (int u = 0; u < 4; ++u)
-            for (int c = 0; c < dim; ++c) acc[c] += __ldg(dattr + (int64_t)n4[u] * ATTR_STRIDE + off + c);
+            if (t4[u])
+                for (int c = 0; c < dim; ++c) acc[c] += __ldg(dattr + (int64_t)n4[u] * ATTR_STRIDE + off + c);
     }
     for (; i < e; i += 256) {
         const uint32_t n = __ldg(perm + i);
-        for (int c = 0; c < dim; ++c) acc[c] += __ldg(dattr + (int64_t)n * ATTR_STRIDE + off + c);
+        if ((__ldg(touched + (n >> 5)) >> (n & 31)) & 1u)
+            for (int c = 0; c < dim; ++c) acc[c] += __ldg(dattr + (int64_t)n * ATTR_STRIDE + off + c);
     }
     for (int c = 0; c < dim; ++c) {
         const float t = block_sum_256(acc[c], s_tmp);
@@ -340,10 +351,11 @@ __global__ void __launch_bounds__(256) codebook_reduce_kernel(const __grid_const
     }
 }
 
-cudaError_t launch_codebook_reduce(const CodebookJobs& J, int64_t N, const float* dattr, cudaStream_t st) {
+cudaError_t launch_codebook_reduce(const CodebookJobs& J, int64_t N, const float* dattr, const uint32_t* touched,
+                                   cudaStream_t st) {
     if (J.n == 0 || J.block_start[J.n] == 0) return cudaSuccess;
     count_launches(1);
-    codebook_reduce_kernel<<<J.block_start[J.n], 256, 0, st>>>(J, N, dattr);
+    codebook_reduce_kernel<<<J.block_start[J.n], 256, 0, st>>>(J, N, dattr, touched);
     return cudaGetLastError();
 }
 
@@ -474,8 +486,9 @@ __global__ void loss_l1_kernel(int64_t n_pix, int64_t total, const float* __rest
     const float inv_c = 1.f / (3.f * (float)total);
     const float inv_d = nv > 0.f ? w_depth / nv : 0.f;
     float acc = 0.f;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = e / n_pix, i = e - v * n_pix;
+    const int64_t v = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pix; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = v * n_pix + i;
         const float m = (gate >= 0.f && !(S[e] > gate)) ? 0.f : 1.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -503,8 +516,10 @@ cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const flo
     if (blocks > 148 * 8) blocks = 148 * 8;
     count_launches(2);
     count_valid_kernel<<<(unsigned)blocks, 256, 0, st>>>(Dt, total, valid_count);
-    loss_l1_kernel<<<(unsigned)blocks, 256, 0, st>>>(n_pix, total, C, D, S, Ct, Dt, w_depth, gate, valid_count, dC, dD,
-                                                     loss);
+    int64_t bx = ceil_div(n_pix, 256);
+    if (bx > 148 * 8) bx = 148 * 8;
+    loss_l1_kernel<<<dim3((unsigned)bx, (unsigned)n_views), 256, 0, st>>>(n_pix, total, C, D, S, Ct, Dt, w_depth, gate,
+                                                                          valid_count, dC, dD, loss);
     return cudaGetLastError();
 }
 

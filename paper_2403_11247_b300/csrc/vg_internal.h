@@ -33,7 +33,6 @@ constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 constexpr int DUP_THREADS = 256;
 constexpr int DUP_ITEMS = 4;
 constexpr int DUP_TILE = DUP_THREADS * DUP_ITEMS;
-constexpr uint32_t DUP_SMALL = 16;  // rects up to this many tiles are emitted by one thread
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -41,9 +40,13 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 void count_launches(int n);
 
 // preprocess.cu
+int preprocess_blocks(int64_t N);
 cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& cs, float4* xy, float4* conic_o,
                               float4* rgbd, uint2* rect, uint32_t* ntiles, uint32_t* dkey, uint32_t* scratch,
-                              uint32_t* state, cudaStream_t st);
+                              uint32_t* state, uint32_t* blk_count, cudaStream_t st);
+// visible slots, in (view, Gaussian) order within each preprocess block, to keys_out / vals_out
+cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count, uint32_t* blk_base,
+                           uint32_t* keys_out, uint32_t* vals_out, cudaStream_t st);
 cudaError_t launch_rvq_decode(int dim, int L, int K, const float* cb, const uint8_t* idx, const float* raw,
                               int64_t n, float* out, cudaStream_t st);
 
@@ -57,7 +60,7 @@ cudaError_t launch_sort_pass(const uint32_t* keys_in, const uint32_t* vals_in, u
                              cudaStream_t st);
 int sort_pass_grid(uint32_t n_cap);
 cudaError_t launch_hist(const uint32_t* keys, int64_t n, int passes, uint32_t* hist, cudaStream_t st);
-cudaError_t launch_duplicate(const uint32_t* sorted_slots, const uint32_t* scratch_nvis, const uint32_t* ntiles,
+cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, const uint32_t* ntiles,
                              const uint2* rect, int64_t N, const Views& V, uint32_t* pkeys, uint32_t* pvals,
                              uint32_t cap, uint32_t* scratch, int tile_passes, unsigned long long* lookback,
                              const uint32_t* state, uint32_t epoch_offset, uint32_t* err, int64_t max_slots,
@@ -79,8 +82,8 @@ cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, const ui
 // grad.cu
 cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, const float* g2d, float* dattr,
                          float* raw_grad0, float* raw_grad1, float* raw_grad2, float* raw_grad3, float* d_xyz,
-                         float* d_l, float* d_off, float* d_mask, float* pose_part, int* n_blocks_out,
-                         cudaStream_t st);
+                         float* d_l, float* d_off, float* d_mask, float* pose_part, uint32_t* touched,
+                         int* n_blocks_out, cudaStream_t st);
 int chain_blocks(int64_t N);
 // codebook-gradient reductions of all coded groups in one launch: block
 // range [block_start[j], block_start[j+1]) serves group job j, one block per
@@ -93,7 +96,8 @@ struct CodebookJobs {
     float* out[4];
     int32_t block_start[5];
 };
-cudaError_t launch_codebook_reduce(const CodebookJobs& J, int64_t N, const float* dattr, cudaStream_t st);
+cudaError_t launch_codebook_reduce(const CodebookJobs& J, int64_t N, const float* dattr, const uint32_t* touched,
+                                   cudaStream_t st);
 cudaError_t launch_seg_from_hist(const uint32_t* hist, int K, uint32_t* seg, cudaStream_t st);
 cudaError_t launch_icp(const SceneDev& S, const Views& V, const float* q, const float* w, float* part, int n_blocks,
                        cudaStream_t st);

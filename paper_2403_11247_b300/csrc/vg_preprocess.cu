@@ -13,7 +13,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
                                                          float4* __restrict__ xy, float4* __restrict__ conic_o,
                                                          float4* __restrict__ rgbd, uint2* __restrict__ rect,
                                                          uint32_t* __restrict__ ntiles, uint32_t* __restrict__ dkey,
-                                                         uint32_t* __restrict__ scratch, uint32_t* state) {
+                                                         uint32_t* __restrict__ scratch, uint32_t* state,
+                                                         uint32_t* __restrict__ blk_count) {
     __shared__ uint32_t s_hist[4 * 256];
     __shared__ uint32_t s_cnt[2];
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_hist[i] = 0;
@@ -57,7 +58,6 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
             opac = 1.f / (1.f + expf(-ol));
         }
     }
-    const uint32_t live_mask = __ballot_sync(0xffffffffu, live);
     for (int v = 0; v < V.n; ++v) {
         uint32_t key = 0xffffffffu;  // culled slots sort last
         if (live) {
@@ -151,12 +151,14 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
                 dkey[slot] = 0xffffffffu;
             }
         }
-        // depth-key digit histograms; most lanes share the high digits
-        if (live) {
+        // depth-key digit histograms of the visible slots; most lanes share
+        // the high digits
+        const uint32_t vis_mask = __ballot_sync(0xffffffffu, live && key != 0xffffffffu);
+        if (live && key != 0xffffffffu) {
 #pragma unroll
             for (int pass = 0; pass < 4; ++pass) {
                 const uint32_t b = (key >> (8 * pass)) & 255u;
-                const uint32_t peers = __match_any_sync(live_mask, b);
+                const uint32_t peers = __match_any_sync(vis_mask, b);
                 if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_hist[pass * 256 + b], (uint32_t)__popc(peers));
             }
         }
@@ -167,15 +169,93 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
         uint32_t h = s_hist[i];
         if (h) atomicAdd(scratch + SCR_DEPTH_HIST + i, h);
     }
-    if (threadIdx.x == 0 && s_cnt[0]) atomicAdd(scratch + SCR_NVIS, s_cnt[0]);
+    if (threadIdx.x == 0) {
+        if (s_cnt[0]) atomicAdd(scratch + SCR_NVIS, s_cnt[0]);
+        blk_count[blockIdx.x] = s_cnt[0];
+    }
 }
+
+// exclusive scan of the per-block visible counts (one block)
+__global__ void __launch_bounds__(1024) block_scan_kernel(const uint32_t* __restrict__ cnt, int n,
+                                                          uint32_t* __restrict__ base) {
+    __shared__ uint32_t s_w[32];
+    __shared__ uint32_t s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += 1024) {
+        const int i = c0 + threadIdx.x;
+        const uint32_t x = i < n ? cnt[i] : 0u;
+        uint32_t inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t t = s_w[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            s_w[lane] = t;  // inclusive warp prefix
+        }
+        __syncthreads();
+        const uint32_t wpre = warp ? s_w[warp - 1] : 0u;
+        if (i < n) base[i] = s_carry + wpre + inc - x;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += s_w[31];
+        __syncthreads();
+    }
+}
+
+// order-preserving compaction of the visible slots: block b of the preprocess
+// grid covers Gaussians [256 b, 256 b + 256) of every view; its visible slots
+// go, view by view and in Gaussian order, to [base[b], base[b] + count[b])
+__global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Views V, int64_t N,
+                                                      const uint32_t* __restrict__ dkey,
+                                                      const uint32_t* __restrict__ base, uint32_t* __restrict__ keys_out,
+                                                      uint32_t* __restrict__ vals_out) {
+    __shared__ uint32_t s_tmp[8];
+    const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    uint32_t off = base[blockIdx.x];
+    for (int v = 0; v < V.n; ++v) {
+        const int64_t slot = (int64_t)v * N + n;
+        const uint32_t key = n < N ? dkey[slot] : 0xffffffffu;
+        const uint32_t f = key != 0xffffffffu;
+        uint32_t tot;
+        const uint32_t pre = block_excl_scan_256(f, s_tmp, &tot);
+        if (f) {
+            keys_out[off + pre] = key;
+            vals_out[off + pre] = (uint32_t)slot;
+        }
+        off += tot;
+    }
+}
+
+int preprocess_blocks(int64_t N) { return (int)ceil_div(N > 0 ? N : 1, 256); }
 
 cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& cs, float4* xy, float4* conic_o,
                               float4* rgbd, uint2* rect, uint32_t* ntiles, uint32_t* dkey, uint32_t* scratch,
-                              uint32_t* state, cudaStream_t st) {
-    int64_t blocks = ceil_div(S.N > 0 ? S.N : 1, 256);
+                              uint32_t* state, uint32_t* blk_count, cudaStream_t st) {
+    const int blocks = preprocess_blocks(S.N);
     count_launches(1);
-    preprocess_kernel<<<(unsigned)blocks, 256, 0, st>>>(S, V, cs, xy, conic_o, rgbd, rect, ntiles, dkey, scratch, state);
+    preprocess_kernel<<<(unsigned)blocks, 256, 0, st>>>(S, V, cs, xy, conic_o, rgbd, rect, ntiles, dkey, scratch, state,
+                                                        blk_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count, uint32_t* blk_base,
+                           uint32_t* keys_out, uint32_t* vals_out, cudaStream_t st) {
+    const int blocks = preprocess_blocks(N);
+    count_launches(2);
+    block_scan_kernel<<<1, 1024, 0, st>>>(blk_count, blocks, blk_base);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    compact_kernel<<<blocks, 256, 0, st>>>(V, N, dkey, blk_base, keys_out, vals_out);
     return cudaGetLastError();
 }
 

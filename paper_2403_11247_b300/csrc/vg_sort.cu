@@ -205,40 +205,37 @@ cudaError_t launch_hist(const uint32_t* keys, int64_t n, int passes, uint32_t* h
 }
 
 // ---------------------------------------------------------------------------
-// scan of tile counts in depth order + pair emission (persistent partitions)
+// pair offsets: exclusive scan of the tile counts of the depth-sorted visible
+// slots (persistent partitions, decoupled look-back)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
-    const uint32_t* __restrict__ sorted_slots, const uint32_t* __restrict__ ntiles, const uint2* __restrict__ rect,
-    int64_t N, const __grid_constant__ Views V, uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals, uint32_t cap,
-    uint32_t* scratch, int tile_passes, unsigned long long* lookback, const uint32_t* state, uint32_t epoch_offset,
+__global__ void __launch_bounds__(DUP_THREADS) pair_offsets_kernel(
+    const uint32_t* __restrict__ sorted_slots, const uint32_t* __restrict__ ntiles, uint32_t* __restrict__ offsets,
+    uint32_t cap, uint32_t* scratch, unsigned long long* lookback, const uint32_t* state, uint32_t epoch_offset,
     uint32_t* err) {
-    __shared__ uint32_t s_hist[3 * 256];
     __shared__ uint32_t s_tmp[8];
     __shared__ uint32_t s_pid;
     __shared__ uint32_t s_excl;
     const int tid = threadIdx.x;
-    for (int i = tid; i < 3 * 256; i += DUP_THREADS) s_hist[i] = 0;
     const uint32_t nvis = scratch[SCR_NVIS];
     const uint32_t nparts = (nvis + DUP_TILE - 1) / DUP_TILE;
     const uint32_t epoch = state[ST_EPOCH] + epoch_offset;
     uint32_t* counter = scratch + SCR_CNT_DUP;
-    __syncthreads();
     for (;;) {
         if (tid == 0) s_pid = atomicAdd(counter, 1u);
         __syncthreads();
         const uint32_t pid = s_pid;
         if (pid >= nparts) break;
-        uint32_t slot[DUP_ITEMS], cnt[DUP_ITEMS];
+        uint32_t cnt[DUP_ITEMS];
         uint32_t local = 0;
+        const uint32_t base = pid * DUP_TILE + tid * DUP_ITEMS;
 #pragma unroll
         for (int i = 0; i < DUP_ITEMS; ++i) {
-            const uint32_t pos = pid * DUP_TILE + tid * DUP_ITEMS + i;
-            slot[i] = pos < nvis ? sorted_slots[pos] : 0u;
-            cnt[i] = pos < nvis ? ntiles[slot[i]] : 0u;
+            const uint32_t pos = base + i;
+            cnt[i] = pos < nvis ? ntiles[sorted_slots[pos]] : 0u;
             local += cnt[i];
         }
         uint32_t agg;
-        uint32_t pre = block_excl_scan_256(local, s_tmp, &agg);
+        const uint32_t pre = block_excl_scan_256(local, s_tmp, &agg);
         if (tid == 0) {
             st_volatile64(lookback + pid, lb_make(epoch, pid == 0 ? LB_INC : LB_AGG, agg));
             uint32_t excl = 0;
@@ -253,91 +250,86 @@ __global__ void __launch_bounds__(DUP_THREADS) duplicate_kernel(
             }
         }
         __syncthreads();
-        // rects of up to DUP_SMALL tiles: the owning thread emits them; larger
-        // ones (a Gaussian close to the camera can cover thousands of tiles)
-        // are emitted by the whole warp, one tile per lane, coalesced
-        uint32_t item_off[DUP_ITEMS];
-        {
-            uint32_t off = s_excl + pre;
-#pragma unroll
-            for (int i = 0; i < DUP_ITEMS; ++i) {
-                item_off[i] = off;
-                off += cnt[i];
-            }
-        }
+        uint32_t off = s_excl + pre;
 #pragma unroll
         for (int i = 0; i < DUP_ITEMS; ++i) {
-            if (cnt[i] == 0 || cnt[i] > DUP_SMALL) continue;
-            const uint32_t s = slot[i];
-            const int v = (int)(s / (uint64_t)N);
-            const uint2 r = rect[s];
-            const int x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff, y1 = r.y >> 16;
-            const int tbase = V.v[v].tile_base, tw = V.v[v].tiles_x;
-            uint32_t off = item_off[i];
-            for (int ty = y0; ty < y1; ++ty)
-                for (int txi = x0; txi < x1; ++txi, ++off) {
-                    if (off >= cap) continue;
-                    const uint32_t key = (uint32_t)(tbase + ty * tw + txi);
-                    pkeys[off] = key;
-                    pvals[off] = s;
-                    for (int p = 0; p < tile_passes; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 255u)], 1u);
-                }
-        }
-        const int lane = tid & 31;
-#pragma unroll
-        for (int i = 0; i < DUP_ITEMS; ++i) {
-            uint32_t big = __ballot_sync(0xffffffffu, cnt[i] > DUP_SMALL);
-            while (big) {
-                const int src = __ffs(big) - 1;
-                big &= big - 1;
-                const uint32_t s = __shfl_sync(0xffffffffu, slot[i], src);
-                const uint32_t o = __shfl_sync(0xffffffffu, item_off[i], src);
-                const uint32_t c = __shfl_sync(0xffffffffu, cnt[i], src);
-                const int v = (int)(s / (uint64_t)N);
-                const uint2 r = rect[s];
-                const int x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff;
-                const uint32_t w = (uint32_t)(x1 - x0);
-                const int tbase = V.v[v].tile_base, tw = V.v[v].tiles_x;
-                for (uint32_t e0 = 0; e0 < c; e0 += 32) {
-                    const uint32_t e = e0 + lane;
-                    const bool live = e < c && o + e < cap;
-                    const uint32_t active = __ballot_sync(0xffffffffu, live);
-                    if (!live) continue;
-                    const uint32_t ry = e / w, rx = e - ry * w;
-                    const uint32_t key = (uint32_t)(tbase + (y0 + (int)ry) * tw + x0 + (int)rx);
-                    pkeys[o + e] = key;
-                    pvals[o + e] = s;
-                    for (int p = 0; p < tile_passes; ++p)
-                        hist_add_warp(s_hist + p * 256, (key >> (8 * p)) & 255u, active);
-                }
-            }
+            if (base + i < nvis) offsets[base + i] = off;
+            off += cnt[i];
         }
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------------
+// pair emission: one thread per (Gaussian, tile) pair, balanced however the
+// tiles are spread over Gaussians (a Gaussian close to the camera can cover
+// thousands of tiles); pair e belongs to the sorted slot j with
+// offsets[j] <= e < offsets[j+1], tiles in row-major order of its rect
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) emit_pairs_kernel(
+    const uint32_t* __restrict__ sorted_slots, const uint32_t* __restrict__ offsets, const uint2* __restrict__ rect,
+    int64_t N, const __grid_constant__ Views V, uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals, uint32_t cap,
+    uint32_t* scratch, int tile_passes) {
+    __shared__ uint32_t s_hist[3 * 256];
+    for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) s_hist[i] = 0;
     __syncthreads();
-    for (int i = tid; i < tile_passes * 256; i += DUP_THREADS) {
+    const uint32_t nvis = scratch[SCR_NVIS];
+    const uint32_t P = min(scratch[SCR_PAIRS], cap);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t e0 = blockIdx.x * blockDim.x; e0 < P; e0 += stride) {
+        const uint32_t e = e0 + threadIdx.x;
+        const bool live = e < P;
+        const uint32_t active = __ballot_sync(0xffffffffu, live);
+        if (!live) continue;
+        // last j with offsets[j] <= e
+        uint32_t lo = 0, hi = nvis;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(offsets + mid) <= e) lo = mid; else hi = mid;
+        }
+        const uint32_t s = __ldg(sorted_slots + lo);
+        const uint32_t local = e - __ldg(offsets + lo);
+        const uint2 r = __ldg(rect + s);
+        const uint32_t x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff;
+        const uint32_t w = x1 - x0;
+        const uint32_t ry = local / w, rx = local - ry * w;
+        const int v = (int)(s / (uint64_t)N);
+        const uint32_t key = (uint32_t)(V.v[v].tile_base + (int)(y0 + ry) * V.v[v].tiles_x + (int)(x0 + rx));
+        pkeys[e] = key;
+        pvals[e] = s;
+        for (int p = 0; p < tile_passes; ++p) hist_add_warp(s_hist + p * 256, (key >> (8 * p)) & 255u, active);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < tile_passes * 256; i += blockDim.x) {
         const uint32_t h = s_hist[i];
         if (h) atomicAdd(scratch + SCR_TILE_HIST + i, h);
     }
 }
 
-cudaError_t launch_duplicate(const uint32_t* sorted_slots, const uint32_t* /*scratch_nvis*/, const uint32_t* ntiles,
-                             const uint2* rect, int64_t N, const Views& V, uint32_t* pkeys, uint32_t* pvals, uint32_t cap,
+cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, const uint32_t* ntiles, const uint2* rect,
+                             int64_t N, const Views& V, uint32_t* pkeys, uint32_t* pvals, uint32_t cap,
                              uint32_t* scratch, int tile_passes, unsigned long long* lookback, const uint32_t* state,
                              uint32_t epoch_offset, uint32_t* err, int64_t max_slots, cudaStream_t st) {
-    static int max_grid = 0;
+    static int max_grid = 0, sms = 148;
     if (!max_grid) {
-        int dev = 0, sms = 148, per = 1;
+        int dev = 0, per = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, duplicate_kernel, DUP_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_offsets_kernel, DUP_THREADS, 0);
         max_grid = sms * (per > 0 ? per : 1);
     }
     int64_t parts = ceil_div(max_slots > 0 ? max_slots : 1, DUP_TILE);
     int grid = (int)(parts < max_grid ? parts : max_grid);
-    count_launches(1);
-    duplicate_kernel<<<grid, DUP_THREADS, 0, st>>>(sorted_slots, ntiles, rect, N, V, pkeys, pvals, cap, scratch,
-                                                   tile_passes, lookback, state, epoch_offset, err);
+    count_launches(2);
+    pair_offsets_kernel<<<grid, DUP_THREADS, 0, st>>>(sorted_slots, ntiles, offsets, cap, scratch, lookback, state,
+                                                      epoch_offset, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int64_t eg = ceil_div((int64_t)cap, 256);
+    if (eg > (int64_t)sms * 8) eg = (int64_t)sms * 8;
+    if (eg < 1) eg = 1;
+    emit_pairs_kernel<<<(unsigned)eg, 256, 0, st>>>(sorted_slots, offsets, rect, N, V, pkeys, pvals, cap, scratch,
+                                                     tile_passes);
     return cudaGetLastError();
 }
 
