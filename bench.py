@@ -288,7 +288,10 @@ def run_ours(args):
     # launch shape of the blend kernels, picked on this workload
     from paper_2403_11247_b300.autotune import autotune_ppt
     b = w["bufs"]
-    tune = autotune_ppt(w["sh"], [w["cam"]], w["ctx"], b["dC"], b["dD"], None, w["grads"], reps=5)
+    if args.no_autotune:
+        tune = {"ppt_fwd": args.ppt_fwd or 2, "ppt_bwd": args.ppt_bwd or 2, "autotuned": False}
+    else:
+        tune = autotune_ppt(w["sh"], [w["cam"]], w["ctx"], b["dC"], b["dD"], None, w["grads"], reps=5)
     if args.ppt_fwd:
         tune["ppt_fwd"] = args.ppt_fwd
     if args.ppt_bwd:
@@ -458,6 +461,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="launch the step's kernels one by one")
     ap.add_argument("--ppt-fwd", type=int, default=0, help="override the autotuned forward pixels per thread")
     ap.add_argument("--ppt-bwd", type=int, default=0, help="override the autotuned backward pixels per thread")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -223,7 +223,9 @@ vg_status vg_ctx_profile_read(vg_ctx* ctx, vg_stream stream, double* ms_total, i
  * count is vg_stats.pairs).
  *   VG_BUF_XY         float4 [slots]  projected mean (u, v) and the half extents of the
  *                                     box where alpha can reach alpha_min (slot = view*N + n)
- *   VG_BUF_CONIC      float4 [slots]  inverse 2D covariance a, b, c and opacity
+ *   VG_BUF_CONIC      float4 [slots]  base-2 exponent coefficients -a/2 log2 e, -b log2 e,
+ *                                     -c/2 log2 e of the inverse 2D covariance [[a,b],[b,c]]
+ *                                     and log2(alpha_min / opacity)
  *   VG_BUF_RGBD       float4 [slots]  r, g, b, camera depth
  *   VG_BUF_RECT       uint2  [slots]  tile rect x0|y0<<16, x1|y1<<16
  *   VG_BUF_NTILES     uint32 [slots]  tiles touched (0 = culled)

@@ -236,6 +236,14 @@ vg_status vg_scene_upload(const vg_scene_desc* d, int32_t flags, vg_stream strea
     for (int gi = 0; gi < 4; ++gi) VG_TRY(check_group(*gr[gi], gi, N));
     if (d->mask_logit && !(d->mask_eps > 0.f && d->mask_eps < 1.f))
         return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: mask_eps must be in (0, 1)");
+    {
+        // the preprocess stages every codebook in shared memory
+        size_t cb_bytes = 0;
+        for (int gi = 0; gi < 4; ++gi)
+            if (gr[gi]->stages > 0) cb_bytes += (size_t)gr[gi]->stages * gr[gi]->codewords * gr[gi]->dim * 4;
+        if (cb_bytes > 200 * 1024)
+            return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: codebooks exceed 200 KB in total");
+    }
     cudaStream_t st = (cudaStream_t)stream;
 
     vg_scene* sc = new vg_scene();

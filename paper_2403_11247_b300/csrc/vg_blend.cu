@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     const float Y0 = (float)(ty * TILE + warp * 2 * PPT), Y1 = Y0 + (float)(2 * PPT - 1);
 
     int px[PPT], py[PPT];
+    float fpx[PPT], fpy[PPT];
     bool done[PPT];
     float T[PPT], acc[PPT][5];
     uint32_t last[PPT], stop_at[PPT], nb[PPT];
@@ -72,6 +73,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
         pixel_of<PPT>(threadIdx.x, k, lx, ly);
         px[k] = tx * TILE + lx;
         py[k] = ty * TILE + ly;
+        fpx[k] = (float)px[k];
+        fpy[k] = (float)py[k];
         done[k] = !(px[k] < vi.W && py[k] < vi.H);
         T[k] = 1.f;
         last[k] = 0;
@@ -114,11 +117,11 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     if (done[k]) continue;
-                    const float dx = g.x - (float)px[k], dy = g.y - (float)py[k];
-                    const float power = gauss_power(co.x, co.y, co.z, dx, dy);
-                    if (power > 0.f) continue;
-                    const float alpha = fminf(cs.alpha_max, __fmul_rn(co.w, __expf(power)));
-                    if (alpha < cs.alpha_min) continue;
+                    const float dx = __fsub_rn(g.x, fpx[k]), dy = __fsub_rn(g.y, fpy[k]);
+                    const float p2 = gauss_p2(co.x, co.y, co.z, dx, dy);
+                    const float q = __fsub_rn(p2, co.w);
+                    if (p2 > 0.f || q < 0.f) continue;  // positive exponent, or alpha < alpha_min
+                    const float alpha = fminf(cs.alpha_max, __fmul_rn(cs.alpha_min, fast_exp2(q)));
                     const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                     if (Tn < cs.t_min) {
                         done[k] = true;
@@ -207,7 +210,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     unsigned long long* bwd_pairs, int count) {
     constexpr int NT = TILE_PIX / PPT;
     __shared__ float4 s_xy[BLEND_BATCH];
-    __shared__ float4 s_co[BLEND_BATCH];
+    __shared__ float4 s_co[BLEND_BATCH];   // base-2 exponent coefficients and threshold
+    __shared__ float4 s_nat[BLEND_BATCH];  // inverse 2D covariance a, b, c and 1/opacity
     __shared__ float4 s_cd[BLEND_BATCH];
     __shared__ uint32_t s_slot[BLEND_BATCH];
     __shared__ uint32_t s_max;
@@ -223,6 +227,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     const float Y0 = (float)(ty * TILE + warp * 2 * PPT), Y1 = Y0 + (float)(2 * PPT - 1);
 
     int px[PPT], py[PPT];
+    float fpx[PPT], fpy[PPT];
     uint32_t nc[PPT];
     float T[PPT], Bk[PPT], gp[PPT][5];
     uint32_t mymax = 0;
@@ -232,6 +237,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
         pixel_of<PPT>(threadIdx.x, k, lx, ly);
         px[k] = tx * TILE + lx;
         py[k] = ty * TILE + ly;
+        fpx[k] = (float)px[k];
+        fpy[k] = (float)py[k];
         const bool inside = px[k] < vi.W && py[k] < vi.H;
         const int64_t i = (int64_t)py[k] * vi.W + px[k];
         nc[k] = inside ? ncontrib[pb + i] : 0u;
@@ -270,7 +277,12 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
             const uint32_t s = pvals[bstart + i];
             s_slot[i] = s;
             s_xy[i] = xy[s];
-            s_co[i] = conic_o[s];
+            const float4 co = conic_o[s];
+            s_co[i] = co;
+            // natural-unit conic and 1/opacity: a = -2 ln2 A2, b = -ln2 B2,
+            // c = -2 ln2 C2, 1/o = 2^thr / alpha_min
+            s_nat[i] = make_float4(-2.f * LN2 * co.x, -LN2 * co.y, -2.f * LN2 * co.z,
+                                   fast_exp2(co.w) / cs.alpha_min);
             s_cd[i] = rgbd[s];
         }
         __syncthreads();
@@ -290,6 +302,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
                 const uint32_t jl = bstart - rg.x + (uint32_t)i;
                 const float4 g = s_xy[i];
                 const float4 co = s_co[i];
+                const float4 nat = s_nat[i];
                 const float4 cd = s_cd[i];
                 float vals[10];
 #pragma unroll
@@ -298,14 +311,14 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     if (jl >= nc[k]) continue;
-                    const float dx = g.x - (float)px[k], dy = g.y - (float)py[k];
-                    const float power = gauss_power(co.x, co.y, co.z, dx, dy);
-                    if (power > 0.f) continue;
-                    const float G = __expf(power);
-                    const float x = __fmul_rn(co.w, G);
+                    const float dx = __fsub_rn(g.x, fpx[k]), dy = __fsub_rn(g.y, fpy[k]);
+                    const float p2 = gauss_p2(co.x, co.y, co.z, dx, dy);
+                    const float q = __fsub_rn(p2, co.w);
+                    if (p2 > 0.f || q < 0.f) continue;
+                    const float x = __fmul_rn(cs.alpha_min, fast_exp2(q));  // o e^power before the cap
                     const float alpha = fminf(cs.alpha_max, x);
-                    if (alpha < cs.alpha_min) continue;
-                    const float inv = 1.f / (1.f - alpha);
+                    const float G = x * nat.w;                               // e^power
+                    const float inv = __fdividef(1.f, 1.f - alpha);  // hardware reciprocal, ~2 ulp
                     T[k] *= inv;  // transmittance in front of this Gaussian
                     const float w = gp[k][0] * cd.x + gp[k][1] * cd.y + gp[k][2] * cd.z + gp[k][3] * cd.w + gp[k][4];
                     const float dA = T[k] * w - Bk[k] * inv;
@@ -318,8 +331,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
                     if (x <= cs.alpha_max) {
                         const float dp = alpha * dA;
                         vals[5] = fmaf(G, dA, vals[5]);
-                        vals[0] -= dp * (co.x * dx + co.y * dy);
-                        vals[1] -= dp * (co.y * dx + co.z * dy);
+                        vals[0] -= dp * (nat.x * dx + nat.y * dy);
+                        vals[1] -= dp * (nat.y * dx + nat.z * dy);
                         vals[2] -= 0.5f * dp * dx * dx;
                         vals[3] -= dp * dx * dy;
                         vals[4] -= 0.5f * dp * dy * dy;

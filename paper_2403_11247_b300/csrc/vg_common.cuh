@@ -105,6 +105,25 @@ __device__ __forceinline__ void decode_attr(const SceneDev& S, int g, int64_t n,
     }
 }
 
+// same, with the group's codebook staged in shared memory
+template <int D>
+__device__ __forceinline__ void decode_attr_smem(const SceneDev& S, int g, int64_t n, const float* cb, float* out) {
+    if (S.L[g] > 0) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) out[c] = 0.f;
+        const int K = S.K[g];
+        for (int s = 0; s < S.L[g]; ++s) {
+            const int k = __ldg(S.idx[g] + (int64_t)s * S.N + n);
+            const float* w = cb + (s * K + k) * D;
+#pragma unroll
+            for (int c = 0; c < D; ++c) out[c] += w[c];
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < D; ++c) out[c] = __ldg(S.raw[g] + n * D + c);
+    }
+}
+
 // Eq. 7 with the binning rounding: mu_c = xa_c + (O_c * l_c), no FMA
 __device__ __forceinline__ void anchor_mean(const SceneDev& S, int64_t n, float mu[3]) {
     int64_t a = n / S.k;
@@ -135,12 +154,26 @@ __device__ __forceinline__ void quat_rot(const float q[4], float R[3][3]) {
     R[2][0] = 2.f * (x * z - w * y);       R[2][1] = 2.f * (y * z + w * x);       R[2][2] = 1.f - 2.f * (x * x + y * y);
 }
 
-// Exponent of the 2D Gaussian, -1/2 (a dx^2 + c dy^2) - b dx dy, with every
-// rounding spelled out so the forward and backward kernels decide alike.
-__device__ __forceinline__ float gauss_power(float a, float b, float c, float dx, float dy) {
-    float q = __fmaf_rn(__fmul_rn(a, dx), dx, __fmul_rn(__fmul_rn(c, dy), dy));
-    float bxy = __fmul_rn(__fmul_rn(b, dx), dy);
-    return __fmaf_rn(-0.5f, q, -bxy);
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float LN2 = 0.6931471805599453f;
+
+// The per-slot conic record holds the exponent in base 2:
+//   A2 = -a/2 log2(e), B2 = -b log2(e), C2 = -c/2 log2(e),
+// so that p2 = dx (A2 dx + B2 dy) + C2 dy^2 = log2(e) (-1/2 d^T conic d), and
+//   thr = log2(alpha_min / o).
+// Then alpha >= alpha_min  <=>  q = p2 - thr >= 0, and alpha = alpha_min 2^q:
+// a pixel is rejected before any exponential.  Every rounding is spelled out
+// so that the forward and backward kernels take identical decisions.
+__device__ __forceinline__ float gauss_p2(float A2, float B2, float C2, float dx, float dy) {
+    const float inner = __fmaf_rn(A2, dx, __fmul_rn(B2, dy));
+    return __fmaf_rn(dx, inner, __fmul_rn(__fmul_rn(C2, dy), dy));
+}
+
+// 2^x with the hardware base-2 exponential unit
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {

@@ -17,8 +17,22 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
                                                          uint32_t* __restrict__ blk_count) {
     __shared__ uint32_t s_hist[4 * 256];
     __shared__ uint32_t s_cnt[2];
+    extern __shared__ float s_cb[];  // the coded groups' codebooks, group after group
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_hist[i] = 0;
     if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
+    int cb_off[4];
+    {
+        int off = 0;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            cb_off[g] = off;
+            if (S.L[g] > 0) {
+                const int sz = S.L[g] * S.K[g] * gdim(g);
+                for (int i = threadIdx.x; i < sz; i += blockDim.x) s_cb[off + i] = __ldg(S.cb[g] + i);
+                off += sz;
+            }
+        }
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) state[ST_EPOCH] += 16u;  // fresh lookback epochs for this forward
     __syncthreads();
 
@@ -31,11 +45,22 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
     float opac = 0.f;
     if (live) {
         anchor_mean(S, n, mu);
-        decode_attr<3>(S, 0, n, ls);
-        decode_attr<4>(S, 1, n, q);
-        decode_attr<1>(S, 2, n, &ol);
-        decode_attr<3>(S, 3, n, rgb);
         active = S.mask ? (__ldg(S.mask + n) > S.mask_thr) : true;
+        // a Gaussian behind the near plane of every view needs no attributes
+        bool in_front = false;
+        for (int v = 0; v < V.n && !in_front; ++v) {
+            float T[12], pc[3];
+            view_pose(V, v, T);
+            cam_point(T, mu, pc);
+            in_front = pc[2] > V.v[v].near_plane;
+        }
+        active = active && in_front;
+    }
+    if (live && active) {
+        decode_attr_smem<3>(S, 0, n, s_cb + cb_off[0], ls);
+        decode_attr_smem<4>(S, 1, n, s_cb + cb_off[1], q);
+        decode_attr_smem<1>(S, 2, n, s_cb + cb_off[2], &ol);
+        decode_attr_smem<3>(S, 3, n, s_cb + cb_off[3], rgb);
         float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
         active = active && (qq > 0.f);
         if (active) {
@@ -139,7 +164,9 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
             }
             if (ok) {
                 xy[slot] = make_float4(u, vv, ex, ey);
-                conic_o[slot] = make_float4(a, b, c, opac);
+                // base-2 exponent coefficients and the opacity threshold
+                const float thr = opac > 0.f ? log2f(cs.alpha_min / opac) : 3.0e38f;
+                conic_o[slot] = make_float4(-0.5f * LOG2E * a, -LOG2E * b, -0.5f * LOG2E * c, thr);
                 rgbd[slot] = make_float4(rgb[0], rgb[1], rgb[2], p[2]);
                 rect[slot] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
                 ntiles[slot] = cnt;
@@ -238,13 +265,25 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
 
 int preprocess_blocks(int64_t N) { return (int)ceil_div(N > 0 ? N : 1, 256); }
 
+static size_t codebook_smem(const SceneDev& S) {
+    size_t n = 0;
+    for (int g = 0; g < 4; ++g)
+        if (S.L[g] > 0) n += (size_t)S.L[g] * S.K[g] * gdim(g);
+    return n * sizeof(float);
+}
+
 cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& cs, float4* xy, float4* conic_o,
                               float4* rgbd, uint2* rect, uint32_t* ntiles, uint32_t* dkey, uint32_t* scratch,
                               uint32_t* state, uint32_t* blk_count, cudaStream_t st) {
     const int blocks = preprocess_blocks(S.N);
+    const size_t smem = codebook_smem(S);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(preprocess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     count_launches(1);
-    preprocess_kernel<<<(unsigned)blocks, 256, 0, st>>>(S, V, cs, xy, conic_o, rgbd, rect, ntiles, dkey, scratch, state,
-                                                        blk_count);
+    preprocess_kernel<<<(unsigned)blocks, 256, smem, st>>>(S, V, cs, xy, conic_o, rgbd, rect, ntiles, dkey, scratch,
+                                                           state, blk_count);
     return cudaGetLastError();
 }
 
