@@ -234,7 +234,7 @@ vg_status vg_ctx_profile_read(vg_ctx* ctx, vg_stream stream, double* ms_total, i
  *   VG_BUF_RANGES     uint2  [tiles]  [start, end) of each tile's list
  *   VG_BUF_T_FINAL    float  [pixels] transmittance after compositing
  *   VG_BUF_N_CONTRIB  uint32 [pixels] list position + 1 of the last blended Gaussian
- *   VG_BUF_G2D        float  [slots][10] du dv da db dc dopacity dr dg db ddepth */
+ *   VG_BUF_G2D        float  [slots][12] du dv da db dc dopacity dr dg db ddepth, 2 pad */
 enum {
     VG_BUF_XY = 0, VG_BUF_CONIC, VG_BUF_RGBD, VG_BUF_RECT, VG_BUF_NTILES, VG_BUF_PAIR_KEYS, VG_BUF_PAIR_VALS,
     VG_BUF_RANGES, VG_BUF_T_FINAL, VG_BUF_N_CONTRIB, VG_BUF_G2D

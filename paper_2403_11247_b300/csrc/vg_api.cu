@@ -165,6 +165,7 @@ struct vg_ctx {
         scratch, state, dattr, pose_part, icp_part, loss_scratch, pair_off, blk_count, blk_base, touched;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
+    bool g2d_clean = false;
     Views views{};
     int64_t fwd_N = -1;
     const vg_scene* fwd_scene = nullptr;
@@ -371,7 +372,7 @@ vg_status vg_ctx_create(int64_t pair_capacity, vg_ctx** out) {
     *out = nullptr;
     vg_ctx* c = new vg_ctx();
     vg_status s = c->state.ensure(ST_WORDS * 4, nullptr, "state");
-    if (s == VG_OK) s = c->scratch.ensure(SCR_WORDS * 4, nullptr, "scratch");
+    if (s == VG_OK) s = c->scratch.ensure(SCR_WORDS * 4 + 4096 * 4, nullptr, "scratch");
     if (s == VG_OK) s = c->loss_scratch.ensure(16, nullptr, "loss");
     if (s != VG_OK) {
         delete c;
@@ -613,6 +614,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
         VG_TRY(ctx->dval[b].ensure(slots * 4, st, "depth values"));
     }
     VG_TRY(ctx->ranges.ensure((size_t)V.total_tiles * 8, st, "ranges"));
+    VG_TRY(ctx->scratch.ensure((size_t)(SCR_WORDS + V.total_tiles) * 4, st, "scratch"));
     VG_TRY(ctx->Tfin.ensure(pixels * 4, st, "T_final"));
     VG_TRY(ctx->ncontrib.ensure(pixels * 4, st, "n_contrib"));
     const int64_t lb_parts = std::max(ceil_div(slots, SORT_TILE), ceil_div(ctx->pair_cap, SORT_TILE));
@@ -628,7 +630,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     unsigned long long* lb = ctx->lookback.as<unsigned long long>();
     const bool prof_graph = capturing(st);
     const bool prof_on = ctx->prof.on;
-    VG_STAGE(VG_STAGE_MEMSET, cudaMemsetAsync(scr, 0, SCR_WORDS * 4, st));
+    VG_STAGE(VG_STAGE_MEMSET, cudaMemsetAsync(scr, 0, (size_t)(SCR_WORDS + V.total_tiles) * 4, st));
     VG_STAGE(VG_STAGE_PREPROCESS,
              launch_preprocess(sd, V, cs, ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
                                ctx->rect.as<uint2>(), ctx->ntiles.as<uint32_t>(), ctx->dkey[1].as<uint32_t>(), scr,
@@ -672,8 +674,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
              })());
     const int fin = tp & 1;
     ctx->final_pair = fin;
-    VG_STAGE(VG_STAGE_RANGES, launch_ranges(ctx->pkey[fin].as<uint32_t>(), scr + SCR_PAIRS, cap, V.total_tiles,
-                                            ctx->ranges.as<uint2>(), st));
+    VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr + SCR_TILE_COUNTS, V.total_tiles, ctx->ranges.as<uint2>(), st));
     VG_STAGE(VG_STAGE_BLEND_FWD,
              launch_blend_fwd(V, cs, params->ppt_fwd, ctx->ranges.as<uint2>(), ctx->pval[fin].as<uint32_t>(),
                               ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(), C, D, S,
@@ -708,7 +709,9 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     if (!same_views(V, ctx->views)) return fail(VG_ERR_INVALID_ARG, "vg_render_bwd: cameras differ from the forward");
     const SceneDev& sd = scene->dev;
     const int64_t N = sd.N, slots = N * n_views;
+    if (ctx->g2d.bytes < (size_t)slots * G2D_STRIDE * 4) ctx->g2d_clean = false;
     VG_TRY(ctx->g2d.ensure(slots * G2D_STRIDE * 4, st, "g2d"));
+
     const int nb = chain_blocks(N);
     VG_TRY(ctx->pose_part.ensure((size_t)n_views * nb * 6 * 4, st, "pose partials"));
     bool need_attr = false;
@@ -719,7 +722,13 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
 
     const bool prof_graph = capturing(st);
     const bool prof_on = ctx->prof.on;
-    VG_STAGE(VG_STAGE_MEMSET, cudaMemsetAsync(ctx->g2d.p, 0, slots * G2D_STRIDE * 4, st));
+    if (!ctx->g2d_clean) {  // rows of slots that were never visible stay zero from here on
+        VG_CUDA(cudaMemsetAsync(ctx->g2d.p, 0, ctx->g2d.bytes, st));
+        ctx->g2d_clean = true;
+    }
+    VG_STAGE(VG_STAGE_MEMSET, launch_zero_visible_g2d(ctx->dval[0].as<uint32_t>(),
+                                                      ctx->scratch.as<uint32_t>() + SCR_NVIS, (uint32_t)slots,
+                                                      ctx->g2d.as<float>(), st));
     VG_STAGE(VG_STAGE_BLEND_BWD,
              launch_blend_bwd(V, cs, params->ppt_bwd, ctx->ranges.as<uint2>(), ctx->pval[ctx->final_pair].as<uint32_t>(),
                               ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
@@ -736,7 +745,7 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
                  launch_chain(sd, V, cs, ctx->g2d.as<float>(), need_attr ? ctx->dattr.as<float>() : nullptr, raws[0],
                               raws[1], raws[2], raws[3], grads->anchor_xyz, grads->anchor_l, grads->offsets,
                               grads->mask_logit, ctx->pose_part.as<float>(), ctx->touched.as<uint32_t>(),
-                              &ctx->pose_blocks, st));
+                              ctx->ntiles.as<uint32_t>(), &ctx->pose_blocks, st));
     } else {
         VG_CUDA(cudaMemsetAsync(ctx->pose_part.p, 0, (size_t)n_views * nb * 6 * 4, st));
         ctx->pose_blocks = nb;

@@ -66,7 +66,7 @@ struct SceneDev {
 __host__ __device__ constexpr int gdim(int g) { return g == 0 ? 3 : (g == 1 ? 4 : (g == 2 ? 1 : 3)); }
 __host__ __device__ constexpr int goff(int g) { return g == 0 ? 0 : (g == 1 ? 3 : (g == 2 ? 7 : 8)); }
 constexpr int ATTR_STRIDE = 11;
-constexpr int G2D_STRIDE = 10;  // du dv da db dc dopacity dr dg db ddepth
+constexpr int G2D_STRIDE = 12;  // du dv da db dc dopacity dr dg db ddepth, 2 pad (16-byte rows)
 
 __device__ __forceinline__ int view_of_tile(const Views& V, int gt) {
     int lo = 0, hi = V.n - 1;

@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
                                                              float* raw0, float* raw1, float* raw2, float* raw3,
                                                              float* d_xyz, float* d_l, float* d_off, float* d_mask,
                                                              float* __restrict__ pose_part,
-                                                             uint32_t* __restrict__ touched_mask) {
+                                                             uint32_t* __restrict__ touched_mask,
+                                                             const uint32_t* __restrict__ ntiles) {
     __shared__ float s_red[8][6];
     const int64_t n = (int64_t)blockIdx.x * CHAIN_THREADS + threadIdx.x;
     const bool live = n < S.N;
@@ -38,9 +39,11 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
     float R[3][3], s[3] = {1, 1, 1}, qn[4] = {1, 0, 0, 0}, qnorm = 1.f, Sig[3][3];
     // most Gaussians reach no pixel of any view: their gradients are zero and
     // they need no decode
+    // only slots visible in the last forward carry gradient rows
     bool touched = false;
     if (live) {
         for (int v = 0; v < V.n && !touched; ++v) {
+            if (ntiles[(int64_t)v * S.N + n] == 0u) continue;
             const float* gg = g2d + ((int64_t)v * S.N + n) * G2D_STRIDE;
 #pragma unroll
             for (int c = 0; c < 10; ++c) touched |= gg[c] != 0.f;
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
     float dmu[3] = {0, 0, 0}, dSig[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, dop = 0.f, drgb[3] = {0, 0, 0};
     for (int v = 0; v < V.n; ++v) {
         float pose[6] = {0, 0, 0, 0, 0, 0};
-        if (live && active) {
+        if (live && active && ntiles[(int64_t)v * S.N + n] != 0u) {
             const float* gg = g2d + ((int64_t)v * S.N + n) * G2D_STRIDE;
             float g[10];
             bool nz = false;
@@ -299,14 +302,36 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
 
 int chain_blocks(int64_t N) { return (int)ceil_div(N > 0 ? N : 1, CHAIN_THREADS); }
 
+// zero the gradient rows of the visible slots (the only rows the backward
+// blend writes); all other rows are kept at zero
+__global__ void zero_visible_g2d_kernel(const uint32_t* __restrict__ vis, const uint32_t* __restrict__ nvis_dev,
+                                        uint32_t max_vis, float* __restrict__ g2d) {
+    const uint32_t n = min(*nvis_dev, max_vis);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n * 3; e += gridDim.x * blockDim.x) {
+        const uint32_t s = vis[e / 3];
+        reinterpret_cast<float4*>(g2d + (int64_t)s * G2D_STRIDE)[e % 3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+cudaError_t launch_zero_visible_g2d(const uint32_t* vis_slots, const uint32_t* nvis_dev, uint32_t max_vis, float* g2d,
+                                    cudaStream_t st) {
+    int64_t blocks = ceil_div((int64_t)max_vis * 3, 256);
+    if (blocks > 148 * 4) blocks = 148 * 4;
+    if (blocks < 1) blocks = 1;
+    count_launches(1);
+    zero_visible_g2d_kernel<<<(unsigned)blocks, 256, 0, st>>>(vis_slots, nvis_dev, max_vis, g2d);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, const float* g2d, float* dattr, float* r0,
                          float* r1, float* r2, float* r3, float* d_xyz, float* d_l, float* d_off, float* d_mask,
-                         float* pose_part, uint32_t* touched, int* n_blocks_out, cudaStream_t st) {
+                         float* pose_part, uint32_t* touched, const uint32_t* ntiles, int* n_blocks_out,
+                         cudaStream_t st) {
     const int blocks = chain_blocks(S.N);
     if (n_blocks_out) *n_blocks_out = blocks;
     count_launches(1);
     chain_kernel<<<blocks, CHAIN_THREADS, 0, st>>>(S, V, cs, g2d, dattr, r0, r1, r2, r3, d_xyz, d_l, d_off, d_mask,
-                                                   pose_part, touched);
+                                                   pose_part, touched, ntiles);
     return cudaGetLastError();
 }
 

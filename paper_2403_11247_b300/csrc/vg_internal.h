@@ -18,6 +18,7 @@ constexpr int SCR_CNT_DUP = 1798;
 constexpr int SCR_CNT_TILE = 1799;     // 3 pass counters
 constexpr int SCR_LOSS_VALID = 1802;
 constexpr int SCR_WORDS = 1808;
+constexpr int SCR_TILE_COUNTS = SCR_WORDS;  // per-tile pair counts follow, [total_tiles]
 
 // persistent state words
 constexpr int ST_EPOCH = 0;
@@ -33,6 +34,7 @@ constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 constexpr int DUP_THREADS = 256;
 constexpr int DUP_ITEMS = 4;
 constexpr int DUP_TILE = DUP_THREADS * DUP_ITEMS;
+constexpr int EMIT_SMEM_TILES = 16384;  // per-tile counts kept in shared memory up to this many tiles
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -65,8 +67,8 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, co
                              uint32_t cap, uint32_t* scratch, int tile_passes, unsigned long long* lookback,
                              const uint32_t* state, uint32_t epoch_offset, uint32_t* err, int64_t max_slots,
                              cudaStream_t st);
-cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* pairs_dev, uint32_t cap, int n_tiles, uint2* ranges,
-                          cudaStream_t st);
+// per-tile [start, end) from the per-tile pair counts (one-block scan)
+cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, cudaStream_t st);
 cudaError_t launch_epoch_bump(uint32_t* state, uint32_t by, cudaStream_t st);
 
 // blend.cu
@@ -83,7 +85,9 @@ cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, const ui
 cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, const float* g2d, float* dattr,
                          float* raw_grad0, float* raw_grad1, float* raw_grad2, float* raw_grad3, float* d_xyz,
                          float* d_l, float* d_off, float* d_mask, float* pose_part, uint32_t* touched,
-                         int* n_blocks_out, cudaStream_t st);
+                         const uint32_t* ntiles, int* n_blocks_out, cudaStream_t st);
+cudaError_t launch_zero_visible_g2d(const uint32_t* vis_slots, const uint32_t* nvis_dev, uint32_t max_vis, float* g2d,
+                                    cudaStream_t st);
 int chain_blocks(int64_t N);
 // codebook-gradient reductions of all coded groups in one launch: block
 // range [block_start[j], block_start[j+1]) serves group job j, one block per

@@ -271,7 +271,12 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(
     int64_t N, const __grid_constant__ Views V, uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals, uint32_t cap,
     uint32_t* scratch, int tile_passes) {
     __shared__ uint32_t s_hist[3 * 256];
+    extern __shared__ uint32_t s_tiles[];  // per-tile counts when they fit, else counted in global memory
+    const bool tiles_in_smem = V.total_tiles <= EMIT_SMEM_TILES;
     for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) s_hist[i] = 0;
+    if (tiles_in_smem)
+        for (int i = threadIdx.x; i < V.total_tiles; i += blockDim.x) s_tiles[i] = 0;
+    uint32_t* tile_counts = scratch + SCR_TILE_COUNTS;
     __syncthreads();
     const uint32_t nvis = scratch[SCR_NVIS];
     const uint32_t P = min(scratch[SCR_PAIRS], cap);
@@ -298,12 +303,24 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(
         pkeys[e] = key;
         pvals[e] = s;
         for (int p = 0; p < tile_passes; ++p) hist_add_warp(s_hist + p * 256, (key >> (8 * p)) & 255u, active);
+        {
+            const uint32_t peers = __match_any_sync(active, key);
+            if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) {
+                if (tiles_in_smem) atomicAdd(s_tiles + key, (uint32_t)__popc(peers));
+                else atomicAdd(tile_counts + key, (uint32_t)__popc(peers));
+            }
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < tile_passes * 256; i += blockDim.x) {
         const uint32_t h = s_hist[i];
         if (h) atomicAdd(scratch + SCR_TILE_HIST + i, h);
     }
+    if (tiles_in_smem)
+        for (int i = threadIdx.x; i < V.total_tiles; i += blockDim.x) {
+            const uint32_t h = s_tiles[i];
+            if (h) atomicAdd(tile_counts + i, h);
+        }
 }
 
 cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, const uint32_t* ntiles, const uint2* rect,
@@ -328,35 +345,57 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, co
     int64_t eg = ceil_div((int64_t)cap, 256);
     if (eg > (int64_t)sms * 8) eg = (int64_t)sms * 8;
     if (eg < 1) eg = 1;
-    emit_pairs_kernel<<<(unsigned)eg, 256, 0, st>>>(sorted_slots, offsets, rect, N, V, pkeys, pvals, cap, scratch,
-                                                     tile_passes);
+    const size_t smem = V.total_tiles <= EMIT_SMEM_TILES ? (size_t)V.total_tiles * 4 : 0;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(emit_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    emit_pairs_kernel<<<(unsigned)eg, 256, smem, st>>>(sorted_slots, offsets, rect, N, V, pkeys, pvals, cap, scratch,
+                                                        tile_passes);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// per-tile [start, end) of the sorted pair keys by binary search
+// per-tile [start, end): exclusive scan of the per-tile pair counts (one block)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* keys, uint32_t n, uint32_t x) {
-    uint32_t lo = 0, hi = n;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (keys[mid] < x) lo = mid + 1; else hi = mid;
+__global__ void __launch_bounds__(1024) ranges_kernel(const uint32_t* __restrict__ cnt, int n, uint2* __restrict__ ranges) {
+    __shared__ uint32_t s_w[32];
+    __shared__ uint32_t s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += 1024) {
+        const int i = c0 + threadIdx.x;
+        const uint32_t x = i < n ? cnt[i] : 0u;
+        uint32_t inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t t = s_w[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            s_w[lane] = t;
+        }
+        __syncthreads();
+        const uint32_t start = s_carry + (warp ? s_w[warp - 1] : 0u) + inc - x;
+        if (i < n) ranges[i] = make_uint2(start, start + x);
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += s_w[31];
+        __syncthreads();
     }
-    return lo;
 }
 
-__global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* pairs_dev, uint32_t cap, int n_tiles,
-                              uint2* __restrict__ ranges) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_tiles) return;
-    const uint32_t n = min(*pairs_dev, cap);
-    ranges[t] = make_uint2(lower_bound_u32(keys, n, (uint32_t)t), lower_bound_u32(keys, n, (uint32_t)t + 1u));
-}
-
-cudaError_t launch_ranges(const uint32_t* keys, const uint32_t* pairs_dev, uint32_t cap, int n_tiles, uint2* ranges,
-                          cudaStream_t st) {
+cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, cudaStream_t st) {
     count_launches(1);
-    ranges_kernel<<<(unsigned)ceil_div(n_tiles, 256), 256, 0, st>>>(keys, pairs_dev, cap, n_tiles, ranges);
+    ranges_kernel<<<1, 1024, 0, st>>>(tile_counts, n_tiles, ranges);
     return cudaGetLastError();
 }
 

@@ -389,7 +389,7 @@ VG_BUF = dict(xy=0, conic=1, rgbd=2, rect=3, ntiles=4, pair_keys=5, pair_vals=6,
               g2d=10)
 _BUF_DTYPE = dict(xy=("float32", 4), conic=("float32", 4), rgbd=("float32", 4), rect=("uint32", 2),
                   ntiles=("uint32", 1), pair_keys=("uint32", 1), pair_vals=("uint32", 1), ranges=("uint32", 2),
-                  t_final=("float32", 1), n_contrib=("uint32", 1), g2d=("float32", 10))
+                  t_final=("float32", 1), n_contrib=("uint32", 1), g2d=("float32", 12))
 
 
 def vg_ctx_buffer(ctx: CtxHandle, which: str, count: int, stream=None) -> np.ndarray:

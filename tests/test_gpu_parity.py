@@ -171,7 +171,7 @@ def backward_parity(scene, cams, label, seed=77, **pkw):
     gg = to_np_grads(grads)
     og = o.backward(dC, dD, dS, threads=8)
     worst = {}
-    g2d = V.vg_ctx_buffer(ctx, "g2d", o.n_slots)
+    g2d = V.vg_ctx_buffer(ctx, "g2d", o.n_slots)[:, :10]
     worst["g2d"] = grad_tolerance_check(g2d, og["g2d"], label + ":g2d")
     for name in ("anchor_xyz", "anchor_l", "offsets", "logscale", "rot", "opacity", "rgb"):
         worst[name] = grad_tolerance_check(gg[name], og[name], f"{label}:{name}")
