@@ -317,6 +317,26 @@ vg_status vg_pose_step(int32_t n_views, float* pose, const float* dxi, float* m,
 /* Number of CUDA kernels libvg has enqueued in this process (host count). */
 int64_t vg_launch_count(void);
 
+/* vg_loss_l1 without a ctx, for callers that cannot allocate device memory
+ * (the paper has no counterpart: this is a library facility).  Making a
+ * vg_ctx allocates; code that runs while another framework owns the device
+ * allocator, real-time threads that must not risk the device-wide
+ * synchronisation of cudaMalloc, or code that only enqueues into streams it
+ * does not own, can call this instead.  Same arguments, layout and results as
+ * vg_loss_l1 (minus the ctx).  Its scratch -- one valid-pixel counter per view
+ * -- is a file-scope device array of VG_NOALLOC_MAX_VIEWS words that every GPU
+ * loading the library holds until the process exits; n_views above that limit
+ * returns VG_ERR_INVALID_ARG.  It calls no cudaMalloc or cudaFree and clears
+ * the counters it uses on `stream` before each use.  The first call on each
+ * device (with that device current) looks the array's device address up with
+ * cudaGetSymbolAddress; make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU (unordered streams)
+ * race on it and must be serialised by the caller. */
+#define VG_NOALLOC_MAX_VIEWS 256
+vg_status vg_loss_l1_noalloc(int32_t n_views, int64_t n_pix, const float* C, const float* D, const float* S,
+                             const float* Ct, const float* Dt, float w_depth, float gate,
+                             float* dC, float* dD, float* dS, float* loss, vg_stream stream);
+
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char* vg_last_error(void);
 

@@ -18,14 +18,20 @@ using namespace vgk;
 
 #include <atomic>
 
+namespace {
+thread_local std::string g_err;
+}  // namespace
+
 namespace vgk {
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+vg_status set_error(vg_status s, const char* msg) {
+    g_err = msg;
+    return s;
+}
 }  // namespace vgk
 
 namespace {
-
-thread_local std::string g_err;
 
 vg_status fail(vg_status s, const std::string& msg) {
     g_err = msg;

@@ -40,6 +40,8 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // kernels enqueued by this library in this process (host-side count)
 void count_launches(int n);
+// record the message returned by vg_last_error() and return s
+vg_status set_error(vg_status s, const char* msg);
 
 // preprocess.cu
 int preprocess_blocks(int64_t N);

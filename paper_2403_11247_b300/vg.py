@@ -96,6 +96,7 @@ def lib():
             "vg_render_bwd": [P, P, I32, P, P, P, P, P, P, P],
             "vg_pose_grad": [P, I32, P, P, P, P, P],
             "vg_loss_l1": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P, P],
+            "vg_loss_l1_noalloc": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P],
             "vg_adam_step": [P, I32, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
             "vg_pose_step": [I32, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
         }
@@ -465,11 +466,33 @@ def vg_launch_count() -> int:
     return int(lib().vg_launch_count())
 
 
+VG_NOALLOC_MAX_VIEWS = 256
+
+
+def vg_loss_l1_noalloc(n_views: int, n_pix: int, C_, D, S, Ct, Dt, w_depth: float, gate: float,
+                       dC=None, dD=None, dS=None, loss=None, stream=None):
+    """vg_loss_l1 without a ctx: its scratch is a static device array, so the
+    call allocates no device memory (outputs are allocated here only when the
+    caller passes none)."""
+    torch = _torch()
+    if dC is None:
+        dC = torch.empty_like(C_)
+    if dD is None:
+        dD = torch.empty_like(D)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=C_.device)
+    _check(lib().vg_loss_l1_noalloc(int(n_views), int(n_pix), _ptr(C_), _ptr(D), _ptr(S), _ptr(Ct), _ptr(Dt),
+                                    float(w_depth), float(gate), _ptr(dC), _ptr(dD), _ptr(dS), _ptr(loss),
+                                    _stream(stream)), "vg_loss_l1_noalloc")
+    return dC, dD, dS, loss
+
+
 def exported_symbols():
     return ["vg_scene_upload", "vg_scene_free", "vg_scene_size", "vg_ctx_create", "vg_ctx_free", "vg_ctx_reserve",
             "vg_check", "vg_ctx_stats", "vg_ctx_reset_counters", "vg_ctx_buffer", "vg_ctx_profile",
             "vg_ctx_profile_read", "vg_adam_step", "vg_pose_step", "vg_rvq_decode", "vg_render_fwd",
-            "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_last_error", "vg_default_params", "vg_launch_count"]
+            "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
+            "vg_launch_count"]
 
 
 def render_with_retry(scene: SceneHandle, cams, params, ctx: CtxHandle, stream=None, max_tries: int = 4):
