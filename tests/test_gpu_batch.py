@@ -1,0 +1,96 @@
+"""The batching form: B views in one launch sequence equal B single-view
+launches; a captured graph of iterations equals the same iterations launched
+one by one; the local bundle adjustment moves perturbed keyframe poses
+toward the poses the targets were rendered from."""
+import numpy as np
+import pytest
+
+from paper_2403_11247_b300 import synth
+from paper_2403_11247_b300 import vg as V
+
+from gpu_common import grad_tolerance_check
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_11247_b300 import build
+    build.build()
+    return t
+
+
+def kf(perturbed=True, n=4, w=160, h=120, f=125.0):
+    return synth.keyframe_cameras(n_views=n, width=w, height=h, f=f, perturbed=perturbed)
+
+
+def test_multiview_launch_equals_single_view_launches(torch):
+    sc = synth.tiny_scene()
+    cams = kf()
+    sh = V.vg_scene_upload(sc)
+    ctx = V.vg_ctx_create(0)
+    prm = V.default_params()
+    Cb, Db, Sb = [x.cpu().numpy() for x in V.render_with_retry(sh, cams, prm, ctx)]
+    P = cams[0].width * cams[0].height
+    rng = np.random.default_rng(0)
+    ups = [rng.uniform(-1, 1, s).astype(np.float32) for s in (3 * P * len(cams), P * len(cams), P * len(cams))]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    V.vg_render_bwd(sh, cams, prm, ctx, *[t(u) for u in ups])
+    dxi_b = V.vg_pose_grad(ctx, len(cams))[0].cpu().numpy()
+    for v, c in enumerate(cams):
+        ctx1 = V.vg_ctx_create(0)
+        C1, D1, S1 = [x.cpu().numpy() for x in V.render_with_retry(sh, [c], prm, ctx1)]
+        assert np.array_equal(C1, Cb[3 * P * v:3 * P * (v + 1)])
+        assert np.array_equal(D1, Db[P * v:P * (v + 1)]) and np.array_equal(S1, Sb[P * v:P * (v + 1)])
+        V.vg_render_bwd(sh, [c], prm, ctx1, t(ups[0][3 * P * v:3 * P * (v + 1)]), t(ups[1][P * v:P * (v + 1)]),
+                        t(ups[2][P * v:P * (v + 1)]))
+        dxi_1 = V.vg_pose_grad(ctx1, 1)[0].cpu().numpy()[0]
+        grad_tolerance_check(dxi_1, dxi_b[v], f"pose {v}", rtol=1e-4, atol_frac=1e-5)
+
+
+def _window(torch, n=4):
+    from paper_2403_11247_b300.autograd import SceneParams
+    from paper_2403_11247_b300.batch import LocalBA
+    sc = synth.tiny_scene()
+    truth = kf(perturbed=False, n=n)
+    scene = SceneParams.from_synth(sc, requires_grad=False)
+    sh = scene.handle()
+    ctx = V.vg_ctx_create(0)
+    Ct, Dt, _ = V.render_with_retry(sh, truth, V.default_params(), ctx)
+    return LocalBA(scene, kf(perturbed=True, n=n), Ct.clone(), Dt.clone()), truth
+
+
+def test_graph_replay_equals_eager_iterations(torch):
+    ba, _ = _window(torch)
+    pose0 = ba.pose.clone()
+    ba.capture(10)
+    ba.pose.copy_(pose0)
+    ba.reset_optimiser()
+    torch.cuda.synchronize()
+    ba.replay()
+    torch.cuda.synchronize()
+    assert ba.check() == V.VG_OK
+    via_graph = ba.pose.clone()
+    ba.pose.copy_(pose0)
+    ba.reset_optimiser()
+    ba.iterate(10)
+    torch.cuda.synchronize()
+    assert torch.allclose(ba.pose, via_graph, atol=2e-5), (ba.pose - via_graph).abs().max()
+    assert not torch.equal(ba.pose, pose0)
+
+
+def test_local_ba_reduces_pose_error(torch):
+    from paper_2403_11247_b300.batch import pose_errors
+    ba, truth = _window(torch, n=8)
+    T_true = np.stack([np.asarray(c.T_cw, np.float64) for c in truth])
+    before = pose_errors(ba.pose.cpu().numpy().astype(np.float64), T_true)
+    ba.capture(50)
+    ba.replay()
+    torch.cuda.synchronize()
+    assert ba.check() == V.VG_OK
+    after = pose_errors(ba.pose.cpu().numpy().astype(np.float64), T_true)
+    assert after[:, 0].mean() < 0.6 * before[:, 0].mean(), (before, after)
+    assert after[:, 1].mean() < 0.6 * before[:, 1].mean(), (before, after)
