@@ -26,6 +26,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -218,6 +220,97 @@ def cpu_baseline(O, synth, scene, cam, tcam, budget_s=15.0):
             "sample": f"{iters} oracle fwd+bwd iterations on a {H_IMG // 8}-row band (1/8) of the 1200x680 image "
                       f"(full 320k-Gaussian scene decoded and binned each time), scaled to full images; "
                       f"{dt:.1f} s on {threads} OpenMP threads"}
+
+
+SERVING_SCENES = (50000, 300000, 1000000, 2000000)
+SERVING_SIZES = ((320, 240), (640, 480), (1280, 720), (1920, 1080))
+
+
+def serving_leg(torch, V, synth, rates, seconds, p_track=0.3):
+    """Continuous batching against one-request-at-a-time launches on the same
+    Poisson traces: four resident room scenes of 50k/300k/1M/2M Gaussians,
+    render and pose-track requests of 320x240 to 1920x1080."""
+    from paper_2403_11247_b300 import serve
+    scenes = {i: V.vg_scene_upload(synth.serving_scene(n, 2000 + i)) for i, n in enumerate(SERVING_SCENES)}
+    wl = serve.RoomWorkload(scenes, SERVING_SIZES)
+    batched = serve.Server(scenes, n_streams=4, max_views=16)
+    serial = serve.Server(scenes, n_streams=1, max_views=1)
+    # size every workspace and the pinned-memory cache on traces of their own
+    for srv in (batched, serial):
+        srv.serve(wl.trace(seed=77, rate=max(rates), duration=0.3, p_track=p_track), realtime=False,
+                  keep_results=False)
+        for k, rate in enumerate(rates):
+            srv.serve(wl.trace(seed=78 + k, rate=rate, duration=0.25, p_track=p_track), keep_results=False)
+    torch.cuda.synchronize()
+    out = {"scenes_gaussians": list(SERVING_SCENES), "sizes": [f"{w}x{h}" for w, h in SERVING_SIZES],
+           "p_track": p_track, "seconds": seconds,
+           "admission": "memory estimate of the launches in flight <= half the free HBM at start",
+           "batched_form": "4 streams, up to 16 same-scene requests (<= 8 x 1920x1080 pixels) per launch sequence",
+           "serial_form": "1 stream, 1 request per launch sequence, arrival order", "runs": []}
+    for k, rate in enumerate(rates):
+        trace = wl.trace(seed=100 + k, rate=rate, duration=seconds, p_track=p_track)
+        row = {"rate_rps": rate, "requests": len(trace)}
+        for name, srv in (("batched", batched), ("serial", serial)):
+            serve.reset(trace)
+            row[name] = srv.serve(trace, keep_results=False)
+        row["p99_speedup"] = row["serial"]["p99_ms"] / row["batched"]["p99_ms"]
+        out["runs"].append(row)
+        log(f"serving {rate:.0f} req/s: batched p50 {row['batched']['p50_ms']:.2f} p99 "
+            f"{row['batched']['p99_ms']:.2f} ms {row['batched']['throughput_rps']:.0f} rps; serial p50 "
+            f"{row['serial']['p50_ms']:.2f} p99 {row['serial']['p99_ms']:.2f} ms "
+            f"{row['serial']['throughput_rps']:.0f} rps")
+    return out
+
+
+def local_ba_leg(torch, V, synth, iters=50):
+    """Sliding-window local BA on the mapping room: 8 keyframes of 640x480
+    with perturbed poses, one multi-view launch sequence per iteration,
+    `iters` iterations captured in one CUDA graph, against the same
+    iterations launched one by one."""
+    from paper_2403_11247_b300.autograd import SceneParams
+    from paper_2403_11247_b300.autotune import autotune_ppt
+    from paper_2403_11247_b300.batch import LocalBA, pose_errors
+    sc = synth.room_scene()
+    scene = SceneParams.from_synth(sc, requires_grad=False)
+    sh = scene.handle()
+    truth = [synth.room_camera(640, 480, 500.0, pose_seed=300 + i, jitter_deg=3.0, jitter_m=0.1) for i in range(8)]
+    rng = np.random.default_rng(1003)
+    pert = [synth.camera(c.fx, c.fy, c.cx, c.cy, c.width, c.height, synth.perturb_pose(c.T_cw, rng, 2.0, 0.05), c.near)
+            for c in truth]
+    ctx = V.vg_ctx_create(0)
+    Ct, Dt, _ = V.render_with_retry(sh, truth, V.default_params(), ctx)
+    ba = LocalBA(scene, pert, Ct.clone(), Dt.clone(), lr_rot=1e-3, lr_trans=1e-3)
+    tune = autotune_ppt(sh, ba.cams, ba.ctx, ba.dC, ba.dD, None, ba.grads, reps=3, pose_dev=ba.pose)
+    ba.params = V.default_params(pose_dev=ba.pose, ppt_fwd=tune["ppt_fwd"], ppt_bwd=tune["ppt_bwd"])
+    T_true = np.stack([np.asarray(c.T_cw, np.float64) for c in truth])
+    pose0 = ba.pose.clone()
+    ba.capture(iters)
+    res = {"keyframes": 8, "size": "640x480", "iters_per_graph": iters, "autotune": tune}
+    for name in ("graph", "eager"):
+        times = []
+        for _ in range(3):
+            ba.pose.copy_(pose0)
+            ba.reset_optimiser()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            if name == "graph":
+                ba.replay()
+            else:
+                ba.iterate(iters)
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        if ba.check() != V.VG_OK:
+            raise RuntimeError("local BA: device status not OK")
+        res[f"{name}_iters_per_s"] = iters / (min(times) / 1000.0)
+    before = pose_errors(pose0.cpu().numpy().astype(np.float64), T_true)
+    after = pose_errors(ba.pose.cpu().numpy().astype(np.float64), T_true)
+    res["pose_err_deg_before_after"] = [float(before[:, 0].mean()), float(after[:, 0].mean())]
+    res["pose_err_m_before_after"] = [float(before[:, 1].mean()), float(after[:, 1].mean())]
+    log(f"local BA: graph {res['graph_iters_per_s']:.0f} it/s, eager {res['eager_iters_per_s']:.0f} it/s, "
+        f"rot err {res['pose_err_deg_before_after']}, trans err {res['pose_err_m_before_after']}")
+    return res
 
 
 def run_reference(args):
@@ -434,6 +527,12 @@ def run_ours(args):
         O.build()
         cpu = cpu_baseline(O, synth, w["scene"], w["cam"], w["tcam"])
 
+    serving = ba_res = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_leg(torch, V, synth, args.serving_rates, args.serving_seconds)
+    if rank == 0 and not args.no_local_ba:
+        ba_res = local_ba_leg(torch, V, synth)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -444,7 +543,8 @@ def run_ours(args):
                 "gpu_launches": launches, "launches_per_step": launches / max(1, args.steps),
                 "cuda_graph": graph is not None, "autotune": tune, "clocks": clocks,
                 "stages_ms_per_step": {k: v[0] / K for k, v in prof.items()},
-                "p50_step_ms": statistics.median(step_ms), "p99_step_ms": sorted(step_ms)[int(0.99 * (len(step_ms) - 1))]}
+                "p50_step_ms": statistics.median(step_ms), "p99_step_ms": sorted(step_ms)[int(0.99 * (len(step_ms) - 1))],
+                "serving": serving, "local_ba": ba_res}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -462,6 +562,10 @@ def main():
     ap.add_argument("--ppt-fwd", type=int, default=0, help="override the autotuned forward pixels per thread")
     ap.add_argument("--ppt-bwd", type=int, default=0, help="override the autotuned backward pixels per thread")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serving-rates", type=float, nargs="+", default=[500.0, 2000.0])
+    ap.add_argument("--serving-seconds", type=float, default=1.5)
+    ap.add_argument("--no-local-ba", action="store_true", help="skip the local bundle-adjustment leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

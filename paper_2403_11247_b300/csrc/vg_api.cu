@@ -25,6 +25,15 @@ thread_local std::string g_err;
 namespace vgk {
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+cudaError_t allow_dynamic_smem(const void* kernel, size_t dynamic_bytes) {
+    if (dynamic_bytes == 0) return cudaSuccess;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    if (fa.sharedSizeBytes + dynamic_bytes <= 48 * 1024) return cudaSuccess;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= dynamic_bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dynamic_bytes);
+}
 vg_status set_error(vg_status s, const char* msg) {
     g_err = msg;
     return s;

@@ -40,6 +40,9 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // kernels enqueued by this library in this process (host-side count)
 void count_launches(int n);
+// Raise a kernel's dynamic shared-memory limit when its static plus dynamic
+// shared memory passes the 48 KB that launches get without opting in.
+cudaError_t allow_dynamic_smem(const void* kernel, size_t dynamic_bytes);
 // record the message returned by vg_last_error() and return s
 vg_status set_error(vg_status s, const char* msg);
 

@@ -277,10 +277,8 @@ cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& c
                               uint32_t* state, uint32_t* blk_count, cudaStream_t st) {
     const int blocks = preprocess_blocks(S.N);
     const size_t smem = codebook_smem(S);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(preprocess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = allow_dynamic_smem((const void*)preprocess_kernel, smem);
+    if (e != cudaSuccess) return e;
     count_launches(1);
     preprocess_kernel<<<(unsigned)blocks, 256, smem, st>>>(S, V, cs, xy, conic_o, rgbd, rect, ntiles, dkey, scratch,
                                                            state, blk_count);

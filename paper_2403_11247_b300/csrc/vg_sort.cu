@@ -346,10 +346,8 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, co
     if (eg > (int64_t)sms * 8) eg = (int64_t)sms * 8;
     if (eg < 1) eg = 1;
     const size_t smem = V.total_tiles <= EMIT_SMEM_TILES ? (size_t)V.total_tiles * 4 : 0;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(emit_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    e = allow_dynamic_smem((const void*)emit_pairs_kernel, smem);
+    if (e != cudaSuccess) return e;
     emit_pairs_kernel<<<(unsigned)eg, 256, smem, st>>>(sorted_slots, offsets, rect, N, V, pkeys, pvals, cap, scratch,
                                                         tile_passes);
     return cudaGetLastError();

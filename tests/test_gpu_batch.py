@@ -51,6 +51,22 @@ def test_multiview_launch_equals_single_view_launches(torch):
         grad_tolerance_check(dxi_1, dxi_b[v], f"pose {v}", rtol=1e-4, atol_frac=1e-5)
 
 
+def test_ten_view_launch_near_the_shared_memory_limit(torch):
+    """10 views of 640x480 (12,000 tiles): the pair emitter's per-tile counts
+    plus its static histograms pass 48 KB of shared memory, so the launch
+    must opt in to the larger limit; images equal single-view launches."""
+    sc = synth.tiny_scene()
+    cams = kf(n=10, w=640, h=480, f=500.0)
+    sh = V.vg_scene_upload(sc)
+    prm = V.default_params()
+    Cb, Db, Sb = [x.cpu().numpy() for x in V.render_with_retry(sh, cams, prm, V.vg_ctx_create(0))]
+    P = 640 * 480
+    for v in (0, 9):
+        C1, D1, S1 = [x.cpu().numpy() for x in V.render_with_retry(sh, [cams[v]], prm, V.vg_ctx_create(0))]
+        assert np.array_equal(C1, Cb[3 * P * v:3 * P * (v + 1)])
+        assert np.array_equal(D1, Db[P * v:P * (v + 1)]) and np.array_equal(S1, Sb[P * v:P * (v + 1)])
+
+
 def _window(torch, n=4):
     from paper_2403_11247_b300.autograd import SceneParams
     from paper_2403_11247_b300.batch import LocalBA
