@@ -15,7 +15,7 @@
 //   dL/dalpha_i = T_i w_i - B_i / (1 - alpha_i).
 //
 // Thread layout: a block is one 16x16 tile; with PPT pixels per thread a warp
-// owns a compact 16 x 2*PPT block of rows, so one test per (warp, Gaussian)
+// owns a compact rectangle of 32*PPT pixels, so one test per (warp, Gaussian)
 // against the Gaussian's alpha >= alpha_min bounding box (half extents from
 // the preprocess, widened for FP32 rounding) skips Gaussians that every
 // pixel of the warp would skip anyway; the per-pixel decisions are unchanged.
@@ -28,15 +28,37 @@ namespace vgk {
 
 constexpr int BLEND_BATCH = 256;
 
-// pixel (lx, ly) in the tile of pixel slot k of thread t for PPT pixels per thread
+// Each warp owns a rectangle of 32*PPT pixels of the tile, as square as the
+// 16x16 tile allows (8x4, 8x8, 16x8 for PPT 1, 2, 4): a square footprint
+// meets fewer Gaussians of a given size than a strip of the same area, and
+// every Gaussian the warp meets costs a cross-lane reduction in the backward.
+template <int PPT>
+struct WarpRect {
+    static constexpr int W = PPT >= 4 ? 16 : 8;       // rectangle width in pixels
+    static constexpr int H = 32 * PPT / W;            // rectangle height
+    static constexpr int PER_ROW = TILE / W;          // rectangles per tile row
+};
+
+// pixel (lx, ly) in the tile of pixel slot k of thread t
 template <int PPT>
 __device__ __forceinline__ void pixel_of(int t, int k, int& lx, int& ly) {
-    const int w = t >> 5, l = t & 31;
-    lx = l & 15;
-    ly = w * 2 * PPT + (l >> 4) + 2 * k;
+    using R = WarpRect<PPT>;
+    const int w = t >> 5, j = (t & 31) + 32 * k;
+    lx = (w % R::PER_ROW) * R::W + j % R::W;
+    ly = (w / R::PER_ROW) * R::H + j / R::W;
 }
 
-// does the box [X0, X0+15] x [Y0, Y0+2*PPT-1] meet the Gaussian's alpha box?
+// pixel bounds [X0, X1] x [Y0, Y1] of warp w's rectangle in tile (tx, ty)
+template <int PPT>
+__device__ __forceinline__ void warp_rect(int tx, int ty, int w, float& X0, float& X1, float& Y0, float& Y1) {
+    using R = WarpRect<PPT>;
+    X0 = (float)(tx * TILE + (w % R::PER_ROW) * R::W);
+    X1 = X0 + (float)(R::W - 1);
+    Y0 = (float)(ty * TILE + (w / R::PER_ROW) * R::H);
+    Y1 = Y0 + (float)(R::H - 1);
+}
+
+// does the box [X0, X1] x [Y0, Y1] meet the Gaussian's alpha box?
 __device__ __forceinline__ bool warp_hits(const float4 g, float X0, float X1, float Y0, float Y1) {
     const float cx = fminf(fmaxf(g.x, X0), X1), cy = fminf(fmaxf(g.y, Y0), Y1);
     return fabsf(g.x - cx) <= g.z && fabsf(g.y - cy) <= g.w;
@@ -59,8 +81,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     const int t = gt - vi.tile_base;
     const int tx = t % vi.tiles_x, ty = t / vi.tiles_x;
     const int warp = threadIdx.x >> 5;
-    const float X0 = (float)(tx * TILE), X1 = X0 + (float)(TILE - 1);
-    const float Y0 = (float)(ty * TILE + warp * 2 * PPT), Y1 = Y0 + (float)(2 * PPT - 1);
+    float X0, X1, Y0, Y1;
+    warp_rect<PPT>(tx, ty, warp, X0, X1, Y0, Y1);
 
     int px[PPT], py[PPT];
     float fpx[PPT], fpy[PPT];
@@ -223,8 +245,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     const int tx = t % vi.tiles_x, ty = t / vi.tiles_x;
     const int64_t HW = (int64_t)vi.W * vi.H, pb = vi.pix_base;
     const int warp = threadIdx.x >> 5;
-    const float X0 = (float)(tx * TILE), X1 = X0 + (float)(TILE - 1);
-    const float Y0 = (float)(ty * TILE + warp * 2 * PPT), Y1 = Y0 + (float)(2 * PPT - 1);
+    float X0, X1, Y0, Y1;
+    warp_rect<PPT>(tx, ty, warp, X0, X1, Y0, Y1);
 
     int px[PPT], py[PPT];
     float fpx[PPT], fpy[PPT];
