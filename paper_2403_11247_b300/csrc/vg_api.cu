@@ -176,7 +176,7 @@ struct StageProfiler {
 struct vg_ctx {
     StageProfiler prof;
     int64_t pair_cap = 0;
-    DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, Tfin, ncontrib, lookback,
+    DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, tile_order, Tfin, ncontrib, lookback,
         scratch, state, dattr, pose_part, icp_part, loss_scratch, pair_off, blk_count, blk_base, touched;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
@@ -629,6 +629,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
         VG_TRY(ctx->dval[b].ensure(slots * 4, st, "depth values"));
     }
     VG_TRY(ctx->ranges.ensure((size_t)V.total_tiles * 8, st, "ranges"));
+    VG_TRY(ctx->tile_order.ensure((size_t)V.total_tiles * 4, st, "tile order"));
     VG_TRY(ctx->scratch.ensure((size_t)(SCR_WORDS + V.total_tiles) * 4, st, "scratch"));
     VG_TRY(ctx->Tfin.ensure(pixels * 4, st, "T_final"));
     VG_TRY(ctx->ncontrib.ensure(pixels * 4, st, "n_contrib"));
@@ -689,9 +690,11 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
              })());
     const int fin = tp & 1;
     ctx->final_pair = fin;
-    VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr + SCR_TILE_COUNTS, V.total_tiles, ctx->ranges.as<uint2>(), st));
+    VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr + SCR_TILE_COUNTS, V.total_tiles, ctx->ranges.as<uint2>(),
+                                           ctx->tile_order.as<uint32_t>(), st));
     VG_STAGE(VG_STAGE_BLEND_FWD,
-             launch_blend_fwd(V, cs, params->ppt_fwd, ctx->ranges.as<uint2>(), ctx->pval[fin].as<uint32_t>(),
+             launch_blend_fwd(V, cs, params->ppt_fwd, ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
+                              ctx->pval[fin].as<uint32_t>(),
                               ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(), C, D, S,
                               ctx->Tfin.as<float>(), ctx->ncontrib.as<uint32_t>(),
                               (unsigned long long*)(state + ST_EVALS), (unsigned long long*)(state + ST_BLENDED),
@@ -745,7 +748,8 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
                                                       ctx->scratch.as<uint32_t>() + SCR_NVIS, (uint32_t)slots,
                                                       ctx->g2d.as<float>(), st));
     VG_STAGE(VG_STAGE_BLEND_BWD,
-             launch_blend_bwd(V, cs, params->ppt_bwd, ctx->ranges.as<uint2>(), ctx->pval[ctx->final_pair].as<uint32_t>(),
+             launch_blend_bwd(V, cs, params->ppt_bwd, ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
+                              ctx->pval[ctx->final_pair].as<uint32_t>(),
                               ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
                               ctx->Tfin.as<float>(), ctx->ncontrib.as<uint32_t>(), dC, dD, dS, ctx->g2d.as<float>(),
                               (unsigned long long*)(ctx->state.as<uint32_t>() + ST_BWD), params->count_evals, st));

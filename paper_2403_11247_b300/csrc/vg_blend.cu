@@ -66,7 +66,8 @@ __device__ __forceinline__ bool warp_hits(const float4 g, float X0, float X1, fl
 
 template <int PPT>
 __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
-    const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pvals,
+    const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    const uint32_t* __restrict__ pvals,
     const float4* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
     float* __restrict__ C, float* __restrict__ D, float* __restrict__ S, float* __restrict__ Tfin,
     uint32_t* __restrict__ ncontrib, unsigned long long* evals, unsigned long long* blended, int count_evals) {
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     __shared__ float4 s_co[BLEND_BATCH];
     __shared__ float4 s_cd[BLEND_BATCH];
 
-    const int gt = blockIdx.x;
+    const int gt = (int)order[blockIdx.x];  // longest tile lists first
     const int v = view_of_tile(V, gt);
     const ViewInfo& vi = V.v[v];
     const int t = gt - vi.tile_base;
@@ -225,7 +226,8 @@ __device__ __forceinline__ void warp_reduce_add10(const float v[10], float* dst)
 
 template <int PPT>
 __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
-    const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ pvals,
+    const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    const uint32_t* __restrict__ pvals,
     const float4* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
     const float* __restrict__ Tfin, const uint32_t* __restrict__ ncontrib, const float* __restrict__ dC,
     const float* __restrict__ dD, const float* __restrict__ dS, float* __restrict__ g2d,
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     __shared__ uint32_t s_slot[BLEND_BATCH];
     __shared__ uint32_t s_max;
 
-    const int gt = blockIdx.x;
+    const int gt = (int)order[blockIdx.x];  // longest tile lists first
     const int v = view_of_tile(V, gt);
     const ViewInfo& vi = V.v[v];
     const int t = gt - vi.tile_base;
@@ -368,14 +370,15 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     }
 }
 
-cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* pvals,
+cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* order,
+                             const uint32_t* pvals,
                              const float4* xy, const float4* conic_o, const float4* rgbd, float* C, float* D, float* S,
                              float* Tfin, uint32_t* ncontrib, unsigned long long* evals, unsigned long long* blended,
                              int count_evals, cudaStream_t st) {
     if (V.total_tiles <= 0) return cudaSuccess;
     count_launches(1);
 #define VG_FWD(P)                                                                                                   \
-    blend_fwd_kernel<P><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, pvals, xy, conic_o, rgbd, C, D, S, Tfin, \
+    blend_fwd_kernel<P><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, order, pvals, xy, conic_o, rgbd, C, D, S, Tfin, \
                                                                 ncontrib, evals, blended, count_evals)
     if (ppt == 4) VG_FWD(4);
     else if (ppt == 2) VG_FWD(2);
@@ -384,14 +387,15 @@ cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const ui
     return cudaGetLastError();
 }
 
-cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* pvals,
+cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* order,
+                             const uint32_t* pvals,
                              const float4* xy, const float4* conic_o, const float4* rgbd, const float* Tfin,
                              const uint32_t* ncontrib, const float* dC, const float* dD, const float* dS, float* g2d,
                              unsigned long long* bwd_pairs, int count, cudaStream_t st) {
     if (V.total_tiles <= 0) return cudaSuccess;
     count_launches(1);
 #define VG_BWD(P)                                                                                                    \
-    blend_bwd_kernel<P><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, pvals, xy, conic_o, rgbd, Tfin, ncontrib, \
+    blend_bwd_kernel<P><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, order, pvals, xy, conic_o, rgbd, Tfin, ncontrib, \
                                                                 dC, dD, dS, g2d, bwd_pairs, count)
     if (ppt == 1) VG_BWD(1);
     else if (ppt == 2) VG_BWD(2);

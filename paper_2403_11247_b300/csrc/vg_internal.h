@@ -73,15 +73,17 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, co
                              const uint32_t* state, uint32_t epoch_offset, uint32_t* err, int64_t max_slots,
                              cudaStream_t st);
 // per-tile [start, end) from the per-tile pair counts (one-block scan)
-cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, cudaStream_t st);
+cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, uint32_t* order, cudaStream_t st);
 cudaError_t launch_epoch_bump(uint32_t* state, uint32_t by, cudaStream_t st);
 
 // blend.cu
-cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* pvals,
+cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* order,
+                             const uint32_t* pvals,
                              const float4* xy, const float4* conic_o, const float4* rgbd, float* C, float* D,
                              float* S, float* Tfin, uint32_t* ncontrib, unsigned long long* evals,
                              unsigned long long* blended, int count_evals, cudaStream_t st);
-cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* pvals,
+cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* order,
+                             const uint32_t* pvals,
                              const float4* xy, const float4* conic_o, const float4* rgbd, const float* Tfin,
                              const uint32_t* ncontrib, const float* dC, const float* dD, const float* dS,
                              float* g2d, unsigned long long* bwd_pairs, int count, cudaStream_t st);

@@ -354,17 +354,36 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, co
 }
 
 // ---------------------------------------------------------------------------
-// per-tile [start, end): exclusive scan of the per-tile pair counts (one block)
+// per-tile [start, end): exclusive scan of the per-tile pair counts, and the
+// order in which the compositing kernels take the tiles: longest lists first
+// (256 buckets of list length, descending; any order within a bucket), so
+// that the long tiles start early and the short ones fill in behind them
+// instead of a cluster of long neighbouring tiles running last (one block)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) ranges_kernel(const uint32_t* __restrict__ cnt, int n, uint2* __restrict__ ranges) {
+constexpr int ORDER_BUCKETS = 256;
+
+__device__ __forceinline__ int order_bucket(uint32_t c, uint32_t cmax) {
+    // 0 for the longest lists, ORDER_BUCKETS - 1 for empty ones
+    return ORDER_BUCKETS - 1 - (int)(((uint64_t)c * (ORDER_BUCKETS - 1)) / (cmax > 0 ? cmax : 1u));
+}
+
+__global__ void __launch_bounds__(1024) ranges_kernel(const uint32_t* __restrict__ cnt, int n, uint2* __restrict__ ranges,
+                                                      uint32_t* __restrict__ order) {
     __shared__ uint32_t s_w[32];
-    __shared__ uint32_t s_carry;
+    __shared__ uint32_t s_carry, s_max;
+    __shared__ uint32_t s_bin[ORDER_BUCKETS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
+    if (threadIdx.x == 0) {
+        s_carry = 0;
+        s_max = 0;
+    }
+    for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) s_bin[i] = 0;
     __syncthreads();
+    uint32_t mymax = 0;
     for (int c0 = 0; c0 < n; c0 += 1024) {
         const int i = c0 + threadIdx.x;
         const uint32_t x = i < n ? cnt[i] : 0u;
+        mymax = max(mymax, x);
         uint32_t inc = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -389,11 +408,41 @@ __global__ void __launch_bounds__(1024) ranges_kernel(const uint32_t* __restrict
         if (threadIdx.x == 0) s_carry += s_w[31];
         __syncthreads();
     }
+    if (!order) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
+    if (lane == 0) atomicMax(&s_max, mymax);
+    __syncthreads();
+    const uint32_t cmax = s_max;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_bin[order_bucket(cnt[i], cmax)], 1u);
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the bucket sizes, 8 buckets per lane
+        uint32_t v[ORDER_BUCKETS / 32], tot = 0;
+#pragma unroll
+        for (int k = 0; k < ORDER_BUCKETS / 32; ++k) {
+            v[k] = s_bin[lane * (ORDER_BUCKETS / 32) + k];
+            tot += v[k];
+        }
+        uint32_t inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        uint32_t run = inc - tot;
+#pragma unroll
+        for (int k = 0; k < ORDER_BUCKETS / 32; ++k) {
+            s_bin[lane * (ORDER_BUCKETS / 32) + k] = run;
+            run += v[k];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) order[atomicAdd(&s_bin[order_bucket(cnt[i], cmax)], 1u)] = (uint32_t)i;
 }
 
-cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, cudaStream_t st) {
+cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, uint32_t* order, cudaStream_t st) {
     count_launches(1);
-    ranges_kernel<<<1, 1024, 0, st>>>(tile_counts, n_tiles, ranges);
+    ranges_kernel<<<1, 1024, 0, st>>>(tile_counts, n_tiles, ranges, order);
     return cudaGetLastError();
 }
 
