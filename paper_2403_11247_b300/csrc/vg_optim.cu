@@ -12,26 +12,57 @@ struct AdamPack {
     float* m[16];
     float* v[16];
     int64_t size[16];
-    int64_t block_start[17];
 };
 
+__device__ __forceinline__ void adam_update(float& p, float& m, float& v, float g, float b1, float b2, float step_size,
+                                            float inv_sqrt_bc2, float eps) {
+    m = b1 * m + (1.f - b1) * g;
+    v = b2 * v + (1.f - b2) * g * g;
+    p -= step_size * m / (sqrtf(v) * inv_sqrt_bc2 + eps);
+}
+
+// grid-stride over every tensor in turn, four elements per load where the
+// four arrays of a tensor are 16-byte aligned (the bias corrections are
+// computed once per thread, not once per element)
 __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamPack A, float lr, float b1, float b2,
                                                    float eps, const int32_t* step_dev, int32_t step_host) {
-    int t = 0;
-    while (t + 1 < A.n && (int64_t)blockIdx.x >= A.block_start[t + 1]) ++t;
     const int32_t step = step_dev ? step_dev[0] : step_host;
     const float bc1 = 1.f - powf(b1, (float)step);
     const float bc2 = 1.f - powf(b2, (float)step);
     const float step_size = lr / bc1;
     const float inv_sqrt_bc2 = rsqrtf(bc2);
-    const int64_t i = ((int64_t)blockIdx.x - A.block_start[t]) * 256 + threadIdx.x;
-    if (i >= A.size[t]) return;
-    const float g = A.g[t][i];
-    const float m = b1 * A.m[t][i] + (1.f - b1) * g;
-    const float v = b2 * A.v[t][i] + (1.f - b2) * g * g;
-    A.m[t][i] = m;
-    A.v[t][i] = v;
-    A.p[t][i] -= step_size * m / (sqrtf(v) * inv_sqrt_bc2 + eps);
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    for (int t = 0; t < A.n; ++t) {
+        float* __restrict__ P = A.p[t];
+        const float* __restrict__ G = A.g[t];
+        float* __restrict__ M = A.m[t];
+        float* __restrict__ Vv = A.v[t];
+        const int64_t n = A.size[t];
+        const bool vec = ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(G) |
+                           reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(Vv)) & 15u) == 0;
+        const int64_t n4 = vec ? n / 4 : 0;
+        for (int64_t i = tid; i < n4; i += nthr) {
+            float4 p = reinterpret_cast<float4*>(P)[i];
+            float4 m = reinterpret_cast<float4*>(M)[i];
+            float4 v = reinterpret_cast<float4*>(Vv)[i];
+            const float4 g = reinterpret_cast<const float4*>(G)[i];
+            adam_update(p.x, m.x, v.x, g.x, b1, b2, step_size, inv_sqrt_bc2, eps);
+            adam_update(p.y, m.y, v.y, g.y, b1, b2, step_size, inv_sqrt_bc2, eps);
+            adam_update(p.z, m.z, v.z, g.z, b1, b2, step_size, inv_sqrt_bc2, eps);
+            adam_update(p.w, m.w, v.w, g.w, b1, b2, step_size, inv_sqrt_bc2, eps);
+            reinterpret_cast<float4*>(P)[i] = p;
+            reinterpret_cast<float4*>(M)[i] = m;
+            reinterpret_cast<float4*>(Vv)[i] = v;
+        }
+        for (int64_t i = n4 * 4 + tid; i < n; i += nthr) {
+            float p = P[i], m = M[i], v = Vv[i];
+            adam_update(p, m, v, G[i], b1, b2, step_size, inv_sqrt_bc2, eps);
+            P[i] = p;
+            M[i] = m;
+            Vv[i] = v;
+        }
+    }
 }
 
 __global__ void step_increment_kernel(int32_t* step_dev) { step_dev[0] += 1; }
@@ -41,18 +72,18 @@ cudaError_t launch_adam(int n, float* const* p, const float* const* g, float* co
                         int32_t step_host, cudaStream_t st) {
     AdamPack A;
     A.n = n;
-    int64_t blocks = 0;
+    int64_t total = 0;
     for (int i = 0; i < n; ++i) {
         A.p[i] = p[i];
         A.g[i] = g[i];
         A.m[i] = m[i];
         A.v[i] = v[i];
         A.size[i] = size[i];
-        A.block_start[i] = blocks;
-        blocks += ceil_div(size[i], 256);
+        total += size[i];
     }
-    A.block_start[n] = blocks;
-    if (blocks > 0) {
+    if (total > 0) {
+        int64_t blocks = ceil_div(ceil_div(total, 4), 256);
+        if (blocks > 148 * 4) blocks = 148 * 4;
         count_launches(1);
         adam_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, lr, b1, b2, eps, step_dev, step_host);
         cudaError_t e = cudaGetLastError();
