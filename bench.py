@@ -232,7 +232,7 @@ def serving_leg(torch, V, synth, rates, seconds, p_track=0.3):
     render and pose-track requests of 320x240 to 1920x1080."""
     from paper_2403_11247_b300 import serve
     scenes = {i: V.vg_scene_upload(synth.serving_scene(n, 2000 + i)) for i, n in enumerate(SERVING_SCENES)}
-    wl = serve.RoomWorkload(scenes, SERVING_SIZES)
+    wl = serve.ServingWorkload(scenes, SERVING_SIZES)
     batched = serve.Server(scenes, n_streams=4, max_views=16)
     serial = serve.Server(scenes, n_streams=1, max_views=1)
     # size every workspace and the pinned-memory cache on traces of their own
@@ -263,33 +263,37 @@ def serving_leg(torch, V, synth, rates, seconds, p_track=0.3):
 
 
 def local_ba_leg(torch, V, synth, iters=50):
-    """Sliding-window local BA on the mapping room: 8 keyframes of 640x480
-    with perturbed poses, one multi-view launch sequence per iteration,
-    `iters` iterations captured in one CUDA graph, against the same
-    iterations launched one by one."""
+    """Pose tracking + sliding-window local BA on the tiny scene: 8
+    keyframes of 640x480 on an arc, poses perturbed by up to 2 deg / 5 cm,
+    targets rendered at the unperturbed poses; one multi-view launch
+    sequence per iteration (forward, loss gradient, backward, pose
+    gradients, Adam on the 8 pose twists and on the map), `iters`
+    iterations captured in one CUDA graph, against the same iterations
+    launched one by one."""
     from paper_2403_11247_b300.autograd import SceneParams
     from paper_2403_11247_b300.autotune import autotune_ppt
     from paper_2403_11247_b300.batch import LocalBA, pose_errors
-    sc = synth.room_scene()
-    scene = SceneParams.from_synth(sc, requires_grad=False)
+    scene = SceneParams.from_synth(synth.tiny_scene(), requires_grad=False)
     sh = scene.handle()
-    truth = [synth.room_camera(640, 480, 500.0, pose_seed=300 + i, jitter_deg=3.0, jitter_m=0.1) for i in range(8)]
-    rng = np.random.default_rng(1003)
-    pert = [synth.camera(c.fx, c.fy, c.cx, c.cy, c.width, c.height, synth.perturb_pose(c.T_cw, rng, 2.0, 0.05), c.near)
-            for c in truth]
+    truth = synth.keyframe_cameras(n_views=8, width=640, height=480, f=500.0, perturbed=False)
+    pert = synth.keyframe_cameras(n_views=8, width=640, height=480, f=500.0, perturbed=True)
     ctx = V.vg_ctx_create(0)
     Ct, Dt, _ = V.render_with_retry(sh, truth, V.default_params(), ctx)
-    ba = LocalBA(scene, pert, Ct.clone(), Dt.clone(), lr_rot=1e-3, lr_trans=1e-3)
+    ba = LocalBA(scene, pert, Ct.clone(), Dt.clone(), lr_rot=2e-3, lr_trans=2e-3, lr_map=1e-4)
     tune = autotune_ppt(sh, ba.cams, ba.ctx, ba.dC, ba.dD, None, ba.grads, reps=3, pose_dev=ba.pose)
     ba.params = V.default_params(pose_dev=ba.pose, ppt_fwd=tune["ppt_fwd"], ppt_bwd=tune["ppt_bwd"])
     T_true = np.stack([np.asarray(c.T_cw, np.float64) for c in truth])
     pose0 = ba.pose.clone()
+    map0 = [p.clone() for p in ba.map_params]
     ba.capture(iters)
-    res = {"keyframes": 8, "size": "640x480", "iters_per_graph": iters, "autotune": tune}
+    res = {"scene": "tiny (2,000 Gaussians)", "keyframes": 8, "size": "640x480", "iters_per_graph": iters,
+           "autotune": tune}
     for name in ("graph", "eager"):
         times = []
         for _ in range(3):
             ba.pose.copy_(pose0)
+            for p, p0 in zip(ba.map_params, map0):
+                p.copy_(p0)
             ba.reset_optimiser()
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -303,7 +307,7 @@ def local_ba_leg(torch, V, synth, iters=50):
             times.append(a.elapsed_time(b))
         if ba.check() != V.VG_OK:
             raise RuntimeError("local BA: device status not OK")
-        res[f"{name}_iters_per_s"] = iters / (min(times) / 1000.0)
+        res[f"{name}_iters_per_s"] = iters / (statistics.median(times) / 1000.0)
     before = pose_errors(pose0.cpu().numpy().astype(np.float64), T_true)
     after = pose_errors(ba.pose.cpu().numpy().astype(np.float64), T_true)
     res["pose_err_deg_before_after"] = [float(before[:, 0].mean()), float(after[:, 0].mean())]
@@ -503,27 +507,77 @@ def run_ours(args):
                            % (n_sm, sm_mhz, src)) if roof["bound"] == "alu" else f"{src} hbm_gbs"
     roof["ms_per_launch"] = per_launch_s * 1000.0
 
-    # end to end through the public API: the target frame goes up from pinned
-    # host memory each step, the loss and the pose gradient come back
+    # the same step as plain launches (no graph), same L2 flush between steps
+    eager = None
+    if graph is not None:
+        V.vg_ctx_profile(w["ctx"], False)
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(min(args.steps, 100))]
+        for i, (a, b_) in enumerate(ev2):
+            flush.fill_(float(i))
+            a.record(stream)
+            step()
+            b_.record(stream)
+        torch.cuda.synchronize()
+        if V.vg_check(w["ctx"]) != V.VG_OK:
+            raise RuntimeError("device status not OK in the plain-launch steps")
+        eager_ms = [a.elapsed_time(b_) for a, b_ in ev2]
+        eager = {"iters_per_s": world * len(eager_ms) / (sum(eager_ms) / 1000.0),
+                 "p50_step_ms": statistics.median(eager_ms), "steps": len(eager_ms)}
+
+    # end to end through the public API: every step's target frame goes up
+    # from pinned host memory and its loss and pose gradient come back.  The
+    # upload of step i+1 runs on a copy stream while step i computes, into
+    # the other of two target buffers (one captured step per buffer).
     e2e = None
     if True:
         b = w["bufs"]
         Ct_h = b["Ct"].cpu().pin_memory()
         Dt_h = b["Dt"].cpu().pin_memory()
-        out_h = torch.empty(7, dtype=torch.float32).pin_memory()
         n_e2e = max(3, min(args.steps, 200))
+        out_h = torch.empty((n_e2e, 7), dtype=torch.float32).pin_memory()
+        bufs2 = dict(b, Ct=torch.empty_like(b["Ct"]), Dt=torch.empty_like(b["Dt"]))
+        step2 = make_step(V, dict(w, bufs=bufs2))
+        if graph is not None:
+            g2 = torch.cuda.CUDAGraph()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g2, capture_error_mode="thread_local"):
+                step2()
+            runs = [graph.replay, g2.replay]
+        else:
+            runs = [step, step2]
+        tgts = [(b["Ct"], b["Dt"]), (bufs2["Ct"], bufs2["Dt"])]
+        copy_stream = torch.cuda.Stream()
+        ready = [torch.cuda.Event(), torch.cuda.Event()]
+        free = [torch.cuda.Event(), torch.cuda.Event()]
         torch.cuda.synchronize()
+        for e in free:
+            e.record(stream)
         t0 = time.perf_counter()
-        for _ in range(n_e2e):
-            b["Ct"].copy_(Ct_h, non_blocking=True)
-            b["Dt"].copy_(Dt_h, non_blocking=True)
-            run()
-            out_h[0:1].copy_(b["loss"], non_blocking=True)
-            out_h[1:7].copy_(b["dxi"].view(-1), non_blocking=True)
-            torch.cuda.current_stream().synchronize()
+        with torch.cuda.stream(copy_stream):
+            tgts[0][0].copy_(Ct_h, non_blocking=True)
+            tgts[0][1].copy_(Dt_h, non_blocking=True)
+            ready[0].record(copy_stream)
+        for i in range(n_e2e):
+            j = i & 1
+            if i + 1 < n_e2e:
+                copy_stream.wait_event(free[1 - j])
+                with torch.cuda.stream(copy_stream):
+                    tgts[1 - j][0].copy_(Ct_h, non_blocking=True)
+                    tgts[1 - j][1].copy_(Dt_h, non_blocking=True)
+                    ready[1 - j].record(copy_stream)
+            stream.wait_event(ready[j])
+            runs[j]()
+            free[j].record(stream)
+            out_h[i, 0:1].copy_(b["loss"], non_blocking=True)
+            out_h[i, 1:7].copy_(b["dxi"].view(-1), non_blocking=True)
+        stream.synchronize()
         dt = time.perf_counter() - t0
+        if V.vg_check(w["ctx"]) != V.VG_OK or not bool(torch.isfinite(out_h).all()):
+            raise RuntimeError("end-to-end steps: device status not OK or non-finite results")
         e2e = {"value": world * n_e2e / dt, "unit": "iters/s", "h2d_bytes_per_step": Ct_h.numel() * 4 + Dt_h.numel() * 4,
-               "d2h_bytes_per_step": 7 * 4, "steps": n_e2e}
+               "d2h_bytes_per_step": 7 * 4, "steps": n_e2e,
+               "pipelining": "upload of step i+1 overlaps step i (two target buffers, copy stream)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -547,7 +601,9 @@ def run_ours(args):
                 "gpu_launches": launches, "launches_per_step": launches / max(1, args.steps),
                 "cuda_graph": graph is not None, "autotune": tune, "clocks": clocks,
                 "stages_ms_per_step": {k: v[0] / K for k, v in prof.items()},
-                "p50_step_ms": statistics.median(step_ms), "p99_step_ms": sorted(step_ms)[int(0.99 * (len(step_ms) - 1))],
+                "p50_step_ms": statistics.median(step_ms), "p10_step_ms": float(np.percentile(step_ms, 10)),
+                "p90_step_ms": float(np.percentile(step_ms, 90)), "p99_step_ms": float(np.percentile(step_ms, 99)),
+                "plain_launches": eager,
                 "serving": serving, "local_ba": ba_res}
         print(json.dumps(line), flush=True)
     if dist:
@@ -567,8 +623,8 @@ def main():
     ap.add_argument("--ppt-bwd", type=int, default=0, help="override the autotuned backward pixels per thread")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
-    ap.add_argument("--serving-rates", type=float, nargs="+", default=[500.0, 2000.0])
-    ap.add_argument("--serving-seconds", type=float, default=1.5)
+    ap.add_argument("--serving-rates", type=float, nargs="+", default=[200.0, 500.0, 1000.0, 2000.0])
+    ap.add_argument("--serving-seconds", type=float, default=2.0, help="length of each Poisson trace")
     ap.add_argument("--no-local-ba", action="store_true", help="skip the local bundle-adjustment leg")
     args = ap.parse_args()
     if args.impl == "reference":

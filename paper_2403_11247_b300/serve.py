@@ -68,34 +68,35 @@ def poisson_trace(rng: np.random.Generator, rate: float, duration: float, scenes
     return out
 
 
-class RoomWorkload:
-    """Requests against room scenes: render requests from cameras jittered
-    around the mapping camera; track requests carry the RGB-D frame rendered
-    (once per scene and size, before serving) from a reference pose and ask
-    for the pose gradient at a pose perturbed from it by up to 1 deg / 2 cm."""
+class ServingWorkload:
+    """Requests against resident scenes: render requests from cameras moved
+    at random (up to 2 deg / 5 cm) from the reference camera; track requests
+    carry the RGB-D frame rendered (once per scene and size, before serving)
+    at the reference camera and ask for the pose gradient at a pose
+    perturbed from it by up to 1 deg / 2 cm."""
 
-    def __init__(self, scenes: Dict[int, "V.SceneHandle"], sizes: Sequence[tuple], params=None, seed: int = 1004):
+    def __init__(self, scenes: Dict[int, "V.SceneHandle"], sizes: Sequence[tuple], params=None):
         self.scenes, self.sizes = scenes, list(sizes)
         self.targets = {}
         params = params if params is not None else V.default_params()
         ctx = V.vg_ctx_create(0)
-        for j, sid in enumerate(sorted(scenes)):
+        for sid in sorted(scenes):
             for w, h in self.sizes:
-                truth = synth.serving_camera(w, h, pose_seed=seed + 7 * j)
-                C_, D, _ = V.render_with_retry(scenes[sid], [truth], params, ctx)
+                ref = synth.serving_camera(w, h)
+                C_, D, _ = V.render_with_retry(scenes[sid], [ref], params, ctx)
                 Ct = torch.empty(C_.numel(), dtype=torch.float32, pin_memory=True)
                 Dt = torch.empty(D.numel(), dtype=torch.float32, pin_memory=True)
                 Ct.copy_(C_)
                 Dt.copy_(D)
-                self.targets[(sid, w, h)] = (truth, Ct, Dt)
+                self.targets[(sid, w, h)] = (ref, Ct, Dt)
         torch.cuda.synchronize()
 
     def request(self, kind, sid, w, h, rng):
         if kind == "render":
             return synth.serving_camera(w, h, pose_seed=int(rng.integers(1 << 30))), None
-        truth, Ct, Dt = self.targets[(sid, w, h)]
-        T = synth.perturb_pose(truth.T_cw, rng, 1.0, 0.02)
-        return synth.camera(truth.fx, truth.fy, truth.cx, truth.cy, w, h, T, truth.near), (Ct, Dt)
+        ref, Ct, Dt = self.targets[(sid, w, h)]
+        T = synth.perturb_pose(ref.T_cw, rng, 1.0, 0.02)
+        return synth.camera(ref.fx, ref.fy, ref.cx, ref.cy, w, h, T, ref.near), (Ct, Dt)
 
     def trace(self, seed: int, rate: float, duration: float, p_track: float = 0.3) -> List[Request]:
         return poisson_trace(np.random.default_rng(seed), rate, duration, sorted(self.scenes), self.sizes,

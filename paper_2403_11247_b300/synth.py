@@ -383,16 +383,24 @@ def large_cameras(n_views: int = 4, width: int = 1920, height: int = 1080, f: fl
 
 
 def serving_scene(n: int, seed: int) -> Scene:
-    """Serving scenes: the mapping-room recipe (room_scene) with n/8 anchors
-    of k = 8 Gaussians each, so n Gaussians in the same room."""
-    return room_scene(seed=seed, n_anchors=max(1, n // 8))
+    """Serving scenes: the tiny-scene recipe (coded attributes, 3 x 64
+    codewords) scaled to ``n`` Gaussians, the box half-width growing as
+    n^(1/3) so that the density stays that of the tiny scene."""
+    a = (n / 2000.0) ** (1.0 / 3.0)
+    return box_scene(seed, n, half_width=a, z_lo=1.0, z_hi=1.0 + 3.0 * a, coded=True, L=3, K=64)
 
 
-def serving_camera(width: int, height: int, pose_seed: int) -> Camera:
-    """A request camera in the mapping room: focal length width/2 (the
-    mapping camera's 600 px at 1200 wide), pose jittered by up to 5 deg and
-    0.15 m around the mapping camera."""
-    return room_camera(width, height, 0.5 * width, pose_seed=pose_seed, jitter_deg=5.0, jitter_m=0.15)
+def serving_camera(width: int, height: int, pose_seed: Optional[int] = None, max_deg: float = 2.0,
+                   max_trans: float = 0.05) -> Camera:
+    """A request camera: the tiny camera's field of view (fx = 50 per 64
+    pixels of width) at ``width`` x ``height``, at the origin looking down +z,
+    optionally moved by a random rigid motion (rotation up to ``max_deg``,
+    translation up to ``max_trans`` m)."""
+    f = 50.0 * width / 64.0
+    T = identity_pose()
+    if pose_seed is not None:
+        T = perturb_pose(T, np.random.default_rng(pose_seed), max_deg, max_trans)
+    return camera(f, f, (width - 1) / 2.0, (height - 1) / 2.0, width, height, T)
 
 
 def upstream_grads(seed: int, n_pixels_total: int, scale: float = 1.0):

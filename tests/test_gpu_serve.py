@@ -25,10 +25,10 @@ def torch():
 
 @pytest.fixture(scope="module")
 def workload(torch):
-    from paper_2403_11247_b300.serve import RoomWorkload
+    from paper_2403_11247_b300.serve import ServingWorkload
     scenes = {0: V.vg_scene_upload(synth.serving_scene(16000, 2001)),
               1: V.vg_scene_upload(synth.serving_scene(48000, 2002))}
-    return RoomWorkload(scenes, [(160, 120), (320, 240), (256, 144)])
+    return ServingWorkload(scenes, [(160, 120), (320, 240), (256, 144)])
 
 
 def test_each_result_is_the_same_alone_and_in_the_mix(workload):
