@@ -42,6 +42,27 @@ FWD_FLOP_EVAL = 14        # offset, quadratic form, exp argument, opacity produc
 FWD_FLOP_BLEND = 12       # transmittance update, 4 FMA accumulations, silhouette
 BWD_FLOP_WALK = 14        # per walked pair: offset, quadratic form, exp argument, opacity product
 BWD_FLOP_BLEND = 49       # per blended pair: T recovery, dL/dalpha, colour/depth/opacity/conic/mean partials
+# DRAM bytes (read + write) per launch of the compositing kernels from one ncu
+# capture of this workload (profiles/step_kernels__mapping_1200x680.md), valid
+# while the kernels' sources hash to the value they had when captured
+BLEND_SOURCES = ("paper_2403_11247_b300/csrc/vg_blend.cu", "paper_2403_11247_b300/csrc/vg_common.cuh",
+                 "paper_2403_11247_b300/csrc/vg_internal.h")
+NCU_TRAFFIC = {"blend_bwd": ("5844dd311c2d43fd", 24.431872e6 + 0.0),
+               "blend_fwd": ("5844dd311c2d43fd", 3.941888e6 + 6.144e3)}
+
+
+def ncu_traffic(stage: str):
+    """Per-launch DRAM traffic of `stage` from the recorded capture, or None
+    if the kernel sources changed since."""
+    import hashlib
+    if stage not in NCU_TRAFFIC:
+        return None
+    h = hashlib.sha256()
+    for f in BLEND_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    sha, nbytes = NCU_TRAFFIC[stage]
+    return nbytes if h.hexdigest()[:16] == sha else None
 
 
 def log(*a):
@@ -189,37 +210,53 @@ def make_step(V, w):
 # the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
 
-def oracle_iteration(O, synth, scene, cam, tcam, threads, band_rows=None):
-    """One oracle fwd+bwd iteration (target render, forward, L1 loss,
-    backward) on a horizontal band of the image (full image if None);
-    returns the fraction of the image it covered."""
-    import numpy as np
+def oracle_band(O, synth, scene, cam, tcam, band_rows=None):
+    """The cameras of a horizontal band of the image (full image if None),
+    the band's target frame (rendered once, outside any timing) and the
+    fraction of the image the band covers."""
     if band_rows is not None and band_rows < cam.height:
         y0 = (cam.height - band_rows) // 2
         band = lambda c: synth.camera(c.fx, c.fy, c.cx, c.cy - y0, c.width, band_rows, c.T_cw, c.near)
         cam, tcam = band(cam), band(tcam)
-    t = O.Oracle(scene, [tcam]).forward(threads=threads)
+    t = O.Oracle(scene, [tcam]).forward(threads=os.cpu_count() or 1)
+    return cam, t, cam.height / float(H_IMG)
+
+
+def oracle_iteration(O, scene, cam, target, threads):
+    """One oracle iteration of the step: decode + project + bin, forward,
+    L1 loss gradient against the target frame, backward."""
+    import numpy as np
     o = O.Oracle(scene, [cam])
     f = o.forward(threads=threads)
-    _, dC, dD = O.loss_l1(f["C"], f["D"], f["S"], t["C"], t["D"], 0.5)
+    _, dC, dD = O.loss_l1(f["C"], f["D"], f["S"], target["C"], target["D"], 0.5)
     o.backward(dC, dD, np.zeros_like(f["S"]), threads=threads)
-    return cam.height / float(H_IMG)
 
 
-def cpu_baseline(O, synth, scene, cam, tcam, budget_s=15.0):
-    threads = os.cpu_count() or 1
+def time_oracle(O, scene, cam, target, frac, threads, budget_s):
     t0 = time.perf_counter()
-    frac = oracle_iteration(O, synth, scene, cam, tcam, threads, band_rows=H_IMG // 8)
+    oracle_iteration(O, scene, cam, target, threads)
     first = time.perf_counter() - t0
-    iters, work = 1, frac
+    iters = 1
     while time.perf_counter() - t0 + first < budget_s:
-        work += oracle_iteration(O, synth, scene, cam, tcam, threads, band_rows=H_IMG // 8)
+        oracle_iteration(O, scene, cam, target, threads)
         iters += 1
     dt = time.perf_counter() - t0
-    return {"value": work / dt, "unit": "iters/s", "cores": threads, "kind": "oracle",
-            "sample": f"{iters} oracle fwd+bwd iterations on a {H_IMG // 8}-row band (1/8) of the 1200x680 image "
-                      f"(full 320k-Gaussian scene decoded and binned each time), scaled to full images; "
-                      f"{dt:.1f} s on {threads} OpenMP threads"}
+    return iters * frac / dt, iters, dt
+
+
+def cpu_baseline(O, synth, scene, cam, tcam, budget_s=12.0, single_budget_s=6.0):
+    """The oracle on the host cores, whole 1200x680 images: all cores
+    (OpenMP over pixel rows) for ~budget_s, then one thread for at least one
+    iteration."""
+    threads = os.cpu_count() or 1
+    bcam, target, frac = oracle_band(O, synth, scene, cam, tcam)
+    value, iters, dt = time_oracle(O, scene, bcam, target, frac, threads, budget_s)
+    v1, it1, dt1 = time_oracle(O, scene, bcam, target, frac, 1, single_budget_s)
+    return {"value": value, "unit": "iters/s", "cores": threads, "kind": "oracle",
+            "sample": f"{iters} oracle iterations (decode, project, bin, forward, L1 loss gradient, backward) "
+                      f"of the whole 1200x680 image and 320k-Gaussian scene, {dt:.1f} s on {threads} OpenMP "
+                      f"threads",
+            "single_thread": {"value": v1, "cores": 1, "sample": f"{it1} whole-image iterations, {dt1:.1f} s"}}
 
 
 SERVING_SCENES = (50000, 300000, 1000000, 2000000)
@@ -329,26 +366,28 @@ def run_reference(args):
     tcam = synth.room_camera(pose_seed=7, jitter_deg=1.0, jitter_m=0.02)
     threads = os.cpu_count() or 1
     # size the per-step band so that warmup + steps end within ~3 minutes
+    bcam, target, frac = oracle_band(O, synth, scene, cam, tcam, band_rows=H_IMG // 8)
     t0 = time.perf_counter()
-    oracle_iteration(O, synth, scene, cam, tcam, threads, band_rows=H_IMG // 8)
+    oracle_iteration(O, scene, bcam, target, threads)
     per_band = time.perf_counter() - t0
     total = max(1, args.steps + args.warmup)
     rows = int(min(H_IMG, max(16, H_IMG // 8 * (150.0 / (total * per_band)))))
+    bcam, target, frac = oracle_band(O, synth, scene, cam, tcam, band_rows=rows)
     for _ in range(args.warmup):
-        oracle_iteration(O, synth, scene, cam, tcam, threads, band_rows=rows)
-    work = 0.0
+        oracle_iteration(O, scene, bcam, target, threads)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        work += oracle_iteration(O, synth, scene, cam, tcam, threads, band_rows=rows)
+        oracle_iteration(O, scene, bcam, target, threads)
     dt = time.perf_counter() - t0
-    value = work / dt
+    value = args.steps * frac / dt
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / max(1, args.steps),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "sample_rows": rows},
            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": threads, "kind": "oracle",
-                            "sample": f"each step: one oracle fwd+bwd on a {rows}-row band of the 1200x680 image, "
-                                      f"scaled to full images"},
+                            "sample": f"each step: one oracle iteration (decode, project, bin, forward, L1 loss "
+                                      f"gradient, backward) on a {rows}-row band of the 1200x680 image, scaled to "
+                                      f"full images"},
            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
@@ -489,13 +528,13 @@ def run_ours(args):
         walked, blended = stats["bwd_pairs"] / K, stats["blended"] / K
         flops = BWD_FLOP_WALK * walked + BWD_FLOP_BLEND * blended
         roof = {"bound": "alu", "achieved": flops / per_launch_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                "traffic": None, "kernel": "blend_bwd_kernel",
+                "traffic": ncu_traffic("blend_bwd"), "kernel": "blend_bwd_kernel",
                 "work": f"{walked:.4g} walked + {blended:.4g} blended pairs per launch"}
     elif dom == "blend_fwd":
         ev, blended = stats["evaluated"] / K, stats["blended"] / K
         flops = FWD_FLOP_EVAL * ev + FWD_FLOP_BLEND * blended
         roof = {"bound": "alu", "achieved": flops / per_launch_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                "traffic": None, "kernel": "blend_fwd_kernel",
+                "traffic": ncu_traffic("blend_fwd"), "kernel": "blend_fwd_kernel",
                 "work": f"{ev:.4g} evaluated + {blended:.4g} blended pairs per launch"}
     else:
         n = 320000
@@ -614,8 +653,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the step's kernels one by one")
