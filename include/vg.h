@@ -207,7 +207,10 @@ vg_status vg_ctx_reset_counters(vg_ctx* ctx, vg_stream stream);
  * ms_total[s] (sum of event-to-event durations) and launches[s].  Calls made
  * during stream capture record their events as external event nodes of the
  * graph; those records persist (until the ctx is freed) and report the most
- * recent replay of the graph. */
+ * recent replay of the graph.  VG_STAGE_CHAIN includes the codebook
+ * gradients (accumulated in the same pass); VG_STAGE_CODEBOOK records
+ * nothing and is kept for the numbering.  VG_STAGE_MEMSET covers the zeroing
+ * before the backward. */
 enum {
     VG_STAGE_PREPROCESS = 0, VG_STAGE_DEPTH_SORT, VG_STAGE_DUPLICATE, VG_STAGE_TILE_SORT, VG_STAGE_RANGES,
     VG_STAGE_BLEND_FWD, VG_STAGE_LOSS, VG_STAGE_BLEND_BWD, VG_STAGE_CHAIN, VG_STAGE_CODEBOOK, VG_STAGE_POSE,

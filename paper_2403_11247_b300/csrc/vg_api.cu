@@ -129,7 +129,6 @@ struct vg_scene {
     SceneDev dev{};
     bool owned = false;
     std::vector<void*> owned_ptrs;
-    DevBuf perm[4], seg[4];
     ~vg_scene() {
         for (void* p : owned_ptrs) cudaFree(p);
     }
@@ -177,7 +176,7 @@ struct vg_ctx {
     StageProfiler prof;
     int64_t pair_cap = 0;
     DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, tile_order, Tfin, ncontrib, lookback,
-        scratch, state, dattr, pose_part, icp_part, loss_scratch, pair_off, blk_count, blk_base, touched;
+        scratch, state, pose_part, icp_part, loss_scratch, pair_off, blk_count, blk_base, vis;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
     bool g2d_clean = false;
@@ -330,42 +329,7 @@ vg_status vg_scene_upload(const vg_scene_desc* d, int32_t flags, vg_stream strea
         }
     }
 
-    // per-stage codeword -> Gaussian lists for the codebook-gradient reduction:
-    // one stable 8-bit radix pass of Gaussian ids keyed by their index byte
-    bool any_coded = false;
-    for (int gi = 0; gi < 4; ++gi) any_coded |= (S.L[gi] > 0 && N > 0);
-    if (any_coded) {
-        DevBuf keys, keys_out, hist, lb, state;
-        const int64_t parts = ceil_div(N, SORT_TILE);
-        VG_TRY(fin(keys.ensure((size_t)N * 4, st, "keys")));
-        VG_TRY(fin(keys_out.ensure((size_t)N * 4, st, "keys_out")));
-        VG_TRY(fin(hist.ensure(256 * 4 * 2, st, "hist")));
-        VG_TRY(fin(lb.ensure((size_t)parts * 256 * 8, st, "lookback")));
-        VG_TRY(fin(state.ensure(ST_WORDS * 4, st, "state")));
-        VG_CUDA(cudaMemsetAsync(lb.p, 0, lb.bytes, st));
-        VG_CUDA(cudaMemsetAsync(state.p, 0, state.bytes, st));
-        uint32_t epoch_off = 1;
-        for (int gi = 0; gi < 4; ++gi) {
-            if (S.L[gi] <= 0) continue;
-            const int L = S.L[gi], K = S.K[gi];
-            VG_TRY(fin(sc->perm[gi].ensure((size_t)L * N * 4, st, "perm")));
-            VG_TRY(fin(sc->seg[gi].ensure((size_t)L * (K + 1) * 4, st, "seg")));
-            for (int s = 0; s < L; ++s) {
-                uint32_t* h = hist.as<uint32_t>();
-                VG_CUDA(cudaMemsetAsync(h, 0, 256 * 4 * 2, st));
-                VG_CUDA(launch_idx_to_keys(S.idx[gi] + (int64_t)s * N, N, keys.as<uint32_t>(), st));
-                VG_CUDA(launch_hist(keys.as<uint32_t>(), N, 1, h, st));
-                VG_CUDA(launch_sort_pass(keys.as<uint32_t>(), nullptr, keys_out.as<uint32_t>(),
-                                         sc->perm[gi].as<uint32_t>() + (int64_t)s * N, nullptr, (uint32_t)N, 0, h,
-                                         lb.as<unsigned long long>(), h + 256, state.as<uint32_t>(), epoch_off++,
-                                         state.as<uint32_t>() + ST_ERR, sort_pass_grid((uint32_t)N), st));
-                VG_CUDA(launch_seg_from_hist(h, K, sc->seg[gi].as<uint32_t>() + (int64_t)s * (K + 1), st));
-            }
-        }
-        VG_CUDA(cudaStreamSynchronize(st));
-    } else {
-        VG_CUDA(cudaStreamSynchronize(st));
-    }
+    VG_CUDA(cudaStreamSynchronize(st));
     *out = sc;
     return VG_OK;
 }
@@ -628,6 +592,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
         VG_TRY(ctx->dkey[b].ensure(slots * 4, st, "depth keys"));
         VG_TRY(ctx->dval[b].ensure(slots * 4, st, "depth values"));
     }
+    VG_TRY(ctx->vis.ensure(slots * 4, st, "visible slots"));
     VG_TRY(ctx->ranges.ensure((size_t)V.total_tiles * 8, st, "ranges"));
     VG_TRY(ctx->tile_order.ensure((size_t)V.total_tiles * 4, st, "tile order"));
     VG_TRY(ctx->scratch.ensure((size_t)(SCR_WORDS + V.total_tiles) * 4, st, "scratch"));
@@ -657,7 +622,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     VG_STAGE(VG_STAGE_DEPTH_SORT, ([&]() -> cudaError_t {
                  cudaError_t e = launch_compact(V, N, ctx->dkey[1].as<uint32_t>(), ctx->blk_count.as<uint32_t>(),
                                                 ctx->blk_base.as<uint32_t>(), ctx->dkey[0].as<uint32_t>(),
-                                                ctx->dval[0].as<uint32_t>(), st);
+                                                ctx->dval[0].as<uint32_t>(), ctx->vis.as<uint32_t>(), st);
                  if (e != cudaSuccess) return e;
                  for (int p = 0; p < 4; ++p) {
                      const int i = p & 1, o = i ^ 1;
@@ -732,11 +697,38 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
 
     const int nb = chain_blocks(N);
     VG_TRY(ctx->pose_part.ensure((size_t)n_views * nb * 6 * 4, st, "pose partials"));
-    bool need_attr = false;
     float* gptr[4] = {grads->logscale, grads->rot, grads->opacity, grads->rgb};
-    for (int gi = 0; gi < 4; ++gi) need_attr |= (sd.L[gi] > 0 && gptr[gi]);
-    if (need_attr) VG_TRY(ctx->dattr.ensure(N * ATTR_STRIDE * 4, st, "attribute grads"));
-    VG_TRY(ctx->touched.ensure((size_t)ceil_div(N, 32) * 4 + 1024, st, "touched mask"));
+
+    // the scene-gradient arrays the chain accumulates into, zeroed together
+    // with the visible slots' gradient rows before the backward compositing
+    ChainOut O;
+    std::memset(&O, 0, sizeof(O));
+    ZeroList Z;
+    std::memset(&Z, 0, sizeof(Z));
+    auto zero = [&Z](float* p, int64_t count) {
+        if (p && count > 0) {
+            Z.p[Z.n] = p;
+            Z.count[Z.n++] = count;
+        }
+    };
+    for (int gi = 0; gi < 4; ++gi) {
+        if (sd.L[gi] > 0) {
+            O.cb[gi] = gptr[gi];
+            zero(gptr[gi], (int64_t)sd.L[gi] * sd.K[gi] * GDIMS[gi]);
+        } else {
+            O.raw[gi] = gptr[gi];
+            zero(gptr[gi], N * GDIMS[gi]);
+        }
+    }
+    O.d_xyz = grads->anchor_xyz;
+    O.d_l = grads->anchor_l;
+    O.d_off = grads->offsets;
+    O.d_mask = sd.mask ? grads->mask_logit : nullptr;
+    O.pose_part = ctx->pose_part.as<float>();
+    zero(grads->anchor_xyz, sd.n_anchors * 3);
+    zero(grads->anchor_l, sd.n_anchors * 3);
+    zero(grads->offsets, N * 3);
+    zero(grads->mask_logit, N);
 
     const bool prof_graph = capturing(st);
     const bool prof_on = ctx->prof.on;
@@ -744,51 +736,17 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
         VG_CUDA(cudaMemsetAsync(ctx->g2d.p, 0, ctx->g2d.bytes, st));
         ctx->g2d_clean = true;
     }
-    VG_STAGE(VG_STAGE_MEMSET, launch_zero_visible_g2d(ctx->dval[0].as<uint32_t>(),
-                                                      ctx->scratch.as<uint32_t>() + SCR_NVIS, (uint32_t)slots,
-                                                      ctx->g2d.as<float>(), st));
+    VG_STAGE(VG_STAGE_MEMSET, launch_zero_bwd(ctx->vis.as<uint32_t>(), ctx->scratch.as<uint32_t>() + SCR_NVIS,
+                                              (uint32_t)slots, ctx->g2d.as<float>(), Z, st));
     VG_STAGE(VG_STAGE_BLEND_BWD,
              launch_blend_bwd(V, cs, params->ppt_bwd, ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
                               ctx->pval[ctx->final_pair].as<uint32_t>(),
                               ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
                               ctx->Tfin.as<float>(), ctx->ncontrib.as<uint32_t>(), dC, dD, dS, ctx->g2d.as<float>(),
                               (unsigned long long*)(ctx->state.as<uint32_t>() + ST_BWD), params->count_evals, st));
-    if ((32 % sd.k) != 0) {
-        if (grads->anchor_xyz) VG_CUDA(cudaMemsetAsync(grads->anchor_xyz, 0, sd.n_anchors * 12, st));
-        if (grads->anchor_l) VG_CUDA(cudaMemsetAsync(grads->anchor_l, 0, sd.n_anchors * 12, st));
-    }
-    float* raws[4];
-    for (int gi = 0; gi < 4; ++gi) raws[gi] = sd.L[gi] > 0 ? nullptr : gptr[gi];
-    if (N > 0) {
-        VG_STAGE(VG_STAGE_CHAIN,
-                 launch_chain(sd, V, cs, ctx->g2d.as<float>(), need_attr ? ctx->dattr.as<float>() : nullptr, raws[0],
-                              raws[1], raws[2], raws[3], grads->anchor_xyz, grads->anchor_l, grads->offsets,
-                              grads->mask_logit, ctx->pose_part.as<float>(), ctx->touched.as<uint32_t>(),
-                              ctx->ntiles.as<uint32_t>(), &ctx->pose_blocks, st));
-    } else {
-        VG_CUDA(cudaMemsetAsync(ctx->pose_part.p, 0, (size_t)n_views * nb * 6 * 4, st));
-        ctx->pose_blocks = nb;
-    }
-    CodebookJobs jobs;
-    std::memset(&jobs, 0, sizeof(jobs));
-    for (int gi = 0; gi < 4; ++gi) {
-        if (sd.L[gi] <= 0 || !gptr[gi]) continue;
-        if (N == 0) {
-            VG_CUDA(cudaMemsetAsync(gptr[gi], 0, (size_t)sd.L[gi] * sd.K[gi] * GDIMS[gi] * 4, st));
-            continue;
-        }
-        const int j = jobs.n++;
-        jobs.K[j] = sd.K[gi];
-        jobs.dim[j] = GDIMS[gi];
-        jobs.off[j] = goff(gi);
-        jobs.perm[j] = scene->perm[gi].as<uint32_t>();
-        jobs.seg[j] = scene->seg[gi].as<uint32_t>();
-        jobs.out[j] = gptr[gi];
-        jobs.block_start[j + 1] = jobs.block_start[j] + sd.L[gi] * sd.K[gi];
-    }
-    if (jobs.n > 0)
-        VG_STAGE(VG_STAGE_CODEBOOK,
-                 launch_codebook_reduce(jobs, N, ctx->dattr.as<float>(), ctx->touched.as<uint32_t>(), st));
+    VG_STAGE(VG_STAGE_CHAIN, launch_chain(sd, V, cs, ctx->g2d.as<float>(), ctx->vis.as<uint32_t>(),
+                                          ctx->scratch.as<uint32_t>() + SCR_NVIS, (uint32_t)slots, O,
+                                          &ctx->pose_blocks, st));
     ctx->bwd_scene = sd;
     ctx->views = V;
     ctx->have_bwd = true;

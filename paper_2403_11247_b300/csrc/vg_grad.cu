@@ -1,8 +1,8 @@
-// vg_grad.cu -- per-Gaussian chain rule from 2D gradients to the scene
-// (projection Eq. 2-3, anchor decode Eq. 7, codebook decode Eq. 14, mask
-// straight-through estimator Eq. 11-12), the camera-pose twist gradient, the
-// deterministic codebook-gradient reduction, the ICP term (Eq. 20) and the L1
-// photometric/depth loss gradient images.
+// vg_grad.cu -- chain rule from the 2D gradients of the visible slots to the
+// scene (projection Eq. 2-3, anchor decode Eq. 7, codebook decode Eq. 14,
+// mask straight-through estimator Eq. 11-12) with the codebook gradients
+// accumulated in the same pass, the camera-pose twist gradient, the ICP term
+// (Eq. 20) and the L1 photometric/depth loss gradient images.
 #include "vg_internal.h"
 
 namespace vgk {
@@ -22,74 +22,71 @@ __device__ __forceinline__ float block_sum_256(float x, float* s_tmp /*[8]*/) {
     return t;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const __grid_constant__ Views V, Consts cs,
-                                                             const float* __restrict__ g2d, float* __restrict__ dattr,
-                                                             float* raw0, float* raw1, float* raw2, float* raw3,
-                                                             float* d_xyz, float* d_l, float* d_off, float* d_mask,
-                                                             float* __restrict__ pose_part,
-                                                             uint32_t* __restrict__ touched_mask,
-                                                             const uint32_t* __restrict__ ntiles) {
-    __shared__ float s_red[8][6];
-    const int64_t n = (int64_t)blockIdx.x * CHAIN_THREADS + threadIdx.x;
-    const bool live = n < S.N;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    float mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, ol = 0, rgb[3];
-    bool active = false;
-    float R[3][3], s[3] = {1, 1, 1}, qn[4] = {1, 0, 0, 0}, qnorm = 1.f, Sig[3][3];
-    // most Gaussians reach no pixel of any view: their gradients are zero and
-    // they need no decode
-    // only slots visible in the last forward carry gradient rows
-    bool touched = false;
-    if (live) {
-        for (int v = 0; v < V.n && !touched; ++v) {
-            if (ntiles[(int64_t)v * S.N + n] == 0u) continue;
-            const float* gg = g2d + ((int64_t)v * S.N + n) * G2D_STRIDE;
+// One thread per visible (view, Gaussian) slot: the slot's 2D gradient row
+// (from the backward compositing) through the projection (Eq. 3), the
+// covariance (Eq. 2), the activations, the anchor decode (Eq. 7), the
+// codebook decode (Eq. 14) and the mask (Eq. 11-12) to the scene, plus the
+// slot's pose-twist contribution.  The chain rule is linear in the row, so
+// a Gaussian seen in several views gets the sum of its slots' contributions:
+// every scene gradient is accumulated with atomics into arrays zeroed by
+// zero_bwd_kernel.  Codebook gradients accumulate per block in shared
+// memory (when the codebooks fit) and are flushed once per block.
+__global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
+    SceneDev S, const __grid_constant__ Views V, Consts cs, const float* __restrict__ g2d,
+    const uint32_t* __restrict__ vis, const uint32_t* __restrict__ nvis_dev, uint32_t max_vis, ChainOut O) {
+    extern __shared__ float s_dyn[];  // [V.n][6] pose sums, then the codebook-gradient accumulators
+    float* s_pose = s_dyn;
+    float* s_cb = s_dyn + V.n * 6;
+    const int n_acc = V.n * 6 + (O.cb_in_smem ? O.cb_total : 0);
+    for (int i = threadIdx.x; i < n_acc; i += blockDim.x) s_dyn[i] = 0.f;
+    __syncthreads();
+    const uint32_t nvis = min(*nvis_dev, max_vis);
+    const int lane = threadIdx.x & 31;
+    // warp-uniform trip count, so that the pose sums can use warp shuffles
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nvis;
+         base += gridDim.x * blockDim.x) {
+        const uint32_t e = base + lane;
+        float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int pv = -1;  // view of this lane's pose contribution, -1 = none
+        do {
+            if (e >= nvis) break;
+            const uint32_t slot = vis[e];
+            const int v = (int)(slot / (uint64_t)S.N);
+            const int64_t n = (int64_t)slot - (int64_t)v * S.N;
+            float g[12];
+            {
+                const float4* row = reinterpret_cast<const float4*>(g2d + (int64_t)slot * G2D_STRIDE);
+                const float4 r0 = row[0], r1 = row[1], r2 = row[2];
+                g[0] = r0.x; g[1] = r0.y; g[2] = r0.z; g[3] = r0.w;
+                g[4] = r1.x; g[5] = r1.y; g[6] = r1.z; g[7] = r1.w;
+                g[8] = r2.x; g[9] = r2.y; g[10] = r2.z; g[11] = r2.w;
+            }
+            bool nz = false;
 #pragma unroll
-            for (int c = 0; c < 10; ++c) touched |= gg[c] != 0.f;
-        }
-    }
-    {
-        const uint32_t tm = __ballot_sync(0xffffffffu, live && touched);
-        if (lane == 0) touched_mask[n >> 5] = tm;
-    }
-    if (live && touched) {
-        anchor_mean(S, n, mu);
-        decode_attr<3>(S, 0, n, ls);
-        decode_attr<4>(S, 1, n, q);
-        decode_attr<1>(S, 2, n, &ol);
-        decode_attr<3>(S, 3, n, rgb);
-        active = S.mask ? (__ldg(S.mask + n) > S.mask_thr) : true;
-        const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-        active = active && qq > 0.f;
-        if (active) {
-            qnorm = sqrtf(qq);
+            for (int c = 0; c < 10; ++c) nz |= g[c] != 0.f;
+            if (!nz) break;
+            float mu[3], ls[3], q[4], ol, rgb[3];
+            anchor_mean(S, n, mu);
+            decode_attr<3>(S, 0, n, ls);
+            decode_attr<4>(S, 1, n, q);
+            decode_attr<1>(S, 2, n, &ol);
+            decode_attr<3>(S, 3, n, rgb);
+            const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+            if (!(qq > 0.f)) break;
+            const float qnorm = sqrtf(qq);
+            float qn[4], s[3], R[3][3], Sig[3][3];
 #pragma unroll
             for (int c = 0; c < 4; ++c) qn[c] = q[c] / qnorm;
 #pragma unroll
             for (int c = 0; c < 3; ++c) s[c] = expf(ls[c]);
-        }
-    }
-    quat_rot(qn, R);
+            quat_rot(qn, R);
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
+            for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            Sig[r][c] = R[r][0] * R[c][0] * s[0] * s[0] + R[r][1] * R[c][1] * s[1] * s[1] + R[r][2] * R[c][2] * s[2] * s[2];
-
-    float dmu[3] = {0, 0, 0}, dSig[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, dop = 0.f, drgb[3] = {0, 0, 0};
-    for (int v = 0; v < V.n; ++v) {
-        float pose[6] = {0, 0, 0, 0, 0, 0};
-        if (live && active && ntiles[(int64_t)v * S.N + n] != 0u) {
-            const float* gg = g2d + ((int64_t)v * S.N + n) * G2D_STRIDE;
-            float g[10];
-            bool nz = false;
-#pragma unroll
-            for (int c = 0; c < 10; ++c) {
-                g[c] = gg[c];
-                nz |= g[c] != 0.f;
-            }
-            if (nz) {
+                for (int c = 0; c < 3; ++c)
+                    Sig[r][c] = R[r][0] * R[c][0] * s[0] * s[0] + R[r][1] * R[c][1] * s[1] * s[1] + R[r][2] * R[c][2] * s[2] * s[2];
+            float dmu[3] = {0, 0, 0}, dSig[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, dop = 0.f, drgb[3] = {0, 0, 0};
+            {
                 const ViewInfo& vi = V.v[v];
                 float T[12];
                 view_pose(V, v, T);
@@ -106,13 +103,13 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
                 const float J00 = fx / z, J02 = -fx * txz / z, J11 = fy / z, J12 = -fy * tyz / z;
                 const float W[3][3] = {{T[0], T[1], T[2]}, {T[4], T[5], T[6]}, {T[8], T[9], T[10]}};
                 float T1[3][3], Sc[3][3];
-#pragma unroll
+        #pragma unroll
                 for (int r = 0; r < 3; ++r)
-#pragma unroll
+        #pragma unroll
                     for (int c = 0; c < 3; ++c) T1[r][c] = W[r][0] * Sig[0][c] + W[r][1] * Sig[1][c] + W[r][2] * Sig[2][c];
-#pragma unroll
+        #pragma unroll
                 for (int r = 0; r < 3; ++r)
-#pragma unroll
+        #pragma unroll
                     for (int c = 0; c < 3; ++c) Sc[r][c] = T1[r][0] * W[c][0] + T1[r][1] * W[c][1] + T1[r][2] * W[c][2];
                 const float A = J00 * J00 * Sc[0][0] + 2.f * J00 * J02 * Sc[0][2] + J02 * J02 * Sc[2][2] + cs.dilation;
                 const float B = J00 * J11 * Sc[0][1] + J00 * J12 * Sc[0][2] + J02 * J11 * Sc[1][2] + J02 * J12 * Sc[2][2];
@@ -127,14 +124,14 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
                 const float hB = 0.5f * dB;
                 const float Jr[2][3] = {{J00, 0.f, J02}, {0.f, J11, J12}};
                 float dSc[3][3];
-#pragma unroll
+        #pragma unroll
                 for (int r = 0; r < 3; ++r)
-#pragma unroll
+        #pragma unroll
                     for (int c = 0; c < 3; ++c)
                         dSc[r][c] = dA * Jr[0][r] * Jr[0][c] + hB * (Jr[0][r] * Jr[1][c] + Jr[1][r] * Jr[0][c]) +
                                     dC * Jr[1][r] * Jr[1][c];
                 float JS[2][3];
-#pragma unroll
+        #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     JS[0][c] = J00 * Sc[0][c] + J02 * Sc[2][c];
                     JS[1][c] = J11 * Sc[1][c] + J12 * Sc[2][c];
@@ -154,16 +151,16 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
                 dp[1] = dv * fy / z + dJ12 * dJ12_dy;
                 dp[2] = -du * fx * x / z2 - dv * fy * y / z2 + ddepth - dJ00 * fx / z2 - dJ11 * fy / z2 +
                         dJ02 * dJ02_dz + dJ12 * dJ12_dz;
-#pragma unroll
+        #pragma unroll
                 for (int c = 0; c < 3; ++c) dmu[c] += W[0][c] * dp[0] + W[1][c] * dp[1] + W[2][c] * dp[2];
                 float T2[3][3];
-#pragma unroll
+        #pragma unroll
                 for (int r = 0; r < 3; ++r)
-#pragma unroll
+        #pragma unroll
                     for (int c = 0; c < 3; ++c) T2[r][c] = dSc[r][0] * W[0][c] + dSc[r][1] * W[1][c] + dSc[r][2] * W[2][c];
-#pragma unroll
+        #pragma unroll
                 for (int r = 0; r < 3; ++r)
-#pragma unroll
+        #pragma unroll
                     for (int c = 0; c < 3; ++c) dSig[r][c] += W[0][r] * T2[0][c] + W[1][r] * T2[1][c] + W[2][r] * T2[2][c];
                 dop += g[5];
                 drgb[0] += g[6];
@@ -171,9 +168,9 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
                 drgb[2] += g[8];
                 // left perturbation: p += phi x p + rho ; Sc += [phi]x Sc - Sc [phi]x
                 float M[3][3];
-#pragma unroll
+        #pragma unroll
                 for (int r = 0; r < 3; ++r)
-#pragma unroll
+        #pragma unroll
                     for (int c = 0; c < 3; ++c)
                         M[r][c] = Sc[r][0] * dSc[0][c] + Sc[r][1] * dSc[1][c] + Sc[r][2] * dSc[2][c] -
                                   (dSc[r][0] * Sc[0][c] + dSc[r][1] * Sc[1][c] + dSc[r][2] * Sc[2][c]);
@@ -184,233 +181,173 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(SceneDev S, const 
                 pose[4] = p[2] * dp[0] - p[0] * dp[2] - 2.f * M[0][2];
                 pose[5] = p[0] * dp[1] - p[1] * dp[0] - 2.f * M[1][0];
             }
-        }
-        // block reduction of the six pose components for view v
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            float x = pose[c];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0) s_red[warp][c] = x;
-        }
-        __syncthreads();
-        if (threadIdx.x < 6) {
-            float t = 0.f;
-            for (int w = 0; w < CHAIN_THREADS / 32; ++w) t += s_red[w][threadIdx.x];
-            pose_part[((int64_t)v * gridDim.x + blockIdx.x) * 6 + threadIdx.x] = t;
-        }
-        __syncthreads();
-    }
-
-    // Sigma = M M^T with M = R diag(s)
-    float dls[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dol = 0.f, ds[3] = {0, 0, 0}, o = 0.f;
-    if (live && active) {
-        float dM[3][3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float acc = 0.f;
-#pragma unroll
-                for (int m = 0; m < 3; ++m) acc += (dSig[r][m] + dSig[m][r]) * R[m][c] * s[c];
-                dM[r][c] = acc;
+            pv = v;
+            // Sigma = M M^T with M = R diag(s)
+            float dls[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dol = 0.f, ds[3] = {0, 0, 0}, o = 0.f;
+            {
+                float dM[3][3];
+        #pragma unroll
+                for (int r = 0; r < 3; ++r)
+        #pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        float acc = 0.f;
+        #pragma unroll
+                        for (int m = 0; m < 3; ++m) acc += (dSig[r][m] + dSig[m][r]) * R[m][c] * s[c];
+                        dM[r][c] = acc;
+                    }
+                float dR[3][3];
+        #pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    ds[c] = dM[0][c] * R[0][c] + dM[1][c] * R[1][c] + dM[2][c] * R[2][c];
+                    dls[c] = ds[c] * s[c];
+        #pragma unroll
+                    for (int r = 0; r < 3; ++r) dR[r][c] = dM[r][c] * s[c];
+                }
+                const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+                float dqn[4];
+                dqn[0] = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
+                dqn[1] = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] - w * dR[1][2] + z * dR[2][0] +
+                                w * dR[2][1] - 2.f * x * dR[2][2]);
+                dqn[2] = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] - w * dR[2][0] +
+                                z * dR[2][1] - 2.f * y * dR[2][2]);
+                dqn[3] = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
+                                y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+                const float dot = qn[0] * dqn[0] + qn[1] * dqn[1] + qn[2] * dqn[2] + qn[3] * dqn[3];
+        #pragma unroll
+                for (int c = 0; c < 4; ++c) dq[c] = (dqn[c] - qn[c] * dot) / qnorm;
+                o = 1.f / (1.f + expf(-ol));
+                dol = dop * o * (1.f - o);
             }
-        float dR[3][3];
+            // attribute gradients: raw arrays, or the indexed codewords of every stage
+            const float* vals[4] = {dls, dq, &dol, drgb};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            ds[c] = dM[0][c] * R[0][c] + dM[1][c] * R[1][c] + dM[2][c] * R[2][c];
-            dls[c] = ds[c] * s[c];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) dR[r][c] = dM[r][c] * s[c];
-        }
-        const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
-        float dqn[4];
-        dqn[0] = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
-        dqn[1] = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] - w * dR[1][2] + z * dR[2][0] +
-                        w * dR[2][1] - 2.f * x * dR[2][2]);
-        dqn[2] = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] - w * dR[2][0] +
-                        z * dR[2][1] - 2.f * y * dR[2][2]);
-        dqn[3] = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
-                        y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
-        const float dot = qn[0] * dqn[0] + qn[1] * dqn[1] + qn[2] * dqn[2] + qn[3] * dqn[3];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) dq[c] = (dqn[c] - qn[c] * dot) / qnorm;
-        o = 1.f / (1.f + expf(-ol));
-        dol = dop * o * (1.f - o);
-    } else {
-        drgb[0] = drgb[1] = drgb[2] = 0.f;
-    }
-    if (live) {
-        const float* vals[4] = {dls, dq, &dol, drgb};
-        float* raws[4] = {raw0, raw1, raw2, raw3};
-#pragma unroll
-        for (int gi = 0; gi < 4; ++gi) {
-            const int d = gdim(gi);
-            if (S.L[gi] > 0) {
-                // untouched Gaussians are skipped by the codebook reduction
-                if (dattr && touched)
-                    for (int c = 0; c < d; ++c) dattr[n * ATTR_STRIDE + goff(gi) + c] = vals[gi][c];
-            } else if (raws[gi]) {
-                for (int c = 0; c < d; ++c) raws[gi][n * d + c] = vals[gi][c];
+            for (int gi = 0; gi < 4; ++gi) {
+                const int d = gdim(gi);
+                if (S.L[gi] > 0) {
+                    if (!O.cb[gi]) continue;
+                    for (int st = 0; st < S.L[gi]; ++st) {
+                        const int k = __ldg(S.idx[gi] + (int64_t)st * S.N + n);
+                        const int j = (st * S.K[gi] + k) * d;
+                        float* dst = O.cb_in_smem ? s_cb + O.cb_off[gi] + j : O.cb[gi] + j;
+                        for (int c = 0; c < d; ++c) atomicAdd(dst + c, vals[gi][c]);
+                    }
+                } else if (O.raw[gi]) {
+                    for (int c = 0; c < d; ++c) atomicAdd(O.raw[gi] + n * d + c, vals[gi][c]);
+                }
             }
-        }
-        if (d_mask && S.mask) {
-            float dm = 0.f;
-            if (active) {
+            if (O.d_mask && S.mask) {
                 const float sm = 1.f / (1.f + expf(-__ldg(S.mask + n)));
-                dm = (ds[0] * s[0] + ds[1] * s[1] + ds[2] * s[2] + dop * o) * sm * (1.f - sm);
+                atomicAdd(O.d_mask + n, (ds[0] * s[0] + ds[1] * s[1] + ds[2] * s[2] + dop * o) * sm * (1.f - sm));
             }
-            d_mask[n] = dm;
-        } else if (d_mask) {
-            d_mask[n] = 0.f;
-        }
-    }
-    // Eq. 7: d x_a = sum_i dmu_i, d O_i = dmu_i * l, d l = sum_i dmu_i * O_i
-    const int64_t a = live ? n / S.k : 0;
-    float gl[3] = {0, 0, 0}, gx[3] = {dmu[0], dmu[1], dmu[2]};
-    if (live) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float l = __ldg(S.l + a * 3 + c);
-            if (d_off) d_off[n * 3 + c] = dmu[c] * l;
-            gl[c] = dmu[c] * __ldg(S.off + n * 3 + c);
-        }
-    }
-    if ((32 % S.k) == 0) {
-        for (int off = S.k >> 1; off > 0; off >>= 1) {
+            // Eq. 7: d x_a = sum_i dmu_i, d O_i = dmu_i * l, d l = sum_i dmu_i * O_i
+            const int64_t a = n / S.k;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                gx[c] += __shfl_xor_sync(0xffffffffu, gx[c], off);
-                gl[c] += __shfl_xor_sync(0xffffffffu, gl[c], off);
+                if (O.d_off) atomicAdd(O.d_off + n * 3 + c, dmu[c] * __ldg(S.l + a * 3 + c));
+                if (O.d_xyz) atomicAdd(O.d_xyz + a * 3 + c, dmu[c]);
+                if (O.d_l) atomicAdd(O.d_l + a * 3 + c, dmu[c] * __ldg(S.off + n * 3 + c));
+            }
+        } while (0);
+        // pose sums: one butterfly per warp when its lanes share a view (the
+        // slots are in view order, so they nearly always do)
+        const uint32_t has = __ballot_sync(0xffffffffu, pv >= 0);
+        if (has) {
+            const int v0 = __shfl_sync(0xffffffffu, pv, __ffs(has) - 1);
+            if (__all_sync(0xffffffffu, pv < 0 || pv == v0)) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    float x = pose[c];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                    if (lane == 0) atomicAdd(s_pose + v0 * 6 + c, x);
+                }
+            } else if (pv >= 0) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) atomicAdd(s_pose + pv * 6 + c, pose[c]);
             }
         }
-        if (live && (n % S.k) == 0) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (d_xyz) d_xyz[a * 3 + c] = gx[c];
-                if (d_l) d_l[a * 3 + c] = gl[c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < V.n * 6; i += blockDim.x)
+        O.pose_part[((int64_t)(i / 6) * gridDim.x + blockIdx.x) * 6 + i % 6] = s_pose[i];
+    if (O.cb_in_smem) {
+        for (int gi = 0; gi < 4; ++gi) {
+            if (S.L[gi] <= 0 || !O.cb[gi]) continue;
+            const int sz = S.L[gi] * S.K[gi] * gdim(gi);
+            for (int j = threadIdx.x; j < sz; j += blockDim.x) {
+                const float t = s_cb[O.cb_off[gi] + j];
+                if (t != 0.f) atomicAdd(O.cb[gi] + j, t);
             }
-        }
-    } else if (live) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (d_xyz) atomicAdd(d_xyz + a * 3 + c, gx[c]);
-            if (d_l) atomicAdd(d_l + a * 3 + c, gl[c]);
         }
     }
 }
 
-int chain_blocks(int64_t N) { return (int)ceil_div(N > 0 ? N : 1, CHAIN_THREADS); }
+int chain_blocks(int64_t) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    return 2 * sms;
+}
 
-// zero the gradient rows of the visible slots (the only rows the backward
-// blend writes); all other rows are kept at zero
-__global__ void zero_visible_g2d_kernel(const uint32_t* __restrict__ vis, const uint32_t* __restrict__ nvis_dev,
-                                        uint32_t max_vis, float* __restrict__ g2d) {
+// before the backward: zero the gradient rows of the visible slots (the only
+// rows the backward compositing writes; all other rows stay zero) and every
+// scene-gradient array the chain kernel accumulates into
+__global__ void zero_bwd_kernel(const uint32_t* __restrict__ vis, const uint32_t* __restrict__ nvis_dev,
+                                uint32_t max_vis, float* __restrict__ g2d, ZeroList Z) {
     const uint32_t n = min(*nvis_dev, max_vis);
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n * 3; e += gridDim.x * blockDim.x) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthr = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = tid; e < (int64_t)n * 3; e += nthr) {
         const uint32_t s = vis[e / 3];
         reinterpret_cast<float4*>(g2d + (int64_t)s * G2D_STRIDE)[e % 3] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    for (int j = 0; j < Z.n; ++j) {
+        float* p = Z.p[j];
+        const int64_t cnt = Z.count[j];
+        const bool vec = (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+        const int64_t n4 = vec ? cnt / 4 : 0;
+        for (int64_t i = tid; i < n4; i += nthr) reinterpret_cast<float4*>(p)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t i = n4 * 4 + tid; i < cnt; i += nthr) p[i] = 0.f;
+    }
 }
 
-cudaError_t launch_zero_visible_g2d(const uint32_t* vis_slots, const uint32_t* nvis_dev, uint32_t max_vis, float* g2d,
-                                    cudaStream_t st) {
-    int64_t blocks = ceil_div((int64_t)max_vis * 3, 256);
+cudaError_t launch_zero_bwd(const uint32_t* vis_slots, const uint32_t* nvis_dev, uint32_t max_vis, float* g2d,
+                            const ZeroList& Z, cudaStream_t st) {
+    int64_t work = (int64_t)max_vis * 3;
+    for (int j = 0; j < Z.n; ++j) work = work > Z.count[j] / 4 ? work : Z.count[j] / 4;
+    int64_t blocks = ceil_div(work > 0 ? work : 1, 256);
     if (blocks > 148 * 4) blocks = 148 * 4;
-    if (blocks < 1) blocks = 1;
     count_launches(1);
-    zero_visible_g2d_kernel<<<(unsigned)blocks, 256, 0, st>>>(vis_slots, nvis_dev, max_vis, g2d);
+    zero_bwd_kernel<<<(unsigned)blocks, 256, 0, st>>>(vis_slots, nvis_dev, max_vis, g2d, Z);
     return cudaGetLastError();
 }
 
-cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, const float* g2d, float* dattr, float* r0,
-                         float* r1, float* r2, float* r3, float* d_xyz, float* d_l, float* d_off, float* d_mask,
-                         float* pose_part, uint32_t* touched, const uint32_t* ntiles, int* n_blocks_out,
-                         cudaStream_t st) {
+size_t chain_smem(const SceneDev& S, const Views& V, ChainOut* O) {
+    int off = 0;
+    for (int gi = 0; gi < 4; ++gi) {
+        O->cb_off[gi] = off;
+        if (S.L[gi] > 0 && O->cb[gi]) off += S.L[gi] * S.K[gi] * gdim(gi);
+    }
+    O->cb_total = off;
+    const size_t pose_bytes = (size_t)V.n * 6 * sizeof(float);
+    const size_t cb_bytes = (size_t)off * sizeof(float);
+    // codebook accumulators in shared memory up to 96 KB, else global atomics
+    O->cb_in_smem = (off > 0 && pose_bytes + cb_bytes <= 96 * 1024) ? 1 : 0;
+    return pose_bytes + (O->cb_in_smem ? cb_bytes : 0);
+}
+
+cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, const float* g2d, const uint32_t* vis,
+                         const uint32_t* nvis_dev, uint32_t max_vis, ChainOut O, int* n_blocks_out, cudaStream_t st) {
     const int blocks = chain_blocks(S.N);
     if (n_blocks_out) *n_blocks_out = blocks;
+    const size_t smem = chain_smem(S, V, &O);
+    cudaError_t e = allow_dynamic_smem((const void*)chain_kernel, smem);
+    if (e != cudaSuccess) return e;
     count_launches(1);
-    chain_kernel<<<blocks, CHAIN_THREADS, 0, st>>>(S, V, cs, g2d, dattr, r0, r1, r2, r3, d_xyz, d_l, d_off, d_mask,
-                                                   pose_part, touched, ntiles);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// codebook gradients: dC^s[k] = sum over Gaussians n with idx[s][n] == k of
-// the attribute gradient of n, as a segmented sum over a per-stage
-// codeword-sorted Gaussian list (deterministic, no atomics)
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) codebook_reduce_kernel(const __grid_constant__ CodebookJobs J, int64_t N,
-                                                                const float* __restrict__ dattr,
-                                                                const uint32_t* __restrict__ touched) {
-    __shared__ float s_tmp[8];
-    int j = 0;
-    while (j + 1 < J.n && (int)blockIdx.x >= J.block_start[j + 1]) ++j;
-    const int local = blockIdx.x - J.block_start[j];
-    const int K = J.K[j], dim = J.dim[j], off = J.off[j];
-    const int s = local / K, k = local % K;
-    const uint32_t* perm = J.perm[j] + (int64_t)s * N;
-    const uint32_t b = J.seg[j][s * (K + 1) + k], e = J.seg[j][s * (K + 1) + k + 1];
-    float acc[4] = {0, 0, 0, 0};
-    // four independent gathers in flight per thread
-    uint32_t i = b + threadIdx.x;
-    for (; i + 3 * 256 < e; i += 4 * 256) {
-        uint32_t n4[4], t4[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) n4[u] = __ldg(perm + i + u * 256);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) t4[u] = (__ldg(touched + (n4[u] >> 5)) >> (n4[u] & 31)) & 1u;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (t4[u])
-                for (int c = 0; c < dim; ++c) acc[c] += __ldg(dattr + (int64_t)n4[u] * ATTR_STRIDE + off + c);
-    }
-    for (; i < e; i += 256) {
-        const uint32_t n = __ldg(perm + i);
-        if ((__ldg(touched + (n >> 5)) >> (n & 31)) & 1u)
-            for (int c = 0; c < dim; ++c) acc[c] += __ldg(dattr + (int64_t)n * ATTR_STRIDE + off + c);
-    }
-    for (int c = 0; c < dim; ++c) {
-        const float t = block_sum_256(acc[c], s_tmp);
-        if (threadIdx.x == 0) J.out[j][((int64_t)s * K + k) * dim + c] = t;
-    }
-}
-
-cudaError_t launch_codebook_reduce(const CodebookJobs& J, int64_t N, const float* dattr, const uint32_t* touched,
-                                   cudaStream_t st) {
-    if (J.n == 0 || J.block_start[J.n] == 0) return cudaSuccess;
-    count_launches(1);
-    codebook_reduce_kernel<<<J.block_start[J.n], 256, 0, st>>>(J, N, dattr, touched);
-    return cudaGetLastError();
-}
-
-__global__ void seg_from_hist_kernel(const uint32_t* hist, int K, uint32_t* seg) {
-    if (threadIdx.x == 0) {
-        uint32_t acc = 0;
-        for (int k = 0; k < K; ++k) {
-            seg[k] = acc;
-            acc += hist[k];
-        }
-        seg[K] = acc;
-    }
-}
-
-cudaError_t launch_seg_from_hist(const uint32_t* hist, int K, uint32_t* seg, cudaStream_t st) {
-    count_launches(1);
-    seg_from_hist_kernel<<<1, 32, 0, st>>>(hist, K, seg);
-    return cudaGetLastError();
-}
-
-__global__ void idx_to_keys_kernel(const uint8_t* __restrict__ idx, int64_t n, uint32_t* __restrict__ keys) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        keys[i] = idx[i];
-}
-
-cudaError_t launch_idx_to_keys(const uint8_t* idx, int64_t n, uint32_t* keys, cudaStream_t st) {
-    int64_t blocks = ceil_div(n > 0 ? n : 1, 256);
-    if (blocks > 148 * 16) blocks = 148 * 16;
-    count_launches(1);
-    idx_to_keys_kernel<<<(unsigned)blocks, 256, 0, st>>>(idx, n, keys);
+    chain_kernel<<<blocks, CHAIN_THREADS, smem, st>>>(S, V, cs, g2d, vis, nvis_dev, max_vis, O);
     return cudaGetLastError();
 }
 

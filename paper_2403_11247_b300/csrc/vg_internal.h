@@ -53,7 +53,7 @@ cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& c
                               uint32_t* state, uint32_t* blk_count, cudaStream_t st);
 // visible slots, in (view, Gaussian) order within each preprocess block, to keys_out / vals_out
 cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count, uint32_t* blk_base,
-                           uint32_t* keys_out, uint32_t* vals_out, cudaStream_t st);
+                           uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, cudaStream_t st);
 cudaError_t launch_rvq_decode(int dim, int L, int K, const float* cb, const uint8_t* idx, const float* raw,
                               int64_t n, float* out, cudaStream_t st);
 
@@ -66,7 +66,6 @@ cudaError_t launch_sort_pass(const uint32_t* keys_in, const uint32_t* vals_in, u
                              const uint32_t* state, uint32_t epoch_offset, uint32_t* err, int grid,
                              cudaStream_t st);
 int sort_pass_grid(uint32_t n_cap);
-cudaError_t launch_hist(const uint32_t* keys, int64_t n, int passes, uint32_t* hist, cudaStream_t st);
 cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, const uint32_t* ntiles,
                              const uint2* rect, int64_t N, const Views& V, uint32_t* pkeys, uint32_t* pvals,
                              uint32_t cap, uint32_t* scratch, int tile_passes, unsigned long long* lookback,
@@ -89,27 +88,26 @@ cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, const ui
                              float* g2d, unsigned long long* bwd_pairs, int count, cudaStream_t st);
 
 // grad.cu
-cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, const float* g2d, float* dattr,
-                         float* raw_grad0, float* raw_grad1, float* raw_grad2, float* raw_grad3, float* d_xyz,
-                         float* d_l, float* d_off, float* d_mask, float* pose_part, uint32_t* touched,
-                         const uint32_t* ntiles, int* n_blocks_out, cudaStream_t st);
-cudaError_t launch_zero_visible_g2d(const uint32_t* vis_slots, const uint32_t* nvis_dev, uint32_t max_vis, float* g2d,
-                                    cudaStream_t st);
-int chain_blocks(int64_t N);
-// codebook-gradient reductions of all coded groups in one launch: block
-// range [block_start[j], block_start[j+1]) serves group job j, one block per
-// (stage, codeword)
-struct CodebookJobs {
-    int32_t n;
-    int32_t K[4], dim[4], off[4];
-    const uint32_t* perm[4];
-    const uint32_t* seg[4];
-    float* out[4];
-    int32_t block_start[5];
+// where the chain kernel accumulates the scene gradients (device pointers;
+// NULL = not wanted); cb_off/cb_total/cb_in_smem are filled by the launcher
+struct ChainOut {
+    float* raw[4];   // per-Gaussian attribute gradients of uncoded groups [N][d]
+    float* cb[4];    // codebook gradients of coded groups [L][K][d]
+    float *d_xyz, *d_l, *d_off, *d_mask;
+    float* pose_part;  // [views][chain blocks][6]
+    int32_t cb_off[4], cb_total, cb_in_smem;
 };
-cudaError_t launch_codebook_reduce(const CodebookJobs& J, int64_t N, const float* dattr, const uint32_t* touched,
-                                   cudaStream_t st);
-cudaError_t launch_seg_from_hist(const uint32_t* hist, int K, uint32_t* seg, cudaStream_t st);
+// arrays the zeroing kernel clears before the backward
+struct ZeroList {
+    int32_t n;
+    float* p[12];
+    int64_t count[12];
+};
+cudaError_t launch_zero_bwd(const uint32_t* vis_slots, const uint32_t* nvis_dev, uint32_t max_vis, float* g2d,
+                            const ZeroList& Z, cudaStream_t st);
+cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, const float* g2d, const uint32_t* vis,
+                         const uint32_t* nvis_dev, uint32_t max_vis, ChainOut O, int* n_blocks_out, cudaStream_t st);
+int chain_blocks(int64_t N);
 cudaError_t launch_icp(const SceneDev& S, const Views& V, const float* q, const float* w, float* part, int n_blocks,
                        cudaStream_t st);
 int icp_blocks(int64_t N);
@@ -118,7 +116,6 @@ cudaError_t launch_pose_final(int n_views, const float* pose_part, int n_pose_bl
 cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const float* D, const float* S,
                            const float* Ct, const float* Dt, float w_depth, float gate, float* dC, float* dD,
                            float* loss, uint32_t* valid_count, cudaStream_t st);
-cudaError_t launch_idx_to_keys(const uint8_t* idx, int64_t n, uint32_t* keys, cudaStream_t st);
 
 // optim.cu
 cudaError_t launch_adam(int n, float* const* p, const float* const* g, float* const* m, float* const* v,

@@ -241,11 +241,13 @@ __global__ void __launch_bounds__(1024) block_scan_kernel(const uint32_t* __rest
 
 // order-preserving compaction of the visible slots: block b of the preprocess
 // grid covers Gaussians [256 b, 256 b + 256) of every view; its visible slots
-// go, view by view and in Gaussian order, to [base[b], base[b] + count[b])
+// go, view by view and in Gaussian order, to [base[b], base[b] + count[b]);
+// vals_copy (may be NULL) keeps that slot order for the backward's per-slot
+// passes (the depth sort overwrites vals_out)
 __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Views V, int64_t N,
                                                       const uint32_t* __restrict__ dkey,
                                                       const uint32_t* __restrict__ base, uint32_t* __restrict__ keys_out,
-                                                      uint32_t* __restrict__ vals_out) {
+                                                      uint32_t* __restrict__ vals_out, uint32_t* __restrict__ vals_copy) {
     __shared__ uint32_t s_tmp[8];
     const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
     uint32_t off = base[blockIdx.x];
@@ -258,6 +260,7 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
         if (f) {
             keys_out[off + pre] = key;
             vals_out[off + pre] = (uint32_t)slot;
+            if (vals_copy) vals_copy[off + pre] = (uint32_t)slot;
         }
         off += tot;
     }
@@ -286,13 +289,13 @@ cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& c
 }
 
 cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count, uint32_t* blk_base,
-                           uint32_t* keys_out, uint32_t* vals_out, cudaStream_t st) {
+                           uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, cudaStream_t st) {
     const int blocks = preprocess_blocks(N);
     count_launches(2);
     block_scan_kernel<<<1, 1024, 0, st>>>(blk_count, blocks, blk_base);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    compact_kernel<<<blocks, 256, 0, st>>>(V, N, dkey, blk_base, keys_out, vals_out);
+    compact_kernel<<<blocks, 256, 0, st>>>(V, N, dkey, blk_base, keys_out, vals_out, vals_copy);
     return cudaGetLastError();
 }
 

@@ -182,28 +182,6 @@ cudaError_t launch_sort_pass(const uint32_t* keys_in, const uint32_t* vals_in, u
     return cudaGetLastError();
 }
 
-// digit histograms of u32 keys for `passes` 8-bit digits (hist must be zeroed)
-__global__ void hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int passes, uint32_t* hist) {
-    __shared__ uint32_t s[4 * 256];
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s[i] = 0;
-    __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&s[p * 256 + ((k >> (8 * p)) & 255u)], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
-        if (s[i]) atomicAdd(hist + i, s[i]);
-}
-
-cudaError_t launch_hist(const uint32_t* keys, int64_t n, int passes, uint32_t* hist, cudaStream_t st) {
-    int64_t blocks = ceil_div(n > 0 ? n : 1, 1024);
-    if (blocks > 148 * 8) blocks = 148 * 8;
-    count_launches(1);
-    hist_kernel<<<(unsigned)blocks, 256, 0, st>>>(keys, n, passes, hist);
-    return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------------------
 // pair offsets: exclusive scan of the tile counts of the depth-sorted visible
 // slots (persistent partitions, decoupled look-back)
