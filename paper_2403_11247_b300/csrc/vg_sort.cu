@@ -259,13 +259,28 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(
     const uint32_t nvis = scratch[SCR_NVIS];
     const uint32_t P = min(scratch[SCR_PAIRS], cap);
     const uint32_t stride = gridDim.x * blockDim.x;
+    __shared__ uint32_t s_bounds[2];
     for (uint32_t e0 = blockIdx.x * blockDim.x; e0 < P; e0 += stride) {
+        // the slots of the block's first and last pair bound every thread's
+        // search: two full searches per block, then short ones
+        if (threadIdx.x < 2) {
+            const uint32_t t = threadIdx.x == 0 ? e0 : min(e0 + blockDim.x, P) - 1;
+            uint32_t lo = 0, hi = nvis;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (__ldg(offsets + mid) <= t) lo = mid; else hi = mid;
+            }
+            s_bounds[threadIdx.x] = lo;
+        }
+        __syncthreads();
+        const uint32_t blo = s_bounds[0], bhi = s_bounds[1] + 1;
+        __syncthreads();
         const uint32_t e = e0 + threadIdx.x;
         const bool live = e < P;
         const uint32_t active = __ballot_sync(0xffffffffu, live);
         if (!live) continue;
         // last j with offsets[j] <= e
-        uint32_t lo = 0, hi = nvis;
+        uint32_t lo = blo, hi = bhi;
         while (hi - lo > 1) {
             const uint32_t mid = (lo + hi) >> 1;
             if (__ldg(offsets + mid) <= e) lo = mid; else hi = mid;
