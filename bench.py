@@ -353,6 +353,64 @@ def local_ba_leg(torch, V, synth, iters=50):
     return res
 
 
+def large_leg(torch, V, synth, steps=20):
+    """Large scene: 375k anchors x 8 = 3M Gaussians over 20 x 20 m, RVQ
+    3 x 256, 30% masked, four 1920x1080 views in one launch sequence:
+    forward, L1 loss gradient against a render from jittered cameras,
+    backward and pose gradients, captured as one graph and replayed."""
+    sc = synth.large_scene()
+    cams = synth.large_cameras()
+    tcams = [synth.camera(c.fx, c.fy, c.cx, c.cy, c.width, c.height,
+                          synth.perturb_pose(c.T_cw, np.random.default_rng(50 + i), 1.0, 0.02), c.near)
+             for i, c in enumerate(cams)]
+    sh = V.vg_scene_upload(sc)
+    ctx = V.vg_ctx_create(0)
+    params = V.default_params()
+    Ct, Dt, _ = V.render_with_retry(sh, tcams, params, ctx)
+    Ct, Dt = Ct.clone(), Dt.clone()
+    V.render_with_retry(sh, cams, params, ctx)
+    st = V.vg_ctx_stats(ctx)
+    V.vg_ctx_reserve(ctx, int(st["pairs"] * 1.2) + 4096)
+    P = cams[0].width * cams[0].height
+    f32 = dict(dtype=torch.float32, device="cuda")
+    C_, D, S = torch.empty(3 * 4 * P, **f32), torch.empty(4 * P, **f32), torch.empty(4 * P, **f32)
+    dC, dD, loss = torch.empty(3 * 4 * P, **f32), torch.empty(4 * P, **f32), torch.empty(1, **f32)
+    dxi = torch.empty((4, 6), **f32)
+    grads = V.grads_like(sh)
+
+    def step():
+        V.vg_render_fwd(sh, cams, params, ctx, C_, D, S)
+        V.vg_loss_l1(4, P, C_, D, S, Ct, Dt, 0.5, -1.0, ctx, dC=dC, dD=dD, loss=loss)
+        V.vg_render_bwd(sh, cams, params, ctx, dC, dD, None, grads)
+        V.vg_pose_grad(ctx, 4, dxi=dxi)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="thread_local"):
+        step()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    if V.vg_check(ctx) != V.VG_OK:
+        raise RuntimeError("large scene: device status not OK")
+    ms = statistics.median(times)
+    tiles = 4 * ((cams[0].width + 15) // 16) * ((cams[0].height + 15) // 16)
+    res = {"gaussians": int(sc.offsets.shape[0] * sc.offsets.shape[1]), "views": 4, "size": "1920x1080",
+           "ms_per_step": ms, "iters_per_s": 1000.0 / ms, "mpix_per_s": 4 * P / ms / 1e3,
+           "pairs": st["pairs"], "mean_list_per_tile": st["pairs"] / tiles, "visible_slots": st["visible"],
+           "steps": steps}
+    log(f"large scene: {ms:.2f} ms per 4-view fwd+bwd, {res['mean_list_per_tile']:.0f} Gaussians per tile")
+    return res
+
+
 def run_reference(args):
     rank, world, _ = env_dist()
     if rank != 0:
@@ -640,7 +698,9 @@ def run_ours(args):
         O.build()
         cpu = cpu_baseline(O, synth, w["scene"], w["cam"], w["tcam"])
 
-    serving = ba_res = None
+    serving = ba_res = large = None
+    if rank == 0 and not args.no_large:
+        large = large_leg(torch, V, synth)
     if rank == 0 and not args.no_serving:
         serving = serving_leg(torch, V, synth, args.serving_rates, args.serving_seconds)
     if rank == 0 and not args.no_local_ba:
@@ -660,7 +720,7 @@ def run_ours(args):
                 "p50_step_ms": statistics.median(step_ms), "p10_step_ms": float(np.percentile(step_ms, 10)),
                 "p90_step_ms": float(np.percentile(step_ms, 90)), "p99_step_ms": float(np.percentile(step_ms, 99)),
                 "plain_launches": eager,
-                "serving": serving, "local_ba": ba_res}
+                "serving": serving, "local_ba": ba_res, "large_scene": large}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -682,6 +742,7 @@ def main():
     ap.add_argument("--serving-rates", type=float, nargs="+", default=[200.0, 500.0, 1000.0, 2000.0])
     ap.add_argument("--serving-seconds", type=float, default=2.0, help="length of each Poisson trace")
     ap.add_argument("--no-local-ba", action="store_true", help="skip the local bundle-adjustment leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the large-scene leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

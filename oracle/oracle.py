@@ -90,6 +90,8 @@ def lib():
         _lib.orc_loss_l1.restype = C.c_double
         _lib.orc_loss_l1.argtypes = [C.c_int64, P, P, P, P, P, C.c_double, C.c_double, P, P]
         _lib.orc_rvq_decode.argtypes = [C.c_int, C.c_int, C.c_int, P, P, C.c_int64, P]
+        _lib.orc_set_window.restype = C.c_int
+        _lib.orc_set_window.argtypes = [P] + [C.c_int] * 5
     return _lib
 
 
@@ -195,6 +197,12 @@ class Oracle:
         self.n_pairs = L.orc_n_pairs(self.ctx)
         self.n_tiles = L.orc_n_tiles(self.ctx)
         self.n_pixels = L.orc_n_pixels(self.ctx)
+
+    def set_window(self, view: int, x0: int, y0: int, x1: int, y1: int):
+        """Composite (forward and backward) only pixels [x0, x1) x [y0, y1)
+        of ``view``; binning stays that of the whole image."""
+        if lib().orc_set_window(self.ctx, int(view), int(x0), int(y0), int(x1), int(y1)) != 0:
+            raise ValueError("bad view")
 
     def __del__(self):
         if getattr(self, "ctx", None):

@@ -91,6 +91,7 @@ struct orc_ctx {
     int* tiles_y;
     int64_t* tile_base;
     int64_t* pix_base;
+    int* win;            /* per view x0, y0, x1, y1: the pixels composited */
     int64_t n_tiles, n_pix;
     int64_t* tile_start;
     int64_t* list;
@@ -325,6 +326,13 @@ orc_ctx* orc_create(const orc_scene* scene, const orc_camera* cams, int n_views,
     ctx->tiles_y = (int*)malloc(sizeof(int) * n_views);
     ctx->tile_base = (int64_t*)malloc(sizeof(int64_t) * (n_views + 1));
     ctx->pix_base = (int64_t*)malloc(sizeof(int64_t) * (n_views + 1));
+    ctx->win = (int*)malloc(sizeof(int) * 4 * (n_views > 0 ? n_views : 1));
+    for (int v = 0; v < n_views; ++v) {
+        ctx->win[4 * v + 0] = 0;
+        ctx->win[4 * v + 1] = 0;
+        ctx->win[4 * v + 2] = cams[v].width;
+        ctx->win[4 * v + 3] = cams[v].height;
+    }
     ctx->tile_base[0] = 0;
     ctx->pix_base[0] = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -405,7 +413,7 @@ void orc_free(orc_ctx* ctx)
 {
     if (!ctx) return;
     free(ctx->cams); free(ctx->g); free(ctx->shp); free(ctx->pr);
-    free(ctx->tiles_x); free(ctx->tiles_y); free(ctx->tile_base); free(ctx->pix_base);
+    free(ctx->tiles_x); free(ctx->tiles_y); free(ctx->tile_base); free(ctx->pix_base); free(ctx->win);
     free(ctx->tile_start); free(ctx->list); free(ctx->tile_ambiguous);
     free(ctx);
 }
@@ -414,6 +422,20 @@ int64_t orc_n_slots(const orc_ctx* ctx) { return (int64_t)ctx->nv * ctx->N; }
 int64_t orc_n_pairs(const orc_ctx* ctx) { return ctx->n_pairs; }
 int64_t orc_n_tiles(const orc_ctx* ctx) { return ctx->n_tiles; }
 int64_t orc_n_pixels(const orc_ctx* ctx) { return ctx->n_pix; }
+
+int orc_set_window(orc_ctx* ctx, int v, int x0, int y0, int x1, int y1)
+{
+    if (v < 0 || v >= ctx->nv) return -1;
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > ctx->cams[v].width) x1 = ctx->cams[v].width;
+    if (y1 > ctx->cams[v].height) y1 = ctx->cams[v].height;
+    ctx->win[4 * v + 0] = x0;
+    ctx->win[4 * v + 1] = y0;
+    ctx->win[4 * v + 2] = x1 > x0 ? x1 : x0;
+    ctx->win[4 * v + 3] = y1 > y0 ? y1 : y0;
+    return 0;
+}
 
 void orc_get_proj(const orc_ctx* ctx, double* proj, float* bin32, int32_t* flags)
 {
@@ -535,8 +557,8 @@ int64_t orc_forward(orc_ctx* ctx, double* C, double* D, double* S, double* T_fin
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(threads) schedule(dynamic, 4) reduction(+ : vt)
 #endif
-        for (int py = 0; py < Ht; ++py)
-            for (int px = 0; px < Wd; ++px) {
+        for (int py = ctx->win[4 * v + 1]; py < ctx->win[4 * v + 3]; ++py)
+            for (int px = ctx->win[4 * v + 0]; px < ctx->win[4 * v + 2]; ++px) {
                 double out[5], Tf;
                 int32_t nc, ne;
                 uint8_t f;
@@ -714,8 +736,8 @@ void orc_backward(orc_ctx* ctx, const double* dCimg, const double* dDimg, const 
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 4)
 #endif
-            for (int py = 0; py < Ht; ++py)
-                for (int px = 0; px < Wd; ++px) {
+            for (int py = ctx->win[4 * v + 1]; py < ctx->win[4 * v + 3]; ++py)
+                for (int px = ctx->win[4 * v + 0]; px < ctx->win[4 * v + 2]; ++px) {
                     int64_t i = (int64_t)py * Wd + px;
                     double gp[5];
                     gp[0] = dCimg ? dCimg[3 * pb + i] : 0;

@@ -66,6 +66,13 @@ int64_t orc_n_pairs(const orc_ctx* ctx);
 int64_t orc_n_tiles(const orc_ctx* ctx);
 int64_t orc_n_pixels(const orc_ctx* ctx);
 
+/* Restrict compositing (forward and backward) of view v to the pixels
+ * [x0, x1) x [y0, y1) (clipped to the image); the others are skipped (their
+ * outputs untouched, their upstream gradients ignored).  Projection, culling
+ * and tile lists are those of the whole image.  Default: the whole image.
+ * Returns -1 for a bad view. */
+int orc_set_window(orc_ctx* ctx, int v, int x0, int y0, int x1, int y1);
+
 /* Per-slot projection results (slot = view * N + n); any pointer may be NULL.
  * proj: [slots][16] = u, v, depth, conic a, b, c, opacity, r, g, b, valid,
  *        radius, rect x0, y0, x1, y1.  bin32: [slots][3] = FP32 u, v, depth.

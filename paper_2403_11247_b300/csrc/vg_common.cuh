@@ -87,6 +87,38 @@ __device__ __forceinline__ void view_pose(const Views& V, int v, float T[12]) {
     }
 }
 
+// The 2D covariance of Eq. 3 plus the low-pass dilation, J W Sigma W^T J^T +
+// dil I, evaluated as M M^T + dil I with M = J W R diag(s) (2x3, rows m0,
+// m1; Sigma = (R diag(s)) (R diag(s))^T, RS = R diag(s)): A = |m0|^2 + dil,
+// B = m0.m1, C = |m1|^2 + dil, and the determinant by Lagrange's identity,
+// det = |m0 x m1|^2 + dil (|m0|^2 + |m1|^2) + dil^2, a sum of non-negative
+// terms (AC - B^2 cancels catastrophically for thin splats seen edge-on).
+// T is the row-major 3x4 world->camera pose (W = its 3x3 part).
+__device__ __forceinline__ void cov2d(float J00, float J02, float J11, float J12, const float T[12],
+                                      const float RS[3][3], float dil, float& A, float& B, float& C, float& det) {
+    float jw0[3], jw1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        jw0[c] = J00 * T[c] + J02 * T[8 + c];
+        jw1[c] = J11 * T[4 + c] + J12 * T[8 + c];
+    }
+    float m0[3], m1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        m0[c] = jw0[0] * RS[0][c] + jw0[1] * RS[1][c] + jw0[2] * RS[2][c];
+        m1[c] = jw1[0] * RS[0][c] + jw1[1] * RS[1][c] + jw1[2] * RS[2][c];
+    }
+    const float a0 = m0[0] * m0[0] + m0[1] * m0[1] + m0[2] * m0[2];
+    const float c0 = m1[0] * m1[0] + m1[1] * m1[1] + m1[2] * m1[2];
+    B = m0[0] * m1[0] + m0[1] * m1[1] + m0[2] * m1[2];
+    const float x0 = m0[1] * m1[2] - m0[2] * m1[1];
+    const float x1 = m0[2] * m1[0] - m0[0] * m1[2];
+    const float x2 = m0[0] * m1[1] - m0[1] * m1[0];
+    A = a0 + dil;
+    C = c0 + dil;
+    det = (x0 * x0 + x1 * x1 + x2 * x2) + dil * (a0 + c0) + dil * dil;
+}
+
 template <int D>
 __device__ __forceinline__ void decode_attr(const SceneDev& S, int g, int64_t n, float* out) {
     if (S.L[g] > 0) {

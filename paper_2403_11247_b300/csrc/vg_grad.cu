@@ -111,10 +111,12 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                 for (int r = 0; r < 3; ++r)
         #pragma unroll
                     for (int c = 0; c < 3; ++c) Sc[r][c] = T1[r][0] * W[c][0] + T1[r][1] * W[c][1] + T1[r][2] * W[c][2];
-                const float A = J00 * J00 * Sc[0][0] + 2.f * J00 * J02 * Sc[0][2] + J02 * J02 * Sc[2][2] + cs.dilation;
-                const float B = J00 * J11 * Sc[0][1] + J00 * J12 * Sc[0][2] + J02 * J11 * Sc[1][2] + J02 * J12 * Sc[2][2];
-                const float C = J11 * J11 * Sc[1][1] + 2.f * J11 * J12 * Sc[1][2] + J12 * J12 * Sc[2][2] + cs.dilation;
-                const float det = A * C - B * B;
+                float A, B, C, det, RS[3][3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) RS[r][c] = R[r][c] * s[c];
+                cov2d(J00, J02, J11, J12, T, RS, cs.dilation, A, B, C, det);
                 const float i2 = 1.f / (det * det);
                 const float da = g[2], db = g[3], dc = g[4];
                 // conic = inverse of [[A,B],[B,C]]

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
     uint32_t n_vis = 0;
     float mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, ol = 0.f, rgb[3] = {0, 0, 0};
     bool active = false;
-    float Sig[6] = {0, 0, 0, 0, 0, 0};  // xx xy xz yy yz zz
+    float RS[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // R diag(s): Sigma = RS RS^T
     float opac = 0.f;
     if (live) {
         anchor_mean(S, n, mu);
@@ -68,18 +68,12 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
             float qn[4] = {q[0] * qn_inv, q[1] * qn_inv, q[2] * qn_inv, q[3] * qn_inv};
             float R[3][3];
             quat_rot(qn, R);
-            float s2[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                float s = expf(ls[c]);
-                s2[c] = s * s;
+                const float sc = expf(ls[c]);
+#pragma unroll
+                for (int r = 0; r < 3; ++r) RS[r][c] = R[r][c] * sc;
             }
-            Sig[0] = R[0][0] * R[0][0] * s2[0] + R[0][1] * R[0][1] * s2[1] + R[0][2] * R[0][2] * s2[2];
-            Sig[1] = R[0][0] * R[1][0] * s2[0] + R[0][1] * R[1][1] * s2[1] + R[0][2] * R[1][2] * s2[2];
-            Sig[2] = R[0][0] * R[2][0] * s2[0] + R[0][1] * R[2][1] * s2[1] + R[0][2] * R[2][2] * s2[2];
-            Sig[3] = R[1][0] * R[1][0] * s2[0] + R[1][1] * R[1][1] * s2[1] + R[1][2] * R[1][2] * s2[2];
-            Sig[4] = R[1][0] * R[2][0] * s2[0] + R[1][1] * R[2][1] * s2[1] + R[1][2] * R[2][2] * s2[2];
-            Sig[5] = R[2][0] * R[2][0] * s2[0] + R[2][1] * R[2][1] * s2[1] + R[2][2] * R[2][2] * s2[2];
             opac = 1.f / (1.f + expf(-ol));
         }
     }
@@ -110,24 +104,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
                     }
                     const float J00 = vi.fx / z, J02 = -vi.fx * txz / z;
                     const float J11 = vi.fy / z, J12 = -vi.fy * tyz / z;
-                    // Sc = W Sigma W^T
-                    float W[3][3] = {{T[0], T[1], T[2]}, {T[4], T[5], T[6]}, {T[8], T[9], T[10]}};
-                    float Sm[3][3] = {{Sig[0], Sig[1], Sig[2]}, {Sig[1], Sig[3], Sig[4]}, {Sig[2], Sig[4], Sig[5]}};
-                    float T1[3][3], Sc[3][3];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc)
-                            T1[r][cc] = W[r][0] * Sm[0][cc] + W[r][1] * Sm[1][cc] + W[r][2] * Sm[2][cc];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc)
-                            Sc[r][cc] = T1[r][0] * W[cc][0] + T1[r][1] * W[cc][1] + T1[r][2] * W[cc][2];
-                    const float A = J00 * J00 * Sc[0][0] + 2.f * J00 * J02 * Sc[0][2] + J02 * J02 * Sc[2][2] + cs.dilation;
-                    const float B = J00 * J11 * Sc[0][1] + J00 * J12 * Sc[0][2] + J02 * J11 * Sc[1][2] + J02 * J12 * Sc[2][2];
-                    const float C = J11 * J11 * Sc[1][1] + 2.f * J11 * J12 * Sc[1][2] + J12 * J12 * Sc[2][2] + cs.dilation;
-                    const float det = A * C - B * B;
+                    float A, B, C, det;
+                    cov2d(J00, J02, J11, J12, T, RS, cs.dilation, A, B, C, det);
                     ok = det > 0.f;
                     if (ok) {
                         const float inv = 1.f / det;
@@ -144,8 +122,9 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
                             ex = sqrtf(tau * A) * 1.0001f + 1e-3f;
                             ey = sqrtf(tau * C) * 1.0001f + 1e-3f;
                         }
-                        const float mid = 0.5f * (A + C);
-                        const float lam = mid + sqrtf(fmaxf(0.f, mid * mid - det));
+                        // largest eigenvalue; mid^2 - det written as a sum of squares
+                        const float mid = 0.5f * (A + C), hd = 0.5f * (A - C);
+                        const float lam = mid + sqrtf(hd * hd + B * B);
                         float rr = cs.sigma_cull * sqrtf(lam);
                         int radius = (rr < (float)RADIUS_MAX) ? (int)ceilf(rr) : RADIUS_MAX;
                         const float rf = (float)radius;

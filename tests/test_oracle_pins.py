@@ -574,3 +574,80 @@ def test_loss_l1_matches_definition():
     Lg, dCg, _ = O.loss_l1(C_, D_, S_, Ct, Dt, 0.5, gate=0.99)
     gate = np.tile(S_ > 0.99, 3)
     assert np.allclose(dCg, np.where(gate, np.sign(C_ - Ct) / (3 * n), 0))
+
+
+# ---------------------------------------------------------------------------
+# exact identities of the reverse mode
+# ---------------------------------------------------------------------------
+
+def _decoded_raw_twin(coded_scene):
+    """The same scene with every coded group replaced by its decoded values
+    (numpy gather-sum, not the oracle's decode)."""
+    groups = {}
+    for name, g in coded_scene.groups.items():
+        if g.coded:
+            dec = sum(g.codebook[s][g.idx[s].astype(np.int64)] for s in range(g.codebook.shape[0]))
+            groups[name] = synth.Group(g.dim, raw=dec.astype(np.float32))
+        else:
+            groups[name] = g
+    return synth.Scene(coded_scene.anchor_xyz, coded_scene.anchor_l, coded_scene.offsets, groups,
+                       coded_scene.mask_logit, coded_scene.mask_eps)
+
+
+def test_codebook_gradient_is_the_scatter_sum_of_attribute_gradients():
+    """dL/dC^s[k] = sum of dL/dattr_n over the Gaussians whose stage-s index
+    is k (Eq. 14 is a sum of gathers), checked against the per-Gaussian
+    gradients of the decoded twin scene."""
+    sc = synth.room_scene(seed=1002, n_anchors=600)
+    cams = [synth.room_camera(96, 64, 48.0)]
+    ups = synth.upstream_grads(5, 96 * 64, scale=1.0)
+    g_coded = O.Oracle(sc, cams).backward(*ups)
+    g_raw = O.Oracle(_decoded_raw_twin(sc), cams).backward(*ups)
+    for name, g in sc.groups.items():
+        per_gauss = np.asarray(g_raw[name], np.float64)
+        L, K, d = g.codebook.shape
+        want = np.zeros((L, K, d))
+        for s in range(L):
+            np.add.at(want[s], g.idx[s].astype(np.int64), per_gauss)
+        got = np.asarray(g_coded[name], np.float64)
+        # the twin's attributes are the FP32 rounding of the FP64 decode
+        assert np.abs(got - want).max() <= 1e-6 * np.abs(want).max(), name
+
+
+def test_translational_pose_gradient_is_the_rotated_sum_of_mean_gradients():
+    """d/d rho of L(exp(xi^) T_cw) at 0 = sum_n dL/dp_c,n = R_cw sum_n dL/dmu_n,
+    and sum_n dL/dmu_n = sum over anchors of dL/dx_a (Eq. 7)."""
+    sc = synth.room_scene(seed=1002, n_anchors=800)
+    cams = [synth.room_camera(96, 64, 48.0, pose_seed=3, jitter_deg=5.0, jitter_m=0.1)]
+    o = O.Oracle(sc, cams)
+    g = o.backward(*synth.upstream_grads(6, 96 * 64, scale=1.0))
+    R = np.asarray(cams[0].T_cw, np.float64)[:, :3]
+    want = R @ np.asarray(g["anchor_xyz"], np.float64).sum(axis=0)
+    got = np.asarray(g["pose"], np.float64)[0][:3]
+    # exact up to R R^T = I for the FP32 rotation (~1e-7)
+    assert np.abs(got - want).max() <= 1e-6 * np.abs(want).max(), (got, want)
+
+
+def test_window_restricts_compositing_to_its_pixels():
+    """A window composites exactly the whole-image values inside it and
+    nothing outside; its backward equals the whole-image backward of
+    upstream gradients that vanish outside it."""
+    sc = synth.tiny_scene()
+    cams = [synth.tiny_camera()]
+    full = O.Oracle(sc, cams)
+    f = full.forward()
+    o = O.Oracle(sc, cams)
+    o.set_window(0, 16, 16, 48, 32)
+    w = o.forward()
+    W, H = cams[0].width, cams[0].height
+    inside = np.zeros((H, W), bool)
+    inside[16:32, 16:48] = True
+    m = inside.ravel()
+    assert np.array_equal(w["S"][m], f["S"][m]) and np.all(w["S"][~m] == 0)
+    assert np.array_equal(w["C"][np.tile(m, 3)], f["C"][np.tile(m, 3)])
+    ups = synth.upstream_grads(8, W * H, scale=1.0)
+    ups_in = [ups[0] * np.tile(m, 3), ups[1] * m, ups[2] * m]
+    gw = o.backward(*ups)
+    gf = full.backward(*ups_in)
+    for k in gf:
+        assert np.allclose(np.asarray(gw[k]), np.asarray(gf[k]), rtol=1e-12, atol=1e-15), k
