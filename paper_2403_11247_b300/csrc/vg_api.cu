@@ -695,8 +695,7 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     if (ctx->g2d.bytes < (size_t)slots * G2D_STRIDE * 4) ctx->g2d_clean = false;
     VG_TRY(ctx->g2d.ensure(slots * G2D_STRIDE * 4, st, "g2d"));
 
-    const int nb = chain_blocks(N);
-    VG_TRY(ctx->pose_part.ensure((size_t)n_views * nb * 6 * 4, st, "pose partials"));
+    VG_TRY(ctx->pose_part.ensure((size_t)n_views * 6 * 4, st, "pose sums"));
     float* gptr[4] = {grads->logscale, grads->rot, grads->opacity, grads->rgb};
 
     // the scene-gradient arrays the chain accumulates into, zeroed together
@@ -724,7 +723,8 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     O.d_l = grads->anchor_l;
     O.d_off = grads->offsets;
     O.d_mask = sd.mask ? grads->mask_logit : nullptr;
-    O.pose_part = ctx->pose_part.as<float>();
+    O.pose_sum = ctx->pose_part.as<float>();
+    zero(O.pose_sum, (int64_t)n_views * 6);
     zero(grads->anchor_xyz, sd.n_anchors * 3);
     zero(grads->anchor_l, sd.n_anchors * 3);
     zero(grads->offsets, N * 3);
@@ -773,8 +773,8 @@ vg_status vg_pose_grad(vg_ctx* ctx, int32_t n_views, const float* icp_q, const f
     } else if (icp_loss) {
         VG_CUDA(cudaMemsetAsync(icp_loss, 0, (size_t)n_views * 4, st));
     }
-    VG_STAGE(VG_STAGE_POSE, launch_pose_final(n_views, ctx->pose_part.as<float>(), ctx->pose_blocks, icp_part, nbi,
-                                              dxi, icp_q ? icp_loss : nullptr, st));
+    VG_STAGE(VG_STAGE_POSE, launch_pose_final(n_views, ctx->pose_part.as<float>(), icp_part, nbi, dxi,
+                                              icp_q ? icp_loss : nullptr, st));
     return VG_OK;
 }
 

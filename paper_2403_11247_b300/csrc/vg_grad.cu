@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
     }
     __syncthreads();
     for (int i = threadIdx.x; i < V.n * 6; i += blockDim.x)
-        O.pose_part[((int64_t)(i / 6) * gridDim.x + blockIdx.x) * 6 + i % 6] = s_pose[i];
+        if (s_pose[i] != 0.f) atomicAdd(O.pose_sum + i, s_pose[i]);
     if (O.cb_in_smem) {
         for (int gi = 0; gi < 4; ++gi) {
             if (S.L[gi] <= 0 || !O.cb[gi]) continue;
@@ -404,28 +404,30 @@ cudaError_t launch_icp(const SceneDev& S, const Views& V, const float* q, const 
     return cudaGetLastError();
 }
 
-__global__ void pose_final_kernel(const float* __restrict__ pose_part, int nb, const float* __restrict__ icp_part,
-                                  int nbi, float* __restrict__ dxi, float* __restrict__ icp_loss) {
+// dxi = the chain's pose sums (+ the ICP term's block partials, if any)
+__global__ void pose_final_kernel(const float* __restrict__ pose_sum, const float* __restrict__ icp_part, int nbi,
+                                  float* __restrict__ dxi, float* __restrict__ icp_loss) {
     __shared__ float s_tmp[8];
     const int v = blockIdx.x;
+    if (!icp_part) {
+        if (threadIdx.x < 6) dxi[v * 6 + threadIdx.x] = pose_sum[v * 6 + threadIdx.x];
+        return;
+    }
     for (int c = 0; c < 7; ++c) {
         float acc = 0.f;
-        if (c < 6)
-            for (int j = threadIdx.x; j < nb; j += blockDim.x) acc += pose_part[((int64_t)v * nb + j) * 6 + c];
-        if (icp_part)
-            for (int j = threadIdx.x; j < nbi; j += blockDim.x) acc += icp_part[((int64_t)v * nbi + j) * 7 + c];
+        for (int j = threadIdx.x; j < nbi; j += blockDim.x) acc += icp_part[((int64_t)v * nbi + j) * 7 + c];
         const float t = block_sum_256(acc, s_tmp);
         if (threadIdx.x == 0) {
-            if (c < 6) dxi[v * 6 + c] = t;
+            if (c < 6) dxi[v * 6 + c] = pose_sum[v * 6 + c] + t;
             else if (icp_loss) icp_loss[v] = t;
         }
     }
 }
 
-cudaError_t launch_pose_final(int n_views, const float* pose_part, int nb, const float* icp_part, int nbi, float* dxi,
+cudaError_t launch_pose_final(int n_views, const float* pose_sum, const float* icp_part, int nbi, float* dxi,
                               float* icp_loss, cudaStream_t st) {
     count_launches(1);
-    pose_final_kernel<<<n_views, 256, 0, st>>>(pose_part, nb, icp_part, nbi, dxi, icp_loss);
+    pose_final_kernel<<<n_views, icp_part ? 256 : 32, 0, st>>>(pose_sum, icp_part, nbi, dxi, icp_loss);
     return cudaGetLastError();
 }
 
@@ -434,39 +436,84 @@ cudaError_t launch_pose_final(int n_views, const float* pose_part, int nb, const
 // ---------------------------------------------------------------------------
 __global__ void count_valid_kernel(const float* __restrict__ Dt, int64_t n, uint32_t* count) {
     uint32_t c = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        c += Dt[i] > 0.f;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthr = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = (reinterpret_cast<uintptr_t>(Dt) & 15u) == 0 ? n / 4 : 0;
+    for (int64_t i = tid; i < n4; i += nthr) {
+        const float4 d = reinterpret_cast<const float4*>(Dt)[i];
+        c += (d.x > 0.f) + (d.y > 0.f) + (d.z > 0.f) + (d.w > 0.f);
+    }
+    for (int64_t i = n4 * 4 + tid; i < n; i += nthr) c += Dt[i] > 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
+// one pixel of the loss: colour residuals of the three planes, depth residual
+__device__ __forceinline__ float loss_pixel(float c0, float c1, float c2, float t0, float t1, float t2, float d,
+                                            float dt, float s, float gate, float inv_c, float inv_d, float& g0,
+                                            float& g1, float& g2, float& gd) {
+    const float m = (gate >= 0.f && !(s > gate)) ? 0.f : 1.f;
+    const float r0 = c0 - t0, r1 = c1 - t1, r2 = c2 - t2, rd = d - dt;
+    auto sgn = [](float r) { return (r > 0.f) ? 1.f : ((r < 0.f) ? -1.f : 0.f); };
+    g0 = m * sgn(r0) * inv_c;
+    g1 = m * sgn(r1) * inv_c;
+    g2 = m * sgn(r2) * inv_c;
+    const bool valid = dt > 0.f;
+    gd = valid ? m * sgn(rd) * inv_d : 0.f;
+    return m * (fabsf(r0) + fabsf(r1) + fabsf(r2)) * inv_c + (valid ? m * fabsf(rd) * inv_d : 0.f);
+}
+
 __global__ void loss_l1_kernel(int64_t n_pix, int64_t total, const float* __restrict__ C, const float* __restrict__ D,
                                const float* __restrict__ S, const float* __restrict__ Ct, const float* __restrict__ Dt,
                                float w_depth, float gate, const uint32_t* __restrict__ valid_count,
-                               float* __restrict__ dC, float* __restrict__ dD, float* __restrict__ loss) {
+                               float* __restrict__ dC, float* __restrict__ dD, float* __restrict__ loss, int vec) {
     __shared__ float s_tmp[8];
     const float nv = (float)(*valid_count);
     const float inv_c = 1.f / (3.f * (float)total);
     const float inv_d = nv > 0.f ? w_depth / nv : 0.f;
     float acc = 0.f;
     const int64_t v = blockIdx.y;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pix; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = v * n_pix + i;
-        const float m = (gate >= 0.f && !(S[e] > gate)) ? 0.f : 1.f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int64_t k = (v * 3 + c) * n_pix + i;
-            const float r = C[k] - Ct[k];
-            const float sg = (r > 0.f) ? 1.f : ((r < 0.f) ? -1.f : 0.f);
-            dC[k] = m * sg * inv_c;
-            acc += m * fabsf(r) * inv_c;
-        }
-        const float rd = D[e] - Dt[e];
-        const bool valid = Dt[e] > 0.f;
-        const float sd = (rd > 0.f) ? 1.f : ((rd < 0.f) ? -1.f : 0.f);
-        dD[e] = valid ? m * sd * inv_d : 0.f;
-        acc += valid ? m * fabsf(rd) * inv_d : 0.f;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthr = (int64_t)gridDim.x * blockDim.x;
+    const float* c0p = C + (v * 3 + 0) * n_pix;
+    const float* c1p = C + (v * 3 + 1) * n_pix;
+    const float* c2p = C + (v * 3 + 2) * n_pix;
+    const float* t0p = Ct + (v * 3 + 0) * n_pix;
+    const float* t1p = Ct + (v * 3 + 1) * n_pix;
+    const float* t2p = Ct + (v * 3 + 2) * n_pix;
+    const float* dp = D + v * n_pix;
+    const float* dtp = Dt + v * n_pix;
+    const float* sp = S + v * n_pix;
+    float* g0p = dC + (v * 3 + 0) * n_pix;
+    float* g1p = dC + (v * 3 + 1) * n_pix;
+    float* g2p = dC + (v * 3 + 2) * n_pix;
+    float* gdp = dD + v * n_pix;
+    const int64_t n4 = vec ? n_pix / 4 : 0;  // four pixels per step where every plane is 16-byte aligned
+    for (int64_t i = tid; i < n4; i += nthr) {
+        const float4 c0 = reinterpret_cast<const float4*>(c0p)[i], c1 = reinterpret_cast<const float4*>(c1p)[i],
+                     c2 = reinterpret_cast<const float4*>(c2p)[i];
+        const float4 t0 = reinterpret_cast<const float4*>(t0p)[i], t1 = reinterpret_cast<const float4*>(t1p)[i],
+                     t2 = reinterpret_cast<const float4*>(t2p)[i];
+        const float4 d = reinterpret_cast<const float4*>(dp)[i], dt = reinterpret_cast<const float4*>(dtp)[i];
+        float4 s = make_float4(1.f, 1.f, 1.f, 1.f);
+        if (gate >= 0.f) s = reinterpret_cast<const float4*>(sp)[i];
+        float4 g0, g1, g2, gd;
+        acc += loss_pixel(c0.x, c1.x, c2.x, t0.x, t1.x, t2.x, d.x, dt.x, s.x, gate, inv_c, inv_d, g0.x, g1.x, g2.x, gd.x);
+        acc += loss_pixel(c0.y, c1.y, c2.y, t0.y, t1.y, t2.y, d.y, dt.y, s.y, gate, inv_c, inv_d, g0.y, g1.y, g2.y, gd.y);
+        acc += loss_pixel(c0.z, c1.z, c2.z, t0.z, t1.z, t2.z, d.z, dt.z, s.z, gate, inv_c, inv_d, g0.z, g1.z, g2.z, gd.z);
+        acc += loss_pixel(c0.w, c1.w, c2.w, t0.w, t1.w, t2.w, d.w, dt.w, s.w, gate, inv_c, inv_d, g0.w, g1.w, g2.w, gd.w);
+        reinterpret_cast<float4*>(g0p)[i] = g0;
+        reinterpret_cast<float4*>(g1p)[i] = g1;
+        reinterpret_cast<float4*>(g2p)[i] = g2;
+        reinterpret_cast<float4*>(gdp)[i] = gd;
+    }
+    for (int64_t i = n4 * 4 + tid; i < n_pix; i += nthr) {
+        float g0, g1, g2, gd;
+        acc += loss_pixel(c0p[i], c1p[i], c2p[i], t0p[i], t1p[i], t2p[i], dp[i], dtp[i], gate >= 0.f ? sp[i] : 1.f, gate,
+                          inv_c, inv_d, g0, g1, g2, gd);
+        g0p[i] = g0;
+        g1p[i] = g1;
+        g2p[i] = g2;
+        gdp[i] = gd;
     }
     const float t = block_sum_256(acc, s_tmp);
     if (threadIdx.x == 0) atomicAdd(loss, t);
@@ -476,14 +523,16 @@ cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const flo
                            const float* Dt, float w_depth, float gate, float* dC, float* dD, float* loss,
                            uint32_t* valid_count, cudaStream_t st) {
     const int64_t total = (int64_t)n_views * n_pix;
-    int64_t blocks = ceil_div(total > 0 ? total : 1, 256);
+    int64_t blocks = ceil_div(ceil_div(total > 0 ? total : 1, 4), 256);
     if (blocks > 148 * 8) blocks = 148 * 8;
     count_launches(2);
     count_valid_kernel<<<(unsigned)blocks, 256, 0, st>>>(Dt, total, valid_count);
-    int64_t bx = ceil_div(n_pix, 256);
+    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    const int vec = (n_pix % 4 == 0) && al(C) && al(D) && al(Ct) && al(Dt) && al(dC) && al(dD) && (gate < 0.f || al(S));
+    int64_t bx = ceil_div(vec ? ceil_div(n_pix, 4) : n_pix, 256);
     if (bx > 148 * 8) bx = 148 * 8;
     loss_l1_kernel<<<dim3((unsigned)bx, (unsigned)n_views), 256, 0, st>>>(n_pix, total, C, D, S, Ct, Dt, w_depth, gate,
-                                                                          valid_count, dC, dD, loss);
+                                                                          valid_count, dC, dD, loss, vec);
     return cudaGetLastError();
 }
 

@@ -94,7 +94,7 @@ struct ChainOut {
     float* raw[4];   // per-Gaussian attribute gradients of uncoded groups [N][d]
     float* cb[4];    // codebook gradients of coded groups [L][K][d]
     float *d_xyz, *d_l, *d_off, *d_mask;
-    float* pose_part;  // [views][chain blocks][6]
+    float* pose_sum;   // [views][6], zeroed before the backward
     int32_t cb_off[4], cb_total, cb_in_smem;
 };
 // arrays the zeroing kernel clears before the backward
@@ -111,8 +111,8 @@ int chain_blocks(int64_t N);
 cudaError_t launch_icp(const SceneDev& S, const Views& V, const float* q, const float* w, float* part, int n_blocks,
                        cudaStream_t st);
 int icp_blocks(int64_t N);
-cudaError_t launch_pose_final(int n_views, const float* pose_part, int n_pose_blocks, const float* icp_part,
-                              int n_icp_blocks, float* dxi, float* icp_loss, cudaStream_t st);
+cudaError_t launch_pose_final(int n_views, const float* pose_sum, const float* icp_part, int n_icp_blocks,
+                              float* dxi, float* icp_loss, cudaStream_t st);
 cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const float* D, const float* S,
                            const float* Ct, const float* Dt, float w_depth, float gate, float* dC, float* dD,
                            float* loss, uint32_t* valid_count, cudaStream_t st);
