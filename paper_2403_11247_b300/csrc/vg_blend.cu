@@ -58,10 +58,35 @@ __device__ __forceinline__ void warp_rect(int tx, int ty, int w, float& X0, floa
     Y1 = Y0 + (float)(R::H - 1);
 }
 
-// does the box [X0, X1] x [Y0, Y1] meet the Gaussian's alpha box?
-__device__ __forceinline__ bool warp_hits(const float4 g, float X0, float X1, float Y0, float Y1) {
+// can a pixel of [X0, X1] x [Y0, Y1] have alpha >= alpha_min for this
+// Gaussian?  First its alpha box, then the ellipse itself: the base-2
+// exponent p2(dx, dy) = A2 dx^2 + B2 dx dy + C2 dy^2 (dx = u - px, dy = v - py,
+// concave) must reach thr somewhere on the rectangle.  Its maximum there is 0
+// if the centre lies inside, else it lies on an edge facing the centre,
+// where p2 is a concave parabola in the free coordinate (vertex clamped to
+// the edge).  The margin covers FP32 rounding of the pixels' own tests, so a
+// pixel that passes is never culled.
+__device__ __forceinline__ bool warp_hits(const float4 g, const float4 co, float X0, float X1, float Y0, float Y1) {
     const float cx = fminf(fmaxf(g.x, X0), X1), cy = fminf(fmaxf(g.y, Y0), Y1);
-    return fabsf(g.x - cx) <= g.z && fabsf(g.y - cy) <= g.w;
+    if (!(fabsf(g.x - cx) <= g.z && fabsf(g.y - cy) <= g.w)) return false;
+    if (cx == g.x && cy == g.y) return true;
+    // each candidate is raised by 1e-5 of its terms' magnitudes: FP32
+    // rounding of a pixel's own p2 is far smaller, even where the terms of a
+    // thin ellipse cancel
+    auto p2up = [&](float dx, float dy) {
+        const float t1 = co.x * dx * dx, t2 = co.y * dx * dy, t3 = co.z * dy * dy;
+        return (t1 + t2 + t3) + 1e-5f * (fabsf(t1) + fabsf(t2) + fabsf(t3));
+    };
+    float best = -INFINITY;
+    if (cx != g.x) {  // edge px = cx, dy over [v - Y1, v - Y0]
+        const float dx = g.x - cx;
+        best = fmaxf(best, p2up(dx, fminf(fmaxf(-co.y * dx / (2.f * co.z), g.y - Y1), g.y - Y0)));
+    }
+    if (cy != g.y) {  // edge py = cy, dx over [u - X1, u - X0]
+        const float dy = g.y - cy;
+        best = fmaxf(best, p2up(fminf(fmaxf(-co.y * dy / (2.f * co.x), g.x - X1), g.x - X0), dy));
+    }
+    return best >= co.w - (1e-3f + 1e-3f * fabsf(co.w));
 }
 
 template <int PPT>
@@ -131,7 +156,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
             if (__all_sync(0xffffffffu, wdone)) break;
             // each lane tests one Gaussian of the chunk against the warp's pixels
             const int il = c0 + lane;
-            uint32_t m = __ballot_sync(0xffffffffu, il < cnt && warp_hits(s_xy[il], X0, X1, Y0, Y1));
+            uint32_t m = __ballot_sync(0xffffffffu, il < cnt && warp_hits(s_xy[il], s_co[il], X0, X1, Y0, Y1));
             while (m) {
                 const int i = c0 + __ffs(m) - 1;
                 m &= m - 1;
@@ -317,7 +342,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
             // back to front (highest set bit first)
             const int il = c0 + lane;
             const bool hit = il < c1 && (bstart - rg.x + (uint32_t)il) < warp_max &&
-                             warp_hits(s_xy[il], X0, X1, Y0, Y1);
+                             warp_hits(s_xy[il], s_co[il], X0, X1, Y0, Y1);
             uint32_t m = __ballot_sync(0xffffffffu, hit);
             while (m) {
                 const int hb = 31 - __clz(m);
