@@ -46,8 +46,8 @@ BWD_FLOP_BLEND = 49       # per blended pair: T recovery, dL/dalpha, colour/dept
 # capture of this workload (profiles/step_kernels__mapping_1200x680.md), valid
 # while the kernels' sources hash to the value they had when captured
 BLEND_SOURCES = ("paper_2403_11247_b300/csrc/vg_blend.cu", "paper_2403_11247_b300/csrc/vg_common.cuh")
-NCU_TRAFFIC = {"blend_bwd": ("b9ce6b01e25e3adf", 24.431872e6 + 0.0),
-               "blend_fwd": ("b9ce6b01e25e3adf", 3.941888e6 + 6.144e3)}
+NCU_TRAFFIC = {"blend_bwd": ("e7901a4f47fbfe19", 24.429824e6 + 0.0),
+               "blend_fwd": ("e7901a4f47fbfe19", 3.186944e6 + 0.0)}
 
 
 def ncu_traffic(stage: str):
@@ -411,6 +411,114 @@ def large_leg(torch, V, synth, steps=20):
     return res
 
 
+def time_gpu_step(torch, V, sh, cams, Ct, Dt, reps=20):
+    """Median ms of one graph-replayed fwd + L1 loss gradient + bwd + pose
+    gradient over `cams` (one launch sequence)."""
+    ctx = V.vg_ctx_create(0)
+    params = V.default_params()
+    V.render_with_retry(sh, cams, params, ctx)
+    V.vg_ctx_reserve(ctx, int(V.vg_ctx_stats(ctx)["pairs"] * 1.3) + 4096)
+    P = cams[0].width * cams[0].height
+    B = len(cams)
+    f32 = dict(dtype=torch.float32, device="cuda")
+    C_, D, S = torch.empty(3 * B * P, **f32), torch.empty(B * P, **f32), torch.empty(B * P, **f32)
+    dC, dD, loss = torch.empty(3 * B * P, **f32), torch.empty(B * P, **f32), torch.empty(1, **f32)
+    dxi = torch.empty((B, 6), **f32)
+    grads = V.grads_like(sh)
+
+    def step():
+        V.vg_render_fwd(sh, cams, params, ctx, C_, D, S)
+        V.vg_loss_l1(B, P, C_, D, S, Ct, Dt, 0.5, -1.0, ctx, dC=dC, dD=dD, loss=loss)
+        V.vg_render_bwd(sh, cams, params, ctx, dC, dD, None, grads)
+        V.vg_pose_grad(ctx, B, dxi=dxi)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="thread_local"):
+        step()
+    times = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    if V.vg_check(ctx) != V.VG_OK:
+        raise RuntimeError("device status not OK")
+    return statistics.median(times)
+
+
+def time_oracle_iter(O, scene, cams, target, threads, window=None, runs=3):
+    """Median seconds of one oracle iteration (decode, project, bin, forward,
+    L1 loss gradient, backward); with `window` = (x0, y0, x1, y1) only that
+    part of every view is composited and the time is scaled to whole images
+    (compositing share by pixel fraction, the rest as measured)."""
+    import numpy as np
+    ts = []
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        o = O.Oracle(scene, cams)
+        t1 = time.perf_counter()
+        if window is not None:
+            for v in range(len(cams)):
+                o.set_window(v, *window)
+        f = o.forward(threads=threads)
+        _, dC, dD = O.loss_l1(f["C"], f["D"], f["S"], target["C"], target["D"], 0.5)
+        o.backward(dC, dD, np.zeros_like(f["S"]), threads=threads)
+        t2 = time.perf_counter()
+        comp = t2 - t1
+        if window is not None:
+            frac = (window[2] - window[0]) * (window[3] - window[1]) / float(cams[0].width * cams[0].height)
+            comp /= frac
+        ts.append((t1 - t0) + comp)
+    return statistics.median(ts)
+
+
+def configs_table(torch, V, synth, threads):
+    """GPU step times and oracle iteration times (one thread and all
+    threads) for the five configurations."""
+    from oracle import oracle as O
+    O.build()
+    out = {}
+    rows = [
+        ("1 tiny", synth.tiny_scene(), [synth.tiny_camera()], None),
+        ("2 mapping", synth.room_scene(), [synth.room_camera()], None),
+        ("3 track + local BA window", synth.tiny_scene(),
+         synth.keyframe_cameras(n_views=8, width=640, height=480, f=500.0, perturbed=True), None),
+        ("5 large", synth.large_scene(), synth.large_cameras(), (896, 480, 1024, 560)),
+    ]
+    for name, sc, cams, window in rows:
+        sh = V.vg_scene_upload(sc)
+        ctx = V.vg_ctx_create(0)
+        tcams = [synth.camera(c.fx, c.fy, c.cx, c.cy, c.width, c.height,
+                              synth.perturb_pose(c.T_cw, np.random.default_rng(7 + i), 1.0, 0.02), c.near)
+                 for i, c in enumerate(cams)]
+        Ct, Dt, _ = V.render_with_retry(sh, tcams, V.default_params(), ctx)
+        ms = time_gpu_step(torch, V, sh, cams, Ct.clone(), Dt.clone())
+        pix = sum(c.width * c.height for c in cams)
+        row = {"gaussians": int(sc.n), "views": len(cams), "size": f"{cams[0].width}x{cams[0].height}",
+               "gpu_ms_per_iter": ms, "gpu_iters_per_s": 1000.0 / ms, "gpu_mpix_per_s": pix / ms / 1e3}
+        target = {"C": Ct.double().cpu().numpy(), "D": Dt.double().cpu().numpy()}
+        if window is None:
+            row["oracle_s_per_iter_1thread"] = time_oracle_iter(O, sc, cams, target, 1, runs=1 if sc.n > 10000 else 3)
+            row["oracle_s_per_iter_all"] = time_oracle_iter(O, sc, cams, target, threads)
+        else:
+            P1 = cams[0].width * cams[0].height
+            t1 = {"C": target["C"][:3 * P1], "D": target["D"][:P1]}
+            row["oracle_s_per_iter_all"] = len(cams) * time_oracle_iter(O, sc, cams[:1], t1, threads, window=window,
+                                                                        runs=1)
+            row["oracle_sample"] = (f"view 0 only, times {len(cams)} views; composited window {window}, "
+                                    f"compositing time scaled by the pixel fraction")
+        row["oracle_threads"] = threads
+        out[name] = row
+        log(f"config {name}: GPU {ms:.3f} ms/iter; oracle {row.get('oracle_s_per_iter_1thread', float('nan')):.2f} "
+            f"s (1 thread), {row['oracle_s_per_iter_all']:.2f} s ({threads} threads)")
+    return out
+
+
 def run_reference(args):
     rank, world, _ = env_dist()
     if rank != 0:
@@ -620,6 +728,11 @@ def run_ours(args):
                            % (n_sm, sm_mhz, src)) if roof["bound"] == "alu" else f"{src} hbm_gbs"
     roof["ms_per_launch"] = per_launch_s * 1000.0
 
+    # measured throughput of the units the derived peaks assume (probes)
+    probes = V.probe_peaks()
+    roof["probe_fp32_tflops"] = probes["fma"]["value"]
+    roof["probe_frac"] = roof["achieved"] / probes["fma"]["value"] if roof["bound"] == "alu" else None
+
     # the same step as plain launches (no graph), same L2 flush between steps
     eager = None
     if graph is not None:
@@ -698,6 +811,9 @@ def run_ours(args):
         O.build()
         cpu = cpu_baseline(O, synth, w["scene"], w["cam"], w["tcam"])
 
+    table = None
+    if rank == 0 and args.configs:
+        table = configs_table(torch, V, synth, os.cpu_count() or 1)
     serving = ba_res = large = None
     if rank == 0 and not args.no_large:
         large = large_leg(torch, V, synth)
@@ -720,7 +836,10 @@ def run_ours(args):
                 "p50_step_ms": statistics.median(step_ms), "p10_step_ms": float(np.percentile(step_ms, 10)),
                 "p90_step_ms": float(np.percentile(step_ms, 90)), "p99_step_ms": float(np.percentile(step_ms, 99)),
                 "plain_launches": eager,
-                "serving": serving, "local_ba": ba_res, "large_scene": large}
+                "serving": serving, "local_ba": ba_res, "large_scene": large, "configs_table": table,
+                "peak_probes": {k: {"value": v["value"], "unit": v["unit"]} for k, v in probes.items()},
+                "derived_peaks": {"fp32_tflops": alu_peak, "ex2_g_per_s": n_sm * 16 * sm_mhz * 1e6 / 1e9,
+                                  "smem_tb_per_s": n_sm * 128 * sm_mhz * 1e6 / 1e12}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -743,6 +862,8 @@ def main():
     ap.add_argument("--serving-seconds", type=float, default=2.0, help="length of each Poisson trace")
     ap.add_argument("--no-local-ba", action="store_true", help="skip the local bundle-adjustment leg")
     ap.add_argument("--no-large", action="store_true", help="skip the large-scene leg")
+    ap.add_argument("--configs", action="store_true",
+                    help="also time every configuration on the GPU and the oracle (minutes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

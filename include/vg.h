@@ -340,6 +340,21 @@ vg_status vg_loss_l1_noalloc(int32_t n_views, int64_t n_pix, const float* C, con
                              const float* Ct, const float* Dt, float w_depth, float gate,
                              float* dC, float* dD, float* dS, float* loss, vg_stream stream);
 
+/* Throughput probe for roofline denominators (a measurement facility; the
+ * paper has no counterpart).  Enqueues one kernel on `stream` over a grid of
+ * (SM count x 8) blocks of 256 threads, each thread running `iters` steps of:
+ *   kind 0: 8 independent FP32 fused multiply-adds  (units: FLOP, FMA = 2)
+ *   kind 1: 8 independent base-2 exponentials       (units: exponentials)
+ *   kind 2: one conflict-free 16-byte shared load   (units: bytes)
+ *   kind 3: one float atomic add, a distinct address per thread (units: atomics)
+ *   kind 4: one float atomic add, one address per warp          (units: atomics)
+ * and writes to *units the work the launch does; time it with events on
+ * `stream`.  `buf` is a device array of at least buf_floats >= grid threads
+ * floats (kinds 3-4 add into it; kinds 0-2 never write it in practice).
+ * VG_ERR_INVALID_ARG for a bad kind, iters < 1 or a small buffer. */
+vg_status vg_probe_peak(int32_t kind, int32_t iters, float* buf, int64_t buf_floats, int64_t* units,
+                        vg_stream stream);
+
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char* vg_last_error(void);
 

@@ -97,6 +97,7 @@ def lib():
             "vg_pose_grad": [P, I32, P, P, P, P, P],
             "vg_loss_l1": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P, P],
             "vg_loss_l1_noalloc": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P],
+            "vg_probe_peak": [I32, I32, P, I64, P, P],
             "vg_adam_step": [P, I32, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
             "vg_pose_step": [I32, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
         }
@@ -492,7 +493,34 @@ def exported_symbols():
             "vg_check", "vg_ctx_stats", "vg_ctx_reset_counters", "vg_ctx_buffer", "vg_ctx_profile",
             "vg_ctx_profile_read", "vg_adam_step", "vg_pose_step", "vg_rvq_decode", "vg_render_fwd",
             "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
-            "vg_launch_count"]
+            "vg_launch_count", "vg_probe_peak"]
+
+
+PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),
+          "atomic_distinct": (3, 200, "G atomics/s", 1e9), "atomic_per_warp": (4, 50, "G atomics/s", 1e9)}
+
+
+def probe_peaks(reps: int = 5) -> Dict[str, dict]:
+    """Measured throughput of each vg_probe_peak kind (best of `reps` launches,
+    CUDA events on the current stream)."""
+    torch = _torch()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    n = sms * 8 * 256
+    buf = torch.zeros(n, dtype=torch.float32, device="cuda")
+    units = C.c_int64()
+    out = {}
+    for name, (kind, iters, unit, scale) in PROBES.items():
+        best = None
+        for _ in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            _check(lib().vg_probe_peak(kind, iters, _ptr(buf), n, C.byref(units), _stream(None)), "vg_probe_peak")
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        out[name] = {"value": units.value / (best / 1e3) / scale, "unit": unit, "ms": best}
+    return out
 
 
 def render_with_retry(scene: SceneHandle, cams, params, ctx: CtxHandle, stream=None, max_tries: int = 4):
