@@ -838,7 +838,7 @@ def run_ours(args):
                 "plain_launches": eager,
                 "serving": serving, "local_ba": ba_res, "large_scene": large, "configs_table": table,
                 "peak_probes": {k: {"value": v["value"], "unit": v["unit"]} for k, v in probes.items()},
-                "derived_peaks": {"fp32_tflops": alu_peak, "ex2_g_per_s": n_sm * 16 * sm_mhz * 1e6 / 1e9,
+                "derived_peaks": {"fp32_tflops": alu_peak, "ex2_g_per_s": n_sm * 32 * sm_mhz * 1e6 / 1e9,
                                   "smem_tb_per_s": n_sm * 128 * sm_mhz * 1e6 / 1e12}}
         print(json.dumps(line), flush=True)
     if dist:
