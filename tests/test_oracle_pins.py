@@ -651,3 +651,100 @@ def test_window_restricts_compositing_to_its_pixels():
     gf = full.backward(*ups_in)
     for k in gf:
         assert np.allclose(np.asarray(gw[k]), np.asarray(gf[k]), rtol=1e-12, atol=1e-15), k
+
+
+# ---------------------------------------------------------------------------
+# Eq. 14 (second line) and Eq. 15: residual quantisation encode and its loss
+# ---------------------------------------------------------------------------
+
+def test_rvq_encode_single_stage_is_the_nearest_codeword():
+    from oracle.rvq_encode import rvq_encode
+    rng = np.random.default_rng(70)
+    cb = rng.normal(size=(1, 64, 3)).astype(np.float32)
+    x = rng.normal(size=(500, 3)).astype(np.float32)
+    d = ((cb[0][None, :, :].astype(np.float64) - x[:, None, :].astype(np.float64)) ** 2).sum(-1)
+    srt = np.sort(d, axis=1)
+    clear = (srt[:, 1] - srt[:, 0]) > 1e-5 * srt[:, 1]      # no near-tie the FP32 order could flip
+    assert clear.mean() > 0.95
+    idx = rvq_encode(cb, x)
+    assert np.array_equal(idx[0][clear], d.argmin(axis=1)[clear])
+
+
+def test_rvq_encode_recovers_digits():
+    """Codewords k * 16^-(s+1) in every component and vectors sum_s d_s
+    16^-(s+1) with digits d_s < 8: the tail after stage s is below half the
+    stage's spacing, so the nearest codeword is the digit itself and the
+    encoding returns exactly the digits."""
+    from oracle.rvq_encode import rvq_encode
+    L, K, d = 4, 16, 3
+    cb = np.zeros((L, K, d), np.float32)
+    for s in range(L):
+        cb[s] = (np.arange(K, dtype=np.float64)[:, None] * 16.0 ** -(s + 1)).astype(np.float32)
+    rng = np.random.default_rng(71)
+    digits = rng.integers(0, K // 2, size=(L, 300))
+    x = np.zeros((300, d), np.float64)
+    for s in range(L):
+        x += (digits[s] * 16.0 ** -(s + 1))[:, None]
+    idx = rvq_encode(cb, x.astype(np.float32))
+    assert np.array_equal(idx, digits.astype(np.uint8))
+
+
+def test_rvq_encode_ties_go_to_the_lowest_index_and_error_never_grows():
+    from oracle import oracle as Ob
+    from oracle.rvq_encode import rvq_encode
+    rng = np.random.default_rng(72)
+    cb = rng.normal(scale=0.5, size=(3, 32, 4)).astype(np.float32)
+    cb[:, 0] = 0.0                      # a zero codeword in every stage: a stage can always keep the residual
+    cb[:, 9] = cb[:, 5]                 # duplicates: 9 must never be chosen
+    x = rng.normal(size=(400, 4)).astype(np.float32)
+    idx = rvq_encode(cb, x)
+    assert not np.any(idx == 9)
+    err_prev = np.inf
+    for s in range(1, 4):
+        rec = Ob.rvq_decode(cb[:s], idx[:s])
+        err = ((x.astype(np.float64) - rec) ** 2).sum(1)
+        assert np.all(err <= np.minimum(err_prev, ((x.astype(np.float64)) ** 2).sum(1)) * (1 + 1e-5) + 1e-9)
+        err_prev = err
+
+
+def test_rvq_loss_matches_definition_and_finite_differences():
+    from oracle.rvq_encode import rvq_encode, rvq_loss
+    rng = np.random.default_rng(73)
+    cb = rng.normal(scale=0.3, size=(3, 8, 2))
+    x = rng.normal(size=(50, 2))
+    idx = rvq_encode(cb.astype(np.float32), x.astype(np.float32))
+    loss, grad = rvq_loss(cb, x, idx)
+    # the definition, written as a loop over items and stages
+    want = 0.0
+    for n in range(50):
+        lhat = np.zeros(2)
+        for s in range(3):
+            e = (x[n] - lhat) - cb[s][idx[s][n]]
+            want += e @ e
+            lhat += cb[s][idx[s][n]]
+    assert abs(loss - want / (50 * 8)) < 1e-12
+    # finite differences of the loss with the stop-gradient residuals held
+    # fixed (sg: a perturbed codeword moves only its own term)
+    h = 1e-6
+    R = []
+    lhat = np.zeros((50, 2))
+    for s in range(3):
+        R.append(x - lhat)
+        lhat = lhat + cb[s][idx[s].astype(int)]
+
+    def sg_loss(c):
+        return sum(float(((R[s] - c[s][idx[s].astype(int)]) ** 2).sum()) for s in range(3)) / (50 * 8)
+    for s, k, c in [(0, int(idx[0][0]), 0), (1, int(idx[1][3]), 1), (2, int(idx[2][7]), 0)]:
+        cp, cm = cb.copy(), cb.copy()
+        cp[s, k, c] += h
+        cm[s, k, c] -= h
+        fd = (sg_loss(cp) - sg_loss(cm)) / (2 * h)
+        assert abs(fd - grad[s, k, c]) <= 1e-6 * max(1.0, abs(fd)), (s, k, c, fd, grad[s, k, c])
+    for s in range(3):
+        lhat = np.zeros((50, 2))
+        for t in range(s):
+            lhat += cb[t][idx[t].astype(int)]
+        r = x - lhat
+        g = np.zeros((8, 2))
+        np.add.at(g, idx[s].astype(int), 2 * (cb[s][idx[s].astype(int)] - r))
+        assert np.allclose(grad[s], g / (50 * 8), rtol=1e-12, atol=1e-15)
