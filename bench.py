@@ -519,6 +519,48 @@ def configs_table(torch, V, synth, threads):
     return out
 
 
+def rvq_leg(torch, V, n=320000, L=3, K=64, reps=20):
+    """Residual quantisation encode + codebook loss and gradient (Eq. 14-15)
+    of the mapping scene's four attribute groups (n items each; dims 3, 4,
+    1, 3; 3 stages of 64 codewords), against the numpy oracle on 20k items."""
+    from oracle.rvq_encode import rvq_encode
+    rng = np.random.default_rng(9)
+    groups = []
+    for d in (3, 4, 1, 3):
+        cb = torch.from_numpy((rng.normal(size=(L, K, d)) * 0.5 ** np.arange(L)[:, None, None]).astype(np.float32)).cuda()
+        x = torch.from_numpy(rng.normal(size=(n, d)).astype(np.float32)).cuda()
+        groups.append((cb, x, torch.empty((L, n), dtype=torch.uint8, device="cuda"), torch.empty(1, device="cuda"),
+                       torch.empty_like(cb)))
+
+    def run():
+        for cb, x, idx, loss, dcb in groups:
+            V.vg_rvq_encode(cb, x, idx=idx, loss=loss, dcodebook=dcb)
+
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        run()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    ms = statistics.median(times)
+    m = 20000
+    t0 = time.perf_counter()
+    for cb, x, _, _, _ in groups:
+        rvq_encode(cb.cpu().numpy(), x[:m].cpu().numpy())
+    cpu_s = (time.perf_counter() - t0) * n / m
+    flop = sum(n * L * K * d * 3 for d in (3, 4, 1, 3))   # subtract, multiply, add per component
+    res = {"items": n, "groups": "dims 3, 4, 1, 3", "stages": L, "codewords": K, "ms_per_encode": ms,
+           "g_items_per_s": 4 * n / ms / 1e6, "distance_tflops": flop / ms / 1e9,
+           "oracle_s_per_encode": cpu_s, "oracle_sample": f"numpy on {m} items per group, scaled"}
+    log(f"rvq encode: {ms:.3f} ms for 4 x {n} items ({res['distance_tflops']:.1f} TFLOP/s of distances)")
+    return res
+
+
 def run_reference(args):
     rank, world, _ = env_dist()
     if rank != 0:
@@ -814,7 +856,9 @@ def run_ours(args):
     table = None
     if rank == 0 and args.configs:
         table = configs_table(torch, V, synth, os.cpu_count() or 1)
-    serving = ba_res = large = None
+    serving = ba_res = large = rvq = None
+    if rank == 0:
+        rvq = rvq_leg(torch, V)
     if rank == 0 and not args.no_large:
         large = large_leg(torch, V, synth)
     if rank == 0 and not args.no_serving:
@@ -837,6 +881,7 @@ def run_ours(args):
                 "p90_step_ms": float(np.percentile(step_ms, 90)), "p99_step_ms": float(np.percentile(step_ms, 99)),
                 "plain_launches": eager,
                 "serving": serving, "local_ba": ba_res, "large_scene": large, "configs_table": table,
+                "rvq_encode": rvq,
                 "peak_probes": {k: {"value": v["value"], "unit": v["unit"]} for k, v in probes.items()},
                 "derived_peaks": {"fp32_tflops": alu_peak, "ex2_g_per_s": n_sm * 32 * sm_mhz * 1e6 / 1e9,
                                   "smem_tb_per_s": n_sm * 128 * sm_mhz * 1e6 / 1e12}}

@@ -249,6 +249,23 @@ vg_status vg_ctx_buffer(const vg_ctx* ctx, int32_t which, const void** ptr, int6
  * device arrays; out is [n_items][dim].  A raw group (stages == 0) is copied. */
 vg_status vg_rvq_decode(const vg_attr_group* group, int64_t n_items, float* out, vg_stream stream);
 
+/* Eq. 14, second line, and Eq. 15: residual vector quantisation of n_items
+ * vectors x [n_items][dim] (device) with group's codebooks [stages][codewords]
+ * [dim] (device; group->idx and ->raw are ignored).  Stage s = 0..L-1 picks
+ *   idx[s][n] = argmin_k || C^s[k] - (x_n - sum_{t<s} C^t[idx[t][n]]) ||^2,
+ * the first minimum on ties; the decision is taken in FP32 in a fixed order
+ * (running sum over stages, residual, squared differences summed over
+ * components in order, no fused multiply-add).  idx is [stages][n_items]
+ * uint8 (device).  If loss (device float[1]) is non-NULL it receives
+ *   L = 1/(n K) sum_s sum_n || sg[r_{s,n}] - C^s[idx[s][n]] ||^2,
+ * r the residual entering stage s; if dcodebook (device, codebook layout) is
+ * non-NULL it receives dL/dC (2/(n K) times the sum of C^s[k] - r over the
+ * items assigned to k).  Both are overwritten.  1 <= codewords <= 256,
+ * 1 <= dim <= 16, codebooks within 200 KB (100 KB with dcodebook); else
+ * VG_ERR_INVALID_ARG.  n_items == 0 writes zeros to loss and dcodebook. */
+vg_status vg_rvq_encode(const vg_attr_group* group, int64_t n_items, const float* x, uint8_t* idx, float* loss,
+                        float* dcodebook, vg_stream stream);
+
 /* Forward render of n_views (1..64) cameras (HOST array) of one scene in one
  * launch sequence: decode (Eq. 7, 11-12, 14) and project (Eq. 2-3) every
  * Gaussian for every view, bin (Gaussian, tile) pairs and order each tile's

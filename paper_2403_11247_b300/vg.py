@@ -98,6 +98,7 @@ def lib():
             "vg_loss_l1": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P, P],
             "vg_loss_l1_noalloc": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P],
             "vg_probe_peak": [I32, I32, P, I64, P, P],
+            "vg_rvq_encode": [P, I64, P, P, P, P, P],
             "vg_adam_step": [P, I32, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
             "vg_pose_step": [I32, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
         }
@@ -305,6 +306,24 @@ def vg_rvq_decode(codebook, idx, out=None, stream=None):
     return out
 
 
+def vg_rvq_encode(codebook, x, idx=None, loss=None, dcodebook=None, want_loss=True, want_grad=True, stream=None):
+    """codebook [L,K,d] f32 CUDA, x [n,d] f32 CUDA -> (idx [L,n] u8, loss [1], dcodebook [L,K,d])."""
+    torch = _torch()
+    L, K, d = codebook.shape
+    n = x.shape[0]
+    dev = codebook.device
+    if idx is None:
+        idx = torch.empty((L, n), dtype=torch.uint8, device=dev)
+    if loss is None and want_loss:
+        loss = torch.empty(1, dtype=torch.float32, device=dev)
+    if dcodebook is None and want_grad:
+        dcodebook = torch.empty_like(codebook)
+    g = vg_attr_group(int(d), int(L), int(K), _ptr(codebook), None, None)
+    _check(lib().vg_rvq_encode(C.byref(g), int(n), _ptr(x), _ptr(idx), _ptr(loss), _ptr(dcodebook),
+                               _stream(stream)), "vg_rvq_encode")
+    return idx, loss, dcodebook
+
+
 def image_sizes(cams):
     return [c.width * c.height for c in cams]
 
@@ -493,7 +512,7 @@ def exported_symbols():
             "vg_check", "vg_ctx_stats", "vg_ctx_reset_counters", "vg_ctx_buffer", "vg_ctx_profile",
             "vg_ctx_profile_read", "vg_adam_step", "vg_pose_step", "vg_rvq_decode", "vg_render_fwd",
             "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
-            "vg_launch_count", "vg_probe_peak"]
+            "vg_launch_count", "vg_probe_peak", "vg_rvq_encode"]
 
 
 PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),
