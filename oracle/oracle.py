@@ -90,6 +90,7 @@ def lib():
         _lib.orc_loss_l1.restype = C.c_double
         _lib.orc_loss_l1.argtypes = [C.c_int64, P, P, P, P, P, C.c_double, C.c_double, P, P]
         _lib.orc_rvq_decode.argtypes = [C.c_int, C.c_int, C.c_int, P, P, C.c_int64, P]
+        _lib.orc_hit_counts.argtypes = [P, P, P, C.c_int]
         _lib.orc_set_window.restype = C.c_int
         _lib.orc_set_window.argtypes = [P] + [C.c_int] * 5
     return _lib
@@ -197,6 +198,14 @@ class Oracle:
         self.n_pairs = L.orc_n_pairs(self.ctx)
         self.n_tiles = L.orc_n_tiles(self.ctx)
         self.n_pixels = L.orc_n_pixels(self.ctx)
+
+    def hit_counts(self, threads: int = 1):
+        """Eq. 13's h: per Gaussian, the (view, pixel) pairs where it is
+        blended; and whether it is visible in some view."""
+        hits = np.zeros(self.N, np.int64)
+        seen = np.zeros(self.N, np.int32)
+        lib().orc_hit_counts(self.ctx, _p(hits), _p(seen), int(threads))
+        return hits, seen
 
     def set_window(self, view: int, x0: int, y0: int, x1: int, y1: int):
         """Composite (forward and backward) only pixels [x0, x1) x [y0, y1)

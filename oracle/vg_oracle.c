@@ -579,6 +579,49 @@ int64_t orc_forward(orc_ctx* ctx, double* C, double* D, double* S, double* T_fin
 }
 
 /* ------------------------------------------------------------------------ */
+/* hit counts (sliding-window mask, Eq. 13): per Gaussian, the number of     */
+/* (view, pixel) pairs where it is blended; seen: visible (an unempty tile  */
+/* rect) in any view.  Both are ADDED to / OR-ed into the caller's arrays.  */
+void orc_hit_counts(orc_ctx* ctx, int64_t* hits, int32_t* seen, int threads)
+{
+    int64_t N = ctx->N;
+    if (seen)
+        for (int64_t s = 0; s < (int64_t)ctx->nv * N; ++s)
+            if (ctx->pr[s].valid) seen[s % N] = 1;
+    if (!hits) return;
+    int64_t maxlen = 1;
+    for (int64_t t = 0; t < ctx->n_tiles; ++t) {
+        int64_t l = ctx->tile_start[t + 1] - ctx->tile_start[t];
+        if (l > maxlen) maxlen = l;
+    }
+    if (threads < 1) threads = 1;
+    for (int v = 0; v < ctx->nv; ++v) {
+#ifdef _OPENMP
+#pragma omp parallel num_threads(threads)
+#endif
+        {
+            step_t* steps = (step_t*)malloc(sizeof(step_t) * maxlen);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 4)
+#endif
+            for (int py = ctx->win[4 * v + 1]; py < ctx->win[4 * v + 3]; ++py)
+                for (int px = ctx->win[4 * v + 0]; px < ctx->win[4 * v + 2]; ++px) {
+                    double out[5];
+                    int m = walk_pixel(ctx, v, px, py, steps, out, NULL, NULL, NULL, NULL);
+                    for (int i = 0; i < m; ++i) {
+                        int64_t n = steps[i].slot % N;
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                        hits[n] += 1;
+                    }
+                }
+            free(steps);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* backward                                                                  */
 /* ------------------------------------------------------------------------ */
 

@@ -95,6 +95,12 @@ void orc_get_decoded(const orc_ctx* ctx, double* out);
 int64_t orc_forward(orc_ctx* ctx, double* C, double* D, double* S, double* T_final,
                     int32_t* n_contrib, int32_t* n_eval, uint8_t* flags, int threads);
 
+/* Hit counts of the sliding-window mask (Eq. 13): hits[n] += the number of
+ * (view, pixel) pairs, within each view's window, where Gaussian n is
+ * blended; seen[n] = 1 where Gaussian n is visible (an unempty tile rect) in
+ * some view.  Either may be NULL. */
+void orc_hit_counts(orc_ctx* ctx, int64_t* hits, int32_t* seen, int threads);
+
 /* Reverse mode of the forward for upstream images dC, dD, dS (same layout).
  * Outputs (any may be NULL; all are overwritten):
  *   g2d     [slots][10]: du dv da db dc dopacity dr dg db ddepth

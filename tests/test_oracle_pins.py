@@ -748,3 +748,58 @@ def test_rvq_loss_matches_definition_and_finite_differences():
         g = np.zeros((8, 2))
         np.add.at(g, idx[s].astype(int), 2 * (cb[s][idx[s].astype(int)] - r))
         assert np.allclose(grad[s], g / (50 * 8), rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# sliding-window mask: hit counts (Eq. 13), mask loss, removal
+# ---------------------------------------------------------------------------
+
+def test_hit_counts_single_gaussian_closed_form():
+    """One Gaussian: its hit count is the number of image pixels where
+    alpha = o exp(-q/2) reaches 1/255 (it can never trigger the stop)."""
+    c = cam(60.0, 60.0, 31.5, 23.5, 64, 48)
+    sc = raw_scene([[0.1, -0.05, 2.0]], [[math.log(0.08), math.log(0.05), math.log(0.06)]],
+                   [[0.9, 0.1, 0.3, -0.2]], [0.8], [[0.2, 0.5, 0.7]])
+    o = O.Oracle(sc, [c])
+    hits, seen = o.hit_counts()
+    proj, _, _ = o.projection()
+    u, v, a, b, cc, op = proj[0, 0], proj[0, 1], proj[0, 3], proj[0, 4], proj[0, 5], proj[0, 6]
+    ys, xs = np.mgrid[0:48, 0:64]
+    dx, dy = u - xs, v - ys
+    alpha = np.minimum(0.99, op * np.exp(-0.5 * (a * dx * dx + 2 * b * dx * dy + cc * dy * dy)))
+    # only pixels inside the Gaussian's tile rect are tested
+    r0, r1, r2, r3 = (int(t) for t in proj[0, 12:16])
+    inrect = (xs >= r0 * 16) & (xs < r2 * 16) & (ys >= r1 * 16) & (ys < r3 * 16)
+    want = int(((alpha >= 1 / 255) & inrect).sum())
+    assert want > 100 and hits[0] == want and seen[0] == 1
+
+
+def test_hit_counts_sum_to_blended_pairs_and_views_add():
+    sc = synth.tiny_scene()
+    cams = [synth.tiny_camera(), synth.tiny_camera()]
+    h2, s2 = O.Oracle(sc, cams).hit_counts(threads=4)
+    h1, s1 = O.Oracle(sc, cams[:1]).hit_counts(threads=4)
+    assert np.array_equal(h2, 2 * h1) and np.array_equal(s2, s1)
+    assert h1.sum() > 0 and np.all(h1[s1 == 0] == 0)
+
+
+def test_mask_loss_and_prune_definitions():
+    from oracle.mask import mask_loss, mask_prune, sigmoid
+    rng = np.random.default_rng(80)
+    m = rng.normal(size=200)
+    vis = rng.uniform(size=200) < 0.4
+    L, g = mask_loss(m, vis, weight=0.5)
+    assert abs(L - 0.5 * np.mean(sigmoid(m[vis]))) < 1e-15
+    h = 1e-6
+    for j in np.flatnonzero(vis)[:5]:
+        mp, mm = m.copy(), m.copy()
+        mp[j] += h
+        mm[j] -= h
+        fd = (mask_loss(mp, vis, 0.5)[0] - mask_loss(mm, vis, 0.5)[0]) / (2 * h)
+        assert abs(fd - g[j]) < 1e-8
+    assert np.all(g[~vis] == 0)
+    hits = rng.integers(0, 5, 200)
+    seen = rng.uniform(size=200) < 0.7
+    nm, removed = mask_prune(m, hits, seen, 0.5, 2)
+    assert np.array_equal(removed, (m <= 0) | (seen & (hits < 2)))
+    assert np.all(np.isneginf(nm[removed])) and np.array_equal(nm[~removed], m[~removed])
