@@ -125,7 +125,13 @@ typedef struct {
  * pose_dev: optional DEVICE array [n_views][12] read instead of the
  *   cameras' T_cw (lets a captured CUDA graph follow poses updated on the
  *   device).  count_evals: accumulate evaluated (pixel, Gaussian) pairs into
- *   the ctx counter (vg_ctx_stats). */
+ *   the ctx counter (vg_ctx_stats).
+ * hit_count, seen: optional DEVICE arrays [N] for the sliding-window mask
+ *   (Sec. "Sliding Window-based Online Mask", Eq. 13).  vg_render_fwd ADDS
+ *   to hit_count[n] the number of (view, pixel) pairs where Gaussian n is
+ *   blended and sets seen[n] = 1 where Gaussian n is visible (an unempty
+ *   tile rect) in some view; nothing clears them, so a sliding window
+ *   accumulates over its frames.  NULL = off. */
 typedef struct {
     int32_t tile;
     int32_t batch;
@@ -134,6 +140,8 @@ typedef struct {
     int32_t count_evals;
     const float* pose_dev;
     int32_t ppt_fwd, ppt_bwd;
+    uint32_t* hit_count;
+    uint32_t* seen;
 } vg_render_params;
 
 /* Gradient outputs of vg_render_bwd (DEVICE pointers, caller-allocated; each
@@ -356,6 +364,26 @@ int64_t vg_launch_count(void);
 vg_status vg_loss_l1_noalloc(int32_t n_views, int64_t n_pix, const float* C, const float* D, const float* S,
                              const float* Ct, const float* Dt, float w_depth, float gate,
                              float* dC, float* dD, float* dS, float* loss, vg_stream stream);
+
+/* Sliding-window online mask (Sec. "Sliding Window-based Online Mask").
+ * vg_mask_loss: over the Gaussians visible (an unempty tile rect) in some
+ * view of the last vg_render_fwd of `scene` on `ctx` (frustum selection;
+ * N_w of them), writes loss[0] = weight/N_w * sum Sig(m_n) (Eq. 13, L_m) and
+ * ADDS weight/N_w * Sig'(m_n) to dmask_logit[n] for those n ([N], device;
+ * e.g. the mask gradient vg_render_bwd wrote).  Either output may be NULL.
+ * vg_mask_prune, at the window bound: every Gaussian whose mask is off
+ * (m <= logit(mask_eps), the renderer's own test) or that was seen in the
+ * window (seen[n] != 0) but hit fewer than min_hits rays (hit_count[n],
+ * both accumulated by vg_render_fwd, see vg_render_params) is removed: its
+ * mask logit becomes -inf in the scene's own array (the caller's array for a
+ * borrowed scene), so it is culled from then on.  removed [N] (0/1) and
+ * n_removed[0] are optional device outputs; hit_count and seen are both
+ * given or both NULL (then only the mask decides).  VG_ERR_INVALID_ARG for
+ * a scene without mask logits. */
+vg_status vg_mask_loss(const vg_scene* scene, vg_ctx* ctx, float weight, float* dmask_logit, float* loss,
+                       vg_stream stream);
+vg_status vg_mask_prune(vg_scene* scene, const uint32_t* hit_count, const uint32_t* seen, uint32_t min_hits,
+                        uint32_t* removed, uint32_t* n_removed, vg_stream stream);
 
 /* Throughput probe for roofline denominators (a measurement facility; the
  * paper has no counterpart).  Enqueues one kernel on `stream` over a grid of

@@ -556,6 +556,9 @@ static vg_status build_views(const vg_camera* cams, int32_t n_views, const vg_re
     cs->dilation = p->dilation;
     cs->sigma_cull = p->sigma_cull;
     cs->jacobian_clamp = p->jacobian_clamp;
+    cs->hit_count = p->hit_count;
+    cs->seen = p->seen;
+    cs->n_gauss = 0;  // set by the caller that knows the scene
     *pixels = pb;
     return VG_OK;
 }
@@ -574,6 +577,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     Consts cs;
     int64_t pixels = 0;
     VG_TRY(build_views(cams, n_views, params, &V, &cs, &pixels));
+    cs.n_gauss = scene->dev.N;
     const SceneDev& sd = scene->dev;
     const int64_t N = sd.N;
     const int64_t slots = N * n_views;
@@ -793,6 +797,27 @@ vg_status vg_loss_l1(int32_t n_views, int64_t n_pix, const float* C, const float
     VG_STAGE(VG_STAGE_LOSS, launch_loss_l1(n_views, n_pix, C, D, S, Ct, Dt, w_depth, gate, dC, dD, loss,
                                            ctx->loss_scratch.as<uint32_t>(), st));
     return VG_OK;
+}
+
+vg_status vg_mask_loss(const vg_scene* scene, vg_ctx* ctx, float weight, float* dmask_logit, float* loss,
+                       vg_stream stream) {
+    if (!scene || !ctx) return fail(VG_ERR_INVALID_ARG, "vg_mask_loss: null argument");
+    if (!scene->dev.mask) return fail(VG_ERR_INVALID_ARG, "vg_mask_loss: the scene has no mask logits");
+    if (!ctx->have_fwd || ctx->fwd_scene != scene)
+        return fail(VG_ERR_INVALID_ARG, "vg_mask_loss: no vg_render_fwd of this scene on this ctx");
+    uint32_t* su = ctx->loss_scratch.as<uint32_t>();
+    return vg_mask_kernels_loss(scene->dev, ctx->views, ctx->ntiles.as<uint32_t>(), weight, dmask_logit, loss, su,
+                                reinterpret_cast<float*>(su + 1), (cudaStream_t)stream);
+}
+
+vg_status vg_mask_prune(vg_scene* scene, const uint32_t* hit_count, const uint32_t* seen, uint32_t min_hits,
+                        uint32_t* removed, uint32_t* n_removed, vg_stream stream) {
+    if (!scene) return fail(VG_ERR_INVALID_ARG, "vg_mask_prune: null scene");
+    if (!scene->dev.mask) return fail(VG_ERR_INVALID_ARG, "vg_mask_prune: the scene has no mask logits");
+    if ((hit_count == nullptr) != (seen == nullptr))
+        return fail(VG_ERR_INVALID_ARG, "vg_mask_prune: hit_count and seen go together");
+    return vg_mask_kernels_prune(const_cast<float*>(scene->dev.mask), scene->dev.mask_thr, hit_count, seen, min_hits,
+                                 scene->dev.N, removed, n_removed, (cudaStream_t)stream);
 }
 
 vg_status vg_adam_step(const vg_adam_tensor* tensors, int32_t n, float lr, float beta1, float beta2, float eps,

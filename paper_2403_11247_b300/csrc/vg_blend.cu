@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     __shared__ float4 s_xy[BLEND_BATCH];
     __shared__ float4 s_co[BLEND_BATCH];
     __shared__ float4 s_cd[BLEND_BATCH];
+    __shared__ uint32_t s_gid[BLEND_BATCH];  // Gaussian ids, for the optional hit counts
 
     const int gt = (int)order[blockIdx.x];  // longest tile lists first
     const int v = view_of_tile(V, gt);
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
                 s_xy[i] = xy[s];
                 s_co[i] = conic_o[s];
                 s_cd[i] = rgbd[s];
+                if (cs.hit_count) s_gid[i] = (uint32_t)(s % (uint64_t)cs.n_gauss);
             }
         }
         __syncthreads();
@@ -162,6 +164,11 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
                 m &= m - 1;
                 const float4 g = s_xy[i];
                 const float4 co = s_co[i];
+                uint32_t hb = 0;  // this lane's pixels that blend Gaussian i (hit counts)
+                if (cs.hit_count) {
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) hb -= nb[k];
+                }
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     if (done[k]) continue;
@@ -186,6 +193,12 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
                     T[k] = Tn;
                     last[k] = b - rg.x + i + 1;
                     ++nb[k];
+                }
+                if (cs.hit_count) {
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) hb += nb[k];
+                    const uint32_t tot = __reduce_add_sync(0xffffffffu, hb);
+                    if (lane == 0 && tot) atomicAdd(cs.hit_count + s_gid[i], tot);
                 }
             }
         }

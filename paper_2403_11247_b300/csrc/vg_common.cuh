@@ -43,6 +43,9 @@ struct Views {
 struct Consts {
     float alpha_max, alpha_min, t_min, dilation, sigma_cull;
     int32_t jacobian_clamp;
+    uint32_t* hit_count;  // [N] blended (view, pixel) pairs per Gaussian, added to; NULL = off
+    uint32_t* seen;       // [N] set to 1 where a Gaussian is visible in some view; NULL = off
+    int64_t n_gauss;      // N, for the two arrays above
 };
 
 // Scene arrays as the kernels see them (device pointers).

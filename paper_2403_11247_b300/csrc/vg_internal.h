@@ -75,6 +75,12 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, co
 cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, uint32_t* order, cudaStream_t st);
 cudaError_t launch_epoch_bump(uint32_t* state, uint32_t by, cudaStream_t st);
 
+// mask.cu
+vg_status vg_mask_kernels_loss(const SceneDev& S, const Views& V, const uint32_t* ntiles, float weight, float* dmask,
+                               float* loss, uint32_t* scratch_u, float* scratch_f, cudaStream_t st);
+vg_status vg_mask_kernels_prune(float* m, float thr, const uint32_t* hits, const uint32_t* seen, uint32_t min_hits,
+                                int64_t N, uint32_t* removed, uint32_t* n_removed, cudaStream_t st);
+
 // blend.cu
 cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* order,
                              const uint32_t* pvals,

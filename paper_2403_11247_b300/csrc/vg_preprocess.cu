@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
                 key = __float_as_uint(p[2]);
                 dkey[slot] = key;
                 ++n_vis;
+                if (cs.seen) cs.seen[n] = 1u;
             } else {
                 ntiles[slot] = 0u;
                 dkey[slot] = 0xffffffffu;

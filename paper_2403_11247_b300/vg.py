@@ -55,7 +55,7 @@ class vg_render_params(C.Structure):
                 ("alpha_max", C.c_float), ("alpha_min", C.c_float), ("t_min", C.c_float), ("dilation", C.c_float),
                 ("sigma_cull", C.c_float), ("clamp_factor", C.c_float),
                 ("jacobian_clamp", C.c_int32), ("count_evals", C.c_int32), ("pose_dev", C.c_void_p),
-                ("ppt_fwd", C.c_int32), ("ppt_bwd", C.c_int32)]
+                ("ppt_fwd", C.c_int32), ("ppt_bwd", C.c_int32), ("hit_count", C.c_void_p), ("seen", C.c_void_p)]
 
 
 class vg_scene_grads(C.Structure):
@@ -99,6 +99,8 @@ def lib():
             "vg_loss_l1_noalloc": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P],
             "vg_probe_peak": [I32, I32, P, I64, P, P],
             "vg_rvq_encode": [P, I64, P, P, P, P, P],
+            "vg_mask_loss": [P, P, C.c_float, P, P, P],
+            "vg_mask_prune": [P, P, P, C.c_uint32, P, P, P],
             "vg_adam_step": [P, I32, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
             "vg_pose_step": [I32, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
         }
@@ -160,8 +162,8 @@ def _host_or_dev_ptr(a):
 def default_params(**kw) -> vg_render_params:
     p = lib().vg_default_params()
     for k, v in kw.items():
-        if k == "pose_dev":
-            p.pose_dev = _ptr(v)
+        if k in ("pose_dev", "hit_count", "seen"):
+            setattr(p, k, _ptr(v))
         else:
             setattr(p, k, v)
     return p
@@ -322,6 +324,26 @@ def vg_rvq_encode(codebook, x, idx=None, loss=None, dcodebook=None, want_loss=Tr
     _check(lib().vg_rvq_encode(C.byref(g), int(n), _ptr(x), _ptr(idx), _ptr(loss), _ptr(dcodebook),
                                _stream(stream)), "vg_rvq_encode")
     return idx, loss, dcodebook
+
+
+def vg_mask_loss(scene: SceneHandle, ctx: CtxHandle, weight: float = 1.0, dmask=None, loss=None, stream=None):
+    """Mask loss over the last forward's visible Gaussians; adds its gradient to dmask."""
+    torch = _torch()
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    _check(lib().vg_mask_loss(scene.handle, ctx.handle, float(weight), _ptr(dmask), _ptr(loss), _stream(stream)),
+           "vg_mask_loss")
+    return loss
+
+
+def vg_mask_prune(scene: SceneHandle, hit_count=None, seen=None, min_hits: int = 1, removed=None, n_removed=None,
+                  stream=None):
+    torch = _torch()
+    if n_removed is None:
+        n_removed = torch.empty(1, dtype=torch.int32, device="cuda")
+    _check(lib().vg_mask_prune(scene.handle, _ptr(hit_count), _ptr(seen), int(min_hits), _ptr(removed),
+                               _ptr(n_removed), _stream(stream)), "vg_mask_prune")
+    return n_removed
 
 
 def image_sizes(cams):
@@ -512,7 +534,7 @@ def exported_symbols():
             "vg_check", "vg_ctx_stats", "vg_ctx_reset_counters", "vg_ctx_buffer", "vg_ctx_profile",
             "vg_ctx_profile_read", "vg_adam_step", "vg_pose_step", "vg_rvq_decode", "vg_render_fwd",
             "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
-            "vg_launch_count", "vg_probe_peak", "vg_rvq_encode"]
+            "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune"]
 
 
 PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),
