@@ -89,7 +89,7 @@ __device__ __forceinline__ bool warp_hits(const float4 g, const float4 co, float
     return best >= co.w - (1e-3f + 1e-3f * fabsf(co.w));
 }
 
-template <int PPT>
+template <int PPT, bool HITS>
 __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pvals,
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
                 s_xy[i] = xy[s];
                 s_co[i] = conic_o[s];
                 s_cd[i] = rgbd[s];
-                if (cs.hit_count) s_gid[i] = (uint32_t)(s % (uint64_t)cs.n_gauss);
+                if (HITS) s_gid[i] = (uint32_t)(s % (uint64_t)cs.n_gauss);
             }
         }
         __syncthreads();
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
                 const float4 g = s_xy[i];
                 const float4 co = s_co[i];
                 uint32_t hb = 0;  // this lane's pixels that blend Gaussian i (hit counts)
-                if (cs.hit_count) {
+                if (HITS) {
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) hb -= nb[k];
                 }
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
                     last[k] = b - rg.x + i + 1;
                     ++nb[k];
                 }
-                if (cs.hit_count) {
+                if (HITS) {
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) hb += nb[k];
                     const uint32_t tot = __reduce_add_sync(0xffffffffu, hb);
@@ -415,9 +415,15 @@ cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const ui
                              int count_evals, cudaStream_t st) {
     if (V.total_tiles <= 0) return cudaSuccess;
     count_launches(1);
-#define VG_FWD(P)                                                                                                   \
-    blend_fwd_kernel<P><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, order, pvals, xy, conic_o, rgbd, C, D, S, Tfin, \
-                                                                ncontrib, evals, blended, count_evals)
+#define VG_FWD(P)                                                                                               \
+    do {                                                                                                        \
+        if (cs.hit_count)                                                                                       \
+            blend_fwd_kernel<P, true><<<V.total_tiles, TILE_PIX / P, 0, st>>>(                                  \
+                V, cs, ranges, order, pvals, xy, conic_o, rgbd, C, D, S, Tfin, ncontrib, evals, blended, count_evals); \
+        else                                                                                                    \
+            blend_fwd_kernel<P, false><<<V.total_tiles, TILE_PIX / P, 0, st>>>(                                 \
+                V, cs, ranges, order, pvals, xy, conic_o, rgbd, C, D, S, Tfin, ncontrib, evals, blended, count_evals); \
+    } while (0)
     if (ppt == 4) VG_FWD(4);
     else if (ppt == 2) VG_FWD(2);
     else VG_FWD(1);
