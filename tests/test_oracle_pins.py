@@ -803,3 +803,50 @@ def test_mask_loss_and_prune_definitions():
     nm, removed = mask_prune(m, hits, seen, 0.5, 2)
     assert np.array_equal(removed, (m <= 0) | (seen & (hits < 2)))
     assert np.all(np.isneginf(nm[removed])) and np.array_equal(nm[~removed], m[~removed])
+
+
+# ---------------------------------------------------------------------------
+# the SSIM term of the bundle-adjustment loss
+# ---------------------------------------------------------------------------
+
+def test_ssim_identical_images_and_constant_closed_form():
+    from oracle.ssim import C1, ssim_loss
+    rng = np.random.default_rng(90)
+    x = rng.uniform(size=3 * 24 * 32)
+    L, g = ssim_loss(x, x, 1, 32, 24)
+    assert abs(L) < 1e-12 and np.abs(g).max() < 1e-12
+    # two constant images a, b: away from the border (all window weights
+    # inside) the variances vanish and SSIM = (2ab + C1) / (a^2 + b^2 + C1)
+    a, b = 0.3, 0.7
+    from oracle import ssim as S
+    w = S.window()
+    xa = np.full((24, 32), a)
+    xb = np.full((24, 32), b)
+    mx, my = S._filt(xa, w), S._filt(xb, w)
+    sxx = S._filt(xa * xa, w) - mx * mx
+    syy = S._filt(xb * xb, w) - my * my
+    sxy = S._filt(xa * xb, w) - mx * my
+    Smap = (2 * mx * my + C1) * (2 * sxy + S.C2) / ((mx * mx + my * my + C1) * (sxx + syy + S.C2))
+    assert abs(Smap[12, 16] - (2 * a * b + C1) / (a * a + b * b + C1)) < 1e-12
+
+
+def test_ssim_window_is_the_normalised_gaussian():
+    from oracle.ssim import window
+    w = window()
+    assert w.shape == (11, 11) and abs(w.sum() - 1) < 1e-15
+    assert abs(w[5, 6] / w[5, 5] - math.exp(-1 / (2 * 1.5 ** 2))) < 1e-14
+
+
+def test_ssim_gradient_matches_finite_differences():
+    from oracle.ssim import ssim_loss
+    rng = np.random.default_rng(91)
+    x = rng.uniform(size=3 * 20 * 18)
+    y = np.clip(x + rng.normal(scale=0.1, size=x.size), 0, 1)
+    L, g = ssim_loss(x, y, 1, 18, 20)
+    h = 1e-6
+    for j in rng.choice(x.size, 12, replace=False):
+        xp, xm = x.copy(), x.copy()
+        xp[j] += h
+        xm[j] -= h
+        fd = (ssim_loss(xp, y, 1, 18, 20)[0] - ssim_loss(xm, y, 1, 18, 20)[0]) / (2 * h)
+        assert abs(fd - g[j]) <= 1e-6 * max(1e-3, abs(fd)), (j, fd, g[j])
