@@ -850,3 +850,27 @@ def test_ssim_gradient_matches_finite_differences():
         xm[j] -= h
         fd = (ssim_loss(xp, y, 1, 18, 20)[0] - ssim_loss(xm, y, 1, 18, 20)[0]) / (2 * h)
         assert abs(fd - g[j]) <= 1e-6 * max(1e-3, abs(fd)), (j, fd, g[j])
+
+
+# ---------------------------------------------------------------------------
+# projective data association for the ICP term
+# ---------------------------------------------------------------------------
+
+def test_projective_association_on_a_plane():
+    """A fronto-parallel target plane at depth 2.5: every Gaussian within the
+    distance gate gets the plane's point on its pixel's ray, which lies on the
+    plane and within half a pixel's footprint of the mean's own ray."""
+    from oracle.icp_assoc import associate
+    rng = np.random.default_rng(95)
+    c = cam(80.0, 80.0, 31.5, 23.5, 64, 48)
+    mu = np.stack([rng.uniform(-0.8, 0.8, 400), rng.uniform(-0.6, 0.6, 400), rng.uniform(2.4, 2.6, 400)], 1)
+    Dt = np.full(64 * 48, 2.5)
+    q, w = associate(mu, np.ones(400, bool), [c], Dt, 0.2)
+    ok = w[0] > 0
+    assert ok.sum() > 300
+    assert np.allclose(q[0, ok, 2], 2.5)
+    ray = mu[ok] / mu[ok, 2:3] * 2.5          # the mean's own ray at the plane
+    assert np.abs(q[0, ok, :2] - ray[:, :2]).max() <= 0.5 * 2.5 / 80.0 + 1e-12
+    # gated: a plane 0.5 m behind the means gives no correspondence at max_dist 0.2
+    q2, w2 = associate(mu, np.ones(400, bool), [c], np.full(64 * 48, 3.0), 0.2)
+    assert w2.sum() == 0
