@@ -365,6 +365,32 @@ vg_status vg_loss_l1_noalloc(int32_t n_views, int64_t n_pix, const float* C, con
                              const float* Ct, const float* Dt, float w_depth, float gate,
                              float* dC, float* dD, float* dS, float* loss, vg_stream stream);
 
+/* Projective data association for the ICP term (Eq. 20; the paper's "closest
+ * points" q_i, taken here as the target depth map's point on the ray of the
+ * pixel each Gaussian mean projects to).  For view v and Gaussian n kept by
+ * its mask, with p = T_cw mu in front of the near plane: pixel (px, py) =
+ * the nearest integers to (fx x/z + cx, fy y/z + cy); if inside the image,
+ * with target depth d = Dt[view][py][px] > 0 and |z - d| < max_dist:
+ *   q[v][n] = ((px - cx) d / fx, (py - cy) d / fy, d)  (camera frame),
+ *   w[v][n] = weight (the ICP term's lambda, per correspondence);
+ * otherwise q = 0, w = 0.  Dt [n_views][H][W], q [n_views][N][3] and
+ * w [n_views][N] are device arrays, ready for vg_pose_grad's icp_q/icp_w;
+ * params->pose_dev is honoured like in vg_render_fwd. */
+vg_status vg_icp_associate(const vg_scene* scene, const vg_camera* cams, int32_t n_views,
+                           const vg_render_params* params, const float* Dt, float max_dist, float weight, float* q,
+                           float* w, vg_stream stream);
+
+/* The SSIM term the local-to-global bundle adjustment adds to the RGB
+ * rendering (Sec. "Tracking and Local-to-Global Bundle Adjustment"; the
+ * paper names the loss, this is the structural similarity of Wang et al.):
+ * per colour channel, 11x11 Gaussian window (sigma 1.5), zero padding,
+ * C1 = 0.01^2, C2 = 0.03^2;  L = 1 - mean SSIM(C, Ct) over the n_views x 3
+ * planes of width x height ([view][3][H][W], device).  Writes weight * L to
+ * loss[0] and ADDS weight * dL/dC to dC (e.g. after vg_loss_l1 wrote it);
+ * either may be NULL.  Workspace: 8 floats per colour value in the ctx. */
+vg_status vg_ssim_loss(vg_ctx* ctx, int32_t n_views, int32_t width, int32_t height, const float* C, const float* Ct,
+                       float weight, float* dC, float* loss, vg_stream stream);
+
 /* Sliding-window online mask (Sec. "Sliding Window-based Online Mask").
  * vg_mask_loss: over the Gaussians visible (an unempty tile rect) in some
  * view of the last vg_render_fwd of `scene` on `ctx` (frustum selection;

@@ -5,7 +5,8 @@ many iterations in one CUDA graph.
 
 Every iteration: forward render of the B keyframes (one launch per stage,
 views in the keys), L1 colour + weighted L1 depth loss gradient against the
-keyframes' RGB-D targets, backward to the map and to the B pose twists,
+keyframes' RGB-D targets (plus, with w_ssim > 0, the SSIM term on the
+colour), backward to the map and to the B pose twists,
 Adam on the poses (the pose moves by exp(-step^) on the left) and Adam on the
 map.  Poses live in a device array read by the kernels, so a captured graph
 follows them as they change; the step counters live on the device too.
@@ -24,7 +25,7 @@ from .autograd import SceneParams
 class LocalBA:
     def __init__(self, scene: SceneParams, cams: Sequence, Ct: torch.Tensor, Dt: torch.Tensor,
                  lr_rot: float = 2e-3, lr_trans: float = 2e-3, lr_map: float = 0.0, w_depth: float = 0.5,
-                 ppt_fwd: int = 0, ppt_bwd: int = 0, pair_headroom: float = 2.0):
+                 ppt_fwd: int = 0, ppt_bwd: int = 0, pair_headroom: float = 2.0, w_ssim: float = 0.0):
         self.scene = scene
         self.cams = list(cams)
         self.B = len(self.cams)
@@ -38,6 +39,7 @@ class LocalBA:
             raise ValueError("keyframes of one window share an image size")
         self.P = self.cams[0].width * self.cams[0].height
         self.w_depth = w_depth
+        self.w_ssim = w_ssim
         self.lr_rot, self.lr_trans, self.lr_map = lr_rot, lr_trans, lr_map
         self.ctx = V.vg_ctx_create(0)
         self.sh = scene.handle()
@@ -48,6 +50,7 @@ class LocalBA:
         self.dC = torch.empty(3 * B * P, **f32)
         self.dD = torch.empty(B * P, **f32)
         self.loss = torch.zeros(1, **f32)
+        self.ssim_loss = torch.zeros(1, **f32)
         self.dxi = torch.zeros((B, 6), **f32)
         self.pm = torch.zeros((B, 6), **f32)
         self.pv = torch.zeros((B, 6), **f32)
@@ -82,6 +85,9 @@ class LocalBA:
             V.vg_render_fwd(self.sh, self.cams, self.params, self.ctx, self.C, self.D, self.S)
             V.vg_loss_l1(self.B, self.P, self.C, self.D, self.S, self.Ct, self.Dt, self.w_depth, -1.0, self.ctx,
                          dC=self.dC, dD=self.dD, loss=self.loss)
+            if self.w_ssim > 0:  # the SSIM term the bundle adjustment adds to the RGB rendering
+                V.vg_ssim_loss(self.ctx, self.B, self.cams[0].width, self.cams[0].height, self.C, self.Ct,
+                               self.w_ssim, dC=self.dC, loss=self.ssim_loss)
             V.vg_render_bwd(self.sh, self.cams, self.params, self.ctx, self.dC, self.dD, None, self.grads)
             V.vg_pose_grad(self.ctx, self.B, dxi=self.dxi)
             V.vg_pose_step(self.pose, self.dxi, self.pm, self.pv, self.lr_rot, self.lr_trans, step_dev=self.pose_step)

@@ -176,7 +176,7 @@ struct vg_ctx {
     StageProfiler prof;
     int64_t pair_cap = 0;
     DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, tile_order, Tfin, ncontrib, lookback,
-        scratch, state, pose_part, icp_part, loss_scratch, pair_off, blk_count, blk_base, vis;
+        scratch, state, pose_part, icp_part, loss_scratch, pair_off, blk_count, blk_base, vis, ssim_ws;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
     bool g2d_clean = false;
@@ -797,6 +797,26 @@ vg_status vg_loss_l1(int32_t n_views, int64_t n_pix, const float* C, const float
     VG_STAGE(VG_STAGE_LOSS, launch_loss_l1(n_views, n_pix, C, D, S, Ct, Dt, w_depth, gate, dC, dD, loss,
                                            ctx->loss_scratch.as<uint32_t>(), st));
     return VG_OK;
+}
+
+vg_status vg_icp_associate(const vg_scene* scene, const vg_camera* cams, int32_t n_views, const vg_render_params* params,
+                           const float* Dt, float max_dist, float weight, float* q, float* w, vg_stream stream) {
+    if (!scene || !Dt || !q || !w) return fail(VG_ERR_INVALID_ARG, "vg_icp_associate: null argument");
+    Views V;
+    Consts cs;
+    int64_t pixels = 0;
+    VG_TRY(build_views(cams, n_views, params, &V, &cs, &pixels));
+    return launch_icp_associate(scene->dev, V, Dt, max_dist, weight, q, w, (cudaStream_t)stream);
+}
+
+vg_status vg_ssim_loss(vg_ctx* ctx, int32_t n_views, int32_t width, int32_t height, const float* C, const float* Ct,
+                       float weight, float* dC, float* loss, vg_stream stream) {
+    if (!ctx || !C || !Ct || n_views < 1 || width < 1 || height < 1)
+        return fail(VG_ERR_INVALID_ARG, "vg_ssim_loss: null argument or empty size");
+    const int64_t total = (int64_t)3 * n_views * width * height;
+    cudaStream_t st = (cudaStream_t)stream;
+    VG_TRY(ctx->ssim_ws.ensure((size_t)(8 * total + 1) * 4, st, "ssim workspace"));
+    return launch_ssim(n_views, width, height, C, Ct, weight, dC, loss, ctx->ssim_ws.as<float>(), st);
 }
 
 vg_status vg_mask_loss(const vg_scene* scene, vg_ctx* ctx, float weight, float* dmask_logit, float* loss,

@@ -75,6 +75,14 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, co
 cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, uint32_t* order, cudaStream_t st);
 cudaError_t launch_epoch_bump(uint32_t* state, uint32_t by, cudaStream_t st);
 
+// ssim.cu: workspace ws holds 8 * 3 * n_views * W * H + 1 floats
+vg_status launch_ssim(int n_views, int W, int H, const float* C, const float* Ct, float weight, float* dC, float* loss,
+                      float* ws, cudaStream_t st);
+
+// icp.cu
+vg_status launch_icp_associate(const SceneDev& S, const Views& V, const float* Dt, float max_dist, float weight, float* q,
+                               float* w, cudaStream_t st);
+
 // mask.cu
 vg_status vg_mask_kernels_loss(const SceneDev& S, const Views& V, const uint32_t* ntiles, float weight, float* dmask,
                                float* loss, uint32_t* scratch_u, float* scratch_f, cudaStream_t st);

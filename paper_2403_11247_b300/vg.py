@@ -100,6 +100,8 @@ def lib():
             "vg_probe_peak": [I32, I32, P, I64, P, P],
             "vg_rvq_encode": [P, I64, P, P, P, P, P],
             "vg_mask_loss": [P, P, C.c_float, P, P, P],
+            "vg_ssim_loss": [P, I32, I32, I32, P, P, C.c_float, P, P, P],
+            "vg_icp_associate": [P, P, I32, P, P, C.c_float, C.c_float, P, P, P],
             "vg_mask_prune": [P, P, P, C.c_uint32, P, P, P],
             "vg_adam_step": [P, I32, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
             "vg_pose_step": [I32, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
@@ -346,6 +348,30 @@ def vg_mask_prune(scene: SceneHandle, hit_count=None, seen=None, min_hits: int =
     return n_removed
 
 
+def vg_ssim_loss(ctx: CtxHandle, n_views: int, width: int, height: int, C_, Ct, weight: float = 1.0, dC=None,
+                 loss=None, stream=None):
+    torch = _torch()
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=C_.device)
+    _check(lib().vg_ssim_loss(ctx.handle, int(n_views), int(width), int(height), _ptr(C_), _ptr(Ct), float(weight),
+                              _ptr(dC), _ptr(loss), _stream(stream)), "vg_ssim_loss")
+    return loss
+
+
+def vg_icp_associate(scene: SceneHandle, cams, params, Dt, max_dist: float = 0.1, weight: float = 1.0, q=None, w=None,
+                     stream=None):
+    torch = _torch()
+    V_ = len(cams)
+    if q is None:
+        q = torch.empty((V_, scene.n, 3), dtype=torch.float32, device="cuda")
+    if w is None:
+        w = torch.empty((V_, scene.n), dtype=torch.float32, device="cuda")
+    p = params if params is not None else default_params()
+    _check(lib().vg_icp_associate(scene.handle, cameras(cams), V_, C.byref(p), _ptr(Dt), float(max_dist), float(weight),
+                                  _ptr(q), _ptr(w), _stream(stream)), "vg_icp_associate")
+    return q, w
+
+
 def image_sizes(cams):
     return [c.width * c.height for c in cams]
 
@@ -534,7 +560,7 @@ def exported_symbols():
             "vg_check", "vg_ctx_stats", "vg_ctx_reset_counters", "vg_ctx_buffer", "vg_ctx_profile",
             "vg_ctx_profile_read", "vg_adam_step", "vg_pose_step", "vg_rvq_decode", "vg_render_fwd",
             "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
-            "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune"]
+            "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune", "vg_ssim_loss", "vg_icp_associate"]
 
 
 PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),

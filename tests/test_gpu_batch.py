@@ -110,3 +110,24 @@ def test_local_ba_reduces_pose_error(torch):
     after = pose_errors(ba.pose.cpu().numpy().astype(np.float64), T_true)
     assert after[:, 0].mean() < 0.6 * before[:, 0].mean(), (before, after)
     assert after[:, 1].mean() < 0.6 * before[:, 1].mean(), (before, after)
+
+
+def test_local_ba_with_the_ssim_term(torch):
+    from paper_2403_11247_b300.autograd import SceneParams
+    from paper_2403_11247_b300.batch import LocalBA, pose_errors
+    sc = synth.tiny_scene()
+    truth = kf(perturbed=False, n=4)
+    scene = SceneParams.from_synth(sc, requires_grad=False)
+    sh = scene.handle()
+    ctx = V.vg_ctx_create(0)
+    Ct, Dt, _ = V.render_with_retry(sh, truth, V.default_params(), ctx)
+    ba = LocalBA(scene, kf(perturbed=True, n=4), Ct.clone(), Dt.clone(), w_ssim=0.2)
+    T_true = np.stack([np.asarray(c.T_cw, np.float64) for c in truth])
+    before = pose_errors(ba.pose.cpu().numpy().astype(np.float64), T_true)
+    ba.capture(40)
+    ba.replay()
+    torch.cuda.synchronize()
+    assert ba.check() == V.VG_OK
+    after = pose_errors(ba.pose.cpu().numpy().astype(np.float64), T_true)
+    assert float(ba.ssim_loss.item()) >= 0.0
+    assert after[:, 0].mean() < 0.7 * before[:, 0].mean(), (before, after)
