@@ -353,6 +353,69 @@ def local_ba_leg(torch, V, synth, iters=50):
     return res
 
 
+def tracking_leg(torch, V, synth, scene, n_frames=10, iters=90):
+    """Camera tracking on the mapping scene at 1200x680: a 10-frame path
+    through the room, targets rendered at the true poses (depth normalised by
+    coverage, like a sensor's), frames 0-1 at their true poses, every later
+    frame from the constant-velocity prediction of the two before it, then
+    `iters` tracking iterations (render, gated L1 + depth loss, backward to the
+    pose, projective ICP association and term, Adam on the pose) replayed as
+    one CUDA graph.  Also times the SSIM term of the local BA on its 8
+    keyframes of 640x480."""
+    from paper_2403_11247_b300.batch import pose_errors
+    from paper_2403_11247_b300.track import Tracker, constant_velocity
+    sh = V.vg_scene_upload(scene)
+    truth = synth.room_trajectory(n_frames)
+    ctx = V.vg_ctx_create(0)
+    targets = []
+    for c in truth:
+        C_, D, S = V.render_with_retry(sh, [c], V.default_params(), ctx)
+        Dn = torch.where(S > 0.5, D / S.clamp_min(1e-6), torch.zeros_like(D))
+        targets.append((C_.clone(), Dn.contiguous()))
+    tr = Tracker(sh, truth[0], iters=iters)
+    est = [np.asarray(truth[0].T_cw, np.float64), np.asarray(truth[1].T_cw, np.float64)]
+    init_err, ms = [], []
+    for t in range(2, n_frames):
+        T0 = constant_velocity(est[-2], est[-1])
+        init_err.append(pose_errors(T0[None], np.asarray(truth[t].T_cw, np.float64)[None])[0])
+        if t == 2:
+            tr.track(*targets[t], T0)      # captures the graph
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        est.append(tr.track(*targets[t], T0))
+        ms.append((time.perf_counter() - t0) * 1e3)
+    T_true = np.stack([np.asarray(c.T_cw, np.float64) for c in truth[2:]])
+    err = pose_errors(np.stack(est[2:]), T_true)
+    init_err = np.asarray(init_err)
+    res = {"scene": "mapping scene (320,000 Gaussians)", "size": "1200x680", "frames": n_frames - 2,
+           "iters_per_frame": iters, "ms_per_frame": statistics.median(ms),
+           "iters_per_s": iters / (statistics.median(ms) / 1e3),
+           "timing": "host clock around graph replay + synchronize + pose readback, median over frames",
+           "init_err_deg_m": [float(init_err[:, 0].mean()), float(init_err[:, 1].mean())],
+           "tracked_err_deg_m": [float(err[:, 0].mean()), float(err[:, 1].mean())]}
+    # the SSIM term at the local BA's size
+    B, Wk, Hk = 8, 640, 480
+    rng = np.random.default_rng(5)
+    x = torch.from_numpy(rng.uniform(size=3 * B * Wk * Hk).astype(np.float32)).cuda()
+    y = (x + 0.1 * torch.randn_like(x)).clamp(0, 1)
+    dC = torch.zeros_like(x)
+    loss = torch.zeros(1, device="cuda")
+    for _ in range(3):
+        V.vg_ssim_loss(ctx, B, Wk, Hk, x, y, 0.2, dC=dC, loss=loss)
+    times = []
+    for _ in range(20):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        V.vg_ssim_loss(ctx, B, Wk, Hk, x, y, 0.2, dC=dC, loss=loss)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    res["ssim_8x640x480_ms"] = statistics.median(times)
+    log(f"tracking: {res['ms_per_frame']:.2f} ms/frame ({iters} iters), err {res['tracked_err_deg_m']} "
+        f"from {res['init_err_deg_m']}; ssim {res['ssim_8x640x480_ms']:.3f} ms")
+    return res
+
+
 def large_leg(torch, V, synth, steps=20):
     """Large scene: 375k anchors x 8 = 3M Gaussians over 20 x 20 m, RVQ
     3 x 256, 30% masked, four 1920x1080 views in one launch sequence:
@@ -856,9 +919,11 @@ def run_ours(args):
     table = None
     if rank == 0 and args.configs:
         table = configs_table(torch, V, synth, os.cpu_count() or 1)
-    serving = ba_res = large = rvq = None
+    serving = ba_res = large = rvq = track = None
     if rank == 0:
         rvq = rvq_leg(torch, V)
+    if rank == 0 and not args.no_tracking:
+        track = tracking_leg(torch, V, synth, w["scene"])
     if rank == 0 and not args.no_large:
         large = large_leg(torch, V, synth)
     if rank == 0 and not args.no_serving:
@@ -881,7 +946,7 @@ def run_ours(args):
                 "p90_step_ms": float(np.percentile(step_ms, 90)), "p99_step_ms": float(np.percentile(step_ms, 99)),
                 "plain_launches": eager,
                 "serving": serving, "local_ba": ba_res, "large_scene": large, "configs_table": table,
-                "rvq_encode": rvq,
+                "rvq_encode": rvq, "tracking": track,
                 "peak_probes": {k: {"value": v["value"], "unit": v["unit"]} for k, v in probes.items()},
                 "derived_peaks": {"fp32_tflops": alu_peak, "ex2_g_per_s": n_sm * 32 * sm_mhz * 1e6 / 1e9,
                                   "smem_tb_per_s": n_sm * 128 * sm_mhz * 1e6 / 1e12}}
@@ -907,6 +972,7 @@ def main():
     ap.add_argument("--serving-seconds", type=float, default=2.0, help="length of each Poisson trace")
     ap.add_argument("--no-local-ba", action="store_true", help="skip the local bundle-adjustment leg")
     ap.add_argument("--no-large", action="store_true", help="skip the large-scene leg")
+    ap.add_argument("--no-tracking", action="store_true", help="skip the camera-tracking leg")
     ap.add_argument("--configs", action="store_true",
                     help="also time every configuration on the GPU and the oracle (minutes)")
     args = ap.parse_args()
