@@ -874,3 +874,146 @@ def test_projective_association_on_a_plane():
     # gated: a plane 0.5 m behind the means gives no correspondence at max_dist 0.2
     q2, w2 = associate(mu, np.ones(400, bool), [c], np.full(64 * 48, 3.0), 0.2)
     assert w2.sum() == 0
+
+
+# ---------------------------------------------------------------------------
+# anchor growing (Sec. "Sequential Anchor Point Growing", Eq. 10)
+# ---------------------------------------------------------------------------
+
+def test_splitmix64_published_outputs():
+    """The first three outputs of SplitMix64 seeded with 0, as published
+    with the generator (Steele, Lea and Flood 2014; the reference outputs
+    used to seed the xoshiro family)."""
+    from oracle.grow import GAMMA, MASK64, splitmix64
+    got = [splitmix64((i * GAMMA) & MASK64) for i in range(3)]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def _hand_growth_case():
+    # (position, gradient sum, count) per Gaussian; eps_g 1, tau_g 0.5, 3 levels
+    rows = [((0.3, 0.3, 0.3), 1.2, 2),      # voxel mean 0.6: grows at level 1 only
+            ((2.3, 0.1, 0.1), 3.0, 1),      # 3.0: levels 1, 2, 3
+            ((2.6, 0.6, 0.6), 5.0, 1),      # same level-1 voxel; its level-2 voxel holds the new level-1 anchor
+            ((5.2, 0.2, 0.2), 10.0, 1),     # level-1 voxel holds a scene anchor; levels 2, 3
+            ((-0.5, 0.5, 0.5), 0.2, 1),     # level-1 voxel mean (0.2 + 0.9) / 2 = 0.55
+            ((-0.7, 0.2, 0.2), 0.9, 1),
+            ((-1.5, 0.5, 0.5), 0.9, 3),     # averages 0.3 and 0.3: mean 0.3 (a sum would pass)
+            ((-1.2, 0.3, 0.3), 0.3, 1),
+            ((-2.1, 0.9, 0.9), 0.3, 3),     # averages 0.1 and 1.0: mean 0.55 (pair-weighted 0.325)
+            ((-2.9, 0.1, 0.1), 1.0, 1),     # level 2: 1.0 is not above tau_2 = 1
+            ((10.2, 0.2, 0.2), 5.0, 0)]     # never seen
+    mu = np.array([r[0] for r in rows], np.float32)
+    gs = np.array([r[1] for r in rows], np.float32)
+    gc = np.array([r[2] for r in rows], np.int64)
+    anchors = np.array([[5.9, 0.9, 0.9]], np.float32)
+    expected = {(1, (0.5, 0.5, 0.5)), (1, (2.5, 0.5, 0.5)), (1, (-0.5, 0.5, 0.5)), (1, (-2.5, 0.5, 0.5)),
+                (2, (2.375, 0.125, 0.125)), (2, (5.125, 0.125, 0.125)),
+                (3, (2.28125, 0.09375, 0.09375)), (3, (2.59375, 0.59375, 0.59375)),
+                (3, (5.21875, 0.21875, 0.21875))}
+    return mu, gs, gc, anchors, expected
+
+
+def test_anchor_growing_hand_case():
+    """Eq. 10's levels (eps / 4^(m-1), tau * 2^(m-1)), the voxel mean of the
+    per-Gaussian averages, strict threshold, occupancy by scene anchors and by
+    anchors grown at coarser levels, unseen Gaussians left out: every
+    expected centre worked out by hand."""
+    from oracle.grow import grow
+    mu, gs, gc, anchors, expected = _hand_growth_case()
+    out = grow(mu, gs, gc, anchors, 1.0, 0.5, levels=3, p_drop=0.0)
+    got = {(m, tuple(float(x) for x in c)) for m, _, c in out}
+    assert got == expected
+    assert len(out) == len(expected)
+
+
+def test_anchor_growing_brute_force_voxel_means():
+    """Random Gaussians on a small grid: the grown set equals a brute-force
+    enumeration of every voxel of every level (pure Python loops over the
+    Gaussians per voxel)."""
+    from oracle.grow import grow
+    rng = np.random.default_rng(21)
+    n = 300
+    mu = rng.uniform(-1.0, 1.0, size=(n, 3)).astype(np.float32)
+    gc = rng.integers(0, 4, size=n)
+    gs = (gc * rng.uniform(0.0, 2.0, size=n)).astype(np.float32)
+    anchors = rng.uniform(-1.0, 1.0, size=(5, 3)).astype(np.float32)
+    eps_g, tau_g = 0.5, 0.6
+    out = grow(mu, gs, gc, anchors, eps_g, tau_g, levels=2, p_drop=0.0)
+    est = [tuple(a) for a in anchors.tolist()]
+    want = set()
+    for m in (1, 2):
+        eps = eps_g / 4 ** (m - 1)
+        tau = tau_g * 2 ** (m - 1)
+        cells = {}
+        for i in range(n):
+            if gc[i] == 0:
+                continue
+            cell = tuple(int(np.floor(np.float32(mu[i][c]) / np.float32(eps))) for c in range(3))
+            cells.setdefault(cell, []).append(float(np.float32(gs[i]) / np.float32(gc[i])))
+        occ = {tuple(int(np.floor(np.float32(a[c]) / np.float32(eps))) for c in range(3)) for a in est}
+        grown = []
+        for cell, avgs in cells.items():
+            if cell not in occ and sum(avgs) / len(avgs) > tau:
+                grown.append(tuple(float(np.float32((cell[c] + 0.5) * eps)) for c in range(3)))
+        want |= {(m, g) for g in grown}
+        est += grown
+    got = {(m, tuple(float(x) for x in c)) for m, _, c in out}
+    assert got == want and len(want) > 10
+
+
+def test_anchor_growing_random_elimination():
+    """p_drop 0 keeps every candidate, 1 drops all; the kept sets are nested
+    as p_drop grows; the kept fraction is binomial around 1 - p_drop."""
+    from oracle.grow import grow
+    rng = np.random.default_rng(22)
+    n = 4000
+    mu = rng.uniform(-10.0, 10.0, size=(n, 3)).astype(np.float32)
+    gc = np.ones(n, np.int64)
+    gs = np.full(n, 2.0, np.float32)
+    anchors = np.zeros((0, 3), np.float32)
+    full = {(m, k) for m, k, _ in grow(mu, gs, gc, anchors, 0.05, 1.0, levels=1, p_drop=0.0, seed=7)}
+    assert len(full) == n
+    assert grow(mu, gs, gc, anchors, 0.05, 1.0, levels=1, p_drop=1.0, seed=7) == []
+    k3 = {(m, k) for m, k, _ in grow(mu, gs, gc, anchors, 0.05, 1.0, levels=1, p_drop=0.3, seed=7)}
+    k7 = {(m, k) for m, k, _ in grow(mu, gs, gc, anchors, 0.05, 1.0, levels=1, p_drop=0.7, seed=7)}
+    assert k7 <= k3 <= full
+    for kept, p in ((k3, 0.3), (k7, 0.7)):
+        sd = np.sqrt(n * p * (1 - p))
+        assert abs(len(kept) - n * (1 - p)) < 5 * sd, (len(kept), p)
+    other = {(m, k) for m, k, _ in grow(mu, gs, gc, anchors, 0.05, 1.0, levels=1, p_drop=0.3, seed=8)}
+    assert other != k3
+
+
+def test_anchor_positions_and_prune_definitions():
+    """mu = x_a + O l per Gaussian; an anchor seen with mean opacity below
+    tau_alpha is removed on all its Gaussians, an unseen one never, the
+    threshold itself is kept."""
+    from oracle.grow import positions, prune
+    xa = np.array([[1.0, 2.0, 3.0]], np.float32)
+    l = np.array([[0.5, 2.0, 1.0]], np.float32)
+    off = np.array([[[1.0, 1.0, 1.0], [-2.0, 0.0, 0.25]]], np.float32)
+    assert np.array_equal(positions(xa, l, off), np.array([[1.5, 4.0, 4.0], [0.0, 2.0, 3.25]], np.float32))
+    k = 2
+    m0 = np.zeros(8)
+    s = np.array([0.05, 0.3, 0.0, 0.2], np.float32)
+    c = np.array([1, 2, 0, 2])
+    m, removed = prune(m0, s, c, k, 0.1)
+    assert removed.tolist() == [True, False, False, False]
+    assert np.isneginf(m[:2]).all() and np.all(m[2:] == 0)
+
+
+def test_growing_statistics_definition():
+    """Per pair: |(du, dv)| to its Gaussian, opacity to its anchor, counts;
+    views add; invalid slots contribute nothing."""
+    from oracle.grow import accumulate
+    k, n_views, N = 2, 2, 4
+    g2d = np.zeros((n_views * N, 10))
+    g2d[0, :2] = (3.0, 4.0)
+    g2d[1, :2] = (0.6, 0.8)
+    g2d[N + 0, :2] = (5.0, 12.0)
+    g2d[N + 3, :2] = (8.0, 6.0)
+    valid = np.array([1, 1, 0, 0, 1, 0, 0, 1])
+    opa = np.array([0.1, 0.2, 0.9, 0.9, 0.3, 0.9, 0.9, 0.4])
+    gs, gc, os_, oc = accumulate(g2d, valid, opa, k, n_views)
+    assert np.allclose(gs, [5.0 + 13.0, 1.0, 0.0, 10.0]) and gc.tolist() == [2, 1, 0, 1]
+    assert np.allclose(os_, [0.1 + 0.2 + 0.3, 0.4]) and oc.tolist() == [3, 1]
