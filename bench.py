@@ -355,7 +355,8 @@ def local_ba_leg(torch, V, synth, iters=50):
 
 def tracking_leg(torch, V, synth, scene, n_frames=10, iters=90):
     """Camera tracking on the mapping scene at 1200x680: a 10-frame path
-    through the room, targets rendered at the true poses (depth normalised by
+    through the room shaken per frame by up to 0.3 deg / 1 cm (so that the
+    constant-velocity prediction is off), targets rendered at the true poses (depth normalised by
     coverage, like a sensor's), frames 0-1 at their true poses, every later
     frame from the constant-velocity prediction of the two before it, then
     `iters` tracking iterations (render, gated L1 + depth loss, backward to the
@@ -365,7 +366,7 @@ def tracking_leg(torch, V, synth, scene, n_frames=10, iters=90):
     from paper_2403_11247_b300.batch import pose_errors
     from paper_2403_11247_b300.track import Tracker, constant_velocity
     sh = V.vg_scene_upload(scene)
-    truth = synth.room_trajectory(n_frames)
+    truth = synth.room_trajectory(n_frames, jitter_deg=0.3, jitter_m=0.01)
     ctx = V.vg_ctx_create(0)
     targets = []
     for c in truth:
@@ -413,6 +414,65 @@ def tracking_leg(torch, V, synth, scene, n_frames=10, iters=90):
     res["ssim_8x640x480_ms"] = statistics.median(times)
     log(f"tracking: {res['ms_per_frame']:.2f} ms/frame ({iters} iters), err {res['tracked_err_deg_m']} "
         f"from {res['init_err_deg_m']}; ssim {res['ssim_8x640x480_ms']:.3f} ms")
+    return res
+
+
+def growing_leg(torch, V, synth, scene, reps=20, with_oracle=True):
+    """Anchor growing on the mapping scene (320,000 Gaussians): the growing
+    statistics of one 1200x680 backward (vg_grow_accumulate), and one growing
+    pass over three voxel levels (eps_g 0.2 m) with the seeded statistics of
+    the parity tests (about 70% of the Gaussians seen), against the numpy
+    oracle on the same inputs."""
+    sh = V.vg_scene_upload(scene)
+    ctx = V.vg_ctx_create(0)
+    cam = [synth.room_camera()]
+    params = V.default_params()
+    C_, D, S = V.render_with_retry(sh, cam, params, ctx)
+    dC, dD = torch.full_like(C_, 1e-6), torch.full_like(D, 1e-6)
+    V.vg_render_bwd(sh, cam, params, ctx, dC, dD, None, grads={})
+    A, k = scene.offsets.shape[0], scene.offsets.shape[1]
+    N = A * k
+    gs = torch.zeros(N, device="cuda")
+    gc = torch.zeros(N, dtype=torch.int32, device="cuda")
+    os_ = torch.zeros(A, device="cuda")
+    oc = torch.zeros(A, dtype=torch.int32, device="cuda")
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    acc_ms = timed(lambda: V.vg_grow_accumulate(sh, ctx, gs, gc, os_, oc))
+    rng = np.random.default_rng(100)
+    cnt = np.where(rng.uniform(size=N) < 0.7, rng.integers(1, 5, size=N), 0).astype(np.int32)
+    s = (cnt * rng.lognormal(mean=-1.0, sigma=1.0, size=N)).astype(np.float32)
+    g_s, g_c = torch.from_numpy(s).cuda(), torch.from_numpy(cnt).cuda()
+    out = [None]
+
+    def run():
+        out[0] = V.vg_anchor_grow(sh, ctx, g_s, g_c, 0.2, 0.5, 3, 0.25, 99, 1 << 20)
+    grow_ms = timed(run)
+    n_new = int(out[0][2].item())
+    res = {"gaussians": N, "visible_slots": int(V.vg_ctx_stats(ctx)["visible"]), "accumulate_ms": acc_ms,
+           "grow_ms_3_levels": grow_ms, "new_anchors": n_new, "g_gaussians_per_s": 3 * N / grow_ms / 1e6,
+           "cpu_baseline": None}
+    if with_oracle:
+        from oracle.grow import grow, positions
+        t0 = time.perf_counter()
+        ref = grow(positions(scene.anchor_xyz, scene.anchor_l, scene.offsets), s, cnt, scene.anchor_xyz, 0.2, 0.5, 3,
+                   0.25, 99)
+        res["cpu_baseline"] = {"kind": "oracle", "s_per_grow": time.perf_counter() - t0, "new_anchors": len(ref),
+                               "cores": 1, "sample": "the whole growing pass, numpy"}
+    log(f"growing: accumulate {acc_ms * 1e3:.1f} us, grow {grow_ms:.3f} ms ({n_new} new anchors)")
     return res
 
 
@@ -582,11 +642,10 @@ def configs_table(torch, V, synth, threads):
     return out
 
 
-def rvq_leg(torch, V, n=320000, L=3, K=64, reps=20):
+def rvq_leg(torch, V, n=320000, L=3, K=64, reps=20, with_oracle=True):
     """Residual quantisation encode + codebook loss and gradient (Eq. 14-15)
     of the mapping scene's four attribute groups (n items each; dims 3, 4,
     1, 3; 3 stages of 64 codewords), against the numpy oracle on 20k items."""
-    from oracle.rvq_encode import rvq_encode
     rng = np.random.default_rng(9)
     groups = []
     for d in (3, 4, 1, 3):
@@ -612,10 +671,13 @@ def rvq_leg(torch, V, n=320000, L=3, K=64, reps=20):
         times.append(a.elapsed_time(b))
     ms = statistics.median(times)
     m = 20000
-    t0 = time.perf_counter()
-    for cb, x, _, _, _ in groups:
-        rvq_encode(cb.cpu().numpy(), x[:m].cpu().numpy())
-    cpu_s = (time.perf_counter() - t0) * n / m
+    cpu_s = None
+    if with_oracle:
+        from oracle.rvq_encode import rvq_encode
+        t0 = time.perf_counter()
+        for cb, x, _, _, _ in groups:
+            rvq_encode(cb.cpu().numpy(), x[:m].cpu().numpy())
+        cpu_s = (time.perf_counter() - t0) * n / m
     flop = sum(n * L * K * d * 3 for d in (3, 4, 1, 3))   # subtract, multiply, add per component
     res = {"items": n, "groups": "dims 3, 4, 1, 3", "stages": L, "codewords": K, "ms_per_encode": ms,
            "g_items_per_s": 4 * n / ms / 1e6, "distance_tflops": flop / ms / 1e9,
@@ -919,11 +981,12 @@ def run_ours(args):
     table = None
     if rank == 0 and args.configs:
         table = configs_table(torch, V, synth, os.cpu_count() or 1)
-    serving = ba_res = large = rvq = track = None
+    serving = ba_res = large = rvq = track = growing = None
     if rank == 0:
-        rvq = rvq_leg(torch, V)
+        rvq = rvq_leg(torch, V, with_oracle=not args.no_cpu_baseline)
     if rank == 0 and not args.no_tracking:
         track = tracking_leg(torch, V, synth, w["scene"])
+        growing = growing_leg(torch, V, synth, w["scene"], with_oracle=not args.no_cpu_baseline)
     if rank == 0 and not args.no_large:
         large = large_leg(torch, V, synth)
     if rank == 0 and not args.no_serving:
@@ -946,7 +1009,7 @@ def run_ours(args):
                 "p90_step_ms": float(np.percentile(step_ms, 90)), "p99_step_ms": float(np.percentile(step_ms, 99)),
                 "plain_launches": eager,
                 "serving": serving, "local_ba": ba_res, "large_scene": large, "configs_table": table,
-                "rvq_encode": rvq, "tracking": track,
+                "rvq_encode": rvq, "tracking": track, "anchor_growing": growing,
                 "peak_probes": {k: {"value": v["value"], "unit": v["unit"]} for k, v in probes.items()},
                 "derived_peaks": {"fp32_tflops": alu_peak, "ex2_g_per_s": n_sm * 32 * sm_mhz * 1e6 / 1e9,
                                   "smem_tb_per_s": n_sm * 128 * sm_mhz * 1e6 / 1e12}}

@@ -411,6 +411,47 @@ vg_status vg_mask_loss(const vg_scene* scene, vg_ctx* ctx, float weight, float* 
 vg_status vg_mask_prune(vg_scene* scene, const uint32_t* hit_count, const uint32_t* seen, uint32_t min_hits,
                         uint32_t* removed, uint32_t* n_removed, vg_stream stream);
 
+/* Sequential anchor growing and opacity-based anchor removal (Sec.
+ * "Sequential Anchor Point Growing", Eq. 10).
+ * vg_grow_accumulate, after vg_render_bwd of `scene` on `ctx`: for every
+ * (view, Gaussian) pair visible in that forward, ADDS the norm of the loss
+ * gradient with respect to the projected mean, sqrt(du^2 + dv^2) in pixel
+ * units, to grad_sum[n] and 1 to grad_cnt[n] ([N], device), and the
+ * Gaussian's opacity sigmoid(o_n) to opa_sum[a] and 1 to opa_cnt[a] ([A],
+ * device; a = n / k).  Either pair of arrays may be NULL (both of a pair).
+ * vg_anchor_grow: for levels m = 1..levels, voxel size eps_m = eps_g / 4^(m-1)
+ * and threshold tau_m = tau_g * 2^(m-1): every voxel floor(mu / eps_m) (FP32;
+ * mu = x_a + O l) whose Gaussians with grad_cnt > 0 have a mean of their
+ * averages grad_sum / grad_cnt (FP32) above tau_m, that holds no anchor of
+ * the scene and none grown at a coarser level, and that survives the random
+ * elimination (kept iff SplitMix64(key ^ (seed + m * 0x9E3779B97F4A7C15))
+ * >> 11 >= floor(p_drop * 2^53), key the voxel index packed as
+ * (ix + 2^20) << 42 | (iy + 2^20) << 21 | (iz + 2^20)), gets a new anchor at
+ * its centre ((index + 0.5) * eps_m, FP32): new_xyz [cap][3] and, if not
+ * NULL, new_level [cap] (m) receive up to cap of them in unspecified order;
+ * n_new[0] (device) receives how many there were (more than cap: the output
+ * is truncated and finer levels saw only the first cap; call again with a
+ * larger cap).  The voxel mean is decided exactly: each average enters as
+ * rint(avg * 2^32) (clamped to +-2^52) in a 64-bit integer sum compared in
+ * FP64 with (tau_m * 2^32) * count; non-finite averages and voxel indices
+ * outside [-2^20, 2^20) are skipped.  Workspace: a hash table of
+ * 24 bytes x the next power of two >= 2 (A + N + cap) + 1024, in the ctx.
+ * vg_anchor_prune: every anchor with opa_cnt[a] > 0 and
+ * opa_sum[a] < tau_alpha * opa_cnt[a] (FP32) is removed: the mask logits of
+ * its k Gaussians become -inf in the scene's own array; removed [A] (0/1) and
+ * n_removed[0] are optional device outputs.
+ * Errors: VG_ERR_INVALID_ARG for null arrays, levels outside 1..8,
+ * eps_g <= 0, p_drop outside [0, 1], cap < 0, or (prune) a scene without
+ * mask logits; vg_grow_accumulate needs a vg_render_bwd of this scene on
+ * this ctx. */
+vg_status vg_grow_accumulate(const vg_scene* scene, vg_ctx* ctx, float* grad_sum, uint32_t* grad_cnt, float* opa_sum,
+                             uint32_t* opa_cnt, vg_stream stream);
+vg_status vg_anchor_grow(const vg_scene* scene, vg_ctx* ctx, const float* grad_sum, const uint32_t* grad_cnt,
+                         float eps_g, float tau_g, int32_t levels, double p_drop, uint64_t seed, int64_t cap,
+                         float* new_xyz, int32_t* new_level, uint32_t* n_new, vg_stream stream);
+vg_status vg_anchor_prune(vg_scene* scene, const float* opa_sum, const uint32_t* opa_cnt, float tau_alpha,
+                          uint32_t* removed, uint32_t* n_removed, vg_stream stream);
+
 /* Throughput probe for roofline denominators (a measurement facility; the
  * paper has no counterpart).  Enqueues one kernel on `stream` over a grid of
  * (SM count x 8) blocks of 256 threads, each thread running `iters` steps of:

@@ -176,7 +176,7 @@ struct vg_ctx {
     StageProfiler prof;
     int64_t pair_cap = 0;
     DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, tile_order, Tfin, ncontrib, lookback,
-        scratch, state, pose_part, icp_part, loss_scratch, pair_off, blk_count, blk_base, vis, ssim_ws;
+        scratch, state, pose_part, icp_part, loss_scratch, pair_off, blk_count, blk_base, vis, ssim_ws, grow_ws;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
     bool g2d_clean = false;
@@ -421,6 +421,7 @@ vg_status vg_check(vg_ctx* ctx, vg_stream stream) {
     if (s.flags) {
         VG_CUDA(cudaMemset(ctx->state.as<uint32_t>() + ST_ERR, 0, 4));
         if (s.flags & ERR_WAIT) return fail(VG_ERR_TIMEOUT, "a bounded device wait ran out");
+        if (s.flags & ERR_TABLE) return fail(VG_ERR_CAPACITY, "anchor-growing hash table full");
         return fail(VG_ERR_CAPACITY, "pair buffer too small: " + std::to_string(s.pairs) + " pairs needed, capacity " +
                                          std::to_string(s.pair_capacity));
     }
@@ -672,6 +673,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     ctx->fwd_N = N;
     ctx->fwd_scene = scene;
     ctx->have_fwd = true;
+    ctx->have_bwd = false;
     return VG_OK;
 }
 
@@ -838,6 +840,45 @@ vg_status vg_mask_prune(vg_scene* scene, const uint32_t* hit_count, const uint32
         return fail(VG_ERR_INVALID_ARG, "vg_mask_prune: hit_count and seen go together");
     return vg_mask_kernels_prune(const_cast<float*>(scene->dev.mask), scene->dev.mask_thr, hit_count, seen, min_hits,
                                  scene->dev.N, removed, n_removed, (cudaStream_t)stream);
+}
+
+vg_status vg_grow_accumulate(const vg_scene* scene, vg_ctx* ctx, float* grad_sum, uint32_t* grad_cnt, float* opa_sum,
+                             uint32_t* opa_cnt, vg_stream stream) {
+    if (!scene || !ctx) return fail(VG_ERR_INVALID_ARG, "vg_grow_accumulate: null argument");
+    if ((grad_sum == nullptr) != (grad_cnt == nullptr) || (opa_sum == nullptr) != (opa_cnt == nullptr))
+        return fail(VG_ERR_INVALID_ARG, "vg_grow_accumulate: sums and counts go together");
+    if (!ctx->have_bwd || ctx->fwd_scene != scene)
+        return fail(VG_ERR_INVALID_ARG, "vg_grow_accumulate: no vg_render_bwd of this scene on this ctx");
+    if (scene->dev.N == 0 || (!grad_sum && !opa_sum)) return VG_OK;
+    const uint32_t slots = (uint32_t)(ctx->views.n * scene->dev.N);
+    VG_CUDA(launch_grow_stats(scene->dev, ctx->vis.as<uint32_t>(), ctx->scratch.as<uint32_t>() + SCR_NVIS, slots,
+                              ctx->g2d.as<float>(), grad_sum, grad_cnt, opa_sum, opa_cnt, (cudaStream_t)stream));
+    return VG_OK;
+}
+
+vg_status vg_anchor_grow(const vg_scene* scene, vg_ctx* ctx, const float* grad_sum, const uint32_t* grad_cnt,
+                         float eps_g, float tau_g, int32_t levels, double p_drop, uint64_t seed, int64_t cap,
+                         float* new_xyz, int32_t* new_level, uint32_t* n_new, vg_stream stream) {
+    if (!scene || !ctx || !grad_sum || !grad_cnt || !n_new || (cap > 0 && !new_xyz))
+        return fail(VG_ERR_INVALID_ARG, "vg_anchor_grow: null argument");
+    if (levels < 1 || levels > 8 || !(eps_g > 0.f) || !(p_drop >= 0.0 && p_drop <= 1.0) || cap < 0)
+        return fail(VG_ERR_INVALID_ARG, "vg_anchor_grow: levels must be 1..8, eps_g > 0, p_drop in [0, 1], cap >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t slots = grow_table_slots(scene->dev.n_anchors, scene->dev.N, cap);
+    VG_TRY(ctx->grow_ws.ensure((size_t)slots * 24, st, "anchor-growing table"));
+    const unsigned long long drop_below = (unsigned long long)std::floor(p_drop * 9007199254740992.0);
+    VG_CUDA(launch_grow(scene->dev, grad_sum, grad_cnt, eps_g, tau_g, levels, drop_below, (unsigned long long)seed,
+                        new_xyz, new_level, n_new, cap, ctx->grow_ws.p, slots, ctx->state.as<uint32_t>() + ST_ERR, st));
+    return VG_OK;
+}
+
+vg_status vg_anchor_prune(vg_scene* scene, const float* opa_sum, const uint32_t* opa_cnt, float tau_alpha,
+                          uint32_t* removed, uint32_t* n_removed, vg_stream stream) {
+    if (!scene || !opa_sum || !opa_cnt) return fail(VG_ERR_INVALID_ARG, "vg_anchor_prune: null argument");
+    if (!scene->dev.mask) return fail(VG_ERR_INVALID_ARG, "vg_anchor_prune: the scene has no mask logits");
+    VG_CUDA(launch_anchor_prune(const_cast<float*>(scene->dev.mask), scene->dev.n_anchors, scene->dev.k, opa_sum,
+                                opa_cnt, tau_alpha, removed, n_removed, (cudaStream_t)stream));
+    return VG_OK;
 }
 
 vg_status vg_adam_step(const vg_adam_tensor* tensors, int32_t n, float lr, float beta1, float beta2, float eps,

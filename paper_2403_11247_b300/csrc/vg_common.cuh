@@ -14,6 +14,7 @@ constexpr int TILE_PIX = TILE * TILE;
 // device status bits (vg_stats.flags)
 constexpr uint32_t ERR_WAIT = 1u;      // a bounded spin ran out
 constexpr uint32_t ERR_OVERFLOW = 2u;  // pair buffer too small
+constexpr uint32_t ERR_TABLE = 4u;     // the anchor-growing hash table was full
 
 // a bounded spin gives up after this many polls (~1 s of L2 round trips)
 constexpr uint32_t SPIN_LIMIT = 1u << 21;

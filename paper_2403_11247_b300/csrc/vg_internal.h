@@ -83,6 +83,17 @@ vg_status launch_ssim(int n_views, int W, int H, const float* C, const float* Ct
 vg_status launch_icp_associate(const SceneDev& S, const Views& V, const float* Dt, float max_dist, float weight, float* q,
                                float* w, cudaStream_t st);
 
+// grow.cu
+int64_t grow_table_slots(int64_t A, int64_t N, int64_t cap);
+cudaError_t launch_grow_stats(const SceneDev& S, const uint32_t* vis, const uint32_t* nvis_dev, uint32_t max_vis,
+                              const float* g2d, float* gacc, uint32_t* gcnt, float* oacc, uint32_t* ocnt,
+                              cudaStream_t st);
+cudaError_t launch_grow(const SceneDev& S, const float* gacc, const uint32_t* gcnt, float eps_g, float tau_g, int levels,
+                        unsigned long long drop_below, unsigned long long seed, float* new_xyz, int32_t* new_level,
+                        uint32_t* n_new, int64_t cap, void* ws, int64_t slots, uint32_t* err, cudaStream_t st);
+cudaError_t launch_anchor_prune(float* mask, int64_t A, int k, const float* oacc, const uint32_t* ocnt, float tau_alpha,
+                                uint32_t* removed, uint32_t* n_removed, cudaStream_t st);
+
 // mask.cu
 vg_status vg_mask_kernels_loss(const SceneDev& S, const Views& V, const uint32_t* ntiles, float weight, float* dmask,
                                float* loss, uint32_t* scratch_u, float* scratch_f, cudaStream_t st);

@@ -299,16 +299,22 @@ def room_camera(width: int = 1200, height: int = 680, f: float = 600.0, pose_see
 
 
 def room_trajectory(n_frames: int = 10, width: int = 1200, height: int = 680, f: float = 600.0,
-                    step_m: float = 0.01, step_deg: float = 0.25) -> List[Camera]:
-    """A smooth handheld-like path through the room: the camera of
-    room_camera() slides sideways by step_m and turns by step_deg about the
-    vertical per frame, with a small vertical bob."""
+                    step_m: float = 0.01, step_deg: float = 0.25, jitter_deg: float = 0.0, jitter_m: float = 0.0,
+                    seed: int = 1006) -> List[Camera]:
+    """A handheld-like path through the room: the camera of room_camera()
+    slides sideways by step_m and turns by step_deg about the vertical per
+    frame, with a small vertical bob, each pose then shaken by a random rigid
+    motion (up to jitter_deg / jitter_m)."""
+    rng = np.random.default_rng(seed)
     cams = []
     for i in range(n_frames):
         eye = np.array([2.25 - 0.5 * step_m * n_frames + step_m * i, 2.0, 1.3 + 0.01 * math.sin(0.7 * i)])
         a = math.radians(step_deg * (i - 0.5 * n_frames))
         target = eye + np.array([2.0 * math.sin(a), 2.0 * math.cos(a), -0.6])
-        cams.append(camera(f, f, (width - 1) / 2.0, (height - 1) / 2.0, width, height, look_at(eye, target)))
+        T = look_at(eye, target)
+        if jitter_deg > 0 or jitter_m > 0:
+            T = perturb_pose(T, rng, jitter_deg, jitter_m)
+        cams.append(camera(f, f, (width - 1) / 2.0, (height - 1) / 2.0, width, height, T))
     return cams
 
 

@@ -103,6 +103,9 @@ def lib():
             "vg_ssim_loss": [P, I32, I32, I32, P, P, C.c_float, P, P, P],
             "vg_icp_associate": [P, P, I32, P, P, C.c_float, C.c_float, P, P, P],
             "vg_mask_prune": [P, P, P, C.c_uint32, P, P, P],
+            "vg_grow_accumulate": [P, P, P, P, P, P, P],
+            "vg_anchor_grow": [P, P, P, P, C.c_float, C.c_float, I32, C.c_double, C.c_uint64, I64, P, P, P, P],
+            "vg_anchor_prune": [P, P, P, C.c_float, P, P, P],
             "vg_adam_step": [P, I32, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
             "vg_pose_step": [I32, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
         }
@@ -338,6 +341,44 @@ def vg_mask_loss(scene: SceneHandle, ctx: CtxHandle, weight: float = 1.0, dmask=
     return loss
 
 
+def vg_grow_accumulate(scene: SceneHandle, ctx: CtxHandle, grad_sum=None, grad_cnt=None, opa_sum=None, opa_cnt=None,
+                       stream=None):
+    """Adds the last backward's per-pair growing statistics to the given
+    accumulators (grad_sum/grad_cnt [N], opa_sum/opa_cnt [A])."""
+    _check(lib().vg_grow_accumulate(scene.handle, ctx.handle, _ptr(grad_sum), _ptr(grad_cnt), _ptr(opa_sum),
+                                    _ptr(opa_cnt), _stream(stream)), "vg_grow_accumulate")
+
+
+def vg_anchor_grow(scene: SceneHandle, ctx: CtxHandle, grad_sum, grad_cnt, eps_g: float, tau_g: float, levels: int = 3,
+                   p_drop: float = 0.0, seed: int = 0, cap: int = 65536, new_xyz=None, new_level=None, n_new=None,
+                   stream=None):
+    """New anchor centres on the multi-resolution voxel grid; returns
+    (new_xyz [cap][3], new_level [cap], n_new [1]) device tensors, the first
+    min(n_new, cap) rows valid, in unspecified order."""
+    torch = _torch()
+    if new_xyz is None:
+        new_xyz = torch.empty((max(cap, 1), 3), dtype=torch.float32, device="cuda")
+    if new_level is None:
+        new_level = torch.empty(max(cap, 1), dtype=torch.int32, device="cuda")
+    if n_new is None:
+        n_new = torch.empty(1, dtype=torch.int32, device="cuda")
+    _check(lib().vg_anchor_grow(scene.handle, ctx.handle, _ptr(grad_sum), _ptr(grad_cnt), float(eps_g), float(tau_g),
+                                int(levels), float(p_drop), int(seed) & ((1 << 64) - 1), int(cap), _ptr(new_xyz),
+                                _ptr(new_level), _ptr(n_new), _stream(stream)), "vg_anchor_grow")
+    return new_xyz, new_level, n_new
+
+
+def vg_anchor_prune(scene: SceneHandle, opa_sum, opa_cnt, tau_alpha: float, removed=None, n_removed=None, stream=None):
+    """Removes (mask logit -inf on all k Gaussians) every anchor seen with a
+    mean opacity below tau_alpha; returns n_removed [1]."""
+    torch = _torch()
+    if n_removed is None:
+        n_removed = torch.empty(1, dtype=torch.int32, device="cuda")
+    _check(lib().vg_anchor_prune(scene.handle, _ptr(opa_sum), _ptr(opa_cnt), float(tau_alpha), _ptr(removed),
+                                 _ptr(n_removed), _stream(stream)), "vg_anchor_prune")
+    return n_removed
+
+
 def vg_mask_prune(scene: SceneHandle, hit_count=None, seen=None, min_hits: int = 1, removed=None, n_removed=None,
                   stream=None):
     torch = _torch()
@@ -560,7 +601,8 @@ def exported_symbols():
             "vg_check", "vg_ctx_stats", "vg_ctx_reset_counters", "vg_ctx_buffer", "vg_ctx_profile",
             "vg_ctx_profile_read", "vg_adam_step", "vg_pose_step", "vg_rvq_decode", "vg_render_fwd",
             "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
-            "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune", "vg_ssim_loss", "vg_icp_associate"]
+            "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune", "vg_ssim_loss", "vg_icp_associate",
+            "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune"]
 
 
 PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),
