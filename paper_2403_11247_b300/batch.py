@@ -117,7 +117,9 @@ def pose_errors(T_a: np.ndarray, T_b: np.ndarray):
     out = []
     for A, Bm in zip(T_a.reshape(-1, 3, 4), T_b.reshape(-1, 3, 4)):
         Rr = A[:, :3] @ Bm[:, :3].T
-        ang = np.degrees(np.arccos(np.clip((np.trace(Rr) - 1) / 2, -1.0, 1.0)))
+        # atan2(sin, cos) of the relative rotation: accurate for small angles too
+        sin = 0.5 * np.linalg.norm([Rr[2, 1] - Rr[1, 2], Rr[0, 2] - Rr[2, 0], Rr[1, 0] - Rr[0, 1]])
+        ang = np.degrees(np.arctan2(sin, (np.trace(Rr) - 1) / 2))
         ca = -A[:, :3].T @ A[:, 3]
         cb = -Bm[:, :3].T @ Bm[:, 3]
         out.append((ang, float(np.linalg.norm(ca - cb))))

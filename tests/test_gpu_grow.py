@@ -72,13 +72,17 @@ def test_anchor_growing_edge_cases(torch):
     assert got == want and len(want) > 0
     got, want = _grow_both(torch, sc, gs, gc, 0.2, 0.5, 3, 1.0, 0)
     assert got == want == []
-    # one level, the hand case of the oracle's pins through the scene layout:
-    # anchors at the Gaussian positions with zero offsets
+    # the hand case of the oracle's pins through the scene layout: one
+    # Gaussian per anchor, each anchor far away (x = 50 + 3 i) and the offset
+    # carrying the Gaussian to its position (FP32 rounding moves none of them
+    # across a voxel face that matters), plus the established anchor
     from test_oracle_pins import _hand_growth_case
     mu, hs, hc, anchors, expected = _hand_growth_case()
     n = len(mu)
-    xyz = np.concatenate([mu, anchors]).astype(np.float32)
-    hand = synth.Scene(xyz, np.ones_like(xyz), np.zeros((n + 1, 1, 3), np.float32),
+    far = np.stack([50.0 + 3.0 * np.arange(n), np.full(n, 50.0), np.full(n, 50.0)], 1).astype(np.float32)
+    xyz = np.concatenate([far, anchors]).astype(np.float32)
+    off = np.concatenate([mu - far, np.zeros((1, 3), np.float32)]).astype(np.float32)[:, None, :]
+    hand = synth.Scene(xyz, np.ones_like(xyz), off,
                        {k: synth.Group(d, raw=np.zeros((n + 1, d), np.float32))
                         for k, d in (("logscale", 3), ("rot", 4), ("opacity", 1), ("rgb", 3))}, None, 0.5)
     gs_h = np.concatenate([hs, [0.0]]).astype(np.float32)
