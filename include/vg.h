@@ -56,6 +56,10 @@ typedef enum {
 #define VG_TILE 16          /* tile side in pixels (the only supported value) */
 #define VG_MAX_VIEWS 64     /* views per launch */
 #define VG_MAX_CODEWORDS 256 /* 1-byte indices */
+#define VG_SORT_AUTO 0       /* vg_render_params.sort_mode: per-tile unless it overflowed on this ctx */
+#define VG_SORT_GLOBAL 1     /* radix sort of the visible slots by depth, then pairs stably by tile */
+#define VG_SORT_TILE 2       /* pairs by tile only; each tile's list sorted by depth in the forward */
+#define VG_TILE_SORT_CAP 1024 /* longest tile list the per-tile sort takes */
 
 /* Pinhole camera.  T_cw: row-major 3x4 world->camera transform [R | t];
  * camera x right, y down, z forward.  A point projects to
@@ -131,7 +135,17 @@ typedef struct {
  *   to hit_count[n] the number of (view, pixel) pairs where Gaussian n is
  *   blended and sets seen[n] = 1 where Gaussian n is visible (an unempty
  *   tile rect) in some view; nothing clears them, so a sliding window
- *   accumulates over its frames.  NULL = off. */
+ *   accumulates over its frames.  NULL = off.
+ * sort_mode: how the (tile, depth, index) order of the pairs is built; both
+ *   give the same order.  VG_SORT_GLOBAL: a stable radix sort of the visible
+ *   slots on their FP32 depth bits, pairs emitted in that order, then a
+ *   stable sort by tile.  VG_SORT_TILE: pairs emitted in slot order and
+ *   sorted by tile; the forward compositing kernel sorts each tile's list by
+ *   (depth bits, slot) in shared memory and writes it back for the backward.
+ *   A tile list longer than VG_TILE_SORT_CAP cannot be sorted so: the
+ *   forward's outputs are then invalid, the next vg_check returns
+ *   VG_ERR_CAPACITY, and the ctx uses VG_SORT_GLOBAL from then on under
+ *   VG_SORT_AUTO (the default). */
 typedef struct {
     int32_t tile;
     int32_t batch;
@@ -142,6 +156,7 @@ typedef struct {
     int32_t ppt_fwd, ppt_bwd;
     uint32_t* hit_count;
     uint32_t* seen;
+    int32_t sort_mode;
 } vg_render_params;
 
 /* Gradient outputs of vg_render_bwd (DEVICE pointers, caller-allocated; each

@@ -179,6 +179,7 @@ struct vg_ctx {
         scratch, state, pose_part, icp_part, loss_scratch, pair_off, blk_count, blk_base, vis, ssim_ws, grow_ws;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
+    bool tile_sort_failed = false;  // a tile list overflowed the per-tile sort: VG_SORT_AUTO sorts globally
     bool g2d_clean = false;
     Views views{};
     int64_t fwd_N = -1;
@@ -422,6 +423,13 @@ vg_status vg_check(vg_ctx* ctx, vg_stream stream) {
         VG_CUDA(cudaMemset(ctx->state.as<uint32_t>() + ST_ERR, 0, 4));
         if (s.flags & ERR_WAIT) return fail(VG_ERR_TIMEOUT, "a bounded device wait ran out");
         if (s.flags & ERR_TABLE) return fail(VG_ERR_CAPACITY, "anchor-growing hash table full");
+        if (s.flags & ERR_TILE_LIST) {
+            ctx->tile_sort_failed = true;
+            if (!(s.flags & ERR_OVERFLOW))
+                return fail(VG_ERR_CAPACITY, "a tile list longer than VG_TILE_SORT_CAP (" +
+                                                 std::to_string(VG_TILE_SORT_CAP) +
+                                                 "): this ctx sorts globally from the next forward under VG_SORT_AUTO");
+        }
         return fail(VG_ERR_CAPACITY, "pair buffer too small: " + std::to_string(s.pairs) + " pairs needed, capacity " +
                                          std::to_string(s.pair_capacity));
     }
@@ -559,6 +567,9 @@ static vg_status build_views(const vg_camera* cams, int32_t n_views, const vg_re
     cs->jacobian_clamp = p->jacobian_clamp;
     cs->hit_count = p->hit_count;
     cs->seen = p->seen;
+    cs->depth_hist = 1;
+    if (p->sort_mode < VG_SORT_AUTO || p->sort_mode > VG_SORT_TILE)
+        return fail(VG_ERR_INVALID_ARG, "sort_mode must be VG_SORT_AUTO, VG_SORT_GLOBAL or VG_SORT_TILE");
     cs->n_gauss = 0;  // set by the caller that knows the scene
     *pixels = pb;
     return VG_OK;
@@ -614,6 +625,9 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     uint32_t* state = ctx->state.as<uint32_t>();
     uint32_t* err = state + ST_ERR;
     unsigned long long* lb = ctx->lookback.as<unsigned long long>();
+    const bool tile_sort = params->sort_mode == VG_SORT_TILE ||
+                           (params->sort_mode == VG_SORT_AUTO && !ctx->tile_sort_failed);
+    cs.depth_hist = tile_sort ? 0 : 1;
     const bool prof_graph = capturing(st);
     const bool prof_on = ctx->prof.on;
     VG_STAGE(VG_STAGE_MEMSET, cudaMemsetAsync(scr, 0, (size_t)(SCR_WORDS + V.total_tiles) * 4, st));
@@ -621,15 +635,17 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
              launch_preprocess(sd, V, cs, ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
                                ctx->rect.as<uint2>(), ctx->ntiles.as<uint32_t>(), ctx->dkey[1].as<uint32_t>(), scr,
                                state, ctx->blk_count.as<uint32_t>(), st));
-    // depth order of the visible slots: order-preserving compaction, then a
-    // stable radix sort on the FP32 depth bits (ties keep Gaussian order)
+    // depth order of the visible slots: order-preserving compaction, then
+    // (global sort) a stable radix sort on the FP32 depth bits (ties keep
+    // Gaussian order); with the per-tile sort the compacted order stays and
+    // the forward compositing kernel orders each tile's list instead
     const int dgrid = sort_pass_grid((uint32_t)slots);
     VG_STAGE(VG_STAGE_DEPTH_SORT, ([&]() -> cudaError_t {
                  cudaError_t e = launch_compact(V, N, ctx->dkey[1].as<uint32_t>(), ctx->blk_count.as<uint32_t>(),
                                                 ctx->blk_base.as<uint32_t>(), ctx->dkey[0].as<uint32_t>(),
                                                 ctx->dval[0].as<uint32_t>(), ctx->vis.as<uint32_t>(), st);
                  if (e != cudaSuccess) return e;
-                 for (int p = 0; p < 4; ++p) {
+                 for (int p = 0; p < (tile_sort ? 0 : 4); ++p) {
                      const int i = p & 1, o = i ^ 1;
                      e = launch_sort_pass(ctx->dkey[i].as<uint32_t>(), ctx->dval[i].as<uint32_t>(),
                                           ctx->dkey[o].as<uint32_t>(), ctx->dval[o].as<uint32_t>(), scr + SCR_NVIS,
@@ -664,7 +680,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
                                            ctx->tile_order.as<uint32_t>(), st));
     VG_STAGE(VG_STAGE_BLEND_FWD,
              launch_blend_fwd(V, cs, params->ppt_fwd, ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
-                              ctx->pval[fin].as<uint32_t>(),
+                              ctx->pval[fin].as<uint32_t>(), tile_sort ? ctx->dkey[1].as<uint32_t>() : nullptr, err,
                               ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(), C, D, S,
                               ctx->Tfin.as<float>(), ctx->ncontrib.as<uint32_t>(),
                               (unsigned long long*)(state + ST_EVALS), (unsigned long long*)(state + ST_BLENDED),

@@ -89,18 +89,93 @@ __device__ __forceinline__ bool warp_hits(const float4 g, const float4 co, float
     return best >= co.w - (1e-3f + 1e-3f * fabsf(co.w));
 }
 
-template <int PPT, bool HITS>
+// (key, slot) pairs compared lexicographically: depth bits, then slot index
+__device__ __forceinline__ bool kv_less(uint32_t ka, uint32_t va, uint32_t kb, uint32_t vb) {
+    return ka < kb || (ka == kb && va < vb);
+}
+
+// ascending bitonic sort of one (key, value) pair per lane across the warp
+__device__ __forceinline__ void warp_sort32(uint32_t& k, uint32_t& s, int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+        const bool asc = (lane & size) == 0;
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const uint32_t ok = __shfl_xor_sync(0xffffffffu, k, stride);
+            const uint32_t os = __shfl_xor_sync(0xffffffffu, s, stride);
+            const bool lower = (lane & stride) == 0;
+            const bool other_less = kv_less(ok, os, k, s);
+            // in an ascending run the lower lane keeps the smaller pair
+            if ((lower == asc) ? other_less : !other_less) {
+                k = ok;
+                s = os;
+            }
+        }
+    }
+}
+
+// Sorts the tile's list pvals[rg.x, rg.y) by (depth key, slot) in place:
+// each warp sorts 32-entry chunks in registers, then every entry's final
+// position is its rank in its chunk plus, per other chunk, the number of
+// entries below it (a 5-step binary search; keys are unique).  The caller
+// guarantees n <= VG_TILE_SORT_CAP; s_kv holds VG_TILE_SORT_CAP pairs.
+template <int NT>
+__device__ __forceinline__ void tile_sort(uint32_t* __restrict__ pvals, uint2 rg, const uint32_t* __restrict__ dkey,
+                                          uint2* s_kv) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t n = rg.y - rg.x;
+    const int nch = (int)((n + 31) >> 5);
+    for (int c = warp; c < nch; c += NT / 32) {
+        const uint32_t e = (uint32_t)c * 32 + lane;
+        uint32_t k = 0xffffffffu, sl = 0xffffffffu;  // padding sorts last
+        if (e < n) {
+            sl = pvals[rg.x + e];
+            k = dkey[sl];
+        }
+        warp_sort32(k, sl, lane);
+        s_kv[e] = make_uint2(k, sl);
+    }
+    __syncthreads();
+    for (uint32_t e = threadIdx.x; e < n; e += NT) {
+        const uint2 me = s_kv[e];
+        const int c = (int)(e >> 5);
+        uint32_t pos = e & 31u;
+        for (int c2 = 0; c2 < nch; ++c2) {
+            if (c2 == c) continue;
+            const uint2* b = s_kv + c2 * 32;
+            if (kv_less(b[31].x, b[31].y, me.x, me.y)) {
+                pos += 32;
+                continue;
+            }
+            uint32_t lo = 0;  // entries of chunk c2 below me: the longest prefix with b[lo - 1] < me
+#pragma unroll
+            for (uint32_t step = 16; step > 0; step >>= 1) {
+                const uint2 x = b[lo + step - 1];
+                if (kv_less(x.x, x.y, me.x, me.y)) lo += step;
+            }
+            pos += lo;
+        }
+        pvals[rg.x + pos] = me.y;
+    }
+    __syncthreads();  // the sorted list (global) and the freed shared memory are ready for the block
+}
+
+template <int PPT, bool HITS, bool TSORT>
 __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
-    const uint32_t* __restrict__ pvals,
+    uint32_t* __restrict__ pvals, const uint32_t* __restrict__ dkey, uint32_t* __restrict__ err,
     const float4* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
     float* __restrict__ C, float* __restrict__ D, float* __restrict__ S, float* __restrict__ Tfin,
     uint32_t* __restrict__ ncontrib, unsigned long long* evals, unsigned long long* blended, int count_evals) {
     constexpr int NT = TILE_PIX / PPT;
-    __shared__ float4 s_xy[BLEND_BATCH];
-    __shared__ float4 s_co[BLEND_BATCH];
-    __shared__ float4 s_cd[BLEND_BATCH];
-    __shared__ uint32_t s_gid[BLEND_BATCH];  // Gaussian ids, for the optional hit counts
+    // staging of one batch of the tile's Gaussians; before that, the per-tile
+    // sort's buffer (VG_TILE_SORT_CAP x 8 bytes) in the same memory
+    __shared__ __align__(16) unsigned char s_raw[BLEND_BATCH * (3 * sizeof(float4) + sizeof(uint32_t))];
+    static_assert(sizeof(s_raw) >= VG_TILE_SORT_CAP * sizeof(uint2), "sort buffer");
+    float4* s_xy = reinterpret_cast<float4*>(s_raw);
+    float4* s_co = s_xy + BLEND_BATCH;
+    float4* s_cd = s_co + BLEND_BATCH;
+    uint32_t* s_gid = reinterpret_cast<uint32_t*>(s_cd + BLEND_BATCH);  // Gaussian ids, for the optional hit counts
 
     const int gt = (int)order[blockIdx.x];  // longest tile lists first
     const int v = view_of_tile(V, gt);
@@ -134,6 +209,12 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     }
     const int lane = threadIdx.x & 31;
     const uint2 rg = ranges[gt];
+    if (TSORT && rg.y - rg.x > 1) {
+        if (rg.y - rg.x <= (uint32_t)VG_TILE_SORT_CAP)
+            tile_sort<NT>(pvals, rg, dkey, reinterpret_cast<uint2*>(s_raw));
+        else if (threadIdx.x == 0)
+            atomicOr(err, ERR_TILE_LIST);  // composited unsorted; the outputs are flagged invalid
+    }
     for (uint32_t b = rg.x; b < rg.y; b += BLEND_BATCH) {
         int alldone = 1;
 #pragma unroll
@@ -409,25 +490,29 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
 }
 
 cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* order,
-                             const uint32_t* pvals,
+                             uint32_t* pvals, const uint32_t* dkey, uint32_t* err,
                              const float4* xy, const float4* conic_o, const float4* rgbd, float* C, float* D, float* S,
                              float* Tfin, uint32_t* ncontrib, unsigned long long* evals, unsigned long long* blended,
                              int count_evals, cudaStream_t st) {
     if (V.total_tiles <= 0) return cudaSuccess;
     count_launches(1);
+#define VG_FWD3(P, H, TS)                                                                                       \
+    blend_fwd_kernel<P, H, TS><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, order, pvals, dkey, err, xy, \
+                                                                       conic_o, rgbd, C, D, S, Tfin, ncontrib,  \
+                                                                       evals, blended, count_evals)
 #define VG_FWD(P)                                                                                               \
     do {                                                                                                        \
-        if (cs.hit_count)                                                                                       \
-            blend_fwd_kernel<P, true><<<V.total_tiles, TILE_PIX / P, 0, st>>>(                                  \
-                V, cs, ranges, order, pvals, xy, conic_o, rgbd, C, D, S, Tfin, ncontrib, evals, blended, count_evals); \
-        else                                                                                                    \
-            blend_fwd_kernel<P, false><<<V.total_tiles, TILE_PIX / P, 0, st>>>(                                 \
-                V, cs, ranges, order, pvals, xy, conic_o, rgbd, C, D, S, Tfin, ncontrib, evals, blended, count_evals); \
+        if (cs.hit_count) {                                                                                     \
+            if (dkey) VG_FWD3(P, true, true); else VG_FWD3(P, true, false);                                     \
+        } else {                                                                                                \
+            if (dkey) VG_FWD3(P, false, true); else VG_FWD3(P, false, false);                                   \
+        }                                                                                                       \
     } while (0)
     if (ppt == 4) VG_FWD(4);
     else if (ppt == 2) VG_FWD(2);
     else VG_FWD(1);
 #undef VG_FWD
+#undef VG_FWD3
     return cudaGetLastError();
 }
 

@@ -15,6 +15,7 @@ constexpr int TILE_PIX = TILE * TILE;
 constexpr uint32_t ERR_WAIT = 1u;      // a bounded spin ran out
 constexpr uint32_t ERR_OVERFLOW = 2u;  // pair buffer too small
 constexpr uint32_t ERR_TABLE = 4u;     // the anchor-growing hash table was full
+constexpr uint32_t ERR_TILE_LIST = 8u; // a tile list longer than the per-tile sort takes
 
 // a bounded spin gives up after this many polls (~1 s of L2 round trips)
 constexpr uint32_t SPIN_LIMIT = 1u << 21;
@@ -47,6 +48,7 @@ struct Consts {
     uint32_t* hit_count;  // [N] blended (view, pixel) pairs per Gaussian, added to; NULL = off
     uint32_t* seen;       // [N] set to 1 where a Gaussian is visible in some view; NULL = off
     int64_t n_gauss;      // N, for the two arrays above
+    int32_t depth_hist;   // the preprocess accumulates depth-key digit histograms (global depth sort)
 };
 
 // Scene arrays as the kernels see them (device pointers).

@@ -101,8 +101,9 @@ vg_status vg_mask_kernels_prune(float* m, float thr, const uint32_t* hits, const
                                 int64_t N, uint32_t* removed, uint32_t* n_removed, cudaStream_t st);
 
 // blend.cu
+// dkey non-NULL: sort each tile's list by (dkey[slot], slot) first (VG_SORT_TILE)
 cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* order,
-                             const uint32_t* pvals,
+                             uint32_t* pvals, const uint32_t* dkey, uint32_t* err,
                              const float4* xy, const float4* conic_o, const float4* rgbd, float* C, float* D,
                              float* S, float* Tfin, uint32_t* ncontrib, unsigned long long* evals,
                              unsigned long long* blended, int count_evals, cudaStream_t st);

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev S, const __gri
         // depth-key digit histograms of the visible slots; most lanes share
         // the high digits
         const uint32_t vis_mask = __ballot_sync(0xffffffffu, live && key != 0xffffffffu);
-        if (live && key != 0xffffffffu) {
+        if (cs.depth_hist && live && key != 0xffffffffu) {
 #pragma unroll
             for (int pass = 0; pass < 4; ++pass) {
                 const uint32_t b = (key >> (8 * pass)) & 255u;

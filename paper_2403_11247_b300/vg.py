@@ -22,6 +22,8 @@ VG_OK, VG_ERR_INVALID_ARG, VG_ERR_OOM, VG_ERR_CUDA, VG_ERR_CAPACITY, VG_ERR_TIME
 STATUS_NAMES = ["VG_OK", "VG_ERR_INVALID_ARG", "VG_ERR_OOM", "VG_ERR_CUDA", "VG_ERR_CAPACITY", "VG_ERR_TIMEOUT",
                 "VG_ERR_UNIMPLEMENTED"]
 VG_SCENE_COPY, VG_SCENE_BORROW = 0, 1
+VG_SORT_AUTO, VG_SORT_GLOBAL, VG_SORT_TILE = 0, 1, 2
+VG_TILE_SORT_CAP = 1024
 VG_MAX_VIEWS = 64
 GROUPS = ("logscale", "rot", "opacity", "rgb")
 GDIM = {"logscale": 3, "rot": 4, "opacity": 1, "rgb": 3}
@@ -55,7 +57,8 @@ class vg_render_params(C.Structure):
                 ("alpha_max", C.c_float), ("alpha_min", C.c_float), ("t_min", C.c_float), ("dilation", C.c_float),
                 ("sigma_cull", C.c_float), ("clamp_factor", C.c_float),
                 ("jacobian_clamp", C.c_int32), ("count_evals", C.c_int32), ("pose_dev", C.c_void_p),
-                ("ppt_fwd", C.c_int32), ("ppt_bwd", C.c_int32), ("hit_count", C.c_void_p), ("seen", C.c_void_p)]
+                ("ppt_fwd", C.c_int32), ("ppt_bwd", C.c_int32), ("hit_count", C.c_void_p), ("seen", C.c_void_p),
+                ("sort_mode", C.c_int32)]
 
 
 class vg_scene_grads(C.Structure):

@@ -62,8 +62,8 @@ def test_rvq_decode_matches_oracle(cuda, L, K, d, n):
 # binning: bit-exact against the oracle's FP32 decisions
 # ---------------------------------------------------------------------------
 
-def check_binning(scene, cams):
-    sh, ctx, params, *_ = gpu_forward(scene, cams)
+def check_binning(scene, cams, **pkw):
+    sh, ctx, params, *_ = gpu_forward(scene, cams, **pkw)
     o = O.Oracle(scene, cams)
     proj, b32, border = o.projection()
     slots = o.n_slots
@@ -110,15 +110,64 @@ def check_binning(scene, cams):
     return P, n_border, int(bl.sum())
 
 
-def test_binning_bit_exact_tiny(cuda):
-    P, nb, nbl = check_binning(synth.tiny_scene(), [synth.tiny_camera()])
+SORTS = [V.VG_SORT_GLOBAL, V.VG_SORT_TILE]
+
+
+@pytest.mark.parametrize("sort_mode", SORTS)
+def test_binning_bit_exact_tiny(cuda, sort_mode):
+    """12 tiles with lists of ~800 entries: the per-tile sort's longest
+    merges."""
+    P, nb, nbl = check_binning(synth.tiny_scene(), [synth.tiny_camera()], sort_mode=sort_mode)
     assert P > 1000
 
 
-def test_binning_bit_exact_room_two_views_mixed_sizes(cuda):
+@pytest.mark.parametrize("sort_mode", SORTS)
+def test_binning_bit_exact_room_two_views_mixed_sizes(cuda, sort_mode):
     sc = small_room()
-    P, nb, nbl = check_binning(sc, [small_room_cam(320, 180, 160.0), small_room_cam(200, 136, 100.0, seed=3)])
+    P, nb, nbl = check_binning(sc, [small_room_cam(320, 180, 160.0), small_room_cam(200, 136, 100.0, seed=3)],
+                               sort_mode=sort_mode)
     assert P > 5000
+
+
+def test_sort_modes_give_identical_lists_images_and_gradients(cuda):
+    torch = cuda
+    sc = small_room(4000)
+    cams = [small_room_cam(320, 180, 160.0), small_room_cam(200, 136, 100.0, seed=3)]
+    sh = V.vg_scene_upload(sc)
+    out = {}
+    for mode in SORTS:
+        ctx = V.vg_ctx_create(0)
+        params = V.default_params(sort_mode=mode)
+        C_, D, S = V.render_with_retry(sh, cams, params, ctx)
+        P = V.vg_ctx_stats(ctx)["pairs"]
+        lists = V.vg_ctx_buffer(ctx, "pair_vals", P).copy()
+        dC, dD, dS = synth.upstream_grads(5, S.numel())
+        g = V.vg_render_bwd(sh, cams, params, ctx, t(dC, torch), t(dD, torch), t(dS, torch))
+        torch.cuda.synchronize()
+        out[mode] = (C_.cpu().numpy(), D.cpu().numpy(), S.cpu().numpy(), lists, to_np_grads(g))
+    a, b = out[V.VG_SORT_GLOBAL], out[V.VG_SORT_TILE]
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+    for name in a[4]:    # float atomics: summation order differs, the terms do not
+        grad_tolerance_check(b[4][name], a[4][name], "sort modes:" + name, rtol=1e-4, atol_frac=1e-5)
+
+
+def test_tile_list_over_the_per_tile_cap_is_flagged_and_auto_falls_back(cuda):
+    sc, cams = synth.tiny_scene(n=4000), [synth.tiny_camera()]
+    sh = V.vg_scene_upload(sc)
+    ref_ctx = V.vg_ctx_create(0)
+    ref = V.render_with_retry(sh, cams, V.default_params(sort_mode=V.VG_SORT_GLOBAL), ref_ctx)
+    ranges = V.vg_ctx_buffer(ref_ctx, "ranges", 12)
+    assert (ranges[:, 1] - ranges[:, 0]).max() > V.VG_TILE_SORT_CAP
+    ctx = V.vg_ctx_create(0)
+    V.vg_ctx_reserve(ctx, V.vg_ctx_stats(ref_ctx)["pairs"] + 1024)
+    V.vg_render_fwd(sh, cams, V.default_params(sort_mode=V.VG_SORT_TILE), ctx)
+    assert V.vg_check(ctx) == V.VG_ERR_CAPACITY
+    assert V.vg_check(ctx) == V.VG_OK   # the flag was cleared
+    out = V.vg_render_fwd(sh, cams, V.default_params(), ctx)   # auto: global from now on
+    assert V.vg_check(ctx) == V.VG_OK
+    for x, y in zip(out, ref):
+        assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
 
 
 # ---------------------------------------------------------------------------
