@@ -200,7 +200,7 @@ class Server:
         pix = sum(r.cam.width * r.cam.height for r in batch)
         return pix * (BYTES_PER_PIXEL + PAIRS_PER_PIXEL * BYTES_PER_PAIR) + n * len(batch) * BYTES_PER_SLOT
 
-    def _launch(self, lane: _Lane, batch: List[Request]):
+    def _launch(self, lane: _Lane, batch: List[Request], retry: bool = False):
         sh = self.scenes[batch[0].scene]
         cams = [r.cam for r in batch]
         f32 = dict(dtype=torch.float32, device=self.device)
@@ -242,18 +242,21 @@ class Server:
         lane.event, lane.batch, lane.host = ev, batch, host
         lane.bytes = self.estimate(batch)
         self.in_flight += lane.bytes
-        self.launches += 1
+        if not retry:      # a redone launch is counted in retries only
+            self.launches += 1
 
     def _finish(self, lane: _Lane, t0: float, keep_results: bool) -> List[Request]:
         st = V.vg_check(lane.ctx, lane.stream)
         batch = lane.batch
         self.in_flight -= lane.bytes
         if st == V.VG_ERR_CAPACITY:
-            # the pair buffer overflowed: grow it and redo this launch
+            # the pair buffer (or a tile list, for the per-tile sort) overflowed:
+            # grow the buffer and redo this launch (the ctx sorts globally from
+            # now on if a tile list was too long)
             need = V.vg_ctx_stats(lane.ctx, lane.stream)["pairs"]
             V.vg_ctx_reserve(lane.ctx, int(need * 1.5) + 4096)
             self.retries += 1
-            self._launch(lane, batch)
+            self._launch(lane, batch, retry=True)
             return []
         if st != V.VG_OK:
             raise V.VgError(st, "serve", V.lib().vg_last_error().decode(errors="replace"))
