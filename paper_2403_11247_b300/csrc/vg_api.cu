@@ -655,16 +655,25 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
                  }
                  return cudaSuccess;
              })());
-    // pairs in depth order, then stable by tile
+    // pairs in depth order, then stable by tile (global sort); or in slot
+    // order, then grouped by tile without order (per-tile sort)
     const int tp = tile_passes_for(V.total_tiles);
     const uint32_t cap = (uint32_t)ctx->pair_cap;
     VG_STAGE(VG_STAGE_DUPLICATE,
              launch_duplicate(ctx->dval[0].as<uint32_t>(), ctx->pair_off.as<uint32_t>(), ctx->ntiles.as<uint32_t>(),
                               ctx->rect.as<uint2>(), N, V, ctx->pkey[0].as<uint32_t>(), ctx->pval[0].as<uint32_t>(), cap,
-                              scr, tp, lb, state, 4u, err, slots, st));
+                              scr, tile_sort ? 0 : tp, lb, state, 4u, err, slots, st));
     const int tgrid = sort_pass_grid(cap);
+    if (tile_sort) {
+        VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr + SCR_TILE_COUNTS, V.total_tiles, ctx->ranges.as<uint2>(),
+                                               ctx->tile_order.as<uint32_t>(), st));
+        VG_STAGE(VG_STAGE_TILE_SORT,
+                 launch_tile_scatter(ctx->pkey[0].as<uint32_t>(), ctx->pval[0].as<uint32_t>(), scr + SCR_PAIRS, cap,
+                                     ctx->ranges.as<uint2>(), scr + SCR_TILE_COUNTS, ctx->pkey[1].as<uint32_t>(),
+                                     ctx->pval[1].as<uint32_t>(), st));
+    }
     VG_STAGE(VG_STAGE_TILE_SORT, ([&]() -> cudaError_t {
-                 for (int p = 0; p < tp; ++p) {
+                 for (int p = 0; p < (tile_sort ? 0 : tp); ++p) {
                      const int i = p & 1, o = i ^ 1;
                      cudaError_t e = launch_sort_pass(
                          ctx->pkey[i].as<uint32_t>(), ctx->pval[i].as<uint32_t>(), ctx->pkey[o].as<uint32_t>(),
@@ -674,10 +683,11 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
                  }
                  return cudaSuccess;
              })());
-    const int fin = tp & 1;
+    const int fin = tile_sort ? 1 : (tp & 1);
     ctx->final_pair = fin;
-    VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr + SCR_TILE_COUNTS, V.total_tiles, ctx->ranges.as<uint2>(),
-                                           ctx->tile_order.as<uint32_t>(), st));
+    if (!tile_sort)
+        VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr + SCR_TILE_COUNTS, V.total_tiles, ctx->ranges.as<uint2>(),
+                                               ctx->tile_order.as<uint32_t>(), st));
     VG_STAGE(VG_STAGE_BLEND_FWD,
              launch_blend_fwd(V, cs, params->ppt_fwd, ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
                               ctx->pval[fin].as<uint32_t>(), tile_sort ? ctx->dkey[1].as<uint32_t>() : nullptr, err,

@@ -74,6 +74,11 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, co
 // per-tile [start, end) from the per-tile pair counts (one-block scan)
 cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, uint32_t* order, cudaStream_t st);
 cudaError_t launch_epoch_bump(uint32_t* state, uint32_t by, cudaStream_t st);
+// group the pairs by tile (unordered within a tile) into the ranges; counts
+// (the per-tile pair counts the ranges came from) end at zero
+cudaError_t launch_tile_scatter(const uint32_t* keys_in, const uint32_t* vals_in, const uint32_t* n_dev, uint32_t cap,
+                                const uint2* ranges, uint32_t* counts, uint32_t* keys_out, uint32_t* vals_out,
+                                cudaStream_t st);
 
 // ssim.cu: workspace ws holds 8 * 3 * n_views * W * H + 1 floats
 vg_status launch_ssim(int n_views, int W, int H, const float* C, const float* Ct, float weight, float* dC, float* loss,

@@ -439,6 +439,52 @@ cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* range
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// grouping by tile without order (per-tile sort): pair e goes to a free
+// position of its tile's range, claimed by counting the tile's pair count
+// down (one atomic per run of equal tiles in a warp); the forward compositing
+// kernel then orders each tile's list, so the claim order does not matter
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) tile_scatter_kernel(const uint32_t* __restrict__ keys_in,
+                                                           const uint32_t* __restrict__ vals_in,
+                                                           const uint32_t* __restrict__ n_dev, uint32_t cap,
+                                                           const uint2* __restrict__ ranges, uint32_t* counts,
+                                                           uint32_t* __restrict__ keys_out,
+                                                           uint32_t* __restrict__ vals_out) {
+    const uint32_t P = min(*n_dev, cap);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < P; e += gridDim.x * blockDim.x) {
+        const uint32_t key = keys_in[e];
+        const uint32_t peers = __match_any_sync(__activemask(), key);
+        const int leader = __ffs(peers) - 1;
+        const uint32_t n = (uint32_t)__popc(peers);
+        uint32_t top = 0;
+        if ((int)(threadIdx.x & 31) == leader) top = atomicSub(counts + key, n);
+        top = __shfl_sync(peers, top, leader);
+        const uint32_t pos = ranges[key].x + top - n + (uint32_t)__popc(peers & lanemask_lt());
+        keys_out[pos] = key;
+        vals_out[pos] = vals_in[e];
+    }
+}
+
+cudaError_t launch_tile_scatter(const uint32_t* keys_in, const uint32_t* vals_in, const uint32_t* n_dev, uint32_t cap,
+                                const uint2* ranges, uint32_t* counts, uint32_t* keys_out, uint32_t* vals_out,
+                                cudaStream_t st) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 148;
+    }
+    int64_t grid = ceil_div((int64_t)cap, 256);
+    if (grid > (int64_t)sms * 8) grid = (int64_t)sms * 8;
+    if (grid < 1) grid = 1;
+    count_launches(1);
+    tile_scatter_kernel<<<(unsigned)grid, 256, 0, st>>>(keys_in, vals_in, n_dev, cap, ranges, counts, keys_out,
+                                                       vals_out);
+    return cudaGetLastError();
+}
+
 __global__ void epoch_bump_kernel(uint32_t* state, uint32_t by) { state[ST_EPOCH] += by; }
 
 cudaError_t launch_epoch_bump(uint32_t* state, uint32_t by, cudaStream_t st) {
