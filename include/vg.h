@@ -402,7 +402,8 @@ vg_status vg_icp_associate(const vg_scene* scene, const vg_camera* cams, int32_t
  * C1 = 0.01^2, C2 = 0.03^2;  L = 1 - mean SSIM(C, Ct) over the n_views x 3
  * planes of width x height ([view][3][H][W], device).  Writes weight * L to
  * loss[0] and ADDS weight * dL/dC to dC (e.g. after vg_loss_l1 wrote it);
- * either may be NULL.  Workspace: 8 floats per colour value in the ctx. */
+ * either may be NULL.  One kernel per 32x32 tile of a colour plane; the
+ * ctx holds only the SSIM sum. */
 vg_status vg_ssim_loss(vg_ctx* ctx, int32_t n_views, int32_t width, int32_t height, const float* C, const float* Ct,
                        float weight, float* dC, float* loss, vg_stream stream);
 

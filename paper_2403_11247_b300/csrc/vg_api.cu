@@ -841,9 +841,9 @@ vg_status vg_ssim_loss(vg_ctx* ctx, int32_t n_views, int32_t width, int32_t heig
                        float weight, float* dC, float* loss, vg_stream stream) {
     if (!ctx || !C || !Ct || n_views < 1 || width < 1 || height < 1)
         return fail(VG_ERR_INVALID_ARG, "vg_ssim_loss: null argument or empty size");
-    const int64_t total = (int64_t)3 * n_views * width * height;
+    if (n_views > 21845) return fail(VG_ERR_INVALID_ARG, "vg_ssim_loss: more than 21845 views");
     cudaStream_t st = (cudaStream_t)stream;
-    VG_TRY(ctx->ssim_ws.ensure((size_t)(8 * total + 1) * 4, st, "ssim workspace"));
+    VG_TRY(ctx->ssim_ws.ensure(16, st, "ssim sum"));
     return launch_ssim(n_views, width, height, C, Ct, weight, dC, loss, ctx->ssim_ws.as<float>(), st);
 }
 
