@@ -433,118 +433,9 @@ __global__ void __launch_bounds__(1024) ranges_kernel(const uint32_t* __restrict
     for (int i = threadIdx.x; i < n; i += blockDim.x) order[atomicAdd(&s_bin[order_bucket(cnt[i], cmax)], 1u)] = (uint32_t)i;
 }
 
-// the same for up to 1024 x RANGE_ITEMS tiles with every count loaded once,
-// RANGE_ITEMS consecutive tiles per thread (16-byte loads), so that the scan
-// costs one memory round trip instead of one per 1024 tiles
-constexpr int RANGE_ITEMS = 16;
-
-__global__ void __launch_bounds__(1024) ranges_blocked_kernel(const uint32_t* __restrict__ cnt, int n,
-                                                              uint2* __restrict__ ranges, uint32_t* __restrict__ order) {
-    __shared__ uint32_t s_w[32];
-    __shared__ uint32_t s_max;
-    __shared__ uint32_t s_bin[ORDER_BUCKETS];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i0 = threadIdx.x * RANGE_ITEMS;
-    uint32_t x[RANGE_ITEMS];
-    if (i0 + RANGE_ITEMS <= n) {
-#pragma unroll
-        for (int q = 0; q < RANGE_ITEMS / 4; ++q) {
-            const uint4 u = reinterpret_cast<const uint4*>(cnt + i0)[q];
-            x[4 * q] = u.x;
-            x[4 * q + 1] = u.y;
-            x[4 * q + 2] = u.z;
-            x[4 * q + 3] = u.w;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < RANGE_ITEMS; ++k) x[k] = i0 + k < n ? cnt[i0 + k] : 0u;
-    }
-    if (threadIdx.x == 0) s_max = 0;
-    for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) s_bin[i] = 0;
-    uint32_t tot = 0, mymax = 0;
-#pragma unroll
-    for (int k = 0; k < RANGE_ITEMS; ++k) {
-        tot += x[k];
-        mymax = max(mymax, x[k]);
-    }
-    uint32_t inc = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
-    if (lane == 31) s_w[warp] = inc;
-    __syncthreads();
-    if (lane == 0) atomicMax(&s_max, mymax);
-    if (warp == 0) {
-        uint32_t t = s_w[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        s_w[lane] = t;
-    }
-    __syncthreads();
-    uint32_t run = (warp ? s_w[warp - 1] : 0u) + inc - tot;
-#pragma unroll
-    for (int k = 0; k < RANGE_ITEMS; ++k) {
-        if (i0 + k < n) ranges[i0 + k] = make_uint2(run, run + x[k]);
-        run += x[k];
-    }
-    if (!order) return;
-    const uint32_t cmax = s_max;
-    // bucket counts; lanes of a warp with the same bucket add once (tiles of
-    // similar length share buckets, so plain shared atomics would serialise)
-#pragma unroll
-    for (int k = 0; k < RANGE_ITEMS; ++k) {
-        const int b = i0 + k < n ? order_bucket(x[k], cmax) : -1;
-        const uint32_t peers = __match_any_sync(0xffffffffu, b);
-        if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_bin[b], (uint32_t)__popc(peers));
-    }
-    __syncthreads();
-    if (warp == 0) {  // exclusive scan of the bucket sizes, 8 buckets per lane
-        uint32_t v[ORDER_BUCKETS / 32], t = 0;
-#pragma unroll
-        for (int k = 0; k < ORDER_BUCKETS / 32; ++k) {
-            v[k] = s_bin[lane * (ORDER_BUCKETS / 32) + k];
-            t += v[k];
-        }
-        uint32_t c = t;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, c, o);
-            if (lane >= o) c += y;
-        }
-        uint32_t r = c - t;
-#pragma unroll
-        for (int k = 0; k < ORDER_BUCKETS / 32; ++k) {
-            s_bin[lane * (ORDER_BUCKETS / 32) + k] = r;
-            r += v[k];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < RANGE_ITEMS; ++k) {
-        const int b = i0 + k < n ? order_bucket(x[k], cmax) : -1;
-        const uint32_t peers = __match_any_sync(0xffffffffu, b);
-        const int leader = __ffs(peers) - 1;
-        uint32_t base = 0;
-        if (b >= 0 && lane == leader) base = atomicAdd(&s_bin[b], (uint32_t)__popc(peers));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (b >= 0) order[base + (uint32_t)__popc(peers & lanemask_lt())] = (uint32_t)(i0 + k);
-    }
-}
-
 cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, uint32_t* order, cudaStream_t st) {
     count_launches(1);
-    // the blocked form needs 16-byte aligned counts
-    if (n_tiles <= 1024 * RANGE_ITEMS && (reinterpret_cast<uintptr_t>(tile_counts) & 15u) == 0)
-        ranges_blocked_kernel<<<1, 1024, 0, st>>>(tile_counts, n_tiles, ranges, order);
-    else
-        ranges_kernel<<<1, 1024, 0, st>>>(tile_counts, n_tiles, ranges, order);
+    ranges_kernel<<<1, 1024, 0, st>>>(tile_counts, n_tiles, ranges, order);
     return cudaGetLastError();
 }
 
