@@ -10,7 +10,9 @@
 // tile plus a 5-pixel halo; SSIM there and the three coefficient maps of its
 // gradient (d/dmu_x, d/dsigma_x^2, d/dsigma_xy, pre-combined; zero outside the
 // image, the adjoint of the zero padding); the same two passes over the
-// coefficient maps give dL/dx = G*A + 2 x (G*B) + y (G*Cc) on the tile.  The
+// coefficient maps give dL/dx = G*A + 2 x (G*B) + y (G*Cc) on the tile.  Each
+// thread of a pass slides along a strip of outputs with the inputs in
+// registers (one shared-memory load per input, not per tap).  The
 // halo is recomputed by neighbouring tiles instead of going through memory:
 // C and C_target are read (from L2 for the halo) and dC read-modify-written,
 // 16 bytes per colour value.
@@ -25,6 +27,7 @@ constexpr int SSIM_T = 32;                  // output tile side
 constexpr int SSIM_S = SSIM_T + 2 * SSIM_R;  // statistics region side (42)
 constexpr int SSIM_I = SSIM_T + 4 * SSIM_R;  // input region side (52)
 constexpr int SSIM_SMEM_FLOATS = 2 * SSIM_I * SSIM_I + 5 * SSIM_I * SSIM_S + 3 * SSIM_S * SSIM_S;
+static_assert(SSIM_S % 7 == 0 && SSIM_T % 8 == 0 && SSIM_T % 4 == 0, "strip lengths of the filter passes");
 
 struct SsimWin {
     float w[2 * SSIM_R + 1];
@@ -55,54 +58,81 @@ __global__ void __launch_bounds__(256) ssim_tile_kernel(int W, int H, const floa
         sy[i] = in ? yp[(int64_t)gy * W + gx] : 0.f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < SSIM_I * SSIM_S; i += blockDim.x) {
-        const int r = i / SSIM_S, c = i - r * SSIM_S;
-        float a[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    // horizontal pass of x, y, x^2, y^2, xy: a thread slides along 7 outputs
+    // of one row, every input loaded once from shared memory
+    for (int it = threadIdx.x; it < SSIM_I * (SSIM_S / 7); it += blockDim.x) {
+        const int r = it / (SSIM_S / 7), c0 = (it - r * (SSIM_S / 7)) * 7;
+        float a[7][5];
 #pragma unroll
-        for (int k = 0; k <= 2 * SSIM_R; ++k) {
-            const float wk = win.w[k];
-            const float u = sx[r * SSIM_I + c + k], v = sy[r * SSIM_I + c + k];
-            a[0] += wk * u;
-            a[1] += wk * v;
-            a[2] += wk * (u * u);
-            a[3] += wk * (v * v);
-            a[4] += wk * (u * v);
+        for (int j = 0; j < 7; ++j)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) a[j][q] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 7 + 2 * SSIM_R; ++i) {
+            const float u = sx[r * SSIM_I + c0 + i], v = sy[r * SSIM_I + c0 + i];
+            const float f[5] = {u, v, u * u, v * v, u * v};
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
+                const int k = i - j;
+                if (k < 0 || k > 2 * SSIM_R) continue;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) a[j][q] += win.w[k] * f[q];
+            }
         }
 #pragma unroll
-        for (int q = 0; q < 5; ++q) hs[q * SSIM_I * SSIM_S + i] = a[q];
+        for (int j = 0; j < 7; ++j)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) hs[q * SSIM_I * SSIM_S + r * SSIM_S + c0 + j] = a[j][q];
     }
     __syncthreads();
+    // vertical pass, SSIM and the coefficient maps: a thread slides down 7
+    // outputs of one column
     float local = 0.f;
-    for (int i = threadIdx.x; i < SSIM_S * SSIM_S; i += blockDim.x) {
-        const int r = i / SSIM_S, c = i - r * SSIM_S;
-        const int gy = oy - SSIM_R + r, gx = ox - SSIM_R + c;
-        float A = 0.f, B = 0.f, Cc = 0.f;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int it = threadIdx.x; it < SSIM_S * (SSIM_S / 7); it += blockDim.x) {
+        const int c = it % SSIM_S, r0 = (it / SSIM_S) * 7;
+        float m[7][5];
 #pragma unroll
-            for (int k = 0; k <= 2 * SSIM_R; ++k) {
-                const float wk = win.w[k];
+        for (int j = 0; j < 7; ++j)
 #pragma unroll
-                for (int q = 0; q < 5; ++q) m[q] += wk * hs[q * SSIM_I * SSIM_S + (r + k) * SSIM_S + c];
+            for (int q = 0; q < 5; ++q) m[j][q] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 7 + 2 * SSIM_R; ++i) {
+            float h[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) h[q] = hs[q * SSIM_I * SSIM_S + (r0 + i) * SSIM_S + c];
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
+                const int k = i - j;
+                if (k < 0 || k > 2 * SSIM_R) continue;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) m[j][q] += win.w[k] * h[q];
             }
-            const float mx = m[0], my = m[1];
-            const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
-            const float a1 = 2.f * mx * my + C1, a2 = 2.f * sxy + C2;
-            const float b1 = mx * mx + my * my + C1, b2 = sxx + syy + C2;
-            const float inv_b = 1.f / (b1 * b2);
-            const float S = a1 * a2 * inv_b;
-            // each pixel's SSIM counts once: in the tile that owns it
-            if (r >= SSIM_R && r < SSIM_R + SSIM_T && c >= SSIM_R && c < SSIM_R + SSIM_T) local += S;
-            const float dmx = 2.f * my * a2 * inv_b - 2.f * mx * S / b1;
-            const float dsxx = -S / b2;
-            const float dsxy = 2.f * a1 * inv_b;
-            A = -(dmx - 2.f * mx * dsxx - my * dsxy) * inv_m;
-            B = -dsxx * inv_m;
-            Cc = -dsxy * inv_m;
         }
-        coef[i] = A;
-        coef[SSIM_S * SSIM_S + i] = B;
-        coef[2 * SSIM_S * SSIM_S + i] = Cc;
+        const int gx = ox - SSIM_R + c;
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            const int r = r0 + j, gy = oy - SSIM_R + r;
+            float A = 0.f, B = 0.f, Cc = 0.f;
+            if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                const float mx = m[j][0], my = m[j][1];
+                const float sxx = m[j][2] - mx * mx, syy = m[j][3] - my * my, sxy = m[j][4] - mx * my;
+                const float a1 = 2.f * mx * my + C1, a2 = 2.f * sxy + C2;
+                const float b1 = mx * mx + my * my + C1, b2 = sxx + syy + C2;
+                const float inv_b = 1.f / (b1 * b2);
+                const float S = a1 * a2 * inv_b;
+                // each pixel's SSIM counts once: in the tile that owns it
+                if (r >= SSIM_R && r < SSIM_R + SSIM_T && c >= SSIM_R && c < SSIM_R + SSIM_T) local += S;
+                const float dmx = 2.f * my * a2 * inv_b - 2.f * mx * S / b1;
+                const float dsxx = -S / b2;
+                const float dsxy = 2.f * a1 * inv_b;
+                A = -(dmx - 2.f * mx * dsxx - my * dsxy) * inv_m;
+                B = -dsxx * inv_m;
+                Cc = -dsxy * inv_m;
+            }
+            coef[r * SSIM_S + c] = A;
+            coef[SSIM_S * SSIM_S + r * SSIM_S + c] = B;
+            coef[2 * SSIM_S * SSIM_S + r * SSIM_S + c] = Cc;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
@@ -114,33 +144,63 @@ __global__ void __launch_bounds__(256) ssim_tile_kernel(int W, int H, const floa
         atomicAdd(ssim_sum, t);
     }
     if (!dx) return;
-    for (int i = threadIdx.x; i < SSIM_S * SSIM_T; i += blockDim.x) {
-        const int r = i / SSIM_T, c = i - r * SSIM_T;
-        float a[3] = {0.f, 0.f, 0.f};
+    // horizontal pass of the coefficient maps: 8 outputs of one row per thread
+    for (int it = threadIdx.x; it < SSIM_S * (SSIM_T / 8); it += blockDim.x) {
+        const int r = it % SSIM_S, c0 = (it / SSIM_S) * 8;
+        float a[8][3];
 #pragma unroll
-        for (int k = 0; k <= 2 * SSIM_R; ++k) {
-            const float wk = win.w[k];
+        for (int j = 0; j < 8; ++j)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) a[q] += wk * coef[q * SSIM_S * SSIM_S + r * SSIM_S + c + k];
+            for (int q = 0; q < 3; ++q) a[j][q] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8 + 2 * SSIM_R; ++i) {
+            float f[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) f[q] = coef[q * SSIM_S * SSIM_S + r * SSIM_S + c0 + i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = i - j;
+                if (k < 0 || k > 2 * SSIM_R) continue;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) a[j][q] += win.w[k] * f[q];
+            }
         }
 #pragma unroll
-        for (int q = 0; q < 3; ++q) hc[q * SSIM_S * SSIM_T + i] = a[q];
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) hc[q * SSIM_S * SSIM_T + r * SSIM_T + c0 + j] = a[j][q];
     }
     __syncthreads();
+    // vertical pass and the gradient: 4 outputs of one column per thread
     float* dp = dx + blockIdx.z * HW;
-    for (int i = threadIdx.x; i < SSIM_T * SSIM_T; i += blockDim.x) {
-        const int r = i / SSIM_T, c = i - r * SSIM_T;
-        const int gy = oy + r, gx = ox + c;
-        if (gy >= H || gx >= W) continue;
-        float g[3] = {0.f, 0.f, 0.f};
+    for (int it = threadIdx.x; it < SSIM_T * (SSIM_T / 4); it += blockDim.x) {
+        const int c = it % SSIM_T, r0 = (it / SSIM_T) * 4;
+        float g[4][3];
 #pragma unroll
-        for (int k = 0; k <= 2 * SSIM_R; ++k) {
-            const float wk = win.w[k];
+        for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) g[q] += wk * hc[q * SSIM_S * SSIM_T + (r + k) * SSIM_T + c];
+            for (int q = 0; q < 3; ++q) g[j][q] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4 + 2 * SSIM_R; ++i) {
+            float f[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) f[q] = hc[q * SSIM_S * SSIM_T + (r0 + i) * SSIM_T + c];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int k = i - j;
+                if (k < 0 || k > 2 * SSIM_R) continue;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) g[j][q] += win.w[k] * f[q];
+            }
         }
-        const int j = (r + 2 * SSIM_R) * SSIM_I + c + 2 * SSIM_R;
-        dp[(int64_t)gy * W + gx] += weight * (g[0] + 2.f * sx[j] * g[1] + sy[j] * g[2]);
+        const int gx = ox + c;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = r0 + j, gy = oy + r;
+            if (gy >= H || gx >= W) continue;
+            const int jj = (r + 2 * SSIM_R) * SSIM_I + c + 2 * SSIM_R;
+            dp[(int64_t)gy * W + gx] += weight * (g[j][0] + 2.f * sx[jj] * g[j][1] + sy[jj] * g[j][2]);
+        }
     }
 }
 
