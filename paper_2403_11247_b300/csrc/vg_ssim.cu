@@ -26,7 +26,10 @@ constexpr int SSIM_R = 5;                   // window radius (11 taps)
 constexpr int SSIM_T = 32;                  // output tile side
 constexpr int SSIM_S = SSIM_T + 2 * SSIM_R;  // statistics region side (42)
 constexpr int SSIM_I = SSIM_T + 4 * SSIM_R;  // input region side (52)
-constexpr int SSIM_SMEM_FLOATS = 2 * SSIM_I * SSIM_I + 5 * SSIM_I * SSIM_S + 3 * SSIM_S * SSIM_S;
+// the coefficient maps reuse the inputs' memory, their horizontal pass the
+// statistics': 65 KB, three blocks per SM
+constexpr int SSIM_SMEM_FLOATS = 2 * SSIM_I * SSIM_I + 5 * SSIM_I * SSIM_S;
+static_assert(3 * SSIM_S * SSIM_S <= 2 * SSIM_I * SSIM_I && 3 * SSIM_S * SSIM_T <= 5 * SSIM_I * SSIM_S, "aliasing");
 static_assert(SSIM_S % 7 == 0 && SSIM_T % 8 == 0 && SSIM_T % 4 == 0, "strip lengths of the filter passes");
 
 struct SsimWin {
@@ -41,7 +44,7 @@ __global__ void __launch_bounds__(256) ssim_tile_kernel(int W, int H, const floa
     float* sx = sm;                              // [52][52] inputs, zero outside the image
     float* sy = sx + SSIM_I * SSIM_I;
     float* hs = sy + SSIM_I * SSIM_I;            // [5][52][42] horizontal statistics
-    float* coef = hs + 5 * SSIM_I * SSIM_S;      // [3][42][42] coefficient maps
+    float* coef = sm;                            // [3][42][42] coefficient maps (reuses sx, sy)
     float* hc = hs;                              // [3][42][32] their horizontal pass (reuses hs)
     __shared__ float s_tmp[8];
     const int ox = blockIdx.x * SSIM_T, oy = blockIdx.y * SSIM_T;
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(256) ssim_tile_kernel(int W, int H, const floa
     }
     __syncthreads();
     // vertical pass, SSIM and the coefficient maps: a thread slides down 7
-    // outputs of one column
+    // outputs of one column (the inputs' memory is free from here on)
     float local = 0.f;
     for (int it = threadIdx.x; it < SSIM_S * (SSIM_S / 7); it += blockDim.x) {
         const int c = it % SSIM_S, r0 = (it / SSIM_S) * 7;
@@ -198,8 +201,8 @@ __global__ void __launch_bounds__(256) ssim_tile_kernel(int W, int H, const floa
         for (int j = 0; j < 4; ++j) {
             const int r = r0 + j, gy = oy + r;
             if (gy >= H || gx >= W) continue;
-            const int jj = (r + 2 * SSIM_R) * SSIM_I + c + 2 * SSIM_R;
-            dp[(int64_t)gy * W + gx] += weight * (g[j][0] + 2.f * sx[jj] * g[j][1] + sy[jj] * g[j][2]);
+            const int64_t e = (int64_t)gy * W + gx;
+            dp[e] += weight * (g[j][0] + 2.f * xp[e] * g[j][1] + yp[e] * g[j][2]);
         }
     }
 }
