@@ -925,10 +925,13 @@ def run_ours(args):
     e2e = None
     if True:
         b = w["bufs"]
-        Ct_h = b["Ct"].cpu().pin_memory()
-        Dt_h = b["Dt"].cpu().pin_memory()
+        # staging buffers from the library's page-locked host allocator
+        Ct_h = V.host_empty(b["Ct"].numel())
+        Ct_h.copy_(b["Ct"].cpu())
+        Dt_h = V.host_empty(b["Dt"].numel())
+        Dt_h.copy_(b["Dt"].cpu())
         n_e2e = max(3, min(args.steps, 200))
-        out_h = torch.empty((n_e2e, 7), dtype=torch.float32).pin_memory()
+        out_h = V.host_empty((n_e2e, 7))
         bufs2 = dict(b, Ct=torch.empty_like(b["Ct"]), Dt=torch.empty_like(b["Dt"]))
         step2 = make_step(V, dict(w, bufs=bufs2))
         if graph is not None:

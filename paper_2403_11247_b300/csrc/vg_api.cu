@@ -3,6 +3,8 @@
 // sequence of each call.  Nothing here synchronises the stream except
 // vg_scene_upload, vg_check and vg_ctx_stats.
 #include <cuda_runtime.h>
+#include <stdlib.h>
+#include <sys/mman.h>
 
 #include <algorithm>
 #include <cmath>
@@ -866,6 +868,36 @@ vg_status vg_mask_prune(vg_scene* scene, const uint32_t* hit_count, const uint32
         return fail(VG_ERR_INVALID_ARG, "vg_mask_prune: hit_count and seen go together");
     return vg_mask_kernels_prune(const_cast<float*>(scene->dev.mask), scene->dev.mask_thr, hit_count, seen, min_hits,
                                  scene->dev.N, removed, n_removed, (cudaStream_t)stream);
+}
+
+vg_status vg_host_alloc(int64_t bytes, void** out) {
+    if (!out || bytes <= 0) return fail(VG_ERR_INVALID_ARG, "vg_host_alloc: bytes must be > 0");
+    *out = nullptr;
+    const size_t align = (size_t)2 << 20;
+    const size_t size = ((size_t)bytes + align - 1) / align * align;
+    void* p = nullptr;
+    if (posix_memalign(&p, align, size) != 0 || !p) return fail(VG_ERR_OOM, "vg_host_alloc: out of host memory");
+    madvise(p, size, MADV_HUGEPAGE);  // a hint: fewer, larger pages for the DMA engine to translate
+    std::memset(p, 0, size);
+    cudaError_t e = cudaHostRegister(p, size, cudaHostRegisterDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free(p);
+        return fail(VG_ERR_CUDA, std::string("vg_host_alloc: cudaHostRegister: ") + cudaGetErrorString(e));
+    }
+    *out = p;
+    return VG_OK;
+}
+
+vg_status vg_host_free(void* ptr) {
+    if (!ptr) return VG_OK;
+    cudaError_t e = cudaHostUnregister(ptr);
+    free(ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(VG_ERR_CUDA, std::string("vg_host_free: cudaHostUnregister: ") + cudaGetErrorString(e));
+    }
+    return VG_OK;
 }
 
 vg_status vg_grow_accumulate(const vg_scene* scene, vg_ctx* ctx, float* grad_sum, uint32_t* grad_cnt, float* opa_sum,

@@ -84,8 +84,9 @@ class ServingWorkload:
             for w, h in self.sizes:
                 ref = synth.serving_camera(w, h)
                 C_, D, _ = V.render_with_retry(scenes[sid], [ref], params, ctx)
-                Ct = torch.empty(C_.numel(), dtype=torch.float32, pin_memory=True)
-                Dt = torch.empty(D.numel(), dtype=torch.float32, pin_memory=True)
+                # the targets track requests upload: page-locked, huge-page backed
+                Ct = V.host_empty(C_.numel())
+                Dt = V.host_empty(D.numel())
                 Ct.copy_(C_)
                 Dt.copy_(D)
                 self.targets[(sid, w, h)] = (ref, Ct, Dt)

@@ -109,6 +109,8 @@ def lib():
             "vg_grow_accumulate": [P, P, P, P, P, P, P],
             "vg_anchor_grow": [P, P, P, P, C.c_float, C.c_float, I32, C.c_double, C.c_uint64, I64, P, P, P, P],
             "vg_anchor_prune": [P, P, P, C.c_float, P, P, P],
+            "vg_host_alloc": [I64, P],
+            "vg_host_free": [P],
             "vg_adam_step": [P, I32, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
             "vg_pose_step": [I32, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
         }
@@ -278,6 +280,32 @@ def vg_ctx_create(pair_capacity: int = 0) -> CtxHandle:
     h = C.c_void_p()
     _check(lib().vg_ctx_create(int(pair_capacity), C.byref(h)), "vg_ctx_create")
     return CtxHandle(h.value)
+
+
+def vg_host_alloc(nbytes: int) -> int:
+    p = C.c_void_p()
+    _check(lib().vg_host_alloc(int(nbytes), C.byref(p)), "vg_host_alloc")
+    return p.value
+
+
+def vg_host_free(ptr: int):
+    _check(lib().vg_host_free(C.c_void_p(ptr)), "vg_host_free")
+
+
+def host_empty(shape, dtype=None):
+    """A CPU tensor in vg_host_alloc memory (page-locked, huge-page backed):
+    the staging buffer for frames streamed to the device.  The memory is
+    freed when the last tensor viewing it is gone."""
+    import weakref
+    torch = _torch()
+    dtype = dtype or torch.float32
+    shape = (shape,) if isinstance(shape, int) else tuple(shape)
+    n = int(np.prod(shape)) if shape else 1
+    nbytes = max(1, n * torch.empty((), dtype=dtype).element_size())
+    ptr = vg_host_alloc(nbytes)
+    buf = (C.c_char * nbytes).from_address(ptr)
+    weakref.finalize(buf, vg_host_free, ptr)
+    return torch.frombuffer(buf, dtype=dtype, count=n).view(shape)
 
 
 def vg_ctx_reserve(ctx: CtxHandle, pair_capacity: int):
@@ -605,7 +633,7 @@ def exported_symbols():
             "vg_ctx_profile_read", "vg_adam_step", "vg_pose_step", "vg_rvq_decode", "vg_render_fwd",
             "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
             "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune", "vg_ssim_loss", "vg_icp_associate",
-            "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune"]
+            "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune", "vg_host_alloc", "vg_host_free"]
 
 
 PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),
