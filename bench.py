@@ -951,22 +951,22 @@ def run_ours(args):
             e.record(stream)
         t0 = time.perf_counter()
         with torch.cuda.stream(copy_stream):
-            tgts[0][0].copy_(Ct_h, non_blocking=True)
-            tgts[0][1].copy_(Dt_h, non_blocking=True)
+            V.vg_memcpy_async(tgts[0][0], Ct_h, copy_stream)
+            V.vg_memcpy_async(tgts[0][1], Dt_h, copy_stream)
             ready[0].record(copy_stream)
         for i in range(n_e2e):
             j = i & 1
             if i + 1 < n_e2e:
                 copy_stream.wait_event(free[1 - j])
                 with torch.cuda.stream(copy_stream):
-                    tgts[1 - j][0].copy_(Ct_h, non_blocking=True)
-                    tgts[1 - j][1].copy_(Dt_h, non_blocking=True)
+                    V.vg_memcpy_async(tgts[1 - j][0], Ct_h, copy_stream)
+                    V.vg_memcpy_async(tgts[1 - j][1], Dt_h, copy_stream)
                     ready[1 - j].record(copy_stream)
             stream.wait_event(ready[j])
             runs[j]()
             free[j].record(stream)
-            out_h[i, 0:1].copy_(b["loss"], non_blocking=True)
-            out_h[i, 1:7].copy_(b["dxi"].view(-1), non_blocking=True)
+            V.vg_memcpy_async(out_h[i, 0:1], b["loss"], stream)
+            V.vg_memcpy_async(out_h[i, 1:7], b["dxi"].view(-1), stream)
         stream.synchronize()
         dt = time.perf_counter() - t0
         if V.vg_check(w["ctx"]) != V.VG_OK or not bool(torch.isfinite(out_h).all()):

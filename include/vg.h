@@ -226,6 +226,11 @@ vg_status vg_ctx_free(vg_ctx* ctx);
  * a no-op); the caller keeps no device work reading it in flight. */
 vg_status vg_host_alloc(int64_t bytes, void** out);
 vg_status vg_host_free(void* ptr);
+/* One asynchronous copy of `bytes` between any two of host memory (page-
+ * locked for asynchrony, e.g. from vg_host_alloc) and device memory, in
+ * `stream` order (cudaMemcpyAsync with the direction inferred from the
+ * pointers).  VG_ERR_INVALID_ARG for a negative size or NULL pointers. */
+vg_status vg_memcpy_async(void* dst, const void* src, int64_t bytes, vg_stream stream);
 /* Grow the pair buffer to at least `pair_capacity` (no-op if large enough). */
 vg_status vg_ctx_reserve(vg_ctx* ctx, int64_t pair_capacity);
 /* Synchronise `stream`, read the counters into *out (may be NULL), return

@@ -879,7 +879,9 @@ vg_status vg_host_alloc(int64_t bytes, void** out) {
     if (posix_memalign(&p, align, size) != 0 || !p) return fail(VG_ERR_OOM, "vg_host_alloc: out of host memory");
     madvise(p, size, MADV_HUGEPAGE);  // a hint: fewer, larger pages for the DMA engine to translate
     std::memset(p, 0, size);
-    cudaError_t e = cudaHostRegister(p, size, cudaHostRegisterDefault);
+    // portable: page-locked for every CUDA context of the process (the
+    // caller's framework may run its own runtime beside this library's)
+    cudaError_t e = cudaHostRegister(p, size, cudaHostRegisterPortable);
     if (e != cudaSuccess) {
         cudaGetLastError();
         free(p);
@@ -897,6 +899,13 @@ vg_status vg_host_free(void* ptr) {
         cudaGetLastError();
         return fail(VG_ERR_CUDA, std::string("vg_host_free: cudaHostUnregister: ") + cudaGetErrorString(e));
     }
+    return VG_OK;
+}
+
+vg_status vg_memcpy_async(void* dst, const void* src, int64_t bytes, vg_stream stream) {
+    if (bytes < 0 || (bytes > 0 && (!dst || !src))) return fail(VG_ERR_INVALID_ARG, "vg_memcpy_async: bad arguments");
+    if (bytes == 0) return VG_OK;
+    VG_CUDA(cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDefault, (cudaStream_t)stream));
     return VG_OK;
 }
 

@@ -111,6 +111,7 @@ def lib():
             "vg_anchor_prune": [P, P, P, C.c_float, P, P, P],
             "vg_host_alloc": [I64, P],
             "vg_host_free": [P],
+            "vg_memcpy_async": [P, P, I64, P],
             "vg_adam_step": [P, I32, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
             "vg_pose_step": [I32, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
         }
@@ -290,6 +291,19 @@ def vg_host_alloc(nbytes: int) -> int:
 
 def vg_host_free(ptr: int):
     _check(lib().vg_host_free(C.c_void_p(ptr)), "vg_host_free")
+
+
+def vg_memcpy_async(dst, src, stream=None):
+    """Copies tensor src into tensor dst (same number of bytes; host or
+    device) in stream order through the library."""
+    nb = src.numel() * src.element_size()
+    if dst.numel() * dst.element_size() != nb:
+        raise ValueError("vg_memcpy_async: sizes differ")
+    def any_ptr(t):
+        if not t.is_contiguous():
+            raise ValueError("vg_memcpy_async: tensors must be contiguous")
+        return t.data_ptr()
+    _check(lib().vg_memcpy_async(any_ptr(dst), any_ptr(src), int(nb), _stream(stream)), "vg_memcpy_async")
 
 
 def host_empty(shape, dtype=None):
@@ -633,7 +647,7 @@ def exported_symbols():
             "vg_ctx_profile_read", "vg_adam_step", "vg_pose_step", "vg_rvq_decode", "vg_render_fwd",
             "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
             "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune", "vg_ssim_loss", "vg_icp_associate",
-            "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune", "vg_host_alloc", "vg_host_free"]
+            "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune", "vg_host_alloc", "vg_host_free", "vg_memcpy_async"]
 
 
 PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),

@@ -27,12 +27,12 @@ def test_host_buffers_are_pinned_and_round_trip(torch):
     src = np.random.default_rng(1).normal(size=n).astype(np.float32)
     h.copy_(torch.from_numpy(src))
     d = torch.empty(n, device="cuda")
+    back = V.host_empty(n)
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        d.copy_(h, non_blocking=True)
+        V.vg_memcpy_async(d, h, s)
         d.mul_(2.0)
-        back = V.host_empty(n)
-        back.copy_(d, non_blocking=True)
+        V.vg_memcpy_async(back, d, s)
     s.synchronize()
     assert np.array_equal(back.numpy(), 2.0 * src)
     v = h[10:20]               # a view keeps the memory alive
