@@ -927,9 +927,9 @@ def run_ours(args):
         b = w["bufs"]
         # staging buffers from the library's page-locked host allocator
         Ct_h = V.host_empty(b["Ct"].numel())
-        Ct_h.copy_(b["Ct"].cpu())
+        V.vg_host_stage(Ct_h, b["Ct"].cpu())
         Dt_h = V.host_empty(b["Dt"].numel())
-        Dt_h.copy_(b["Dt"].cpu())
+        V.vg_host_stage(Dt_h, b["Dt"].cpu())
         n_e2e = max(3, min(args.steps, 200))
         out_h = V.host_empty((n_e2e, 7))
         bufs2 = dict(b, Ct=torch.empty_like(b["Ct"]), Dt=torch.empty_like(b["Dt"]))

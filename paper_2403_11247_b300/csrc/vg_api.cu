@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdlib.h>
 #include <sys/mman.h>
+#if defined(__x86_64__)
+#include <emmintrin.h>
+#endif
 
 #include <algorithm>
 #include <cmath>
@@ -899,6 +902,33 @@ vg_status vg_host_free(void* ptr) {
         cudaGetLastError();
         return fail(VG_ERR_CUDA, std::string("vg_host_free: cudaHostUnregister: ") + cudaGetErrorString(e));
     }
+    return VG_OK;
+}
+
+vg_status vg_host_stage(void* dst, const void* src, int64_t bytes) {
+    if (bytes < 0 || (bytes > 0 && (!dst || !src))) return fail(VG_ERR_INVALID_ARG, "vg_host_stage: bad arguments");
+    char* d = static_cast<char*>(dst);
+    const char* s = static_cast<const char*>(src);
+    int64_t i = 0;
+#if defined(__x86_64__)
+    // streaming stores: the data goes to memory, not to this core's caches
+    const int64_t head = (int64_t)((16 - (reinterpret_cast<uintptr_t>(d) & 15)) & 15);
+    for (; i < head && i < bytes; ++i) d[i] = s[i];
+    for (; i + 64 <= bytes; i += 64) {
+        const __m128i a = _mm_loadu_si128(reinterpret_cast<const __m128i*>(s + i));
+        const __m128i b = _mm_loadu_si128(reinterpret_cast<const __m128i*>(s + i + 16));
+        const __m128i c = _mm_loadu_si128(reinterpret_cast<const __m128i*>(s + i + 32));
+        const __m128i e = _mm_loadu_si128(reinterpret_cast<const __m128i*>(s + i + 48));
+        _mm_stream_si128(reinterpret_cast<__m128i*>(d + i), a);
+        _mm_stream_si128(reinterpret_cast<__m128i*>(d + i + 16), b);
+        _mm_stream_si128(reinterpret_cast<__m128i*>(d + i + 32), c);
+        _mm_stream_si128(reinterpret_cast<__m128i*>(d + i + 48), e);
+    }
+    for (; i < bytes; ++i) d[i] = s[i];
+    _mm_sfence();
+#else
+    std::memcpy(d, s, (size_t)bytes);
+#endif
     return VG_OK;
 }
 

@@ -87,8 +87,8 @@ class ServingWorkload:
                 # the targets track requests upload: page-locked, huge-page backed
                 Ct = V.host_empty(C_.numel())
                 Dt = V.host_empty(D.numel())
-                Ct.copy_(C_)
-                Dt.copy_(D)
+                V.vg_host_stage(Ct, C_.cpu())
+                V.vg_host_stage(Dt, D.cpu())
                 self.targets[(sid, w, h)] = (ref, Ct, Dt)
         torch.cuda.synchronize()
 

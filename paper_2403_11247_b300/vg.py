@@ -112,6 +112,7 @@ def lib():
             "vg_host_alloc": [I64, P],
             "vg_host_free": [P],
             "vg_memcpy_async": [P, P, I64, P],
+            "vg_host_stage": [P, P, I64],
             "vg_adam_step": [P, I32, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
             "vg_pose_step": [I32, P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, P, I32, P],
         }
@@ -304,6 +305,21 @@ def vg_memcpy_async(dst, src, stream=None):
             raise ValueError("vg_memcpy_async: tensors must be contiguous")
         return t.data_ptr()
     _check(lib().vg_memcpy_async(any_ptr(dst), any_ptr(src), int(nb), _stream(stream)), "vg_memcpy_async")
+
+
+def vg_host_stage(dst, src):
+    """Writes CPU tensor (or numpy array) src into CPU tensor dst, e.g. a
+    host_empty staging buffer, with streaming stores (see vg.h)."""
+    if isinstance(src, np.ndarray):
+        src = np.ascontiguousarray(src)
+        sp, nb = src.ctypes.data, src.nbytes
+    else:
+        if not src.is_contiguous() or src.is_cuda:
+            raise ValueError("vg_host_stage: src must be a contiguous host tensor")
+        sp, nb = src.data_ptr(), src.numel() * src.element_size()
+    if dst.is_cuda or not dst.is_contiguous() or dst.numel() * dst.element_size() != nb:
+        raise ValueError("vg_host_stage: dst must be a contiguous host tensor of the same size")
+    _check(lib().vg_host_stage(C.c_void_p(dst.data_ptr()), C.c_void_p(sp), int(nb)), "vg_host_stage")
 
 
 def host_empty(shape, dtype=None):
@@ -647,7 +663,7 @@ def exported_symbols():
             "vg_ctx_profile_read", "vg_adam_step", "vg_pose_step", "vg_rvq_decode", "vg_render_fwd",
             "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
             "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune", "vg_ssim_loss", "vg_icp_associate",
-            "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune", "vg_host_alloc", "vg_host_free", "vg_memcpy_async"]
+            "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune", "vg_host_alloc", "vg_host_free", "vg_memcpy_async", "vg_host_stage"]
 
 
 PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),

@@ -7,6 +7,7 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 from paper_2403_11247_b300 import build as B
@@ -104,3 +105,17 @@ def test_product_path_has_no_oracle_import():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle|liboracle|vg_oracle|orc_", text, flags=re.M), f
+
+
+def test_host_stage_copies_like_memcpy_at_any_alignment_and_size(lib):
+    """The streaming-store staging copy is host only: it runs without a GPU."""
+    import torch
+    rng = np.random.default_rng(3)
+    for n in (0, 1, 15, 16, 63, 64, 65, 1000, 4099):
+        for off in (0, 1, 7, 16):
+            src = rng.integers(0, 256, size=n).astype(np.uint8)
+            dst = torch.zeros(n + off, dtype=torch.uint8)
+            V.vg_host_stage(dst[off:], src)
+            assert np.array_equal(dst.numpy()[off:], src) and not dst.numpy()[:off].any()
+    with pytest.raises(ValueError):
+        V.vg_host_stage(torch.zeros(3), np.zeros(4, np.float32))
