@@ -227,8 +227,9 @@ class Server:
                 res = torch.empty(7 * B, **f32)
                 dxi, loss = res[:6 * B].view(B, 6), res[6 * B:]
                 for i, r in enumerate(batch):
-                    Ct[3 * n * i:3 * n * (i + 1)].copy_(r.target[0], non_blocking=True)
-                    Dt[n * i:n * (i + 1)].copy_(r.target[1], non_blocking=True)
+                    # staged targets (library host memory): copied through the library
+                    V.vg_memcpy_async(Ct[3 * n * i:3 * n * (i + 1)], r.target[0], lane.stream)
+                    V.vg_memcpy_async(Dt[n * i:n * (i + 1)], r.target[1], lane.stream)
                 for i in range(B):
                     c3, c1 = slice(3 * n * i, 3 * n * (i + 1)), slice(n * i, n * (i + 1))
                     V.vg_loss_l1(1, n, C_[c3], D[c1], S[c1], Ct[c3], Dt[c1], self.w_depth, -1.0, lane.ctx,
