@@ -42,8 +42,10 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
     __syncthreads();
     const uint32_t nvis = min(*nvis_dev, max_vis);
     const int lane = threadIdx.x & 31;
-    // warp-uniform trip count, so that the pose sums can use warp shuffles
-    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nvis;
+    // warp-uniform trip count, so that the pose sums can use warp shuffles;
+    // consecutive 32-slot chunks go to consecutive blocks, so that a visible
+    // set smaller than the grid still spreads over every SM
+    for (uint32_t base = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32u; base < nvis;
          base += gridDim.x * blockDim.x) {
         const uint32_t e = base + lane;
         float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};

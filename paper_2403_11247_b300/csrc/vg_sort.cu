@@ -354,18 +354,24 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, co
 // instead of a cluster of long neighbouring tiles running last (one block)
 // ---------------------------------------------------------------------------
 constexpr int ORDER_BUCKETS = 256;
+constexpr int RANGES_SMEM_TILES = 32768;  // counts staged in shared memory up to this many tiles (128 KB)
 
 __device__ __forceinline__ int order_bucket(uint32_t c, uint32_t cmax) {
     // 0 for the longest lists, ORDER_BUCKETS - 1 for empty ones
     return ORDER_BUCKETS - 1 - (int)(((uint64_t)c * (ORDER_BUCKETS - 1)) / (cmax > 0 ? cmax : 1u));
 }
 
-__global__ void __launch_bounds__(1024) ranges_kernel(const uint32_t* __restrict__ cnt, int n, uint2* __restrict__ ranges,
-                                                      uint32_t* __restrict__ order) {
+__global__ void __launch_bounds__(1024) ranges_kernel(const uint32_t* __restrict__ cnt_g, int n,
+                                                      uint2* __restrict__ ranges, uint32_t* __restrict__ order,
+                                                      int staged) {
     __shared__ uint32_t s_w[32];
     __shared__ uint32_t s_carry, s_max;
     __shared__ uint32_t s_bin[ORDER_BUCKETS];
+    extern __shared__ uint32_t s_cnt[];  // the counts, when they fit: one coalesced load for all three uses
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (staged)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) s_cnt[i] = cnt_g[i];
+    const uint32_t* cnt = staged ? s_cnt : cnt_g;
     if (threadIdx.x == 0) {
         s_carry = 0;
         s_max = 0;
@@ -435,7 +441,11 @@ __global__ void __launch_bounds__(1024) ranges_kernel(const uint32_t* __restrict
 
 cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, uint32_t* order, cudaStream_t st) {
     count_launches(1);
-    ranges_kernel<<<1, 1024, 0, st>>>(tile_counts, n_tiles, ranges, order);
+    const int staged = n_tiles <= RANGES_SMEM_TILES ? 1 : 0;
+    const size_t smem = staged ? (size_t)n_tiles * 4 : 0;
+    cudaError_t e = allow_dynamic_smem((const void*)ranges_kernel, smem);
+    if (e != cudaSuccess) return e;
+    ranges_kernel<<<1, 1024, smem, st>>>(tile_counts, n_tiles, ranges, order, staged);
     return cudaGetLastError();
 }
 
