@@ -93,6 +93,8 @@ def lib():
         _lib.orc_hit_counts.argtypes = [P, P, P, C.c_int]
         _lib.orc_set_window.restype = C.c_int
         _lib.orc_set_window.argtypes = [P] + [C.c_int] * 5
+        _lib.orc_set_pixel_mask.restype = None
+        _lib.orc_set_pixel_mask.argtypes = [P, P]
     return _lib
 
 
@@ -212,6 +214,19 @@ class Oracle:
         of ``view``; binning stays that of the whole image."""
         if lib().orc_set_window(self.ctx, int(view), int(x0), int(y0), int(x1), int(y1)) != 0:
             raise ValueError("bad view")
+
+    def set_pixel_mask(self, mask: Optional[np.ndarray]):
+        """Composite only the pixels where mask (uint8, one entry per pixel of
+        every view, views in order) is non-zero; None = all pixels."""
+        if mask is None:
+            self._pmask = None
+            lib().orc_set_pixel_mask(self.ctx, None)
+            return
+        m = np.ascontiguousarray(mask, dtype=np.uint8).ravel()
+        if m.size != self.n_pixels:
+            raise ValueError("pixel mask size differs from the views' pixel count")
+        self._pmask = m  # kept alive while the oracle uses it
+        lib().orc_set_pixel_mask(self.ctx, m.ctypes.data)
 
     def __del__(self):
         if getattr(self, "ctx", None):

@@ -92,6 +92,7 @@ struct orc_ctx {
     int64_t* tile_base;
     int64_t* pix_base;
     int* win;            /* per view x0, y0, x1, y1: the pixels composited */
+    const uint8_t* pmask; /* [n_pix] 0 = pixel not composited (sampled rays); NULL = all (caller-owned) */
     int64_t n_tiles, n_pix;
     int64_t* tile_start;
     int64_t* list;
@@ -423,6 +424,8 @@ int64_t orc_n_pairs(const orc_ctx* ctx) { return ctx->n_pairs; }
 int64_t orc_n_tiles(const orc_ctx* ctx) { return ctx->n_tiles; }
 int64_t orc_n_pixels(const orc_ctx* ctx) { return ctx->n_pix; }
 
+void orc_set_pixel_mask(orc_ctx* ctx, const uint8_t* mask) { ctx->pmask = mask; }
+
 int orc_set_window(orc_ctx* ctx, int v, int x0, int y0, int x1, int y1)
 {
     if (v < 0 || v >= ctx->nv) return -1;
@@ -562,8 +565,9 @@ int64_t orc_forward(orc_ctx* ctx, double* C, double* D, double* S, double* T_fin
                 double out[5], Tf;
                 int32_t nc, ne;
                 uint8_t f;
-                walk_pixel(ctx, v, px, py, NULL, out, &Tf, &nc, &ne, &f);
                 int64_t i = (int64_t)py * Wd + px;
+                if (ctx->pmask && !ctx->pmask[pb + i]) continue;
+                walk_pixel(ctx, v, px, py, NULL, out, &Tf, &nc, &ne, &f);
                 if (C) { C[3 * pb + i] = out[0]; C[3 * pb + HW + i] = out[1]; C[3 * pb + 2 * HW + i] = out[2]; }
                 if (D) D[pb + i] = out[3];
                 if (S) S[pb + i] = out[4];
@@ -607,6 +611,7 @@ void orc_hit_counts(orc_ctx* ctx, int64_t* hits, int32_t* seen, int threads)
             for (int py = ctx->win[4 * v + 1]; py < ctx->win[4 * v + 3]; ++py)
                 for (int px = ctx->win[4 * v + 0]; px < ctx->win[4 * v + 2]; ++px) {
                     double out[5];
+                    if (ctx->pmask && !ctx->pmask[ctx->pix_base[v] + (int64_t)py * ctx->cams[v].width + px]) continue;
                     int m = walk_pixel(ctx, v, px, py, steps, out, NULL, NULL, NULL, NULL);
                     for (int i = 0; i < m; ++i) {
                         int64_t n = steps[i].slot % N;
@@ -782,6 +787,7 @@ void orc_backward(orc_ctx* ctx, const double* dCimg, const double* dDimg, const 
             for (int py = ctx->win[4 * v + 1]; py < ctx->win[4 * v + 3]; ++py)
                 for (int px = ctx->win[4 * v + 0]; px < ctx->win[4 * v + 2]; ++px) {
                     int64_t i = (int64_t)py * Wd + px;
+                    if (ctx->pmask && !ctx->pmask[pb + i]) continue;
                     double gp[5];
                     gp[0] = dCimg ? dCimg[3 * pb + i] : 0;
                     gp[1] = dCimg ? dCimg[3 * pb + HW + i] : 0;

@@ -73,6 +73,13 @@ int64_t orc_n_pixels(const orc_ctx* ctx);
  * Returns -1 for a bad view. */
 int orc_set_window(orc_ctx* ctx, int v, int x0, int y0, int x1, int y1);
 
+/* Composite (forward, backward, hit counts) only the pixels whose entry of
+ * mask [n_pix] (views in order, each row-major) is non-zero: the sampled
+ * rays of a bundle-adjustment step; the other pixels' outputs are left
+ * untouched and their upstream gradients ignored.  The caller keeps mask
+ * alive; NULL restores every pixel. */
+void orc_set_pixel_mask(orc_ctx* ctx, const uint8_t* mask);
+
 /* Per-slot projection results (slot = view * N + n); any pointer may be NULL.
  * proj: [slots][16] = u, v, depth, conic a, b, c, opacity, r, g, b, valid,
  *        radius, rect x0, y0, x1, y1.  bin32: [slots][3] = FP32 u, v, depth.

@@ -1017,3 +1017,79 @@ def test_growing_statistics_definition():
     gs, gc, os_, oc = accumulate(g2d, valid, opa, k, n_views)
     assert np.allclose(gs, [5.0 + 13.0, 1.0, 0.0, 10.0]) and gc.tolist() == [2, 1, 0, 1]
     assert np.allclose(os_, [0.1 + 0.2 + 0.3, 0.4]) and oc.tolist() == [3, 1]
+
+
+# ---------------------------------------------------------------------------
+# random-ray sampling and the loss over the sampled rays (the BA's rays)
+# ---------------------------------------------------------------------------
+
+def test_ray_sampler_follows_splitmix64_and_rates():
+    from oracle.grow import GAMMA, MASK64, splitmix64
+    from oracle.rays import sample_rays, splitmix64_array
+    rng = np.random.default_rng(4)
+    st = rng.integers(0, 2 ** 63, size=200, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
+    assert [int(x) for x in splitmix64_array(st)] == [splitmix64(int(x)) for x in st]
+    n = 100000
+    assert sample_rays(n, 0.0, 3, 0).sum() == 0 and sample_rays(n, 1.0, 3, 0).sum() == n
+    a, b = sample_rays(n, 0.1, 3, 0), sample_rays(n, 0.3, 3, 0)
+    assert np.all(a <= b)                       # nested as the rate grows
+    for m, p in ((a, 0.1), (b, 0.3)):
+        assert abs(m.sum() - n * p) < 5 * np.sqrt(n * p * (1 - p))
+    assert not np.array_equal(a, sample_rays(n, 0.1, 3, 1))   # a new round draws new rays
+    # pixel 5 at round 2 by the rule itself
+    key = (3 + 2 * GAMMA) & MASK64
+    assert sample_rays(8, 0.5, 3, 2)[5] == int((splitmix64(key ^ 5) >> 11) < 2 ** 52)
+
+
+def test_masked_loss_hand_case_and_full_mask_reduces_to_the_loss():
+    from oracle.rays import loss_l1_masked
+    # two views of two pixels; pixel (0, 1) and (1, 0) sampled
+    C = np.array([[1.0, 2.0], [0.0, 0.0], [0.5, 0.5], [3.0, 1.0], [1.0, 1.0], [0.0, 2.0]])   # [v][c][p] flattened
+    Ct = np.zeros_like(C)
+    D = np.array([1.0, 5.0, 2.0, 2.0])
+    Dt = np.array([0.5, 6.0, 0.0, 1.0])
+    S = np.ones(4)
+    mask = np.array([0, 1, 1, 0])
+    L, dC, dD = loss_l1_masked(C.ravel(), D, S, Ct.ravel(), Dt, mask, 2, w_depth=0.5)
+    # colour: sampled values |2|+|0|+|0.5| (view 0, pixel 1) and |3|+|1|+|0| (view 1, pixel 0) over 3*2
+    # depth: only (0, 1) is valid (view 1 pixel 0 has Dt = 0): |5-6| * 0.5 / 1
+    assert abs(L - ((2.0 + 0.0 + 0.5 + 3.0 + 1.0 + 0.0) / 6.0 + 0.5)) < 1e-15
+    assert np.allclose(dD, [0.0, -0.5, 0.0, 0.0])
+    assert np.allclose(dC.reshape(2, 3, 2)[0, :, 0], 0.0) and np.allclose(dC.reshape(2, 3, 2)[1, :, 1], 0.0)
+    # every pixel sampled: the bench loss of one view (the C oracle's)
+    rng = np.random.default_rng(6)
+    P = 97
+    Cf, Ctf = rng.uniform(size=3 * P), rng.uniform(size=3 * P)
+    Df, Dtf = rng.uniform(1, 3, size=P), np.where(rng.uniform(size=P) < 0.8, rng.uniform(1, 3, size=P), 0.0)
+    Sf = rng.uniform(size=P)
+    L1, dC1, dD1 = loss_l1_masked(Cf, Df, Sf, Ctf, Dtf, np.ones(P), 1, w_depth=0.5, gate=0.3)
+    L2, dC2, dD2 = O.loss_l1(Cf, Df, Sf, Ctf, Dtf, w_depth=0.5, gate=0.3)
+    assert abs(L1 - L2) < 1e-12 and np.allclose(dC1, dC2, atol=1e-15) and np.allclose(dD1, dD2, atol=1e-15)
+
+
+def test_oracle_pixel_mask_composites_only_the_sampled_rays():
+    """With a pixel mask the oracle's images equal the full render on the
+    sampled pixels and stay zero elsewhere; its backward equals the full
+    backward with the upstream gradients of the other pixels zeroed."""
+    from oracle.rays import sample_rays
+    sc = synth.tiny_scene()
+    cams = [synth.tiny_camera(), synth.tiny_camera()]
+    o = O.Oracle(sc, cams)
+    full = o.forward()
+    P = o.n_pixels
+    m = sample_rays(P, 0.3, 9, 0)
+    om = O.Oracle(sc, cams)
+    om.set_pixel_mask(m)
+    part = om.forward()
+    keep = m.astype(bool)
+    assert np.array_equal(part["S"][keep], full["S"][keep]) and not part["S"][~keep].any()
+    assert np.array_equal(part["D"][keep], full["D"][keep])
+    rng = np.random.default_rng(2)
+    dC, dD, dS = rng.normal(size=3 * P), rng.normal(size=P), rng.normal(size=P)
+    mC = np.concatenate([np.tile(m[v * (P // 2):(v + 1) * (P // 2)], 3) for v in range(2)])
+    gm = om.backward(dC, dD, dS)
+    gf = o.backward(dC * mC, dD * m, dS * m)
+    for k in ("anchor_xyz", "offsets", "logscale", "rot", "opacity", "rgb"):
+        if k in gm and gm[k] is not None:
+            assert np.allclose(gm[k], gf[k], rtol=1e-12, atol=1e-15), k
+    assert np.allclose(gm["pose"], gf["pose"], rtol=1e-12, atol=1e-15)
