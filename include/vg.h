@@ -145,7 +145,12 @@ typedef struct {
  *   A tile list longer than VG_TILE_SORT_CAP cannot be sorted so: the
  *   forward's outputs are then invalid, the next vg_check returns
  *   VG_ERR_CAPACITY, and the ctx uses VG_SORT_GLOBAL from then on under
- *   VG_SORT_AUTO (the default). */
+ *   VG_SORT_AUTO (the default).
+ * pixel_mask: optional DEVICE array [total pixels of all views, in view
+ *   order, each row-major] of 0/1: only pixels with 1 are composited (the
+ *   sampled rays of a bundle-adjustment step, Sec. "Tracking and
+ *   Local-to-Global Bundle Adjustment"); the others get C = D = S = 0 and
+ *   are skipped by the backward.  NULL = every pixel.  See vg_sample_rays. */
 typedef struct {
     int32_t tile;
     int32_t batch;
@@ -157,6 +162,7 @@ typedef struct {
     uint32_t* hit_count;
     uint32_t* seen;
     int32_t sort_mode;
+    const uint8_t* pixel_mask;
 } vg_render_params;
 
 /* Gradient outputs of vg_render_bwd (DEVICE pointers, caller-allocated; each
@@ -385,6 +391,25 @@ vg_status vg_pose_step(int32_t n_views, float* pose, const float* dxi, float* m,
 
 /* Number of CUDA kernels libvg has enqueued in this process (host count). */
 int64_t vg_launch_count(void);
+
+/* vg_loss_l1 over the sampled rays only: pixels with pixel_mask 0 (same
+ * layout as vg_render_params.pixel_mask) get zero gradient, and the means
+ * run over the sampled pixels (colour) and the sampled pixels with Dt > 0
+ * (depth).  pixel_mask = NULL is vg_loss_l1. */
+vg_status vg_loss_l1_masked(int32_t n_views, int64_t n_pix, const float* C, const float* D, const float* S,
+                            const float* Ct, const float* Dt, const uint8_t* pixel_mask, float w_depth, float gate,
+                            float* dC, float* dD, float* dS, float* loss, vg_ctx* ctx, vg_stream stream);
+
+/* Random-ray sampling for the bundle adjustment (Sec. "Tracking and
+ * Local-to-Global Bundle Adjustment": rays sampled from the keyframe
+ * database): mask[p] = 1 iff SplitMix64((seed + r * 0x9E3779B97F4A7C15) ^ p)
+ * >> 11 < floor(rate * 2^53) for p in [0, n), else 0, with r = round_dev[0]
+ * when round_dev is non-NULL (a device counter, e.g. an optimiser step, so
+ * that a captured graph draws new rays on every replay) else round_host.
+ * SplitMix64 is the generator of Steele, Lea and Flood (OOPSLA 2014).
+ * VG_ERR_INVALID_ARG for n < 0, a NULL mask or rate outside [0, 1]. */
+vg_status vg_sample_rays(uint8_t* mask, int64_t n, double rate, uint64_t seed, const int32_t* round_dev,
+                         int32_t round_host, vg_stream stream);
 
 /* vg_loss_l1 without a ctx, for callers that cannot allocate device memory
  * (the paper has no counterpart: this is a library facility).  Making a

@@ -573,6 +573,7 @@ static vg_status build_views(const vg_camera* cams, int32_t n_views, const vg_re
     cs->hit_count = p->hit_count;
     cs->seen = p->seen;
     cs->depth_hist = 1;
+    cs->pix_mask = p->pixel_mask;
     if (p->sort_mode < VG_SORT_AUTO || p->sort_mode > VG_SORT_TILE)
         return fail(VG_ERR_INVALID_ARG, "sort_mode must be VG_SORT_AUTO, VG_SORT_GLOBAL or VG_SORT_TILE");
     cs->n_gauss = 0;  // set by the caller that knows the scene
@@ -818,6 +819,22 @@ vg_status vg_pose_grad(vg_ctx* ctx, int32_t n_views, const float* icp_q, const f
 vg_status vg_loss_l1(int32_t n_views, int64_t n_pix, const float* C, const float* D, const float* S, const float* Ct,
                      const float* Dt, float w_depth, float gate, float* dC, float* dD, float* dS, float* loss,
                      vg_ctx* ctx, vg_stream stream) {
+    return vg_loss_l1_masked(n_views, n_pix, C, D, S, Ct, Dt, nullptr, w_depth, gate, dC, dD, dS, loss, ctx, stream);
+}
+
+vg_status vg_sample_rays(uint8_t* mask, int64_t n, double rate, uint64_t seed, const int32_t* round_dev,
+                         int32_t round_host, vg_stream stream) {
+    if (n < 0 || (n > 0 && !mask) || !(rate >= 0.0 && rate <= 1.0))
+        return fail(VG_ERR_INVALID_ARG, "vg_sample_rays: n >= 0, a mask and rate in [0, 1] are needed");
+    const unsigned long long keep_below = (unsigned long long)std::floor(rate * 9007199254740992.0);
+    VG_CUDA(launch_sample_rays(mask, n, (unsigned long long)seed, round_dev, round_host, keep_below,
+                               (cudaStream_t)stream));
+    return VG_OK;
+}
+
+vg_status vg_loss_l1_masked(int32_t n_views, int64_t n_pix, const float* C, const float* D, const float* S,
+                            const float* Ct, const float* Dt, const uint8_t* pixel_mask, float w_depth, float gate,
+                            float* dC, float* dD, float* dS, float* loss, vg_ctx* ctx, vg_stream stream) {
     if (!ctx || !C || !D || !Ct || !Dt || !dC || !dD || !loss || n_views < 1 || n_pix < 1)
         return fail(VG_ERR_INVALID_ARG, "vg_loss_l1: null argument or empty size");
     if (gate >= 0.f && !S) return fail(VG_ERR_INVALID_ARG, "vg_loss_l1: gate needs S");
@@ -827,7 +844,7 @@ vg_status vg_loss_l1(int32_t n_views, int64_t n_pix, const float* C, const float
     VG_CUDA(cudaMemsetAsync(ctx->loss_scratch.p, 0, 16, st));
     VG_CUDA(cudaMemsetAsync(loss, 0, 4, st));
     if (dS) VG_CUDA(cudaMemsetAsync(dS, 0, (size_t)n_views * n_pix * 4, st));
-    VG_STAGE(VG_STAGE_LOSS, launch_loss_l1(n_views, n_pix, C, D, S, Ct, Dt, w_depth, gate, dC, dD, loss,
+    VG_STAGE(VG_STAGE_LOSS, launch_loss_l1(n_views, n_pix, C, D, S, Ct, Dt, pixel_mask, w_depth, gate, dC, dD, loss,
                                            ctx->loss_scratch.as<uint32_t>(), st));
     return VG_OK;
 }

@@ -200,6 +200,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
         fpx[k] = (float)px[k];
         fpy[k] = (float)py[k];
         done[k] = !(px[k] < vi.W && py[k] < vi.H);
+        // a pixel that is not a sampled ray is left out from the start
+        if (!done[k] && cs.pix_mask) done[k] = cs.pix_mask[vi.pix_base + (int64_t)py[k] * vi.W + px[k]] == 0;
         T[k] = 1.f;
         last[k] = 0;
         stop_at[k] = 0xffffffffu;
@@ -210,10 +212,16 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     const int lane = threadIdx.x & 31;
     const uint2 rg = ranges[gt];
     if (TSORT && rg.y - rg.x > 1) {
-        if (rg.y - rg.x <= (uint32_t)VG_TILE_SORT_CAP)
-            tile_sort<NT>(pvals, rg, dkey, reinterpret_cast<uint2*>(s_raw));
-        else if (threadIdx.x == 0)
-            atomicOr(err, ERR_TILE_LIST);  // composited unsorted; the outputs are flagged invalid
+        int alldone = 1;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) alldone &= (int)done[k];
+        // a tile without a pixel to composite needs no order (its backward walks nothing)
+        if (__syncthreads_count(alldone) < NT) {
+            if (rg.y - rg.x <= (uint32_t)VG_TILE_SORT_CAP)
+                tile_sort<NT>(pvals, rg, dkey, reinterpret_cast<uint2*>(s_raw));
+            else if (threadIdx.x == 0)
+                atomicOr(err, ERR_TILE_LIST);  // composited unsorted; the outputs are flagged invalid
+        }
     }
     for (uint32_t b = rg.x; b < rg.y; b += BLEND_BATCH) {
         int alldone = 1;

@@ -49,7 +49,20 @@ struct Consts {
     uint32_t* seen;       // [N] set to 1 where a Gaussian is visible in some view; NULL = off
     int64_t n_gauss;      // N, for the two arrays above
     int32_t depth_hist;   // the preprocess accumulates depth-key digit histograms (global depth sort)
+    const uint8_t* pix_mask;  // [pixels] 0 = not composited (sampled rays); NULL = every pixel
 };
+
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): the output for generator state `state` (the
+// golden gamma added, then the published finaliser); used as a counter-based
+// generator keyed by (seed, counter)
+constexpr unsigned long long GOLDEN_GAMMA = 0x9E3779B97F4A7C15ull;
+__host__ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long state) {
+    unsigned long long z = state + GOLDEN_GAMMA;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
 
 // Scene arrays as the kernels see them (device pointers).
 struct SceneDev {

@@ -436,42 +436,61 @@ cudaError_t launch_pose_final(int n_views, const float* pose_sum, const float* i
 // ---------------------------------------------------------------------------
 // L1 colour + weighted L1 depth (valid where the target depth > 0)
 // ---------------------------------------------------------------------------
-__global__ void count_valid_kernel(const float* __restrict__ Dt, int64_t n, uint32_t* count) {
-    uint32_t c = 0;
+// count[0] += sampled pixels with Dt > 0; with a mask also count[1] += sampled pixels
+__global__ void count_valid_kernel(const float* __restrict__ Dt, const uint8_t* __restrict__ mask, int64_t n,
+                                   uint32_t* count) {
+    uint32_t c = 0, ns = 0;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthr = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n4 = (reinterpret_cast<uintptr_t>(Dt) & 15u) == 0 ? n / 4 : 0;
+    const bool vec = (reinterpret_cast<uintptr_t>(Dt) & 15u) == 0 && (reinterpret_cast<uintptr_t>(mask) & 3u) == 0;
+    const int64_t n4 = vec ? n / 4 : 0;
     for (int64_t i = tid; i < n4; i += nthr) {
         const float4 d = reinterpret_cast<const float4*>(Dt)[i];
-        c += (d.x > 0.f) + (d.y > 0.f) + (d.z > 0.f) + (d.w > 0.f);
+        if (mask) {
+            const uchar4 m = reinterpret_cast<const uchar4*>(mask)[i];
+            c += (m.x && d.x > 0.f) + (m.y && d.y > 0.f) + (m.z && d.z > 0.f) + (m.w && d.w > 0.f);
+            ns += (m.x != 0) + (m.y != 0) + (m.z != 0) + (m.w != 0);
+        } else {
+            c += (d.x > 0.f) + (d.y > 0.f) + (d.z > 0.f) + (d.w > 0.f);
+        }
     }
-    for (int64_t i = n4 * 4 + tid; i < n; i += nthr) c += Dt[i] > 0.f;
+    for (int64_t i = n4 * 4 + tid; i < n; i += nthr) {
+        const bool m = mask ? mask[i] != 0 : true;
+        c += m && Dt[i] > 0.f;
+        ns += m;
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        ns += __shfl_xor_sync(0xffffffffu, ns, o);
+    }
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+    if ((threadIdx.x & 31) == 0 && mask && ns) atomicAdd(count + 1, ns);
 }
 
 // one pixel of the loss: colour residuals of the three planes, depth residual
 __device__ __forceinline__ float loss_pixel(float c0, float c1, float c2, float t0, float t1, float t2, float d,
                                             float dt, float s, float gate, float inv_c, float inv_d, float& g0,
-                                            float& g1, float& g2, float& gd) {
-    const float m = (gate >= 0.f && !(s > gate)) ? 0.f : 1.f;
+                                            float& g1, float& g2, float& gd, bool sampled = true) {
+    const float m = (!sampled || (gate >= 0.f && !(s > gate))) ? 0.f : 1.f;
     const float r0 = c0 - t0, r1 = c1 - t1, r2 = c2 - t2, rd = d - dt;
     auto sgn = [](float r) { return (r > 0.f) ? 1.f : ((r < 0.f) ? -1.f : 0.f); };
     g0 = m * sgn(r0) * inv_c;
     g1 = m * sgn(r1) * inv_c;
     g2 = m * sgn(r2) * inv_c;
-    const bool valid = dt > 0.f;
+    const bool valid = sampled && dt > 0.f;
     gd = valid ? m * sgn(rd) * inv_d : 0.f;
     return m * (fabsf(r0) + fabsf(r1) + fabsf(r2)) * inv_c + (valid ? m * fabsf(rd) * inv_d : 0.f);
 }
 
 __global__ void loss_l1_kernel(int64_t n_pix, int64_t total, const float* __restrict__ C, const float* __restrict__ D,
                                const float* __restrict__ S, const float* __restrict__ Ct, const float* __restrict__ Dt,
-                               float w_depth, float gate, const uint32_t* __restrict__ valid_count,
-                               float* __restrict__ dC, float* __restrict__ dD, float* __restrict__ loss, int vec) {
+                               const uint8_t* __restrict__ mask, float w_depth, float gate,
+                               const uint32_t* __restrict__ valid_count, float* __restrict__ dC,
+                               float* __restrict__ dD, float* __restrict__ loss, int vec) {
     __shared__ float s_tmp[8];
-    const float nv = (float)(*valid_count);
-    const float inv_c = 1.f / (3.f * (float)total);
+    const float nv = (float)valid_count[0];
+    const float nsamp = mask ? (float)valid_count[1] : (float)total;
+    const float inv_c = nsamp > 0.f ? 1.f / (3.f * nsamp) : 0.f;
     const float inv_d = nv > 0.f ? w_depth / nv : 0.f;
     float acc = 0.f;
     const int64_t v = blockIdx.y;
@@ -489,6 +508,7 @@ __global__ void loss_l1_kernel(int64_t n_pix, int64_t total, const float* __rest
     float* g1p = dC + (v * 3 + 1) * n_pix;
     float* g2p = dC + (v * 3 + 2) * n_pix;
     float* gdp = dD + v * n_pix;
+    const uint8_t* mp = mask ? mask + v * n_pix : nullptr;
     const int64_t n4 = vec ? n_pix / 4 : 0;  // four pixels per step where every plane is 16-byte aligned
     for (int64_t i = tid; i < n4; i += nthr) {
         const float4 c0 = reinterpret_cast<const float4*>(c0p)[i], c1 = reinterpret_cast<const float4*>(c1p)[i],
@@ -498,11 +518,17 @@ __global__ void loss_l1_kernel(int64_t n_pix, int64_t total, const float* __rest
         const float4 d = reinterpret_cast<const float4*>(dp)[i], dt = reinterpret_cast<const float4*>(dtp)[i];
         float4 s = make_float4(1.f, 1.f, 1.f, 1.f);
         if (gate >= 0.f) s = reinterpret_cast<const float4*>(sp)[i];
+        uchar4 ms = make_uchar4(1, 1, 1, 1);
+        if (mp) ms = reinterpret_cast<const uchar4*>(mp)[i];
         float4 g0, g1, g2, gd;
-        acc += loss_pixel(c0.x, c1.x, c2.x, t0.x, t1.x, t2.x, d.x, dt.x, s.x, gate, inv_c, inv_d, g0.x, g1.x, g2.x, gd.x);
-        acc += loss_pixel(c0.y, c1.y, c2.y, t0.y, t1.y, t2.y, d.y, dt.y, s.y, gate, inv_c, inv_d, g0.y, g1.y, g2.y, gd.y);
-        acc += loss_pixel(c0.z, c1.z, c2.z, t0.z, t1.z, t2.z, d.z, dt.z, s.z, gate, inv_c, inv_d, g0.z, g1.z, g2.z, gd.z);
-        acc += loss_pixel(c0.w, c1.w, c2.w, t0.w, t1.w, t2.w, d.w, dt.w, s.w, gate, inv_c, inv_d, g0.w, g1.w, g2.w, gd.w);
+        acc += loss_pixel(c0.x, c1.x, c2.x, t0.x, t1.x, t2.x, d.x, dt.x, s.x, gate, inv_c, inv_d, g0.x, g1.x, g2.x, gd.x,
+                          ms.x != 0);
+        acc += loss_pixel(c0.y, c1.y, c2.y, t0.y, t1.y, t2.y, d.y, dt.y, s.y, gate, inv_c, inv_d, g0.y, g1.y, g2.y, gd.y,
+                          ms.y != 0);
+        acc += loss_pixel(c0.z, c1.z, c2.z, t0.z, t1.z, t2.z, d.z, dt.z, s.z, gate, inv_c, inv_d, g0.z, g1.z, g2.z, gd.z,
+                          ms.z != 0);
+        acc += loss_pixel(c0.w, c1.w, c2.w, t0.w, t1.w, t2.w, d.w, dt.w, s.w, gate, inv_c, inv_d, g0.w, g1.w, g2.w, gd.w,
+                          ms.w != 0);
         reinterpret_cast<float4*>(g0p)[i] = g0;
         reinterpret_cast<float4*>(g1p)[i] = g1;
         reinterpret_cast<float4*>(g2p)[i] = g2;
@@ -511,7 +537,7 @@ __global__ void loss_l1_kernel(int64_t n_pix, int64_t total, const float* __rest
     for (int64_t i = n4 * 4 + tid; i < n_pix; i += nthr) {
         float g0, g1, g2, gd;
         acc += loss_pixel(c0p[i], c1p[i], c2p[i], t0p[i], t1p[i], t2p[i], dp[i], dtp[i], gate >= 0.f ? sp[i] : 1.f, gate,
-                          inv_c, inv_d, g0, g1, g2, gd);
+                          inv_c, inv_d, g0, g1, g2, gd, mp ? mp[i] != 0 : true);
         g0p[i] = g0;
         g1p[i] = g1;
         g2p[i] = g2;
@@ -522,19 +548,39 @@ __global__ void loss_l1_kernel(int64_t n_pix, int64_t total, const float* __rest
 }
 
 cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const float* D, const float* S, const float* Ct,
-                           const float* Dt, float w_depth, float gate, float* dC, float* dD, float* loss,
-                           uint32_t* valid_count, cudaStream_t st) {
+                           const float* Dt, const uint8_t* mask, float w_depth, float gate, float* dC, float* dD,
+                           float* loss, uint32_t* valid_count, cudaStream_t st) {
     const int64_t total = (int64_t)n_views * n_pix;
     int64_t blocks = ceil_div(ceil_div(total > 0 ? total : 1, 4), 256);
     if (blocks > 148 * 8) blocks = 148 * 8;
     count_launches(2);
-    count_valid_kernel<<<(unsigned)blocks, 256, 0, st>>>(Dt, total, valid_count);
+    count_valid_kernel<<<(unsigned)blocks, 256, 0, st>>>(Dt, mask, total, valid_count);
     auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-    const int vec = (n_pix % 4 == 0) && al(C) && al(D) && al(Ct) && al(Dt) && al(dC) && al(dD) && (gate < 0.f || al(S));
+    const int vec = (n_pix % 4 == 0) && al(C) && al(D) && al(Ct) && al(Dt) && al(dC) && al(dD) &&
+                    (gate < 0.f || al(S)) && (reinterpret_cast<uintptr_t>(mask) & 3u) == 0;
     int64_t bx = ceil_div(vec ? ceil_div(n_pix, 4) : n_pix, 256);
     if (bx > 148 * 8) bx = 148 * 8;
-    loss_l1_kernel<<<dim3((unsigned)bx, (unsigned)n_views), 256, 0, st>>>(n_pix, total, C, D, S, Ct, Dt, w_depth, gate,
-                                                                          valid_count, dC, dD, loss, vec);
+    loss_l1_kernel<<<dim3((unsigned)bx, (unsigned)n_views), 256, 0, st>>>(n_pix, total, C, D, S, Ct, Dt, mask, w_depth,
+                                                                          gate, valid_count, dC, dD, loss, vec);
+    return cudaGetLastError();
+}
+
+__global__ void sample_rays_kernel(uint8_t* __restrict__ mask, int64_t n, unsigned long long seed,
+                                   const int32_t* __restrict__ round_dev, int32_t round_host,
+                                   unsigned long long keep_below) {
+    const unsigned long long r = (unsigned long long)(uint32_t)(round_dev ? round_dev[0] : round_host);
+    const unsigned long long key = seed + r * GOLDEN_GAMMA;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        mask[p] = (splitmix64(key ^ (unsigned long long)p) >> 11) < keep_below ? 1 : 0;
+}
+
+cudaError_t launch_sample_rays(uint8_t* mask, int64_t n, unsigned long long seed, const int32_t* round_dev,
+                               int32_t round_host, unsigned long long keep_below, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = ceil_div(n, 256);
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    count_launches(1);
+    sample_rays_kernel<<<(unsigned)blocks, 256, 0, st>>>(mask, n, seed, round_dev, round_host, keep_below);
     return cudaGetLastError();
 }
 

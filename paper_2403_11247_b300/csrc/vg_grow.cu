@@ -24,14 +24,6 @@ namespace vgk {
 
 constexpr unsigned long long GROW_EMPTY = ~0ull;
 constexpr int GROW_BIAS = 1 << 20;
-constexpr unsigned long long GOLDEN_GAMMA = 0x9E3779B97F4A7C15ull;
-
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long state) {
-    unsigned long long z = state + GOLDEN_GAMMA;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
 
 // packed voxel index of p at voxel size eps, or GROW_EMPTY when a component
 // is outside [-2^20, 2^20) or not finite

@@ -144,9 +144,12 @@ cudaError_t launch_icp(const SceneDev& S, const Views& V, const float* q, const 
 int icp_blocks(int64_t N);
 cudaError_t launch_pose_final(int n_views, const float* pose_sum, const float* icp_part, int n_icp_blocks,
                               float* dxi, float* icp_loss, cudaStream_t st);
+cudaError_t launch_sample_rays(uint8_t* mask, int64_t n, unsigned long long seed, const int32_t* round_dev,
+                               int32_t round_host, unsigned long long keep_below, cudaStream_t st);
+// mask non-NULL: only sampled pixels count (vg_loss_l1_masked); valid_count holds two words
 cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const float* D, const float* S,
-                           const float* Ct, const float* Dt, float w_depth, float gate, float* dC, float* dD,
-                           float* loss, uint32_t* valid_count, cudaStream_t st);
+                           const float* Ct, const float* Dt, const uint8_t* mask, float w_depth, float gate, float* dC,
+                           float* dD, float* loss, uint32_t* valid_count, cudaStream_t st);
 
 // optim.cu
 cudaError_t launch_adam(int n, float* const* p, const float* const* g, float* const* m, float* const* v,

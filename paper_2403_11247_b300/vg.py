@@ -58,7 +58,7 @@ class vg_render_params(C.Structure):
                 ("sigma_cull", C.c_float), ("clamp_factor", C.c_float),
                 ("jacobian_clamp", C.c_int32), ("count_evals", C.c_int32), ("pose_dev", C.c_void_p),
                 ("ppt_fwd", C.c_int32), ("ppt_bwd", C.c_int32), ("hit_count", C.c_void_p), ("seen", C.c_void_p),
-                ("sort_mode", C.c_int32)]
+                ("sort_mode", C.c_int32), ("pixel_mask", C.c_void_p)]
 
 
 class vg_scene_grads(C.Structure):
@@ -99,6 +99,8 @@ def lib():
             "vg_render_bwd": [P, P, I32, P, P, P, P, P, P, P],
             "vg_pose_grad": [P, I32, P, P, P, P, P],
             "vg_loss_l1": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P, P],
+            "vg_loss_l1_masked": [I32, I64, P, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P, P],
+            "vg_sample_rays": [P, I64, C.c_double, C.c_uint64, P, I32, P],
             "vg_loss_l1_noalloc": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P],
             "vg_probe_peak": [I32, I32, P, I64, P, P],
             "vg_rvq_encode": [P, I64, P, P, P, P, P],
@@ -174,7 +176,7 @@ def _host_or_dev_ptr(a):
 def default_params(**kw) -> vg_render_params:
     p = lib().vg_default_params()
     for k, v in kw.items():
-        if k in ("pose_dev", "hit_count", "seen"):
+        if k in ("pose_dev", "hit_count", "seen", "pixel_mask"):
             setattr(p, k, _ptr(v))
         else:
             setattr(p, k, v)
@@ -556,6 +558,30 @@ def vg_loss_l1(n_views: int, n_pix: int, C_, D, S, Ct, Dt, w_depth: float, gate:
     return dC, dD, dS, loss
 
 
+def vg_loss_l1_masked(n_views: int, n_pix: int, C_, D, S, Ct, Dt, pixel_mask, w_depth: float, gate: float,
+                      ctx: CtxHandle, dC=None, dD=None, dS=None, loss=None, stream=None):
+    """vg_loss_l1 over the sampled rays (pixel_mask uint8, one entry per pixel of every view)."""
+    torch = _torch()
+    if dC is None:
+        dC = torch.empty_like(C_)
+    if dD is None:
+        dD = torch.empty_like(D)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=C_.device)
+    _check(lib().vg_loss_l1_masked(int(n_views), int(n_pix), _ptr(C_), _ptr(D), _ptr(S), _ptr(Ct), _ptr(Dt),
+                                   _ptr(pixel_mask), float(w_depth), float(gate), _ptr(dC), _ptr(dD), _ptr(dS),
+                                   _ptr(loss), ctx.handle, _stream(stream)), "vg_loss_l1_masked")
+    return dC, dD, dS, loss
+
+
+def vg_sample_rays(mask, rate: float, seed: int, round_dev=None, round_host: int = 0, stream=None):
+    """Fills the uint8 device array mask with the rays sampled at this round
+    (see vg.h); round_dev: optional int32 device counter."""
+    _check(lib().vg_sample_rays(_ptr(mask), int(mask.numel()), float(rate), int(seed) & ((1 << 64) - 1),
+                                _ptr(round_dev), int(round_host), _stream(stream)), "vg_sample_rays")
+    return mask
+
+
 VG_BUF = dict(xy=0, conic=1, rgbd=2, rect=3, ntiles=4, pair_keys=5, pair_vals=6, ranges=7, t_final=8, n_contrib=9,
               g2d=10)
 _BUF_DTYPE = dict(xy=("float32", 4), conic=("float32", 4), rgbd=("float32", 4), rect=("uint32", 2),
@@ -663,7 +689,8 @@ def exported_symbols():
             "vg_ctx_profile_read", "vg_adam_step", "vg_pose_step", "vg_rvq_decode", "vg_render_fwd",
             "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
             "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune", "vg_ssim_loss", "vg_icp_associate",
-            "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune", "vg_host_alloc", "vg_host_free", "vg_memcpy_async", "vg_host_stage"]
+            "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune", "vg_host_alloc", "vg_host_free", "vg_memcpy_async", "vg_host_stage",
+            "vg_loss_l1_masked", "vg_sample_rays"]
 
 
 PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),
