@@ -10,6 +10,8 @@ colour), backward to the map and to the B pose twists,
 Adam on the poses (the pose moves by exp(-step^) on the left) and Adam on the
 map.  Poses live in a device array read by the kernels, so a captured graph
 follows them as they change; the step counters live on the device too.
+With ray_rate < 1 each iteration fits only a random subset of the keyframes'
+pixels (the BA's sampled rays), redrawn on the device every iteration.
 """
 from __future__ import annotations
 
@@ -25,14 +27,21 @@ from .autograd import SceneParams
 class LocalBA:
     def __init__(self, scene: SceneParams, cams: Sequence, Ct: torch.Tensor, Dt: torch.Tensor,
                  lr_rot: float = 2e-3, lr_trans: float = 2e-3, lr_map: float = 0.0, w_depth: float = 0.5,
-                 ppt_fwd: int = 0, ppt_bwd: int = 0, pair_headroom: float = 2.0, w_ssim: float = 0.0):
+                 ppt_fwd: int = 0, ppt_bwd: int = 0, pair_headroom: float = 2.0, w_ssim: float = 0.0,
+                 ray_rate: float = 1.0, ray_seed: int = 0):
         self.scene = scene
         self.cams = list(cams)
         self.B = len(self.cams)
         dev = torch.device("cuda", torch.cuda.current_device())
         f32 = dict(dtype=torch.float32, device=dev)
         self.pose = torch.tensor(np.stack([np.asarray(c.T_cw, np.float32).reshape(12) for c in self.cams]), **f32)
-        self.params = V.default_params(pose_dev=self.pose, ppt_fwd=ppt_fwd, ppt_bwd=ppt_bwd)
+        # random rays (rate < 1): every iteration composites and fits only a
+        # fresh random subset of the keyframes' pixels, drawn on the device
+        # with the pose step as the round, so a captured graph redraws them
+        self.ray_rate, self.ray_seed = float(ray_rate), int(ray_seed)
+        n_pix_all = len(self.cams) * self.cams[0].width * self.cams[0].height
+        self.rays = torch.ones(n_pix_all, dtype=torch.uint8, device=dev) if self.ray_rate < 1.0 else None
+        self.params = V.default_params(pose_dev=self.pose, ppt_fwd=ppt_fwd, ppt_bwd=ppt_bwd, pixel_mask=self.rays)
         self.Ct, self.Dt = Ct.contiguous(), Dt.contiguous()
         sizes = {(c.width, c.height) for c in self.cams}
         if len(sizes) != 1:
@@ -82,9 +91,11 @@ class LocalBA:
     def iterate(self, n: int = 1):
         """Enqueue n iterations on the current stream (no host sync)."""
         for _ in range(n):
+            if self.rays is not None:
+                V.vg_sample_rays(self.rays, self.ray_rate, self.ray_seed, round_dev=self.pose_step)
             V.vg_render_fwd(self.sh, self.cams, self.params, self.ctx, self.C, self.D, self.S)
-            V.vg_loss_l1(self.B, self.P, self.C, self.D, self.S, self.Ct, self.Dt, self.w_depth, -1.0, self.ctx,
-                         dC=self.dC, dD=self.dD, loss=self.loss)
+            V.vg_loss_l1_masked(self.B, self.P, self.C, self.D, self.S, self.Ct, self.Dt, self.rays, self.w_depth,
+                                -1.0, self.ctx, dC=self.dC, dD=self.dD, loss=self.loss)
             if self.w_ssim > 0:  # the SSIM term the bundle adjustment adds to the RGB rendering
                 V.vg_ssim_loss(self.ctx, self.B, self.cams[0].width, self.cams[0].height, self.C, self.Ct,
                                self.w_ssim, dC=self.dC, loss=self.ssim_loss)
