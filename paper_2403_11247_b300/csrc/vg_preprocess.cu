@@ -17,6 +17,9 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(SceneDev S, const __
                                                          uint32_t* __restrict__ blk_count) {
     __shared__ uint32_t s_hist[4 * 256];
     __shared__ uint32_t s_cnt[2];
+    constexpr int LS_STAGES = 8;            // stages the log-scale bound below covers
+    __shared__ float s_lsw[8][LS_STAGES];   // per warp, per stage: largest log-scale codebook entry
+    __shared__ float s_lsb;                 // bound on every decodable log-scale component
     extern __shared__ float s_cb[];  // the coded groups' codebooks, group after group
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_hist[i] = 0;
     if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
@@ -35,6 +38,34 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(SceneDev S, const __
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) state[ST_EPOCH] += 16u;  // fresh lookback epochs for this forward
     __syncthreads();
+    // A decoded log-scale component is a sum over stages of one codeword
+    // entry each, so it is at most the sum of each stage's largest entry:
+    // with that scale bound, a Gaussian whose 3-sigma box cannot reach any
+    // tile of any view is culled before its attributes are decoded.  The box
+    // bound uses |J|_F >= |J|_2, a 1% and 2-pixel margin covers FP32
+    // rounding, so no Gaussian the full test keeps is lost.
+    const bool ls_bound = S.L[0] > 0 && S.L[0] <= LS_STAGES;
+    if (ls_bound) {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, per = S.K[0] * 3;
+        for (int st = 0; st < S.L[0]; ++st) {
+            float mx = -INFINITY;
+            for (int i = threadIdx.x; i < per; i += blockDim.x) mx = fmaxf(mx, s_cb[cb_off[0] + st * per + i]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) s_lsw[w][st] = mx;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float tot = 0.f;
+            for (int st = 0; st < S.L[0]; ++st) {
+                float mx = -INFINITY;
+                for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) mx = fmaxf(mx, s_lsw[ww][st]);
+                tot += mx;
+            }
+            s_lsb = tot;
+        }
+        __syncthreads();
+    }
 
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = n < S.N;
@@ -55,6 +86,30 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(SceneDev S, const __
             in_front = pc[2] > V.v[v].near_plane;
         }
         active = active && in_front;
+        if (active && ls_bound) {
+            const float smax = expf(s_lsb) * 1.001f;
+            bool reach = false;
+            for (int v = 0; v < V.n && !reach; ++v) {
+                const ViewInfo& vi = V.v[v];
+                float T[12], pc[3];
+                view_pose(V, v, T);
+                cam_point(T, mu, pc);
+                if (!(pc[2] > vi.near_plane)) continue;
+                const float iz = 1.f / pc[2];
+                float tx = pc[0] * iz, ty = pc[1] * iz;
+                const float u = vi.fx * tx + vi.cx, vv = vi.fy * ty + vi.cy;
+                if (cs.jacobian_clamp) {
+                    tx = fminf(fmaxf(tx, -vi.limx), vi.limx);
+                    ty = fminf(fmaxf(ty, -vi.limy), vi.limy);
+                }
+                const float fz = vi.fx * iz, gz = vi.fy * iz;
+                const float jf2 = fz * fz * (1.f + tx * tx) + gz * gz * (1.f + ty * ty);
+                const float r = cs.sigma_cull * sqrtf(jf2 * smax * smax + cs.dilation) * 1.01f + 2.f;
+                reach = u + r >= 0.f && u - r < (float)(vi.tiles_x * TILE) && vv + r >= 0.f &&
+                        vv - r < (float)(vi.tiles_y * TILE);
+            }
+            active = reach;
+        }
     }
     if (live && active) {
         decode_attr_smem<3>(S, 0, n, s_cb + cb_off[0], ls);
