@@ -358,7 +358,8 @@ vg_status vg_ctx_create(int64_t pair_capacity, vg_ctx** out) {
     vg_ctx* c = new vg_ctx();
     vg_status s = c->state.ensure(ST_WORDS * 4, nullptr, "state");
     if (s == VG_OK) s = c->scratch.ensure(SCR_WORDS * 4 + 4096 * 4, nullptr, "scratch");
-    if (s == VG_OK) s = c->loss_scratch.ensure(16, nullptr, "loss");
+    if (s == VG_OK) s = c->loss_scratch.ensure(32, nullptr, "loss");
+    if (s == VG_OK && cudaMemset(c->loss_scratch.p, 0, 32) != cudaSuccess) s = fail(VG_ERR_CUDA, "cudaMemset");
     if (s != VG_OK) {
         delete c;
         return s;
@@ -841,11 +842,10 @@ vg_status vg_loss_l1_masked(int32_t n_views, int64_t n_pix, const float* C, cons
     cudaStream_t st = (cudaStream_t)stream;
     const bool prof_graph = capturing(st);
     const bool prof_on = ctx->prof.on;
-    VG_CUDA(cudaMemsetAsync(ctx->loss_scratch.p, 0, 16, st));
-    VG_CUDA(cudaMemsetAsync(loss, 0, 4, st));
     if (dS) VG_CUDA(cudaMemsetAsync(dS, 0, (size_t)n_views * n_pix * 4, st));
+    // words 4..6 of the loss scratch: kept zero between calls by the kernels
     VG_STAGE(VG_STAGE_LOSS, launch_loss_l1(n_views, n_pix, C, D, S, Ct, Dt, pixel_mask, w_depth, gate, dC, dD, loss,
-                                           ctx->loss_scratch.as<uint32_t>(), st));
+                                           ctx->loss_scratch.as<uint32_t>() + 4, st));
     return VG_OK;
 }
 

@@ -436,9 +436,11 @@ cudaError_t launch_pose_final(int n_views, const float* pose_sum, const float* i
 // ---------------------------------------------------------------------------
 // L1 colour + weighted L1 depth (valid where the target depth > 0)
 // ---------------------------------------------------------------------------
-// count[0] += sampled pixels with Dt > 0; with a mask also count[1] += sampled pixels
+// count[0] += sampled pixels with Dt > 0; with a mask also count[1] += sampled
+// pixels; zeroes the loss value the loss kernel then accumulates into
 __global__ void count_valid_kernel(const float* __restrict__ Dt, const uint8_t* __restrict__ mask, int64_t n,
-                                   uint32_t* count) {
+                                   uint32_t* count, float* loss) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *loss = 0.f;
     uint32_t c = 0, ns = 0;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthr = (int64_t)gridDim.x * blockDim.x;
     const bool vec = (reinterpret_cast<uintptr_t>(Dt) & 15u) == 0 && (reinterpret_cast<uintptr_t>(mask) & 3u) == 0;
@@ -485,7 +487,7 @@ __device__ __forceinline__ float loss_pixel(float c0, float c1, float c2, float 
 __global__ void loss_l1_kernel(int64_t n_pix, int64_t total, const float* __restrict__ C, const float* __restrict__ D,
                                const float* __restrict__ S, const float* __restrict__ Ct, const float* __restrict__ Dt,
                                const uint8_t* __restrict__ mask, float w_depth, float gate,
-                               const uint32_t* __restrict__ valid_count, float* __restrict__ dC,
+                               uint32_t* valid_count, float* __restrict__ dC,
                                float* __restrict__ dD, float* __restrict__ loss, int vec) {
     __shared__ float s_tmp[8];
     const float nv = (float)valid_count[0];
@@ -544,7 +546,17 @@ __global__ void loss_l1_kernel(int64_t n_pix, int64_t total, const float* __rest
         gdp[i] = gd;
     }
     const float t = block_sum_256(acc, s_tmp);
-    if (threadIdx.x == 0) atomicAdd(loss, t);
+    if (threadIdx.x == 0) {
+        atomicAdd(loss, t);
+        // the last block to finish clears the counters for the next call
+        // (every block has read them by then), so no memset precedes a call
+        __threadfence();
+        if (atomicAdd(valid_count + 2, 1u) == gridDim.x * gridDim.y - 1) {
+            valid_count[0] = 0u;
+            valid_count[1] = 0u;
+            valid_count[2] = 0u;
+        }
+    }
 }
 
 cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const float* D, const float* S, const float* Ct,
@@ -554,7 +566,7 @@ cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const flo
     int64_t blocks = ceil_div(ceil_div(total > 0 ? total : 1, 4), 256);
     if (blocks > 148 * 8) blocks = 148 * 8;
     count_launches(2);
-    count_valid_kernel<<<(unsigned)blocks, 256, 0, st>>>(Dt, mask, total, valid_count);
+    count_valid_kernel<<<(unsigned)blocks, 256, 0, st>>>(Dt, mask, total, valid_count, loss);
     auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
     const int vec = (n_pix % 4 == 0) && al(C) && al(D) && al(Ct) && al(Dt) && al(dC) && al(dD) &&
                     (gate < 0.f || al(S)) && (reinterpret_cast<uintptr_t>(mask) & 3u) == 0;
