@@ -294,7 +294,7 @@ int chain_blocks(int64_t) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 148;
     }
-    return 2 * sms;
+    return sms;
 }
 
 // before the backward: zero the gradient rows of the visible slots (the only
