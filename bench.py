@@ -75,6 +75,19 @@ def env_dist():
     return rank, world, local
 
 
+def job_rate(per_rank_ms: float, units_per_rank: int, world: int, dist=None, device="cpu"):
+    """Whole-job rate of N replicas: the units all ranks processed over the
+    slowest rank's time (max over ranks).  Returns (rate per second, the
+    max-over-ranks milliseconds)."""
+    t = float(per_rank_ms)
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return world * units_per_rank / (t / 1000.0), t
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -831,10 +844,7 @@ def run_ours(args):
     total_ms = sum(step_ms)
     status = V.vg_check(w["ctx"])
     clocks = sampler.stop()
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value, total_ms = job_rate(total_ms, args.steps, world, dist if dist else None, device="cuda")
     if status != V.VG_OK:
         raise RuntimeError(f"device status {V.STATUS_NAMES[status]} in the timed region: run invalid")
 
@@ -861,7 +871,6 @@ def run_ours(args):
     if V.vg_check(w["ctx"]) != V.VG_OK:
         raise RuntimeError("device status not OK in the profiled steps")
 
-    value = world * args.steps / (total_ms / 1000.0)
     mpix = value * W_IMG * H_IMG / 1e6
 
     # roofline of the dominant stage, timed with events on the launching stream
