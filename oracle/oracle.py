@@ -116,6 +116,25 @@ def mask_threshold(eps: float) -> float:
     return float(np.float32(math.log(eps / (1.0 - eps))))
 
 
+def rvq_decode_fp32(codebook: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """Eq. 14, first line, summed in FP32 in stage order (the kernels' order)."""
+    cb = np.asarray(codebook, np.float32)
+    ix = np.asarray(idx)
+    acc = np.zeros((ix.shape[1], cb.shape[2]), np.float32)
+    for s in range(cb.shape[0]):
+        acc = acc + cb[s][ix[s].astype(np.int64)]
+    return acc
+
+
+def rvq_scatter(grad: np.ndarray, idx: np.ndarray, shape) -> np.ndarray:
+    """Gradient of a decoded array [n][d] with respect to its codebook
+    [L][K][d]: codeword k of stage s collects the rows whose index is k."""
+    out = np.zeros(shape)
+    for s in range(shape[0]):
+        np.add.at(out[s], np.asarray(idx[s], np.int64), grad)
+    return out
+
+
 def rvq_decode(codebook: np.ndarray, idx: np.ndarray) -> np.ndarray:
     """Eq. 14 (first line): sum over stages of the indexed codewords, FP64."""
     cb = np.ascontiguousarray(codebook, np.float64)
@@ -147,9 +166,17 @@ class Oracle:
         sc = _Scene()
         sc.n_anchors = scene.n_anchors
         sc.k = scene.k
+        # R-VQ coded offsets / scaling factors (Eq. 14) enter as their decoded
+        # values; the decode is FP32 in stage order because the means decide
+        # the binning in FP32
+        self.off_rvq = getattr(scene, "offsets_rvq", None)
+        self.l_rvq = getattr(scene, "l_rvq", None)
+        off_src = scene.offsets if self.off_rvq is None else \
+            rvq_decode_fp32(self.off_rvq.codebook, self.off_rvq.idx).reshape(scene.n_anchors, scene.k, 3)
+        l_src = scene.anchor_l if self.l_rvq is None else rvq_decode_fp32(self.l_rvq.codebook, self.l_rvq.idx)
         self.anchor_xyz = f64("anchor_xyz", scene.anchor_xyz)
-        self.anchor_l = f64("anchor_l", scene.anchor_l)
-        self.offsets = f64("offsets", scene.offsets)
+        self.anchor_l = f64("anchor_l", l_src)
+        self.offsets = f64("offsets", off_src)
         sc.anchor_xyz, sc.anchor_l, sc.offsets = _p(self.anchor_xyz), _p(self.anchor_l), _p(self.offsets)
         self.coded = []
         for gi, name in enumerate(GROUPS):
@@ -284,6 +311,12 @@ class Oracle:
         out = dict(g2d=g2d, anchor_xyz=dxyz, anchor_l=dl, offsets=doff, mask_logit=dm, pose=dpose)
         for gi, name in enumerate(GROUPS):
             out[name] = dattr[gi]
+        # coded offsets / scaling factors: the indexed codeword of every stage
+        # receives the gradient of its value (Eq. 14 is a sum over stages)
+        for key, g, raw in (("offsets", self.off_rvq, doff), ("anchor_l", self.l_rvq, dl)):
+            if g is not None:
+                out[key + "_raw"] = raw
+                out[key] = rvq_scatter(raw.reshape(-1, 3), np.asarray(g.idx), g.codebook.shape)
         return out
 
     def icp(self, q, w):

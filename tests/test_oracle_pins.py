@@ -1093,3 +1093,68 @@ def test_oracle_pixel_mask_composites_only_the_sampled_rays():
         if k in gm and gm[k] is not None:
             assert np.allclose(gm[k], gf[k], rtol=1e-12, atol=1e-15), k
     assert np.allclose(gm["pose"], gf["pose"], rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# R-VQ coded offsets and scaling factors (the paper's R-VQ targets, Eq. 14)
+# ---------------------------------------------------------------------------
+
+def _coded_geometry_fd_scene(seed):
+    sc = fd_scene(False, seed=seed)
+    rng = np.random.default_rng(seed + 100)
+    L, K = 2, 3
+    ocb = rng.normal(0, 0.04, (L, K, 3)).astype(np.float32)
+    lcb = rng.normal(0, 0.1, (L, K, 3)).astype(np.float32)
+    lcb[0] += 1.0
+    og = synth.Group(3, codebook=ocb, idx=rng.integers(0, K, (L, sc.n), dtype=np.uint8))
+    lg = synth.Group(3, codebook=lcb, idx=rng.integers(0, K, (L, sc.n_anchors), dtype=np.uint8))
+    import dataclasses
+    return dataclasses.replace(sc, offsets=None, anchor_l=None, offsets_rvq=og, l_rvq=lg, k_coded=sc.k)
+
+
+def test_coded_geometry_decodes_in_fp32_stage_order_and_renders_as_decoded():
+    """A coded scene renders exactly like the raw scene holding the FP32
+    stage-order sums of its codewords (numpy float32 adds)."""
+    import dataclasses
+    sc = _coded_geometry_fd_scene(50)
+    og, lg = sc.offsets_rvq, sc.l_rvq
+    off = np.zeros((sc.n, 3), np.float32)
+    l = np.zeros((sc.n_anchors, 3), np.float32)
+    for s in range(2):
+        off = off + og.codebook[s][og.idx[s].astype(int)]
+        l = l + lg.codebook[s][lg.idx[s].astype(int)]
+    raw = dataclasses.replace(sc, offsets=off.reshape(sc.n_anchors, sc.k, 3), anchor_l=l, offsets_rvq=None,
+                              l_rvq=None, k_coded=0)
+    cams = fd_cams(1)
+    a, b = O.Oracle(sc, cams).forward(), O.Oracle(raw, cams).forward()
+    for key in ("C", "D", "S"):
+        assert np.array_equal(a[key], b[key])
+
+
+def test_fd_coded_offset_and_scale_codebooks():
+    """Central differences of the objective in every codeword entry of the
+    offset and scaling-factor codebooks (decoded in FP64 around the point)
+    against the scattered analytic gradients."""
+    sc = _coded_geometry_fd_scene(51)
+    cams = fd_cams(1)
+    o = O.Oracle(sc, cams)
+    f = o.forward()
+    assert f["S"].max() > 0.5 and not np.any(f["flags"])
+    ups = [u.astype(np.float64) for u in synth.upstream_grads(99, o.n_pixels, scale=o.n_pixels)]
+    grads = o.backward(*ups)
+    for key, g, shape in (("offsets", sc.offsets_rvq, (sc.n_anchors, sc.k, 3)), ("anchor_l", sc.l_rvq,
+                                                                                  (sc.n_anchors, 3))):
+        cb = np.asarray(g.codebook, np.float64)
+        ix = np.asarray(g.idx, np.int64)
+        fd = np.zeros(cb.size)
+        for j in range(cb.size):
+            vals = []
+            for sgn in (1.0, -1.0):
+                c2 = cb.copy()
+                c2.flat[j] += sgn * 1e-6
+                dec = sum(c2[s][ix[s]] for s in range(cb.shape[0])).reshape(shape)
+                vals.append(_objective(sc, cams, ups, {key: dec}))
+            fd[j] = (vals[0] - vals[1]) / 2e-6
+        an = grads[key].ravel()
+        assert an.shape == fd.shape
+        assert np.abs(fd - an).max() <= 2e-5 * max(1e-6, np.abs(fd).max()), (key, fd, an)
