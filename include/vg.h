@@ -109,6 +109,16 @@ typedef struct {
     vg_attr_group logscale, rot, opacity, rgb;
     const float* mask_logit; /* [N] or NULL */
     float mask_eps;
+    /* R-VQ coded offsets and scaling factors (Sec. "Residual Codebook
+     * Quantization", Eq. 14: the offset O and scaling factor l are what the
+     * paper's R-VQ compresses).  With offsets_rvq.stages > 0, O_n (n = a*k + i)
+     * is the sum over stages of offsets_rvq.codebook[s][idx[s][n]] (dim 3,
+     * idx [L][N]) and `offsets` is not read; with l_rvq.stages > 0, l_a is the
+     * sum of l_rvq.codebook[s][idx[s][a]] (dim 3, idx [L][Na], one code per
+     * anchor) and `anchor_l` is not read.  Sums are FP32 in stage order.
+     * stages = 0 (a zeroed struct) keeps the raw arrays. */
+    vg_attr_group offsets_rvq;
+    vg_attr_group l_rvq;
 } vg_scene_desc;
 
 /* Per-pixel compositing constants (readings of Eq. 16-18; the paper leaves
@@ -167,7 +177,8 @@ typedef struct {
 
 /* Gradient outputs of vg_render_bwd (DEVICE pointers, caller-allocated; each
  * may be NULL to skip it; every non-NULL array is fully overwritten):
- *   anchor_xyz [Na][3], anchor_l [Na][3], offsets [Na][k][3];
+ *   anchor_xyz [Na][3], anchor_l [Na][3], offsets [Na][k][3] -- or, for
+ *   R-VQ coded offsets / scaling factors, their [L][K][3] codebook gradients;
  *   per attribute group: [L][K][dim] codebook gradient for a coded group,
  *   [N][dim] for a raw group; mask_logit [N] (straight-through estimator of
  *   Eq. 11: dL/dm = (sum_j dL/ds_j s_j + dL/do o) sigmoid'(m) for kept

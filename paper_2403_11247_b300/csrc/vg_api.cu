@@ -251,8 +251,16 @@ vg_status vg_scene_upload(const vg_scene_desc* d, int32_t flags, vg_stream strea
     if (d->n_anchors < 0 || d->k < 1) return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: n_anchors < 0 or k < 1");
     const int64_t N = d->n_anchors * (int64_t)d->k;
     if (N >= (int64_t)1 << 30) return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: more than 2^30 Gaussians");
-    if (d->n_anchors > 0 && (!d->anchor_xyz || !d->anchor_l || !d->offsets))
+    const bool off_coded = d->offsets_rvq.stages > 0, l_coded = d->l_rvq.stages > 0;
+    if (d->n_anchors > 0 && (!d->anchor_xyz || (!d->anchor_l && !l_coded) || (!d->offsets && !off_coded)))
         return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: null anchor array");
+    for (const vg_attr_group* g : {&d->offsets_rvq, &d->l_rvq}) {
+        if (g->stages < 0) return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: R-VQ stages < 0");
+        if (g->stages > 0 && (g->dim != 3 || g->codewords < 1 || g->codewords > VG_MAX_CODEWORDS || !g->codebook ||
+                              (N > 0 && !g->idx)))
+            return fail(VG_ERR_INVALID_ARG, "vg_scene_upload: coded offsets / scaling factors need dim 3, "
+                                            "1..256 codewords, a codebook and indices");
+    }
     const vg_attr_group* gr[4] = {&d->logscale, &d->rot, &d->opacity, &d->rgb};
     for (int gi = 0; gi < 4; ++gi) VG_TRY(check_group(*gr[gi], gi, N));
     if (d->mask_logit && !(d->mask_eps > 0.f && d->mask_eps < 1.f))
@@ -284,9 +292,22 @@ vg_status vg_scene_upload(const vg_scene_desc* d, int32_t flags, vg_stream strea
         for (const void* p : ptrs)
             if (p && !is_device_ptr(p)) return fin(fail(VG_ERR_INVALID_ARG, "VG_SCENE_BORROW needs device pointers"));
         S.xyz = d->anchor_xyz;
-        S.l = d->anchor_l;
-        S.off = d->offsets;
+        S.l = l_coded ? nullptr : d->anchor_l;
+        S.off = off_coded ? nullptr : d->offsets;
         S.mask = d->mask_logit;
+        S.Lo = d->offsets_rvq.stages;
+        S.Ko = off_coded ? d->offsets_rvq.codewords : 0;
+        S.cbo = off_coded ? d->offsets_rvq.codebook : nullptr;
+        S.idxo = off_coded ? d->offsets_rvq.idx : nullptr;
+        S.Ll = d->l_rvq.stages;
+        S.Kl = l_coded ? d->l_rvq.codewords : 0;
+        S.cbl = l_coded ? d->l_rvq.codebook : nullptr;
+        S.idxl = l_coded ? d->l_rvq.idx : nullptr;
+        {
+            const void* cp[] = {S.l, S.off, S.cbo, S.idxo, S.cbl, S.idxl};
+            for (const void* p : cp)
+                if (p && !is_device_ptr(p)) return fin(fail(VG_ERR_INVALID_ARG, "VG_SCENE_BORROW needs device pointers"));
+        }
         for (int gi = 0; gi < 4; ++gi) {
             const vg_attr_group& g = *gr[gi];
             S.L[gi] = g.stages;
@@ -316,8 +337,20 @@ vg_status vg_scene_upload(const vg_scene_desc* d, int32_t flags, vg_stream strea
         };
         const size_t Na = (size_t)d->n_anchors;
         VG_TRY(fin(copy(d->anchor_xyz, Na * 3 * 4, (const void**)&S.xyz)));
-        VG_TRY(fin(copy(d->anchor_l, Na * 3 * 4, (const void**)&S.l)));
-        VG_TRY(fin(copy(d->offsets, (size_t)N * 3 * 4, (const void**)&S.off)));
+        if (!l_coded) VG_TRY(fin(copy(d->anchor_l, Na * 3 * 4, (const void**)&S.l)));
+        if (!off_coded) VG_TRY(fin(copy(d->offsets, (size_t)N * 3 * 4, (const void**)&S.off)));
+        S.Lo = d->offsets_rvq.stages;
+        S.Ll = d->l_rvq.stages;
+        if (off_coded) {
+            S.Ko = d->offsets_rvq.codewords;
+            VG_TRY(fin(copy(d->offsets_rvq.codebook, (size_t)S.Lo * S.Ko * 12, (const void**)&S.cbo)));
+            VG_TRY(fin(copy(d->offsets_rvq.idx, (size_t)S.Lo * N, (const void**)&S.idxo)));
+        }
+        if (l_coded) {
+            S.Kl = d->l_rvq.codewords;
+            VG_TRY(fin(copy(d->l_rvq.codebook, (size_t)S.Ll * S.Kl * 12, (const void**)&S.cbl)));
+            VG_TRY(fin(copy(d->l_rvq.idx, (size_t)S.Ll * Na, (const void**)&S.idxl)));
+        }
         VG_TRY(fin(copy(d->mask_logit, (size_t)N * 4, (const void**)&S.mask)));
         for (int gi = 0; gi < 4; ++gi) {
             const vg_attr_group& g = *gr[gi];
@@ -765,8 +798,9 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     O.pose_sum = ctx->pose_part.as<float>();
     zero(O.pose_sum, (int64_t)n_views * 6);
     zero(grads->anchor_xyz, sd.n_anchors * 3);
-    zero(grads->anchor_l, sd.n_anchors * 3);
-    zero(grads->offsets, N * 3);
+    // coded scaling factors / offsets receive [L][K][3] codebook gradients
+    zero(grads->anchor_l, sd.Ll > 0 ? (int64_t)sd.Ll * sd.Kl * 3 : sd.n_anchors * 3);
+    zero(grads->offsets, sd.Lo > 0 ? (int64_t)sd.Lo * sd.Ko * 3 : N * 3);
     zero(grads->mask_logit, N);
 
     const bool prof_graph = capturing(st);

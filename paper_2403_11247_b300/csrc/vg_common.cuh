@@ -78,6 +78,12 @@ struct SceneDev {
     const float* raw[4];
     const float* mask;
     float mask_thr;
+    // R-VQ coded offsets (idx [Lo][N]) and scaling factors (idx [Ll][Na]); L = 0: raw arrays
+    int32_t Lo, Ko, Ll, Kl;
+    const float* cbo;
+    const float* cbl;
+    const uint8_t* idxo;
+    const uint8_t* idxl;
 };
 
 // attribute group dims and their offsets in the packed 11-float attribute
@@ -175,16 +181,45 @@ __device__ __forceinline__ void decode_attr_smem(const SceneDev& S, int g, int64
     }
 }
 
+// offset O_n and scaling factor l_a: raw, or the FP32 stage-order sum of
+// their R-VQ codewords (Eq. 14)
+__device__ __forceinline__ void scene_offset(const SceneDev& S, int64_t n, float o[3]) {
+    if (S.Lo > 0) {
+        o[0] = o[1] = o[2] = 0.f;
+        for (int s = 0; s < S.Lo; ++s) {
+            const float* w = S.cbo + ((int64_t)s * S.Ko + __ldg(S.idxo + (int64_t)s * S.N + n)) * 3;
+            o[0] += __ldg(w);
+            o[1] += __ldg(w + 1);
+            o[2] += __ldg(w + 2);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[c] = __ldg(S.off + n * 3 + c);
+    }
+}
+__device__ __forceinline__ void scene_scale(const SceneDev& S, int64_t a, float l[3]) {
+    if (S.Ll > 0) {
+        l[0] = l[1] = l[2] = 0.f;
+        for (int s = 0; s < S.Ll; ++s) {
+            const float* w = S.cbl + ((int64_t)s * S.Kl + __ldg(S.idxl + (int64_t)s * S.n_anchors + a)) * 3;
+            l[0] += __ldg(w);
+            l[1] += __ldg(w + 1);
+            l[2] += __ldg(w + 2);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) l[c] = __ldg(S.l + a * 3 + c);
+    }
+}
+
 // Eq. 7 with the binning rounding: mu_c = xa_c + (O_c * l_c), no FMA
 __device__ __forceinline__ void anchor_mean(const SceneDev& S, int64_t n, float mu[3]) {
-    int64_t a = n / S.k;
+    const int64_t a = n / S.k;
+    float o[3], l[3];
+    scene_offset(S, n, o);
+    scene_scale(S, a, l);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float xa = __ldg(S.xyz + a * 3 + c);
-        float o = __ldg(S.off + n * 3 + c);
-        float l = __ldg(S.l + a * 3 + c);
-        mu[c] = __fadd_rn(xa, __fmul_rn(o, l));
-    }
+    for (int c = 0; c < 3; ++c) mu[c] = __fadd_rn(__ldg(S.xyz + a * 3 + c), __fmul_rn(o[c], l[c]));
 }
 
 // camera-space point with the binning rounding: ((W0 m0 + W1 m1) + W2 m2) + t

@@ -22,6 +22,17 @@ __device__ __forceinline__ float block_sum_256(float x, float* s_tmp /*[8]*/) {
     return t;  // valid in thread 0
 }
 
+// codebook accumulators of the chain kernel: group gi's size (0 = none) and
+// its global gradient array
+__host__ __device__ inline int chain_cb_size(const SceneDev& S, const ChainOut& O, int gi) {
+    if (gi < 4) return (S.L[gi] > 0 && O.cb[gi]) ? S.L[gi] * S.K[gi] * gdim(gi) : 0;
+    if (gi == 4) return (S.Lo > 0 && O.d_off) ? S.Lo * S.Ko * 3 : 0;
+    return (S.Ll > 0 && O.d_l) ? S.Ll * S.Kl * 3 : 0;
+}
+__host__ __device__ inline float* chain_cb_dst(const ChainOut& O, int gi) {
+    return gi < 4 ? O.cb[gi] : (gi == 4 ? O.d_off : O.d_l);
+}
+
 // One thread per visible (view, Gaussian) slot: the slot's 2D gradient row
 // (from the backward compositing) through the projection (Eq. 3), the
 // covariance (Eq. 2), the activations, the anchor decode (Eq. 7), the
@@ -243,13 +254,36 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                 const float sm = 1.f / (1.f + expf(-__ldg(S.mask + n)));
                 atomicAdd(O.d_mask + n, (ds[0] * s[0] + ds[1] * s[1] + ds[2] * s[2] + dop * o) * sm * (1.f - sm));
             }
-            // Eq. 7: d x_a = sum_i dmu_i, d O_i = dmu_i * l, d l = sum_i dmu_i * O_i
+            // Eq. 7: d x_a = sum_i dmu_i, d O_i = dmu_i * l, d l = sum_i dmu_i * O_i;
+            // coded O or l pass their gradient to the indexed codeword of every stage
             const int64_t a = n / S.k;
+            float oo[3], la[3];
+            scene_offset(S, n, oo);
+            scene_scale(S, a, la);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (O.d_off) atomicAdd(O.d_off + n * 3 + c, dmu[c] * __ldg(S.l + a * 3 + c));
+            for (int c = 0; c < 3; ++c)
                 if (O.d_xyz) atomicAdd(O.d_xyz + a * 3 + c, dmu[c]);
-                if (O.d_l) atomicAdd(O.d_l + a * 3 + c, dmu[c] * __ldg(S.off + n * 3 + c));
+            if (O.d_off) {
+                if (S.Lo > 0) {
+                    for (int st = 0; st < S.Lo; ++st) {
+                        const int j = (st * S.Ko + __ldg(S.idxo + (int64_t)st * S.N + n)) * 3;
+                        float* dst = O.cb_in_smem ? s_cb + O.cb_off[4] + j : O.d_off + j;
+                        for (int c = 0; c < 3; ++c) atomicAdd(dst + c, dmu[c] * la[c]);
+                    }
+                } else {
+                    for (int c = 0; c < 3; ++c) atomicAdd(O.d_off + n * 3 + c, dmu[c] * la[c]);
+                }
+            }
+            if (O.d_l) {
+                if (S.Ll > 0) {
+                    for (int st = 0; st < S.Ll; ++st) {
+                        const int j = (st * S.Kl + __ldg(S.idxl + (int64_t)st * S.n_anchors + a)) * 3;
+                        float* dst = O.cb_in_smem ? s_cb + O.cb_off[5] + j : O.d_l + j;
+                        for (int c = 0; c < 3; ++c) atomicAdd(dst + c, dmu[c] * oo[c]);
+                    }
+                } else {
+                    for (int c = 0; c < 3; ++c) atomicAdd(O.d_l + a * 3 + c, dmu[c] * oo[c]);
+                }
             }
         } while (0);
         // pose sums: one butterfly per warp when its lanes share a view (the
@@ -275,12 +309,12 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
     for (int i = threadIdx.x; i < V.n * 6; i += blockDim.x)
         if (s_pose[i] != 0.f) atomicAdd(O.pose_sum + i, s_pose[i]);
     if (O.cb_in_smem) {
-        for (int gi = 0; gi < 4; ++gi) {
-            if (S.L[gi] <= 0 || !O.cb[gi]) continue;
-            const int sz = S.L[gi] * S.K[gi] * gdim(gi);
+        for (int gi = 0; gi < 6; ++gi) {
+            const int sz = chain_cb_size(S, O, gi);
+            float* dst = chain_cb_dst(O, gi);
             for (int j = threadIdx.x; j < sz; j += blockDim.x) {
                 const float t = s_cb[O.cb_off[gi] + j];
-                if (t != 0.f) atomicAdd(O.cb[gi] + j, t);
+                if (t != 0.f) atomicAdd(dst + j, t);
             }
         }
     }
@@ -331,9 +365,9 @@ cudaError_t launch_zero_bwd(const uint32_t* vis_slots, const uint32_t* nvis_dev,
 
 size_t chain_smem(const SceneDev& S, const Views& V, ChainOut* O) {
     int off = 0;
-    for (int gi = 0; gi < 4; ++gi) {
+    for (int gi = 0; gi < 6; ++gi) {
         O->cb_off[gi] = off;
-        if (S.L[gi] > 0 && O->cb[gi]) off += S.L[gi] * S.K[gi] * gdim(gi);
+        off += chain_cb_size(S, *O, gi);
     }
     O->cb_total = off;
     const size_t pose_bytes = (size_t)V.n * 6 * sizeof(float);

@@ -126,7 +126,9 @@ struct ChainOut {
     float* cb[4];    // codebook gradients of coded groups [L][K][d]
     float *d_xyz, *d_l, *d_off, *d_mask;
     float* pose_sum;   // [views][6], zeroed before the backward
-    int32_t cb_off[4], cb_total, cb_in_smem;
+    // shared-memory accumulator offsets: the four attribute codebooks, then the
+    // R-VQ offset codebook (4) and scaling-factor codebook (5) when coded
+    int32_t cb_off[6], cb_total, cb_in_smem;
 };
 // arrays the zeroing kernel clears before the backward
 struct ZeroList {

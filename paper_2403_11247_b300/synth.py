@@ -48,6 +48,11 @@ class Scene:
     groups: Dict[str, Group]
     mask_logit: Optional[np.ndarray] = None   # [N] f32
     mask_eps: float = 0.5
+    # R-VQ coded offsets (idx [L][N]) and scaling factors (idx [L][Na]); when
+    # set, `offsets` / `anchor_l` are None and only the codes describe them
+    offsets_rvq: Optional[Group] = None
+    l_rvq: Optional[Group] = None
+    k_coded: int = 0                          # k when the offsets are coded
 
     @property
     def n_anchors(self) -> int:
@@ -55,7 +60,7 @@ class Scene:
 
     @property
     def k(self) -> int:
-        return int(self.offsets.shape[1])
+        return int(self.offsets.shape[1]) if self.offsets is not None else int(self.k_coded)
 
     @property
     def n(self) -> int:
@@ -175,6 +180,27 @@ def coded_groups(rng: np.random.Generator, n: int, L: int, K: int,
     for g in groups.values():
         g.idx = rng.integers(0, K, size=(L, n), dtype=np.uint8)
     return groups
+
+
+def code_geometry(scene: Scene, seed: int, L: int = 3, K: int = 64, l_centre: float = 0.05,
+                  offset_std: float = 0.6) -> Scene:
+    """The scene with R-VQ coded offsets and scaling factors in place of the
+    raw ones: seeded codebooks (stage 1 drawn like the raw values -- offsets
+    N(0, offset_std), scaling factors around l_centre -- later stages residual
+    codewords with 1/4^(s-1) of the spread) and uniform 1-byte indices.  The
+    codes are the scene: no decoded copy is kept."""
+    rng = np.random.default_rng(seed)
+    na, k = scene.n_anchors, scene.k
+    ocb = np.zeros((L, K, 3), np.float32)
+    ocb[0] = rng.normal(0.0, offset_std, size=(K, 3))
+    lcb = np.zeros((L, K, 3), np.float32)
+    lcb[0] = rng.uniform(0.8 * l_centre, 1.2 * l_centre, size=(K, 3))
+    for s in range(1, L):
+        ocb[s] = rng.normal(0.0, offset_std / 4.0 ** s, size=(K, 3))
+        lcb[s] = rng.normal(0.0, 0.1 * l_centre / 4.0 ** s, size=(K, 3))
+    og = Group(3, codebook=ocb, idx=rng.integers(0, K, size=(L, na * k), dtype=np.uint8))
+    lg = Group(3, codebook=lcb, idx=rng.integers(0, K, size=(L, na), dtype=np.uint8))
+    return dataclasses.replace(scene, offsets=None, anchor_l=None, offsets_rvq=og, l_rvq=lg, k_coded=k)
 
 
 def mask_logits(rng: np.random.Generator, n: int, frac_masked: float) -> np.ndarray:

@@ -49,7 +49,8 @@ class vg_scene_desc(C.Structure):
     _fields_ = [("n_anchors", C.c_int64), ("k", C.c_int32),
                 ("anchor_xyz", C.c_void_p), ("anchor_l", C.c_void_p), ("offsets", C.c_void_p),
                 ("logscale", vg_attr_group), ("rot", vg_attr_group), ("opacity", vg_attr_group), ("rgb", vg_attr_group),
-                ("mask_logit", C.c_void_p), ("mask_eps", C.c_float)]
+                ("mask_logit", C.c_void_p), ("mask_eps", C.c_float),
+                ("offsets_rvq", vg_attr_group), ("l_rvq", vg_attr_group)]
 
 
 class vg_render_params(C.Structure):
@@ -210,6 +211,7 @@ class SceneHandle:
         self.k = k
         self.coded = coded          # group -> (L, K) for coded groups
         self.masked = masked
+        self.coded_geometry = {}    # "offsets" / "anchor_l" -> (L, K) when R-VQ coded
 
     def free(self):
         if self.handle:
@@ -235,11 +237,17 @@ def vg_scene_upload(scene, flags: int = VG_SCENE_COPY, stream=None) -> SceneHand
             keep.append(ref)
         return p
 
+    off_rvq = getattr(scene, "offsets_rvq", None)
+    l_rvq = getattr(scene, "l_rvq", None)
     desc.n_anchors = int(scene.anchor_xyz.shape[0])
-    desc.k = int(scene.offsets.shape[1])
+    desc.k = int(scene.k) if hasattr(scene, "k") else int(scene.offsets.shape[1])
     desc.anchor_xyz = put(scene.anchor_xyz)
-    desc.anchor_l = put(scene.anchor_l)
-    desc.offsets = put(scene.offsets)
+    desc.anchor_l = put(scene.anchor_l) if l_rvq is None else None
+    desc.offsets = put(scene.offsets) if off_rvq is None else None
+    for grp, g in ((desc.offsets_rvq, off_rvq), (desc.l_rvq, l_rvq)):
+        if g is not None:
+            grp.dim, grp.stages, grp.codewords = 3, int(g.codebook.shape[0]), int(g.codebook.shape[1])
+            grp.codebook, grp.idx, grp.raw = put(g.codebook), put(g.idx), None
     coded = {}
     for name in GROUPS:
         g = scene.groups[name]
@@ -259,8 +267,15 @@ def vg_scene_upload(scene, flags: int = VG_SCENE_COPY, stream=None) -> SceneHand
     h = C.c_void_p()
     _check(lib().vg_scene_upload(C.byref(desc), flags, _stream(stream), C.byref(h)), "vg_scene_upload")
     n = desc.n_anchors * desc.k
-    return SceneHandle(h.value, keep if flags == VG_SCENE_BORROW else None, n, desc.n_anchors, desc.k, coded,
-                       scene.mask_logit is not None)
+    geom = {}
+    if off_rvq is not None:
+        geom["offsets"] = tuple(int(x) for x in off_rvq.codebook.shape[:2])
+    if l_rvq is not None:
+        geom["anchor_l"] = tuple(int(x) for x in l_rvq.codebook.shape[:2])
+    h_ = SceneHandle(h.value, keep if flags == VG_SCENE_BORROW else None, n, desc.n_anchors, desc.k, coded,
+                     scene.mask_logit is not None)
+    h_.coded_geometry = geom
+    return h_
 
 
 class CtxHandle:
@@ -506,6 +521,9 @@ def grads_like(scene: SceneHandle, device=None, mask=True):
     f = dict(dtype=torch.float32, device=dev)
     g = dict(anchor_xyz=torch.empty((scene.n_anchors, 3), **f), anchor_l=torch.empty((scene.n_anchors, 3), **f),
              offsets=torch.empty((scene.n_anchors, scene.k, 3), **f))
+    # R-VQ coded offsets / scaling factors: [L][K][3] codebook gradients
+    for name, (L, K) in getattr(scene, "coded_geometry", {}).items():
+        g[name] = torch.empty((L, K, 3), **f)
     for name in GROUPS:
         if name in scene.coded:
             L, K = scene.coded[name]
