@@ -30,10 +30,16 @@ PARAM_ORDER = ("anchor_xyz", "anchor_l", "offsets", "logscale", "rot", "opacity"
 class SceneParams:
     """Map parameters as CUDA tensors, laid out as the C ABI expects."""
 
-    def __init__(self, anchor_xyz, anchor_l, offsets, groups: Dict[str, dict], mask_logit=None, mask_eps=0.5):
+    def __init__(self, anchor_xyz, anchor_l, offsets, groups: Dict[str, dict], mask_logit=None, mask_eps=0.5,
+                 offsets_rvq: Optional[dict] = None, l_rvq: Optional[dict] = None, k: int = 0):
         self.anchor_xyz = anchor_xyz
         self.anchor_l = anchor_l
         self.offsets = offsets
+        # R-VQ coded offsets / scaling factors: {"codebook": [L,K,3], "idx": [L,n] uint8};
+        # their codebooks are then the parameters in place of `offsets` / `anchor_l`
+        self.offsets_rvq = _Group(**offsets_rvq) if offsets_rvq is not None else None
+        self.l_rvq = _Group(**l_rvq) if l_rvq is not None else None
+        self.k = int(offsets.shape[1]) if offsets is not None else int(k)
         # groups[name] = {"codebook": [L,K,d], "idx": [L,N] uint8} or {"raw": [N,d]}
         self.groups = {k: _Group(**g) for k, g in groups.items()}
         self.mask_logit = mask_logit
@@ -49,14 +55,24 @@ class SceneParams:
                 groups[k] = {"codebook": t(g.codebook), "idx": t(g.idx)}
             else:
                 groups[k] = {"raw": t(g.raw)}
-        out = cls(t(scene.anchor_xyz), t(scene.anchor_l), t(scene.offsets), groups,
-                  None if scene.mask_logit is None else t(scene.mask_logit), scene.mask_eps)
+        geom = {}
+        for name in ("offsets_rvq", "l_rvq"):
+            g = getattr(scene, name, None)
+            if g is not None:
+                geom[name] = {"codebook": t(g.codebook), "idx": t(g.idx)}
+        out = cls(t(scene.anchor_xyz), None if scene.anchor_l is None else t(scene.anchor_l),
+                  None if scene.offsets is None else t(scene.offsets), groups,
+                  None if scene.mask_logit is None else t(scene.mask_logit), scene.mask_eps, k=scene.k, **geom)
         if requires_grad:
             for p in out.parameters():
                 p.requires_grad_(True)
         return out
 
     def tensor(self, name):
+        if name == "offsets" and self.offsets_rvq is not None:
+            return self.offsets_rvq.codebook
+        if name == "anchor_l" and self.l_rvq is not None:
+            return self.l_rvq.codebook
         if name in ("anchor_xyz", "anchor_l", "offsets", "mask_logit"):
             return getattr(self, name)
         g = self.groups[name]

@@ -57,13 +57,22 @@ def append_anchors(scene, new_xyz, new_level, eps_g: float, opacity: float = 0.1
     """A SceneParams holding `scene`'s anchors followed by the grown ones."""
     from .autograd import SceneParams
     M = int(new_xyz.shape[0])
-    k = scene.offsets.shape[1]
+    k = scene.k
     dev = scene.anchor_xyz.device
     eps = (eps_g / torch.pow(4.0, new_level.to(torch.float32) - 1.0)).to(dev)
     cat = lambda a, b: torch.cat([a.detach(), b.to(a.dtype)], 0).contiguous()
     anchor_xyz = cat(scene.anchor_xyz, new_xyz)
-    anchor_l = cat(scene.anchor_l, eps[:, None].expand(M, 3))
-    offsets = cat(scene.offsets, torch.zeros((M, k, 3), device=dev))
+    l_new = eps[:, None].expand(M, 3).contiguous()
+    o_new = torch.zeros((M * k, 3), device=dev)
+    geom = {}
+    # coded scaling factors / offsets: the new values get their residual codes
+    for key, g, val, raw_name in (("l_rvq", scene.l_rvq, l_new, "anchor_l"),
+                                  ("offsets_rvq", scene.offsets_rvq, o_new, "offsets")):
+        if g is not None:
+            idx, _, _ = V.vg_rvq_encode(g.codebook.detach(), val, want_loss=False, want_grad=False)
+            geom[key] = {"codebook": g.codebook.detach().clone(), "idx": torch.cat([g.idx, idx], 1).contiguous()}
+    anchor_l = cat(scene.anchor_l, l_new) if scene.l_rvq is None else None
+    offsets = cat(scene.offsets, o_new.view(M, k, 3)) if scene.offsets_rvq is None else None
     init = {
         "logscale": torch.log(0.5 * eps)[:, None].expand(M, 3).repeat_interleave(k, 0),
         "rot": torch.tensor([1.0, 0.0, 0.0, 0.0], device=dev).expand(M * k, 4),
@@ -81,4 +90,4 @@ def append_anchors(scene, new_xyz, new_level, eps_g: float, opacity: float = 0.1
     mask = None
     if scene.mask_logit is not None:
         mask = cat(scene.mask_logit, torch.full((M * k,), mask_logit, device=dev))
-    return SceneParams(anchor_xyz, anchor_l, offsets, groups, mask, scene.mask_eps)
+    return SceneParams(anchor_xyz, anchor_l, offsets, groups, mask, scene.mask_eps, k=k, **geom)

@@ -73,3 +73,25 @@ def test_coded_geometry_gradients_match_the_oracle(torch):
     V.vg_pose_grad(ctx, 2, dxi=dxi)
     for v in range(2):
         grad_tolerance_check(dxi[v].cpu().numpy(), og["pose"][v], f"coded geometry:pose{v}")
+
+
+def test_autograd_and_growing_on_a_coded_geometry_scene(torch):
+    """The autograd form differentiates the offset and scaling-factor
+    codebooks; grown anchors get residual codes for their initial values."""
+    from paper_2403_11247_b300.autograd import SceneParams, render
+    from paper_2403_11247_b300.grow import append_anchors
+    sc = synth.code_geometry(synth.room_scene(seed=1002, n_anchors=1500), seed=78)
+    scene = SceneParams.from_synth(sc)
+    cams = [synth.room_camera(200, 120, 100.0)]
+    C_, D, S = render(scene, cams)
+    (C_.sum() + D.sum()).backward()
+    og, lg = scene.offsets_rvq.codebook.grad, scene.l_rvq.codebook.grad
+    assert og is not None and lg is not None and og.abs().sum() > 0 and lg.abs().sum() > 0
+    xyz = torch.tensor([[2.0, 3.0, 1.0], [1.0, 3.5, 0.5]], device="cuda")
+    lev = torch.tensor([1, 2], dtype=torch.int32, device="cuda")
+    grown = append_anchors(scene, xyz, lev, 0.2)
+    assert grown.l_rvq.idx.shape[1] == sc.n_anchors + 2
+    assert grown.offsets_rvq.idx.shape[1] == (sc.n_anchors + 2) * sc.k
+    with torch.no_grad():
+        C2, _, _ = render(grown, cams)
+    assert torch.isfinite(C2).all()
