@@ -66,8 +66,7 @@ def append_anchors(scene, new_xyz, new_level, eps_g: float, opacity: float = 0.1
     o_new = torch.zeros((M * k, 3), device=dev)
     geom = {}
     # coded scaling factors / offsets: the new values get their residual codes
-    for key, g, val, raw_name in (("l_rvq", scene.l_rvq, l_new, "anchor_l"),
-                                  ("offsets_rvq", scene.offsets_rvq, o_new, "offsets")):
+    for key, g, val in (("l_rvq", scene.l_rvq, l_new), ("offsets_rvq", scene.offsets_rvq, o_new)):
         if g is not None:
             idx, _, _ = V.vg_rvq_encode(g.codebook.detach(), val, want_loss=False, want_grad=False)
             geom[key] = {"codebook": g.codebook.detach().clone(), "idx": torch.cat([g.idx, idx], 1).contiguous()}
