@@ -109,3 +109,28 @@ def test_prune_removes_masked_and_rarely_hit_gaussians(torch):
     seen2 = torch.zeros(N, dtype=torch.int32, device="cuda")
     V.render_with_retry(sh, cams, V.default_params(seen=seen2), ctx)
     assert not np.any(seen2.cpu().numpy()[want])
+
+
+def test_sliding_window_removes_at_the_bound_and_restarts(torch):
+    """A window of three frames: counts grow inside it, removal happens at
+    the bound with the rule of the oracle on the window's counts, and the
+    next window starts from zero."""
+    from paper_2403_11247_b300.autograd import SceneParams
+    from paper_2403_11247_b300.window import SlidingWindowMask
+    sc, cams = scene_and_cams()
+    scene = SceneParams.from_synth(sc, requires_grad=False)
+    sh = scene.handle()
+    win = SlidingWindowMask(sh, window=3, min_hits=40)
+    ctx = V.vg_ctx_create(0)
+    m0 = scene.mask_logit.cpu().numpy().copy()
+    for f in range(3):
+        V.render_with_retry(sh, [cams[f % 2]], win.params(), ctx)
+        if f < 2:
+            assert win.end_frame() == 0
+    hits, seen = win.hits.cpu().numpy().copy(), win.seen.cpu().numpy().copy()
+    assert hits.sum() > 0
+    n = win.end_frame()
+    ref_m, ref_removed = mask_prune(m0, hits, seen, sc.mask_eps, 40)
+    assert n == int(ref_removed.sum()) > 0
+    assert np.array_equal(np.isneginf(scene.mask_logit.cpu().numpy()), np.isneginf(ref_m))
+    assert int(win.hits.sum()) == 0 and int(win.seen.sum()) == 0 and win.frames == 0
