@@ -234,7 +234,7 @@ vg_status vg_ctx_free(vg_ctx* ctx);
  * results it reads back (the paper has no counterpart): 2 MB aligned,
  * transparent huge pages requested (madvise), zero-filled, then registered
  * with the CUDA driver (cudaHostRegister), so that copies from it run as
- * asynchronous DMA.  Measured on the B300 machines here, 13 MB host->device
+ * asynchronous DMA.  Measured on a B300 system (PCIe Gen6), 13 MB host->device
  * copies from such memory ran at ~55 GB/s, while from cudaHostAlloc'd
  * buffers they ran at 10-40 GB/s depending on the allocation.
  * vg_host_alloc: *out receives the pointer (bytes > 0); VG_ERR_OOM if the
@@ -246,7 +246,7 @@ vg_status vg_host_free(void* ptr);
 /* Host-to-host copy of `bytes` into a staging buffer with streaming
  * (non-temporal) stores on x86-64, a plain copy elsewhere: the written lines
  * do not stay dirty in the CPU caches.  The copy engine's reads of lines a
- * core had just written measured ~15 GB/s on the B300 machines here, against
+ * core had just written measured ~15 GB/s on a B300 system, against
  * ~55 GB/s for lines in memory; stage each frame with this call before
  * vg_memcpy_async.  Synchronous; VG_ERR_INVALID_ARG for a negative size or
  * NULL pointers. */
