@@ -234,9 +234,10 @@ vg_status vg_ctx_free(vg_ctx* ctx);
  * results it reads back (the paper has no counterpart): 2 MB aligned,
  * transparent huge pages requested (madvise), zero-filled, then registered
  * with the CUDA driver (cudaHostRegister), so that copies from it run as
- * asynchronous DMA.  Measured on a B300 system (PCIe Gen6), 13 MB host->device
- * copies from such memory ran at ~55 GB/s, while from cudaHostAlloc'd
- * buffers they ran at 10-40 GB/s depending on the allocation.
+ * asynchronous DMA.  Measured on a B300 system (PCIe Gen6), 13 MB
+ * host->device copies from such memory ran at ~55 GB/s when its lines were
+ * in memory; written by a core just before, they ran at ~15 GB/s (the
+ * copy engine then reads dirty cache lines): fill it with vg_host_stage.
  * vg_host_alloc: *out receives the pointer (bytes > 0); VG_ERR_OOM if the
  * memory cannot be had, VG_ERR_CUDA if registration fails.
  * vg_host_free: unregisters and frees a pointer from vg_host_alloc (NULL is
