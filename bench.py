@@ -366,7 +366,7 @@ def local_ba_leg(torch, V, synth, iters=50):
     return res
 
 
-def tracking_leg(torch, V, synth, scene, n_frames=10, iters=90):
+def tracking_leg(torch, V, synth, scene, n_frames=10, iters=90, with_oracle=True):
     """Camera tracking on the mapping scene at 1200x680: a 10-frame path
     through the room shaken per frame by up to 0.3 deg / 1 cm (so that the
     constant-velocity prediction is off), targets rendered at the true poses (depth normalised by
@@ -425,6 +425,20 @@ def tracking_leg(torch, V, synth, scene, n_frames=10, iters=90):
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
     res["ssim_8x640x480_ms"] = statistics.median(times)
+    # algorithmic FLOPs per colour value (FMA = 2): 11-tap horizontal and
+    # vertical passes of 5 statistics (220) and of 3 coefficient maps (132),
+    # the 3 products (3), SSIM and its coefficients (~40), the gradient (5)
+    n_val = 3 * B * Wk * Hk
+    ssim_tflops = 400.0 * n_val / (res["ssim_8x640x480_ms"] * 1e-3) / 1e12
+    res["ssim_roofline"] = {"bound": "alu", "achieved_tflops": ssim_tflops, "flop_per_value": 400,
+                            "values": n_val}
+    if with_oracle:
+        from oracle.ssim import ssim_loss
+        xs, ys = x.cpu().numpy(), y.cpu().numpy()
+        t0 = time.perf_counter()
+        ssim_loss(xs[:3 * Wk * Hk], ys[:3 * Wk * Hk], 1, Wk, Hk)
+        res["ssim_cpu_baseline"] = {"kind": "oracle", "s_per_call": (time.perf_counter() - t0) * B, "cores": 1,
+                                    "sample": "one of the 8 keyframes, numpy FP64, scaled by 8"}
     log(f"tracking: {res['ms_per_frame']:.2f} ms/frame ({iters} iters), err {res['tracked_err_deg_m']} "
         f"from {res['init_err_deg_m']}; ssim {res['ssim_8x640x480_ms']:.3f} ms")
     return res
@@ -997,7 +1011,7 @@ def run_ours(args):
     if rank == 0:
         rvq = rvq_leg(torch, V, with_oracle=not args.no_cpu_baseline)
     if rank == 0 and not args.no_tracking:
-        track = tracking_leg(torch, V, synth, w["scene"])
+        track = tracking_leg(torch, V, synth, w["scene"], with_oracle=not args.no_cpu_baseline)
         growing = growing_leg(torch, V, synth, w["scene"], with_oracle=not args.no_cpu_baseline)
     if rank == 0 and not args.no_large:
         large = large_leg(torch, V, synth)
