@@ -48,6 +48,10 @@ BWD_FLOP_BLEND = 49       # per blended pair: T recovery, dL/dalpha, colour/dept
 BLEND_SOURCES = ("paper_2403_11247_b300/csrc/vg_blend.cu", "paper_2403_11247_b300/csrc/vg_common.cuh")
 NCU_TRAFFIC = {"blend_bwd": ("711ca20acf22bdfa", 24.430848e6 + 0.0),
                "blend_fwd": ("711ca20acf22bdfa", 3.420416e6 + 4864.0)}
+# warp instructions per launch from the same capture: with the live launch
+# time they give the issue rate against the SMs' issue peak (4 schedulers
+# per SM, one warp instruction per clock each)
+NCU_INSTRUCTIONS = {"blend_bwd": 118.3e6, "blend_fwd": 56.8e6}
 
 
 def ncu_traffic(stage: str):
@@ -917,6 +921,11 @@ def run_ours(args):
     roof["peak_source"] = ("derived: %d SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz (max SM clock, %s peaks file)"
                            % (n_sm, sm_mhz, src)) if roof["bound"] == "alu" else f"{src} hbm_gbs"
     roof["ms_per_launch"] = per_launch_s * 1000.0
+    stage = roof["kernel"].replace("_kernel", "")
+    if stage in NCU_INSTRUCTIONS and ncu_traffic(stage) is not None:
+        # FLOPs undercount what a compositing kernel issues (shuffles, loads,
+        # tests): the issue rate shows how close it runs to the SMs' limit
+        roof["issue_frac"] = (NCU_INSTRUCTIONS[stage] / per_launch_s) / (n_sm * 4 * sm_mhz * 1e6)
 
     # measured throughput of the units the derived peaks assume (probes)
     probes = V.probe_peaks()
