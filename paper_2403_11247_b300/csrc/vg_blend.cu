@@ -468,7 +468,6 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
                     if (p2 > 0.f || q < 0.f) continue;
                     const float x = __fmul_rn(cs.alpha_min, fast_exp2(q));  // o e^power before the cap
                     const float alpha = fminf(cs.alpha_max, x);
-                    const float G = x * nat.w;                               // e^power
                     const float inv = __fdividef(1.f, 1.f - alpha);  // hardware reciprocal, ~2 ulp
                     T[k] *= inv;  // transmittance in front of this Gaussian
                     const float w = gp[k][0] * cd.x + gp[k][1] * cd.y + gp[k][2] * cd.z + gp[k][3] * cd.w + gp[k][4];
@@ -480,17 +479,30 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
                     vals[8] = fmaf(wt, gp[k][2], vals[8]);
                     vals[9] = fmaf(wt, gp[k][3], vals[9]);
                     if (x <= cs.alpha_max) {
+                        // the per-Gaussian factors (e^power = x / o, the signs and
+                        // halves of the conic terms) are applied once per visit below
                         const float dp = alpha * dA;
-                        vals[5] = fmaf(G, dA, vals[5]);
-                        vals[0] -= dp * (nat.x * dx + nat.y * dy);
-                        vals[1] -= dp * (nat.y * dx + nat.z * dy);
-                        vals[2] -= 0.5f * dp * dx * dx;
-                        vals[3] -= dp * dx * dy;
-                        vals[4] -= 0.5f * dp * dy * dy;
+                        const float pdx = dp * dx, pdy = dp * dy;
+                        vals[5] = fmaf(x, dA, vals[5]);
+                        vals[0] = fmaf(nat.x, pdx, fmaf(nat.y, pdy, vals[0]));
+                        vals[1] = fmaf(nat.y, pdx, fmaf(nat.z, pdy, vals[1]));
+                        vals[2] = fmaf(pdx, dx, vals[2]);
+                        vals[3] = fmaf(pdx, dy, vals[3]);
+                        vals[4] = fmaf(pdy, dy, vals[4]);
                     }
                     any = true;
                 }
-                if (__any_sync(0xffffffffu, any)) warp_reduce_add10(vals, g2d + (int64_t)s_slot[i] * G2D_STRIDE);
+                if (__any_sync(0xffffffffu, any)) {
+                    // dL/d(u, v) = -sum dp (conic d); dL/d(a, b, c) = -sum dp (dx^2/2, dx dy, dy^2/2);
+                    // dL/do = sum e^power dA with e^power = x / o
+                    vals[0] = -vals[0];
+                    vals[1] = -vals[1];
+                    vals[2] *= -0.5f;
+                    vals[3] = -vals[3];
+                    vals[4] *= -0.5f;
+                    vals[5] *= nat.w;
+                    warp_reduce_add10(vals, g2d + (int64_t)s_slot[i] * G2D_STRIDE);
+                }
             }
         }
         bend = bstart;
