@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
                 m &= m - 1;
                 const float4 g = s_xy[i];
                 const float4 co = s_co[i];
+                const float4 cd = s_cd[i];
                 uint32_t hb = 0;  // this lane's pixels that blend Gaussian i (hit counts)
                 if (HITS) {
 #pragma unroll
@@ -272,7 +273,6 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
                         stop_at[k] = b - rg.x + i;
                         continue;
                     }
-                    const float4 cd = s_cd[i];
                     const float w = alpha * T[k];
                     acc[k][0] = fmaf(cd.x, w, acc[k][0]);
                     acc[k][1] = fmaf(cd.y, w, acc[k][1]);
