@@ -86,10 +86,11 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
             decode_attr<3>(S, 3, n, rgb);
             const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
             if (!(qq > 0.f)) break;
-            const float qnorm = sqrtf(qq);
+            // one reciprocal per slot for every quotient by |q| and by z below
+            const float iq = 1.f / sqrtf(qq);
             float qn[4], s[3], R[3][3], Sig[3][3];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) qn[c] = q[c] / qnorm;
+            for (int c = 0; c < 4; ++c) qn[c] = q[c] * iq;
 #pragma unroll
             for (int c = 0; c < 3; ++c) s[c] = expf(ls[c]);
             quat_rot(qn, R);
@@ -113,7 +114,8 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                     if (txz < -vi.limx || txz > vi.limx) { ux = false; txz = fminf(fmaxf(txz, -vi.limx), vi.limx); }
                     if (tyz < -vi.limy || tyz > vi.limy) { uy = false; tyz = fminf(fmaxf(tyz, -vi.limy), vi.limy); }
                 }
-                const float J00 = fx / z, J02 = -fx * txz / z, J11 = fy / z, J12 = -fy * tyz / z;
+                const float iz = 1.f / z, iz2 = iz * iz;
+                const float J00 = fx * iz, J02 = -fx * txz * iz, J11 = fy * iz, J12 = -fy * tyz * iz;
                 const float W[3][3] = {{T[0], T[1], T[2]}, {T[4], T[5], T[6]}, {T[8], T[9], T[10]}};
                 float T1[3][3], Sc[3][3];
         #pragma unroll
@@ -155,17 +157,16 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                 const float dJ02 = 2.f * (dA * JS[0][2] + hB * JS[1][2]);
                 const float dJ11 = 2.f * (hB * JS[0][1] + dC * JS[1][1]);
                 const float dJ12 = 2.f * (hB * JS[0][2] + dC * JS[1][2]);
-                const float z2 = z * z, z3 = z2 * z;
-                const float dJ02_dx = ux ? -fx / z2 : 0.f;
-                const float dJ12_dy = uy ? -fy / z2 : 0.f;
-                const float dJ02_dz = fx * txz / z2 + (ux ? fx * x / z3 : 0.f);
-                const float dJ12_dz = fy * tyz / z2 + (uy ? fy * y / z3 : 0.f);
+                const float dJ02_dx = ux ? -fx * iz2 : 0.f;
+                const float dJ12_dy = uy ? -fy * iz2 : 0.f;
+                const float dJ02_dz = fx * txz * iz2 + (ux ? fx * x * iz2 * iz : 0.f);
+                const float dJ12_dz = fy * tyz * iz2 + (uy ? fy * y * iz2 * iz : 0.f);
                 const float du = g[0], dv = g[1], ddepth = g[9];
                 float dp[3];
-                dp[0] = du * fx / z + dJ02 * dJ02_dx;
-                dp[1] = dv * fy / z + dJ12 * dJ12_dy;
-                dp[2] = -du * fx * x / z2 - dv * fy * y / z2 + ddepth - dJ00 * fx / z2 - dJ11 * fy / z2 +
-                        dJ02 * dJ02_dz + dJ12 * dJ12_dz;
+                dp[0] = du * fx * iz + dJ02 * dJ02_dx;
+                dp[1] = dv * fy * iz + dJ12 * dJ12_dy;
+                dp[2] = -(du * fx * x + dv * fy * y + dJ00 * fx + dJ11 * fy) * iz2 + ddepth + dJ02 * dJ02_dz +
+                        dJ12 * dJ12_dz;
         #pragma unroll
                 for (int c = 0; c < 3; ++c) dmu[c] += W[0][c] * dp[0] + W[1][c] * dp[1] + W[2][c] * dp[2];
                 float T2[3][3];
@@ -229,14 +230,17 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                                 y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
                 const float dot = qn[0] * dqn[0] + qn[1] * dqn[1] + qn[2] * dqn[2] + qn[3] * dqn[3];
         #pragma unroll
-                for (int c = 0; c < 4; ++c) dq[c] = (dqn[c] - qn[c] * dot) / qnorm;
+                for (int c = 0; c < 4; ++c) dq[c] = (dqn[c] - qn[c] * dot) * iq;
                 o = 1.f / (1.f + expf(-ol));
                 dol = dop * o * (1.f - o);
             }
-            // attribute gradients: raw arrays, or the indexed codewords of every stage
-            const float* vals[4] = {dls, dq, &dol, drgb};
+            // attribute gradients: raw arrays, or the indexed codewords of every
+            // stage (values picked by compile-time group and component, so that
+            // they stay in registers)
+            auto gval = [&](int gi, int c) -> float { return gi == 0 ? dls[c] : (gi == 1 ? dq[c] : (gi == 2 ? dol : drgb[c])); };
 #pragma unroll
             for (int gi = 0; gi < 4; ++gi) {
+                constexpr int dmax = 4;
                 const int d = gdim(gi);
                 if (S.L[gi] > 0) {
                     if (!O.cb[gi]) continue;
@@ -244,10 +248,14 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                         const int k = __ldg(S.idx[gi] + (int64_t)st * S.N + n);
                         const int j = (st * S.K[gi] + k) * d;
                         float* dst = O.cb_in_smem ? s_cb + O.cb_off[gi] + j : O.cb[gi] + j;
-                        for (int c = 0; c < d; ++c) atomicAdd(dst + c, vals[gi][c]);
+#pragma unroll
+                        for (int c = 0; c < dmax; ++c)
+                            if (c < d) atomicAdd(dst + c, gval(gi, c));
                     }
                 } else if (O.raw[gi]) {
-                    for (int c = 0; c < d; ++c) atomicAdd(O.raw[gi] + n * d + c, vals[gi][c]);
+#pragma unroll
+                    for (int c = 0; c < dmax; ++c)
+                        if (c < d) atomicAdd(O.raw[gi] + n * d + c, gval(gi, c));
                 }
             }
             if (O.d_mask && S.mask) {

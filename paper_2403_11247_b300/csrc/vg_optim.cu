@@ -12,6 +12,7 @@ struct AdamPack {
     float* m[16];
     float* v[16];
     int64_t size[16];
+    int64_t chunk_end[16];  // running total of ceil(size / 4) over tensors 0..t
 };
 
 __device__ __forceinline__ void adam_update(float& p, float& m, float& v, float g, float b1, float b2, float step_size,
@@ -21,9 +22,11 @@ __device__ __forceinline__ void adam_update(float& p, float& m, float& v, float 
     p -= step_size * m / (sqrtf(v) * inv_sqrt_bc2 + eps);
 }
 
-// grid-stride over every tensor in turn, four elements per load where the
-// four arrays of a tensor are 16-byte aligned (the bias corrections are
-// computed once per thread, not once per element)
+// one index space of four-element chunks over all tensors, so that every
+// thread issues the loads of its chunk at once instead of walking the tensors
+// one after another (one DRAM round trip per launch, not one per tensor); a
+// chunk goes through float4 loads where its tensor's four arrays are 16-byte
+// aligned and it is whole.  The bias corrections are computed once per thread.
 __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamPack A, float lr, float b1, float b2,
                                                    float eps, const int32_t* step_dev, int32_t step_host) {
     const int32_t step = step_dev ? step_dev[0] : step_host;
@@ -31,18 +34,21 @@ __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamP
     const float bc2 = 1.f - powf(b2, (float)step);
     const float step_size = lr / bc1;
     const float inv_sqrt_bc2 = rsqrtf(bc2);
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-    for (int t = 0; t < A.n; ++t) {
+    const int64_t total = A.chunk_end[A.n - 1];
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += nthr) {
+        int t = 0;
+        while (c >= A.chunk_end[t]) ++t;
         float* __restrict__ P = A.p[t];
         const float* __restrict__ G = A.g[t];
         float* __restrict__ M = A.m[t];
         float* __restrict__ Vv = A.v[t];
         const int64_t n = A.size[t];
-        const bool vec = ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(G) |
-                           reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(Vv)) & 15u) == 0;
-        const int64_t n4 = vec ? n / 4 : 0;
-        for (int64_t i = tid; i < n4; i += nthr) {
+        const int64_t i0 = (c - (t ? A.chunk_end[t - 1] : 0)) * 4;
+        const bool vec = i0 + 4 <= n && ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(G) |
+                                          reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(Vv)) & 15u) == 0;
+        if (vec) {
+            const int64_t i = i0 / 4;
             float4 p = reinterpret_cast<float4*>(P)[i];
             float4 m = reinterpret_cast<float4*>(M)[i];
             float4 v = reinterpret_cast<float4*>(Vv)[i];
@@ -54,13 +60,15 @@ __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamP
             reinterpret_cast<float4*>(P)[i] = p;
             reinterpret_cast<float4*>(M)[i] = m;
             reinterpret_cast<float4*>(Vv)[i] = v;
-        }
-        for (int64_t i = n4 * 4 + tid; i < n; i += nthr) {
-            float p = P[i], m = M[i], v = Vv[i];
-            adam_update(p, m, v, G[i], b1, b2, step_size, inv_sqrt_bc2, eps);
-            P[i] = p;
-            M[i] = m;
-            Vv[i] = v;
+        } else {
+            const int64_t i1 = i0 + 4 < n ? i0 + 4 : n;
+            for (int64_t i = i0; i < i1; ++i) {
+                float p = P[i], m = M[i], v = Vv[i];
+                adam_update(p, m, v, G[i], b1, b2, step_size, inv_sqrt_bc2, eps);
+                P[i] = p;
+                M[i] = m;
+                Vv[i] = v;
+            }
         }
     }
 }
@@ -79,11 +87,12 @@ cudaError_t launch_adam(int n, float* const* p, const float* const* g, float* co
         A.m[i] = m[i];
         A.v[i] = v[i];
         A.size[i] = size[i];
-        total += size[i];
+        total += ceil_div(size[i], 4);
+        A.chunk_end[i] = total;
     }
     if (total > 0) {
-        int64_t blocks = ceil_div(ceil_div(total, 4), 256);
-        if (blocks > 148 * 4) blocks = 148 * 4;
+        int64_t blocks = ceil_div(total, 256);
+        if (blocks > 148 * 16) blocks = 148 * 16;
         count_launches(1);
         adam_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, lr, b1, b2, eps, step_dev, step_host);
         cudaError_t e = cudaGetLastError();
