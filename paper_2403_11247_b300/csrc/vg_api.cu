@@ -181,7 +181,7 @@ struct vg_ctx {
     StageProfiler prof;
     int64_t pair_cap = 0;
     DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, tile_order, Tfin, ncontrib, lookback,
-        scratch, state, pose_part, icp_part, loss_scratch, pair_off, blk_count, blk_base, vis, ssim_ws, grow_ws;
+        scratch, state, pose_part, icp_part, loss_scratch, pair_off, chunk_start, blk_count, blk_base, vis, ssim_ws, grow_ws;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
     bool tile_sort_failed = false;  // a tile list overflowed the per-tile sort: VG_SORT_AUTO sorts globally
@@ -641,9 +641,11 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     VG_TRY(ctx->rgbd.ensure(slots * 16, st, "rgbd"));
     VG_TRY(ctx->rect.ensure(slots * 8, st, "rect"));
     VG_TRY(ctx->ntiles.ensure(slots * 4, st, "ntiles"));
-    VG_TRY(ctx->pair_off.ensure(slots * 4, st, "pair offsets"));
-    VG_TRY(ctx->blk_count.ensure((size_t)preprocess_blocks(N) * 4, st, "block counts"));
-    VG_TRY(ctx->blk_base.ensure((size_t)preprocess_blocks(N) * 4, st, "block bases"));
+    VG_TRY(ctx->pair_off.ensure((slots + 1) * 4, st, "pair offsets"));
+    VG_TRY(ctx->chunk_start.ensure((size_t)ceil_div(std::max<int64_t>(ctx->pair_cap, 1), EMIT_CHUNK) * 4, st,
+                                   "pair chunk starts"));
+    VG_TRY(ctx->blk_count.ensure((size_t)preprocess_blocks(N) * 8, st, "block counts"));
+    VG_TRY(ctx->blk_base.ensure((size_t)preprocess_blocks(N) * 8, st, "block bases"));
     for (int b = 0; b < 2; ++b) {
         VG_TRY(ctx->dkey[b].ensure(slots * 4, st, "depth keys"));
         VG_TRY(ctx->dval[b].ensure(slots * 4, st, "depth values"));
@@ -680,10 +682,16 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     // Gaussian order); with the per-tile sort the compacted order stays and
     // the forward compositing kernel orders each tile's list instead
     const int dgrid = sort_pass_grid((uint32_t)slots);
+    const uint32_t cap = (uint32_t)ctx->pair_cap;
+    // with the per-tile sort the pairs follow the compacted order, so the
+    // compaction also produces their offsets (no separate scan)
     VG_STAGE(VG_STAGE_DEPTH_SORT, ([&]() -> cudaError_t {
                  cudaError_t e = launch_compact(V, N, ctx->dkey[1].as<uint32_t>(), ctx->blk_count.as<uint32_t>(),
                                                 ctx->blk_base.as<uint32_t>(), ctx->dkey[0].as<uint32_t>(),
-                                                ctx->dval[0].as<uint32_t>(), ctx->vis.as<uint32_t>(), st);
+                                                ctx->dval[0].as<uint32_t>(), ctx->vis.as<uint32_t>(),
+                                                ctx->ntiles.as<uint32_t>(),
+                                                tile_sort ? ctx->pair_off.as<uint32_t>() : nullptr,
+                                                ctx->chunk_start.as<uint32_t>(), cap, scr, err, st);
                  if (e != cudaSuccess) return e;
                  for (int p = 0; p < (tile_sort ? 0 : 4); ++p) {
                      const int i = p & 1, o = i ^ 1;
@@ -698,9 +706,9 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     // pairs in depth order, then stable by tile (global sort); or in slot
     // order, then grouped by tile without order (per-tile sort)
     const int tp = tile_passes_for(V.total_tiles);
-    const uint32_t cap = (uint32_t)ctx->pair_cap;
     VG_STAGE(VG_STAGE_DUPLICATE,
-             launch_duplicate(ctx->dval[0].as<uint32_t>(), ctx->pair_off.as<uint32_t>(), ctx->ntiles.as<uint32_t>(),
+             launch_duplicate(ctx->dval[0].as<uint32_t>(), ctx->pair_off.as<uint32_t>(),
+                              ctx->chunk_start.as<uint32_t>(), tile_sort, ctx->ntiles.as<uint32_t>(),
                               ctx->rect.as<uint2>(), N, V, ctx->pkey[0].as<uint32_t>(), ctx->pval[0].as<uint32_t>(), cap,
                               scr, tile_sort ? 0 : tp, lb, state, 4u, err, slots, st));
     const int tgrid = sort_pass_grid(cap);

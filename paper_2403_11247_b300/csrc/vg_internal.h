@@ -38,6 +38,15 @@ constexpr int EMIT_SMEM_TILES = 16384;  // per-tile counts kept in shared memory
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// pairs are emitted in chunks of EMIT_CHUNK consecutive pairs, one block each
+constexpr int EMIT_CHUNK = 256;
+// The slot at position j of the pair order owns pairs [o, o + c): every chunk
+// k whose first pair EMIT_CHUNK k lies there (and below cap) starts in it.
+__device__ __forceinline__ void mark_chunks(uint32_t* chunk_start, uint32_t j, uint32_t o, uint32_t c, uint32_t cap) {
+    const uint64_t end = min((uint64_t)o + c, (uint64_t)cap);
+    for (uint64_t k = ((uint64_t)o + EMIT_CHUNK - 1) / EMIT_CHUNK; k * EMIT_CHUNK < end; ++k) chunk_start[k] = j;
+}
+
 // kernels enqueued by this library in this process (host-side count)
 void count_launches(int n);
 // Raise a kernel's dynamic shared-memory limit when its static plus dynamic
@@ -52,8 +61,14 @@ cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& c
                               float4* rgbd, uint2* rect, uint32_t* ntiles, uint32_t* dkey, uint32_t* scratch,
                               uint32_t* state, uint32_t* blk_count, cudaStream_t st);
 // visible slots, in (view, Gaussian) order within each preprocess block, to keys_out / vals_out
+// blk_count / blk_base hold [blocks] visible-slot counts, then (pair_off
+// non-NULL) [blocks] pair counts; with pair_off the pair offsets of the
+// compacted order, the chunk starts, the pair count and the overflow flag
+// are produced here and launch_duplicate skips its own scan
 cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count, uint32_t* blk_base,
-                           uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, cudaStream_t st);
+                           uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, const uint32_t* ntiles,
+                           uint32_t* pair_off, uint32_t* chunk_start, uint32_t cap, uint32_t* scratch, uint32_t* err,
+                           cudaStream_t st);
 cudaError_t launch_rvq_decode(int dim, int L, int K, const float* cb, const uint8_t* idx, const float* raw,
                               int64_t n, float* out, cudaStream_t st);
 
@@ -66,7 +81,11 @@ cudaError_t launch_sort_pass(const uint32_t* keys_in, const uint32_t* vals_in, u
                              const uint32_t* state, uint32_t epoch_offset, uint32_t* err, int grid,
                              cudaStream_t st);
 int sort_pass_grid(uint32_t n_cap);
-cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, const uint32_t* ntiles,
+// offsets has room for [slots + 1] (the last is the pair count) and
+// chunk_start for [ceil(cap / EMIT_CHUNK)]; offsets_ready: both were filled by
+// launch_compact for this order
+cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, uint32_t* chunk_start,
+                             bool offsets_ready, const uint32_t* ntiles,
                              const uint2* rect, int64_t N, const Views& V, uint32_t* pkeys, uint32_t* pvals,
                              uint32_t cap, uint32_t* scratch, int tile_passes, unsigned long long* lookback,
                              const uint32_t* state, uint32_t epoch_offset, uint32_t* err, int64_t max_slots,

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(SceneDev S, const __
 
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = n < S.N;
-    uint32_t n_vis = 0;
+    uint32_t n_vis = 0, n_pair = 0;
     float mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, ol = 0.f, rgb[3] = {0, 0, 0};
     bool active = false;
     float RS[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // R diag(s): Sigma = RS RS^T
@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(SceneDev S, const __
                 key = __float_as_uint(p[2]);
                 dkey[slot] = key;
                 ++n_vis;
+                n_pair += cnt;
                 if (cs.seen) cs.seen[n] = 1u;
             } else {
                 ntiles[slot] = 0u;
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(SceneDev S, const __
         }
     }
     if (n_vis) atomicAdd(&s_cnt[0], n_vis);
+    if (n_pair) atomicAdd(&s_cnt[1], n_pair);
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
         uint32_t h = s_hist[i];
@@ -234,43 +236,61 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(SceneDev S, const __
     if (threadIdx.x == 0) {
         if (s_cnt[0]) atomicAdd(scratch + SCR_NVIS, s_cnt[0]);
         blk_count[blockIdx.x] = s_cnt[0];
+        blk_count[gridDim.x + blockIdx.x] = s_cnt[1];  // the block's (slot, tile) pairs
     }
 }
 
-// exclusive scan of the per-block visible counts (one block)
-__global__ void __launch_bounds__(1024) block_scan_kernel(const uint32_t* __restrict__ cnt, int n,
-                                                          uint32_t* __restrict__ base) {
+// exclusive scans of the per-block counts (one block): arrays = 1, the
+// visible-slot counts; arrays = 2, those and then the per-block pair counts,
+// whose total becomes the pair count of the forward (flagged when above cap)
+// and the sentinel pair_off[visible slots]
+__global__ void __launch_bounds__(1024) block_scan_kernel(const uint32_t* __restrict__ cnt, int n, int arrays,
+                                                          uint32_t* __restrict__ base, uint32_t* __restrict__ scratch,
+                                                          uint32_t* __restrict__ pair_off, uint32_t cap,
+                                                          uint32_t* __restrict__ err) {
     __shared__ uint32_t s_w[32];
     __shared__ uint32_t s_carry;
+    __shared__ uint32_t s_total[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int c0 = 0; c0 < n; c0 += 1024) {
-        const int i = c0 + threadIdx.x;
-        const uint32_t x = i < n ? cnt[i] : 0u;
-        uint32_t inc = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) s_w[warp] = inc;
+    for (int a = 0; a < arrays; ++a) {
+        const uint32_t* in = cnt + (int64_t)a * n;
+        uint32_t* out = base + (int64_t)a * n;
+        if (threadIdx.x == 0) s_carry = 0;
         __syncthreads();
-        if (warp == 0) {
-            uint32_t t = s_w[lane];
+        for (int c0 = 0; c0 < n; c0 += 1024) {
+            const int i = c0 + threadIdx.x;
+            const uint32_t x = i < n ? in[i] : 0u;
+            uint32_t inc = x;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += y;
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
             }
-            s_w[lane] = t;  // inclusive warp prefix
+            if (lane == 31) s_w[warp] = inc;
+            __syncthreads();
+            if (warp == 0) {
+                uint32_t t = s_w[lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                    if (lane >= o) t += y;
+                }
+                s_w[lane] = t;  // inclusive warp prefix
+            }
+            __syncthreads();
+            const uint32_t wpre = warp ? s_w[warp - 1] : 0u;
+            if (i < n) out[i] = s_carry + wpre + inc - x;
+            __syncthreads();
+            if (threadIdx.x == 0) s_carry += s_w[31];
+            __syncthreads();
         }
-        __syncthreads();
-        const uint32_t wpre = warp ? s_w[warp - 1] : 0u;
-        if (i < n) base[i] = s_carry + wpre + inc - x;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += s_w[31];
-        __syncthreads();
+        if (threadIdx.x == 0) s_total[a] = s_carry;
+    }
+    if (arrays == 2 && threadIdx.x == 0) {
+        const uint32_t pairs = s_total[1];
+        scratch[SCR_PAIRS] = pairs;
+        if (pairs > cap) atomicOr(err, ERR_OVERFLOW);
+        pair_off[s_total[0]] = pairs;
     }
 }
 
@@ -278,14 +298,20 @@ __global__ void __launch_bounds__(1024) block_scan_kernel(const uint32_t* __rest
 // grid covers Gaussians [256 b, 256 b + 256) of every view; its visible slots
 // go, view by view and in Gaussian order, to [base[b], base[b] + count[b]);
 // vals_copy (may be NULL) keeps that slot order for the backward's per-slot
-// passes (the depth sort overwrites vals_out)
+// passes (the depth sort overwrites vals_out).  With pair_off (the forms that
+// keep this order for the pairs), the slot at position j also gets its first
+// pair, pair_off[j] (exclusive scan of the tile counts in this order), and
+// marks the 256-pair chunks that start inside its pairs.
 __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Views V, int64_t N,
                                                       const uint32_t* __restrict__ dkey,
                                                       const uint32_t* __restrict__ base, uint32_t* __restrict__ keys_out,
-                                                      uint32_t* __restrict__ vals_out, uint32_t* __restrict__ vals_copy) {
+                                                      uint32_t* __restrict__ vals_out, uint32_t* __restrict__ vals_copy,
+                                                      const uint32_t* __restrict__ ntiles, uint32_t* __restrict__ pair_off,
+                                                      uint32_t* __restrict__ chunk_start, uint32_t cap) {
     __shared__ uint32_t s_tmp[8];
     const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
     uint32_t off = base[blockIdx.x];
+    uint32_t poff = pair_off ? base[gridDim.x + blockIdx.x] : 0u;
     for (int v = 0; v < V.n; ++v) {
         const int64_t slot = (int64_t)v * N + n;
         const uint32_t key = n < N ? dkey[slot] : 0xffffffffu;
@@ -296,6 +322,16 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
             keys_out[off + pre] = key;
             vals_out[off + pre] = (uint32_t)slot;
             if (vals_copy) vals_copy[off + pre] = (uint32_t)slot;
+        }
+        if (pair_off) {
+            const uint32_t c = f ? ntiles[slot] : 0u;
+            uint32_t ctot;
+            const uint32_t cpre = block_excl_scan_256(c, s_tmp, &ctot);
+            if (f) {
+                pair_off[off + pre] = poff + cpre;
+                mark_chunks(chunk_start, off + pre, poff + cpre, c, cap);
+            }
+            poff += ctot;
         }
         off += tot;
     }
@@ -324,13 +360,16 @@ cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& c
 }
 
 cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count, uint32_t* blk_base,
-                           uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, cudaStream_t st) {
+                           uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, const uint32_t* ntiles,
+                           uint32_t* pair_off, uint32_t* chunk_start, uint32_t cap, uint32_t* scratch, uint32_t* err,
+                           cudaStream_t st) {
     const int blocks = preprocess_blocks(N);
     count_launches(2);
-    block_scan_kernel<<<1, 1024, 0, st>>>(blk_count, blocks, blk_base);
+    block_scan_kernel<<<1, 1024, 0, st>>>(blk_count, blocks, pair_off ? 2 : 1, blk_base, scratch, pair_off, cap, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    compact_kernel<<<blocks, 256, 0, st>>>(V, N, dkey, blk_base, keys_out, vals_out, vals_copy);
+    compact_kernel<<<blocks, 256, 0, st>>>(V, N, dkey, blk_base, keys_out, vals_out, vals_copy, ntiles, pair_off,
+                                           chunk_start, cap);
     return cudaGetLastError();
 }
 

@@ -188,8 +188,8 @@ cudaError_t launch_sort_pass(const uint32_t* keys_in, const uint32_t* vals_in, u
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(DUP_THREADS) pair_offsets_kernel(
     const uint32_t* __restrict__ sorted_slots, const uint32_t* __restrict__ ntiles, uint32_t* __restrict__ offsets,
-    uint32_t cap, uint32_t* scratch, unsigned long long* lookback, const uint32_t* state, uint32_t epoch_offset,
-    uint32_t* err) {
+    uint32_t* __restrict__ chunk_start, uint32_t cap, uint32_t* scratch, unsigned long long* lookback,
+    const uint32_t* state, uint32_t epoch_offset, uint32_t* err) {
     __shared__ uint32_t s_tmp[8];
     __shared__ uint32_t s_pid;
     __shared__ uint32_t s_excl;
@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(DUP_THREADS) pair_offsets_kernel(
             s_excl = excl;
             if (pid == nparts - 1) {
                 scratch[SCR_PAIRS] = excl + agg;
+                offsets[nvis] = excl + agg;
                 if (excl + agg > cap) atomicOr(err, ERR_OVERFLOW);
             }
         }
@@ -231,7 +232,10 @@ __global__ void __launch_bounds__(DUP_THREADS) pair_offsets_kernel(
         uint32_t off = s_excl + pre;
 #pragma unroll
         for (int i = 0; i < DUP_ITEMS; ++i) {
-            if (base + i < nvis) offsets[base + i] = off;
+            if (base + i < nvis) {
+                offsets[base + i] = off;
+                mark_chunks(chunk_start, base + i, off, cnt[i], cap);
+            }
             off += cnt[i];
         }
         __syncthreads();
@@ -241,64 +245,75 @@ __global__ void __launch_bounds__(DUP_THREADS) pair_offsets_kernel(
 // ---------------------------------------------------------------------------
 // pair emission: one thread per (Gaussian, tile) pair, balanced however the
 // tiles are spread over Gaussians (a Gaussian close to the camera can cover
-// thousands of tiles); pair e belongs to the sorted slot j with
-// offsets[j] <= e < offsets[j+1], tiles in row-major order of its rect
+// thousands of tiles).  A block takes a chunk of EMIT_CHUNK consecutive pairs;
+// chunk_start names the slot position j0 its first pair belongs to.  Every
+// visible slot owns at least one pair, so positions j0 .. j0 + EMIT_CHUNK
+// cover the chunk: each marks where its pairs start inside the chunk, and an
+// inclusive max-scan over the chunk hands every pair its slot (the owner
+// index only grows along the chunk).  Tiles in row-major order of the rect.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) emit_pairs_kernel(
-    const uint32_t* __restrict__ sorted_slots, const uint32_t* __restrict__ offsets, const uint2* __restrict__ rect,
-    int64_t N, const __grid_constant__ Views V, uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals, uint32_t cap,
+__global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
+    const uint32_t* __restrict__ sorted_slots, const uint32_t* __restrict__ offsets,
+    const uint32_t* __restrict__ chunk_start, const uint2* __restrict__ rect, int64_t N,
+    const __grid_constant__ Views V, uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals, uint32_t cap,
     uint32_t* scratch, int tile_passes) {
     __shared__ uint32_t s_hist[3 * 256];
+    __shared__ uint32_t s_own[EMIT_CHUNK];
+    __shared__ uint32_t s_slot[EMIT_CHUNK + 1], s_first[EMIT_CHUNK + 1];
+    __shared__ uint32_t s_wmax[EMIT_CHUNK / 32];
     extern __shared__ uint32_t s_tiles[];  // per-tile counts when they fit, else counted in global memory
     const bool tiles_in_smem = V.total_tiles <= EMIT_SMEM_TILES;
     for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) s_hist[i] = 0;
     if (tiles_in_smem)
         for (int i = threadIdx.x; i < V.total_tiles; i += blockDim.x) s_tiles[i] = 0;
     uint32_t* tile_counts = scratch + SCR_TILE_COUNTS;
-    __syncthreads();
     const uint32_t nvis = scratch[SCR_NVIS];
     const uint32_t P = min(scratch[SCR_PAIRS], cap);
-    const uint32_t stride = gridDim.x * blockDim.x;
-    __shared__ uint32_t s_bounds[2];
-    for (uint32_t e0 = blockIdx.x * blockDim.x; e0 < P; e0 += stride) {
-        // the slots of the block's first and last pair bound every thread's
-        // search: two full searches per block, then short ones
-        if (threadIdx.x < 2) {
-            const uint32_t t = threadIdx.x == 0 ? e0 : min(e0 + blockDim.x, P) - 1;
-            uint32_t lo = 0, hi = nvis;
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (__ldg(offsets + mid) <= t) lo = mid; else hi = mid;
+    const uint32_t stride = gridDim.x * EMIT_CHUNK;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t e0 = blockIdx.x * EMIT_CHUNK; e0 < P; e0 += stride) {
+        const uint32_t e1 = min(e0 + (uint32_t)EMIT_CHUNK, P);
+        s_own[threadIdx.x] = 0u;
+        __syncthreads();
+        const uint32_t j0 = chunk_start[e0 / EMIT_CHUNK];
+        for (uint32_t t = threadIdx.x; t <= (uint32_t)EMIT_CHUNK; t += EMIT_CHUNK) {
+            const uint32_t j = j0 + t;
+            if (j < nvis) {
+                const uint32_t o = __ldg(offsets + j), o1 = __ldg(offsets + j + 1);
+                s_slot[t] = __ldg(sorted_slots + j);
+                s_first[t] = o;
+                if (o1 > e0 && o < e1) s_own[max(o, e0) - e0] = t;
             }
-            s_bounds[threadIdx.x] = lo;
         }
         __syncthreads();
-        const uint32_t blo = s_bounds[0], bhi = s_bounds[1] + 1;
+        uint32_t own = s_own[threadIdx.x];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, own, o);
+            if (lane >= o) own = max(own, y);
+        }
+        if (lane == 31) s_wmax[warp] = own;
         __syncthreads();
+#pragma unroll
+        for (int w = 0; w < EMIT_CHUNK / 32; ++w)
+            if (w < warp) own = max(own, s_wmax[w]);
         const uint32_t e = e0 + threadIdx.x;
-        const bool live = e < P;
+        const bool live = e < e1;
         const uint32_t active = __ballot_sync(0xffffffffu, live);
-        if (!live) continue;
-        // last j with offsets[j] <= e
-        uint32_t lo = blo, hi = bhi;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (__ldg(offsets + mid) <= e) lo = mid; else hi = mid;
-        }
-        const uint32_t s = __ldg(sorted_slots + lo);
-        const uint32_t local = e - __ldg(offsets + lo);
-        const uint2 r = __ldg(rect + s);
-        const uint32_t x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff;
-        const uint32_t w = x1 - x0;
-        const uint32_t ry = local / w, rx = local - ry * w;
-        const int v = (int)(s / (uint64_t)N);
-        const uint32_t key = (uint32_t)(V.v[v].tile_base + (int)(y0 + ry) * V.v[v].tiles_x + (int)(x0 + rx));
-        pkeys[e] = key;
-        pvals[e] = s;
-        for (int p = 0; p < tile_passes; ++p) hist_add_warp(s_hist + p * 256, (key >> (8 * p)) & 255u, active);
-        {
+        if (live) {
+            const uint32_t s = s_slot[own];
+            const uint32_t local = e - s_first[own];
+            const uint2 r = __ldg(rect + s);
+            const uint32_t x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff;
+            const uint32_t w = x1 - x0;
+            const uint32_t ry = local / w, rx = local - ry * w;
+            const int v = (int)(s / (uint64_t)N);
+            const uint32_t key = (uint32_t)(V.v[v].tile_base + (int)(y0 + ry) * V.v[v].tiles_x + (int)(x0 + rx));
+            pkeys[e] = key;
+            pvals[e] = s;
+            for (int p = 0; p < tile_passes; ++p) hist_add_warp(s_hist + p * 256, (key >> (8 * p)) & 255u, active);
             const uint32_t peers = __match_any_sync(active, key);
-            if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) {
+            if ((uint32_t)lane == (uint32_t)(__ffs(peers) - 1)) {
                 if (tiles_in_smem) atomicAdd(s_tiles + key, (uint32_t)__popc(peers));
                 else atomicAdd(tile_counts + key, (uint32_t)__popc(peers));
             }
@@ -316,7 +331,8 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(
         }
 }
 
-cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, const uint32_t* ntiles, const uint2* rect,
+cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, uint32_t* chunk_start,
+                             bool offsets_ready, const uint32_t* ntiles, const uint2* rect,
                              int64_t N, const Views& V, uint32_t* pkeys, uint32_t* pvals, uint32_t cap,
                              uint32_t* scratch, int tile_passes, unsigned long long* lookback, const uint32_t* state,
                              uint32_t epoch_offset, uint32_t* err, int64_t max_slots, cudaStream_t st) {
@@ -328,21 +344,25 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, co
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_offsets_kernel, DUP_THREADS, 0);
         max_grid = sms * (per > 0 ? per : 1);
     }
-    int64_t parts = ceil_div(max_slots > 0 ? max_slots : 1, DUP_TILE);
-    int grid = (int)(parts < max_grid ? parts : max_grid);
-    count_launches(2);
-    pair_offsets_kernel<<<grid, DUP_THREADS, 0, st>>>(sorted_slots, ntiles, offsets, cap, scratch, lookback, state,
-                                                      epoch_offset, err);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    int64_t eg = ceil_div((int64_t)cap, 256);
+    cudaError_t e;
+    if (!offsets_ready) {
+        int64_t parts = ceil_div(max_slots > 0 ? max_slots : 1, DUP_TILE);
+        int grid = (int)(parts < max_grid ? parts : max_grid);
+        count_launches(1);
+        pair_offsets_kernel<<<grid, DUP_THREADS, 0, st>>>(sorted_slots, ntiles, offsets, chunk_start, cap, scratch,
+                                                          lookback, state, epoch_offset, err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    int64_t eg = ceil_div((int64_t)cap, EMIT_CHUNK);
     if (eg > (int64_t)sms * 8) eg = (int64_t)sms * 8;
     if (eg < 1) eg = 1;
     const size_t smem = V.total_tiles <= EMIT_SMEM_TILES ? (size_t)V.total_tiles * 4 : 0;
     e = allow_dynamic_smem((const void*)emit_pairs_kernel, smem);
     if (e != cudaSuccess) return e;
-    emit_pairs_kernel<<<(unsigned)eg, 256, smem, st>>>(sorted_slots, offsets, rect, N, V, pkeys, pvals, cap, scratch,
-                                                        tile_passes);
+    count_launches(1);
+    emit_pairs_kernel<<<(unsigned)eg, EMIT_CHUNK, smem, st>>>(sorted_slots, offsets, chunk_start, rect, N, V, pkeys,
+                                                               pvals, cap, scratch, tile_passes);
     return cudaGetLastError();
 }
 
