@@ -9,7 +9,7 @@
 
 namespace vgk {
 
-__global__ void __launch_bounds__(256, 4) preprocess_kernel(SceneDev S, const __grid_constant__ Views V, Consts cs,
+__global__ void __launch_bounds__(256, 5) preprocess_kernel(SceneDev S, const __grid_constant__ Views V, Consts cs,
                                                          float4* __restrict__ xy, float4* __restrict__ conic_o,
                                                          float4* __restrict__ rgbd, uint2* __restrict__ rect,
                                                          uint32_t* __restrict__ ntiles, uint32_t* __restrict__ dkey,

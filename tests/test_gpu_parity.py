@@ -129,6 +129,20 @@ def test_binning_bit_exact_room_two_views_mixed_sizes(cuda, sort_mode):
     assert P > 5000
 
 
+@pytest.mark.parametrize("sort_mode", SORTS)
+def test_binning_bit_exact_gaussians_covering_the_whole_image(cuda, sort_mode):
+    """Five Gaussians near the camera span every one of 1,200 tiles (each owns
+    several 256-pair emission chunks), among 600 small ones: the chunked pair
+    emission must hand every pair its slot."""
+    sc = synth.box_scene(4242, 600)
+    ls = sc.groups["logscale"].raw
+    ls[:5] = -0.3
+    sc.anchor_xyz[:5, 2] = np.float32(1.2)
+    cam = synth.camera(500.0, 500.0, 320.0, 240.0, 640, 480, synth.identity_pose())
+    P, nb, nbl = check_binning(sc, [cam], sort_mode=sort_mode)
+    assert P > 5 * 1200
+
+
 def test_sort_modes_give_identical_lists_images_and_gradients(cuda):
     torch = cuda
     sc = small_room(4000)
