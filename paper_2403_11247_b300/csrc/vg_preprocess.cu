@@ -241,56 +241,73 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(SceneDev S, const __
 }
 
 // exclusive scans of the per-block counts (one block): arrays = 1, the
-// visible-slot counts; arrays = 2, those and then the per-block pair counts,
-// whose total becomes the pair count of the forward (flagged when above cap)
-// and the sentinel pair_off[visible slots]
+// visible-slot counts; arrays = 2, those and the per-block pair counts that
+// follow them, scanned together (two consecutive blocks per thread, so one
+// pass covers 2048 blocks), whose total becomes the pair count of the forward
+// (flagged when above cap) and the sentinel pair_off[visible slots]
 __global__ void __launch_bounds__(1024) block_scan_kernel(const uint32_t* __restrict__ cnt, int n, int arrays,
                                                           uint32_t* __restrict__ base, uint32_t* __restrict__ scratch,
                                                           uint32_t* __restrict__ pair_off, uint32_t cap,
                                                           uint32_t* __restrict__ err) {
-    __shared__ uint32_t s_w[32];
-    __shared__ uint32_t s_carry;
-    __shared__ uint32_t s_total[2];
+    __shared__ uint2 s_w[32];
+    __shared__ uint2 s_carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int a = 0; a < arrays; ++a) {
-        const uint32_t* in = cnt + (int64_t)a * n;
-        uint32_t* out = base + (int64_t)a * n;
-        if (threadIdx.x == 0) s_carry = 0;
+    const bool two = arrays == 2;
+    if (threadIdx.x == 0) s_carry = make_uint2(0u, 0u);
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += 2 * 1024) {
+        const int i0 = c0 + 2 * (int)threadIdx.x;
+        const uint32_t a0 = i0 < n ? cnt[i0] : 0u, a1 = i0 + 1 < n ? cnt[i0 + 1] : 0u;
+        const uint32_t b0 = two && i0 < n ? cnt[n + i0] : 0u, b1 = two && i0 + 1 < n ? cnt[n + i0 + 1] : 0u;
+        const uint32_t ta = a0 + a1, tb = b0 + b1;
+        uint32_t ia = ta, ib = tb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t ya = __shfl_up_sync(0xffffffffu, ia, o);
+            const uint32_t yb = __shfl_up_sync(0xffffffffu, ib, o);
+            if (lane >= o) {
+                ia += ya;
+                ib += yb;
+            }
+        }
+        if (lane == 31) s_w[warp] = make_uint2(ia, ib);
         __syncthreads();
-        for (int c0 = 0; c0 < n; c0 += 1024) {
-            const int i = c0 + threadIdx.x;
-            const uint32_t x = i < n ? in[i] : 0u;
-            uint32_t inc = x;
+        if (warp == 0) {
+            uint2 t = s_w[lane];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            if (lane == 31) s_w[warp] = inc;
-            __syncthreads();
-            if (warp == 0) {
-                uint32_t t = s_w[lane];
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-                    if (lane >= o) t += y;
+                const uint32_t ya = __shfl_up_sync(0xffffffffu, t.x, o);
+                const uint32_t yb = __shfl_up_sync(0xffffffffu, t.y, o);
+                if (lane >= o) {
+                    t.x += ya;
+                    t.y += yb;
                 }
-                s_w[lane] = t;  // inclusive warp prefix
             }
-            __syncthreads();
-            const uint32_t wpre = warp ? s_w[warp - 1] : 0u;
-            if (i < n) out[i] = s_carry + wpre + inc - x;
-            __syncthreads();
-            if (threadIdx.x == 0) s_carry += s_w[31];
-            __syncthreads();
+            s_w[lane] = t;  // inclusive warp prefixes
         }
-        if (threadIdx.x == 0) s_total[a] = s_carry;
+        __syncthreads();
+        const uint2 wp = warp ? s_w[warp - 1] : make_uint2(0u, 0u);
+        const uint32_t pa = s_carry.x + wp.x + ia - ta, pb = s_carry.y + wp.y + ib - tb;
+        if (i0 < n) {
+            base[i0] = pa;
+            if (two) base[n + i0] = pb;
+        }
+        if (i0 + 1 < n) {
+            base[i0 + 1] = pa + a0;
+            if (two) base[n + i0 + 1] = pb + b0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_carry.x += s_w[31].x;
+            s_carry.y += s_w[31].y;
+        }
+        __syncthreads();
     }
-    if (arrays == 2 && threadIdx.x == 0) {
-        const uint32_t pairs = s_total[1];
+    if (two && threadIdx.x == 0) {
+        const uint32_t pairs = s_carry.y;
         scratch[SCR_PAIRS] = pairs;
         if (pairs > cap) atomicOr(err, ERR_OVERFLOW);
-        pair_off[s_total[0]] = pairs;
+        pair_off[s_carry.x] = pairs;
     }
 }
 
