@@ -256,14 +256,13 @@ __global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
     const uint32_t* __restrict__ sorted_slots, const uint32_t* __restrict__ offsets,
     const uint32_t* __restrict__ chunk_start, const uint2* __restrict__ rect, int64_t N,
     const __grid_constant__ Views V, uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals, uint32_t cap,
-    uint32_t* scratch, int tile_passes) {
+    uint32_t* scratch, int tile_passes, int tiles_in_smem) {
     __shared__ uint32_t s_hist[3 * 256];
     __shared__ uint32_t s_own[EMIT_CHUNK];
     __shared__ uint32_t s_slot[EMIT_CHUNK + 1], s_first[EMIT_CHUNK + 1];
     __shared__ uint32_t s_wmax[EMIT_CHUNK / 32];
-    extern __shared__ uint32_t s_tiles[];  // per-tile counts when they fit, else counted in global memory
-    const bool tiles_in_smem = V.total_tiles <= EMIT_SMEM_TILES;
-    for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) s_hist[i] = 0;
+    extern __shared__ uint32_t s_tiles[];  // per-tile counts when the block's share of pairs pays for them
+    for (int i = threadIdx.x; i < tile_passes * 256; i += blockDim.x) s_hist[i] = 0;
     if (tiles_in_smem)
         for (int i = threadIdx.x; i < V.total_tiles; i += blockDim.x) s_tiles[i] = 0;
     uint32_t* tile_counts = scratch + SCR_TILE_COUNTS;
@@ -357,12 +356,18 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, ui
     int64_t eg = ceil_div((int64_t)cap, EMIT_CHUNK);
     if (eg > (int64_t)sms * 8) eg = (int64_t)sms * 8;
     if (eg < 1) eg = 1;
-    const size_t smem = V.total_tiles <= EMIT_SMEM_TILES ? (size_t)V.total_tiles * 4 : 0;
+    // per-tile counts: a per-block histogram in shared memory pays for its
+    // zeroing and flush only when a block emits at least as many pairs as
+    // there are tiles; otherwise one global atomic per run of equal tiles
+    const int64_t chunks_per_block = ceil_div(ceil_div((int64_t)cap, EMIT_CHUNK), eg);
+    const int tiles_in_smem = V.total_tiles <= EMIT_SMEM_TILES &&
+                              (int64_t)V.total_tiles <= chunks_per_block * EMIT_CHUNK ? 1 : 0;
+    const size_t smem = tiles_in_smem ? (size_t)V.total_tiles * 4 : 0;
     e = allow_dynamic_smem((const void*)emit_pairs_kernel, smem);
     if (e != cudaSuccess) return e;
     count_launches(1);
     emit_pairs_kernel<<<(unsigned)eg, EMIT_CHUNK, smem, st>>>(sorted_slots, offsets, chunk_start, rect, N, V, pkeys,
-                                                               pvals, cap, scratch, tile_passes);
+                                                               pvals, cap, scratch, tile_passes, tiles_in_smem);
     return cudaGetLastError();
 }
 
