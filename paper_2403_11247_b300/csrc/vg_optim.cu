@@ -15,11 +15,16 @@ struct AdamPack {
     int64_t chunk_end[16];  // running total of ceil(size / 4) over tensors 0..t
 };
 
+// The update's square root and quotient go through the hardware reciprocal
+// square root and the fast divide (about 2 ulp each; the IEEE forms cost more
+// issue slots than the kernel's memory traffic).  sqrt(v) is taken as 0 below
+// the smallest normal number, where it is far under any eps.
 __device__ __forceinline__ void adam_update(float& p, float& m, float& v, float g, float b1, float b2, float step_size,
                                             float inv_sqrt_bc2, float eps) {
     m = b1 * m + (1.f - b1) * g;
     v = b2 * v + (1.f - b2) * g * g;
-    p -= step_size * m / (sqrtf(v) * inv_sqrt_bc2 + eps);
+    const float sv = v >= 1.17549435e-38f ? v * rsqrtf(v) : 0.f;
+    p -= __fdividef(step_size * m, sv * inv_sqrt_bc2 + eps);
 }
 
 // one index space of four-element chunks over all tensors, so that every
