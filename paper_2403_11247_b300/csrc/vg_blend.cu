@@ -20,8 +20,8 @@
 // the preprocess, widened for FP32 rounding) skips Gaussians that every
 // pixel of the warp would skip anyway; the per-pixel decisions are unchanged.
 // In the backward, lanes of a warp hold different pixels of the same
-// Gaussian: their ten partials are reduced with a transposing butterfly (17
-// shuffles) before four lanes issue the global atomics.
+// Gaussian: their ten partials are reduced with a fully transposing butterfly
+// (12 shuffles) and ten lanes issue the global atomics in one instruction.
 #include "vg_internal.h"
 
 namespace vgk {
@@ -321,34 +321,41 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     }
 }
 
-// transposing butterfly: ten per-lane values summed over the warp; lanes 0, 8,
-// 16, 24 end up holding values {0,1,2}, {3,4}, {5,6,7}, {8,9} and add them to dst
-__device__ __forceinline__ void warp_reduce_add10(const float v[10], float* dst) {
+// Fully transposing butterfly: ten per-lane values summed over the warp in
+// 12 shuffles.  Each stage halves the values a lane holds (a lane keeps one
+// half and sends the other to its partner), so at the end lane l holds the
+// warp's sum of value reduce10_index(l) (or nothing, -1), and the ten owners
+// issue one atomic instruction together.
+__device__ __forceinline__ float warp_reduce10(const float v[10]) {
     const int lane = threadIdx.x & 31;
-    const bool h16 = (lane & 16) != 0;
+    const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0, h4 = (lane & 4) != 0, h2 = (lane & 2) != 0;
     float a[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 5; ++k) {  // values k (h16 clear) or k + 5 (h16 set)
         const float send = h16 ? v[k] : v[k + 5];
         const float keep = h16 ? v[k + 5] : v[k];
         a[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
-    const bool h8 = (lane & 8) != 0;
-    float b0 = (h8 ? a[3] : a[0]) + __shfl_xor_sync(0xffffffffu, h8 ? a[0] : a[3], 8);
-    float b1 = (h8 ? a[4] : a[1]) + __shfl_xor_sync(0xffffffffu, h8 ? a[1] : a[4], 8);
-    float b2 = (h8 ? 0.f : a[2]) + __shfl_xor_sync(0xffffffffu, h8 ? a[2] : 0.f, 8);
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-        b0 += __shfl_xor_sync(0xffffffffu, b0, o);
-        b1 += __shfl_xor_sync(0xffffffffu, b1, o);
-        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
-    }
-    if ((lane & 7) == 0) {
-        const int base = (h16 ? 5 : 0) + (h8 ? 3 : 0);
-        atomicAdd(dst + base, b0);
-        atomicAdd(dst + base + 1, b1);
-        if (!h8) atomicAdd(dst + base + 2, b2);
-    }
+    // h8 clear keeps a0, a1, a2; h8 set keeps a3, a4
+    const float b0 = (h8 ? a[3] : a[0]) + __shfl_xor_sync(0xffffffffu, h8 ? a[0] : a[3], 8);
+    const float b1 = (h8 ? a[4] : a[1]) + __shfl_xor_sync(0xffffffffu, h8 ? a[1] : a[4], 8);
+    const float b2 = (h8 ? 0.f : a[2]) + __shfl_xor_sync(0xffffffffu, h8 ? a[2] : 0.f, 8);
+    // h4 clear keeps b0, b1; h4 set keeps b2
+    const float c0 = (h4 ? b2 : b0) + __shfl_xor_sync(0xffffffffu, h4 ? b0 : b2, 4);
+    const float c1 = (h4 ? 0.f : b1) + __shfl_xor_sync(0xffffffffu, h4 ? b1 : 0.f, 4);
+    // h2 clear keeps c0, h2 set keeps c1
+    float d = (h2 ? c1 : c0) + __shfl_xor_sync(0xffffffffu, h2 ? c0 : c1, 2);
+    d += __shfl_xor_sync(0xffffffffu, d, 1);
+    return d;
+}
+
+// the value whose warp sum lane `lane` holds after warp_reduce10 (even lanes
+// only; the odd ones hold copies), -1 for none
+__device__ __forceinline__ int reduce10_index(int lane) {
+    if (lane & 1) return -1;
+    const int sub = ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+    const int k = sub == 0 ? 0 : sub == 1 ? 1 : sub == 2 ? 2 : sub == 4 ? 3 : sub == 5 ? 4 : -1;
+    return k < 0 ? -1 : k + ((lane & 16) ? 5 : 0);
 }
 
 template <int PPT>
@@ -420,6 +427,11 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     const uint32_t end = rg.x + min(s_max, rg.y - rg.x);
     // largest list position this warp still needs
     const uint32_t warp_max = mymax;
+    // this lane's reduced value and its factor: dL/d(u, v) = -sum dp (conic d);
+    // dL/d(a, b, c) = -sum dp (dx^2/2, dx dy, dy^2/2); dL/do = sum e^power dA
+    // with e^power = x / o (the 1/o is the visited Gaussian's); the rest as summed
+    const int red_idx = reduce10_index(threadIdx.x & 31);
+    const float red_scale = (red_idx == 2 || red_idx == 4) ? -0.5f : (red_idx >= 0 && red_idx <= 3) ? -1.f : 1.f;
 
     for (uint32_t bend = end; bend > rg.x;) {
         const uint32_t bstart = (bend - rg.x > (uint32_t)BLEND_BATCH) ? bend - BLEND_BATCH : rg.x;
@@ -493,15 +505,10 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
                     any = true;
                 }
                 if (__any_sync(0xffffffffu, any)) {
-                    // dL/d(u, v) = -sum dp (conic d); dL/d(a, b, c) = -sum dp (dx^2/2, dx dy, dy^2/2);
-                    // dL/do = sum e^power dA with e^power = x / o
-                    vals[0] = -vals[0];
-                    vals[1] = -vals[1];
-                    vals[2] *= -0.5f;
-                    vals[3] = -vals[3];
-                    vals[4] *= -0.5f;
-                    vals[5] *= nat.w;
-                    warp_reduce_add10(vals, g2d + (int64_t)s_slot[i] * G2D_STRIDE);
+                    const float sum = warp_reduce10(vals);
+                    if (red_idx >= 0)
+                        atomicAdd(g2d + (int64_t)s_slot[i] * G2D_STRIDE + red_idx,
+                                  sum * (red_idx == 5 ? nat.w : red_scale));
                 }
             }
         }
