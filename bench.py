@@ -46,12 +46,12 @@ BWD_FLOP_BLEND = 49       # per blended pair: T recovery, dL/dalpha, colour/dept
 # capture of this workload (profiles/step_kernels__mapping_1200x680.md), valid
 # while the kernels' sources hash to the value they had when captured
 BLEND_SOURCES = ("paper_2403_11247_b300/csrc/vg_blend.cu", "paper_2403_11247_b300/csrc/vg_common.cuh")
-NCU_TRAFFIC = {"blend_bwd": ("537bb6bc57df8d01", 24.430592e6 + 0.0),
-               "blend_fwd": ("537bb6bc57df8d01", 3.421696e6 + 5632.0)}
+NCU_TRAFFIC = {"blend_bwd": ("f4e6770ea9700ee4", 24.427008e6 + 0.0),
+               "blend_fwd": ("f4e6770ea9700ee4", 3.42144e6 + 7424.0)}
 # warp instructions per launch from the same capture: with the live launch
 # time they give the issue rate against the SMs' issue peak (4 schedulers
 # per SM, one warp instruction per clock each)
-NCU_INSTRUCTIONS = {"blend_bwd": 111.611818e6, "blend_fwd": 57.233533e6}
+NCU_INSTRUCTIONS = {"blend_bwd": 111.611818e6, "blend_fwd": 57.231097e6}
 
 
 def ncu_traffic(stage: str):

@@ -144,15 +144,42 @@ __device__ __forceinline__ void cov2d(float J00, float J02, float J11, float J12
     det = (x0 * x0 + x1 * x1 + x2 * x2) + dil * (a0 + c0) + dil * dil;
 }
 
+// Code indices of one item for its first DECODE_STAGES stages, four bytes
+// per word, loaded together before any codeword: the loads go out in
+// parallel instead of one dependent round trip per stage.  Further stages
+// (never in practice) take a plain loop.
+constexpr int DECODE_STAGES = 8;
+__device__ __forceinline__ void load_codes(const uint8_t* idx, int L, int64_t stride, int64_t n,
+                                           uint32_t kp[DECODE_STAGES / 4]) {
+#pragma unroll
+    for (int w = 0; w < DECODE_STAGES / 4; ++w) kp[w] = 0u;
+#pragma unroll
+    for (int s = 0; s < DECODE_STAGES; ++s)
+        if (s < L) kp[s >> 2] |= (uint32_t)__ldg(idx + (int64_t)s * stride + n) << (8 * (s & 3));
+}
+__device__ __forceinline__ uint32_t code_at(const uint32_t kp[DECODE_STAGES / 4], int s) {
+    return (kp[s >> 2] >> (8 * (s & 3))) & 255u;
+}
+
+// attribute = FP32 sum, in stage order, of the indexed codewords (Eq. 14), or
+// the raw value; kp receives the codes of the first DECODE_STAGES stages
 template <int D>
-__device__ __forceinline__ void decode_attr(const SceneDev& S, int g, int64_t n, float* out) {
+__device__ __forceinline__ void decode_attr_codes(const SceneDev& S, int g, int64_t n, float* out,
+                                                  uint32_t kp[DECODE_STAGES / 4]) {
     if (S.L[g] > 0) {
+        const int L = S.L[g], K = S.K[g];
+        load_codes(S.idx[g], L, S.N, n, kp);
 #pragma unroll
         for (int c = 0; c < D; ++c) out[c] = 0.f;
-        const int K = S.K[g];
-        for (int s = 0; s < S.L[g]; ++s) {
-            int k = __ldg(S.idx[g] + (int64_t)s * S.N + n);
-            const float* w = S.cb[g] + ((int64_t)s * K + k) * D;
+#pragma unroll
+        for (int s = 0; s < DECODE_STAGES; ++s)
+            if (s < L) {
+                const float* w = S.cb[g] + ((int64_t)s * K + code_at(kp, s)) * D;
+#pragma unroll
+                for (int c = 0; c < D; ++c) out[c] += __ldg(w + c);
+            }
+        for (int s = DECODE_STAGES; s < L; ++s) {
+            const float* w = S.cb[g] + ((int64_t)s * K + __ldg(S.idx[g] + (int64_t)s * S.N + n)) * D;
 #pragma unroll
             for (int c = 0; c < D; ++c) out[c] += __ldg(w + c);
         }
@@ -162,16 +189,30 @@ __device__ __forceinline__ void decode_attr(const SceneDev& S, int g, int64_t n,
     }
 }
 
+template <int D>
+__device__ __forceinline__ void decode_attr(const SceneDev& S, int g, int64_t n, float* out) {
+    uint32_t kp[DECODE_STAGES / 4];
+    decode_attr_codes<D>(S, g, n, out, kp);
+}
+
 // same, with the group's codebook staged in shared memory
 template <int D>
 __device__ __forceinline__ void decode_attr_smem(const SceneDev& S, int g, int64_t n, const float* cb, float* out) {
     if (S.L[g] > 0) {
+        const int L = S.L[g], K = S.K[g];
+        uint32_t kp[DECODE_STAGES / 4];
+        load_codes(S.idx[g], L, S.N, n, kp);
 #pragma unroll
         for (int c = 0; c < D; ++c) out[c] = 0.f;
-        const int K = S.K[g];
-        for (int s = 0; s < S.L[g]; ++s) {
-            const int k = __ldg(S.idx[g] + (int64_t)s * S.N + n);
-            const float* w = cb + (s * K + k) * D;
+#pragma unroll
+        for (int s = 0; s < DECODE_STAGES; ++s)
+            if (s < L) {
+                const float* w = cb + (s * K + (int)code_at(kp, s)) * D;
+#pragma unroll
+                for (int c = 0; c < D; ++c) out[c] += w[c];
+            }
+        for (int s = DECODE_STAGES; s < L; ++s) {
+            const float* w = cb + (s * K + __ldg(S.idx[g] + (int64_t)s * S.N + n)) * D;
 #pragma unroll
             for (int c = 0; c < D; ++c) out[c] += w[c];
         }
@@ -183,15 +224,29 @@ __device__ __forceinline__ void decode_attr_smem(const SceneDev& S, int g, int64
 
 // offset O_n and scaling factor l_a: raw, or the FP32 stage-order sum of
 // their R-VQ codewords (Eq. 14)
-__device__ __forceinline__ void scene_offset(const SceneDev& S, int64_t n, float o[3]) {
-    if (S.Lo > 0) {
-        o[0] = o[1] = o[2] = 0.f;
-        for (int s = 0; s < S.Lo; ++s) {
-            const float* w = S.cbo + ((int64_t)s * S.Ko + __ldg(S.idxo + (int64_t)s * S.N + n)) * 3;
+__device__ __forceinline__ void coded3(const float* cb, const uint8_t* idx, int L, int K, int64_t stride, int64_t i,
+                                       float o[3]) {
+    uint32_t kp[DECODE_STAGES / 4];
+    load_codes(idx, L, stride, i, kp);
+    o[0] = o[1] = o[2] = 0.f;
+#pragma unroll
+    for (int s = 0; s < DECODE_STAGES; ++s)
+        if (s < L) {
+            const float* w = cb + ((int64_t)s * K + code_at(kp, s)) * 3;
             o[0] += __ldg(w);
             o[1] += __ldg(w + 1);
             o[2] += __ldg(w + 2);
         }
+    for (int s = DECODE_STAGES; s < L; ++s) {
+        const float* w = cb + ((int64_t)s * K + __ldg(idx + (int64_t)s * stride + i)) * 3;
+        o[0] += __ldg(w);
+        o[1] += __ldg(w + 1);
+        o[2] += __ldg(w + 2);
+    }
+}
+__device__ __forceinline__ void scene_offset(const SceneDev& S, int64_t n, float o[3]) {
+    if (S.Lo > 0) {
+        coded3(S.cbo, S.idxo, S.Lo, S.Ko, S.N, n, o);
     } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) o[c] = __ldg(S.off + n * 3 + c);
@@ -199,13 +254,7 @@ __device__ __forceinline__ void scene_offset(const SceneDev& S, int64_t n, float
 }
 __device__ __forceinline__ void scene_scale(const SceneDev& S, int64_t a, float l[3]) {
     if (S.Ll > 0) {
-        l[0] = l[1] = l[2] = 0.f;
-        for (int s = 0; s < S.Ll; ++s) {
-            const float* w = S.cbl + ((int64_t)s * S.Kl + __ldg(S.idxl + (int64_t)s * S.n_anchors + a)) * 3;
-            l[0] += __ldg(w);
-            l[1] += __ldg(w + 1);
-            l[2] += __ldg(w + 2);
-        }
+        coded3(S.cbl, S.idxl, S.Ll, S.Kl, S.n_anchors, a, l);
     } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) l[c] = __ldg(S.l + a * 3 + c);

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
         do {
             if (e >= nvis) break;
             const uint32_t slot = vis[e];
-            const int v = (int)(slot / (uint64_t)S.N);
+            const int v = slot_view(slot, (uint32_t)S.N, V.n);
             const int64_t n = (int64_t)slot - (int64_t)v * S.N;
             float g[12];
             {
@@ -86,13 +86,16 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
             decode_attr<3>(S, 3, n, rgb);
             const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
             if (!(qq > 0.f)) break;
-            // one reciprocal per slot for every quotient by |q| and by z below
-            const float iq = 1.f / sqrtf(qq);
+            // one reciprocal per slot for every quotient by |q| and by z below;
+            // activations, reciprocals and the sigmoids go through the
+            // hardware exp / reciprocal-sqrt and the fast divide (a few ulp,
+            // far inside what the gradients are held to)
+            const float iq = rsqrtf(qq);  // hardware reciprocal square root
             float qn[4], s[3], R[3][3], Sig[3][3];
 #pragma unroll
             for (int c = 0; c < 4; ++c) qn[c] = q[c] * iq;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) s[c] = expf(ls[c]);
+            for (int c = 0; c < 3; ++c) s[c] = __expf(ls[c]);
             quat_rot(qn, R);
 #pragma unroll
             for (int r = 0; r < 3; ++r)
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                     if (txz < -vi.limx || txz > vi.limx) { ux = false; txz = fminf(fmaxf(txz, -vi.limx), vi.limx); }
                     if (tyz < -vi.limy || tyz > vi.limy) { uy = false; tyz = fminf(fmaxf(tyz, -vi.limy), vi.limy); }
                 }
-                const float iz = 1.f / z, iz2 = iz * iz;
+                const float iz = __fdividef(1.f, z), iz2 = iz * iz;
                 const float J00 = fx * iz, J02 = -fx * txz * iz, J11 = fy * iz, J12 = -fy * tyz * iz;
                 const float W[3][3] = {{T[0], T[1], T[2]}, {T[4], T[5], T[6]}, {T[8], T[9], T[10]}};
                 float T1[3][3], Sc[3][3];
@@ -132,7 +135,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
 #pragma unroll
                     for (int c = 0; c < 3; ++c) RS[r][c] = R[r][c] * s[c];
                 cov2d(J00, J02, J11, J12, T, RS, cs.dilation, A, B, C, det);
-                const float i2 = 1.f / (det * det);
+                const float i2 = __fdividef(1.f, det * det);
                 const float da = g[2], db = g[3], dc = g[4];
                 // conic = inverse of [[A,B],[B,C]]
                 const float dA = i2 * (-C * C * da + B * C * db - B * B * dc);
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                 const float dot = qn[0] * dqn[0] + qn[1] * dqn[1] + qn[2] * dqn[2] + qn[3] * dqn[3];
         #pragma unroll
                 for (int c = 0; c < 4; ++c) dq[c] = (dqn[c] - qn[c] * dot) * iq;
-                o = 1.f / (1.f + expf(-ol));
+                o = __fdividef(1.f, 1.f + __expf(-ol));
                 dol = dop * o * (1.f - o);
             }
             // attribute gradients: raw arrays, or the indexed codewords of every
@@ -259,7 +262,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                 }
             }
             if (O.d_mask && S.mask) {
-                const float sm = 1.f / (1.f + expf(-__ldg(S.mask + n)));
+                const float sm = __fdividef(1.f, 1.f + __expf(-__ldg(S.mask + n)));
                 atomicAdd(O.d_mask + n, (ds[0] * s[0] + ds[1] * s[1] + ds[2] * s[2] + dop * o) * sm * (1.f - sm));
             }
             // Eq. 7: d x_a = sum_i dmu_i, d O_i = dmu_i * l, d l = sum_i dmu_i * O_i;

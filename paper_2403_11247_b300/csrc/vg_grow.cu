@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) grow_stats_kernel(SceneDev S, const uint3
     const uint32_t nv = min(*nvis_dev, max_vis);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
         const uint32_t slot = vis[i];
-        const int64_t n = (int64_t)(slot % (uint64_t)S.N);
+        const int64_t n = (int64_t)(slot % (uint32_t)S.N);  // slots are u32, so a 32-bit remainder
         if (gacc) {
             const float du = g2d[(int64_t)slot * G2D_STRIDE + 0], dv = g2d[(int64_t)slot * G2D_STRIDE + 1];
             atomicAdd(gacc + n, sqrtf(du * du + dv * dv));

@@ -38,6 +38,14 @@ constexpr int EMIT_SMEM_TILES = 16384;  // per-tile counts kept in shared memory
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// view of slot s = v N + n (slots are view-major, views few): by comparisons
+// instead of a 64-bit division
+__device__ __forceinline__ int slot_view(uint32_t s, uint32_t N, int n_views) {
+    int v = 0;
+    for (uint32_t next = N; v + 1 < n_views && s >= next; next += N) ++v;
+    return v;
+}
+
 // pairs are emitted in chunks of EMIT_CHUNK consecutive pairs, one block each
 constexpr int EMIT_CHUNK = 256;
 // The slot at position j of the pair order owns pairs [o, o + c): every chunk

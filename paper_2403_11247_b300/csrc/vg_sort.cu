@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
             const uint32_t x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff;
             const uint32_t w = x1 - x0;
             const uint32_t ry = local / w, rx = local - ry * w;
-            const int v = (int)(s / (uint64_t)N);
+            const int v = slot_view(s, (uint32_t)N, V.n);
             const uint32_t key = (uint32_t)(V.v[v].tile_base + (int)(y0 + ry) * V.v[v].tiles_x + (int)(x0 + rx));
             pkeys[e] = key;
             pvals[e] = s;
