@@ -77,14 +77,16 @@ __device__ __forceinline__ bool warp_hits(const float4 g, const float4 co, float
         const float t1 = co.x * dx * dx, t2 = co.y * dx * dy, t3 = co.z * dy * dy;
         return (t1 + t2 + t3) + 1e-5f * (fabsf(t1) + fabsf(t2) + fabsf(t3));
     };
+    // (the vertex through the fast divide: a vertex off by a few ulp lowers
+    // the parabola's value there by far less than the margin)
     float best = -INFINITY;
     if (cx != g.x) {  // edge px = cx, dy over [v - Y1, v - Y0]
         const float dx = g.x - cx;
-        best = fmaxf(best, p2up(dx, fminf(fmaxf(-co.y * dx / (2.f * co.z), g.y - Y1), g.y - Y0)));
+        best = fmaxf(best, p2up(dx, fminf(fmaxf(__fdividef(-co.y * dx, 2.f * co.z), g.y - Y1), g.y - Y0)));
     }
     if (cy != g.y) {  // edge py = cy, dx over [u - X1, u - X0]
         const float dy = g.y - cy;
-        best = fmaxf(best, p2up(fminf(fmaxf(-co.y * dy / (2.f * co.x), g.x - X1), g.x - X0), dy));
+        best = fmaxf(best, p2up(fminf(fmaxf(__fdividef(-co.y * dy, 2.f * co.x), g.x - X1), g.x - X0), dy));
     }
     return best >= co.w - (1e-3f + 1e-3f * fabsf(co.w));
 }
