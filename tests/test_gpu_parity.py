@@ -256,6 +256,14 @@ def test_backward_room_rvq_mask(cuda, ppt_fwd, ppt_bwd):
                     ppt_fwd=ppt_fwd, ppt_bwd=ppt_bwd)
 
 
+def test_backward_ten_stage_codebooks(cuda):
+    """Ten R-VQ stages per group: the decode loads the codes of the first
+    eight stages together and takes the last two one by one; images, 2D
+    gradients and codebook gradients must match all the same."""
+    sc = synth.box_scene(46, 1500, coded=True, L=10, K=16, frac_masked=0.2, k=2, offset_std=0.05)
+    backward_parity(sc, [synth.tiny_camera()], "bwd-l10")
+
+
 def test_backward_two_views(cuda):
     backward_parity(small_room(2000), [small_room_cam(200, 120, 100.0), small_room_cam(160, 96, 80.0, seed=7)],
                     "bwd-2v")
