@@ -885,9 +885,10 @@ vg_status vg_loss_l1_masked(int32_t n_views, int64_t n_pix, const float* C, cons
     const bool prof_graph = capturing(st);
     const bool prof_on = ctx->prof.on;
     if (dS) VG_CUDA(cudaMemsetAsync(dS, 0, (size_t)n_views * n_pix * 4, st));
-    // words 4..6 of the loss scratch: kept zero between calls by the kernels
+    // words 4..7 of the loss scratch: kept zero between calls by the kernels
     VG_STAGE(VG_STAGE_LOSS, launch_loss_l1(n_views, n_pix, C, D, S, Ct, Dt, pixel_mask, w_depth, gate, dC, dD, loss,
-                                           ctx->loss_scratch.as<uint32_t>() + 4, st));
+                                           ctx->loss_scratch.as<uint32_t>() + 4,
+                                           ctx->state.as<uint32_t>() + ST_ERR, st));
     return VG_OK;
 }
 

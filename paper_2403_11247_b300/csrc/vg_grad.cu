@@ -604,17 +604,146 @@ __global__ void loss_l1_kernel(int64_t n_pix, int64_t total, const float* __rest
     }
 }
 
+// The same loss in one cooperative launch (every block resident): the blocks
+// count the valid target depths and sampled pixels, meet at a grid-wide
+// barrier (bounded: a spin that runs out flags ERR_WAIT), then write the
+// gradient images and sum the loss.  ctl: [0] valid depths, [1] sampled
+// pixels, [2] blocks arrived, [3] blocks done; the last block done clears
+// all four for the next call.  Four pixels per step (16-byte aligned planes).
+__global__ void __launch_bounds__(256) loss_l1_coop_kernel(
+    int64_t n_pix, int n_views, const float* __restrict__ C, const float* __restrict__ D, const float* __restrict__ S,
+    const float* __restrict__ Ct, const float* __restrict__ Dt, const uint8_t* __restrict__ mask, float w_depth,
+    float gate, uint32_t* ctl, float* __restrict__ dC, float* __restrict__ dD, float* __restrict__ loss, uint32_t* err) {
+    __shared__ float s_tmp[8];
+    __shared__ uint32_t s_cnt[2];
+    const uint32_t q_view = (uint32_t)(n_pix / 4), n_q = q_view * (uint32_t)n_views;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    // phase 1: counts over every view's target depth (and ray mask)
+    uint32_t c = 0, ns = 0;
+    for (uint32_t q = tid; q < n_q; q += nthr) {
+        const float4 d = reinterpret_cast<const float4*>(Dt)[q];
+        if (mask) {
+            const uchar4 m = reinterpret_cast<const uchar4*>(mask)[q];
+            c += (m.x && d.x > 0.f) + (m.y && d.y > 0.f) + (m.z && d.z > 0.f) + (m.w && d.w > 0.f);
+            ns += (m.x != 0) + (m.y != 0) + (m.z != 0) + (m.w != 0);
+        } else {
+            c += (d.x > 0.f) + (d.y > 0.f) + (d.z > 0.f) + (d.w > 0.f);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        ns += __shfl_xor_sync(0xffffffffu, ns, o);
+    }
+    if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        if (c) atomicAdd(&s_cnt[0], c);
+        if (ns) atomicAdd(&s_cnt[1], ns);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_cnt[0]) atomicAdd(ctl + 0, s_cnt[0]);
+        if (mask && s_cnt[1]) atomicAdd(ctl + 1, s_cnt[1]);
+        if (blockIdx.x == 0) *loss = 0.f;
+        __threadfence();
+        atomicAdd(ctl + 2, 1u);
+        const volatile uint32_t* arrived = ctl + 2;
+        uint32_t polls = 0;
+        while (*arrived < gridDim.x && ++polls < SPIN_LIMIT) {
+        }
+        if (polls >= SPIN_LIMIT) atomicOr(err, ERR_WAIT);
+        __threadfence();
+        s_cnt[0] = *(const volatile uint32_t*)(ctl + 0);
+        s_cnt[1] = *(const volatile uint32_t*)(ctl + 1);
+    }
+    __syncthreads();
+    // phase 2: gradient images and the loss
+    const float nv = (float)s_cnt[0];
+    const float nsamp = mask ? (float)s_cnt[1] : (float)((int64_t)n_views * n_pix);
+    const float inv_c = nsamp > 0.f ? 1.f / (3.f * nsamp) : 0.f;
+    const float inv_d = nv > 0.f ? w_depth / nv : 0.f;
+    float acc = 0.f;
+    for (uint32_t q = tid; q < n_q; q += nthr) {
+        const uint32_t v = q / q_view, i = q - v * q_view;
+        const float4* c4 = reinterpret_cast<const float4*>(C) + (int64_t)v * 3 * q_view;
+        const float4* t4 = reinterpret_cast<const float4*>(Ct) + (int64_t)v * 3 * q_view;
+        const float4 c0 = c4[i], c1 = c4[q_view + i], c2 = c4[2 * q_view + i];
+        const float4 t0 = t4[i], t1 = t4[q_view + i], t2 = t4[2 * q_view + i];
+        const float4 d = reinterpret_cast<const float4*>(D)[q], dt = reinterpret_cast<const float4*>(Dt)[q];
+        float4 sv = make_float4(1.f, 1.f, 1.f, 1.f);
+        if (gate >= 0.f) sv = reinterpret_cast<const float4*>(S)[q];
+        uchar4 ms = make_uchar4(1, 1, 1, 1);
+        if (mask) ms = reinterpret_cast<const uchar4*>(mask)[q];
+        float4 g0, g1, g2, gd;
+        acc += loss_pixel(c0.x, c1.x, c2.x, t0.x, t1.x, t2.x, d.x, dt.x, sv.x, gate, inv_c, inv_d, g0.x, g1.x, g2.x,
+                          gd.x, ms.x != 0);
+        acc += loss_pixel(c0.y, c1.y, c2.y, t0.y, t1.y, t2.y, d.y, dt.y, sv.y, gate, inv_c, inv_d, g0.y, g1.y, g2.y,
+                          gd.y, ms.y != 0);
+        acc += loss_pixel(c0.z, c1.z, c2.z, t0.z, t1.z, t2.z, d.z, dt.z, sv.z, gate, inv_c, inv_d, g0.z, g1.z, g2.z,
+                          gd.z, ms.z != 0);
+        acc += loss_pixel(c0.w, c1.w, c2.w, t0.w, t1.w, t2.w, d.w, dt.w, sv.w, gate, inv_c, inv_d, g0.w, g1.w, g2.w,
+                          gd.w, ms.w != 0);
+        float4* gc4 = reinterpret_cast<float4*>(dC) + (int64_t)v * 3 * q_view;
+        gc4[i] = g0;
+        gc4[q_view + i] = g1;
+        gc4[2 * q_view + i] = g2;
+        reinterpret_cast<float4*>(dD)[q] = gd;
+    }
+    const float t = block_sum_256(acc, s_tmp);
+    if (threadIdx.x == 0) {
+        atomicAdd(loss, t);
+        __threadfence();
+        if (atomicAdd(ctl + 3, 1u) == gridDim.x - 1) {
+            ctl[0] = 0u;
+            ctl[1] = 0u;
+            ctl[2] = 0u;
+            ctl[3] = 0u;
+        }
+    }
+}
+
 cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const float* D, const float* S, const float* Ct,
                            const float* Dt, const uint8_t* mask, float w_depth, float gate, float* dC, float* dD,
-                           float* loss, uint32_t* valid_count, cudaStream_t st) {
+                           float* loss, uint32_t* valid_count, uint32_t* err, cudaStream_t st) {
     const int64_t total = (int64_t)n_views * n_pix;
     int64_t blocks = ceil_div(ceil_div(total > 0 ? total : 1, 4), 256);
     if (blocks > 148 * 8) blocks = 148 * 8;
-    count_launches(2);
-    count_valid_kernel<<<(unsigned)blocks, 256, 0, st>>>(Dt, mask, total, valid_count, loss);
     auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
     const int vec = (n_pix % 4 == 0) && al(C) && al(D) && al(Ct) && al(Dt) && al(dC) && al(dD) &&
                     (gate < 0.f || al(S)) && (reinterpret_cast<uintptr_t>(mask) & 3u) == 0;
+    // one cooperative launch where the device takes them and the planes allow
+    // four pixels per step; otherwise a counting kernel, then the loss kernel
+    static int coop_blocks = -1;
+    if (coop_blocks < 0) {
+        int dev = 0, coop = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, loss_l1_coop_kernel, 256, 0);
+        coop_blocks = coop ? sms * per : 0;
+        cudaGetLastError();
+    }
+    if (vec && coop_blocks > 0 && total / 4 < (int64_t)UINT32_MAX && err) {
+        int64_t g = ceil_div(total / 4, 256);
+        if (g > coop_blocks) g = coop_blocks;
+        if (g < 1) g = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)g);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        count_launches(1);
+        return cudaLaunchKernelEx(&cfg, loss_l1_coop_kernel, n_pix, n_views, C, D, S, Ct, Dt, mask, w_depth, gate,
+                                  valid_count, dC, dD, loss, err);
+    }
+    count_launches(2);
+    count_valid_kernel<<<(unsigned)blocks, 256, 0, st>>>(Dt, mask, total, valid_count, loss);
     int64_t bx = ceil_div(vec ? ceil_div(n_pix, 4) : n_pix, 256);
     if (bx > 148 * 8) bx = 148 * 8;
     loss_l1_kernel<<<dim3((unsigned)bx, (unsigned)n_views), 256, 0, st>>>(n_pix, total, C, D, S, Ct, Dt, mask, w_depth,

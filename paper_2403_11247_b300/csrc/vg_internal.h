@@ -176,11 +176,12 @@ cudaError_t launch_pose_final(int n_views, const float* pose_sum, const float* i
 cudaError_t launch_sample_rays(uint8_t* mask, int64_t n, unsigned long long seed, const int32_t* round_dev,
                                int32_t round_host, unsigned long long keep_below, cudaStream_t st);
 // mask non-NULL: only sampled pixels count (vg_loss_l1_masked).  valid_count:
-// three words, zero before the first call; the call leaves them zero (no memset
-// between calls) and writes loss[0] itself
+// four words, zero before the first call; the call leaves them zero (no memset
+// between calls) and writes loss[0] itself.  err: the ctx's status word (the
+// single-launch form's barrier reports a spin that ran out there)
 cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const float* D, const float* S,
                            const float* Ct, const float* Dt, const uint8_t* mask, float w_depth, float gate, float* dC,
-                           float* dD, float* loss, uint32_t* valid_count, cudaStream_t st);
+                           float* dD, float* loss, uint32_t* valid_count, uint32_t* err, cudaStream_t st);
 
 // optim.cu
 cudaError_t launch_adam(int n, float* const* p, const float* const* g, float* const* m, float* const* v,
