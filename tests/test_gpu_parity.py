@@ -291,10 +291,14 @@ def test_pose_grad_with_icp(cuda):
     assert np.allclose(loss.cpu().numpy(), oloss, rtol=1e-5)
 
 
-def test_loss_l1_matches_oracle(cuda):
+@pytest.mark.parametrize("n", [3001, 3000])
+def test_loss_l1_matches_oracle(cuda, n):
+    """n = 3001: the counting kernel, then the loss kernel; n = 3000 (aligned
+    planes, four pixels per step): the single cooperative launch.  Two calls
+    each, so the counters must come back to zero between calls."""
     torch = cuda
     rng = np.random.default_rng(3)
-    nv, n = 2, 3001
+    nv = 2
     C_, Ct = rng.uniform(size=(2, nv * 3 * n)).astype(np.float32)
     D_, Dt, S_ = rng.uniform(0, 3, size=(3, nv * n)).astype(np.float32)
     S_ = rng.uniform(size=nv * n).astype(np.float32)
