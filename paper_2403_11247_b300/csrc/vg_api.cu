@@ -181,7 +181,7 @@ struct vg_ctx {
     StageProfiler prof;
     int64_t pair_cap = 0;
     DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, tile_order, Tfin, ncontrib, lookback,
-        scratch, state, pose_part, icp_part, loss_scratch, pair_off, chunk_start, blk_count, blk_base, vis, ssim_ws, grow_ws;
+        scratch, state, pose_part, icp_part, loss_scratch, pair_off, chunk_start, blk_count, vis, ssim_ws, grow_ws;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
     bool tile_sort_failed = false;  // a tile list overflowed the per-tile sort: VG_SORT_AUTO sorts globally
@@ -645,7 +645,6 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     VG_TRY(ctx->chunk_start.ensure((size_t)ceil_div(std::max<int64_t>(ctx->pair_cap, 1), EMIT_CHUNK) * 4, st,
                                    "pair chunk starts"));
     VG_TRY(ctx->blk_count.ensure((size_t)preprocess_blocks(N) * 8, st, "block counts"));
-    VG_TRY(ctx->blk_base.ensure((size_t)preprocess_blocks(N) * 8, st, "block bases"));
     for (int b = 0; b < 2; ++b) {
         VG_TRY(ctx->dkey[b].ensure(slots * 4, st, "depth keys"));
         VG_TRY(ctx->dval[b].ensure(slots * 4, st, "depth values"));
@@ -687,7 +686,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     // compaction also produces their offsets (no separate scan)
     VG_STAGE(VG_STAGE_DEPTH_SORT, ([&]() -> cudaError_t {
                  cudaError_t e = launch_compact(V, N, ctx->dkey[1].as<uint32_t>(), ctx->blk_count.as<uint32_t>(),
-                                                ctx->blk_base.as<uint32_t>(), ctx->dkey[0].as<uint32_t>(),
+                                                ctx->dkey[0].as<uint32_t>(),
                                                 ctx->dval[0].as<uint32_t>(), ctx->vis.as<uint32_t>(),
                                                 ctx->ntiles.as<uint32_t>(),
                                                 tile_sort ? ctx->pair_off.as<uint32_t>() : nullptr,

@@ -69,11 +69,11 @@ cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& c
                               float4* rgbd, uint2* rect, uint32_t* ntiles, uint32_t* dkey, uint32_t* scratch,
                               uint32_t* state, uint32_t* blk_count, cudaStream_t st);
 // visible slots, in (view, Gaussian) order within each preprocess block, to keys_out / vals_out
-// blk_count / blk_base hold [blocks] visible-slot counts, then (pair_off
-// non-NULL) [blocks] pair counts; with pair_off the pair offsets of the
-// compacted order, the chunk starts, the pair count and the overflow flag
-// are produced here and launch_duplicate skips its own scan
-cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count, uint32_t* blk_base,
+// blk_count holds [blocks] visible-slot counts, then (pair_off non-NULL)
+// [blocks] pair counts; with pair_off the pair offsets of the compacted
+// order, the chunk starts, the pair count and the overflow flag are produced
+// here and launch_duplicate skips its own scan
+cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count,
                            uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, const uint32_t* ntiles,
                            uint32_t* pair_off, uint32_t* chunk_start, uint32_t cap, uint32_t* scratch, uint32_t* err,
                            cudaStream_t st);

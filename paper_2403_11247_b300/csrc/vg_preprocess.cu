@@ -240,95 +240,37 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(SceneDev S, const __
     }
 }
 
-// exclusive scans of the per-block counts (one block): arrays = 1, the
-// visible-slot counts; arrays = 2, those and the per-block pair counts that
-// follow them, scanned together (two consecutive blocks per thread, so one
-// pass covers 2048 blocks), whose total becomes the pair count of the forward
-// (flagged when above cap) and the sentinel pair_off[visible slots]
-__global__ void __launch_bounds__(1024) block_scan_kernel(const uint32_t* __restrict__ cnt, int n, int arrays,
-                                                          uint32_t* __restrict__ base, uint32_t* __restrict__ scratch,
-                                                          uint32_t* __restrict__ pair_off, uint32_t cap,
-                                                          uint32_t* __restrict__ err) {
-    __shared__ uint2 s_w[32];
-    __shared__ uint2 s_carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool two = arrays == 2;
-    if (threadIdx.x == 0) s_carry = make_uint2(0u, 0u);
-    __syncthreads();
-    for (int c0 = 0; c0 < n; c0 += 2 * 1024) {
-        const int i0 = c0 + 2 * (int)threadIdx.x;
-        const uint32_t a0 = i0 < n ? cnt[i0] : 0u, a1 = i0 + 1 < n ? cnt[i0 + 1] : 0u;
-        const uint32_t b0 = two && i0 < n ? cnt[n + i0] : 0u, b1 = two && i0 + 1 < n ? cnt[n + i0 + 1] : 0u;
-        const uint32_t ta = a0 + a1, tb = b0 + b1;
-        uint32_t ia = ta, ib = tb;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t ya = __shfl_up_sync(0xffffffffu, ia, o);
-            const uint32_t yb = __shfl_up_sync(0xffffffffu, ib, o);
-            if (lane >= o) {
-                ia += ya;
-                ib += yb;
-            }
-        }
-        if (lane == 31) s_w[warp] = make_uint2(ia, ib);
-        __syncthreads();
-        if (warp == 0) {
-            uint2 t = s_w[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t ya = __shfl_up_sync(0xffffffffu, t.x, o);
-                const uint32_t yb = __shfl_up_sync(0xffffffffu, t.y, o);
-                if (lane >= o) {
-                    t.x += ya;
-                    t.y += yb;
-                }
-            }
-            s_w[lane] = t;  // inclusive warp prefixes
-        }
-        __syncthreads();
-        const uint2 wp = warp ? s_w[warp - 1] : make_uint2(0u, 0u);
-        const uint32_t pa = s_carry.x + wp.x + ia - ta, pb = s_carry.y + wp.y + ib - tb;
-        if (i0 < n) {
-            base[i0] = pa;
-            if (two) base[n + i0] = pb;
-        }
-        if (i0 + 1 < n) {
-            base[i0 + 1] = pa + a0;
-            if (two) base[n + i0 + 1] = pb + b0;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            s_carry.x += s_w[31].x;
-            s_carry.y += s_w[31].y;
-        }
-        __syncthreads();
-    }
-    if (two && threadIdx.x == 0) {
-        const uint32_t pairs = s_carry.y;
-        scratch[SCR_PAIRS] = pairs;
-        if (pairs > cap) atomicOr(err, ERR_OVERFLOW);
-        pair_off[s_carry.x] = pairs;
-    }
-}
-
 // order-preserving compaction of the visible slots: block b of the preprocess
 // grid covers Gaussians [256 b, 256 b + 256) of every view; its visible slots
-// go, view by view and in Gaussian order, to [base[b], base[b] + count[b]);
-// vals_copy (may be NULL) keeps that slot order for the backward's per-slot
-// passes (the depth sort overwrites vals_out).  With pair_off (the forms that
-// keep this order for the pairs), the slot at position j also gets its first
-// pair, pair_off[j] (exclusive scan of the tile counts in this order), and
-// marks the 256-pair chunks that start inside its pairs.
+// go, view by view and in Gaussian order, to [base, base + count[b]), where
+// base = count[0] + ... + count[b - 1] is summed by the block itself from the
+// preprocess's per-block counts (at most a few thousand words, read from L2:
+// cheaper than a separate scan launch).  vals_copy (may be NULL) keeps that
+// slot order for the backward's per-slot passes (the depth sort overwrites
+// vals_out).  With pair_off (the forms that keep this order for the pairs),
+// the slot at position j also gets its first pair, pair_off[j] (exclusive
+// scan of the tile counts in this order, from the per-block pair counts that
+// follow the slot counts), and marks the 256-pair chunks that start inside
+// its pairs; the last block writes the pair count (flagged when above cap)
+// and the sentinel pair_off[visible slots].
 __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Views V, int64_t N,
                                                       const uint32_t* __restrict__ dkey,
-                                                      const uint32_t* __restrict__ base, uint32_t* __restrict__ keys_out,
+                                                      const uint32_t* __restrict__ cnt, uint32_t* __restrict__ keys_out,
                                                       uint32_t* __restrict__ vals_out, uint32_t* __restrict__ vals_copy,
                                                       const uint32_t* __restrict__ ntiles, uint32_t* __restrict__ pair_off,
-                                                      uint32_t* __restrict__ chunk_start, uint32_t cap) {
+                                                      uint32_t* __restrict__ chunk_start, uint32_t cap,
+                                                      uint32_t* __restrict__ scratch, uint32_t* __restrict__ err) {
     __shared__ uint32_t s_tmp[8];
     const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    uint32_t off = base[blockIdx.x];
-    uint32_t poff = pair_off ? base[gridDim.x + blockIdx.x] : 0u;
+    const int b = (int)blockIdx.x, nb = (int)gridDim.x;
+    uint32_t a = 0, p = 0;
+    for (int j = threadIdx.x; j < b; j += 256) {
+        a += cnt[j];
+        if (pair_off) p += cnt[nb + j];
+    }
+    uint32_t off, poff = 0;
+    block_excl_scan_256(a, s_tmp, &off);
+    if (pair_off) block_excl_scan_256(p, s_tmp, &poff);
     for (int v = 0; v < V.n; ++v) {
         const int64_t slot = (int64_t)v * N + n;
         const uint32_t key = n < N ? dkey[slot] : 0xffffffffu;
@@ -351,6 +293,11 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
             poff += ctot;
         }
         off += tot;
+    }
+    if (pair_off && b == nb - 1 && threadIdx.x == 0) {
+        scratch[SCR_PAIRS] = poff;
+        if (poff > cap) atomicOr(err, ERR_OVERFLOW);
+        pair_off[off] = poff;
     }
 }
 
@@ -376,17 +323,14 @@ cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& c
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count, uint32_t* blk_base,
+cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count,
                            uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, const uint32_t* ntiles,
                            uint32_t* pair_off, uint32_t* chunk_start, uint32_t cap, uint32_t* scratch, uint32_t* err,
                            cudaStream_t st) {
     const int blocks = preprocess_blocks(N);
-    count_launches(2);
-    block_scan_kernel<<<1, 1024, 0, st>>>(blk_count, blocks, pair_off ? 2 : 1, blk_base, scratch, pair_off, cap, err);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    compact_kernel<<<blocks, 256, 0, st>>>(V, N, dkey, blk_base, keys_out, vals_out, vals_copy, ntiles, pair_off,
-                                           chunk_start, cap);
+    count_launches(1);
+    compact_kernel<<<blocks, 256, 0, st>>>(V, N, dkey, blk_count, keys_out, vals_out, vals_copy, ntiles, pair_off,
+                                           chunk_start, cap, scratch, err);
     return cudaGetLastError();
 }
 
