@@ -738,9 +738,17 @@ cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const flo
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        count_launches(1);
-        return cudaLaunchKernelEx(&cfg, loss_l1_coop_kernel, n_pix, n_views, C, D, S, Ct, Dt, mask, w_depth, gate,
-                                  valid_count, dC, dD, loss, err);
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, loss_l1_coop_kernel, n_pix, n_views, C, D, S, Ct, Dt, mask,
+                                                 w_depth, gate, valid_count, dC, dD, loss, err);
+        if (e == cudaSuccess) {
+            count_launches(1);
+            return e;
+        }
+        // fewer SMs than the occupancy query saw (a shared or partitioned
+        // device): the two-launch form below needs no co-residency
+        if (e != cudaErrorCooperativeLaunchTooLarge) return e;
+        cudaGetLastError();
+        coop_blocks = 0;
     }
     count_launches(2);
     count_valid_kernel<<<(unsigned)blocks, 256, 0, st>>>(Dt, mask, total, valid_count, loss);
