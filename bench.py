@@ -46,12 +46,12 @@ BWD_FLOP_BLEND = 49       # per blended pair: T recovery, dL/dalpha, colour/dept
 # capture of this workload (profiles/step_kernels__mapping_1200x680.md), valid
 # while the kernels' sources hash to the value they had when captured
 BLEND_SOURCES = ("paper_2403_11247_b300/csrc/vg_blend.cu", "paper_2403_11247_b300/csrc/vg_common.cuh")
-NCU_TRAFFIC = {"blend_bwd": ("a5899f08b08b9eb2", 24.423424e6 + 0.0),
-               "blend_fwd": ("a5899f08b08b9eb2", 3.419136e6 + 2560.0)}
+NCU_TRAFFIC = {"blend_bwd": ("a5bebdd73b904de9", 24.4288e6 + 0.0),
+               "blend_fwd": ("a5bebdd73b904de9", 3.418624e6 + 2048.0)}
 # warp instructions per launch from the same capture: with the live launch
 # time they give the issue rate against the SMs' issue peak (4 schedulers
 # per SM, one warp instruction per clock each)
-NCU_INSTRUCTIONS = {"blend_bwd": 111.143092e6, "blend_fwd": 56.322523e6}
+NCU_INSTRUCTIONS = {"blend_bwd": 111.143092e6, "blend_fwd": 51.578011e6}
 
 
 def ncu_traffic(stage: str):

@@ -162,7 +162,9 @@ __device__ __forceinline__ void tile_sort(uint32_t* __restrict__ pvals, uint2 rg
     __syncthreads();  // the sorted list (global) and the freed shared memory are ready for the block
 }
 
-template <int PPT, bool HITS, bool TSORT>
+// COUNT: keep the work counters (evaluated and blended pairs); off in the
+// timed form, whose per-pixel loop then skips their bookkeeping
+template <int PPT, bool HITS, bool TSORT, bool COUNT>
 __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
     uint32_t* __restrict__ pvals, const uint32_t* __restrict__ dkey, uint32_t* __restrict__ err,
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
                     const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                     if (Tn < cs.t_min) {
                         done[k] = true;
-                        stop_at[k] = b - rg.x + i;
+                        if (COUNT) stop_at[k] = b - rg.x + i;
                         continue;
                     }
                     const float w = alpha * T[k];
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
                     acc[k][4] += w;
                     T[k] = Tn;
                     last[k] = b - rg.x + i + 1;
-                    ++nb[k];
+                    if (HITS || COUNT) ++nb[k];
                 }
                 if (HITS) {
 #pragma unroll
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
         ev += stop_at[k] != 0xffffffffu ? stop_at[k] + 1 : rg.y - rg.x;
         bl += nb[k];
     }
-    if (count_evals) {
+    if (COUNT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             ev += __shfl_xor_sync(0xffffffffu, ev, o);
@@ -525,10 +527,14 @@ cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const ui
                              int count_evals, cudaStream_t st) {
     if (V.total_tiles <= 0) return cudaSuccess;
     count_launches(1);
+#define VG_FWD4(P, H, TS, CN)                                                                                   \
+    blend_fwd_kernel<P, H, TS, CN><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, order, pvals, dkey, err, \
+                                                                           xy, conic_o, rgbd, C, D, S, Tfin,     \
+                                                                           ncontrib, evals, blended, count_evals)
 #define VG_FWD3(P, H, TS)                                                                                       \
-    blend_fwd_kernel<P, H, TS><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, order, pvals, dkey, err, xy, \
-                                                                       conic_o, rgbd, C, D, S, Tfin, ncontrib,  \
-                                                                       evals, blended, count_evals)
+    do {                                                                                                        \
+        if (count_evals) VG_FWD4(P, H, TS, true); else VG_FWD4(P, H, TS, false);                                \
+    } while (0)
 #define VG_FWD(P)                                                                                               \
     do {                                                                                                        \
         if (cs.hit_count) {                                                                                     \
@@ -542,6 +548,7 @@ cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const ui
     else VG_FWD(1);
 #undef VG_FWD
 #undef VG_FWD3
+#undef VG_FWD4
     return cudaGetLastError();
 }
 
