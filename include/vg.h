@@ -139,7 +139,8 @@ typedef struct {
  * pose_dev: optional DEVICE array [n_views][12] read instead of the
  *   cameras' T_cw (lets a captured CUDA graph follow poses updated on the
  *   device).  count_evals: accumulate evaluated (pixel, Gaussian) pairs into
- *   the ctx counter (vg_ctx_stats).
+ *   the ctx counter (vg_ctx_stats) and keep each pixel's count
+ *   (VG_BUF_N_EVAL).
  * hit_count, seen: optional DEVICE arrays [N] for the sliding-window mask
  *   (Sec. "Sliding Window-based Online Mask", Eq. 13).  vg_render_fwd ADDS
  *   to hit_count[n] the number of (view, pixel) pairs where Gaussian n is
@@ -304,10 +305,12 @@ vg_status vg_ctx_profile_read(vg_ctx* ctx, vg_stream stream, double* ms_total, i
  *   VG_BUF_RANGES     uint2  [tiles]  [start, end) of each tile's list
  *   VG_BUF_T_FINAL    float  [pixels] transmittance after compositing
  *   VG_BUF_N_CONTRIB  uint32 [pixels] list position + 1 of the last blended Gaussian
- *   VG_BUF_G2D        float  [slots][12] du dv da db dc dopacity dr dg db ddepth, 2 pad */
+ *   VG_BUF_G2D        float  [slots][12] du dv da db dc dopacity dr dg db ddepth, 2 pad
+ *   VG_BUF_N_EVAL     uint32 [pixels] list entries the pixel examined, up to and including the
+ *                                     one that stopped it (forwards with count_evals only) */
 enum {
     VG_BUF_XY = 0, VG_BUF_CONIC, VG_BUF_RGBD, VG_BUF_RECT, VG_BUF_NTILES, VG_BUF_PAIR_KEYS, VG_BUF_PAIR_VALS,
-    VG_BUF_RANGES, VG_BUF_T_FINAL, VG_BUF_N_CONTRIB, VG_BUF_G2D
+    VG_BUF_RANGES, VG_BUF_T_FINAL, VG_BUF_N_CONTRIB, VG_BUF_G2D, VG_BUF_N_EVAL
 };
 vg_status vg_ctx_buffer(const vg_ctx* ctx, int32_t which, const void** ptr, int64_t* bytes);
 

@@ -10,11 +10,19 @@ cap 0.99, skip below 1/255, early stop when transmittance would fall below
 1e-4, 16x16 tiles, 3-sigma radius, 0.3 px^2 low-pass dilation, Jacobian clamp
 at 1.3x the half field of view, near plane 0.2 m.
 
-The flag bands mark pixels whose discrete decisions an FP32 evaluation may
-take the other way: alpha and the exponent carry ~5e-6 relative error in FP32
-(band 5e-5); transmittance after a run of high-alpha Gaussians carries up to
-~sum alpha/(1-alpha) x 1e-6 relative error, a few 1e-4 (band 2e-3); the radius
-3 sqrt(lambda_max) carries ~3e-7 (band 5e-6).
+Near-threshold flags mark pixels whose discrete decisions an FP32 evaluation
+may take the other way.  Each decision is measured against the FP32 error
+bound of the quantity that decides it: the exponent carries q_ulps units in
+the last place per unit of (1 + the condition number of the 2D covariance),
+relative to the magnitudes of its terms (rounding the entries of Sigma'
+moves its small eigenvalue by about lambda_max u); alpha adds a floor of
+decision_band (FP32 opacity, base-2 threshold, exp2); the transmittance
+accumulates alpha / (1 - alpha) times alpha's error plus two roundings per
+blended Gaussian, with a safety factor t_band; the radius 3 sqrt(lambda_max)
+carries ~3e-7 (band r_band = 5e-6).  A Gaussian whose tile membership hangs
+on a borderline radius flags only the pixels where it could be blended.
+Flags are bits 0-4 of ``flags`` (images and gradients); ``ctr_flags`` adds
+the pixels whose tile list may differ by a borderline member (work counters).
 """
 from __future__ import annotations
 
@@ -63,7 +71,7 @@ class _Params(C.Structure):
     _fields_ = [("alpha_max", C.c_double), ("alpha_min", C.c_double), ("t_min", C.c_double),
                 ("dilation", C.c_double), ("sigma_cull", C.c_double), ("clamp_factor", C.c_double),
                 ("jacobian_clamp", C.c_int), ("tile", C.c_int), ("r_band", C.c_double),
-                ("decision_band", C.c_double), ("t_band", C.c_double)]
+                ("decision_band", C.c_double), ("t_band", C.c_double), ("q_ulps", C.c_double)]
 
 
 _lib = None
@@ -84,7 +92,9 @@ def lib():
         _lib.orc_get_bins.argtypes = [P, P, P]
         _lib.orc_get_decoded.argtypes = [P, P]
         _lib.orc_forward.restype = C.c_int64
-        _lib.orc_forward.argtypes = [P] * 8 + [C.c_int]
+        _lib.orc_forward.argtypes = [P] * 10 + [C.c_int]
+        _lib.orc_rect_fp64_diff.restype = C.c_int64
+        _lib.orc_rect_fp64_diff.argtypes = [P, P]
         _lib.orc_backward.argtypes = [P] * 14 + [C.c_int]
         _lib.orc_icp.argtypes = [P, P, P, P, P]
         _lib.orc_loss_l1.restype = C.c_double
@@ -104,7 +114,8 @@ def _p(a: Optional[np.ndarray]):
 
 def default_params(**kw) -> Dict[str, float]:
     p = dict(alpha_max=0.99, alpha_min=1.0 / 255.0, t_min=1e-4, dilation=0.3, sigma_cull=3.0,
-             clamp_factor=1.3, jacobian_clamp=1, tile=16, r_band=5e-6, decision_band=5e-5, t_band=2e-3)
+             clamp_factor=1.3, jacobian_clamp=1, tile=16, r_band=5e-6, decision_band=2e-6, t_band=4.0,
+             q_ulps=64.0)
     p.update(kw)
     return p
 
@@ -283,11 +294,24 @@ class Oracle:
     def forward(self, threads: int = 1):
         P = self.n_pixels
         out = dict(C=np.zeros(3 * P), D=np.zeros(P), S=np.zeros(P), T_final=np.zeros(P),
-                   n_contrib=np.zeros(P, np.int32), n_eval=np.zeros(P, np.int32), flags=np.zeros(P, np.uint8))
+                   n_contrib=np.zeros(P, np.int32), n_eval=np.zeros(P, np.int32), flags=np.zeros(P, np.uint8),
+                   C_abs=np.zeros(3 * P), margin=np.zeros(P))
         tot = lib().orc_forward(self.ctx, _p(out["C"]), _p(out["D"]), _p(out["S"]), _p(out["T_final"]),
-                                _p(out["n_contrib"]), _p(out["n_eval"]), _p(out["flags"]), threads)
+                                _p(out["n_contrib"]), _p(out["n_eval"]), _p(out["flags"]), _p(out["C_abs"]),
+                                _p(out["margin"]), threads)
         out["evaluated"] = int(tot)
+        raw = out["flags"]
+        out["ctr_flags"] = raw != 0            # work counters: any flag, list ambiguity included
+        out["flags"] = raw & np.uint8(31)      # images and gradients
         return out
+
+    def rect_fp64_diff(self):
+        """(slots whose FP64-centre tile rect differs from the FP32 one the
+        binning uses, slots with a borderline radius), over the slots whose
+        FP32 projection reaches the rect stage."""
+        nb = C.c_int64(0)
+        d = lib().orc_rect_fp64_diff(self.ctx, C.byref(nb))
+        return int(d), int(nb.value)
 
     def backward(self, dC, dD, dS, threads: int = 1):
         sc = self.scene

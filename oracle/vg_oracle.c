@@ -72,6 +72,9 @@ typedef struct {
     int radius;
     int rect[4];          /* x0 y0 x1 y1 (tiles) */
     int borderline;
+    double qerr;          /* relative FP32 error bound of the exponent (per unit of its term magnitudes) */
+    int reached;          /* the FP32 projection reached the rect stage */
+    int rect64[4];        /* the rect from the FP64 centre, same radius */
 } proj_t;
 
 typedef struct {
@@ -98,6 +101,8 @@ struct orc_ctx {
     int64_t* list;
     int64_t n_pairs;
     uint8_t* tile_ambiguous;
+    int64_t* amb_start;   /* [n_tiles + 1]: per tile, the slots whose membership hangs on a borderline radius */
+    int64_t* amb_slot;
 };
 
 /* ------------------------------------------------------------------------ */
@@ -241,6 +246,21 @@ static void project_slot(const orc_ctx* ctx, int v, int64_t n, proj_t* P)
     int radius = (int)ceil(rr);
     double nearest = floor(rr + 0.5);
     P->borderline = fabs(rr - nearest) <= prm->r_band * rr;
+    /* FP32 error of the exponent -1/2 d^T Sigma'^-1 d: a few units in the
+     * last place per operation, and rounding the entries of Sigma' (of the
+     * size of lambda_max) moves its small eigenvalue by as much, so the
+     * error grows with the condition number lambda_max / lambda_min */
+    double kappa = lam * lam / det;
+    P->qerr = prm->q_ulps * ldexp(1.0, -24) * (1.0 + kappa);
+    P->reached = 1;
+    {
+        double u64 = cam->fx * x / z + cam->cx, v64 = cam->fy * y / z + cam->cy, T = (double)prm->tile;
+        int TX = ctx->tiles_x[v], TY = ctx->tiles_y[v];
+        int r64[4] = {(int)floor((u64 - radius) / T), (int)floor((v64 - radius) / T),
+                      (int)floor((u64 + radius) / T) + 1, (int)floor((v64 + radius) / T) + 1};
+        int lim[4] = {TX, TY, TX, TY};
+        for (int q = 0; q < 4; ++q) P->rect64[q] = r64[q] < 0 ? 0 : (r64[q] > lim[q] ? lim[q] : r64[q]);
+    }
 
     int TX = ctx->tiles_x[v], TY = ctx->tiles_y[v];
     float Tf = (float)prm->tile, rf = (float)radius;
@@ -407,6 +427,45 @@ orc_ctx* orc_create(const orc_scene* scene, const orc_camera* cams, int n_views,
                 if (!inner) ctx->tile_ambiguous[ctx->tile_base[v] + (int64_t)ty * TX + tx] = 1;
             }
     }
+    /* the same (tile, slot) memberships, listed per tile: counted, then filled */
+    ctx->amb_start = (int64_t*)calloc(ctx->n_tiles + 1, sizeof(int64_t));
+    int64_t n_amb = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        int64_t* fill = NULL;
+        if (pass == 1) {
+            for (int64_t t = 0; t < ctx->n_tiles; ++t) ctx->amb_start[t + 1] += ctx->amb_start[t];
+            n_amb = ctx->amb_start[ctx->n_tiles];
+            ctx->amb_slot = (int64_t*)malloc(sizeof(int64_t) * (n_amb > 0 ? n_amb : 1));
+            fill = (int64_t*)calloc(ctx->n_tiles > 0 ? ctx->n_tiles : 1, sizeof(int64_t));
+        }
+        for (int64_t s = 0; s < slots; ++s) {
+            const proj_t* pr = &ctx->pr[s];
+            if (!pr->borderline || pr->z32 == 0.0f) continue;
+            int v = (int)(s / (N > 0 ? N : 1));
+            int TX = ctx->tiles_x[v], TY = ctx->tiles_y[v];
+            int rr[2] = {pr->radius + 1, pr->radius - 1 > 0 ? pr->radius - 1 : 0};
+            int rc[2][4];
+            float Tf = (float)prm->tile;
+            for (int q = 0; q < 2; ++q) {
+                float rf = (float)rr[q];
+                int x0 = (int)floorf((pr->u32 - rf) / Tf), x1 = (int)floorf((pr->u32 + rf) / Tf) + 1;
+                int y0 = (int)floorf((pr->v32 - rf) / Tf), y1 = (int)floorf((pr->v32 + rf) / Tf) + 1;
+                rc[q][0] = x0 < 0 ? 0 : (x0 > TX ? TX : x0);
+                rc[q][2] = x1 < 0 ? 0 : (x1 > TX ? TX : x1);
+                rc[q][1] = y0 < 0 ? 0 : (y0 > TY ? TY : y0);
+                rc[q][3] = y1 < 0 ? 0 : (y1 > TY ? TY : y1);
+            }
+            for (int ty = rc[0][1]; ty < rc[0][3]; ++ty)
+                for (int tx = rc[0][0]; tx < rc[0][2]; ++tx) {
+                    int inner = tx >= rc[1][0] && tx < rc[1][2] && ty >= rc[1][1] && ty < rc[1][3];
+                    if (inner) continue;
+                    int64_t t = ctx->tile_base[v] + (int64_t)ty * TX + tx;
+                    if (pass == 0) ctx->amb_start[t + 1]++;
+                    else ctx->amb_slot[ctx->amb_start[t] + fill[t]++] = s;
+                }
+        }
+        free(fill);
+    }
     return ctx;
 }
 
@@ -416,6 +475,7 @@ void orc_free(orc_ctx* ctx)
     free(ctx->cams); free(ctx->g); free(ctx->shp); free(ctx->pr);
     free(ctx->tiles_x); free(ctx->tiles_y); free(ctx->tile_base); free(ctx->pix_base); free(ctx->win);
     free(ctx->tile_start); free(ctx->list); free(ctx->tile_ambiguous);
+    free(ctx->amb_start); free(ctx->amb_slot);
     free(ctx);
 }
 
@@ -460,6 +520,19 @@ void orc_get_proj(const orc_ctx* ctx, double* proj, float* bin32, int32_t* flags
     }
 }
 
+int64_t orc_rect_fp64_diff(const orc_ctx* ctx, int64_t* n_borderline)
+{
+    int64_t slots = (int64_t)ctx->nv * ctx->N, diff = 0, nb = 0;
+    for (int64_t s = 0; s < slots; ++s) {
+        const proj_t* P = &ctx->pr[s];
+        if (!P->reached) continue;
+        if (P->borderline) ++nb;
+        if (memcmp(P->rect, P->rect64, sizeof(P->rect)) != 0) ++diff;
+    }
+    if (n_borderline) *n_borderline = nb;
+    return diff;
+}
+
 void orc_get_bins(const orc_ctx* ctx, int64_t* tile_start, int64_t* list)
 {
     if (tile_start) memcpy(tile_start, ctx->tile_start, sizeof(int64_t) * (ctx->n_tiles + 1));
@@ -490,20 +563,41 @@ typedef struct {
     int capped;
 } step_t;
 
+/* Distance of value x from threshold t in units of the error bound
+ * rel * |t| (large when the bound is zero). */
+static double band_units(double x, double t, double rel)
+{
+    double b = rel * fabs(t);
+    return b > 0 ? fabs(x - t) / b : 1e300;
+}
+
 /* Walk one pixel's list front to back.  Fills steps (if non-NULL) with every
- * blended Gaussian; returns the number of blended steps. */
+ * blended Gaussian; returns the number of blended steps.
+ *
+ * Near-threshold bookkeeping (flags, margin): the GPU takes every decision
+ * in FP32, this walk in FP64, so each decision is compared with its
+ * threshold in units of the FP32 error bound of the quantity that decides it.
+ *   exponent power: |error| <= qerr * (sum of the magnitudes of its terms)
+ *   alpha (= opacity e^power): relative error <= decision_band + that
+ *   transmittance: relative error accumulates alpha / (1 - alpha) times the
+ *     relative error of alpha plus two roundings per blended Gaussian.
+ * A decision within its bound (margin <= 1) flags the pixel. */
 static int walk_pixel(const orc_ctx* ctx, int v, int px, int py, step_t* steps,
-                      double out[5], double* T_final, int32_t* n_contrib, int32_t* n_eval, uint8_t* flag)
+                      double out[5], double* T_final, int32_t* n_contrib, int32_t* n_eval, uint8_t* flag,
+                      double cabs[3], double* margin_out)
 {
     const orc_params* prm = &ctx->prm;
+    const double u32 = ldexp(1.0, -24);
     int tile = prm->tile;
     int64_t key = ctx->tile_base[v] + (int64_t)(py / tile) * ctx->tiles_x[v] + px / tile;
     int64_t b = ctx->tile_start[key], e = ctx->tile_start[key + 1];
-    double T = 1.0, C0 = 0, C1 = 0, C2 = 0, Dd = 0, Ss = 0;
+    double T = 1.0, C0 = 0, C1 = 0, C2 = 0, Dd = 0, Ss = 0, A0 = 0, A1 = 0, A2 = 0;
+    double eT = 0.0;         /* relative FP32 error bound of T */
+    double margin = 1e300;
     int m = 0;
     int32_t last = 0, evals = 0;
-    uint8_t f = ctx->tile_ambiguous[key] ? 8 : 0;
-    double band = prm->decision_band;
+    int64_t stop_slot = -1;  /* the list entry at which the pixel stopped */
+    uint8_t f = 0;
     for (int64_t j = b; j < e; ++j) {
         int64_t s = ctx->list[j];
         const proj_t* P = &ctx->pr[s];
@@ -513,20 +607,37 @@ static int walk_pixel(const orc_ctx* ctx, int v, int px, int py, step_t* steps,
         double a = P->conic[0], bb = P->conic[1], c = P->conic[2];
         double power = -0.5 * (a * dx * dx + c * dy * dy) - bb * dx * dy;
         double scale = 0.5 * (fabs(a) * dx * dx + fabs(c) * dy * dy) + fabs(bb * dx * dy);
-        if (scale > 0 && power > -band * scale) f |= 16;
+        double perr = P->qerr * scale;                 /* absolute error bound of power */
+        double xerr = prm->decision_band + perr;       /* relative error bound of x */
+        if (scale > 0) {
+            double mu = power < 0 ? -power / perr : 0.0;
+            if (mu <= 1.0) f |= 16;
+            if (mu < margin) margin = mu;
+        }
         if (power > 0) continue;
         double G = exp(power);
         double x = P->opacity * G;
-        if (fabs(x - prm->alpha_min) <= band * prm->alpha_min) f |= 1;
-        if (fabs(x - prm->alpha_max) <= band * prm->alpha_max) f |= 2;
+        double m1 = band_units(x, prm->alpha_min, xerr), m2 = band_units(x, prm->alpha_max, xerr);
+        if (m1 <= 1.0) f |= 1;
+        if (m2 <= 1.0) f |= 2;
+        if (m1 < margin) margin = m1;
+        if (m2 < margin) margin = m2;
         int capped = x > prm->alpha_max;
         double alpha = capped ? prm->alpha_max : x;
         if (alpha < prm->alpha_min) continue;
         double Tn = T * (1.0 - alpha);
-        if (fabs(Tn - prm->t_min) <= prm->t_band * prm->t_min) f |= 4;
-        if (Tn < prm->t_min) break;
+        double ea = capped ? 2.0 * u32 : xerr;
+        double eTn = eT + ea * alpha / (1.0 - alpha) + 2.0 * u32;
+        double m4 = band_units(Tn, prm->t_min, prm->t_band * eTn);
+        if (m4 <= 1.0) f |= 4;
+        if (m4 < margin) margin = m4;
+        if (Tn < prm->t_min) {
+            stop_slot = s;
+            break;
+        }
         double wgt = alpha * T;
         C0 += g->rgb[0] * wgt; C1 += g->rgb[1] * wgt; C2 += g->rgb[2] * wgt;
+        A0 += fabs(g->rgb[0]) * wgt; A1 += fabs(g->rgb[1]) * wgt; A2 += fabs(g->rgb[2]) * wgt;
         Dd += P->p[2] * wgt;
         Ss += wgt;
         if (steps) {
@@ -535,18 +646,49 @@ static int walk_pixel(const orc_ctx* ctx, int v, int px, int py, step_t* steps,
         }
         ++m;
         T = Tn;
+        eT = eTn;
         last = (int32_t)(j - b + 1);
     }
+    if (ctx->tile_ambiguous[key] && (flag || margin_out)) {
+        /* a Gaussian whose membership of this tile hangs on a borderline
+         * radius changes the images only where it passes alpha >= alpha_min
+         * before the pixel's stop; any of them changes the work counters */
+        f |= 32;
+        float zs = stop_slot >= 0 ? ctx->pr[stop_slot].z32 : 0.0f;
+        int64_t ns = stop_slot >= 0 ? stop_slot % ctx->N : 0;
+        for (int64_t q = ctx->amb_start[key]; q < ctx->amb_start[key + 1]; ++q) {
+            int64_t s = ctx->amb_slot[q];
+            const proj_t* P = &ctx->pr[s];
+            if (stop_slot >= 0) {
+                int64_t n = s % ctx->N;
+                if (P->z32 > zs || (P->z32 == zs && n > ns)) continue;  /* ordered after the stop */
+            }
+            double dx = P->uv[0] - px, dy = P->uv[1] - py;
+            double a = P->conic[0], bb = P->conic[1], c = P->conic[2];
+            double power = -0.5 * (a * dx * dx + c * dy * dy) - bb * dx * dy;
+            double scale = 0.5 * (fabs(a) * dx * dx + fabs(c) * dy * dy) + fabs(bb * dx * dy);
+            double perr = P->qerr * scale;
+            if (power > perr) continue;
+            double x = P->opacity * exp(power < 0 ? power : 0.0);
+            if (x >= prm->alpha_min * (1.0 - prm->decision_band - perr)) {
+                f |= 8;
+                margin = 0.0;
+            }
+        }
+    }
     out[0] = C0; out[1] = C1; out[2] = C2; out[3] = Dd; out[4] = Ss;
+    if (cabs) { cabs[0] = A0; cabs[1] = A1; cabs[2] = A2; }
     if (T_final) *T_final = T;
     if (n_contrib) *n_contrib = last;
     if (n_eval) *n_eval = evals;
     if (flag) *flag = f;
+    if (margin_out) *margin_out = margin;
     return m;
 }
 
 int64_t orc_forward(orc_ctx* ctx, double* C, double* D, double* S, double* T_final,
-                    int32_t* n_contrib, int32_t* n_eval, uint8_t* flags, int threads)
+                    int32_t* n_contrib, int32_t* n_eval, uint8_t* flags, double* C_abs, double* margin,
+                    int threads)
 {
     int64_t total = 0;
 #ifdef _OPENMP
@@ -562,13 +704,15 @@ int64_t orc_forward(orc_ctx* ctx, double* C, double* D, double* S, double* T_fin
 #endif
         for (int py = ctx->win[4 * v + 1]; py < ctx->win[4 * v + 3]; ++py)
             for (int px = ctx->win[4 * v + 0]; px < ctx->win[4 * v + 2]; ++px) {
-                double out[5], Tf;
+                double out[5], Tf, ca[3], mg;
                 int32_t nc, ne;
                 uint8_t f;
                 int64_t i = (int64_t)py * Wd + px;
                 if (ctx->pmask && !ctx->pmask[pb + i]) continue;
-                walk_pixel(ctx, v, px, py, NULL, out, &Tf, &nc, &ne, &f);
+                walk_pixel(ctx, v, px, py, NULL, out, &Tf, &nc, &ne, &f, ca, &mg);
                 if (C) { C[3 * pb + i] = out[0]; C[3 * pb + HW + i] = out[1]; C[3 * pb + 2 * HW + i] = out[2]; }
+                if (C_abs) { C_abs[3 * pb + i] = ca[0]; C_abs[3 * pb + HW + i] = ca[1]; C_abs[3 * pb + 2 * HW + i] = ca[2]; }
+                if (margin) margin[pb + i] = mg;
                 if (D) D[pb + i] = out[3];
                 if (S) S[pb + i] = out[4];
                 if (T_final) T_final[pb + i] = Tf;
@@ -612,7 +756,7 @@ void orc_hit_counts(orc_ctx* ctx, int64_t* hits, int32_t* seen, int threads)
                 for (int px = ctx->win[4 * v + 0]; px < ctx->win[4 * v + 2]; ++px) {
                     double out[5];
                     if (ctx->pmask && !ctx->pmask[ctx->pix_base[v] + (int64_t)py * ctx->cams[v].width + px]) continue;
-                    int m = walk_pixel(ctx, v, px, py, steps, out, NULL, NULL, NULL, NULL);
+                    int m = walk_pixel(ctx, v, px, py, steps, out, NULL, NULL, NULL, NULL, NULL, NULL);
                     for (int i = 0; i < m; ++i) {
                         int64_t n = steps[i].slot % N;
 #ifdef _OPENMP
@@ -635,7 +779,7 @@ static void pixel_backward(const orc_ctx* ctx, int v, int px, int py, step_t* st
                            const double gpix[5], double* g2d)
 {
     double out[5];
-    int m = walk_pixel(ctx, v, px, py, steps, out, NULL, NULL, NULL, NULL);
+    int m = walk_pixel(ctx, v, px, py, steps, out, NULL, NULL, NULL, NULL, NULL, NULL);
     double suffix = 0.0; /* sum over later steps j of w_j * alpha_j * T_j */
     for (int k = m - 1; k >= 0; --k) {
         const step_t* st = &steps[k];

@@ -48,8 +48,10 @@ typedef struct {
     int jacobian_clamp;
     int tile;                            /* 16 */
     double r_band;                       /* relative band flagging a borderline radius */
-    double decision_band;                /* relative band flagging near-threshold alpha / exponent decisions */
-    double t_band;                       /* relative band flagging a near-threshold transmittance stop */
+    double decision_band;                /* relative error floor of an FP32 alpha (opacity, threshold, exp2) */
+    double t_band;                       /* safety factor on the transmittance's FP32 error bound */
+    double q_ulps;                       /* FP32 units in the last place of the exponent, per unit of
+                                            (1 + condition number of the 2D covariance) */
 } orc_params;
 
 typedef struct orc_ctx orc_ctx;
@@ -86,6 +88,14 @@ void orc_set_pixel_mask(orc_ctx* ctx, const uint8_t* mask);
  * flags: [slots] bit0 borderline radius. */
 void orc_get_proj(const orc_ctx* ctx, double* proj, float* bin32, int32_t* flags);
 
+/* Tile rects from FP64 against FP32 projected centres: among the slots whose
+ * FP32 projection reaches the rect stage (in front, positive determinant),
+ * the number whose rect from the FP64 centre (u, v) differs from the rect
+ * the binning takes from the FP32 centre (same radius); *n_borderline
+ * (nullable) receives the number of slots whose radius itself is
+ * borderline (r_band). */
+int64_t orc_rect_fp64_diff(const orc_ctx* ctx, int64_t* n_borderline);
+
 /* Per-tile lists: tile_start [n_tiles + 1], list [n_pairs] of slot ids, in the
  * (tile, FP32 depth, Gaussian index) order. */
 void orc_get_bins(const orc_ctx* ctx, int64_t* tile_start, int64_t* list);
@@ -96,11 +106,21 @@ void orc_get_decoded(const orc_ctx* ctx, double* out);
 
 /* Forward compositing (Eq. 16-18).  Images are flat, per-view planar blocks:
  * view v occupies pixels [pix_base[v], pix_base[v] + W*H); C holds three
- * planes per view.  flags: bit0 alpha near alpha_min, bit1 alpha near cap,
- * bit2 transmittance stop near t_min, bit3 borderline-radius Gaussian in the
- * pixel's tile, bit4 power near zero.  Returns total evaluated pairs. */
+ * planes per view.  Any output pointer may be NULL.
+ * flags: a decision of the pixel lies within the FP32 error bound of its
+ * threshold -- bit0 alpha near alpha_min, bit1 alpha near the cap, bit2
+ * transmittance stop near t_min, bit3 a Gaussian whose tile membership
+ * hangs on a borderline radius reaches the pixel (alpha >= alpha_min there,
+ * before the pixel's stop), bit4 exponent near zero; bit5 (work counters
+ * only) the pixel's tile list may differ by such a Gaussian.
+ * C_abs: [3 per pixel, same layout as C] sum over the blended Gaussians of
+ * |colour| alpha T, the magnitude of the sum that C is (equal to |C| when
+ * the colours share one sign).  margin: [pixels] the smallest distance of
+ * any of the pixel's decisions to its threshold, in units of its error
+ * bound (flagged iff <= 1).  Returns total evaluated pairs. */
 int64_t orc_forward(orc_ctx* ctx, double* C, double* D, double* S, double* T_final,
-                    int32_t* n_contrib, int32_t* n_eval, uint8_t* flags, int threads);
+                    int32_t* n_contrib, int32_t* n_eval, uint8_t* flags, double* C_abs, double* margin,
+                    int threads);
 
 /* Hit counts of the sliding-window mask (Eq. 13): hits[n] += the number of
  * (view, pixel) pairs, within each view's window, where Gaussian n is

@@ -181,7 +181,8 @@ struct vg_ctx {
     StageProfiler prof;
     int64_t pair_cap = 0;
     DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, tile_order, Tfin, ncontrib, lookback,
-        scratch, state, pose_part, icp_part, loss_scratch, pair_off, chunk_start, blk_count, vis, ssim_ws, grow_ws;
+        scratch, state, pose_part, icp_part, loss_scratch, pair_off, chunk_start, blk_count, vis, ssim_ws, grow_ws,
+        neval;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
     bool tile_sort_failed = false;  // a tile list overflowed the per-tile sort: VG_SORT_AUTO sorts globally
@@ -527,6 +528,7 @@ vg_status vg_ctx_buffer(const vg_ctx* ctx, int32_t which, const void** ptr, int6
         case VG_BUF_T_FINAL: b = &ctx->Tfin; break;
         case VG_BUF_N_CONTRIB: b = &ctx->ncontrib; break;
         case VG_BUF_G2D: b = &ctx->g2d; break;
+        case VG_BUF_N_EVAL: b = &ctx->neval; break;
         default: return fail(VG_ERR_INVALID_ARG, "vg_ctx_buffer: unknown buffer id");
     }
     *ptr = b->p;
@@ -655,6 +657,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     VG_TRY(ctx->scratch.ensure((size_t)(SCR_WORDS + V.total_tiles) * 4, st, "scratch"));
     VG_TRY(ctx->Tfin.ensure(pixels * 4, st, "T_final"));
     VG_TRY(ctx->ncontrib.ensure(pixels * 4, st, "n_contrib"));
+    if (params->count_evals) VG_TRY(ctx->neval.ensure(pixels * 4, st, "n_eval"));
     const int64_t lb_parts = std::max(ceil_div(slots, SORT_TILE), ceil_div(ctx->pair_cap, SORT_TILE));
     const int64_t lb_entries = std::max(lb_parts * 256, ceil_div(slots, DUP_TILE));
     if (ctx->lookback.bytes < (size_t)lb_entries * 8) {
@@ -741,7 +744,7 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
                               ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(), C, D, S,
                               ctx->Tfin.as<float>(), ctx->ncontrib.as<uint32_t>(),
                               (unsigned long long*)(state + ST_EVALS), (unsigned long long*)(state + ST_BLENDED),
-                              params->count_evals, st));
+                              params->count_evals ? ctx->neval.as<uint32_t>() : nullptr, params->count_evals, st));
     ctx->views = V;
     ctx->fwd_N = N;
     ctx->fwd_scene = scene;

@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     uint32_t* __restrict__ pvals, const uint32_t* __restrict__ dkey, uint32_t* __restrict__ err,
     const float4* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
     float* __restrict__ C, float* __restrict__ D, float* __restrict__ S, float* __restrict__ Tfin,
-    uint32_t* __restrict__ ncontrib, unsigned long long* evals, unsigned long long* blended, int count_evals) {
+    uint32_t* __restrict__ ncontrib, unsigned long long* evals, unsigned long long* blended,
+    uint32_t* __restrict__ neval, int count_evals) {
     constexpr int NT = TILE_PIX / PPT;
     // staging of one batch of the tile's Gaussians; before that, the per-tile
     // sort's buffer (VG_TILE_SORT_CAP x 8 bytes) in the same memory
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
         if (!done[k] && cs.pix_mask) done[k] = cs.pix_mask[vi.pix_base + (int64_t)py[k] * vi.W + px[k]] == 0;
         T[k] = 1.f;
         last[k] = 0;
-        stop_at[k] = 0xffffffffu;
+        stop_at[k] = done[k] ? 0xfffffffeu : 0xffffffffu;  // a pixel left out examines nothing
         nb[k] = 0;
 #pragma unroll
         for (int c = 0; c < 5; ++c) acc[k][c] = 0.f;
@@ -311,7 +312,9 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
         Tfin[pb + i] = T[k];
         ncontrib[pb + i] = last[k];
         // examined list entries: up to and including the stopping one
-        ev += stop_at[k] != 0xffffffffu ? stop_at[k] + 1 : rg.y - rg.x;
+        const uint32_t evk = stop_at[k] == 0xffffffffu ? rg.y - rg.x : stop_at[k] == 0xfffffffeu ? 0u : stop_at[k] + 1;
+        if (COUNT && neval) neval[pb + i] = evk;
+        ev += evk;
         bl += nb[k];
     }
     if (COUNT) {
@@ -524,13 +527,14 @@ cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const ui
                              uint32_t* pvals, const uint32_t* dkey, uint32_t* err,
                              const float4* xy, const float4* conic_o, const float4* rgbd, float* C, float* D, float* S,
                              float* Tfin, uint32_t* ncontrib, unsigned long long* evals, unsigned long long* blended,
-                             int count_evals, cudaStream_t st) {
+                             uint32_t* neval, int count_evals, cudaStream_t st) {
     if (V.total_tiles <= 0) return cudaSuccess;
     count_launches(1);
 #define VG_FWD4(P, H, TS, CN)                                                                                   \
     blend_fwd_kernel<P, H, TS, CN><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, order, pvals, dkey, err, \
                                                                            xy, conic_o, rgbd, C, D, S, Tfin,     \
-                                                                           ncontrib, evals, blended, count_evals)
+                                                                           ncontrib, evals, blended, neval,      \
+                                                                           count_evals)
 #define VG_FWD3(P, H, TS)                                                                                       \
     do {                                                                                                        \
         if (count_evals) VG_FWD4(P, H, TS, true); else VG_FWD4(P, H, TS, false);                                \

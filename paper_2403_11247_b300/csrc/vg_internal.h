@@ -138,7 +138,7 @@ cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const ui
                              uint32_t* pvals, const uint32_t* dkey, uint32_t* err,
                              const float4* xy, const float4* conic_o, const float4* rgbd, float* C, float* D,
                              float* S, float* Tfin, uint32_t* ncontrib, unsigned long long* evals,
-                             unsigned long long* blended, int count_evals, cudaStream_t st);
+                             unsigned long long* blended, uint32_t* neval, int count_evals, cudaStream_t st);
 cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* order,
                              const uint32_t* pvals,
                              const float4* xy, const float4* conic_o, const float4* rgbd, const float* Tfin,

@@ -601,10 +601,10 @@ def vg_sample_rays(mask, rate: float, seed: int, round_dev=None, round_host: int
 
 
 VG_BUF = dict(xy=0, conic=1, rgbd=2, rect=3, ntiles=4, pair_keys=5, pair_vals=6, ranges=7, t_final=8, n_contrib=9,
-              g2d=10)
+              g2d=10, n_eval=11)
 _BUF_DTYPE = dict(xy=("float32", 4), conic=("float32", 4), rgbd=("float32", 4), rect=("uint32", 2),
                   ntiles=("uint32", 1), pair_keys=("uint32", 1), pair_vals=("uint32", 1), ranges=("uint32", 2),
-                  t_final=("float32", 1), n_contrib=("uint32", 1), g2d=("float32", 12))
+                  t_final=("float32", 1), n_contrib=("uint32", 1), g2d=("float32", 12), n_eval=("uint32", 1))
 
 
 def vg_ctx_buffer(ctx: CtxHandle, which: str, count: int, stream=None) -> np.ndarray:

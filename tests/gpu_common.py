@@ -8,19 +8,33 @@ from oracle import oracle as O
 from paper_2403_11247_b300 import synth
 from paper_2403_11247_b300 import vg as V
 
-# Forward tolerance: each channel is a sum of values weighted by alpha_i T_i,
-# the weights summing to S; in FP32 each weight carries at most ~1e-4 relative
-# error (transmittance after a run of high-alpha Gaussians), so per pixel
-#   |C - C_o| <= 1e-4 (|C_o| + c_max S_o) + 1e-6, c_max = 1 for RGB in [0,1],
-#   |D - D_o| <= 1e-4 (|D_o| + z_max S_o) + 1e-6 (1 + z_max),
+# Forward tolerance (1e-4 relative, per pixel):
+#   |C - C_o| <= 1e-4 C_abs + 1e-6, C_abs = sum over the blended Gaussians of
+#     |c| alpha T, the magnitude of the sum C is (= |C_o| where the colours of
+#     the pixel share one sign; R-VQ decoded colours can be negative, and
+#     where they cancel a bound relative to |C_o| would ask for more than
+#     FP32 summation gives),
+#   |D - D_o| <= 1e-4 |D_o| + 1e-6 (1 + z_max),
 #   |S - S_o| <= 1e-4 |S_o| + 1e-6.
-# Pixels the oracle flags as near a threshold get a loose bound instead (one
+# Pixels the oracle flags as near a threshold (a decision within the FP32
+# error bound of the quantity deciding it) get a loose bound instead (one
 # Gaussian's share at a threshold), and are excluded from gradient checks by
-# zeroing their upstream gradient on both sides.
+# zeroing their upstream gradient on both sides.  Every pixel walks its
+# tile's list, and each (pixel, Gaussian) decision it takes carries its own
+# FP32 error, so the number of flagged pixels grows with the evaluated pairs,
+# not with the pixels: measured 1.4-1.6e-5 flagged pixels per evaluated pair
+# on every workload here (0.13% of the mapping image, whose pixels examine
+# ~93 entries each); the cap is twice that, plus MIN_FLAGGED_CAP pixels.
 RTOL_IMG = 1e-4
 ATOL_IMG = 1e-6
 LOOSE = 0.05
-MAX_FLAGGED = 5e-3      # fraction of pixels, plus two tiles' worth for tiny images
+MAX_FLAGGED_PER_EVAL = 3e-5
+MIN_FLAGGED_CAP = 8
+# gradients: |g - o| <= 1e-3 max|o| per array; pose sums 1e-4 relative
+# (+1e-5 of the largest component, for components near zero)
+GRAD_ATOL = 1e-3
+POSE_RTOL = 1e-4
+POSE_ATOL = 1e-5
 
 
 def torch():
@@ -74,38 +88,73 @@ def masked_upstream(seed, f, cams, scale=None):
     return dC * colour_values(ok, cams), dD * ok, dS * ok
 
 
-def assert_forward_parity(scene, cams, label="", **pkw):
-    sh, ctx, params, gC, gD, gS = gpu_forward(scene, cams, **pkw)
-    o = O.Oracle(scene, cams, params=oracle_params(**pkw))
-    f = o.forward(threads=8)
+def flag_cap(n_evaluated, n_pixels=0, stop_frac=0.0):
+    """Flagged-pixel cap: per evaluated pair, plus (workloads where every
+    pixel's transmittance runs out after many high-alpha Gaussians) a
+    fraction of the pixels for their stop decisions."""
+    return MAX_FLAGGED_PER_EVAL * n_evaluated + stop_frac * n_pixels + MIN_FLAGGED_CAP
+
+
+def check_images(gC, gD, gS, f, cams, zmax, label="", stop_frac=0.0):
+    """Per-pixel forward parity; returns the worst err/tol of C, D, S."""
     ok = f["flags"] == 0
     P = f["S"].size
     nflag = int((~ok).sum())
-    assert nflag <= MAX_FLAGGED * P + 512, f"{label}: {nflag} of {P} pixels near a threshold"
-    proj, _, _ = o.projection()
-    zmax = max(1.0, float(proj[proj[:, 10] == 1, 2].max()) if (proj[:, 10] == 1).any() else 1.0)
+    cap = flag_cap(f["evaluated"], P, stop_frac)
+    assert nflag <= cap, (f"{label}: {nflag} of {P} pixels near a threshold (cap {cap:.0f} for "
+                          f"{f['evaluated']} evaluated pairs)")
     okc = colour_mask(ok, cams)
     eC = np.abs(gC - f["C"])
     eD = np.abs(gD - f["D"])
     eS = np.abs(gS - f["S"])
-    S3 = colour_values(f["S"], cams)
-    tolC = RTOL_IMG * (np.abs(f["C"]) + S3) + ATOL_IMG
-    tolD = RTOL_IMG * (np.abs(f["D"]) + zmax * f["S"]) + ATOL_IMG * (1 + zmax)
+    tolC = RTOL_IMG * f["C_abs"] + ATOL_IMG
+    tolD = RTOL_IMG * np.abs(f["D"]) + ATOL_IMG * (1 + zmax)
     tolS = RTOL_IMG * np.abs(f["S"]) + ATOL_IMG
-    badC = (eC > tolC) & okc
-    badD = (eD > tolD) & ok
-    badS = (eS > tolS) & ok
-    msg = (f"{label}: strict-bound misses C {badC.sum()} D {badD.sum()} S {badS.sum()}; "
-           f"max err C {eC[okc].max() if okc.any() else 0:.3g} D {eD[ok].max() if ok.any() else 0:.3g} "
-           f"S {eS[ok].max() if ok.any() else 0:.3g}; flagged {nflag}")
-    assert not badC.any() and not badD.any() and not badS.any(), msg
+    worst = dict(C=float((eC / tolC)[okc].max()) if okc.any() else 0.0,
+                 D=float((eD / tolD)[ok].max()) if ok.any() else 0.0,
+                 S=float((eS / tolS)[ok].max()) if ok.any() else 0.0)
+    msg = (f"{label}: strict-bound misses C {int(((eC > tolC) & okc).sum())} D {int(((eD > tolD) & ok).sum())} "
+           f"S {int(((eS > tolS) & ok).sum())}; worst err/tol {worst}; flagged {nflag}")
+    assert max(worst.values()) <= 1.0, msg
     # flagged pixels: bounded by one Gaussian's share near the threshold
     assert np.all(eC[~okc] <= LOOSE) and np.all(eS[~ok] <= LOOSE) and np.all(eD[~ok] <= LOOSE * zmax), label
+    print(f"{label}: worst err/tol C {worst['C']:.3f} D {worst['D']:.3f} S {worst['S']:.3f}; "
+          f"flagged {nflag} of {P} pixels ({nflag / max(P, 1):.3%}; "
+          f"{nflag / max(f['evaluated'], 1):.2e} per evaluated pair)")
+    return worst
+
+
+def check_counters(ctx, f, label=""):
+    """Per-pixel work counters equal the oracle's outside the pixels flagged
+    for them: the list entries examined (up to and including the stopping
+    one) and the position of the last blended Gaussian."""
+    P = f["S"].size
+    ok = ~f["ctr_flags"]
+    ne = V.vg_ctx_buffer(ctx, "n_eval", P).astype(np.int64)
+    nc = V.vg_ctx_buffer(ctx, "n_contrib", P).astype(np.int64)
+    bad_e = int(((ne != f["n_eval"]) & ok).sum())
+    bad_c = int(((nc != f["n_contrib"]) & ok).sum())
+    assert bad_e == 0 and bad_c == 0, f"{label}: counter mismatches n_eval {bad_e} n_contrib {bad_c}"
+    st = V.vg_ctx_stats(ctx)
+    assert st["evaluated"] == int(ne.sum())
+
+
+def assert_forward_parity(scene, cams, label="", **pkw):
+    pkw.setdefault("count_evals", 1)
+    sh, ctx, params, gC, gD, gS = gpu_forward(scene, cams, **pkw)
+    o = O.Oracle(scene, cams, params=oracle_params(**pkw))
+    f = o.forward(threads=8)
+    proj, _, _ = o.projection()
+    zmax = max(1.0, float(proj[proj[:, 10] == 1, 2].max()) if (proj[:, 10] == 1).any() else 1.0)
+    check_images(gC, gD, gS, f, cams, zmax, label)
+    if pkw.get("count_evals"):
+        check_counters(ctx, f, label)
     return sh, ctx, params, o, f, (gC, gD, gS)
 
 
-def grad_tolerance_check(g, o, name, rtol=2e-3, atol_frac=1e-3):
-    """|g - o| <= atol_frac * max|o| + rtol * |o| elementwise."""
+def grad_tolerance_check(g, o, name, rtol=0.0, atol_frac=GRAD_ATOL):
+    """|g - o| <= atol_frac * max|o| + rtol * |o| elementwise; returns the
+    worst err/tol."""
     g = np.asarray(g, np.float64).ravel()
     o = np.asarray(o, np.float64).ravel()
     scale = max(np.abs(o).max() if o.size else 0.0, 1e-12)
@@ -116,6 +165,12 @@ def grad_tolerance_check(g, o, name, rtol=2e-3, atol_frac=1e-3):
     assert not bad.any(), (f"{name}: {bad.sum()} of {g.size} outside tolerance; max |err| {err.max():.3g} "
                            f"(scale {scale:.3g}); worst err/tol {worst:.3g}")
     return worst
+
+
+def pose_tolerance_check(g, o, name):
+    """Pose-gradient sums: 1e-4 relative per component (+1e-5 of the
+    largest component)."""
+    return grad_tolerance_check(g, o, name, rtol=POSE_RTOL, atol_frac=POSE_ATOL)
 
 
 def to_np_grads(grads):

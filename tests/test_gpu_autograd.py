@@ -8,7 +8,7 @@ from oracle import oracle as O
 from paper_2403_11247_b300 import synth
 from paper_2403_11247_b300 import vg as V
 
-from gpu_common import grad_tolerance_check, masked_upstream
+from gpu_common import grad_tolerance_check, masked_upstream, pose_tolerance_check
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,7 @@ def test_autograd_gradients_match_the_oracle(torch):
     for name in ("logscale", "rot", "opacity", "rgb"):
         grad_tolerance_check(scene.groups[name].codebook.grad.cpu().numpy(), og[name], "autograd:" + name)
     for v in range(len(cams)):
-        grad_tolerance_check(twist.grad[v].cpu().numpy(), og["pose"][v], f"autograd:pose{v}")
+        pose_tolerance_check(twist.grad[v].cpu().numpy(), og["pose"][v], f"autograd:pose{v}")
 
 
 def test_autograd_directional_derivative_matches_gpu_finite_differences(torch):

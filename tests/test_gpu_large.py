@@ -16,7 +16,14 @@ from oracle import oracle as O
 from paper_2403_11247_b300 import synth
 from paper_2403_11247_b300 import vg as V
 
-from gpu_common import ATOL_IMG, LOOSE, RTOL_IMG, grad_tolerance_check
+from gpu_common import check_images, grad_tolerance_check, pose_tolerance_check
+
+
+class _Win:
+    """A window's pixels as a stand-alone image (for the per-pixel checks)."""
+
+    def __init__(self, w, h):
+        self.width, self.height = w, h
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -60,22 +67,16 @@ def test_large_scene_windows_match_the_oracle(torch):
         ys, xs = np.divmod(np.arange(w * h), w)
         pix = (y0 + ys) * W + (x0 + xs)                 # window pixels in the view
         ok = f["flags"][pix] == 0
-        # each pixel tests ~1,000 Gaussians, so one of them sits near a
-        # decision threshold far more often than in the smaller workloads
-        assert (~ok).sum() <= 0.35 * w * h, (~ok).sum()
-        S_o = f["S"][pix]
-        zmax = 60.0
-        for ch in range(3):
-            g = gC[3 * v * HW + ch * HW + pix]
-            oo = f["C"][ch * HW + pix]
-            err = np.abs(g - oo)
-            tol = RTOL_IMG * (np.abs(oo) + S_o) + ATOL_IMG
-            assert np.all(err[ok] <= tol[ok]), (v, ch, int((err[ok] > tol[ok]).sum()), err[ok].max())
-            assert np.all(err[~ok] <= LOOSE)
-        eD = np.abs(gD[v * HW + pix] - f["D"][pix])
-        assert np.all(eD[ok] <= RTOL_IMG * (np.abs(f["D"][pix][ok]) + zmax * S_o[ok]) + ATOL_IMG * (1 + zmax)), v
-        eS = np.abs(gS[v * HW + pix] - S_o)
-        assert np.all(eS[ok] <= RTOL_IMG * S_o[ok] + ATOL_IMG), v
+        fw = dict(flags=f["flags"][pix], S=f["S"][pix], D=f["D"][pix], evaluated=f["evaluated"],
+                  C=np.concatenate([f["C"][ch * HW + pix] for ch in range(3)]),
+                  C_abs=np.concatenate([f["C_abs"][ch * HW + pix] for ch in range(3)]))
+        gw = np.concatenate([gC[3 * v * HW + ch * HW + pix] for ch in range(3)])
+        # ~1,000 Gaussians per tile: every pixel stops, most after several
+        # Gaussians of alpha near the cap, each multiplying the FP32 error of
+        # T by alpha / (1 - alpha); 1.1-1.5% of the pixels take that stop
+        # within its error bound (2% allowed)
+        check_images(gw, gD[v * HW + pix], gS[v * HW + pix], fw, [_Win(w, h)], 60.0, f"large view {v}",
+                     stop_frac=0.02)
         # upstream gradients inside the window, zero at flagged pixels
         okf = ok.astype(np.float32)
         uC = np.zeros(3 * HW, np.float32)
@@ -99,4 +100,4 @@ def test_large_scene_windows_match_the_oracle(torch):
     for name in ("anchor_xyz", "anchor_l", "offsets", "mask_logit", "logscale", "rot", "opacity", "rgb"):
         grad_tolerance_check(grads[name].cpu().numpy(), og[name], "large:" + name)
     for v in range(4):
-        grad_tolerance_check(dxi[v], opose[v], f"large:pose{v}")
+        pose_tolerance_check(dxi[v], opose[v], f"large:pose{v}")

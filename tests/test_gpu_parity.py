@@ -1,9 +1,10 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
 Forward images within 1e-4 relative (+1e-6 absolute) on every pixel the
-oracle does not flag as near a threshold; binning (FP32 u, v, depth bits,
-tile rects, per-tile lists) bit for bit; gradients within 1e-3 of the
-array's scale plus 2e-3 relative; pose gradients likewise.
+oracle does not flag as near a threshold (at most 0.01% of the pixels);
+per-pixel work counters exactly; binning (FP32 u, v, depth bits, tile
+rects, per-tile lists) bit for bit; gradients within 1e-3 of the array's
+scale; pose gradients within 1e-4 relative.
 """
 import math
 
@@ -15,7 +16,7 @@ from paper_2403_11247_b300 import synth
 from paper_2403_11247_b300 import vg as V
 
 from gpu_common import (assert_forward_parity, gpu_forward, grad_tolerance_check, masked_upstream, oracle_params,
-                        to_np_grads)
+                        pose_tolerance_check, to_np_grads)
 
 pytestmark = pytest.mark.gpu
 
@@ -191,9 +192,10 @@ def test_tile_list_over_the_per_tile_cap_is_flagged_and_auto_falls_back(cuda):
 def test_forward_tiny_scene(cuda):
     sc, cams = synth.tiny_scene(), [synth.tiny_camera()]
     sh, ctx, params, o, f, g = assert_forward_parity(sc, cams, "tiny", count_evals=1)
-    ev = V.vg_ctx_stats(ctx)["evaluated"]
-    # evaluated pairs agree exactly unless a decision sits on a threshold
-    assert abs(ev - f["evaluated"]) <= int((f["flags"] != 0).sum()) * 64
+    # the work counters agree pixel for pixel (checked inside); so do the
+    # totals wherever no pixel is flagged for them
+    if not f["ctr_flags"].any():
+        assert V.vg_ctx_stats(ctx)["evaluated"] == f["evaluated"]
 
 
 def test_forward_room_rvq_mask_ragged(cuda):
@@ -241,7 +243,7 @@ def backward_parity(scene, cams, label, seed=77, **pkw):
     if scene.mask_logit is not None:
         worst["mask"] = grad_tolerance_check(gg["mask_logit"], og["mask_logit"], label + ":mask_logit")
     for v in range(len(cams)):
-        worst[f"pose{v}"] = grad_tolerance_check(dxi[v].cpu().numpy(), og["pose"][v], f"{label}:pose{v}")
+        worst[f"pose{v}"] = pose_tolerance_check(dxi[v].cpu().numpy(), og["pose"][v], f"{label}:pose{v}")
     print(label, "worst err/tol", {k: round(x, 3) for k, x in worst.items()})
     return worst
 
@@ -287,7 +289,7 @@ def test_pose_grad_with_icp(cuda):
     oloss, oicp = o.icp(q, w)
     ref = og["pose"] + oicp
     for v in range(len(cams)):
-        grad_tolerance_check(dxi[v].cpu().numpy(), ref[v], f"icp pose {v}", rtol=1e-4, atol_frac=1e-5)
+        pose_tolerance_check(dxi[v].cpu().numpy(), ref[v], f"icp pose {v}")
     assert np.allclose(loss.cpu().numpy(), oloss, rtol=1e-5)
 
 

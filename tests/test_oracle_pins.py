@@ -249,6 +249,91 @@ def test_opaque_front_pair_occludes_everything_behind():
     assert np.abs(full["S"] - front["S"]).max() > 1e-4  # away from the centre the back does show
 
 
+def test_magnitude_sums_are_the_render_of_absolute_colours():
+    """C_abs is the sum over blended Gaussians of |c| alpha T: the compositing
+    weights do not depend on colour, so it equals the C of the same scene
+    with every colour replaced by its absolute value; and it equals |C|
+    where the colours share one sign."""
+    sc = synth.tiny_scene(seed=13, n=700)
+    rgb = sc.groups["rgb"].raw.copy()
+    rgb[::2] -= 0.6                                   # mixed signs
+    g = dict(sc.groups)
+    g["rgb"] = synth.Group(3, raw=rgb)
+    mixed = synth.Scene(sc.anchor_xyz, sc.anchor_l, sc.offsets, g)
+    g2 = dict(sc.groups)
+    g2["rgb"] = synth.Group(3, raw=np.abs(rgb))
+    absolute = synth.Scene(sc.anchor_xyz, sc.anchor_l, sc.offsets, g2)
+    c = synth.tiny_camera()
+    a = O.Oracle(mixed, [c]).forward()
+    b = O.Oracle(absolute, [c]).forward()
+    assert np.allclose(a["C_abs"], b["C"], rtol=1e-12, atol=1e-15)
+    assert np.all(a["C_abs"] >= np.abs(a["C"]) - 1e-15)
+    assert (a["C_abs"] > 1.5 * np.abs(a["C"])).any()      # cancellation does occur
+    p = O.Oracle(sc, [c]).forward()                        # colours in [0, 1]
+    assert np.array_equal(p["C_abs"], p["C"])
+
+
+def test_flags_mark_decisions_at_their_thresholds():
+    """A pixel placed where alpha = alpha_min exactly, and the opaque pair
+    whose second Gaussian takes the transmittance exactly to t_min, are
+    flagged (bits 0 and 2); pixels far from every threshold are not."""
+    # one isotropic Gaussian on the optical axis: sigma^2 = (f s / z)^2 + dil
+    f, ls, z, o_logit = 40.0, float(np.float32(math.log(0.05))), 2.0, 1.5
+    sig2 = (f * math.exp(ls) / z) ** 2 + 0.3
+    o = 1 / (1 + math.exp(-float(np.float32(o_logit))))
+    d = math.sqrt(2 * sig2 * math.log(255 * o))          # alpha(d) = 1/255
+    c = cam(f, f, 10.0 - d, 15.0, 32, 32)                  # the centre lies d px left of pixel (10, 15)
+    sc = raw_scene([[0.0, 0.0, z]], [[ls] * 3], [[1, 0, 0, 0]], [o_logit], [[0.5, 0.5, 0.5]])
+    out = O.Oracle(sc, [c]).forward()
+    row = 15 * 32 + np.arange(32)
+    assert out["flags"][row[10]] & 1
+    assert not (out["flags"][row[4]] & 1) and out["margin"][row[4]] > 1   # close to the centre
+    assert (out["flags"] != 0).mean() < 0.2
+    # the opaque pair of the occlusion pin: T = 0.01 * 0.01 = t_min at the centre
+    pair = raw_scene([[0.0, 0.0, 1.0], [0.001, 0.0, 1.05]], [[0.0] * 3] * 2, [[1, 0, 0, 0]] * 2, [12.0, 12.0],
+                     [[0.1, 0.2, 0.3]] * 2)
+    c2 = cam(50.0, 50.0, 15.5, 15.5, 32, 32)
+    op = O.Oracle(pair, [c2]).forward()
+    assert all(op["flags"][py * 32 + px] & 4 for py in range(12, 20) for px in range(12, 20))
+
+
+def test_fp64_rect_count_sees_a_centre_rounding_across_a_tile_edge():
+    """u = fx x / z + cx with fx = 3, x = fl32(20/3), z = 1, cx = 0: the FP32
+    product 3 x rounds up to 20.0, the exact one is 19.9999995; with radius 4
+    the FP32 rect starts at tile floor(16 / 16) = 1, the FP64 one at
+    floor(15.9999995 / 16) = 0."""
+    x = float(np.float32(20.0 / 3.0))
+    assert np.float32(3.0) * np.float32(x) == np.float32(20.0) and 3.0 * x < 20.0
+    # flat in z (the Jacobian's x/z^2 column would spread a round one):
+    # sigma^2 = 9 s^2 + 0.3 = 1.4025, 3 sigma = 3.55, radius 4
+    ls = [math.log(0.35), math.log(0.35), math.log(1e-4)]
+    sc = raw_scene([[x, 0.0, 1.0]], [ls], [[1, 0, 0, 0]], [0.0], [[0.5, 0.5, 0.5]])
+    o = O.Oracle(sc, [cam(3.0, 3.0, 0.0, 24.0, 64, 48)])
+    proj, _, _ = o.projection()
+    assert proj[0, 11] == 4 and proj[0, 12] == 1
+    assert o.rect_fp64_diff() == (1, 0)
+    # the same Gaussian a pixel to the left has both centres inside tile 0 + 4 px
+    sc2 = raw_scene([[x - 4.0 / 3.0, 0.0, 1.0]], [ls], [[1, 0, 0, 0]], [0.0], [[0.5] * 3])
+    assert O.Oracle(sc2, [cam(3.0, 3.0, 0.0, 24.0, 64, 48)]).rect_fp64_diff() == (0, 0)
+
+
+@pytest.mark.parametrize("workload", ["mapping", "large view 0"])
+def test_fp64_and_fp32_tile_rects_agree(workload):
+    """The binning takes tile rects from the FP32 projected centre; the count
+    of slots whose rect from the FP64 centre differs is reported and must be
+    a negligible share (the radius itself, from FP64 lambda_max, is the same;
+    borderline radii are counted apart)."""
+    if workload == "mapping":
+        o = O.Oracle(synth.room_scene(), [synth.room_camera()])
+    else:
+        o = O.Oracle(synth.large_scene(), synth.large_cameras()[:1])
+    proj, _, _ = o.projection()
+    reached = int((proj[:, 11] > 0).sum())
+    diff, borderline = o.rect_fp64_diff()
+    print(f"{workload}: {diff} of {reached} slots have another FP64 rect; {borderline} borderline radii")
+    assert diff <= 1e-3 * reached and borderline <= 1e-2 * reached
+
+
 def test_permutation_invariance():
     sc = synth.tiny_scene(seed=11, n=600)
     c = synth.tiny_camera()
