@@ -198,7 +198,7 @@ def build_workload(torch, V, synth):
     bufs = dict(C=torch.empty(3 * P, **f32), D=torch.empty(P, **f32), S=torch.empty(P, **f32),
                 dC=torch.empty(3 * P, **f32), dD=torch.empty(P, **f32), out=out, loss=out[0:1],
                 dxi=out[1:7].view(1, 6), Ct=Ct, Dt=Dt)
-    grads = V.grads_like(sh)
+    grads = {k: g.zero_() for k, g in V.grads_like(sh).items()}   # the step's backward accumulates
     plist = [dscene.anchor_xyz, dscene.anchor_l, dscene.offsets, dscene.mask_logit] + \
             [dscene.groups[k].codebook for k in V.GROUPS]
     glist = [grads["anchor_xyz"], grads["anchor_l"], grads["offsets"], grads["mask_logit"]] + \
@@ -211,15 +211,20 @@ def build_workload(torch, V, synth):
 
 
 def make_step(V, w):
+    """One mapping step: forward with the L1 loss gradient written by the
+    compositing kernel, backward accumulating into the map gradients (kept
+    zero by the Adam step, which clears each one once read), pose gradient,
+    Adam on the map."""
     b, sh, ctx, params, cams = w["bufs"], w["sh"], w["ctx"], w["params"], [w["cam"]]
+    p_bwd = type(params).from_buffer_copy(params)
+    p_bwd.grad_accumulate = 1
 
     def step():
-        V.vg_render_fwd(sh, cams, params, ctx, b["C"], b["D"], b["S"])
-        V.vg_loss_l1(1, w["P"], b["C"], b["D"], b["S"], b["Ct"], b["Dt"], 0.5, -1.0, ctx, dC=b["dC"], dD=b["dD"],
-                     loss=b["loss"])
-        V.vg_render_bwd(sh, cams, params, ctx, b["dC"], b["dD"], None, w["grads"])
+        V.vg_render_fwd_l1(sh, cams, params, ctx, b["Ct"], b["Dt"], 0.5, -1.0, b["C"], b["D"], b["S"], b["dC"],
+                           b["dD"], None, b["loss"])
+        V.vg_render_bwd(sh, cams, p_bwd, ctx, b["dC"], b["dD"], None, w["grads"])
         V.vg_pose_grad(ctx, 1, dxi=b["dxi"])
-        V.vg_adam_step(w["plist"], w["glist"], w["ms"], w["vs"], 1e-4, step_dev=w["step_dev"])
+        V.vg_adam_step(w["plist"], w["glist"], w["ms"], w["vs"], 1e-4, step_dev=w["step_dev"], zero_grad=True)
     return step
 
 
@@ -801,6 +806,8 @@ def run_ours(args):
     if args.ppt_bwd:
         tune["ppt_bwd"] = args.ppt_bwd
     w["params"] = V.default_params(ppt_fwd=tune["ppt_fwd"], ppt_bwd=tune["ppt_bwd"])
+    for g in w["grads"].values():   # the tuner's backwards left gradients behind
+        g.zero_()
     step = make_step(V, w)
     for _ in range(3):
         step()

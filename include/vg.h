@@ -161,7 +161,11 @@ typedef struct {
  *   order, each row-major] of 0/1: only pixels with 1 are composited (the
  *   sampled rays of a bundle-adjustment step, Sec. "Tracking and
  *   Local-to-Global Bundle Adjustment"); the others get C = D = S = 0 and
- *   are skipped by the backward.  NULL = every pixel.  See vg_sample_rays. */
+ *   are skipped by the backward.  NULL = every pixel.  See vg_sample_rays.
+ * grad_accumulate: vg_render_bwd ADDS to the scene-gradient arrays instead
+ *   of zeroing them first; the caller keeps them zero between steps (e.g.
+ *   vg_adam_step with zero_grad set clears each gradient after using it).
+ *   0 (default) = the backward zeroes them. */
 typedef struct {
     int32_t tile;
     int32_t batch;
@@ -174,6 +178,7 @@ typedef struct {
     uint32_t* seen;
     int32_t sort_mode;
     const uint8_t* pixel_mask;
+    int32_t grad_accumulate;
 } vg_render_params;
 
 /* Gradient outputs of vg_render_bwd (DEVICE pointers, caller-allocated; each
@@ -359,6 +364,25 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
                         vg_ctx* ctx, const float* dC, const float* dD, const float* dS,
                         const vg_scene_grads* grads, vg_stream stream);
 
+/* vg_render_fwd and vg_loss_l1 of its images in one pass: the same C, D, S,
+ * and the L1 loss gradients and value of Eq. 19's L1 form (the benchmark
+ * loss: mean |C - Ct| + w_depth * mean over target depths > 0 of |D - Dt|,
+ * with the silhouette gate S > gate of Eq. 21 when gate >= 0), written by
+ * the compositing kernel as each pixel is finished: its normalisers (the
+ * target depths > 0, and with params->pixel_mask the sampled pixels, which
+ * then restrict both means as in vg_loss_l1_masked) are counted by the
+ * preprocess before any pixel is composited.  Means run over every pixel of
+ * every view of the call; views may differ in size.  Ct [3 per pixel] and
+ * Dt [pixel] are DEVICE arrays in the layout of C and D; dC, dD (and dS,
+ * zeroed, may be NULL) receive the gradients, loss[0] the value (device
+ * float).  The gradient images equal vg_loss_l1's bit for bit; the loss value
+ * is summed in another order (one atomic add per tile).  Argument errors
+ * (NULL target or output, w_depth < 0) return VG_ERR_INVALID_ARG before any
+ * launch; everything else as vg_render_fwd. */
+vg_status vg_render_fwd_l1(vg_scene* scene, const vg_camera* cams, int32_t n_views, const vg_render_params* params,
+                           vg_ctx* ctx, const float* Ct, const float* Dt, float w_depth, float gate, float* C,
+                           float* D, float* S, float* dC, float* dD, float* dS, float* loss, vg_stream stream);
+
 /* Camera pose gradients of the last vg_render_bwd, for the left
  * perturbation T_cw <- exp(xi^) T_cw, xi = (rho, phi): dxi [n_views][6]
  * (rho then phi).  Optional ICP term (Eq. 20): with icp_q [n_views][N][3]
@@ -384,13 +408,16 @@ vg_status vg_loss_l1(int32_t n_views, int64_t n_pix, const float* C, const float
  * `tensors` is a HOST array of n_tensors records of device pointers (m and v
  * caller-allocated, zero before the first step).  The step number t comes
  * from step_dev[0] when step_dev is non-NULL (then incremented on the device,
- * so a captured graph advances it on every replay), else from step_host. */
+ * so a captured graph advances it on every replay), else from step_host.
+ * zero_grad != 0: grad[i] is set to 0 once read (for a backward that
+ * accumulates, vg_render_params.grad_accumulate). */
 typedef struct {
     float* param;
-    const float* grad;
+    float* grad;
     float* m;
     float* v;
     int64_t n;
+    int32_t zero_grad;
 } vg_adam_tensor;
 vg_status vg_adam_step(const vg_adam_tensor* tensors, int32_t n_tensors, float lr, float beta1, float beta2, float eps,
                        int32_t* step_dev, int32_t step_host, vg_stream stream);

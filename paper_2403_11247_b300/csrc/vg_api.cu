@@ -182,11 +182,16 @@ struct vg_ctx {
     int64_t pair_cap = 0;
     DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, tile_order, Tfin, ncontrib, lookback,
         scratch, state, pose_part, icp_part, loss_scratch, pair_off, chunk_start, blk_count, vis, ssim_ws, grow_ws,
-        neval;
+        neval, loss_blk;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
     bool tile_sort_failed = false;  // a tile list overflowed the per-tile sort: VG_SORT_AUTO sorts globally
     bool g2d_clean = false;
+    bool fwd_zeroed = false;  // the last forward zeroed the visible slots' gradient rows and the pose sums
+    // scratch words known to be zero: a forward leaves every counter it
+    // accumulates back at zero (the visible and pair counts are plain
+    // stores), so only a fresh or grown scratch needs a memset
+    size_t scratch_clean_words = 0;
     Views views{};
     int64_t fwd_N = -1;
     const vg_scene* fwd_scene = nullptr;
@@ -571,6 +576,7 @@ static vg_status build_views(const vg_camera* cams, int32_t n_views, const vg_re
         !(p->dilation >= 0.f) || !(p->sigma_cull > 0.f) || !(p->clamp_factor > 0.f))
         return fail(VG_ERR_INVALID_ARG, "render params out of range");
     std::memset(V, 0, sizeof(*V));
+    std::memset(cs, 0, sizeof(*cs));  // every optional feature off unless set below or by the caller
     V->n = n_views;
     V->pose_dev = p->pose_dev;
     int64_t tb = 0, pb = 0;
@@ -623,8 +629,16 @@ static int tile_passes_for(int total_tiles) {
     return (bits + 7) / 8;
 }
 
-vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views, const vg_render_params* params,
-                        vg_ctx* ctx, float* C, float* D, float* S, vg_stream stream) {
+// the L1 loss a forward computes in its compositing epilogue (vg_render_fwd_l1)
+struct FusedLoss {
+    const float *Ct, *Dt;
+    float *dC, *dD, *dS, *loss;
+    float w_depth, gate;
+};
+
+static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t n_views,
+                                const vg_render_params* params, vg_ctx* ctx, float* C, float* D, float* S,
+                                const FusedLoss* lf, vg_stream stream) {
     if (!scene || !ctx || !C || !D || !S) return fail(VG_ERR_INVALID_ARG, "vg_render_fwd: null argument");
     cudaStream_t st = (cudaStream_t)stream;
     Views V;
@@ -632,6 +646,18 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     int64_t pixels = 0;
     VG_TRY(build_views(cams, n_views, params, &V, &cs, &pixels));
     cs.n_gauss = scene->dev.N;
+    if (lf) {
+        cs.lf_on = 1;
+        cs.lf_Ct = lf->Ct;
+        cs.lf_Dt = lf->Dt;
+        cs.lf_dC = lf->dC;
+        cs.lf_dD = lf->dD;
+        cs.lf_dS = lf->dS;
+        cs.lf_loss = lf->loss;
+        cs.lf_pixels = pixels;
+        cs.lf_wdepth = lf->w_depth;
+        cs.lf_gate = lf->gate;
+    }
     const SceneDev& sd = scene->dev;
     const int64_t N = sd.N;
     const int64_t slots = N * n_views;
@@ -647,6 +673,12 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     VG_TRY(ctx->chunk_start.ensure((size_t)ceil_div(std::max<int64_t>(ctx->pair_cap, 1), EMIT_CHUNK) * 4, st,
                                    "pair chunk starts"));
     VG_TRY(ctx->blk_count.ensure((size_t)preprocess_blocks(N) * 8, st, "block counts"));
+    const int lf_grid = compact_grid(N, cs);
+    if (lf) {
+        VG_TRY(ctx->loss_blk.ensure((size_t)lf_grid * 8, st, "loss block counts"));
+        cs.lf_blk = ctx->loss_blk.as<uint32_t>();
+    }
+
     for (int b = 0; b < 2; ++b) {
         VG_TRY(ctx->dkey[b].ensure(slots * 4, st, "depth keys"));
         VG_TRY(ctx->dval[b].ensure(slots * 4, st, "depth values"));
@@ -654,10 +686,13 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     VG_TRY(ctx->vis.ensure(slots * 4, st, "visible slots"));
     VG_TRY(ctx->ranges.ensure((size_t)V.total_tiles * 8, st, "ranges"));
     VG_TRY(ctx->tile_order.ensure((size_t)V.total_tiles * 4, st, "tile order"));
-    VG_TRY(ctx->scratch.ensure((size_t)(SCR_WORDS + V.total_tiles) * 4, st, "scratch"));
+    const size_t scr_words = (size_t)(SCR_WORDS + V.total_tiles);
+    if (ctx->scratch.bytes < scr_words * 4) ctx->scratch_clean_words = 0;
+    VG_TRY(ctx->scratch.ensure(scr_words * 4, st, "scratch"));
+    VG_TRY(ctx->pose_part.ensure((size_t)n_views * 6 * 4, st, "pose sums"));
     VG_TRY(ctx->Tfin.ensure(pixels * 4, st, "T_final"));
     VG_TRY(ctx->ncontrib.ensure(pixels * 4, st, "n_contrib"));
-    if (params->count_evals) VG_TRY(ctx->neval.ensure(pixels * 4, st, "n_eval"));
+    VG_TRY(ctx->neval.ensure(pixels * 4, st, "n_eval"));  // written by forwards with count_evals
     const int64_t lb_parts = std::max(ceil_div(slots, SORT_TILE), ceil_div(ctx->pair_cap, SORT_TILE));
     const int64_t lb_entries = std::max(lb_parts * 256, ceil_div(slots, DUP_TILE));
     if (ctx->lookback.bytes < (size_t)lb_entries * 8) {
@@ -668,13 +703,20 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     uint32_t* scr = ctx->scratch.as<uint32_t>();
     uint32_t* state = ctx->state.as<uint32_t>();
     uint32_t* err = state + ST_ERR;
+    if (lf) cs.lf_counts = scr + SCR_LOSS_VALID;
     unsigned long long* lb = ctx->lookback.as<unsigned long long>();
     const bool tile_sort = params->sort_mode == VG_SORT_TILE ||
                            (params->sort_mode == VG_SORT_AUTO && !ctx->tile_sort_failed);
     cs.depth_hist = tile_sort ? 0 : 1;
     const bool prof_graph = capturing(st);
     const bool prof_on = ctx->prof.on;
-    VG_STAGE(VG_STAGE_MEMSET, cudaMemsetAsync(scr, 0, (size_t)(SCR_WORDS + V.total_tiles) * 4, st));
+    if (ctx->scratch_clean_words < scr_words) {
+        VG_STAGE(VG_STAGE_MEMSET, cudaMemsetAsync(scr, 0, scr_words * 4, st));
+    }
+    // both forms leave every accumulated word back at zero (the per-tile
+    // form's scatter counts the tile counts down; the global form's ranges
+    // kernel clears its histograms, pass counters and tile counts)
+    ctx->scratch_clean_words = std::max(ctx->scratch_clean_words, scr_words);
     VG_STAGE(VG_STAGE_PREPROCESS,
              launch_preprocess(sd, V, cs, ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
                                ctx->rect.as<uint2>(), ctx->ntiles.as<uint32_t>(), ctx->dkey[1].as<uint32_t>(), scr,
@@ -687,13 +729,19 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     const uint32_t cap = (uint32_t)ctx->pair_cap;
     // with the per-tile sort the pairs follow the compacted order, so the
     // compaction also produces their offsets (no separate scan)
+    // once the ctx has the backward's gradient rows (after its first
+    // backward), the compaction zeroes those of the visible slots, and always
+    // the pose sums, so that the backward needs no zeroing pass of its own
+    float* g2d_rows = (ctx->g2d_clean && ctx->g2d.bytes >= (size_t)slots * G2D_STRIDE * 4) ? ctx->g2d.as<float>()
+                                                                                            : nullptr;
     VG_STAGE(VG_STAGE_DEPTH_SORT, ([&]() -> cudaError_t {
                  cudaError_t e = launch_compact(V, N, ctx->dkey[1].as<uint32_t>(), ctx->blk_count.as<uint32_t>(),
                                                 ctx->dkey[0].as<uint32_t>(),
                                                 ctx->dval[0].as<uint32_t>(), ctx->vis.as<uint32_t>(),
                                                 ctx->ntiles.as<uint32_t>(),
                                                 tile_sort ? ctx->pair_off.as<uint32_t>() : nullptr,
-                                                ctx->chunk_start.as<uint32_t>(), cap, scr, err, st);
+                                                ctx->chunk_start.as<uint32_t>(), cap, scr, err, g2d_rows,
+                                                ctx->pose_part.as<float>(), n_views * 6, cs, st);
                  if (e != cudaSuccess) return e;
                  for (int p = 0; p < (tile_sort ? 0 : 4); ++p) {
                      const int i = p & 1, o = i ^ 1;
@@ -715,8 +763,9 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
                               scr, tile_sort ? 0 : tp, lb, state, 4u, err, slots, st));
     const int tgrid = sort_pass_grid(cap);
     if (tile_sort) {
-        VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr + SCR_TILE_COUNTS, V.total_tiles, ctx->ranges.as<uint2>(),
-                                               ctx->tile_order.as<uint32_t>(), st));
+        VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr, V.total_tiles, ctx->ranges.as<uint2>(),
+                                               ctx->tile_order.as<uint32_t>(), 0, cs.lf_blk, lf_grid,
+                                               scr + SCR_LOSS_VALID, st));
         VG_STAGE(VG_STAGE_TILE_SORT,
                  launch_tile_scatter(ctx->pkey[0].as<uint32_t>(), ctx->pval[0].as<uint32_t>(), scr + SCR_PAIRS, cap,
                                      ctx->ranges.as<uint2>(), scr + SCR_TILE_COUNTS, ctx->pkey[1].as<uint32_t>(),
@@ -736,8 +785,9 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     const int fin = tile_sort ? 1 : (tp & 1);
     ctx->final_pair = fin;
     if (!tile_sort)
-        VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr + SCR_TILE_COUNTS, V.total_tiles, ctx->ranges.as<uint2>(),
-                                               ctx->tile_order.as<uint32_t>(), st));
+        VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr, V.total_tiles, ctx->ranges.as<uint2>(),
+                                               ctx->tile_order.as<uint32_t>(), 1, cs.lf_blk, lf_grid,
+                                               scr + SCR_LOSS_VALID, st));
     VG_STAGE(VG_STAGE_BLEND_FWD,
              launch_blend_fwd(V, cs, params->ppt_fwd, ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
                               ctx->pval[fin].as<uint32_t>(), tile_sort ? ctx->dkey[1].as<uint32_t>() : nullptr, err,
@@ -750,7 +800,22 @@ vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     ctx->fwd_scene = scene;
     ctx->have_fwd = true;
     ctx->have_bwd = false;
+    ctx->fwd_zeroed = g2d_rows != nullptr;
     return VG_OK;
+}
+
+vg_status vg_render_fwd(vg_scene* scene, const vg_camera* cams, int32_t n_views, const vg_render_params* params,
+                        vg_ctx* ctx, float* C, float* D, float* S, vg_stream stream) {
+    return render_forward(scene, cams, n_views, params, ctx, C, D, S, nullptr, stream);
+}
+
+vg_status vg_render_fwd_l1(vg_scene* scene, const vg_camera* cams, int32_t n_views, const vg_render_params* params,
+                           vg_ctx* ctx, const float* Ct, const float* Dt, float w_depth, float gate, float* C,
+                           float* D, float* S, float* dC, float* dD, float* dS, float* loss, vg_stream stream) {
+    if (!Ct || !Dt || !dC || !dD || !loss) return fail(VG_ERR_INVALID_ARG, "vg_render_fwd_l1: null argument");
+    if (!(w_depth >= 0.f)) return fail(VG_ERR_INVALID_ARG, "vg_render_fwd_l1: w_depth must be >= 0");
+    const FusedLoss lf{Ct, Dt, dC, dD, dS, loss, w_depth, gate};
+    return render_forward(scene, cams, n_views, params, ctx, C, D, S, &lf, stream);
 }
 
 static bool same_views(const Views& a, const Views& b) {
@@ -777,7 +842,6 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     if (ctx->g2d.bytes < (size_t)slots * G2D_STRIDE * 4) ctx->g2d_clean = false;
     VG_TRY(ctx->g2d.ensure(slots * G2D_STRIDE * 4, st, "g2d"));
 
-    VG_TRY(ctx->pose_part.ensure((size_t)n_views * 6 * 4, st, "pose sums"));
     float* gptr[4] = {grads->logscale, grads->rot, grads->opacity, grads->rgb};
 
     // the scene-gradient arrays the chain accumulates into, zeroed together
@@ -806,21 +870,28 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     O.d_off = grads->offsets;
     O.d_mask = sd.mask ? grads->mask_logit : nullptr;
     O.pose_sum = ctx->pose_part.as<float>();
-    zero(O.pose_sum, (int64_t)n_views * 6);
     zero(grads->anchor_xyz, sd.n_anchors * 3);
     // coded scaling factors / offsets receive [L][K][3] codebook gradients
     zero(grads->anchor_l, sd.Ll > 0 ? (int64_t)sd.Ll * sd.Kl * 3 : sd.n_anchors * 3);
     zero(grads->offsets, sd.Lo > 0 ? (int64_t)sd.Lo * sd.Ko * 3 : N * 3);
     zero(grads->mask_logit, N);
+    if (params->grad_accumulate) Z.n = 0;  // the caller keeps the scene gradients zero
 
     const bool prof_graph = capturing(st);
     const bool prof_on = ctx->prof.on;
+    // the forward's compaction zeroed the visible rows and the pose sums, for
+    // this backward only (a second backward of the same forward zeroes again)
+    bool rows_zero = ctx->fwd_zeroed;
+    ctx->fwd_zeroed = false;
     if (!ctx->g2d_clean) {  // rows of slots that were never visible stay zero from here on
         VG_CUDA(cudaMemsetAsync(ctx->g2d.p, 0, ctx->g2d.bytes, st));
         ctx->g2d_clean = true;
+        rows_zero = false;  // (the pose sums still need it)
     }
-    VG_STAGE(VG_STAGE_MEMSET, launch_zero_bwd(ctx->vis.as<uint32_t>(), ctx->scratch.as<uint32_t>() + SCR_NVIS,
-                                              (uint32_t)slots, ctx->g2d.as<float>(), Z, st));
+    if (!rows_zero) zero(O.pose_sum, (int64_t)n_views * 6);
+    if (!rows_zero || Z.n > 0)
+        VG_STAGE(VG_STAGE_MEMSET, launch_zero_bwd(ctx->vis.as<uint32_t>(), ctx->scratch.as<uint32_t>() + SCR_NVIS,
+                                                  rows_zero ? 0u : (uint32_t)slots, ctx->g2d.as<float>(), Z, st));
     VG_STAGE(VG_STAGE_BLEND_BWD,
              launch_blend_bwd(V, cs, params->ppt_bwd, ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
                               ctx->pval[ctx->final_pair].as<uint32_t>(),
@@ -1045,10 +1116,11 @@ vg_status vg_adam_step(const vg_adam_tensor* tensors, int32_t n, float lr, float
     if (!tensors || n < 1 || n > 16) return fail(VG_ERR_INVALID_ARG, "vg_adam_step: need 1..16 tensors");
     if (!step_dev && step_host < 1) return fail(VG_ERR_INVALID_ARG, "vg_adam_step: step must be >= 1");
     float* p[16];
-    const float* g[16];
+    float* g[16];
     float* m[16];
     float* v[16];
     int64_t size[16];
+    uint32_t zero_mask = 0;
     for (int i = 0; i < n; ++i) {
         const vg_adam_tensor& t = tensors[i];
         if (t.n < 0 || (t.n > 0 && (!t.param || !t.grad || !t.m || !t.v)))
@@ -1058,8 +1130,10 @@ vg_status vg_adam_step(const vg_adam_tensor* tensors, int32_t n, float lr, float
         m[i] = t.m;
         v[i] = t.v;
         size[i] = t.n;
+        if (t.zero_grad) zero_mask |= 1u << i;
     }
-    VG_CUDA(launch_adam(n, p, g, m, v, size, lr, beta1, beta2, eps, step_dev, step_host, (cudaStream_t)stream));
+    VG_CUDA(launch_adam(n, p, g, m, v, size, zero_mask, lr, beta1, beta2, eps, step_dev, step_host,
+                        (cudaStream_t)stream));
     return VG_OK;
 }
 

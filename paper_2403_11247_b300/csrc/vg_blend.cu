@@ -214,6 +214,18 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
 #pragma unroll
         for (int c = 0; c < 5; ++c) acc[k][c] = 0.f;
     }
+    if (cs.lf_on) {  // the fused loss reads these targets once the pixels are done: start them towards L2
+        const int64_t HWp = (int64_t)vi.W * vi.H;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k)
+            if (px[k] < vi.W && py[k] < vi.H) {
+                const int64_t i = (int64_t)py[k] * vi.W + px[k], pb = vi.pix_base;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(cs.lf_Ct + 3 * pb + i));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(cs.lf_Ct + 3 * pb + HWp + i));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(cs.lf_Ct + 3 * pb + 2 * HWp + i));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(cs.lf_Dt + pb + i));
+            }
+    }
     const int lane = threadIdx.x & 31;
     const uint2 rg = ranges[gt];
     if (TSORT && rg.y - rg.x > 1) {
@@ -299,6 +311,15 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     }
     const int64_t HW = (int64_t)vi.W * vi.H;
     uint32_t ev = 0, bl = 0;
+    // fused L1 loss (vg_render_fwd_l1): its normalisers were counted before
+    // this launch, so each pixel's gradient is final as the pixel is written
+    float lsum = 0.f, inv_c = 0.f, inv_d = 0.f;
+    if (cs.lf_on) {
+        const float nv = (float)cs.lf_counts[0];
+        const float nsamp = cs.pix_mask ? (float)cs.lf_counts[1] : (float)cs.lf_pixels;
+        inv_c = nsamp > 0.f ? 1.f / (3.f * nsamp) : 0.f;
+        inv_d = nv > 0.f ? cs.lf_wdepth / nv : 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         if (!(px[k] < vi.W && py[k] < vi.H)) continue;
@@ -311,6 +332,18 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
         S[pb + i] = acc[k][4];
         Tfin[pb + i] = T[k];
         ncontrib[pb + i] = last[k];
+        if (cs.lf_on) {
+            const bool smp = cs.pix_mask ? cs.pix_mask[pb + i] != 0 : true;
+            float g0, g1, g2, gd;
+            lsum += loss_pixel(acc[k][0], acc[k][1], acc[k][2], __ldg(cs.lf_Ct + 3 * pb + i),
+                               __ldg(cs.lf_Ct + 3 * pb + HW + i), __ldg(cs.lf_Ct + 3 * pb + 2 * HW + i), acc[k][3],
+                               __ldg(cs.lf_Dt + pb + i), acc[k][4], cs.lf_gate, inv_c, inv_d, g0, g1, g2, gd, smp);
+            cs.lf_dC[3 * pb + i] = g0;
+            cs.lf_dC[3 * pb + HW + i] = g1;
+            cs.lf_dC[3 * pb + 2 * HW + i] = g2;
+            cs.lf_dD[pb + i] = gd;
+            if (cs.lf_dS) cs.lf_dS[pb + i] = 0.f;
+        }
         // examined list entries: up to and including the stopping one
         const uint32_t evk = stop_at[k] == 0xffffffffu ? rg.y - rg.x : stop_at[k] == 0xfffffffeu ? 0u : stop_at[k] + 1;
         if (COUNT && neval) neval[pb + i] = evk;
@@ -325,6 +358,19 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
         }
         if ((threadIdx.x & 31) == 0 && ev) atomicAdd(evals, (unsigned long long)ev);
         if ((threadIdx.x & 31) == 0 && bl) atomicAdd(blended, (unsigned long long)bl);
+    }
+    if (cs.lf_on) {  // the block's share of the loss, one atomic per block
+        __shared__ float s_red[NT / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = lsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) t += s_red[w];
+            atomicAdd(cs.lf_loss, t);
+        }
     }
 }
 

@@ -50,6 +50,19 @@ struct Consts {
     int64_t n_gauss;      // N, for the two arrays above
     int32_t depth_hist;   // the preprocess accumulates depth-key digit histograms (global depth sort)
     const uint8_t* pix_mask;  // [pixels] 0 = not composited (sampled rays); NULL = every pixel
+    // L1 loss gradient written by the forward compositing (vg_render_fwd_l1);
+    // lf_on = 0: off
+    int32_t lf_on;
+    const float* lf_Ct;        // [3 per pixel] target colour, per-view planar like C
+    const float* lf_Dt;        // [pixels] target depth
+    float* lf_dC;              // [3 per pixel] dL/dC
+    float* lf_dD;              // [pixels] dL/dD
+    float* lf_dS;              // [pixels] zeroed (may be NULL)
+    float* lf_loss;            // [1] the loss (zeroed by the preprocess, summed by the compositing blocks)
+    uint32_t* lf_blk;          // [2][compaction blocks] per-block counts of valid depths, sampled pixels
+    const uint32_t* lf_counts; // [2] their totals (written by the ranges kernel)
+    int64_t lf_pixels;         // pixels of all views
+    float lf_wdepth, lf_gate;
 };
 
 // SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
@@ -315,6 +328,25 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// One pixel of the L1 loss (mean |C - Ct| + w_depth mean_{Dt > 0} |D - Dt|,
+// inv_c = 1 / (3 pixels), inv_d = w_depth / valid depths): writes the
+// gradients of the three colour planes and the depth, returns the pixel's
+// share of the loss.  A pixel not sampled, or gated out (S <= gate when
+// gate >= 0, Eq. 21), contributes nothing.  sign(0) = 0.
+__device__ __forceinline__ float loss_pixel(float c0, float c1, float c2, float t0, float t1, float t2, float d,
+                                            float dt, float s, float gate, float inv_c, float inv_d, float& g0,
+                                            float& g1, float& g2, float& gd, bool sampled = true) {
+    const float m = (!sampled || (gate >= 0.f && !(s > gate))) ? 0.f : 1.f;
+    const float r0 = c0 - t0, r1 = c1 - t1, r2 = c2 - t2, rd = d - dt;
+    auto sgn = [](float r) { return (r > 0.f) ? 1.f : ((r < 0.f) ? -1.f : 0.f); };
+    g0 = m * sgn(r0) * inv_c;
+    g1 = m * sgn(r1) * inv_c;
+    g2 = m * sgn(r2) * inv_c;
+    const bool valid = sampled && dt > 0.f;
+    gd = valid ? m * sgn(rd) * inv_d : 0.f;
+    return m * (fabsf(r0) + fabsf(r1) + fabsf(r2)) * inv_c + (valid ? m * fabsf(rd) * inv_d : 0.f);
 }
 
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) { return *(const volatile uint32_t*)p; }

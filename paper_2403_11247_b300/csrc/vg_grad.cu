@@ -514,21 +514,6 @@ __global__ void count_valid_kernel(const float* __restrict__ Dt, const uint8_t* 
     if ((threadIdx.x & 31) == 0 && mask && ns) atomicAdd(count + 1, ns);
 }
 
-// one pixel of the loss: colour residuals of the three planes, depth residual
-__device__ __forceinline__ float loss_pixel(float c0, float c1, float c2, float t0, float t1, float t2, float d,
-                                            float dt, float s, float gate, float inv_c, float inv_d, float& g0,
-                                            float& g1, float& g2, float& gd, bool sampled = true) {
-    const float m = (!sampled || (gate >= 0.f && !(s > gate))) ? 0.f : 1.f;
-    const float r0 = c0 - t0, r1 = c1 - t1, r2 = c2 - t2, rd = d - dt;
-    auto sgn = [](float r) { return (r > 0.f) ? 1.f : ((r < 0.f) ? -1.f : 0.f); };
-    g0 = m * sgn(r0) * inv_c;
-    g1 = m * sgn(r1) * inv_c;
-    g2 = m * sgn(r2) * inv_c;
-    const bool valid = sampled && dt > 0.f;
-    gd = valid ? m * sgn(rd) * inv_d : 0.f;
-    return m * (fabsf(r0) + fabsf(r1) + fabsf(r2)) * inv_c + (valid ? m * fabsf(rd) * inv_d : 0.f);
-}
-
 __global__ void loss_l1_kernel(int64_t n_pix, int64_t total, const float* __restrict__ C, const float* __restrict__ D,
                                const float* __restrict__ S, const float* __restrict__ Ct, const float* __restrict__ Dt,
                                const uint8_t* __restrict__ mask, float w_depth, float gate,

@@ -65,6 +65,9 @@ vg_status set_error(vg_status s, const char* msg);
 
 // preprocess.cu
 int preprocess_blocks(int64_t N);
+// the compaction's grid (preprocess_blocks, widened for the fused loss's
+// counts when cs.lf_on)
+int compact_grid(int64_t N, const Consts& cs);
 cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& cs, float4* xy, float4* conic_o,
                               float4* rgbd, uint2* rect, uint32_t* ntiles, uint32_t* dkey, uint32_t* scratch,
                               uint32_t* state, uint32_t* blk_count, cudaStream_t st);
@@ -73,10 +76,14 @@ cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& c
 // [blocks] pair counts; with pair_off the pair offsets of the compacted
 // order, the chunk starts, the pair count and the overflow flag are produced
 // here and launch_duplicate skips its own scan
+// g2d_rows (may be NULL): the backward's per-slot gradient rows, zeroed here
+// for every visible slot; pose_zero [n_pose] (may be NULL): zeroed too.
+// With cs.lf_on it also counts the fused loss's normalisers per block into
+// cs.lf_blk [2][compact_grid] (the ranges kernel sums them).
 cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count,
                            uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, const uint32_t* ntiles,
                            uint32_t* pair_off, uint32_t* chunk_start, uint32_t cap, uint32_t* scratch, uint32_t* err,
-                           cudaStream_t st);
+                           float* g2d_rows, float* pose_zero, int n_pose, const Consts& cs, cudaStream_t st);
 cudaError_t launch_rvq_decode(int dim, int L, int K, const float* cb, const uint8_t* idx, const float* raw,
                               int64_t n, float* out, cudaStream_t st);
 
@@ -98,8 +105,13 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, ui
                              uint32_t cap, uint32_t* scratch, int tile_passes, unsigned long long* lookback,
                              const uint32_t* state, uint32_t epoch_offset, uint32_t* err, int64_t max_slots,
                              cudaStream_t st);
-// per-tile [start, end) from the per-tile pair counts (one-block scan)
-cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, uint32_t* order, cudaStream_t st);
+// per-tile [start, end) from the per-tile pair counts at scratch +
+// SCR_TILE_COUNTS (one-block scan); clear: zero the counts, the digit
+// histograms and the pass counters afterwards (global-sort form).  With
+// lf_blk (may be NULL) also the fused loss's counts: lf_counts[c] = sum of
+// lf_blk[c * lf_grid + b] over b.
+cudaError_t launch_ranges(uint32_t* scratch, int n_tiles, uint2* ranges, uint32_t* order, int clear,
+                          const uint32_t* lf_blk, int lf_grid, uint32_t* lf_counts, cudaStream_t st);
 cudaError_t launch_epoch_bump(uint32_t* state, uint32_t by, cudaStream_t st);
 // group the pairs by tile (unordered within a tile) into the ranges; counts
 // (the per-tile pair counts the ranges came from) end at zero
@@ -184,9 +196,10 @@ cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const flo
                            float* dD, float* loss, uint32_t* valid_count, uint32_t* err, cudaStream_t st);
 
 // optim.cu
-cudaError_t launch_adam(int n, float* const* p, const float* const* g, float* const* m, float* const* v,
-                        const int64_t* size, float lr, float b1, float b2, float eps, int32_t* step_dev,
-                        int32_t step_host, cudaStream_t st);
+// zero_mask bit t: tensor t's gradient is zeroed once read
+cudaError_t launch_adam(int n, float* const* p, float* const* g, float* const* m, float* const* v,
+                        const int64_t* size, uint32_t zero_mask, float lr, float b1, float b2, float eps,
+                        int32_t* step_dev, int32_t step_host, cudaStream_t st);
 cudaError_t launch_pose_step(int n_views, float* pose, const float* dxi, float* m, float* v, float lr_rot,
                              float lr_trans, float b1, float b2, float eps, int32_t* step_dev, int32_t step_host,
                              cudaStream_t st);

@@ -7,8 +7,9 @@ namespace vgk {
 
 struct AdamPack {
     int32_t n;
+    uint32_t zero_mask;  // bit t: tensor t's gradient is zeroed once read
     float* p[16];
-    const float* g[16];
+    float* g[16];
     float* m[16];
     float* v[16];
     int64_t size[16];
@@ -45,7 +46,8 @@ __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamP
         int t = 0;
         while (c >= A.chunk_end[t]) ++t;
         float* __restrict__ P = A.p[t];
-        const float* __restrict__ G = A.g[t];
+        float* __restrict__ G = A.g[t];
+        const bool zg = (A.zero_mask >> t) & 1u;
         float* __restrict__ M = A.m[t];
         float* __restrict__ Vv = A.v[t];
         const int64_t n = A.size[t];
@@ -58,6 +60,7 @@ __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamP
             float4 m = reinterpret_cast<float4*>(M)[i];
             float4 v = reinterpret_cast<float4*>(Vv)[i];
             const float4 g = reinterpret_cast<const float4*>(G)[i];
+            if (zg) reinterpret_cast<float4*>(G)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             adam_update(p.x, m.x, v.x, g.x, b1, b2, step_size, inv_sqrt_bc2, eps);
             adam_update(p.y, m.y, v.y, g.y, b1, b2, step_size, inv_sqrt_bc2, eps);
             adam_update(p.z, m.z, v.z, g.z, b1, b2, step_size, inv_sqrt_bc2, eps);
@@ -69,7 +72,9 @@ __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamP
             const int64_t i1 = i0 + 4 < n ? i0 + 4 : n;
             for (int64_t i = i0; i < i1; ++i) {
                 float p = P[i], m = M[i], v = Vv[i];
-                adam_update(p, m, v, G[i], b1, b2, step_size, inv_sqrt_bc2, eps);
+                const float g = G[i];
+                if (zg) G[i] = 0.f;
+                adam_update(p, m, v, g, b1, b2, step_size, inv_sqrt_bc2, eps);
                 P[i] = p;
                 M[i] = m;
                 Vv[i] = v;
@@ -80,11 +85,12 @@ __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamP
 
 __global__ void step_increment_kernel(int32_t* step_dev) { step_dev[0] += 1; }
 
-cudaError_t launch_adam(int n, float* const* p, const float* const* g, float* const* m, float* const* v,
-                        const int64_t* size, float lr, float b1, float b2, float eps, int32_t* step_dev,
-                        int32_t step_host, cudaStream_t st) {
+cudaError_t launch_adam(int n, float* const* p, float* const* g, float* const* m, float* const* v,
+                        const int64_t* size, uint32_t zero_mask, float lr, float b1, float b2, float eps,
+                        int32_t* step_dev, int32_t step_host, cudaStream_t st) {
     AdamPack A;
     A.n = n;
+    A.zero_mask = zero_mask;
     int64_t total = 0;
     for (int i = 0; i < n; ++i) {
         A.p[i] = p[i];

@@ -37,6 +37,8 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(SceneDev S, const __
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) state[ST_EPOCH] += 16u;  // fresh lookback epochs for this forward
+    // the fused L1 loss's value (summed by the compositing) starts from zero
+    if (cs.lf_on && blockIdx.x == 0 && threadIdx.x == 0) *cs.lf_loss = 0.f;
     __syncthreads();
     // A decoded log-scale component is a sum over stages of one codeword
     // entry each, so it is at most the sum of each stage's largest entry:
@@ -234,7 +236,6 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(SceneDev S, const __
         if (h) atomicAdd(scratch + SCR_DEPTH_HIST + i, h);
     }
     if (threadIdx.x == 0) {
-        if (s_cnt[0]) atomicAdd(scratch + SCR_NVIS, s_cnt[0]);
         blk_count[blockIdx.x] = s_cnt[0];
         blk_count[gridDim.x + blockIdx.x] = s_cnt[1];  // the block's (slot, tile) pairs
     }
@@ -252,17 +253,59 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(SceneDev S, const __
 // scan of the tile counts in this order, from the per-block pair counts that
 // follow the slot counts), and marks the 256-pair chunks that start inside
 // its pairs; the last block writes the pair count (flagged when above cap)
-// and the sentinel pair_off[visible slots].
+// and the sentinel pair_off[visible slots].  The last block also writes the
+// number of visible slots (scratch[SCR_NVIS]): a plain store, so that word
+// needs no zeroing between forwards.
 __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Views V, int64_t N,
                                                       const uint32_t* __restrict__ dkey,
                                                       const uint32_t* __restrict__ cnt, uint32_t* __restrict__ keys_out,
                                                       uint32_t* __restrict__ vals_out, uint32_t* __restrict__ vals_copy,
                                                       const uint32_t* __restrict__ ntiles, uint32_t* __restrict__ pair_off,
                                                       uint32_t* __restrict__ chunk_start, uint32_t cap,
-                                                      uint32_t* __restrict__ scratch, uint32_t* __restrict__ err) {
+                                                      uint32_t* __restrict__ scratch, uint32_t* __restrict__ err,
+                                                      float* __restrict__ g2d_rows, float* __restrict__ pose_zero,
+                                                      int n_pose, int nb, const Consts cs) {
     __shared__ uint32_t s_tmp[8];
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < n_pose; i += 256) pose_zero[i] = 0.f;
+    if (cs.lf_on) {
+        // the fused L1 loss's normalisers, counted before any pixel is
+        // composited: valid target depths and sampled pixels, per block
+        // (plain stores; the ranges kernel sums them).  The grid covers at
+        // most 4,096 pixels a block; blocks past the compaction's own only
+        // count.
+        uint32_t c = 0, ns = 0, ct, nst;
+        const int64_t tid = (int64_t)blockIdx.x * 256 + threadIdx.x, nthr = (int64_t)gridDim.x * 256;
+        // four pixels a load where the depth plane (and the mask) allow it
+        const bool vec = (reinterpret_cast<uintptr_t>(cs.lf_Dt) & 15u) == 0 &&
+                         (reinterpret_cast<uintptr_t>(cs.pix_mask) & 3u) == 0;
+        const int64_t n4 = vec ? cs.lf_pixels / 4 : 0;
+        for (int64_t i = tid; i < n4; i += nthr) {
+            const float4 d = __ldg(reinterpret_cast<const float4*>(cs.lf_Dt) + i);
+            if (cs.pix_mask) {
+                const uchar4 m = reinterpret_cast<const uchar4*>(cs.pix_mask)[i];
+                c += (m.x && d.x > 0.f) + (m.y && d.y > 0.f) + (m.z && d.z > 0.f) + (m.w && d.w > 0.f);
+                ns += (m.x != 0) + (m.y != 0) + (m.z != 0) + (m.w != 0);
+            } else {
+                c += (d.x > 0.f) + (d.y > 0.f) + (d.z > 0.f) + (d.w > 0.f);
+                ns += 4;
+            }
+        }
+        for (int64_t i = n4 * 4 + tid; i < cs.lf_pixels; i += nthr) {
+            const bool smp = cs.pix_mask ? cs.pix_mask[i] != 0 : true;
+            c += smp && __ldg(cs.lf_Dt + i) > 0.f;
+            ns += smp;
+        }
+        block_excl_scan_256(c, s_tmp, &ct);
+        block_excl_scan_256(ns, s_tmp, &nst);
+        if (threadIdx.x == 0) {
+            cs.lf_blk[blockIdx.x] = ct;
+            cs.lf_blk[gridDim.x + blockIdx.x] = nst;
+        }
+    }
+    if ((int)blockIdx.x >= nb) return;
     const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    const int b = (int)blockIdx.x, nb = (int)gridDim.x;
+    const int b = (int)blockIdx.x;
     uint32_t a = 0, p = 0;
     for (int j = threadIdx.x; j < b; j += 256) {
         a += cnt[j];
@@ -281,6 +324,10 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
             keys_out[off + pre] = key;
             vals_out[off + pre] = (uint32_t)slot;
             if (vals_copy) vals_copy[off + pre] = (uint32_t)slot;
+            if (g2d_rows) {  // the backward's gradient row of this slot starts at zero
+                float4* row = reinterpret_cast<float4*>(g2d_rows + slot * G2D_STRIDE);
+                row[0] = row[1] = row[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
         if (pair_off) {
             const uint32_t c = f ? ntiles[slot] : 0u;
@@ -294,14 +341,26 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
         }
         off += tot;
     }
-    if (pair_off && b == nb - 1 && threadIdx.x == 0) {
-        scratch[SCR_PAIRS] = poff;
-        if (poff > cap) atomicOr(err, ERR_OVERFLOW);
-        pair_off[off] = poff;
+    if (b == nb - 1 && threadIdx.x == 0) {
+        scratch[SCR_NVIS] = off;
+        if (pair_off) {
+            scratch[SCR_PAIRS] = poff;
+            if (poff > cap) atomicOr(err, ERR_OVERFLOW);
+            pair_off[off] = poff;
+        }
     }
 }
 
 int preprocess_blocks(int64_t N) { return (int)ceil_div(N > 0 ? N : 1, 256); }
+
+// with the fused loss the compaction grid counts its normalisers too: a
+// block per 4,096 pixels at least
+int compact_grid(int64_t N, const Consts& cs) {
+    const int64_t blocks = preprocess_blocks(N);
+    return (int)(cs.lf_on ? std::max<int64_t>(blocks, ceil_div(cs.lf_pixels, 4096)) : blocks);
+}
+
+
 
 static size_t codebook_smem(const SceneDev& S) {
     size_t n = 0;
@@ -326,11 +385,13 @@ cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& c
 cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count,
                            uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, const uint32_t* ntiles,
                            uint32_t* pair_off, uint32_t* chunk_start, uint32_t cap, uint32_t* scratch, uint32_t* err,
-                           cudaStream_t st) {
+                           float* g2d_rows, float* pose_zero, int n_pose, const Consts& cs, cudaStream_t st) {
     const int blocks = preprocess_blocks(N);
+    const int64_t grid = compact_grid(N, cs);
     count_launches(1);
-    compact_kernel<<<blocks, 256, 0, st>>>(V, N, dkey, blk_count, keys_out, vals_out, vals_copy, ntiles, pair_off,
-                                           chunk_start, cap, scratch, err);
+    compact_kernel<<<(unsigned)grid, 256, 0, st>>>(V, N, dkey, blk_count, keys_out, vals_out, vals_copy, ntiles,
+                                                   pair_off, chunk_start, cap, scratch, err, g2d_rows, pose_zero,
+                                                   pose_zero ? n_pose : 0, blocks, cs);
     return cudaGetLastError();
 }
 

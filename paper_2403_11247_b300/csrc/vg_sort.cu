@@ -386,11 +386,17 @@ __device__ __forceinline__ int order_bucket(uint32_t c, uint32_t cmax) {
     return ORDER_BUCKETS - 1 - (int)(((uint64_t)c * (ORDER_BUCKETS - 1)) / (cmax > 0 ? cmax : 1u));
 }
 
-__global__ void __launch_bounds__(1024) ranges_kernel(const uint32_t* __restrict__ cnt_g, int n,
+// clear: (global-sort form, where this kernel is the last reader) zero the
+// tile counts, the digit histograms and the pass counters afterwards, so the
+// next forward starts from clean scratch without a memset
+__global__ void __launch_bounds__(1024) ranges_kernel(uint32_t* __restrict__ cnt_g, int n,
                                                       uint2* __restrict__ ranges, uint32_t* __restrict__ order,
-                                                      int staged) {
+                                                      int staged, uint32_t* __restrict__ scratch, int clear,
+                                                      const uint32_t* __restrict__ lf_blk, int lf_grid,
+                                                      uint32_t* __restrict__ lf_counts) {
     __shared__ uint32_t s_w[32];
     __shared__ uint32_t s_carry, s_max;
+    __shared__ uint32_t s_lf[2];
     __shared__ uint32_t s_bin[ORDER_BUCKETS];
     extern __shared__ uint32_t s_cnt[];  // the counts, when they fit: one coalesced load for all three uses
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -401,8 +407,25 @@ __global__ void __launch_bounds__(1024) ranges_kernel(const uint32_t* __restrict
         s_carry = 0;
         s_max = 0;
     }
+    if (threadIdx.x < 2) s_lf[threadIdx.x] = 0;
     for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) s_bin[i] = 0;
     __syncthreads();
+    if (lf_blk) {  // the fused loss's normalisers from the compaction's per-block counts
+        uint32_t c = 0, ns = 0;
+        for (int i = threadIdx.x; i < lf_grid; i += blockDim.x) {
+            c += lf_blk[i];
+            ns += lf_blk[lf_grid + i];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            ns += __shfl_xor_sync(0xffffffffu, ns, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&s_lf[0], c);
+            atomicAdd(&s_lf[1], ns);
+        }
+    }
     uint32_t mymax = 0;
     for (int c0 = 0; c0 < n; c0 += 1024) {
         const int i = c0 + threadIdx.x;
@@ -431,6 +454,10 @@ __global__ void __launch_bounds__(1024) ranges_kernel(const uint32_t* __restrict
         __syncthreads();
         if (threadIdx.x == 0) s_carry += s_w[31];
         __syncthreads();
+    }
+    if (lf_blk && threadIdx.x == 0) {  // (s_lf is complete: the scan's barriers came after its adds)
+        lf_counts[0] = s_lf[0];
+        lf_counts[1] = s_lf[1];
     }
     if (!order) return;
 #pragma unroll
@@ -462,15 +489,23 @@ __global__ void __launch_bounds__(1024) ranges_kernel(const uint32_t* __restrict
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) order[atomicAdd(&s_bin[order_bucket(cnt[i], cmax)], 1u)] = (uint32_t)i;
+    if (clear) {
+        __syncthreads();  // every count has been read
+        for (int i = threadIdx.x; i < n; i += blockDim.x) cnt_g[i] = 0u;
+        for (int i = threadIdx.x; i < SCR_NVIS; i += blockDim.x) scratch[i] = 0u;  // digit histograms
+        for (int i = SCR_CNT_DEPTH + (int)threadIdx.x; i < SCR_CNT_TILE + 3; i += blockDim.x) scratch[i] = 0u;
+    }
 }
 
-cudaError_t launch_ranges(const uint32_t* tile_counts, int n_tiles, uint2* ranges, uint32_t* order, cudaStream_t st) {
+cudaError_t launch_ranges(uint32_t* scratch, int n_tiles, uint2* ranges, uint32_t* order, int clear,
+                          const uint32_t* lf_blk, int lf_grid, uint32_t* lf_counts, cudaStream_t st) {
     count_launches(1);
     const int staged = n_tiles <= RANGES_SMEM_TILES ? 1 : 0;
     const size_t smem = staged ? (size_t)n_tiles * 4 : 0;
     cudaError_t e = allow_dynamic_smem((const void*)ranges_kernel, smem);
     if (e != cudaSuccess) return e;
-    ranges_kernel<<<1, 1024, smem, st>>>(tile_counts, n_tiles, ranges, order, staged);
+    ranges_kernel<<<1, 1024, smem, st>>>(scratch + SCR_TILE_COUNTS, n_tiles, ranges, order, staged, scratch, clear,
+                                         lf_blk, lf_grid, lf_counts);
     return cudaGetLastError();
 }
 

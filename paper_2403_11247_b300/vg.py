@@ -59,7 +59,7 @@ class vg_render_params(C.Structure):
                 ("sigma_cull", C.c_float), ("clamp_factor", C.c_float),
                 ("jacobian_clamp", C.c_int32), ("count_evals", C.c_int32), ("pose_dev", C.c_void_p),
                 ("ppt_fwd", C.c_int32), ("ppt_bwd", C.c_int32), ("hit_count", C.c_void_p), ("seen", C.c_void_p),
-                ("sort_mode", C.c_int32), ("pixel_mask", C.c_void_p)]
+                ("sort_mode", C.c_int32), ("pixel_mask", C.c_void_p), ("grad_accumulate", C.c_int32)]
 
 
 class vg_scene_grads(C.Structure):
@@ -97,6 +97,7 @@ def lib():
             "vg_ctx_profile_read": [P, P, P, P],
             "vg_rvq_decode": [P, I64, P, P],
             "vg_render_fwd": [P, P, I32, P, P, P, P, P, P],
+            "vg_render_fwd_l1": [P, P, I32, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P, P, P, P],
             "vg_render_bwd": [P, P, I32, P, P, P, P, P, P, P],
             "vg_pose_grad": [P, I32, P, P, P, P, P],
             "vg_loss_l1": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P, P],
@@ -514,6 +515,29 @@ def vg_render_fwd(scene: SceneHandle, cams, params: Optional[vg_render_params], 
     return C_, D, S
 
 
+def vg_render_fwd_l1(scene: SceneHandle, cams, params: Optional[vg_render_params], ctx: CtxHandle, Ct, Dt,
+                     w_depth: float = 0.5, gate: float = -1.0, C_=None, D=None, S=None, dC=None, dD=None, dS=None,
+                     loss=None, stream=None):
+    """Forward with the L1 loss gradient written by the compositing kernel:
+    returns (C, D, S, dC, dD, loss) CUDA tensors (dS, if given, is zeroed)."""
+    torch = _torch()
+    P = sum(image_sizes(cams))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f32 = dict(dtype=torch.float32, device=dev)
+    C_ = torch.empty(3 * P, **f32) if C_ is None else C_
+    D = torch.empty(P, **f32) if D is None else D
+    S = torch.empty(P, **f32) if S is None else S
+    dC = torch.empty(3 * P, **f32) if dC is None else dC
+    dD = torch.empty(P, **f32) if dD is None else dD
+    loss = torch.empty(1, **f32) if loss is None else loss
+    p = params if params is not None else default_params()
+    cc = cameras(cams)
+    _check(lib().vg_render_fwd_l1(scene.handle, cc, len(cams), C.byref(p), ctx.handle, _ptr(Ct), _ptr(Dt),
+                                  float(w_depth), float(gate), _ptr(C_), _ptr(D), _ptr(S), _ptr(dC), _ptr(dD), _ptr(dS),
+                                  _ptr(loss), _stream(stream)), "vg_render_fwd_l1")
+    return C_, D, S, dC, dD, loss
+
+
 def grads_like(scene: SceneHandle, device=None, mask=True):
     """Allocate a full set of gradient tensors for ``scene``."""
     torch = _torch()
@@ -639,17 +663,20 @@ def _cudart():
 
 
 class vg_adam_tensor(C.Structure):
-    _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p), ("n", C.c_int64)]
+    _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p), ("n", C.c_int64),
+                ("zero_grad", C.c_int32)]
 
 
 def vg_adam_step(params, grads, ms, vs, lr, beta1=0.9, beta2=0.999, eps=1e-15, step_dev=None, step_host=0,
-                 stream=None):
-    """Adam over lists of equally-shaped CUDA tensors (one launch)."""
+                 stream=None, zero_grad=False):
+    """Adam over lists of equally-shaped CUDA tensors (one launch); with
+    zero_grad each gradient is set to zero once read."""
     n = len(params)
     arr = (vg_adam_tensor * n)()
     for i in range(n):
         arr[i].param, arr[i].grad = _ptr(params[i]), _ptr(grads[i])
         arr[i].m, arr[i].v, arr[i].n = _ptr(ms[i]), _ptr(vs[i]), params[i].numel()
+        arr[i].zero_grad = 1 if zero_grad else 0
     _check(lib().vg_adam_step(arr, n, lr, beta1, beta2, eps, _ptr(step_dev), int(step_host), _stream(stream)),
            "vg_adam_step")
 
@@ -708,7 +735,7 @@ def exported_symbols():
             "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
             "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune", "vg_ssim_loss", "vg_icp_associate",
             "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune", "vg_host_alloc", "vg_host_free", "vg_memcpy_async", "vg_host_stage",
-            "vg_loss_l1_masked", "vg_sample_rays"]
+            "vg_loss_l1_masked", "vg_sample_rays", "vg_render_fwd_l1"]
 
 
 PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),

@@ -53,8 +53,8 @@ def test_struct_layouts_match_the_c_header(tmp_path):
 #include <stddef.h>
 #include "vg.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(vg_camera), sizeof(vg_attr_group), sizeof(vg_scene_desc),
-         sizeof(vg_render_params), sizeof(vg_scene_grads), sizeof(vg_stats));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(vg_camera), sizeof(vg_attr_group), sizeof(vg_scene_desc),
+         sizeof(vg_render_params), sizeof(vg_scene_grads), sizeof(vg_stats), sizeof(vg_adam_tensor));
   printf("%zu %zu %zu %zu\\n", offsetof(vg_scene_desc, rot), offsetof(vg_scene_desc, mask_eps),
          offsetof(vg_render_params, pose_dev), offsetof(vg_camera, near_plane));
   return 0;
@@ -65,7 +65,7 @@ int main(void) {
     sizes, offs = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.strip().split("\n")
     assert [int(x) for x in sizes.split()] == [C.sizeof(t) for t in (V.vg_camera, V.vg_attr_group, V.vg_scene_desc,
                                                                       V.vg_render_params, V.vg_scene_grads,
-                                                                      V.vg_stats)]
+                                                                      V.vg_stats, V.vg_adam_tensor)]
     assert [int(x) for x in offs.split()] == [V.vg_scene_desc.rot.offset, V.vg_scene_desc.mask_eps.offset,
                                               V.vg_render_params.pose_dev.offset, V.vg_camera.near_plane.offset]
 
