@@ -276,29 +276,32 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
 #pragma unroll
                     for (int k = 0; k < PPT; ++k) hb -= nb[k];
                 }
+                // branch-free per pixel: a pixel that is done, meets a
+                // positive exponent or an alpha below alpha_min gets alpha =
+                // 0 by select (Tn = T, w = 0: every update an exact no-op); a
+                // pixel that stops is not blended
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    if (done[k]) continue;
                     const float dx = __fsub_rn(g.x, fpx[k]), dy = __fsub_rn(g.y, fpy[k]);
                     const float p2 = gauss_p2(co.x, co.y, co.z, dx, dy);
                     const float q = __fsub_rn(p2, co.w);
-                    if (p2 > 0.f || q < 0.f) continue;  // positive exponent, or alpha < alpha_min
-                    const float alpha = fminf(cs.alpha_max, __fmul_rn(cs.alpha_min, fast_exp2(q)));
+                    const bool live = !done[k] && !(p2 > 0.f) && !(q < 0.f);
+                    const float e2 = fast_exp2(q);
+                    const float alpha = live ? fminf(cs.alpha_max, __fmul_rn(cs.alpha_min, e2)) : 0.f;
                     const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
-                    if (Tn < cs.t_min) {
-                        done[k] = true;
-                        if (COUNT) stop_at[k] = b - rg.x + i;
-                        continue;
-                    }
-                    const float w = alpha * T[k];
+                    const bool stop = live && Tn < cs.t_min;
+                    const bool blend = live && !stop;
+                    if (COUNT) stop_at[k] = stop ? b - rg.x + i : stop_at[k];
+                    done[k] = done[k] || stop;
+                    const float w = blend ? alpha * T[k] : 0.f;
                     acc[k][0] = fmaf(cd.x, w, acc[k][0]);
                     acc[k][1] = fmaf(cd.y, w, acc[k][1]);
                     acc[k][2] = fmaf(cd.z, w, acc[k][2]);
                     acc[k][3] = fmaf(cd.w, w, acc[k][3]);
                     acc[k][4] += w;
-                    T[k] = Tn;
-                    last[k] = b - rg.x + i + 1;
-                    if (HITS || COUNT) ++nb[k];
+                    T[k] = blend ? Tn : T[k];
+                    last[k] = blend ? b - rg.x + i + 1 : last[k];
+                    if (HITS || COUNT) nb[k] += blend ? 1u : 0u;
                 }
                 if (HITS) {
 #pragma unroll
@@ -524,17 +527,24 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
 #pragma unroll
                 for (int c = 0; c < 10; ++c) vals[c] = 0.f;
                 bool any = false;
+                // Branch-free per pixel: a pixel that does not blend this
+                // Gaussian (past its last contributor, positive exponent,
+                // alpha below alpha_min) gets alpha = x = 0 by select, which
+                // makes every update below an exact no-op; a pixel that
+                // blends takes exactly the arithmetic of the walk.  (Whole
+                // warps rarely skip a visited Gaussian, so branching around
+                // the update costs more in reconvergence than it saves.)
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    if (jl >= nc[k]) continue;
                     const float dx = __fsub_rn(g.x, fpx[k]), dy = __fsub_rn(g.y, fpy[k]);
                     const float p2 = gauss_p2(co.x, co.y, co.z, dx, dy);
                     const float q = __fsub_rn(p2, co.w);
-                    if (p2 > 0.f || q < 0.f) continue;
-                    const float x = __fmul_rn(cs.alpha_min, fast_exp2(q));  // o e^power before the cap
+                    const bool live = jl < nc[k] && !(p2 > 0.f) && !(q < 0.f);
+                    const float e2 = fast_exp2(q);
+                    const float x = live ? __fmul_rn(cs.alpha_min, e2) : 0.f;  // o e^power before the cap
                     const float alpha = fminf(cs.alpha_max, x);
                     const float inv = __fdividef(1.f, 1.f - alpha);  // hardware reciprocal, ~2 ulp
-                    T[k] *= inv;  // transmittance in front of this Gaussian
+                    T[k] = live ? T[k] * inv : T[k];  // transmittance in front of this Gaussian
                     const float w = gp[k][0] * cd.x + gp[k][1] * cd.y + gp[k][2] * cd.z + gp[k][3] * cd.w + gp[k][4];
                     const float dA = T[k] * w - Bk[k] * inv;
                     const float wt = alpha * T[k];
@@ -543,19 +553,20 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
                     vals[7] = fmaf(wt, gp[k][1], vals[7]);
                     vals[8] = fmaf(wt, gp[k][2], vals[8]);
                     vals[9] = fmaf(wt, gp[k][3], vals[9]);
-                    if (x <= cs.alpha_max) {
-                        // the per-Gaussian factors (e^power = x / o, the signs and
-                        // halves of the conic terms) are applied once per visit below
-                        const float dp = alpha * dA;
-                        const float pdx = dp * dx, pdy = dp * dy;
-                        vals[5] = fmaf(x, dA, vals[5]);
-                        vals[0] = fmaf(nat.x, pdx, fmaf(nat.y, pdy, vals[0]));
-                        vals[1] = fmaf(nat.y, pdx, fmaf(nat.z, pdy, vals[1]));
-                        vals[2] = fmaf(pdx, dx, vals[2]);
-                        vals[3] = fmaf(pdx, dy, vals[3]);
-                        vals[4] = fmaf(pdy, dy, vals[4]);
-                    }
-                    any = true;
+                    // capped alpha is constant: no conic, mean or opacity terms.
+                    // The per-Gaussian factors (e^power = x / o, the signs and
+                    // halves of the conic terms) are applied once per visit below
+                    const bool unc = x <= cs.alpha_max;
+                    const float dp = unc ? alpha * dA : 0.f;
+                    const float xu = unc ? x : 0.f;
+                    const float pdx = dp * dx, pdy = dp * dy;
+                    vals[5] = fmaf(xu, dA, vals[5]);
+                    vals[0] = fmaf(nat.x, pdx, fmaf(nat.y, pdy, vals[0]));
+                    vals[1] = fmaf(nat.y, pdx, fmaf(nat.z, pdy, vals[1]));
+                    vals[2] = fmaf(pdx, dx, vals[2]);
+                    vals[3] = fmaf(pdx, dy, vals[3]);
+                    vals[4] = fmaf(pdy, dy, vals[4]);
+                    any |= live;
                 }
                 if (__any_sync(0xffffffffu, any)) {
                     const float sum = warp_reduce10(vals);
