@@ -330,7 +330,6 @@ def local_ba_leg(torch, V, synth, iters=50):
     iterations captured in one CUDA graph, against the same iterations
     launched one by one."""
     from paper_2403_11247_b300.autograd import SceneParams
-    from paper_2403_11247_b300.autotune import autotune_ppt
     from paper_2403_11247_b300.batch import LocalBA, pose_errors
     scene = SceneParams.from_synth(synth.tiny_scene(), requires_grad=False)
     sh = scene.handle()
@@ -339,8 +338,7 @@ def local_ba_leg(torch, V, synth, iters=50):
     ctx = V.vg_ctx_create(0)
     Ct, Dt, _ = V.render_with_retry(sh, truth, V.default_params(), ctx)
     ba = LocalBA(scene, pert, Ct.clone(), Dt.clone(), lr_rot=2e-3, lr_trans=2e-3, lr_map=1e-4)
-    tune = autotune_ppt(sh, ba.cams, ba.ctx, ba.dC, ba.dD, None, ba.grads, reps=3, pose_dev=ba.pose)
-    ba.params = V.default_params(pose_dev=ba.pose, ppt_fwd=tune["ppt_fwd"], ppt_bwd=tune["ppt_bwd"])
+    tune = ba.autotune(reps=3)     # pixels per thread, staging batch, persistent CTAs
     T_true = np.stack([np.asarray(c.T_cw, np.float64) for c in truth])
     pose0 = ba.pose.clone()
     map0 = [p.clone() for p in ba.map_params]
@@ -795,17 +793,17 @@ def run_ours(args):
     if st != V.VG_OK:
         raise RuntimeError(f"device status {V.STATUS_NAMES[st]} during warmup")
     # launch shape of the blend kernels, picked on this workload
-    from paper_2403_11247_b300.autotune import autotune_ppt
+    from paper_2403_11247_b300.autotune import autotune_launch, launch_params
     b = w["bufs"]
     if args.no_autotune:
         tune = {"ppt_fwd": args.ppt_fwd or 2, "ppt_bwd": args.ppt_bwd or 2, "autotuned": False}
     else:
-        tune = autotune_ppt(w["sh"], [w["cam"]], w["ctx"], b["dC"], b["dD"], None, w["grads"], reps=5)
+        tune = autotune_launch(w["sh"], [w["cam"]], w["ctx"], b["dC"], b["dD"], None, w["grads"], reps=5)
     if args.ppt_fwd:
         tune["ppt_fwd"] = args.ppt_fwd
     if args.ppt_bwd:
         tune["ppt_bwd"] = args.ppt_bwd
-    w["params"] = V.default_params(ppt_fwd=tune["ppt_fwd"], ppt_bwd=tune["ppt_bwd"])
+    w["params"] = V.default_params(**launch_params(tune))
     for g in w["grads"].values():   # the tuner's backwards left gradients behind
         g.zero_()
     step = make_step(V, w)
@@ -819,9 +817,9 @@ def run_ours(args):
     # nodes) and the device work counters; it is replayed separately for the
     # stage breakdown and the roofline, so that neither costs the timed graph
     # anything.
-    w["params"] = V.default_params(ppt_fwd=tune["ppt_fwd"], ppt_bwd=tune["ppt_bwd"])
+    w["params"] = V.default_params(**launch_params(tune))
     step = make_step(V, w)
-    w_prof = dict(w, params=V.default_params(count_evals=1, ppt_fwd=tune["ppt_fwd"], ppt_bwd=tune["ppt_bwd"]))
+    w_prof = dict(w, params=V.default_params(count_evals=1, **launch_params(tune)))
     step_prof = make_step(V, w_prof)
     graph = graph_prof = None
     launches0 = V.vg_launch_count()

@@ -132,7 +132,13 @@ typedef struct {
  *   [floor((u-r)/16), floor((u+r)/16)+1) x [same for v], clipped to the image;
  *   with jacobian_clamp, x/z and y/z inside the projection Jacobian are
  *   clamped to +-clamp_factor * (W/2)/fx and +-clamp_factor * (H/2)/fy.
- * batch: reserved, 0.
+ * batch: Gaussians the compositing kernels stage in shared memory at a time:
+ *   64, 128 or 256 (0 = 256).  Any value gives the same results.
+ * persist_ctas: 0 (default) launches the compositing kernels with one CTA
+ *   per (view, tile); k in 1..32 launches k CTAs per SM that take (view,
+ *   tile) items, longest list first, from a device counter until none is
+ *   left (a persistent launch; the counter is back at zero after it, so a
+ *   captured graph can replay it).  Same results either way.
  * ppt_fwd, ppt_bwd: pixels per thread in the forward / backward blend
  *   kernels, 1, 2 or 4 (0 = default: 1 forward, 4 backward); a 16x16 tile is
  *   one block of 256 / ppt threads.
@@ -179,6 +185,7 @@ typedef struct {
     int32_t sort_mode;
     const uint8_t* pixel_mask;
     int32_t grad_accumulate;
+    int32_t persist_ctas;
 } vg_render_params;
 
 /* Gradient outputs of vg_render_bwd (DEVICE pointers, caller-allocated; each

@@ -82,6 +82,18 @@ class LocalBA:
         self.graph = None
         self.graph_iters = 0
 
+    def autotune(self, reps: int = 3, cache: Optional[str] = None):
+        """Pick the compositing kernels' launch shape (pixels per thread,
+        staging batch, persistent-CTA count; autotune.autotune_launch) on
+        this window's own views and gradients, and use it from now on (a
+        graph captured before must be captured again)."""
+        from .autotune import autotune_launch, launch_params
+        tuned = autotune_launch(self.sh, self.cams, self.ctx, self.dC, self.dD, None, self.grads, reps=reps,
+                                cache=cache, pose_dev=self.pose, pixel_mask=self.rays)
+        self.params = V.default_params(pose_dev=self.pose, pixel_mask=self.rays, **launch_params(tuned))
+        self.graph, self.graph_iters = None, 0
+        return tuned
+
     def reset_optimiser(self):
         for t in (self.pm, self.pv, *self.mm, *self.mv):
             t.zero_()

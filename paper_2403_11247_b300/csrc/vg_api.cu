@@ -572,6 +572,10 @@ static vg_status build_views(const vg_camera* cams, int32_t n_views, const vg_re
         return fail(VG_ERR_INVALID_ARG, "params.ppt_fwd must be 0, 1, 2 or 4");
     if (p->ppt_bwd != 0 && p->ppt_bwd != 1 && p->ppt_bwd != 2 && p->ppt_bwd != 4)
         return fail(VG_ERR_INVALID_ARG, "params.ppt_bwd must be 0, 1, 2 or 4");
+    if (p->batch != 0 && p->batch != 64 && p->batch != 128 && p->batch != 256)
+        return fail(VG_ERR_INVALID_ARG, "params.batch must be 0, 64, 128 or 256");
+    if (p->persist_ctas < 0 || p->persist_ctas > 32)
+        return fail(VG_ERR_INVALID_ARG, "params.persist_ctas must be in 0..32");
     if (!(p->alpha_max > 0.f && p->alpha_max < 1.f) || !(p->alpha_min >= 0.f) || !(p->t_min >= 0.f) ||
         !(p->dilation >= 0.f) || !(p->sigma_cull > 0.f) || !(p->clamp_factor > 0.f))
         return fail(VG_ERR_INVALID_ARG, "render params out of range");
@@ -616,6 +620,7 @@ static vg_status build_views(const vg_camera* cams, int32_t n_views, const vg_re
     cs->seen = p->seen;
     cs->depth_hist = 1;
     cs->pix_mask = p->pixel_mask;
+    cs->blend_batch = p->batch ? p->batch : 256;
     if (p->sort_mode < VG_SORT_AUTO || p->sort_mode > VG_SORT_TILE)
         return fail(VG_ERR_INVALID_ARG, "sort_mode must be VG_SORT_AUTO, VG_SORT_GLOBAL or VG_SORT_TILE");
     cs->n_gauss = 0;  // set by the caller that knows the scene
@@ -789,7 +794,8 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
                                                ctx->tile_order.as<uint32_t>(), 1, cs.lf_blk, lf_grid,
                                                scr + SCR_LOSS_VALID, st));
     VG_STAGE(VG_STAGE_BLEND_FWD,
-             launch_blend_fwd(V, cs, params->ppt_fwd, ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
+             launch_blend_fwd(V, cs, params->ppt_fwd, params->persist_ctas, state + ST_WORK_FWD,
+                              ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
                               ctx->pval[fin].as<uint32_t>(), tile_sort ? ctx->dkey[1].as<uint32_t>() : nullptr, err,
                               ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(), C, D, S,
                               ctx->Tfin.as<float>(), ctx->ncontrib.as<uint32_t>(),
@@ -893,7 +899,8 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
         VG_STAGE(VG_STAGE_MEMSET, launch_zero_bwd(ctx->vis.as<uint32_t>(), ctx->scratch.as<uint32_t>() + SCR_NVIS,
                                                   rows_zero ? 0u : (uint32_t)slots, ctx->g2d.as<float>(), Z, st));
     VG_STAGE(VG_STAGE_BLEND_BWD,
-             launch_blend_bwd(V, cs, params->ppt_bwd, ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
+             launch_blend_bwd(V, cs, params->ppt_bwd, params->persist_ctas, ctx->state.as<uint32_t>() + ST_WORK_BWD,
+                              ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
                               ctx->pval[ctx->final_pair].as<uint32_t>(),
                               ctx->xy.as<float4>(), ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(),
                               ctx->Tfin.as<float>(), ctx->ncontrib.as<uint32_t>(), dC, dD, dS, ctx->g2d.as<float>(),

@@ -164,9 +164,38 @@ __device__ __forceinline__ void tile_sort(uint32_t* __restrict__ pvals, uint2 rg
 
 // COUNT: keep the work counters (evaluated and blended pairs); off in the
 // timed form, whose per-pixel loop then skips their bookkeeping
-template <int PPT, bool HITS, bool TSORT, bool COUNT>
+// Persistent form (PERSIST): the CTAs of the grid pull (view, tile) items
+// from the longest-first order through the counter work[0], one item ahead
+// (thread 0 holds the next index in `ahead`, so the atomic's round trip
+// overlaps the current item); the last CTA to finish puts work[0] and
+// work[1] back to zero.  Otherwise CTA b takes item b.
+template <bool PERSIST>
+__device__ __forceinline__ bool next_item(uint32_t* work, uint32_t& it, uint32_t& ahead, uint32_t total,
+                                          uint32_t* s_item) {
+    if (!PERSIST) return it < total;
+    __syncthreads();  // the previous item's shared memory is free
+    if (threadIdx.x == 0) {
+        *s_item = ahead;
+        if (ahead < total) ahead = atomicAdd(work, 1u);
+    }
+    __syncthreads();
+    it = *s_item;
+    return it < total;
+}
+template <bool PERSIST>
+__device__ __forceinline__ void finish_items(uint32_t* work) {
+    if (!PERSIST || threadIdx.x != 0) return;
+    __threadfence();
+    if (atomicAdd(work + 1, 1u) == gridDim.x - 1) {  // every CTA has taken its last item
+        work[0] = 0u;
+        work[1] = 0u;
+    }
+}
+
+template <int PPT, bool HITS, bool TSORT, bool COUNT, bool PERSIST>
 __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
-    const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    const __grid_constant__ Views V, Consts cs, uint32_t* work, const uint2* __restrict__ ranges,
+    const uint32_t* __restrict__ order,
     uint32_t* __restrict__ pvals, const uint32_t* __restrict__ dkey, uint32_t* __restrict__ err,
     const float4* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
     float* __restrict__ C, float* __restrict__ D, float* __restrict__ S, float* __restrict__ Tfin,
@@ -181,8 +210,13 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     float4* s_co = s_xy + BLEND_BATCH;
     float4* s_cd = s_co + BLEND_BATCH;
     uint32_t* s_gid = reinterpret_cast<uint32_t*>(s_cd + BLEND_BATCH);  // Gaussian ids, for the optional hit counts
+    __shared__ uint32_t s_item;
+    const uint32_t BB = (uint32_t)cs.blend_batch;
 
-    const int gt = (int)order[blockIdx.x];  // longest tile lists first
+    uint32_t ahead = (PERSIST && threadIdx.x == 0) ? atomicAdd(work, 1u) : 0u;
+    for (uint32_t item = PERSIST ? 0u : blockIdx.x;
+         next_item<PERSIST>(work, item, ahead, (uint32_t)V.total_tiles, &s_item);) {
+    const int gt = (int)order[item];  // longest tile lists first
     const int v = view_of_tile(V, gt);
     const ViewInfo& vi = V.v[v];
     const int t = gt - vi.tile_base;
@@ -240,12 +274,13 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
                 atomicOr(err, ERR_TILE_LIST);  // composited unsorted; the outputs are flagged invalid
         }
     }
-    for (uint32_t b = rg.x; b < rg.y; b += BLEND_BATCH) {
+    for (uint32_t b = rg.x; b < rg.y; b += BB) {
         int alldone = 1;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) alldone &= (int)done[k];
         if (__syncthreads_count(alldone) == NT) break;
-        for (int i = threadIdx.x; i < BLEND_BATCH; i += NT) {
+#pragma unroll 2
+        for (int i = threadIdx.x; i < (int)BB; i += NT) {
             const uint32_t j = b + i;
             if (j < rg.y) {
                 const uint32_t s = pvals[j];
@@ -256,7 +291,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
             }
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)BLEND_BATCH, rg.y - b);
+        const int cnt = (int)min(BB, rg.y - b);
         for (int c0 = 0; c0 < cnt; c0 += 32) {
             int wdone = 1;
 #pragma unroll
@@ -375,6 +410,9 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
             atomicAdd(cs.lf_loss, t);
         }
     }
+    if (!PERSIST) break;
+    }  // items
+    finish_items<PERSIST>(work);
 }
 
 // Fully transposing butterfly: ten per-lane values summed over the warp in
@@ -414,9 +452,10 @@ __device__ __forceinline__ int reduce10_index(int lane) {
     return k < 0 ? -1 : k + ((lane & 16) ? 5 : 0);
 }
 
-template <int PPT>
+template <int PPT, bool PERSIST>
 __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
-    const __grid_constant__ Views V, Consts cs, const uint2* __restrict__ ranges, const uint32_t* __restrict__ order,
+    const __grid_constant__ Views V, Consts cs, uint32_t* work, const uint2* __restrict__ ranges,
+    const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pvals,
     const float4* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
     const float* __restrict__ Tfin, const uint32_t* __restrict__ ncontrib, const float* __restrict__ dC,
@@ -429,8 +468,13 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     __shared__ float4 s_cd[BLEND_BATCH];
     __shared__ uint32_t s_slot[BLEND_BATCH];
     __shared__ uint32_t s_max;
+    __shared__ uint32_t s_item;
+    const uint32_t BB = (uint32_t)cs.blend_batch;
 
-    const int gt = (int)order[blockIdx.x];  // longest tile lists first
+    uint32_t ahead = (PERSIST && threadIdx.x == 0) ? atomicAdd(work, 1u) : 0u;
+    for (uint32_t item = PERSIST ? 0u : blockIdx.x;
+         next_item<PERSIST>(work, item, ahead, (uint32_t)V.total_tiles, &s_item);) {
+    const int gt = (int)order[item];  // longest tile lists first
     const int v = view_of_tile(V, gt);
     const ViewInfo& vi = V.v[v];
     const int t = gt - vi.tile_base;
@@ -490,7 +534,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     const float red_scale = (red_idx == 2 || red_idx == 4) ? -0.5f : (red_idx >= 0 && red_idx <= 3) ? -1.f : 1.f;
 
     for (uint32_t bend = end; bend > rg.x;) {
-        const uint32_t bstart = (bend - rg.x > (uint32_t)BLEND_BATCH) ? bend - BLEND_BATCH : rg.x;
+        const uint32_t bstart = (bend - rg.x > BB) ? bend - BB : rg.x;
         __syncthreads();
         for (int i = threadIdx.x; i < (int)(bend - bstart); i += NT) {
             const uint32_t s = pvals[bstart + i];
@@ -578,20 +622,49 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
         }
         bend = bstart;
     }
+    if (!PERSIST) break;
+    }  // items
+    finish_items<PERSIST>(work);
 }
 
-cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* order,
+static int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 148;
+    }
+    return sms;
+}
+
+static unsigned blend_grid(const Views& V, int persist, uint32_t*& work) {
+    if (persist <= 0) {
+        work = nullptr;
+        return (unsigned)V.total_tiles;
+    }
+    const int64_t g = (int64_t)persist * sm_count();
+    return (unsigned)(g < V.total_tiles ? g : V.total_tiles);
+}
+
+cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, int persist, uint32_t* work,
+                             const uint2* ranges, const uint32_t* order,
                              uint32_t* pvals, const uint32_t* dkey, uint32_t* err,
                              const float4* xy, const float4* conic_o, const float4* rgbd, float* C, float* D, float* S,
                              float* Tfin, uint32_t* ncontrib, unsigned long long* evals, unsigned long long* blended,
                              uint32_t* neval, int count_evals, cudaStream_t st) {
     if (V.total_tiles <= 0) return cudaSuccess;
     count_launches(1);
-#define VG_FWD4(P, H, TS, CN)                                                                                   \
-    blend_fwd_kernel<P, H, TS, CN><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, order, pvals, dkey, err, \
+    const unsigned grid = blend_grid(V, persist, work);
+#define VG_FWD5(P, H, TS, CN, PE)                                                                               \
+    blend_fwd_kernel<P, H, TS, CN, PE><<<grid, TILE_PIX / P, 0, st>>>(V, cs, work, ranges, order, pvals, dkey, err, \
                                                                            xy, conic_o, rgbd, C, D, S, Tfin,     \
                                                                            ncontrib, evals, blended, neval,      \
                                                                            count_evals)
+#define VG_FWD4(P, H, TS, CN)                                                                                   \
+    do {                                                                                                        \
+        if (work) VG_FWD5(P, H, TS, CN, true); else VG_FWD5(P, H, TS, CN, false);                                \
+    } while (0)
 #define VG_FWD3(P, H, TS)                                                                                       \
     do {                                                                                                        \
         if (count_evals) VG_FWD4(P, H, TS, true); else VG_FWD4(P, H, TS, false);                                \
@@ -610,23 +683,31 @@ cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const ui
 #undef VG_FWD
 #undef VG_FWD3
 #undef VG_FWD4
+#undef VG_FWD5
     return cudaGetLastError();
 }
 
-cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* order,
+cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, int persist, uint32_t* work,
+                             const uint2* ranges, const uint32_t* order,
                              const uint32_t* pvals,
                              const float4* xy, const float4* conic_o, const float4* rgbd, const float* Tfin,
                              const uint32_t* ncontrib, const float* dC, const float* dD, const float* dS, float* g2d,
                              unsigned long long* bwd_pairs, int count, cudaStream_t st) {
     if (V.total_tiles <= 0) return cudaSuccess;
     count_launches(1);
+    const unsigned grid = blend_grid(V, persist, work);
+#define VG_BWD2(P, PE)                                                                                               \
+    blend_bwd_kernel<P, PE><<<grid, TILE_PIX / P, 0, st>>>(V, cs, work, ranges, order, pvals, xy, conic_o, rgbd, Tfin, \
+                                                           ncontrib, dC, dD, dS, g2d, bwd_pairs, count)
 #define VG_BWD(P)                                                                                                    \
-    blend_bwd_kernel<P><<<V.total_tiles, TILE_PIX / P, 0, st>>>(V, cs, ranges, order, pvals, xy, conic_o, rgbd, Tfin, ncontrib, \
-                                                                dC, dD, dS, g2d, bwd_pairs, count)
+    do {                                                                                                             \
+        if (work) VG_BWD2(P, true); else VG_BWD2(P, false);                                                          \
+    } while (0)
     if (ppt == 1) VG_BWD(1);
     else if (ppt == 2) VG_BWD(2);
     else VG_BWD(4);
 #undef VG_BWD
+#undef VG_BWD2
     return cudaGetLastError();
 }
 

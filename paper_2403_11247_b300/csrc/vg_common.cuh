@@ -50,6 +50,7 @@ struct Consts {
     int64_t n_gauss;      // N, for the two arrays above
     int32_t depth_hist;   // the preprocess accumulates depth-key digit histograms (global depth sort)
     const uint8_t* pix_mask;  // [pixels] 0 = not composited (sampled rays); NULL = every pixel
+    int32_t blend_batch;      // Gaussians staged in shared memory per batch by the compositing kernels
     // L1 loss gradient written by the forward compositing (vg_render_fwd_l1);
     // lf_on = 0: off
     int32_t lf_on;

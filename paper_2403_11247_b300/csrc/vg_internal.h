@@ -26,7 +26,13 @@ constexpr int ST_ERR = 1;
 constexpr int ST_EVALS = 2;    // u64 at words 2..3: evaluated (pixel, Gaussian) pairs, forward
 constexpr int ST_BLENDED = 4;  // u64 at words 4..5: blended pairs, forward
 constexpr int ST_BWD = 6;      // u64 at words 6..7: pairs walked by the backward
-constexpr int ST_WORDS = 8;
+// persistent compositing launches: next (view, tile) item, CTAs finished
+// (the last CTA out puts both back to zero)
+constexpr int ST_WORK_FWD = 8;
+constexpr int ST_DONE_FWD = 9;
+constexpr int ST_WORK_BWD = 10;
+constexpr int ST_DONE_BWD = 11;
+constexpr int ST_WORDS = 12;
 
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 8;
@@ -146,12 +152,16 @@ vg_status vg_mask_kernels_prune(float* m, float thr, const uint32_t* hits, const
 
 // blend.cu
 // dkey non-NULL: sort each tile's list by (dkey[slot], slot) first (VG_SORT_TILE)
-cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* order,
+// persist > 0: persist CTAs per SM pull tiles from `work` ([0] next item,
+// [1] CTAs done, both zero before and after the launch); 0: a CTA per tile
+cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, int persist, uint32_t* work,
+                             const uint2* ranges, const uint32_t* order,
                              uint32_t* pvals, const uint32_t* dkey, uint32_t* err,
                              const float4* xy, const float4* conic_o, const float4* rgbd, float* C, float* D,
                              float* S, float* Tfin, uint32_t* ncontrib, unsigned long long* evals,
                              unsigned long long* blended, uint32_t* neval, int count_evals, cudaStream_t st);
-cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, const uint2* ranges, const uint32_t* order,
+cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, int persist, uint32_t* work,
+                             const uint2* ranges, const uint32_t* order,
                              const uint32_t* pvals,
                              const float4* xy, const float4* conic_o, const float4* rgbd, const float* Tfin,
                              const uint32_t* ncontrib, const float* dC, const float* dD, const float* dS,

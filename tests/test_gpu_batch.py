@@ -131,3 +131,77 @@ def test_local_ba_with_the_ssim_term(torch):
     after = pose_errors(ba.pose.cpu().numpy().astype(np.float64), T_true)
     assert float(ba.ssim_loss.item()) >= 0.0
     assert after[:, 0].mean() < 0.7 * before[:, 0].mean(), (before, after)
+
+
+@pytest.mark.parametrize("ppt", [1, 2, 4])
+def test_persistent_launch_and_batch_sizes_equal_one_cta_per_tile(torch, ppt):
+    """The persistent compositing launch (CTAs pulling (view, tile) items,
+    longest list first) and every staging batch size give the images of one
+    CTA per tile bit for bit, and the same gradients; two persistent launches
+    in a row agree (the work counters come back to zero)."""
+    sc = synth.tiny_scene()
+    cams = kf(n=4, w=200, h=136, f=160.0)
+    sh = V.vg_scene_upload(sc)
+    P = sum(c.width * c.height for c in cams)
+    rng = np.random.default_rng(3)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ups = [t(rng.uniform(-1, 1, s).astype(np.float32) / P) for s in (3 * P, P, P)]
+
+    def run(**kw):
+        ctx = V.vg_ctx_create(0)
+        prm = V.default_params(ppt_fwd=ppt, ppt_bwd=ppt, count_evals=1, **kw)
+        out = [x.cpu().numpy() for x in V.render_with_retry(sh, cams, prm, ctx)]
+        g = {k: x.cpu().numpy() for k, x in V.vg_render_bwd(sh, cams, prm, ctx, *ups).items()}
+        dxi = V.vg_pose_grad(ctx, len(cams))[0].cpu().numpy()
+        st = V.vg_ctx_stats(ctx)
+        assert V.vg_check(ctx) == V.VG_OK
+        return out, g, dxi, (st["evaluated"], st["blended"], st["bwd_pairs"])
+
+    ref = run()
+    for kw in (dict(persist_ctas=1), dict(persist_ctas=4), dict(persist_ctas=4, batch=64), dict(batch=128),
+               dict(persist_ctas=32)):
+        got = run(**kw)
+        for a, b in zip(ref[0], got[0]):
+            assert np.array_equal(a, b), kw
+        assert got[3] == ref[3], kw                  # the same pairs examined, blended, walked
+        for name in ref[1]:
+            grad_tolerance_check(got[1][name], ref[1][name], f"{kw}: {name}", rtol=1e-5, atol_frac=1e-6)
+        for v in range(len(cams)):
+            grad_tolerance_check(got[2][v], ref[2][v], f"{kw}: pose {v}", rtol=1e-4, atol_frac=1e-5)
+    ctx = V.vg_ctx_create(0)
+    prm = V.default_params(ppt_fwd=ppt, persist_ctas=2)
+    a = [x.cpu().numpy() for x in V.render_with_retry(sh, cams, prm, ctx)]
+    b = [x.cpu().numpy() for x in V.vg_render_fwd(sh, cams, prm, ctx)]
+    assert V.vg_check(ctx) == V.VG_OK
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_persistent_window_in_a_captured_graph_and_the_autotuner(torch, tmp_path):
+    """The local BA window with its autotuned launch shape (a persistent
+    count among them when it wins) replays a captured graph like eager
+    iterations; the tuner's choices come from its grids and are cached by
+    workload shape."""
+    from paper_2403_11247_b300 import autotune as A
+    ba, _ = _window(torch)
+    cache = str(tmp_path / "tune.json")
+    tuned = ba.autotune(reps=2, cache=cache)
+    assert tuned["ppt_fwd"] in A.PPT_CHOICES and tuned["ppt_bwd"] in A.PPT_CHOICES
+    assert tuned["batch"] in A.BATCH_CHOICES and tuned["persist_ctas"] in A.PERSIST_CHOICES
+    assert A.autotune_launch(ba.sh, ba.cams, ba.ctx, cache=cache) == tuned    # from the cache
+    ba.params = V.default_params(pose_dev=ba.pose, **dict(A.launch_params(tuned), persist_ctas=4))
+    pose0 = ba.pose.clone()
+    ba.capture(8)
+    ba.pose.copy_(pose0)
+    ba.reset_optimiser()
+    torch.cuda.synchronize()
+    ba.replay()
+    ba.replay()   # twice: the persistent work counters must be back at zero
+    torch.cuda.synchronize()
+    assert ba.check() == V.VG_OK
+    via_graph = ba.pose.clone()
+    ba.pose.copy_(pose0)
+    ba.reset_optimiser()
+    ba.iterate(16)
+    torch.cuda.synchronize()
+    assert torch.allclose(ba.pose, via_graph, atol=2e-5), (ba.pose - via_graph).abs().max()
