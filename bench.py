@@ -42,6 +42,8 @@ FWD_FLOP_EVAL = 14        # offset, quadratic form, exp argument, opacity produc
 FWD_FLOP_BLEND = 12       # transmittance update, 4 FMA accumulations, silhouette
 BWD_FLOP_WALK = 14        # per walked pair: offset, quadratic form, exp argument, opacity product
 BWD_FLOP_BLEND = 49       # per blended pair: T recovery, dL/dalpha, colour/depth/opacity/conic/mean partials
+CHAIN_FLOP_SLOT = 600     # per visible slot: projection, covariance and rotation reverse mode (FMA = 2)
+ADAM_BYTES_PARAM = 28     # read parameter, gradient, two moments; write parameter, two moments
 # DRAM bytes (read + write) per launch of the compositing kernels from one ncu
 # capture of this workload (profiles/step_kernels__mapping_1200x680.md), valid
 # while the kernels' sources hash to the value they had when captured
@@ -90,6 +92,56 @@ def job_rate(per_rank_ms: float, units_per_rank: int, world: int, dist=None, dev
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
     return world * units_per_rank / (t / 1000.0), t
+
+
+def stage_rooflines(prof, K, stats, wl, hbm_gbs, alu_tflops):
+    """Roofline of every profiled stage of one step: algorithmic work (DRAM
+    bytes or FP32 FLOPs, from the workload's sizes and the device work
+    counters) over the stage's CUDA-event time.  wl: N, views, k,
+    idx_bytes (code bytes per Gaussian), tiles, pixels, sort ('tile' or
+    'global'), tile_passes, fused_loss, g2d (the compaction zeroes the
+    backward's gradient rows)."""
+    N, slots, vis, P = wl["N"], wl["N"] * wl["views"], stats["visible"], stats["pairs"]
+    ev, bl, walked = stats["evaluated"] / K, stats["blended"] / K, stats["bwd_pairs"] / K
+    glob = wl["sort"] == "global"
+    hbm = {
+        "preprocess": (N * (12 + 24 / wl["k"] + 4 + wl["idx_bytes"]) + slots * 8 + vis * 56,
+                       "per Gaussian offset 12 B + anchor and l 24/k B + mask 4 B + code bytes; per slot tile count "
+                       "and depth key 8 B; per visible slot 56 B of records"),
+        "depth_sort": (slots * 4 + vis * 20 + (vis * 48 if wl["g2d"] else 0) + (wl["pixels"] * 4 if wl["fused_loss"]
+                                                                               else 0) + (4 * 16 * vis if glob else 0),
+                       "compaction: depth keys of every slot, 20 B per visible slot (+48 B gradient-row zeroing, "
+                       "+4 B per pixel of target depth for the fused loss; global sort: 4 passes x 16 B per slot)"),
+        "duplicate": (P * 8 + vis * 16 + (vis * 8 if glob else 0), "8 B per pair written, 16 B per visible slot read"),
+        "tile_sort": ((wl["tile_passes"] if glob else 1) * 16 * P + (12 * P if wl.get("long_pass") else 0),
+                      "16 B per pair per pass (scatter: one pass; long-list pass: 12 B more per pair)"),
+        "ranges": (wl["tiles"] * 16, "per tile count read, range and order written"),
+        "loss": (wl["pixels"] * 52, "36 B read + 16 B written per pixel"),
+        "pose": (4 * 6 * wl["views"] * 148, "per-block pose partials"),
+    }
+    alu = {
+        "blend_fwd": (FWD_FLOP_EVAL * ev + FWD_FLOP_BLEND * bl,
+                      f"{FWD_FLOP_EVAL} FLOP per evaluated + {FWD_FLOP_BLEND} per blended pair"),
+        "blend_bwd": (BWD_FLOP_WALK * walked + BWD_FLOP_BLEND * bl,
+                      f"{BWD_FLOP_WALK} FLOP per walked + {BWD_FLOP_BLEND} per blended pair"),
+        "chain": (CHAIN_FLOP_SLOT * vis, f"{CHAIN_FLOP_SLOT} FLOP per visible slot"),
+    }
+    rows = []
+    for stage, (ms, n) in prof.items():
+        if not n or stage in ("memset", "codebook"):
+            continue
+        per = ms / K / 1000.0
+        if stage in alu:
+            w, what = alu[stage]
+            ach = w / per / 1e12
+            rows.append({"stage": stage, "bound": "alu", "work_per_step": w, "work": what, "ms": per * 1e3,
+                         "achieved": ach, "unit": "TFLOP/s", "peak": alu_tflops, "frac": ach / alu_tflops})
+        elif stage in hbm:
+            w, what = hbm[stage]
+            ach = w / per / 1e9
+            rows.append({"stage": stage, "bound": "hbm", "work_per_step": w, "work": what, "ms": per * 1e3,
+                         "achieved": ach, "unit": "GB/s", "peak": hbm_gbs, "frac": ach / hbm_gbs})
+    return rows
 
 
 def measured_peaks():
@@ -210,11 +262,12 @@ def build_workload(torch, V, synth):
                 plist=plist, glist=glist, ms=ms, vs=vs, step_dev=step_dev, P=P)
 
 
-def make_step(V, w):
+def make_step(V, w, adam_events=None):
     """One mapping step: forward with the L1 loss gradient written by the
     compositing kernel, backward accumulating into the map gradients (kept
     zero by the Adam step, which clears each one once read), pose gradient,
-    Adam on the map."""
+    Adam on the map.  adam_events: a pair of timing events (external, so
+    that a captured graph keeps them as nodes) recorded around the Adam step."""
     b, sh, ctx, params, cams = w["bufs"], w["sh"], w["ctx"], w["params"], [w["cam"]]
     p_bwd = type(params).from_buffer_copy(params)
     p_bwd.grad_accumulate = 1
@@ -224,7 +277,11 @@ def make_step(V, w):
                            b["dD"], None, b["loss"])
         V.vg_render_bwd(sh, cams, p_bwd, ctx, b["dC"], b["dD"], None, w["grads"])
         V.vg_pose_grad(ctx, 1, dxi=b["dxi"])
+        if adam_events:
+            adam_events[0].record()
         V.vg_adam_step(w["plist"], w["glist"], w["ms"], w["vs"], 1e-4, step_dev=w["step_dev"], zero_grad=True)
+        if adam_events:
+            adam_events[1].record()
     return step
 
 
@@ -523,7 +580,10 @@ def large_leg(torch, V, synth, steps=20):
              for i, c in enumerate(cams)]
     sh = V.vg_scene_upload(sc)
     ctx = V.vg_ctx_create(0)
-    params = V.default_params()
+    # ~1,600 Gaussians per tile on average (5,500 at most): past what the
+    # compositing kernel sorts itself, so the default form sorts globally
+    # (the per-tile form with its long-list pass is timed below beside it)
+    params = V.default_params(sort_mode=V.VG_SORT_GLOBAL)
     Ct, Dt, _ = V.render_with_retry(sh, tcams, params, ctx)
     Ct, Dt = Ct.clone(), Dt.clone()
     V.render_with_retry(sh, cams, params, ctx)
@@ -561,10 +621,74 @@ def large_leg(torch, V, synth, steps=20):
         raise RuntimeError("large scene: device status not OK")
     ms = statistics.median(times)
     tiles = 4 * ((cams[0].width + 15) // 16) * ((cams[0].height + 15) // 16)
+    # stage times and work counters: a second capture carrying the stage
+    # events, with the work counters on
+    params_c = V.default_params(sort_mode=V.VG_SORT_GLOBAL, count_evals=1)
+
+    def step_c():
+        V.vg_render_fwd(sh, cams, params_c, ctx, C_, D, S)
+        V.vg_loss_l1(4, P, C_, D, S, Ct, Dt, 0.5, -1.0, ctx, dC=dC, dD=dD, loss=loss)
+        V.vg_render_bwd(sh, cams, params_c, ctx, dC, dD, None, grads)
+        V.vg_pose_grad(ctx, 4, dxi=dxi)
+    step_c()
+    torch.cuda.synchronize()
+    V.vg_ctx_profile(ctx, True)
+    gp = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gp, capture_error_mode="thread_local"):
+        step_c()
+    V.vg_ctx_reset_counters(ctx)
+    prof = {}
+    Kp = 5
+    for _ in range(Kp):
+        gp.replay()
+        torch.cuda.synchronize()
+        for k_, (ms_, n_) in V.vg_ctx_profile_read(ctx).items():
+            a_, b_ = prof.get(k_, (0.0, 0))
+            prof[k_] = (a_ + ms_, b_ + n_)
+    V.vg_ctx_profile(ctx, False)
+    stats = V.vg_ctx_stats(ctx)
+    if V.vg_check(ctx) != V.VG_OK:
+        raise RuntimeError("large scene: device status not OK in the profiled steps")
+    peaks, _ = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    alu_peak = n_sm * FP32_PEAK_PER_SM_CLK * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    bits = max(1, (tiles - 1).bit_length())
+    wl = dict(N=int(sc.n), views=4, k=int(sc.k), idx_bytes=sum(g.idx.shape[0] for g in sc.groups.values() if g.coded),
+              tiles=tiles, pixels=4 * P, sort="global", tile_passes=(bits + 7) // 8, fused_loss=False, g2d=True)
+    rows = stage_rooflines(prof, Kp, stats, wl, peaks["hbm_gbs"], alu_peak)
+    # the per-tile form (lists over 1,024 sorted by the long-list pass), same
+    # step in a graph of its own
+    ctx_t = V.vg_ctx_create(0)
+    params_t = V.default_params(sort_mode=V.VG_SORT_TILE)
+    V.render_with_retry(sh, cams, params_t, ctx_t)
+    V.vg_ctx_reserve(ctx_t, int(st["pairs"] * 1.2) + 4096)
+
+    def step_t():
+        V.vg_render_fwd(sh, cams, params_t, ctx_t, C_, D, S)
+        V.vg_loss_l1(4, P, C_, D, S, Ct, Dt, 0.5, -1.0, ctx_t, dC=dC, dD=dD, loss=loss)
+        V.vg_render_bwd(sh, cams, params_t, ctx_t, dC, dD, None, grads)
+        V.vg_pose_grad(ctx_t, 4, dxi=dxi)
+    step_t()
+    torch.cuda.synchronize()
+    gt_ = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gt_, capture_error_mode="thread_local"):
+        step_t()
+    t_times = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        gt_.replay()
+        b.record()
+        torch.cuda.synchronize()
+        t_times.append(a.elapsed_time(b))
+    if V.vg_check(ctx_t) != V.VG_OK:
+        raise RuntimeError("large scene, per-tile form: device status not OK")
     res = {"gaussians": int(sc.offsets.shape[0] * sc.offsets.shape[1]), "views": 4, "size": "1920x1080",
            "ms_per_step": ms, "iters_per_s": 1000.0 / ms, "mpix_per_s": 4 * P / ms / 1e3,
            "pairs": st["pairs"], "mean_list_per_tile": st["pairs"] / tiles, "visible_slots": st["visible"],
-           "steps": steps}
+           "steps": steps, "stages_ms_per_step": {k: v[0] / Kp for k, v in prof.items() if v[1]},
+           "per_kernel_roofline": rows, "sort": "global (lists over 1,024 entries)",
+           "per_tile_form_ms_per_step": statistics.median(t_times)}
     log(f"large scene: {ms:.2f} ms per 4-view fwd+bwd, {res['mean_list_per_tile']:.0f} Gaussians per tile")
     return res
 
@@ -820,7 +944,9 @@ def run_ours(args):
     w["params"] = V.default_params(**launch_params(tune))
     step = make_step(V, w)
     w_prof = dict(w, params=V.default_params(count_evals=1, **launch_params(tune)))
-    step_prof = make_step(V, w_prof)
+    import torch as _t
+    adam_ev = (_t.cuda.Event(enable_timing=True, external=True), _t.cuda.Event(enable_timing=True, external=True))
+    step_prof = make_step(V, w_prof, adam_ev)
     graph = graph_prof = None
     launches0 = V.vg_launch_count()
     if not args.no_graph:
@@ -877,11 +1003,13 @@ def run_ours(args):
     V.vg_ctx_reset_counters(w["ctx"])
     V.vg_ctx_profile(w["ctx"], True)   # clears non-graph records only
     stage_ms, stage_n = {}, {}
+    adam_times = []
     for i in range(K_prof):
         flush.fill_(float(i))
         run_prof()
+        stream.synchronize()
+        adam_times.append(adam_ev[0].elapsed_time(adam_ev[1]))
         if graph_prof is not None:
-            stream.synchronize()
             for k, (ms_, n_) in V.vg_ctx_profile_read(w["ctx"]).items():
                 stage_ms[k] = stage_ms.get(k, 0.0) + ms_
                 stage_n[k] = stage_n.get(k, 0) + n_
@@ -932,6 +1060,19 @@ def run_ours(args):
         # FLOPs undercount what a compositing kernel issues (shuffles, loads,
         # tests): the issue rate shows how close it runs to the SMs' limit
         roof["issue_frac"] = (NCU_INSTRUCTIONS[stage] / per_launch_s) / (n_sm * 4 * sm_mhz * 1e6)
+
+    # every stage of the step against its roofline, and the map's Adam step
+    sc_ = w["scene"]
+    wl_map = dict(N=sc_.n, views=1, k=sc_.k, idx_bytes=sum(g.idx.shape[0] for g in sc_.groups.values() if g.coded),
+                  tiles=((W_IMG + 15) // 16) * ((H_IMG + 15) // 16), pixels=W_IMG * H_IMG, sort="tile", tile_passes=0,
+                  fused_loss=True, g2d=True)
+    kernel_rows = stage_rooflines(prof, K, stats, wl_map, peaks["hbm_gbs"], alu_peak)
+    adam_ms, n_par = statistics.median(adam_times), sum(p.numel() for p in w["plist"])
+    kernel_rows.append({"stage": "adam", "bound": "hbm", "work_per_step": ADAM_BYTES_PARAM * n_par,
+                        "work": f"{ADAM_BYTES_PARAM} B per parameter ({n_par} parameters; zero_grad writes 4 B more)",
+                        "ms": adam_ms, "achieved": ADAM_BYTES_PARAM * n_par / (adam_ms / 1e3) / 1e9, "unit": "GB/s",
+                        "peak": peaks["hbm_gbs"], "frac": ADAM_BYTES_PARAM * n_par / (adam_ms / 1e3) / 1e9 /
+                        peaks["hbm_gbs"], "timing": "event nodes around the Adam step in the profiled capture"})
 
     # measured throughput of the units the derived peaks assume (probes)
     probes = V.probe_peaks()
@@ -1058,6 +1199,8 @@ def run_ours(args):
                 "gpu_launches": launches, "launches_per_step": launches / max(1, args.steps),
                 "cuda_graph": graph is not None, "autotune": tune, "clocks": clocks,
                 "stages_ms_per_step": {k: v[0] / K for k, v in prof.items() if v[1]},
+                "per_kernel_roofline": {"mapping_1200x680": kernel_rows,
+                                        "large_4x1920x1080": (large or {}).get("per_kernel_roofline")},
                 "stages_from": f"{K} replays of a second capture of the step that carries the stage events",
                 "p50_step_ms": statistics.median(step_ms), "p10_step_ms": float(np.percentile(step_ms, 10)),
                 "p90_step_ms": float(np.percentile(step_ms, 90)), "p99_step_ms": float(np.percentile(step_ms, 99)),

@@ -59,7 +59,8 @@ typedef enum {
 #define VG_SORT_AUTO 0       /* vg_render_params.sort_mode: per-tile unless it overflowed on this ctx */
 #define VG_SORT_GLOBAL 1     /* radix sort of the visible slots by depth, then pairs stably by tile */
 #define VG_SORT_TILE 2       /* pairs by tile only; each tile's list sorted by depth in the forward */
-#define VG_TILE_SORT_CAP 1024 /* longest tile list the per-tile sort takes */
+#define VG_TILE_SORT_CAP 1024 /* longest tile list the compositing kernel sorts itself */
+#define VG_TILE_SORT_LONG_CAP 8192 /* longest tile list the per-tile sort takes (long-list pass) */
 
 /* Pinhole camera.  T_cw: row-major 3x4 world->camera transform [R | t];
  * camera x right, y down, z forward.  A point projects to
@@ -153,16 +154,21 @@ typedef struct {
  *   blended and sets seen[n] = 1 where Gaussian n is visible (an unempty
  *   tile rect) in some view; nothing clears them, so a sliding window
  *   accumulates over its frames.  NULL = off.
- * sort_mode: how the (tile, depth, index) order of the pairs is built; both
+ * sort_mode: how the (tile, depth, index) order of the pairs is built; all
  *   give the same order.  VG_SORT_GLOBAL: a stable radix sort of the visible
  *   slots on their FP32 depth bits, pairs emitted in that order, then a
  *   stable sort by tile.  VG_SORT_TILE: pairs emitted in slot order and
- *   sorted by tile; the forward compositing kernel sorts each tile's list by
- *   (depth bits, slot) in shared memory and writes it back for the backward.
- *   A tile list longer than VG_TILE_SORT_CAP cannot be sorted so: the
- *   forward's outputs are then invalid, the next vg_check returns
- *   VG_ERR_CAPACITY, and the ctx uses VG_SORT_GLOBAL from then on under
- *   VG_SORT_AUTO (the default).
+ *   grouped by tile; the forward compositing kernel sorts each tile's list
+ *   of up to VG_TILE_SORT_CAP entries by (depth bits, slot) in shared memory
+ *   and writes it back for the backward, and a pass before it sorts the
+ *   longer lists (up to VG_TILE_SORT_LONG_CAP entries, one CTA each).
+ *   VG_SORT_AUTO (the default): VG_SORT_TILE without the long-list pass
+ *   until a forward on this ctx meets a list over VG_TILE_SORT_CAP, and
+ *   VG_SORT_GLOBAL from then on (for lists that long the global radix
+ *   passes are faster than the long-list pass's comparison sort).  A forward
+ *   that meets a list longer than its form takes leaves its outputs invalid
+ *   and the next vg_check returns VG_ERR_CAPACITY (render again:
+ *   vg.render_with_retry does).
  * pixel_mask: optional DEVICE array [total pixels of all views, in view
  *   order, each row-major] of 0/1: only pixels with 1 are composited (the
  *   sampled rays of a bundle-adjustment step, Sec. "Tracking and

@@ -182,10 +182,13 @@ struct vg_ctx {
     int64_t pair_cap = 0;
     DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, tile_order, Tfin, ncontrib, lookback,
         scratch, state, pose_part, icp_part, loss_scratch, pair_off, chunk_start, blk_count, vis, ssim_ws, grow_ws,
-        neval, loss_blk;
+        neval, loss_blk, long_tiles;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
-    bool tile_sort_failed = false;  // a tile list overflowed the per-tile sort: VG_SORT_AUTO sorts globally
+    // VG_SORT_AUTO's form on this ctx: 0 per-tile sort, 2 global (a list
+    // passed VG_TILE_SORT_CAP; for such lists the global radix passes beat
+    // the long-list pass's comparison sort)
+    int auto_stage = 0;
     bool g2d_clean = false;
     bool fwd_zeroed = false;  // the last forward zeroed the visible slots' gradient rows and the pose sums
     // scratch words known to be zero: a forward leaves every counter it
@@ -468,8 +471,15 @@ vg_status vg_check(vg_ctx* ctx, vg_stream stream) {
         VG_CUDA(cudaMemset(ctx->state.as<uint32_t>() + ST_ERR, 0, 4));
         if (s.flags & ERR_WAIT) return fail(VG_ERR_TIMEOUT, "a bounded device wait ran out");
         if (s.flags & ERR_TABLE) return fail(VG_ERR_CAPACITY, "anchor-growing hash table full");
+        if (s.flags & ERR_TILE_LONG) {
+            ctx->auto_stage = 2;
+            if (!(s.flags & ERR_OVERFLOW))
+                return fail(VG_ERR_CAPACITY, "a tile list longer than VG_TILE_SORT_LONG_CAP (" +
+                                                 std::to_string(VG_TILE_SORT_LONG_CAP) +
+                                                 "): this ctx sorts globally from the next forward under VG_SORT_AUTO");
+        }
         if (s.flags & ERR_TILE_LIST) {
-            ctx->tile_sort_failed = true;
+            ctx->auto_stage = 2;
             if (!(s.flags & ERR_OVERFLOW))
                 return fail(VG_ERR_CAPACITY, "a tile list longer than VG_TILE_SORT_CAP (" +
                                                  std::to_string(VG_TILE_SORT_CAP) +
@@ -711,7 +721,10 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
     if (lf) cs.lf_counts = scr + SCR_LOSS_VALID;
     unsigned long long* lb = ctx->lookback.as<unsigned long long>();
     const bool tile_sort = params->sort_mode == VG_SORT_TILE ||
-                           (params->sort_mode == VG_SORT_AUTO && !ctx->tile_sort_failed);
+                           (params->sort_mode == VG_SORT_AUTO && ctx->auto_stage < 2);
+    const bool long_pass = tile_sort && params->sort_mode == VG_SORT_TILE;
+    cs.long_sorted = long_pass ? 1 : 0;
+    if (long_pass) VG_TRY(ctx->long_tiles.ensure((size_t)V.total_tiles * 4, st, "long tile lists"));
     cs.depth_hist = tile_sort ? 0 : 1;
     const bool prof_graph = capturing(st);
     const bool prof_on = ctx->prof.on;
@@ -770,11 +783,18 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
     if (tile_sort) {
         VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr, V.total_tiles, ctx->ranges.as<uint2>(),
                                                ctx->tile_order.as<uint32_t>(), 0, cs.lf_blk, lf_grid,
-                                               scr + SCR_LOSS_VALID, st));
-        VG_STAGE(VG_STAGE_TILE_SORT,
-                 launch_tile_scatter(ctx->pkey[0].as<uint32_t>(), ctx->pval[0].as<uint32_t>(), scr + SCR_PAIRS, cap,
-                                     ctx->ranges.as<uint2>(), scr + SCR_TILE_COUNTS, ctx->pkey[1].as<uint32_t>(),
-                                     ctx->pval[1].as<uint32_t>(), st));
+                                               scr + SCR_LOSS_VALID,
+                                               long_pass ? ctx->long_tiles.as<uint32_t>() : nullptr, st));
+        VG_STAGE(VG_STAGE_TILE_SORT, ([&]() -> cudaError_t {
+                     cudaError_t e = launch_tile_scatter(ctx->pkey[0].as<uint32_t>(), ctx->pval[0].as<uint32_t>(),
+                                                         scr + SCR_PAIRS, cap, ctx->ranges.as<uint2>(),
+                                                         scr + SCR_TILE_COUNTS, ctx->pkey[1].as<uint32_t>(),
+                                                         ctx->pval[1].as<uint32_t>(), st);
+                     if (e != cudaSuccess || !long_pass) return e;
+                     return launch_tile_sort_long(ctx->ranges.as<uint2>(), ctx->long_tiles.as<uint32_t>(),
+                                                  scr + SCR_N_LONG, ctx->pval[1].as<uint32_t>(),
+                                                  ctx->dkey[1].as<uint32_t>(), err, st);
+                 })());
     }
     VG_STAGE(VG_STAGE_TILE_SORT, ([&]() -> cudaError_t {
                  for (int p = 0; p < (tile_sort ? 0 : tp); ++p) {
@@ -792,7 +812,7 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
     if (!tile_sort)
         VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr, V.total_tiles, ctx->ranges.as<uint2>(),
                                                ctx->tile_order.as<uint32_t>(), 1, cs.lf_blk, lf_grid,
-                                               scr + SCR_LOSS_VALID, st));
+                                               scr + SCR_LOSS_VALID, nullptr, st));
     VG_STAGE(VG_STAGE_BLEND_FWD,
              launch_blend_fwd(V, cs, params->ppt_fwd, params->persist_ctas, state + ST_WORK_FWD,
                               ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),

@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
         if (__syncthreads_count(alldone) < NT) {
             if (rg.y - rg.x <= (uint32_t)VG_TILE_SORT_CAP)
                 tile_sort<NT>(pvals, rg, dkey, reinterpret_cast<uint2*>(s_raw));
-            else if (threadIdx.x == 0)
+            else if (!cs.long_sorted && threadIdx.x == 0)  // (else sorted by the long-list pass)
                 atomicOr(err, ERR_TILE_LIST);  // composited unsorted; the outputs are flagged invalid
         }
     }

@@ -15,7 +15,8 @@ constexpr int TILE_PIX = TILE * TILE;
 constexpr uint32_t ERR_WAIT = 1u;      // a bounded spin ran out
 constexpr uint32_t ERR_OVERFLOW = 2u;  // pair buffer too small
 constexpr uint32_t ERR_TABLE = 4u;     // the anchor-growing hash table was full
-constexpr uint32_t ERR_TILE_LIST = 8u; // a tile list longer than the per-tile sort takes
+constexpr uint32_t ERR_TILE_LIST = 8u; // a tile list longer than the compositing kernel sorts (no long pass)
+constexpr uint32_t ERR_TILE_LONG = 16u; // a tile list longer than the long-list pass sorts
 
 // a bounded spin gives up after this many polls (~1 s of L2 round trips)
 constexpr uint32_t SPIN_LIMIT = 1u << 21;
@@ -51,6 +52,7 @@ struct Consts {
     int32_t depth_hist;   // the preprocess accumulates depth-key digit histograms (global depth sort)
     const uint8_t* pix_mask;  // [pixels] 0 = not composited (sampled rays); NULL = every pixel
     int32_t blend_batch;      // Gaussians staged in shared memory per batch by the compositing kernels
+    int32_t long_sorted;      // lists over VG_TILE_SORT_CAP were sorted by the long-list pass
     // L1 loss gradient written by the forward compositing (vg_render_fwd_l1);
     // lf_on = 0: off
     int32_t lf_on;

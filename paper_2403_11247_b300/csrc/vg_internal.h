@@ -17,6 +17,7 @@ constexpr int SCR_CNT_DEPTH = 1794;    // 4 pass counters
 constexpr int SCR_CNT_DUP = 1798;
 constexpr int SCR_CNT_TILE = 1799;     // 3 pass counters
 constexpr int SCR_LOSS_VALID = 1802;
+constexpr int SCR_N_LONG = 1804;       // tiles with lists over VG_TILE_SORT_CAP (ranges kernel)
 constexpr int SCR_WORDS = 1808;
 constexpr int SCR_TILE_COUNTS = SCR_WORDS;  // per-tile pair counts follow, [total_tiles]
 
@@ -115,9 +116,17 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, ui
 // SCR_TILE_COUNTS (one-block scan); clear: zero the counts, the digit
 // histograms and the pass counters afterwards (global-sort form).  With
 // lf_blk (may be NULL) also the fused loss's counts: lf_counts[c] = sum of
-// lf_blk[c * lf_grid + b] over b.
+// lf_blk[c * lf_grid + b] over b.  With long_tiles (may be NULL) the tiles
+// whose lists pass VG_TILE_SORT_CAP are listed there, their number in
+// scratch[SCR_N_LONG].
 cudaError_t launch_ranges(uint32_t* scratch, int n_tiles, uint2* ranges, uint32_t* order, int clear,
-                          const uint32_t* lf_blk, int lf_grid, uint32_t* lf_counts, cudaStream_t st);
+                          const uint32_t* lf_blk, int lf_grid, uint32_t* lf_counts, uint32_t* long_tiles,
+                          cudaStream_t st);
+// sort the lists of the tiles in long_tiles[0 .. *n_long) by (dkey[slot],
+// slot), one CTA per list, in shared memory (lists over VG_TILE_SORT_LONG_CAP
+// flag ERR_TILE_LONG and stay unsorted)
+cudaError_t launch_tile_sort_long(const uint2* ranges, const uint32_t* long_tiles, const uint32_t* n_long,
+                                  uint32_t* pvals, const uint32_t* dkey, uint32_t* err, cudaStream_t st);
 cudaError_t launch_epoch_bump(uint32_t* state, uint32_t by, cudaStream_t st);
 // group the pairs by tile (unordered within a tile) into the ranges; counts
 // (the per-tile pair counts the ranges came from) end at zero

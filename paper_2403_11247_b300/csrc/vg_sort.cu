@@ -245,21 +245,28 @@ __global__ void __launch_bounds__(DUP_THREADS) pair_offsets_kernel(
 // ---------------------------------------------------------------------------
 // pair emission: one thread per (Gaussian, tile) pair, balanced however the
 // tiles are spread over Gaussians (a Gaussian close to the camera can cover
-// thousands of tiles).  A block takes a chunk of EMIT_CHUNK consecutive pairs;
-// chunk_start names the slot position j0 its first pair belongs to.  Every
-// visible slot owns at least one pair, so positions j0 .. j0 + EMIT_CHUNK
-// cover the chunk: each marks where its pairs start inside the chunk, and an
-// inclusive max-scan over the chunk hands every pair its slot (the owner
-// index only grows along the chunk).  Tiles in row-major order of the rect.
+// thousands of tiles).  A block takes EMIT_R consecutive chunks of
+// EMIT_CHUNK pairs at a time; chunk_start names the slot position j0 the
+// first pair belongs to.  Every visible slot owns at least one pair, so
+// positions j0 .. j0 + EMIT_R * EMIT_CHUNK cover the block's pairs: each
+// marks where its pairs start, and an inclusive max-scan over the pairs
+// hands every pair its slot (the owner index only grows along the pairs).
+// Thread t handles pair t of each chunk, so that a warp still emits 32
+// consecutive pairs at a time, and the chain of dependent loads (chunk
+// start, slot offsets, slot rect) is paid once per EMIT_R chunks.  Tiles in
+// row-major order of the rect.
 // ---------------------------------------------------------------------------
+constexpr int EMIT_R = 4;
+constexpr int EMIT_SPAN = EMIT_R * EMIT_CHUNK;
+
 __global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
     const uint32_t* __restrict__ sorted_slots, const uint32_t* __restrict__ offsets,
     const uint32_t* __restrict__ chunk_start, const uint2* __restrict__ rect, int64_t N,
     const __grid_constant__ Views V, uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals, uint32_t cap,
     uint32_t* scratch, int tile_passes, int tiles_in_smem) {
     __shared__ uint32_t s_hist[3 * 256];
-    __shared__ uint32_t s_own[EMIT_CHUNK];
-    __shared__ uint32_t s_slot[EMIT_CHUNK + 1], s_first[EMIT_CHUNK + 1];
+    __shared__ uint32_t s_own[EMIT_SPAN];
+    __shared__ uint32_t s_slot[EMIT_SPAN + 1], s_first[EMIT_SPAN + 1];
     __shared__ uint32_t s_wmax[EMIT_CHUNK / 32];
     extern __shared__ uint32_t s_tiles[];  // per-tile counts when the block's share of pairs pays for them
     for (int i = threadIdx.x; i < tile_passes * 256; i += blockDim.x) s_hist[i] = 0;
@@ -268,14 +275,15 @@ __global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
     uint32_t* tile_counts = scratch + SCR_TILE_COUNTS;
     const uint32_t nvis = scratch[SCR_NVIS];
     const uint32_t P = min(scratch[SCR_PAIRS], cap);
-    const uint32_t stride = gridDim.x * EMIT_CHUNK;
+    const uint32_t stride = gridDim.x * EMIT_SPAN;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t e0 = blockIdx.x * EMIT_CHUNK; e0 < P; e0 += stride) {
-        const uint32_t e1 = min(e0 + (uint32_t)EMIT_CHUNK, P);
-        s_own[threadIdx.x] = 0u;
+    for (uint32_t e0 = blockIdx.x * EMIT_SPAN; e0 < P; e0 += stride) {
+        const uint32_t e1 = min(e0 + (uint32_t)EMIT_SPAN, P);
+#pragma unroll
+        for (int r = 0; r < EMIT_R; ++r) s_own[r * EMIT_CHUNK + threadIdx.x] = 0u;
         __syncthreads();
         const uint32_t j0 = chunk_start[e0 / EMIT_CHUNK];
-        for (uint32_t t = threadIdx.x; t <= (uint32_t)EMIT_CHUNK; t += EMIT_CHUNK) {
+        for (uint32_t t = threadIdx.x; t <= (uint32_t)EMIT_SPAN; t += EMIT_CHUNK) {
             const uint32_t j = j0 + t;
             if (j < nvis) {
                 const uint32_t o = __ldg(offsets + j), o1 = __ldg(offsets + j + 1);
@@ -285,25 +293,41 @@ __global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
             }
         }
         __syncthreads();
-        uint32_t own = s_own[threadIdx.x];
+        // inclusive max-scan of s_own: a thread's EMIT_R consecutive entries,
+        // then across the threads in front of it
+        uint32_t loc[EMIT_R], run = 0u;
+#pragma unroll
+        for (int r = 0; r < EMIT_R; ++r) {
+            run = max(run, s_own[threadIdx.x * EMIT_R + r]);
+            loc[r] = run;
+        }
+        uint32_t inc = run;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, own, o);
-            if (lane >= o) own = max(own, y);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc = max(inc, y);
         }
-        if (lane == 31) s_wmax[warp] = own;
+        if (lane == 31) s_wmax[warp] = inc;
+        uint32_t pre = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane == 0) pre = 0u;
         __syncthreads();
 #pragma unroll
         for (int w = 0; w < EMIT_CHUNK / 32; ++w)
-            if (w < warp) own = max(own, s_wmax[w]);
-        const uint32_t e = e0 + threadIdx.x;
-        const bool live = e < e1;
-        const uint32_t active = __ballot_sync(0xffffffffu, live);
-        if (live) {
+            if (w < warp) pre = max(pre, s_wmax[w]);
+#pragma unroll
+        for (int r = 0; r < EMIT_R; ++r) s_own[threadIdx.x * EMIT_R + r] = max(pre, loc[r]);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < EMIT_R; ++r) {
+            const uint32_t e = e0 + (uint32_t)(r * EMIT_CHUNK) + threadIdx.x;
+            const bool live = e < e1;
+            const uint32_t active = __ballot_sync(0xffffffffu, live);
+            if (!live) continue;
+            const uint32_t own = s_own[r * EMIT_CHUNK + threadIdx.x];
             const uint32_t s = s_slot[own];
             const uint32_t local = e - s_first[own];
-            const uint2 r = __ldg(rect + s);
-            const uint32_t x0 = r.x & 0xffff, y0 = r.x >> 16, x1 = r.y & 0xffff;
+            const uint2 rc = __ldg(rect + s);
+            const uint32_t x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff;
             const uint32_t w = x1 - x0;
             const uint32_t ry = local / w, rx = local - ry * w;
             const int v = slot_view(s, (uint32_t)N, V.n);
@@ -317,6 +341,7 @@ __global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
                 else atomicAdd(tile_counts + key, (uint32_t)__popc(peers));
             }
         }
+        __syncthreads();  // s_own, s_slot, s_first are read before the next span reuses them
     }
     __syncthreads();
     for (int i = threadIdx.x; i < tile_passes * 256; i += blockDim.x) {
@@ -353,15 +378,15 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, ui
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    int64_t eg = ceil_div((int64_t)cap, EMIT_CHUNK);
+    int64_t eg = ceil_div((int64_t)cap, EMIT_SPAN);
     if (eg > (int64_t)sms * 8) eg = (int64_t)sms * 8;
     if (eg < 1) eg = 1;
     // per-tile counts: a per-block histogram in shared memory pays for its
     // zeroing and flush only when a block emits at least as many pairs as
     // there are tiles; otherwise one global atomic per run of equal tiles
-    const int64_t chunks_per_block = ceil_div(ceil_div((int64_t)cap, EMIT_CHUNK), eg);
+    const int64_t spans_per_block = ceil_div(ceil_div((int64_t)cap, EMIT_SPAN), eg);
     const int tiles_in_smem = V.total_tiles <= EMIT_SMEM_TILES &&
-                              (int64_t)V.total_tiles <= chunks_per_block * EMIT_CHUNK ? 1 : 0;
+                              (int64_t)V.total_tiles <= spans_per_block * EMIT_SPAN ? 1 : 0;
     const size_t smem = tiles_in_smem ? (size_t)V.total_tiles * 4 : 0;
     e = allow_dynamic_smem((const void*)emit_pairs_kernel, smem);
     if (e != cudaSuccess) return e;
@@ -393,9 +418,10 @@ __global__ void __launch_bounds__(1024) ranges_kernel(uint32_t* __restrict__ cnt
                                                       uint2* __restrict__ ranges, uint32_t* __restrict__ order,
                                                       int staged, uint32_t* __restrict__ scratch, int clear,
                                                       const uint32_t* __restrict__ lf_blk, int lf_grid,
-                                                      uint32_t* __restrict__ lf_counts) {
+                                                      uint32_t* __restrict__ lf_counts,
+                                                      uint32_t* __restrict__ long_tiles) {
     __shared__ uint32_t s_w[32];
-    __shared__ uint32_t s_carry, s_max;
+    __shared__ uint32_t s_carry, s_max, s_nlong;
     __shared__ uint32_t s_lf[2];
     __shared__ uint32_t s_bin[ORDER_BUCKETS];
     extern __shared__ uint32_t s_cnt[];  // the counts, when they fit: one coalesced load for all three uses
@@ -408,6 +434,7 @@ __global__ void __launch_bounds__(1024) ranges_kernel(uint32_t* __restrict__ cnt
         s_max = 0;
     }
     if (threadIdx.x < 2) s_lf[threadIdx.x] = 0;
+    if (threadIdx.x == 0) s_nlong = 0;
     for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) s_bin[i] = 0;
     __syncthreads();
     if (lf_blk) {  // the fused loss's normalisers from the compaction's per-block counts
@@ -451,6 +478,7 @@ __global__ void __launch_bounds__(1024) ranges_kernel(uint32_t* __restrict__ cnt
         __syncthreads();
         const uint32_t start = s_carry + (warp ? s_w[warp - 1] : 0u) + inc - x;
         if (i < n) ranges[i] = make_uint2(start, start + x);
+        if (long_tiles && i < n && x > (uint32_t)VG_TILE_SORT_CAP) long_tiles[atomicAdd(&s_nlong, 1u)] = (uint32_t)i;
         __syncthreads();
         if (threadIdx.x == 0) s_carry += s_w[31];
         __syncthreads();
@@ -459,6 +487,7 @@ __global__ void __launch_bounds__(1024) ranges_kernel(uint32_t* __restrict__ cnt
         lf_counts[0] = s_lf[0];
         lf_counts[1] = s_lf[1];
     }
+    if (long_tiles && threadIdx.x == 0) scratch[SCR_N_LONG] = s_nlong;  // (complete: barriers since)
     if (!order) return;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
@@ -498,14 +527,15 @@ __global__ void __launch_bounds__(1024) ranges_kernel(uint32_t* __restrict__ cnt
 }
 
 cudaError_t launch_ranges(uint32_t* scratch, int n_tiles, uint2* ranges, uint32_t* order, int clear,
-                          const uint32_t* lf_blk, int lf_grid, uint32_t* lf_counts, cudaStream_t st) {
+                          const uint32_t* lf_blk, int lf_grid, uint32_t* lf_counts, uint32_t* long_tiles,
+                          cudaStream_t st) {
     count_launches(1);
     const int staged = n_tiles <= RANGES_SMEM_TILES ? 1 : 0;
     const size_t smem = staged ? (size_t)n_tiles * 4 : 0;
     cudaError_t e = allow_dynamic_smem((const void*)ranges_kernel, smem);
     if (e != cudaSuccess) return e;
     ranges_kernel<<<1, 1024, smem, st>>>(scratch + SCR_TILE_COUNTS, n_tiles, ranges, order, staged, scratch, clear,
-                                         lf_blk, lf_grid, lf_counts);
+                                         lf_blk, lf_grid, lf_counts, long_tiles);
     return cudaGetLastError();
 }
 
@@ -552,6 +582,76 @@ cudaError_t launch_tile_scatter(const uint32_t* keys_in, const uint32_t* vals_in
     count_launches(1);
     tile_scatter_kernel<<<(unsigned)grid, 256, 0, st>>>(keys_in, vals_in, n_dev, cap, ranges, counts, keys_out,
                                                        vals_out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// long tile lists (over VG_TILE_SORT_CAP, the forward compositing kernel's
+// own sort): one CTA per list, keys (FP32 depth bits, slot) packed as one
+// 64-bit integer (depth bits high), so that the lexicographic order is the
+// integer order and every key is distinct; padded to a power of two with the
+// largest value and sorted by a bitonic network in shared memory
+// ---------------------------------------------------------------------------
+constexpr int LONG_SORT_THREADS = 512;
+
+__global__ void __launch_bounds__(LONG_SORT_THREADS) tile_sort_long_kernel(
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ long_tiles, const uint32_t* __restrict__ n_long_p,
+    uint32_t* __restrict__ pvals, const uint32_t* __restrict__ dkey, uint32_t* __restrict__ err) {
+    extern __shared__ unsigned long long s_k[];  // VG_TILE_SORT_LONG_CAP entries
+    const uint32_t n_long = *n_long_p;
+    for (uint32_t t = blockIdx.x; t < n_long; t += gridDim.x) {
+        const uint2 rg = ranges[long_tiles[t]];
+        const uint32_t n = rg.y - rg.x;
+        if (n > (uint32_t)VG_TILE_SORT_LONG_CAP) {  // left unsorted: the outputs are flagged invalid
+            if (threadIdx.x == 0) atomicOr(err, ERR_TILE_LONG);
+            continue;
+        }
+        uint32_t np = 1;
+        while (np < n) np <<= 1;
+        for (uint32_t i = threadIdx.x; i < np; i += blockDim.x) {
+            unsigned long long k = ~0ull;
+            if (i < n) {
+                const uint32_t sl = pvals[rg.x + i];
+                k = ((unsigned long long)dkey[sl] << 32) | sl;
+            }
+            s_k[i] = k;
+        }
+        __syncthreads();
+        for (uint32_t size = 2; size <= np; size <<= 1)
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (uint32_t c = threadIdx.x; c < (np >> 1); c += blockDim.x) {
+                    // comparator c joins a (bit `stride` clear) and a + stride
+                    const uint32_t a = ((c & ~(stride - 1u)) << 1) | (c & (stride - 1u));
+                    const bool asc = (a & size) == 0;
+                    const unsigned long long x = s_k[a], y = s_k[a + stride];
+                    if ((x > y) == asc) {
+                        s_k[a] = y;
+                        s_k[a + stride] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) pvals[rg.x + i] = (uint32_t)s_k[i];
+        __syncthreads();  // shared memory free for the next list
+    }
+}
+
+cudaError_t launch_tile_sort_long(const uint2* ranges, const uint32_t* long_tiles, const uint32_t* n_long,
+                                  uint32_t* pvals, const uint32_t* dkey, uint32_t* err, cudaStream_t st) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 148;
+    }
+    const size_t smem = (size_t)VG_TILE_SORT_LONG_CAP * sizeof(unsigned long long);
+    cudaError_t e = allow_dynamic_smem((const void*)tile_sort_long_kernel, smem);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
+    // three 64 KB CTAs per SM; a CTA with no list left exits at once
+    tile_sort_long_kernel<<<(unsigned)(3 * sms), LONG_SORT_THREADS, smem, st>>>(ranges, long_tiles, n_long, pvals,
+                                                                                dkey, err);
     return cudaGetLastError();
 }
 

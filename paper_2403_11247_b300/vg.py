@@ -24,6 +24,7 @@ STATUS_NAMES = ["VG_OK", "VG_ERR_INVALID_ARG", "VG_ERR_OOM", "VG_ERR_CUDA", "VG_
 VG_SCENE_COPY, VG_SCENE_BORROW = 0, 1
 VG_SORT_AUTO, VG_SORT_GLOBAL, VG_SORT_TILE = 0, 1, 2
 VG_TILE_SORT_CAP = 1024
+VG_TILE_SORT_LONG_CAP = 8192
 VG_MAX_VIEWS = 64
 GROUPS = ("logscale", "rot", "opacity", "rgb")
 GDIM = {"logscale": 3, "rot": 4, "opacity": 1, "rgb": 3}

@@ -167,22 +167,52 @@ def test_sort_modes_give_identical_lists_images_and_gradients(cuda):
         grad_tolerance_check(b[4][name], a[4][name], "sort modes:" + name, rtol=1e-4, atol_frac=1e-5)
 
 
-def test_tile_list_over_the_per_tile_cap_is_flagged_and_auto_falls_back(cuda):
+def test_long_tile_lists_sorted_per_tile_bit_exact(cuda):
+    """4,000 Gaussians in 12 tiles: lists of ~1,600 entries, past what the
+    compositing kernel sorts itself; the per-tile form's long-list pass sorts
+    them, lists bit-exact against the oracle, images equal the global sort."""
     sc, cams = synth.tiny_scene(n=4000), [synth.tiny_camera()]
+    P, nb, nbl = check_binning(sc, cams, sort_mode=V.VG_SORT_TILE)
+    o = O.Oracle(sc, cams)
+    ts, _ = o.bins()
+    assert np.diff(ts).max() > V.VG_TILE_SORT_CAP
+    sh = V.vg_scene_upload(sc)
+    a = V.render_with_retry(sh, cams, V.default_params(sort_mode=V.VG_SORT_TILE), V.vg_ctx_create(0))
+    b = V.render_with_retry(sh, cams, V.default_params(sort_mode=V.VG_SORT_GLOBAL), V.vg_ctx_create(0))
+    for x, y in zip(a, b):
+        assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
+
+
+@pytest.mark.parametrize("n", [4000, 30000])
+def test_auto_sort_form_escalates_on_long_lists(cuda, n):
+    """VG_SORT_AUTO starts with the compositing kernel's own sort; a list
+    over VG_TILE_SORT_CAP flags the forward (VG_ERR_CAPACITY) and the ctx
+    sorts globally from then on, with outputs equal to the global sort's
+    bit for bit.  VG_SORT_TILE's long-list pass reports a list over
+    VG_TILE_SORT_LONG_CAP the same way."""
+    sc, cams = synth.tiny_scene(n=n), [synth.tiny_camera()]
     sh = V.vg_scene_upload(sc)
     ref_ctx = V.vg_ctx_create(0)
     ref = V.render_with_retry(sh, cams, V.default_params(sort_mode=V.VG_SORT_GLOBAL), ref_ctx)
     ranges = V.vg_ctx_buffer(ref_ctx, "ranges", 12)
-    assert (ranges[:, 1] - ranges[:, 0]).max() > V.VG_TILE_SORT_CAP
+    longest = int((ranges[:, 1] - ranges[:, 0]).max())
+    assert longest > (V.VG_TILE_SORT_LONG_CAP if n == 30000 else V.VG_TILE_SORT_CAP), longest
     ctx = V.vg_ctx_create(0)
     V.vg_ctx_reserve(ctx, V.vg_ctx_stats(ref_ctx)["pairs"] + 1024)
-    V.vg_render_fwd(sh, cams, V.default_params(sort_mode=V.VG_SORT_TILE), ctx)
+    V.vg_render_fwd(sh, cams, V.default_params(), ctx)
     assert V.vg_check(ctx) == V.VG_ERR_CAPACITY
     assert V.vg_check(ctx) == V.VG_OK   # the flag was cleared
-    out = V.vg_render_fwd(sh, cams, V.default_params(), ctx)   # auto: global from now on
+    V.vg_render_fwd(sh, cams, V.default_params(), ctx)
+    assert V.vg_check(ctx) == V.VG_OK
+    out = V.vg_render_fwd(sh, cams, V.default_params(), ctx)
     assert V.vg_check(ctx) == V.VG_OK
     for x, y in zip(out, ref):
         assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
+    if n == 30000:   # VG_SORT_TILE itself reports the list over its cap
+        t_ctx = V.vg_ctx_create(0)
+        V.vg_ctx_reserve(t_ctx, V.vg_ctx_stats(ref_ctx)["pairs"] + 1024)
+        V.vg_render_fwd(sh, cams, V.default_params(sort_mode=V.VG_SORT_TILE), t_ctx)
+        assert V.vg_check(t_ctx) == V.VG_ERR_CAPACITY
 
 
 # ---------------------------------------------------------------------------
