@@ -282,6 +282,19 @@ vg_status vg_ctx_reserve(vg_ctx* ctx, int64_t pair_capacity);
  * VG_ERR_CAPACITY / VG_ERR_TIMEOUT if a device flag is set (and clear it),
  * else VG_OK. */
 vg_status vg_check(vg_ctx* ctx, vg_stream stream);
+
+/* Bounded device waits (failure detection; no counterpart in the paper).
+ * Every spin a kernel of this ctx makes on another block -- the radix
+ * sort's and the pair-offset scan's decoupled look-back, the cooperative
+ * loss's grid barrier -- gives up after `polls` unsuccessful polls, sets a
+ * device flag and lets the kernel finish (its results are then wrong, every
+ * index stays inside its buffer); the next vg_check returns VG_ERR_TIMEOUT.
+ * The default, 2^21 polls (about a second of L2 round trips), is far above
+ * any wait of a working device; a small limit makes the waits run out (for
+ * tests).  polls = VG_SPIN_LIMIT_DEFAULT_SENTINEL restores the default.
+ * Takes effect from the next call enqueued on the ctx. */
+#define VG_SPIN_LIMIT_DEFAULT_SENTINEL 0xffffffffu
+vg_status vg_ctx_set_spin_limit(vg_ctx* ctx, uint32_t polls);
 vg_status vg_ctx_stats(vg_ctx* ctx, vg_stream stream, vg_stats* out);
 /* Zero the evaluated / blended / backward pair counters (enqueued). */
 vg_status vg_ctx_reset_counters(vg_ctx* ctx, vg_stream stream);
@@ -480,7 +493,10 @@ vg_status vg_sample_rays(uint8_t* mask, int64_t n, double rate, uint64_t seed, c
  * device (with that device current) looks the array's device address up with
  * cudaGetSymbolAddress; make that first call before any stream capture.  All
  * calls share the array: calls that overlap on the GPU (unordered streams)
- * race on it and must be serialised by the caller. */
+ * race on it and must be serialised by the caller.  The array's address is
+ * kept per device ordinal for the life of the process, so the call assumes
+ * the device's primary context (the CUDA runtime's, which PyTorch uses) and
+ * no cudaDeviceReset between calls. */
 #define VG_NOALLOC_MAX_VIEWS 256
 vg_status vg_loss_l1_noalloc(int32_t n_views, int64_t n_pix, const float* C, const float* D, const float* S,
                              const float* Ct, const float* Dt, float w_depth, float gate,

@@ -182,13 +182,14 @@ struct vg_ctx {
     int64_t pair_cap = 0;
     DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, tile_order, Tfin, ncontrib, lookback,
         scratch, state, pose_part, icp_part, loss_scratch, pair_off, chunk_start, blk_count, vis, ssim_ws, grow_ws,
-        neval, loss_blk, long_tiles;
+        neval, loss_blk, long_tiles, part_total, blk_prefix;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
     // VG_SORT_AUTO's form on this ctx: 0 per-tile sort, 2 global (a list
     // passed VG_TILE_SORT_CAP; for such lists the global radix passes beat
     // the long-list pass's comparison sort)
     int auto_stage = 0;
+    uint32_t spin_limit = SPIN_LIMIT_DEFAULT;  // unsuccessful polls before a bounded device wait gives up
     bool g2d_clean = false;
     bool fwd_zeroed = false;  // the last forward zeroed the visible slots' gradient rows and the pose sums
     // scratch words known to be zero: a forward leaves every counter it
@@ -493,6 +494,12 @@ vg_status vg_check(vg_ctx* ctx, vg_stream stream) {
     return VG_OK;
 }
 
+vg_status vg_ctx_set_spin_limit(vg_ctx* ctx, uint32_t polls) {
+    if (!ctx) return fail(VG_ERR_INVALID_ARG, "vg_ctx_set_spin_limit: null ctx");
+    ctx->spin_limit = polls == VG_SPIN_LIMIT_DEFAULT_SENTINEL ? SPIN_LIMIT_DEFAULT : polls;
+    return VG_OK;
+}
+
 vg_status vg_ctx_reset_counters(vg_ctx* ctx, vg_stream stream) {
     if (!ctx) return fail(VG_ERR_INVALID_ARG, "vg_ctx_reset_counters: null ctx");
     VG_CUDA(cudaMemsetAsync(ctx->state.as<uint32_t>() + ST_EVALS, 0, 24, (cudaStream_t)stream));
@@ -688,6 +695,7 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
     VG_TRY(ctx->chunk_start.ensure((size_t)ceil_div(std::max<int64_t>(ctx->pair_cap, 1), EMIT_CHUNK) * 4, st,
                                    "pair chunk starts"));
     VG_TRY(ctx->blk_count.ensure((size_t)preprocess_blocks(N) * 8, st, "block counts"));
+    VG_TRY(ctx->blk_prefix.ensure((size_t)preprocess_blocks(N) * 8, st, "block count prefixes"));
     const int lf_grid = compact_grid(N, cs);
     if (lf) {
         VG_TRY(ctx->loss_blk.ensure((size_t)lf_grid * 8, st, "loss block counts"));
@@ -699,6 +707,7 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
         VG_TRY(ctx->dval[b].ensure(slots * 4, st, "depth values"));
     }
     VG_TRY(ctx->vis.ensure(slots * 4, st, "visible slots"));
+    VG_TRY(ctx->part_total.ensure((size_t)ceil_div(slots, DUP_TILE) * 4, st, "pair partition totals"));
     VG_TRY(ctx->ranges.ensure((size_t)V.total_tiles * 8, st, "ranges"));
     VG_TRY(ctx->tile_order.ensure((size_t)V.total_tiles * 4, st, "tile order"));
     const size_t scr_words = (size_t)(SCR_WORDS + V.total_tiles);
@@ -759,14 +768,16 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
                                                 ctx->ntiles.as<uint32_t>(),
                                                 tile_sort ? ctx->pair_off.as<uint32_t>() : nullptr,
                                                 ctx->chunk_start.as<uint32_t>(), cap, scr, err, g2d_rows,
-                                                ctx->pose_part.as<float>(), n_views * 6, cs, st);
+                                                ctx->pose_part.as<float>(), n_views * 6, cs,
+                                                ctx->blk_prefix.as<uint32_t>(), st);
                  if (e != cudaSuccess) return e;
                  for (int p = 0; p < (tile_sort ? 0 : 4); ++p) {
                      const int i = p & 1, o = i ^ 1;
                      e = launch_sort_pass(ctx->dkey[i].as<uint32_t>(), ctx->dval[i].as<uint32_t>(),
                                           ctx->dkey[o].as<uint32_t>(), ctx->dval[o].as<uint32_t>(), scr + SCR_NVIS,
                                           (uint32_t)slots, 8 * p, scr + SCR_DEPTH_HIST + 256 * p, lb,
-                                          scr + SCR_CNT_DEPTH + p, state, (uint32_t)p, err, dgrid, st);
+                                          scr + SCR_CNT_DEPTH + p, state, (uint32_t)p, err, dgrid, ctx->spin_limit,
+                                          st);
                      if (e != cudaSuccess) return e;
                  }
                  return cudaSuccess;
@@ -778,13 +789,14 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
              launch_duplicate(ctx->dval[0].as<uint32_t>(), ctx->pair_off.as<uint32_t>(),
                               ctx->chunk_start.as<uint32_t>(), tile_sort, ctx->ntiles.as<uint32_t>(),
                               ctx->rect.as<uint2>(), N, V, ctx->pkey[0].as<uint32_t>(), ctx->pval[0].as<uint32_t>(), cap,
-                              scr, tile_sort ? 0 : tp, lb, state, 4u, err, slots, st));
+                              scr, tile_sort ? 0 : tp, ctx->part_total.as<uint32_t>(), err, slots,
+                              ctx->ranges.as<uint2>(), st));
     const int tgrid = sort_pass_grid(cap);
     if (tile_sort) {
         VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr, V.total_tiles, ctx->ranges.as<uint2>(),
                                                ctx->tile_order.as<uint32_t>(), 0, cs.lf_blk, lf_grid,
                                                scr + SCR_LOSS_VALID,
-                                               long_pass ? ctx->long_tiles.as<uint32_t>() : nullptr, st));
+                                               long_pass ? ctx->long_tiles.as<uint32_t>() : nullptr, 0, st));
         VG_STAGE(VG_STAGE_TILE_SORT, ([&]() -> cudaError_t {
                      cudaError_t e = launch_tile_scatter(ctx->pkey[0].as<uint32_t>(), ctx->pval[0].as<uint32_t>(),
                                                          scr + SCR_PAIRS, cap, ctx->ranges.as<uint2>(),
@@ -802,7 +814,7 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
                      cudaError_t e = launch_sort_pass(
                          ctx->pkey[i].as<uint32_t>(), ctx->pval[i].as<uint32_t>(), ctx->pkey[o].as<uint32_t>(),
                          ctx->pval[o].as<uint32_t>(), scr + SCR_PAIRS, cap, 8 * p, scr + SCR_TILE_HIST + 256 * p, lb,
-                         scr + SCR_CNT_TILE + p, state, 5u + (uint32_t)p, err, tgrid, st);
+                         scr + SCR_CNT_TILE + p, state, 5u + (uint32_t)p, err, tgrid, ctx->spin_limit, st);
                      if (e != cudaSuccess) return e;
                  }
                  return cudaSuccess;
@@ -810,9 +822,13 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
     const int fin = tile_sort ? 1 : (tp & 1);
     ctx->final_pair = fin;
     if (!tile_sort)
-        VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr, V.total_tiles, ctx->ranges.as<uint2>(),
-                                               ctx->tile_order.as<uint32_t>(), 1, cs.lf_blk, lf_grid,
-                                               scr + SCR_LOSS_VALID, nullptr, st));
+        VG_STAGE(VG_STAGE_RANGES, ([&]() -> cudaError_t {
+                     cudaError_t e = launch_tile_bounds(ctx->pkey[fin].as<uint32_t>(), scr + SCR_PAIRS, cap,
+                                                        ctx->ranges.as<uint2>(), st);
+                     if (e != cudaSuccess) return e;
+                     return launch_ranges(scr, V.total_tiles, ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
+                                          1, cs.lf_blk, lf_grid, scr + SCR_LOSS_VALID, nullptr, 1, st);
+                 })());
     VG_STAGE(VG_STAGE_BLEND_FWD,
              launch_blend_fwd(V, cs, params->ppt_fwd, params->persist_ctas, state + ST_WORK_FWD,
                               ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
@@ -988,7 +1004,7 @@ vg_status vg_loss_l1_masked(int32_t n_views, int64_t n_pix, const float* C, cons
     // words 4..7 of the loss scratch: kept zero between calls by the kernels
     VG_STAGE(VG_STAGE_LOSS, launch_loss_l1(n_views, n_pix, C, D, S, Ct, Dt, pixel_mask, w_depth, gate, dC, dD, loss,
                                            ctx->loss_scratch.as<uint32_t>() + 4,
-                                           ctx->state.as<uint32_t>() + ST_ERR, st));
+                                           ctx->state.as<uint32_t>() + ST_ERR, ctx->spin_limit, st));
     return VG_OK;
 }
 

@@ -18,8 +18,9 @@ constexpr uint32_t ERR_TABLE = 4u;     // the anchor-growing hash table was full
 constexpr uint32_t ERR_TILE_LIST = 8u; // a tile list longer than the compositing kernel sorts (no long pass)
 constexpr uint32_t ERR_TILE_LONG = 16u; // a tile list longer than the long-list pass sorts
 
-// a bounded spin gives up after this many polls (~1 s of L2 round trips)
-constexpr uint32_t SPIN_LIMIT = 1u << 21;
+// a bounded spin gives up after this many unsuccessful polls (~1 s of L2
+// round trips) unless the ctx sets another limit (vg_ctx_set_spin_limit)
+constexpr uint32_t SPIN_LIMIT_DEFAULT = 1u << 21;
 
 constexpr int RADIUS_MAX = 1 << 20;
 

@@ -3,6 +3,8 @@
 // mask straight-through estimator Eq. 11-12) with the codebook gradients
 // accumulated in the same pass, the camera-pose twist gradient, the ICP term
 // (Eq. 20) and the L1 photometric/depth loss gradient images.
+#include <mutex>
+
 #include "vg_internal.h"
 
 namespace vgk {
@@ -598,7 +600,8 @@ __global__ void loss_l1_kernel(int64_t n_pix, int64_t total, const float* __rest
 __global__ void __launch_bounds__(256) loss_l1_coop_kernel(
     int64_t n_pix, int n_views, const float* __restrict__ C, const float* __restrict__ D, const float* __restrict__ S,
     const float* __restrict__ Ct, const float* __restrict__ Dt, const uint8_t* __restrict__ mask, float w_depth,
-    float gate, uint32_t* ctl, float* __restrict__ dC, float* __restrict__ dD, float* __restrict__ loss, uint32_t* err) {
+    float gate, uint32_t* ctl, float* __restrict__ dC, float* __restrict__ dD, float* __restrict__ loss, uint32_t* err,
+    uint32_t spin_limit) {
     __shared__ float s_tmp[8];
     __shared__ uint32_t s_cnt[2];
     const uint32_t q_view = (uint32_t)(n_pix / 4), n_q = q_view * (uint32_t)n_views;
@@ -635,9 +638,12 @@ __global__ void __launch_bounds__(256) loss_l1_coop_kernel(
         atomicAdd(ctl + 2, 1u);
         const volatile uint32_t* arrived = ctl + 2;
         uint32_t polls = 0;
-        while (*arrived < gridDim.x && ++polls < SPIN_LIMIT) {
+        while (*arrived < gridDim.x) {
+            if (++polls > spin_limit) {  // gives up: the counts may be partial, the call's results wrong
+                atomicOr(err, ERR_WAIT);
+                break;
+            }
         }
-        if (polls >= SPIN_LIMIT) atomicOr(err, ERR_WAIT);
         __threadfence();
         s_cnt[0] = *(const volatile uint32_t*)(ctl + 0);
         s_cnt[1] = *(const volatile uint32_t*)(ctl + 1);
@@ -690,7 +696,7 @@ __global__ void __launch_bounds__(256) loss_l1_coop_kernel(
 
 cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const float* D, const float* S, const float* Ct,
                            const float* Dt, const uint8_t* mask, float w_depth, float gate, float* dC, float* dD,
-                           float* loss, uint32_t* valid_count, uint32_t* err, cudaStream_t st) {
+                           float* loss, uint32_t* valid_count, uint32_t* err, uint32_t spin_limit, cudaStream_t st) {
     const int64_t total = (int64_t)n_views * n_pix;
     int64_t blocks = ceil_div(ceil_div(total > 0 ? total : 1, 4), 256);
     if (blocks > 148 * 8) blocks = 148 * 8;
@@ -699,15 +705,25 @@ cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const flo
                     (gate < 0.f || al(S)) && (reinterpret_cast<uintptr_t>(mask) & 3u) == 0;
     // one cooperative launch where the device takes them and the planes allow
     // four pixels per step; otherwise a counting kernel, then the loss kernel
-    static int coop_blocks = -1;
-    if (coop_blocks < 0) {
-        int dev = 0, coop = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, loss_l1_coop_kernel, 256, 0);
-        coop_blocks = coop ? sms * per : 0;
-        cudaGetLastError();
+    // the co-resident grid, per device (queried once per device, under a lock)
+    static std::mutex mu;
+    static int coop_of[64];
+    static bool known_of[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int coop_blocks = 0;
+    if (dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!known_of[dev]) {
+            int coop = 0, sms = 0, per = 0;
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, loss_l1_coop_kernel, 256, 0);
+            coop_of[dev] = coop ? sms * per : 0;
+            known_of[dev] = true;
+            cudaGetLastError();
+        }
+        coop_blocks = coop_of[dev];
     }
     if (vec && coop_blocks > 0 && total / 4 < (int64_t)UINT32_MAX && err) {
         int64_t g = ceil_div(total / 4, 256);
@@ -724,7 +740,7 @@ cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const flo
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         const cudaError_t e = cudaLaunchKernelEx(&cfg, loss_l1_coop_kernel, n_pix, n_views, C, D, S, Ct, Dt, mask,
-                                                 w_depth, gate, valid_count, dC, dD, loss, err);
+                                                 w_depth, gate, valid_count, dC, dD, loss, err, spin_limit);
         if (e == cudaSuccess) {
             count_launches(1);
             return e;
@@ -733,7 +749,10 @@ cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const flo
         // device): the two-launch form below needs no co-residency
         if (e != cudaErrorCooperativeLaunchTooLarge) return e;
         cudaGetLastError();
-        coop_blocks = 0;
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            coop_of[dev] = 0;
+        }
     }
     count_launches(2);
     count_valid_kernel<<<(unsigned)blocks, 256, 0, st>>>(Dt, mask, total, valid_count, loss);

@@ -86,11 +86,13 @@ cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& c
 // g2d_rows (may be NULL): the backward's per-slot gradient rows, zeroed here
 // for every visible slot; pose_zero [n_pose] (may be NULL): zeroed too.
 // With cs.lf_on it also counts the fused loss's normalisers per block into
-// cs.lf_blk [2][compact_grid] (the ranges kernel sums them).
+// cs.lf_blk [2][compact_grid] (the ranges kernel sums them).  blk_prefix
+// [2][preprocess blocks]: room for the counts' scan, used for large grids.
 cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count,
                            uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, const uint32_t* ntiles,
                            uint32_t* pair_off, uint32_t* chunk_start, uint32_t cap, uint32_t* scratch, uint32_t* err,
-                           float* g2d_rows, float* pose_zero, int n_pose, const Consts& cs, cudaStream_t st);
+                           float* g2d_rows, float* pose_zero, int n_pose, const Consts& cs, uint32_t* blk_prefix,
+                           cudaStream_t st);
 cudaError_t launch_rvq_decode(int dim, int L, int K, const float* cb, const uint8_t* idx, const float* raw,
                               int64_t n, float* out, cudaStream_t st);
 
@@ -101,17 +103,21 @@ cudaError_t launch_sort_pass(const uint32_t* keys_in, const uint32_t* vals_in, u
                              uint32_t* vals_out, const uint32_t* n_dev, uint32_t n_cap, int shift,
                              const uint32_t* hist, unsigned long long* lookback, uint32_t* counter,
                              const uint32_t* state, uint32_t epoch_offset, uint32_t* err, int grid,
-                             cudaStream_t st);
+                             uint32_t spin_limit, cudaStream_t st);
 int sort_pass_grid(uint32_t n_cap);
 // offsets has room for [slots + 1] (the last is the pair count) and
 // chunk_start for [ceil(cap / EMIT_CHUNK)]; offsets_ready: both were filled by
-// launch_compact for this order
+// launch_compact for this order; else part_total [ceil(slots / 1024)] holds
+// the per-partition totals of the reduce-then-scan
 cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, uint32_t* chunk_start,
                              bool offsets_ready, const uint32_t* ntiles,
                              const uint2* rect, int64_t N, const Views& V, uint32_t* pkeys, uint32_t* pvals,
-                             uint32_t cap, uint32_t* scratch, int tile_passes, unsigned long long* lookback,
-                             const uint32_t* state, uint32_t epoch_offset, uint32_t* err, int64_t max_slots,
-                             cudaStream_t st);
+                             uint32_t cap, uint32_t* scratch, int tile_passes, uint32_t* part_total, uint32_t* err,
+                             int64_t max_slots, uint2* ranges, cudaStream_t st);
+// global-sort form: tile ranges from the tile-sorted pair keys (the
+// emission zeroed them; the per-tile counts are not kept)
+cudaError_t launch_tile_bounds(const uint32_t* keys, const uint32_t* n_dev, uint32_t cap, uint2* ranges,
+                               cudaStream_t st);
 // per-tile [start, end) from the per-tile pair counts at scratch +
 // SCR_TILE_COUNTS (one-block scan); clear: zero the counts, the digit
 // histograms and the pass counters afterwards (global-sort form).  With
@@ -119,9 +125,11 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, ui
 // lf_blk[c * lf_grid + b] over b.  With long_tiles (may be NULL) the tiles
 // whose lists pass VG_TILE_SORT_CAP are listed there, their number in
 // scratch[SCR_N_LONG].
+// from_ranges: the ranges are already final (global-sort form): the counts
+// are taken from them and only the order (and the rest) is built.
 cudaError_t launch_ranges(uint32_t* scratch, int n_tiles, uint2* ranges, uint32_t* order, int clear,
                           const uint32_t* lf_blk, int lf_grid, uint32_t* lf_counts, uint32_t* long_tiles,
-                          cudaStream_t st);
+                          int from_ranges, cudaStream_t st);
 // sort the lists of the tiles in long_tiles[0 .. *n_long) by (dkey[slot],
 // slot), one CTA per list, in shared memory (lists over VG_TILE_SORT_LONG_CAP
 // flag ERR_TILE_LONG and stay unsorted)
@@ -209,10 +217,12 @@ cudaError_t launch_sample_rays(uint8_t* mask, int64_t n, unsigned long long seed
 // mask non-NULL: only sampled pixels count (vg_loss_l1_masked).  valid_count:
 // four words, zero before the first call; the call leaves them zero (no memset
 // between calls) and writes loss[0] itself.  err: the ctx's status word (the
-// single-launch form's barrier reports a spin that ran out there)
+// single-launch form's barrier reports a spin that ran out of its spin_limit
+// unsuccessful polls there)
 cudaError_t launch_loss_l1(int n_views, int64_t n_pix, const float* C, const float* D, const float* S,
                            const float* Ct, const float* Dt, const uint8_t* mask, float w_depth, float gate, float* dC,
-                           float* dD, float* loss, uint32_t* valid_count, uint32_t* err, cudaStream_t st);
+                           float* dD, float* loss, uint32_t* valid_count, uint32_t* err, uint32_t spin_limit,
+                           cudaStream_t st);
 
 // optim.cu
 // zero_mask bit t: tensor t's gradient is zeroed once read

@@ -11,8 +11,9 @@
 // Look-back entries are 64-bit: [epoch:32][flag:2][count:30].  The epoch comes
 // from device memory (bumped once per forward), so entries left by earlier
 // sorts never look ready and no memset of the look-back arrays is needed.
-// Every wait on another partition is bounded (SPIN_LIMIT polls); on timeout
-// the kernel sets ERR_WAIT and carries on with a zero count.
+// Every wait on another partition is bounded (spin_limit unsuccessful polls);
+// on timeout the kernel sets ERR_WAIT and carries on with the prefix it has
+// (too small: every position it writes stays inside the output).
 #include "vg_internal.h"
 
 namespace vgk {
@@ -31,7 +32,7 @@ __device__ __forceinline__ unsigned long long lb_make(uint32_t epoch, unsigned l
 constexpr int LB_WINDOW = 8;
 
 __device__ __forceinline__ uint32_t lookback_walk(const unsigned long long* lb, int stride, int col, uint32_t pid,
-                                                  uint32_t epoch, uint32_t* err) {
+                                                  uint32_t epoch, uint32_t* err, uint32_t spin_limit) {
     uint32_t excl = 0;
     int64_t j = (int64_t)pid - 1;
     uint32_t spins = 0;
@@ -51,7 +52,7 @@ __device__ __forceinline__ uint32_t lookback_walk(const unsigned long long* lb, 
             }
         }
         if (stop) break;
-        if (u == 0 && ++spins > SPIN_LIMIT) {
+        if (u == 0 && ++spins > spin_limit) {
             atomicOr(err, ERR_WAIT);
             break;
         }
@@ -70,7 +71,8 @@ __device__ __forceinline__ void hist_add_warp(uint32_t* h, uint32_t b, uint32_t 
 __global__ void __launch_bounds__(SORT_THREADS) onesweep_pass_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const uint32_t* n_dev, uint32_t n_cap, int shift, const uint32_t* __restrict__ hist,
-    unsigned long long* lookback, uint32_t* counter, const uint32_t* state, uint32_t epoch_offset, uint32_t* err) {
+    unsigned long long* lookback, uint32_t* counter, const uint32_t* state, uint32_t epoch_offset, uint32_t* err,
+    uint32_t spin_limit) {
     __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_whist[8][256];
     __shared__ uint32_t s_bpre[256];
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(SORT_THREADS) onesweep_pass_kernel(
         s_bpre[tid] = block_excl_scan_256(total, s_tmp, &btot);
         uint32_t excl = 0;
         if (pid > 0) {
-            excl = lookback_walk(lb, 256, tid, pid, epoch, err);
+            excl = lookback_walk(lb, 256, tid, pid, epoch, err, spin_limit);
             st_volatile64(lb + (int64_t)pid * 256 + tid, lb_make(epoch, LB_INC, excl + total));
         }
         s_gout[tid] = s_base[tid] + excl;
@@ -175,70 +177,75 @@ int sort_pass_grid(uint32_t n_cap) {
 cudaError_t launch_sort_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                              const uint32_t* n_dev, uint32_t n_cap, int shift, const uint32_t* hist,
                              unsigned long long* lookback, uint32_t* counter, const uint32_t* state,
-                             uint32_t epoch_offset, uint32_t* err, int grid, cudaStream_t st) {
+                             uint32_t epoch_offset, uint32_t* err, int grid, uint32_t spin_limit, cudaStream_t st) {
     count_launches(1);
     onesweep_pass_kernel<<<grid, SORT_THREADS, 0, st>>>(keys_in, vals_in, keys_out, vals_out, n_dev, n_cap, shift, hist,
-                                                        lookback, counter, state, epoch_offset, err);
+                                                        lookback, counter, state, epoch_offset, err, spin_limit);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // pair offsets: exclusive scan of the tile counts of the depth-sorted visible
-// slots (persistent partitions, decoupled look-back)
+// slots, reduce then scan (no waits between blocks): block b first totals
+// partition b's DUP_TILE tile counts, then, in a second launch, sums the
+// totals of the partitions in front of it (a few thousand words from L2)
+// and scans its own.  Blocks past the visible slots (the grid is sized for
+// every slot) return at once.
 // ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(DUP_THREADS) pair_totals_kernel(const uint32_t* __restrict__ sorted_slots,
+                                                                 const uint32_t* __restrict__ ntiles,
+                                                                 const uint32_t* __restrict__ scratch,
+                                                                 uint32_t* __restrict__ part_total) {
+    __shared__ uint32_t s_tmp[8];
+    const uint32_t nvis = scratch[SCR_NVIS];
+    const uint32_t base = blockIdx.x * DUP_TILE + threadIdx.x * DUP_ITEMS;
+    if (blockIdx.x * DUP_TILE >= nvis) return;
+    uint32_t local = 0;
+#pragma unroll
+    for (int i = 0; i < DUP_ITEMS; ++i)
+        if (base + i < nvis) local += ntiles[sorted_slots[base + i]];
+    uint32_t agg;
+    block_excl_scan_256(local, s_tmp, &agg);
+    if (threadIdx.x == 0) part_total[blockIdx.x] = agg;
+}
+
 __global__ void __launch_bounds__(DUP_THREADS) pair_offsets_kernel(
     const uint32_t* __restrict__ sorted_slots, const uint32_t* __restrict__ ntiles, uint32_t* __restrict__ offsets,
-    uint32_t* __restrict__ chunk_start, uint32_t cap, uint32_t* scratch, unsigned long long* lookback,
-    const uint32_t* state, uint32_t epoch_offset, uint32_t* err) {
+    uint32_t* __restrict__ chunk_start, uint32_t cap, uint32_t* scratch, const uint32_t* __restrict__ part_total,
+    uint32_t* err) {
     __shared__ uint32_t s_tmp[8];
-    __shared__ uint32_t s_pid;
-    __shared__ uint32_t s_excl;
     const int tid = threadIdx.x;
     const uint32_t nvis = scratch[SCR_NVIS];
-    const uint32_t nparts = (nvis + DUP_TILE - 1) / DUP_TILE;
-    const uint32_t epoch = state[ST_EPOCH] + epoch_offset;
-    uint32_t* counter = scratch + SCR_CNT_DUP;
-    for (;;) {
-        if (tid == 0) s_pid = atomicAdd(counter, 1u);
-        __syncthreads();
-        const uint32_t pid = s_pid;
-        if (pid >= nparts) break;
-        uint32_t cnt[DUP_ITEMS];
-        uint32_t local = 0;
-        const uint32_t base = pid * DUP_TILE + tid * DUP_ITEMS;
+    const uint32_t pid = blockIdx.x, nparts = (nvis + DUP_TILE - 1) / DUP_TILE;
+    if (pid >= nparts) return;
+    uint32_t excl_part = 0;  // the partitions in front of this one
+    for (uint32_t j = tid; j < pid; j += DUP_THREADS) excl_part += part_total[j];
+    uint32_t excl;
+    block_excl_scan_256(excl_part, s_tmp, &excl);
+    uint32_t cnt[DUP_ITEMS];
+    uint32_t local = 0;
+    const uint32_t base = pid * DUP_TILE + tid * DUP_ITEMS;
 #pragma unroll
-        for (int i = 0; i < DUP_ITEMS; ++i) {
-            const uint32_t pos = base + i;
-            cnt[i] = pos < nvis ? ntiles[sorted_slots[pos]] : 0u;
-            local += cnt[i];
-        }
-        uint32_t agg;
-        const uint32_t pre = block_excl_scan_256(local, s_tmp, &agg);
-        if (tid == 0) {
-            st_volatile64(lookback + pid, lb_make(epoch, pid == 0 ? LB_INC : LB_AGG, agg));
-            uint32_t excl = 0;
-            if (pid > 0) {
-                excl = lookback_walk(lookback, 1, 0, pid, epoch, err);
-                st_volatile64(lookback + pid, lb_make(epoch, LB_INC, excl + agg));
-            }
-            s_excl = excl;
-            if (pid == nparts - 1) {
-                scratch[SCR_PAIRS] = excl + agg;
-                offsets[nvis] = excl + agg;
-                if (excl + agg > cap) atomicOr(err, ERR_OVERFLOW);
-            }
-        }
-        __syncthreads();
-        uint32_t off = s_excl + pre;
+    for (int i = 0; i < DUP_ITEMS; ++i) {
+        const uint32_t pos = base + i;
+        cnt[i] = pos < nvis ? ntiles[sorted_slots[pos]] : 0u;
+        local += cnt[i];
+    }
+    uint32_t agg;
+    const uint32_t pre = block_excl_scan_256(local, s_tmp, &agg);
+    if (tid == 0 && pid == nparts - 1) {
+        scratch[SCR_PAIRS] = excl + agg;
+        offsets[nvis] = excl + agg;
+        if (excl + agg > cap) atomicOr(err, ERR_OVERFLOW);
+    }
+    uint32_t off = excl + pre;
 #pragma unroll
-        for (int i = 0; i < DUP_ITEMS; ++i) {
-            if (base + i < nvis) {
-                offsets[base + i] = off;
-                mark_chunks(chunk_start, base + i, off, cnt[i], cap);
-            }
-            off += cnt[i];
+    for (int i = 0; i < DUP_ITEMS; ++i) {
+        if (base + i < nvis) {
+            offsets[base + i] = off;
+            mark_chunks(chunk_start, base + i, off, cnt[i], cap);
         }
-        __syncthreads();
+        off += cnt[i];
     }
 }
 
@@ -263,7 +270,7 @@ __global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
     const uint32_t* __restrict__ sorted_slots, const uint32_t* __restrict__ offsets,
     const uint32_t* __restrict__ chunk_start, const uint2* __restrict__ rect, int64_t N,
     const __grid_constant__ Views V, uint32_t* __restrict__ pkeys, uint32_t* __restrict__ pvals, uint32_t cap,
-    uint32_t* scratch, int tile_passes, int tiles_in_smem) {
+    uint32_t* scratch, int tile_passes, int tiles_in_smem, uint2* __restrict__ ranges_zero) {
     __shared__ uint32_t s_hist[3 * 256];
     __shared__ uint32_t s_own[EMIT_SPAN];
     __shared__ uint32_t s_slot[EMIT_SPAN + 1], s_first[EMIT_SPAN + 1];
@@ -273,6 +280,11 @@ __global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
     if (tiles_in_smem)
         for (int i = threadIdx.x; i < V.total_tiles; i += blockDim.x) s_tiles[i] = 0;
     uint32_t* tile_counts = scratch + SCR_TILE_COUNTS;
+    // global-sort form (ranges_zero): no per-tile counts here -- the ranges
+    // come from the sorted keys later -- but their array starts at zero
+    if (ranges_zero)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V.total_tiles; i += gridDim.x * blockDim.x)
+            ranges_zero[i] = make_uint2(0u, 0u);
     const uint32_t nvis = scratch[SCR_NVIS];
     const uint32_t P = min(scratch[SCR_PAIRS], cap);
     const uint32_t stride = gridDim.x * EMIT_SPAN;
@@ -324,21 +336,28 @@ __global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
             const uint32_t active = __ballot_sync(0xffffffffu, live);
             if (!live) continue;
             const uint32_t own = s_own[r * EMIT_CHUNK + threadIdx.x];
+            if (j0 + own >= nvis) continue;  // (only offsets left wrong by a timed-out wait get here)
             const uint32_t s = s_slot[own];
             const uint32_t local = e - s_first[own];
             const uint2 rc = __ldg(rect + s);
-            const uint32_t x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff;
+            const uint32_t x0 = rc.x & 0xffff, y0 = rc.x >> 16, x1 = rc.y & 0xffff, y1 = rc.y >> 16;
             const uint32_t w = x1 - x0;
+            // a pair past its slot's rect only comes of offsets left wrong by
+            // a timed-out wait (ERR_WAIT is set): skipped, never an index
+            // outside the tiles
+            if (w == 0 || local >= w * (y1 - y0)) continue;
             const uint32_t ry = local / w, rx = local - ry * w;
             const int v = slot_view(s, (uint32_t)N, V.n);
             const uint32_t key = (uint32_t)(V.v[v].tile_base + (int)(y0 + ry) * V.v[v].tiles_x + (int)(x0 + rx));
             pkeys[e] = key;
             pvals[e] = s;
             for (int p = 0; p < tile_passes; ++p) hist_add_warp(s_hist + p * 256, (key >> (8 * p)) & 255u, active);
-            const uint32_t peers = __match_any_sync(active, key);
-            if ((uint32_t)lane == (uint32_t)(__ffs(peers) - 1)) {
-                if (tiles_in_smem) atomicAdd(s_tiles + key, (uint32_t)__popc(peers));
-                else atomicAdd(tile_counts + key, (uint32_t)__popc(peers));
+            if (!ranges_zero) {
+                const uint32_t peers = __match_any_sync(active, key);
+                if ((uint32_t)lane == (uint32_t)(__ffs(peers) - 1)) {
+                    if (tiles_in_smem) atomicAdd(s_tiles + key, (uint32_t)__popc(peers));
+                    else atomicAdd(tile_counts + key, (uint32_t)__popc(peers));
+                }
             }
         }
         __syncthreads();  // s_own, s_slot, s_first are read before the next span reuses them
@@ -358,23 +377,22 @@ __global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
 cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, uint32_t* chunk_start,
                              bool offsets_ready, const uint32_t* ntiles, const uint2* rect,
                              int64_t N, const Views& V, uint32_t* pkeys, uint32_t* pvals, uint32_t cap,
-                             uint32_t* scratch, int tile_passes, unsigned long long* lookback, const uint32_t* state,
-                             uint32_t epoch_offset, uint32_t* err, int64_t max_slots, cudaStream_t st) {
-    static int max_grid = 0, sms = 148;
-    if (!max_grid) {
-        int dev = 0, per = 1;
+                             uint32_t* scratch, int tile_passes, uint32_t* part_total, uint32_t* err,
+                             int64_t max_slots, uint2* ranges, cudaStream_t st) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pair_offsets_kernel, DUP_THREADS, 0);
-        max_grid = sms * (per > 0 ? per : 1);
+        if (sms < 1) sms = 148;
     }
     cudaError_t e;
     if (!offsets_ready) {
-        int64_t parts = ceil_div(max_slots > 0 ? max_slots : 1, DUP_TILE);
-        int grid = (int)(parts < max_grid ? parts : max_grid);
-        count_launches(1);
-        pair_offsets_kernel<<<grid, DUP_THREADS, 0, st>>>(sorted_slots, ntiles, offsets, chunk_start, cap, scratch,
-                                                          lookback, state, epoch_offset, err);
+        const int64_t parts = ceil_div(max_slots > 0 ? max_slots : 1, DUP_TILE);
+        count_launches(2);
+        pair_totals_kernel<<<(unsigned)parts, DUP_THREADS, 0, st>>>(sorted_slots, ntiles, scratch, part_total);
+        pair_offsets_kernel<<<(unsigned)parts, DUP_THREADS, 0, st>>>(sorted_slots, ntiles, offsets, chunk_start, cap,
+                                                                    scratch, part_total, err);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -385,14 +403,67 @@ cudaError_t launch_duplicate(const uint32_t* sorted_slots, uint32_t* offsets, ui
     // zeroing and flush only when a block emits at least as many pairs as
     // there are tiles; otherwise one global atomic per run of equal tiles
     const int64_t spans_per_block = ceil_div(ceil_div((int64_t)cap, EMIT_SPAN), eg);
-    const int tiles_in_smem = V.total_tiles <= EMIT_SMEM_TILES &&
-                              (int64_t)V.total_tiles <= spans_per_block * EMIT_SPAN ? 1 : 0;
+    const int tiles_in_smem = !offsets_ready ? 0 : (V.total_tiles <= EMIT_SMEM_TILES &&
+                              (int64_t)V.total_tiles <= spans_per_block * EMIT_SPAN ? 1 : 0);
     const size_t smem = tiles_in_smem ? (size_t)V.total_tiles * 4 : 0;
     e = allow_dynamic_smem((const void*)emit_pairs_kernel, smem);
     if (e != cudaSuccess) return e;
     count_launches(1);
     emit_pairs_kernel<<<(unsigned)eg, EMIT_CHUNK, smem, st>>>(sorted_slots, offsets, chunk_start, rect, N, V, pkeys,
-                                                               pvals, cap, scratch, tile_passes, tiles_in_smem);
+                                                               pvals, cap, scratch, tile_passes, tiles_in_smem,
+                                                               offsets_ready ? nullptr : ranges);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// tile ranges of the global-sort form, from the tile-sorted keys: a pair that
+// starts a run of equal keys writes the run's start, the pair that ends it
+// the end (empty tiles keep the zero the emission wrote)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) tile_bounds_kernel(const uint32_t* __restrict__ keys,
+                                                         const uint32_t* __restrict__ n_dev, uint32_t cap,
+                                                         uint2* __restrict__ ranges) {
+    const uint32_t P = min(*n_dev, cap);
+    uint32_t* r = reinterpret_cast<uint32_t*>(ranges);
+    // four keys per thread (one 16-byte load; the key arrays are 256-byte
+    // aligned allocations) and their two neighbours
+    const uint32_t q4 = (P + 3) / 4;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < q4; q += gridDim.x * blockDim.x) {
+        const uint32_t e0 = 4 * q;
+        uint32_t k[6];
+        if (e0 + 4 <= P) {
+            const uint4 v = reinterpret_cast<const uint4*>(keys)[q];
+            k[1] = v.x; k[2] = v.y; k[3] = v.z; k[4] = v.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) k[1 + i] = e0 + i < P ? keys[e0 + i] : 0xffffffffu;
+        }
+        k[0] = e0 > 0 ? keys[e0 - 1] : 0xffffffffu;
+        k[5] = e0 + 4 < P ? keys[e0 + 4] : 0xffffffffu;
+#pragma unroll
+        for (int i = 1; i <= 4; ++i) {
+            const uint32_t e = e0 + (uint32_t)(i - 1);
+            if (e >= P) break;
+            if (e == 0 || k[i - 1] != k[i]) r[2 * k[i]] = e;
+            if (e + 1 == P || k[i + 1] != k[i]) r[2 * k[i] + 1] = e + 1;
+        }
+    }
+}
+
+cudaError_t launch_tile_bounds(const uint32_t* keys, const uint32_t* n_dev, uint32_t cap, uint2* ranges,
+                               cudaStream_t st) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 148;
+    }
+    int64_t g = ceil_div(ceil_div((int64_t)cap, 4), 256);
+    if (g > (int64_t)sms * 16) g = (int64_t)sms * 16;
+    if (g < 1) g = 1;
+    count_launches(1);
+    tile_bounds_kernel<<<(unsigned)g, 256, 0, st>>>(keys, n_dev, cap, ranges);
     return cudaGetLastError();
 }
 
@@ -419,15 +490,24 @@ __global__ void __launch_bounds__(1024) ranges_kernel(uint32_t* __restrict__ cnt
                                                       int staged, uint32_t* __restrict__ scratch, int clear,
                                                       const uint32_t* __restrict__ lf_blk, int lf_grid,
                                                       uint32_t* __restrict__ lf_counts,
-                                                      uint32_t* __restrict__ long_tiles) {
+                                                      uint32_t* __restrict__ long_tiles, int from_ranges) {
     __shared__ uint32_t s_w[32];
     __shared__ uint32_t s_carry, s_max, s_nlong;
     __shared__ uint32_t s_lf[2];
     __shared__ uint32_t s_bin[ORDER_BUCKETS];
     extern __shared__ uint32_t s_cnt[];  // the counts, when they fit: one coalesced load for all three uses
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (staged)
+    if (from_ranges) {  // global-sort form: the ranges are final, the counts are their lengths
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint2 r = ranges[i];
+            const uint32_t c = r.y > r.x ? r.y - r.x : 0u;
+            if (staged) s_cnt[i] = c;
+            else cnt_g[i] = c;
+        }
+        __syncthreads();
+    } else if (staged) {
         for (int i = threadIdx.x; i < n; i += blockDim.x) s_cnt[i] = cnt_g[i];
+    }
     const uint32_t* cnt = staged ? s_cnt : cnt_g;
     if (threadIdx.x == 0) {
         s_carry = 0;
@@ -477,7 +557,7 @@ __global__ void __launch_bounds__(1024) ranges_kernel(uint32_t* __restrict__ cnt
         }
         __syncthreads();
         const uint32_t start = s_carry + (warp ? s_w[warp - 1] : 0u) + inc - x;
-        if (i < n) ranges[i] = make_uint2(start, start + x);
+        if (i < n && !from_ranges) ranges[i] = make_uint2(start, start + x);
         if (long_tiles && i < n && x > (uint32_t)VG_TILE_SORT_CAP) long_tiles[atomicAdd(&s_nlong, 1u)] = (uint32_t)i;
         __syncthreads();
         if (threadIdx.x == 0) s_carry += s_w[31];
@@ -528,14 +608,14 @@ __global__ void __launch_bounds__(1024) ranges_kernel(uint32_t* __restrict__ cnt
 
 cudaError_t launch_ranges(uint32_t* scratch, int n_tiles, uint2* ranges, uint32_t* order, int clear,
                           const uint32_t* lf_blk, int lf_grid, uint32_t* lf_counts, uint32_t* long_tiles,
-                          cudaStream_t st) {
+                          int from_ranges, cudaStream_t st) {
     count_launches(1);
     const int staged = n_tiles <= RANGES_SMEM_TILES ? 1 : 0;
     const size_t smem = staged ? (size_t)n_tiles * 4 : 0;
     cudaError_t e = allow_dynamic_smem((const void*)ranges_kernel, smem);
     if (e != cudaSuccess) return e;
     ranges_kernel<<<1, 1024, smem, st>>>(scratch + SCR_TILE_COUNTS, n_tiles, ranges, order, staged, scratch, clear,
-                                         lf_blk, lf_grid, lf_counts, long_tiles);
+                                         lf_blk, lf_grid, lf_counts, long_tiles, from_ranges);
     return cudaGetLastError();
 }
 

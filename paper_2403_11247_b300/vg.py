@@ -94,6 +94,7 @@ def lib():
             "vg_check": [P, P],
             "vg_ctx_stats": [P, P, P],
             "vg_ctx_reset_counters": [P, P],
+            "vg_ctx_set_spin_limit": [P, C.c_uint32],
             "vg_ctx_buffer": [P, I32, P, P],
             "vg_ctx_profile": [P, I32],
             "vg_ctx_profile_read": [P, P, P, P],
@@ -633,6 +634,15 @@ _BUF_DTYPE = dict(xy=("float32", 4), conic=("float32", 4), rgbd=("float32", 4), 
                   t_final=("float32", 1), n_contrib=("uint32", 1), g2d=("float32", 12), n_eval=("uint32", 1))
 
 
+SPIN_LIMIT_DEFAULT = 0xFFFFFFFF
+
+
+def vg_ctx_set_spin_limit(ctx: CtxHandle, polls: int = SPIN_LIMIT_DEFAULT):
+    """Unsuccessful polls before a bounded device wait of this ctx gives up
+    (then vg_check returns VG_ERR_TIMEOUT); the default restores 2^21."""
+    _check(lib().vg_ctx_set_spin_limit(ctx.handle, int(polls) & 0xFFFFFFFF), "vg_ctx_set_spin_limit")
+
+
 def vg_ctx_buffer(ctx: CtxHandle, which: str, count: int, stream=None) -> np.ndarray:
     """Copy ``count`` records of an intermediate workspace array to the host
     (synchronises the stream)."""
@@ -737,7 +747,7 @@ def exported_symbols():
             "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
             "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune", "vg_ssim_loss", "vg_icp_associate",
             "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune", "vg_host_alloc", "vg_host_free", "vg_memcpy_async", "vg_host_stage",
-            "vg_loss_l1_masked", "vg_sample_rays", "vg_render_fwd_l1"]
+            "vg_loss_l1_masked", "vg_sample_rays", "vg_render_fwd_l1", "vg_ctx_set_spin_limit"]
 
 
 PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),

@@ -34,8 +34,12 @@ def test_matches_the_ctx_entry_point_on_two_calls_in_a_row():
     rng = np.random.default_rng(2026)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     ctx = V.vg_ctx_create(0)
-    # two different inputs, so the second call must clear what the first left
-    for call, (nv, n, gate) in enumerate([(3, 5003, -1.0), (2, 7777, 0.5)]):
+    # different inputs in a row, so each call must clear what the one before
+    # left; 640 x 480 planes (a multiple of four pixels, 16-byte aligned)
+    # compare against vg_loss_l1's single cooperative launch, the others
+    # against its counting-then-loss form
+    for call, (nv, n, gate) in enumerate([(3, 5003, -1.0), (2, 7777, 0.5), (2, 640 * 480, -1.0),
+                                          (2, 640 * 480, 0.5)]):
         C_ = rng.uniform(size=nv * 3 * n).astype(np.float32)
         Ct = rng.uniform(size=nv * 3 * n).astype(np.float32)
         D_ = rng.uniform(0, 3, size=nv * n).astype(np.float32)
