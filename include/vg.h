@@ -460,6 +460,11 @@ vg_status vg_pose_step(int32_t n_views, float* pose, const float* dxi, float* m,
 /* Number of CUDA kernels libvg has enqueued in this process (host count). */
 int64_t vg_launch_count(void);
 
+/* Number of workspace allocations (a ctx buffer created or grown) libvg has
+ * made in this process: a serving loop reads it to see whether a launch had
+ * to grow a workspace. */
+int64_t vg_workspace_allocs(void);
+
 /* vg_loss_l1 over the sampled rays only: pixels with pixel_mask 0 (same
  * layout as vg_render_params.pixel_mask) get zero gradient, and the means
  * run over the sampled pixels (colour) and the sampled pixels with Dt > 0

@@ -29,6 +29,7 @@ thread_local std::string g_err;
 
 namespace vgk {
 static std::atomic<long long> g_launches{0};
+static std::atomic<long long> g_ws_allocs{0};  // workspace allocations (DevBuf growth)
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 cudaError_t allow_dynamic_smem(const void* kernel, size_t dynamic_bytes) {
     if (dynamic_bytes == 0) return cudaSuccess;
@@ -67,16 +68,25 @@ bool capturing(cudaStream_t st) {
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    bool pooled = false;  // from the stream-ordered pool (cudaFree of it does not wait for its users)
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
     ~DevBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (pooled) cudaDeviceSynchronize();
+            cudaFree(p);
+        }
         p = nullptr;
         bytes = 0;
+        pooled = false;
     }
-    // grow to at least b bytes (contents are not kept)
+    // grow to at least b bytes (contents are not kept).  Stream-ordered: the
+    // old buffer is freed after the work already queued on `st` (the ctx's
+    // stream, the only one that uses it) and the new one comes from the
+    // device's memory pool, so a growth never waits for the work of other
+    // streams the way cudaFree does.
     vg_status ensure(size_t b, cudaStream_t st, const char* what) {
         if (b == 0) b = 16;
         if (b <= bytes) return VG_OK;
@@ -84,8 +94,27 @@ struct DevBuf {
             return fail(VG_ERR_CAPACITY, std::string("workspace buffer '") + what +
                                              "' must grow, which cannot happen during stream capture; run once "
                                              "outside capture first");
-        release();
-        cudaError_t e = cudaMalloc(&p, b);
+        // (a call on the legacy stream, as vg_ctx_reserve and vg_ctx_create
+        // make, keeps the synchronous free and allocation).  A buffer that
+        // has to grow again grows by at least a quarter, so that a workload
+        // whose sizes creep up (a server's batches) rarely reallocates.
+        if (p) {
+            b = std::max(b, bytes + bytes / 4);
+            if (pooled && st) {
+                if (cudaFreeAsync(p, st) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaDeviceSynchronize();
+                    cudaFree(p);
+                }
+                p = nullptr;
+                bytes = 0;
+                pooled = false;
+            } else {
+                release();
+            }
+        }
+        pooled = st != nullptr;
+        cudaError_t e = pooled ? cudaMallocAsync(&p, b, st) : cudaMalloc(&p, b);
         if (e != cudaSuccess) {
             p = nullptr;
             cudaGetLastError();
@@ -93,6 +122,7 @@ struct DevBuf {
                         std::string("cudaMalloc(") + what + "): " + cudaGetErrorString(e));
         }
         bytes = b;
+        g_ws_allocs.fetch_add(1, std::memory_order_relaxed);
         return VG_OK;
     }
     template <class T>
@@ -208,6 +238,8 @@ extern "C" {
 const char* vg_last_error(void) { return g_err.c_str(); }
 
 int64_t vg_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int64_t vg_workspace_allocs(void) { return (int64_t)g_ws_allocs.load(); }
 
 vg_render_params vg_default_params(void) {
     vg_render_params p;

@@ -48,6 +48,9 @@ class Request:
     target: Optional[tuple] = None   # (Ct [3HW], Dt [HW]) pinned host float32, for "track"
     done: float = -1.0
     result: object = None
+    launched: float = -1.0       # when its launch sequence was enqueued
+    gpu_ms: float = -1.0         # device time of that launch sequence
+    launch_host_ms: float = -1.0  # host time spent enqueueing it
 
 
 def poisson_trace(rng: np.random.Generator, rate: float, duration: float, scenes: Sequence[int],
@@ -163,6 +166,7 @@ def admit(in_flight: int, need: int, budget: int) -> bool:
 def reset(trace: Sequence[Request]):
     for r in trace:
         r.done, r.result = -1.0, None
+        r.launched = r.gpu_ms = r.launch_host_ms = -1.0
 
 
 class _Lane:
@@ -172,6 +176,11 @@ class _Lane:
         self.stream = torch.cuda.Stream(device=device)
         self.ctx = V.vg_ctx_create(pair_reserve)
         self.event = None
+        self.t_start = None        # timing events around the launch sequence
+        self.t_launch = 0.0        # host time of the enqueue (s since the trace start)
+        self.host_ms = 0.0
+        self.pinned = None         # page-locked result buffer, reused by every launch of the lane
+        self.grew = 0              # buffers the current launch had to allocate
         self.batch: List[Request] = []
         self.host = None
         self.bytes = 0
@@ -192,8 +201,21 @@ class Server:
         free, _ = torch.cuda.mem_get_info()
         self.budget = int(free * mem_fraction)
         self.in_flight = 0
+        self._t0 = time.perf_counter()
+        self.growth_ms: List[float] = []
         self.launches = 0
         self.retries = 0
+
+    @staticmethod
+    def _host(lane: _Lane, n: int) -> torch.Tensor:
+        """The lane's page-locked result buffer, at least n floats.  It grows
+        by a quarter beyond the need, rarely: allocating page-locked memory
+        is slow and can wait for the device, so it must not happen per
+        launch."""
+        if lane.pinned is None or lane.pinned.numel() < n:
+            lane.pinned = torch.empty(n + n // 4 + 1024, dtype=torch.float32, pin_memory=True)
+            lane.grew += 1
+        return lane.pinned[:n]
 
     def estimate(self, batch: Sequence[Request]) -> int:
         """Device bytes one launch sequence of `batch` uses."""
@@ -202,16 +224,21 @@ class Server:
         return pix * (BYTES_PER_PIXEL + PAIRS_PER_PIXEL * BYTES_PER_PAIR) + n * len(batch) * BYTES_PER_SLOT
 
     def _launch(self, lane: _Lane, batch: List[Request], retry: bool = False):
+        h0 = time.perf_counter()
+        a0 = V.vg_workspace_allocs()
+        lane.grew = 0
         sh = self.scenes[batch[0].scene]
         cams = [r.cam for r in batch]
         f32 = dict(dtype=torch.float32, device=self.device)
         with torch.cuda.stream(lane.stream):
+            t_start = torch.cuda.Event(enable_timing=True)
+            t_start.record(lane.stream)
             P = sum(c.width * c.height for c in cams)
             out = torch.empty(5 * P, **f32)
             C_, D, S = out[:3 * P], out[3 * P:4 * P], out[4 * P:]
             V.vg_render_fwd(sh, cams, self.params, lane.ctx, C_, D, S, stream=lane.stream)
             if batch[0].kind == "render":
-                host = torch.empty(5 * P, dtype=torch.float32, pin_memory=True)
+                host = self._host(lane, 5 * P)
                 host.copy_(out, non_blocking=True)
                 lane.keep = [out]
             else:
@@ -236,12 +263,18 @@ class Server:
                                  dC=dC[c3], dD=dD[c1], loss=loss[i:i + 1], stream=lane.stream)
                 V.vg_render_bwd(sh, cams, self.params, lane.ctx, dC, dD, None, grads={}, stream=lane.stream)
                 V.vg_pose_grad(lane.ctx, B, dxi=dxi, stream=lane.stream)
-                host = torch.empty(7 * B, dtype=torch.float32, pin_memory=True)
+                host = self._host(lane, 7 * B)
                 host.copy_(res, non_blocking=True)
                 lane.keep = [out, tgt, grad, res]
-            ev = torch.cuda.Event()
+            ev = torch.cuda.Event(enable_timing=True)
             ev.record(lane.stream)
-        lane.event, lane.batch, lane.host = ev, batch, host
+        lane.event, lane.batch, lane.host, lane.t_start = ev, batch, host, t_start
+        h1 = time.perf_counter()
+        lane.t_launch = h0 - self._t0
+        lane.host_ms = (h1 - h0) * 1e3
+        lane.grew += V.vg_workspace_allocs() - a0
+        if lane.grew:
+            self.growth_ms.append(lane.host_ms)
         lane.bytes = self.estimate(batch)
         self.in_flight += lane.bytes
         if not retry:      # a redone launch is counted in retries only
@@ -263,22 +296,25 @@ class Server:
         if st != V.VG_OK:
             raise V.VgError(st, "serve", V.lib().vg_last_error().decode(errors="replace"))
         now = time.perf_counter() - t0
+        gpu_ms = lane.t_start.elapsed_time(lane.event)
         host = lane.host.numpy()
         P = sum(q.cam.width * q.cam.height for q in batch)
         B = len(batch)
         off = 0
         for i, r in enumerate(batch):
             r.done = now
+            r.launched, r.gpu_ms, r.launch_host_ms = lane.t_launch, gpu_ms, lane.host_ms
             if not keep_results:
                 r.result = True
             elif r.kind == "render":
                 n = r.cam.width * r.cam.height
-                r.result = (host[3 * off:3 * (off + n)], host[3 * P + off:3 * P + off + n],
-                            host[4 * P + off:4 * P + off + n])
+                # (copies: the lane's buffer is reused by its next launch)
+                r.result = (host[3 * off:3 * (off + n)].copy(), host[3 * P + off:3 * P + off + n].copy(),
+                            host[4 * P + off:4 * P + off + n].copy())
                 off += n
             else:
                 r.result = (host[6 * i:6 * i + 6].copy(), float(host[6 * B + i]))
-        lane.event, lane.batch, lane.host, lane.keep = None, [], None, []
+        lane.event, lane.batch, lane.host, lane.keep, lane.t_start = None, [], None, [], None
         return batch
 
     def serve(self, trace: List[Request], realtime: bool = True, keep_results: bool = True) -> Dict:
@@ -290,7 +326,9 @@ class Server:
         waiting = Queues()
         n_done = 0
         self.launches = self.retries = 0
-        t0 = time.perf_counter()
+        self.growth_ms = []
+        allocs0 = V.vg_workspace_allocs()
+        t0 = self._t0 = time.perf_counter()
         while n_done < len(trace):
             now = time.perf_counter() - t0
             while pending and (pending[0].arrival <= now or not realtime):
@@ -310,7 +348,13 @@ class Server:
                     progressed = True
             if not progressed:
                 time.sleep(2e-5)
-        return summarize(trace, time.perf_counter() - t0, self.launches, self.retries)
+        out = summarize(trace, time.perf_counter() - t0, self.launches, self.retries)
+        out["workspace_allocs"] = V.vg_workspace_allocs() - allocs0
+        # launches that had to allocate (workspace or page-locked buffer) and
+        # their enqueue times
+        out["growth_launches"] = len(self.growth_ms)
+        out["growth_enqueue_ms_max"] = max(self.growth_ms) if self.growth_ms else 0.0
+        return out
 
 
 def summarize(trace: List[Request], wall: float, launches: int, retries: int = 0) -> Dict:
@@ -318,6 +362,23 @@ def summarize(trace: List[Request], wall: float, launches: int, retries: int = 0
     out = {"requests": len(trace), "wall_s": wall, "throughput_rps": len(trace) / wall, "launches": launches,
            "retries": retries, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
            "mean_ms": float(lat.mean())}
+    # where the slowest 1% spent their time: waiting for a lane (arrival to
+    # enqueue), enqueueing (host), on the device, and from the device's end
+    # to the result being noticed in host memory
+    if all(r.launched >= 0 for r in trace):
+        tail = [r for r, x in zip(trace, lat) if x >= out["p99_ms"]]
+        q = np.array([(r.launched - r.arrival) * 1e3 for r in tail])
+        hm = np.array([r.launch_host_ms for r in tail])
+        g = np.array([r.gpu_ms for r in tail])
+        tot = np.array([(r.done - r.arrival) * 1e3 for r in tail])
+        out["p99_breakdown_ms"] = {"n": len(tail), "queued": float(q.mean()), "enqueue_host": float(hm.mean()),
+                                   "gpu": float(g.mean()), "after_gpu": float((tot - q - hm - g).mean())}
+        hosts = np.array([r.launch_host_ms for r in trace])
+        out["enqueue_host_ms"] = {"p50": float(np.percentile(hosts, 50)), "p99": float(np.percentile(hosts, 99)),
+                                  "max": float(hosts.max())}
+        gall = np.array([r.gpu_ms for r in trace])
+        out["gpu_ms"] = {"p50": float(np.percentile(gall, 50)), "p99": float(np.percentile(gall, 99)),
+                         "max": float(gall.max())}
     for kind in ("render", "track"):
         lk = np.array([r.done - r.arrival for r in trace if r.kind == kind]) * 1e3
         if lk.size:

@@ -133,6 +133,8 @@ def lib():
         L.vg_default_params.argtypes = []
         L.vg_launch_count.restype = C.c_int64
         L.vg_launch_count.argtypes = []
+        L.vg_workspace_allocs.restype = C.c_int64
+        L.vg_workspace_allocs.argtypes = []
         L.vg_scene_size.restype = C.c_int64
         L.vg_scene_size.argtypes = [P]
         _lib = L
@@ -719,6 +721,10 @@ def vg_launch_count() -> int:
     return int(lib().vg_launch_count())
 
 
+def vg_workspace_allocs() -> int:
+    return int(lib().vg_workspace_allocs())
+
+
 VG_NOALLOC_MAX_VIEWS = 256
 
 
@@ -747,7 +753,8 @@ def exported_symbols():
             "vg_render_bwd", "vg_pose_grad", "vg_loss_l1", "vg_loss_l1_noalloc", "vg_last_error", "vg_default_params",
             "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune", "vg_ssim_loss", "vg_icp_associate",
             "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune", "vg_host_alloc", "vg_host_free", "vg_memcpy_async", "vg_host_stage",
-            "vg_loss_l1_masked", "vg_sample_rays", "vg_render_fwd_l1", "vg_ctx_set_spin_limit"]
+            "vg_loss_l1_masked", "vg_sample_rays", "vg_render_fwd_l1", "vg_ctx_set_spin_limit",
+            "vg_workspace_allocs"]
 
 
 PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),
