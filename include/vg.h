@@ -177,7 +177,19 @@ typedef struct {
  * grad_accumulate: vg_render_bwd ADDS to the scene-gradient arrays instead
  *   of zeroing them first; the caller keeps them zero between steps (e.g.
  *   vg_adam_step with zero_grad set clears each gradient after using it).
- *   0 (default) = the backward zeroes them. */
+ *   0 (default) = the backward zeroes them.
+ * list_split: compositing of deep tile lists across CTAs.  With S > 1 each
+ *   tile's list is cut into S consecutive segments, each composited by its
+ *   own CTA (forward: the segments' transmittance products, then each
+ *   segment walked from the transmittance in front of it, then the sums
+ *   combined in order; backward: each segment walked back to front from its
+ *   own final transmittance) -- for images with too few tiles to fill the
+ *   GPU.  0 (default) = automatic: S = min(16, ceil(2 x SMs / tiles)) when
+ *   the views have fewer tiles than the GPU has SMs, else 1; 1 = never;
+ *   2..32 = S.  The images equal the unsplit ones up to FP32 rounding of
+ *   the transmittance products (the same Gaussians are blended except where
+ *   a product lands within rounding of t_min); the backward must use the
+ *   forward's split, which the ctx keeps. */
 typedef struct {
     int32_t tile;
     int32_t batch;
@@ -192,6 +204,7 @@ typedef struct {
     const uint8_t* pixel_mask;
     int32_t grad_accumulate;
     int32_t persist_ctas;
+    int32_t list_split;
 } vg_render_params;
 
 /* Gradient outputs of vg_render_bwd (DEVICE pointers, caller-allocated; each

@@ -219,6 +219,8 @@ struct vg_ctx {
     // passed VG_TILE_SORT_CAP; for such lists the global radix passes beat
     // the long-list pass's comparison sort)
     int auto_stage = 0;
+    int split_S = 1;         // segments per tile list of the last forward (1 = unsplit)
+    DevBuf seg_f, seg_u;     // the split passes' per-segment state, kept for the backward
     uint32_t spin_limit = SPIN_LIMIT_DEFAULT;  // unsuccessful polls before a bounded device wait gives up
     bool g2d_clean = false;
     bool fwd_zeroed = false;  // the last forward zeroed the visible slots' gradient rows and the pose sums
@@ -240,6 +242,22 @@ const char* vg_last_error(void) { return g_err.c_str(); }
 int64_t vg_launch_count(void) { return (int64_t)g_launches.load(); }
 
 int64_t vg_workspace_allocs(void) { return (int64_t)g_ws_allocs.load(); }
+
+// segments per tile list: the caller's choice, or (0) automatic -- split when
+// the views have fewer tiles than the GPU has SMs, into enough segments for
+// about two CTAs per SM
+static int split_segments(int32_t want, int total_tiles) {
+    if (want == 1 || total_tiles <= 0) return 1;
+    if (want > 1) return want;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 148;
+    }
+    if (total_tiles >= sms) return 1;
+    return (int)std::min<int64_t>(16, ceil_div((int64_t)2 * sms, total_tiles));
+}
 
 vg_render_params vg_default_params(void) {
     vg_render_params p;
@@ -625,6 +643,8 @@ static vg_status build_views(const vg_camera* cams, int32_t n_views, const vg_re
         return fail(VG_ERR_INVALID_ARG, "params.batch must be 0, 64, 128 or 256");
     if (p->persist_ctas < 0 || p->persist_ctas > 32)
         return fail(VG_ERR_INVALID_ARG, "params.persist_ctas must be in 0..32");
+    if (p->list_split < 0 || p->list_split > SPLIT_MAX)
+        return fail(VG_ERR_INVALID_ARG, "params.list_split must be in 0..32");
     if (!(p->alpha_max > 0.f && p->alpha_max < 1.f) || !(p->alpha_min >= 0.f) || !(p->t_min >= 0.f) ||
         !(p->dilation >= 0.f) || !(p->sigma_cull > 0.f) || !(p->clamp_factor > 0.f))
         return fail(VG_ERR_INVALID_ARG, "render params out of range");
@@ -861,6 +881,21 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
                      return launch_ranges(scr, V.total_tiles, ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
                                           1, cs.lf_blk, lf_grid, scr + SCR_LOSS_VALID, nullptr, 1, st);
                  })());
+    // deep lists on few tiles: each list split over S CTAs
+    const int split = split_segments(params->list_split, V.total_tiles);
+    if (split > 1) {
+        const size_t px = (size_t)V.total_tiles * split * TILE_PIX;
+        VG_TRY(ctx->seg_f.ensure(px * SPLIT_F * 4, st, "split segment sums"));
+        VG_TRY(ctx->seg_u.ensure(px * SPLIT_U * 4, st, "split segment counts"));
+        VG_STAGE(VG_STAGE_BLEND_FWD,
+                 launch_split_fwd(V, cs, split, ctx->ranges.as<uint2>(), ctx->pval[fin].as<uint32_t>(),
+                                  tile_sort ? ctx->dkey[1].as<uint32_t>() : nullptr, err, ctx->xy.as<float4>(),
+                                  ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(), ctx->seg_f.as<float>(),
+                                  ctx->seg_u.as<uint32_t>(), C, D, S, ctx->Tfin.as<float>(),
+                                  ctx->ncontrib.as<uint32_t>(), (unsigned long long*)(state + ST_EVALS),
+                                  (unsigned long long*)(state + ST_BLENDED),
+                                  params->count_evals ? ctx->neval.as<uint32_t>() : nullptr, params->count_evals, st));
+    } else
     VG_STAGE(VG_STAGE_BLEND_FWD,
              launch_blend_fwd(V, cs, params->ppt_fwd, params->persist_ctas, state + ST_WORK_FWD,
                               ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),
@@ -869,6 +904,7 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
                               ctx->Tfin.as<float>(), ctx->ncontrib.as<uint32_t>(),
                               (unsigned long long*)(state + ST_EVALS), (unsigned long long*)(state + ST_BLENDED),
                               params->count_evals ? ctx->neval.as<uint32_t>() : nullptr, params->count_evals, st));
+    ctx->split_S = split;
     ctx->views = V;
     ctx->fwd_N = N;
     ctx->fwd_scene = scene;
@@ -966,6 +1002,15 @@ vg_status vg_render_bwd(vg_scene* scene, const vg_camera* cams, int32_t n_views,
     if (!rows_zero || Z.n > 0)
         VG_STAGE(VG_STAGE_MEMSET, launch_zero_bwd(ctx->vis.as<uint32_t>(), ctx->scratch.as<uint32_t>() + SCR_NVIS,
                                                   rows_zero ? 0u : (uint32_t)slots, ctx->g2d.as<float>(), Z, st));
+    if (ctx->split_S > 1)
+        VG_STAGE(VG_STAGE_BLEND_BWD,
+                 launch_split_bwd(V, cs, ctx->split_S, ctx->ranges.as<uint2>(),
+                                  ctx->pval[ctx->final_pair].as<uint32_t>(), ctx->xy.as<float4>(),
+                                  ctx->conic_o.as<float4>(), ctx->rgbd.as<float4>(), ctx->seg_f.as<float>(),
+                                  ctx->seg_u.as<uint32_t>(), ctx->ncontrib.as<uint32_t>(), dC, dD, dS,
+                                  ctx->g2d.as<float>(), (unsigned long long*)(ctx->state.as<uint32_t>() + ST_BWD),
+                                  params->count_evals, st));
+    else
     VG_STAGE(VG_STAGE_BLEND_BWD,
              launch_blend_bwd(V, cs, params->ppt_bwd, params->persist_ctas, ctx->state.as<uint32_t>() + ST_WORK_BWD,
                               ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(),

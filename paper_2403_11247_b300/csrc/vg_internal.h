@@ -184,6 +184,24 @@ cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, int pers
                              const uint32_t* ncontrib, const float* dC, const float* dD, const float* dS,
                              float* g2d, unsigned long long* bwd_pairs, int count, cudaStream_t st);
 
+// split.cu: deep tile lists cut into S segments, one CTA per (tile,
+// segment); per-segment state in segf [items][SPLIT_F][256] (product of the
+// segment, its five blended sums, its final T) and segu [items][SPLIT_U][256]
+// (last contributor, blended count, stop position, composited flag), items =
+// tiles x S.  dkey non-NULL: sort each tile's list first (per-tile form).
+constexpr int SPLIT_F = 8;
+constexpr int SPLIT_U = 4;
+constexpr int SPLIT_MAX = 32;
+cudaError_t launch_split_fwd(const Views& V, const Consts& cs, int S, const uint2* ranges, uint32_t* pvals,
+                             const uint32_t* dkey, uint32_t* err, const float4* xy, const float4* conic_o,
+                             const float4* rgbd, float* segf, uint32_t* segu, float* C, float* D, float* Sout,
+                             float* Tfin, uint32_t* ncontrib, unsigned long long* evals, unsigned long long* blended,
+                             uint32_t* neval, int count_evals, cudaStream_t st);
+cudaError_t launch_split_bwd(const Views& V, const Consts& cs, int S, const uint2* ranges, const uint32_t* pvals,
+                             const float4* xy, const float4* conic_o, const float4* rgbd, const float* segf,
+                             const uint32_t* segu, const uint32_t* ncontrib, const float* dC, const float* dD,
+                             const float* dS, float* g2d, unsigned long long* bwd_pairs, int count, cudaStream_t st);
+
 // grad.cu
 // where the chain kernel accumulates the scene gradients (device pointers;
 // NULL = not wanted); cb_off/cb_total/cb_in_smem are filled by the launcher

@@ -61,7 +61,7 @@ class vg_render_params(C.Structure):
                 ("jacobian_clamp", C.c_int32), ("count_evals", C.c_int32), ("pose_dev", C.c_void_p),
                 ("ppt_fwd", C.c_int32), ("ppt_bwd", C.c_int32), ("hit_count", C.c_void_p), ("seen", C.c_void_p),
                 ("sort_mode", C.c_int32), ("pixel_mask", C.c_void_p), ("grad_accumulate", C.c_int32),
-                ("persist_ctas", C.c_int32)]
+                ("persist_ctas", C.c_int32), ("list_split", C.c_int32)]
 
 
 class vg_scene_grads(C.Structure):
