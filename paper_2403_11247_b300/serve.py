@@ -196,7 +196,11 @@ class Server:
         self.lanes = [_Lane(self.device, pair_reserve) for _ in range(n_streams)]
         self.max_views = min(max_views, V.VG_MAX_VIEWS)
         self.max_pixels = max_pixels
-        self.params = params if params is not None else V.default_params()
+        # lists composited unsplit: a request's result must not depend on what
+        # it is batched with (a launch with few tiles would otherwise split
+        # its lists across CTAs, equal to the unsplit result up to rounding);
+        # batching is what fills the GPU here
+        self.params = params if params is not None else V.default_params(list_split=1)
         self.w_depth = w_depth
         free, _ = torch.cuda.mem_get_info()
         self.budget = int(free * mem_fraction)
