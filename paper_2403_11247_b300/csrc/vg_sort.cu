@@ -667,12 +667,129 @@ cudaError_t launch_tile_scatter(const uint32_t* keys_in, const uint32_t* vals_in
 
 // ---------------------------------------------------------------------------
 // long tile lists (over VG_TILE_SORT_CAP, the forward compositing kernel's
-// own sort): one CTA per list, keys (FP32 depth bits, slot) packed as one
-// 64-bit integer (depth bits high), so that the lexicographic order is the
-// integer order and every key is distinct; padded to a power of two with the
-// largest value and sorted by a bitonic network in shared memory
+// own sort), one CTA per list.
+// Up to RADIX_LONG_CAP entries: a least-significant-digit radix sort on the
+// FP32 depth bits in shared memory (four stable passes of 8 bits), then the
+// rare runs of equal depth bits put in slot order, which gives the
+// (depth bits, slot) order.  Each warp owns a contiguous stretch of the list
+// and takes it in rounds of 32 entries: an entry's place among the equal
+// digits of its round comes from match_any, its place among earlier rounds
+// from the warp's running count of that digit, its place among earlier
+// warps and smaller digits from a scan of the warps' digit counts; so every
+// pass keeps the order of equal digits (about 110 instructions per entry
+// against ~500 for a bitonic network on 2,048).
+// Longer lists (up to VG_TILE_SORT_LONG_CAP): keys (depth bits, slot)
+// packed as one 64-bit integer, padded to a power of two with the largest
+// value and sorted by a bitonic network.
 // ---------------------------------------------------------------------------
 constexpr int LONG_SORT_THREADS = 512;
+constexpr int RADIX_LONG_THREADS = 256;
+constexpr int RADIX_LONG_WARPS = RADIX_LONG_THREADS / 32;
+constexpr int RADIX_LONG_CAP = 4096;
+constexpr int RADIX_LONG_ROUNDS = RADIX_LONG_CAP / RADIX_LONG_THREADS;  // rounds of 32 per warp, at most
+
+__global__ void __launch_bounds__(RADIX_LONG_THREADS, 3) tile_radix_long_kernel(
+    const uint2* __restrict__ ranges, const uint32_t* __restrict__ long_tiles, const uint32_t* __restrict__ n_long_p,
+    uint32_t* __restrict__ pvals, const uint32_t* __restrict__ dkey) {
+    extern __shared__ uint32_t s_dyn[];
+    // buffer b holds keys at s_dyn + b * CAP and slots at s_dyn + (2 + b) * CAP
+    auto s_key = [&](int b) { return s_dyn + b * RADIX_LONG_CAP; };
+    auto s_val = [&](int b) { return s_dyn + (2 + b) * RADIX_LONG_CAP; };
+    uint32_t* s_cnt = s_dyn + 4 * RADIX_LONG_CAP;  // [warp][digit] counts, then offsets
+    __shared__ uint32_t s_tmp[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = lanemask_lt();
+    const uint32_t n_long = *n_long_p;
+    for (uint32_t t = blockIdx.x; t < n_long; t += gridDim.x) {
+        const uint2 rg = ranges[long_tiles[t]];
+        const uint32_t n = rg.y - rg.x;
+        if (n > (uint32_t)RADIX_LONG_CAP) continue;  // (the bitonic kernel's)
+        for (uint32_t i = threadIdx.x; i < n; i += RADIX_LONG_THREADS) {
+            const uint32_t sl = pvals[rg.x + i];
+            s_val(0)[i] = sl;
+            s_key(0)[i] = dkey[sl];
+        }
+        // warp w's stretch: [w * seg, min((w + 1) * seg, n)), seg a multiple of 32
+        const uint32_t seg = ((n + RADIX_LONG_WARPS * 32 - 1) / (RADIX_LONG_WARPS * 32)) * 32;
+        const uint32_t w0 = (uint32_t)warp * seg;
+        const int rounds = (int)(seg / 32);
+        int cur = 0;
+        for (int shift = 0; shift < 32; shift += 8) {
+            for (int d = lane; d < 256; d += 32) s_cnt[warp * 256 + d] = 0u;
+            __syncthreads();  // (the previous pass's output and this pass's counts)
+            uint32_t key[RADIX_LONG_ROUNDS], val[RADIX_LONG_ROUNDS], peers[RADIX_LONG_ROUNDS];
+#pragma unroll
+            for (int r = 0; r < RADIX_LONG_ROUNDS; ++r) {
+                if (r >= rounds) break;
+                const uint32_t e = w0 + (uint32_t)r * 32 + (uint32_t)lane;
+                const bool ok = e < n;
+                key[r] = ok ? s_key(cur)[e] : 0u;
+                val[r] = ok ? s_val(cur)[e] : 0u;
+                const uint32_t dg = ok ? ((key[r] >> shift) & 255u) : 256u;
+                peers[r] = __match_any_sync(0xffffffffu, dg);
+                if (ok && (peers[r] & lt) == 0) s_cnt[warp * 256 + dg] += (uint32_t)__popc(peers[r]);
+                __syncwarp();
+            }
+            __syncthreads();
+            {  // offsets: digit-major, then warp
+                const int dg = threadIdx.x;  // one digit per thread (256 threads)
+                uint32_t c[RADIX_LONG_WARPS], tot = 0;
+#pragma unroll
+                for (int w = 0; w < RADIX_LONG_WARPS; ++w) {
+                    c[w] = s_cnt[w * 256 + dg];
+                    tot += c[w];
+                }
+                uint32_t all;
+                uint32_t run = block_excl_scan_256(tot, s_tmp, &all);
+#pragma unroll
+                for (int w = 0; w < RADIX_LONG_WARPS; ++w) {
+                    s_cnt[w * 256 + dg] = run;
+                    run += c[w];
+                }
+            }
+            __syncthreads();
+            const int nxt = cur ^ 1;
+#pragma unroll
+            for (int r = 0; r < RADIX_LONG_ROUNDS; ++r) {
+                if (r >= rounds) break;
+                const uint32_t e = w0 + (uint32_t)r * 32 + (uint32_t)lane;
+                const bool ok = e < n;
+                const uint32_t dg = ok ? ((key[r] >> shift) & 255u) : 0u;
+                const uint32_t base = ok ? s_cnt[warp * 256 + dg] : 0u;
+                __syncwarp();
+                if (ok) {
+                    const uint32_t pos = base + (uint32_t)__popc(peers[r] & lt);
+                    s_key(nxt)[pos] = key[r];
+                    s_val(nxt)[pos] = val[r];
+                    if ((peers[r] & lt) == 0) s_cnt[warp * 256 + dg] = base + (uint32_t)__popc(peers[r]);
+                }
+                __syncwarp();
+            }
+            cur = nxt;
+        }
+        __syncthreads();
+        // runs of equal depth bits (rare): their slots in increasing order
+        for (uint32_t i = threadIdx.x; i < n; i += RADIX_LONG_THREADS) {
+            const uint32_t k = s_key(cur)[i];
+            if ((i == 0 || s_key(cur)[i - 1] != k) && i + 1 < n && s_key(cur)[i + 1] == k) {
+                uint32_t j = i + 1;
+                while (j < n && s_key(cur)[j] == k) ++j;
+                for (uint32_t a = i + 1; a < j; ++a) {  // insertion sort of s_val(cur)[i, j)
+                    const uint32_t v = s_val(cur)[a];
+                    uint32_t b = a;
+                    while (b > i && s_val(cur)[b - 1] > v) {
+                        s_val(cur)[b] = s_val(cur)[b - 1];
+                        --b;
+                    }
+                    s_val(cur)[b] = v;
+                }
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += RADIX_LONG_THREADS) pvals[rg.x + i] = s_val(cur)[i];
+        __syncthreads();  // shared memory free for the next list
+    }
+}
 
 __global__ void __launch_bounds__(LONG_SORT_THREADS) tile_sort_long_kernel(
     const uint2* __restrict__ ranges, const uint32_t* __restrict__ long_tiles, const uint32_t* __restrict__ n_long_p,
@@ -682,6 +799,7 @@ __global__ void __launch_bounds__(LONG_SORT_THREADS) tile_sort_long_kernel(
     for (uint32_t t = blockIdx.x; t < n_long; t += gridDim.x) {
         const uint2 rg = ranges[long_tiles[t]];
         const uint32_t n = rg.y - rg.x;
+        if (n <= (uint32_t)RADIX_LONG_CAP) continue;  // (the radix kernel's)
         if (n > (uint32_t)VG_TILE_SORT_LONG_CAP) {  // left unsorted: the outputs are flagged invalid
             if (threadIdx.x == 0) atomicOr(err, ERR_TILE_LONG);
             continue;
@@ -725,11 +843,21 @@ cudaError_t launch_tile_sort_long(const uint2* ranges, const uint32_t* long_tile
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms < 1) sms = 148;
     }
-    const size_t smem = (size_t)VG_TILE_SORT_LONG_CAP * sizeof(unsigned long long);
-    cudaError_t e = allow_dynamic_smem((const void*)tile_sort_long_kernel, smem);
+    // lists up to 4,096: the radix kernel, three 72 KB CTAs per SM
+    const size_t rsmem = (size_t)(4 * RADIX_LONG_CAP + RADIX_LONG_WARPS * 256) * sizeof(uint32_t);
+    cudaError_t e = allow_dynamic_smem((const void*)tile_radix_long_kernel, rsmem);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    // three 64 KB CTAs per SM; a CTA with no list left exits at once
+    tile_radix_long_kernel<<<(unsigned)(3 * sms), RADIX_LONG_THREADS, rsmem, st>>>(ranges, long_tiles, n_long, pvals,
+                                                                                   dkey);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // longer ones: the bitonic kernel, three 64 KB CTAs per SM; a CTA with no
+    // list left exits at once
+    const size_t smem = (size_t)VG_TILE_SORT_LONG_CAP * sizeof(unsigned long long);
+    e = allow_dynamic_smem((const void*)tile_sort_long_kernel, smem);
+    if (e != cudaSuccess) return e;
+    count_launches(1);
     tile_sort_long_kernel<<<(unsigned)(3 * sms), LONG_SORT_THREADS, smem, st>>>(ranges, long_tiles, n_long, pvals,
                                                                                 dkey, err);
     return cudaGetLastError();

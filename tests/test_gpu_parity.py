@@ -167,15 +167,32 @@ def test_sort_modes_give_identical_lists_images_and_gradients(cuda):
         grad_tolerance_check(b[4][name], a[4][name], "sort modes:" + name, rtol=1e-4, atol_frac=1e-5)
 
 
-def test_long_tile_lists_sorted_per_tile_bit_exact(cuda):
-    """4,000 Gaussians in 12 tiles: lists of ~1,600 entries, past what the
-    compositing kernel sorts itself; the per-tile form's long-list pass sorts
-    them, lists bit-exact against the oracle, images equal the global sort."""
-    sc, cams = synth.tiny_scene(n=4000), [synth.tiny_camera()]
+def _doubled(sc):
+    """Every Gaussian twice: equal depth bits in pairs, ordered by slot."""
+    import dataclasses
+    cat = lambda a: None if a is None else np.concatenate([a, a], axis=0)
+    groups = {k: synth.Group(g.dim, raw=cat(g.raw)) for k, g in sc.groups.items()}
+    return dataclasses.replace(sc, anchor_xyz=cat(sc.anchor_xyz), anchor_l=cat(sc.anchor_l),
+                               offsets=cat(sc.offsets), groups=groups, mask_logit=cat(sc.mask_logit))
+
+
+@pytest.mark.parametrize("case", ["4000", "12000", "2000 doubled"])
+def test_long_tile_lists_sorted_per_tile_bit_exact(cuda, case):
+    """Lists past what the compositing kernel sorts itself (12 tiles): ~1,600
+    entries (4,000 Gaussians; the radix pass), up to ~5,000 (12,000; lists
+    over 4,096 take the bitonic pass), and every Gaussian twice (ties in
+    depth, ordered by slot); the per-tile form's long-list pass sorts them,
+    lists bit-exact against the oracle, images equal the global sort."""
+    sc = synth.tiny_scene(n=int(case.split()[0]))
+    if case.endswith("doubled"):
+        sc = _doubled(sc)
+    cams = [synth.tiny_camera()]
     P, nb, nbl = check_binning(sc, cams, sort_mode=V.VG_SORT_TILE)
     o = O.Oracle(sc, cams)
     ts, _ = o.bins()
     assert np.diff(ts).max() > V.VG_TILE_SORT_CAP
+    if case == "12000":
+        assert np.diff(ts).max() > 4096
     sh = V.vg_scene_upload(sc)
     a = V.render_with_retry(sh, cams, V.default_params(sort_mode=V.VG_SORT_TILE), V.vg_ctx_create(0))
     b = V.render_with_retry(sh, cams, V.default_params(sort_mode=V.VG_SORT_GLOBAL), V.vg_ctx_create(0))
