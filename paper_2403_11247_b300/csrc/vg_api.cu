@@ -212,7 +212,7 @@ struct vg_ctx {
     int64_t pair_cap = 0;
     DevBuf xy, conic_o, rgbd, rect, ntiles, dkey[2], dval[2], g2d, pkey[2], pval[2], ranges, tile_order, Tfin, ncontrib, lookback,
         scratch, state, pose_part, icp_part, loss_scratch, pair_off, chunk_start, blk_count, vis, ssim_ws, grow_ws,
-        neval, loss_blk, long_tiles, part_total, blk_prefix;
+        neval, loss_blk, long_tiles, part_total;
     int final_pair = 0;
     bool have_fwd = false, have_bwd = false;
     // VG_SORT_AUTO's form on this ctx: 0 per-tile sort, 2 global (a list
@@ -747,7 +747,6 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
     VG_TRY(ctx->chunk_start.ensure((size_t)ceil_div(std::max<int64_t>(ctx->pair_cap, 1), EMIT_CHUNK) * 4, st,
                                    "pair chunk starts"));
     VG_TRY(ctx->blk_count.ensure((size_t)preprocess_blocks(N) * 8, st, "block counts"));
-    VG_TRY(ctx->blk_prefix.ensure((size_t)preprocess_blocks(N) * 8, st, "block count prefixes"));
     const int lf_grid = compact_grid(N, cs);
     if (lf) {
         VG_TRY(ctx->loss_blk.ensure((size_t)lf_grid * 8, st, "loss block counts"));
@@ -820,8 +819,7 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
                                                 ctx->ntiles.as<uint32_t>(),
                                                 tile_sort ? ctx->pair_off.as<uint32_t>() : nullptr,
                                                 ctx->chunk_start.as<uint32_t>(), cap, scr, err, g2d_rows,
-                                                ctx->pose_part.as<float>(), n_views * 6, cs,
-                                                ctx->blk_prefix.as<uint32_t>(), st);
+                                                ctx->pose_part.as<float>(), n_views * 6, cs, st);
                  if (e != cudaSuccess) return e;
                  for (int p = 0; p < (tile_sort ? 0 : 4); ++p) {
                      const int i = p & 1, o = i ^ 1;

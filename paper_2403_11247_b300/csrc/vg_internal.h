@@ -86,13 +86,11 @@ cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& c
 // g2d_rows (may be NULL): the backward's per-slot gradient rows, zeroed here
 // for every visible slot; pose_zero [n_pose] (may be NULL): zeroed too.
 // With cs.lf_on it also counts the fused loss's normalisers per block into
-// cs.lf_blk [2][compact_grid] (the ranges kernel sums them).  blk_prefix
-// [2][preprocess blocks]: room for the counts' scan, used for large grids.
+// cs.lf_blk [2][compact_grid] (the ranges kernel sums them).
 cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count,
                            uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, const uint32_t* ntiles,
                            uint32_t* pair_off, uint32_t* chunk_start, uint32_t cap, uint32_t* scratch, uint32_t* err,
-                           float* g2d_rows, float* pose_zero, int n_pose, const Consts& cs, uint32_t* blk_prefix,
-                           cudaStream_t st);
+                           float* g2d_rows, float* pose_zero, int n_pose, const Consts& cs, cudaStream_t st);
 cudaError_t launch_rvq_decode(int dim, int L, int K, const float* cb, const uint8_t* idx, const float* raw,
                               int64_t n, float* out, cudaStream_t st);
 

@@ -264,8 +264,7 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
                                                       uint32_t* __restrict__ chunk_start, uint32_t cap,
                                                       uint32_t* __restrict__ scratch, uint32_t* __restrict__ err,
                                                       float* __restrict__ g2d_rows, float* __restrict__ pose_zero,
-                                                      int n_pose, int nb, const Consts cs,
-                                                      const uint32_t* __restrict__ blk_prefix) {
+                                                      int n_pose, int nb, const Consts cs) {
     __shared__ uint32_t s_tmp[8];
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < n_pose; i += 256) pose_zero[i] = 0.f;
@@ -307,11 +306,11 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
     if ((int)blockIdx.x >= nb) return;
     const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
     const int b = (int)blockIdx.x;
+    // this block's offsets: the sums of the counts of the blocks in front of
+    // it (nb^2 / 2 words over the grid, from L2; on the 3M-Gaussian scene's
+    // 11,719 blocks still faster than a separate one-block scan launch)
     uint32_t off, poff = 0;
-    if (blk_prefix) {  // many blocks: their counts were scanned by one block first
-        off = blk_prefix[b];
-        if (pair_off) poff = blk_prefix[nb + b];
-    } else {
+    {
         uint32_t a = 0, p = 0;
         for (int j = threadIdx.x; j < b; j += 256) {
             a += cnt[j];
@@ -359,48 +358,6 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
 
 int preprocess_blocks(int64_t N) { return (int)ceil_div(N > 0 ? N : 1, 256); }
 
-// Exclusive scans of the preprocess's per-block visible-slot and pair counts
-// (cnt [2][nb]) into prefix [2][nb], by one block: for grids of many blocks,
-// where each compaction block summing the counts in front of it would read
-// nb^2 / 2 words.
-__global__ void __launch_bounds__(1024) block_counts_scan_kernel(const uint32_t* __restrict__ cnt, int nb,
-                                                                 uint32_t* __restrict__ prefix) {
-    __shared__ uint32_t s_w[32];
-    __shared__ uint32_t s_carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int arr = 0; arr < 2; ++arr) {
-        if (threadIdx.x == 0) s_carry = 0;
-        __syncthreads();
-        for (int c0 = 0; c0 < nb; c0 += 1024) {
-            const int i = c0 + (int)threadIdx.x;
-            const uint32_t x = i < nb ? cnt[arr * nb + i] : 0u;
-            uint32_t inc = x;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            if (lane == 31) s_w[warp] = inc;
-            __syncthreads();
-            if (warp == 0) {
-                uint32_t t = s_w[lane];
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-                    if (lane >= o) t += y;
-                }
-                s_w[lane] = t;
-            }
-            __syncthreads();
-            if (i < nb) prefix[arr * nb + i] = s_carry + (warp ? s_w[warp - 1] : 0u) + inc - x;
-            __syncthreads();
-            if (threadIdx.x == 0) s_carry += s_w[31];
-            __syncthreads();
-        }
-    }
-}
-
-constexpr int COMPACT_SCAN_BLOCKS = 2048;  // above this many blocks the counts are scanned first
 
 // with the fused loss the compaction grid counts its normalisers too: a
 // block per 4,096 pixels at least
@@ -434,20 +391,13 @@ cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& c
 cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, const uint32_t* blk_count,
                            uint32_t* keys_out, uint32_t* vals_out, uint32_t* vals_copy, const uint32_t* ntiles,
                            uint32_t* pair_off, uint32_t* chunk_start, uint32_t cap, uint32_t* scratch, uint32_t* err,
-                           float* g2d_rows, float* pose_zero, int n_pose, const Consts& cs, uint32_t* blk_prefix,
-                           cudaStream_t st) {
+                           float* g2d_rows, float* pose_zero, int n_pose, const Consts& cs, cudaStream_t st) {
     const int blocks = preprocess_blocks(N);
     const int64_t grid = compact_grid(N, cs);
-    const bool scan_first = blocks > COMPACT_SCAN_BLOCKS && blk_prefix;
-    if (scan_first) {
-        count_launches(1);
-        block_counts_scan_kernel<<<1, 1024, 0, st>>>(blk_count, blocks, blk_prefix);
-    }
     count_launches(1);
     compact_kernel<<<(unsigned)grid, 256, 0, st>>>(V, N, dkey, blk_count, keys_out, vals_out, vals_copy, ntiles,
                                                    pair_off, chunk_start, cap, scratch, err, g2d_rows, pose_zero,
-                                                   pose_zero ? n_pose : 0, blocks, cs,
-                                                   scan_first ? blk_prefix : nullptr);
+                                                   pose_zero ? n_pose : 0, blocks, cs);
     return cudaGetLastError();
 }
 
