@@ -427,11 +427,12 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
                     // capped alpha is constant: no conic, mean or opacity terms.
                     // The per-Gaussian factors (e^power = x / o, the signs and
                     // halves of the conic terms) are applied once per visit below
-                    const bool unc = x <= cs.alpha_max;
-                    const float dp = unc ? alpha * dA : 0.f;
-                    const float xu = unc ? x : 0.f;
+                    // (uncapped, x is alpha: dp = alpha dA = x dA, and the
+                    // opacity sum takes the same dp)
+                    const float xu = x <= cs.alpha_max ? x : 0.f;
+                    const float dp = xu * dA;
                     const float pdx = dp * dx, pdy = dp * dy;
-                    vals[5] = fmaf(xu, dA, vals[5]);
+                    vals[5] += dp;
                     vals[0] = fmaf(nat.x, pdx, fmaf(nat.y, pdy, vals[0]));
                     vals[1] = fmaf(nat.y, pdx, fmaf(nat.z, pdy, vals[1]));
                     vals[2] = fmaf(pdx, dx, vals[2]);

@@ -495,11 +495,10 @@ __global__ void __launch_bounds__(SPLIT_NT) split_bwd_kernel(
                 vals[7] = wt * gp[1];
                 vals[8] = wt * gp[2];
                 vals[9] = wt * gp[3];
-                const bool unc = x <= cs.alpha_max;
-                const float dp = unc ? alpha * dA : 0.f;
-                const float xu = unc ? x : 0.f;
+                const float xu = x <= cs.alpha_max ? x : 0.f;  // (uncapped, x is alpha)
+                const float dp = xu * dA;
                 const float pdx = dp * dx, pdy = dp * dy;
-                vals[5] = xu * dA;
+                vals[5] = dp;
                 vals[0] = fmaf(nat.x, pdx, nat.y * pdy);
                 vals[1] = fmaf(nat.y, pdx, nat.z * pdy);
                 vals[2] = pdx * dx;
