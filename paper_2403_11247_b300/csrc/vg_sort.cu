@@ -351,7 +351,12 @@ __global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
             const uint32_t key = (uint32_t)(V.v[v].tile_base + (int)(y0 + ry) * V.v[v].tiles_x + (int)(x0 + rx));
             pkeys[e] = key;
             pvals[e] = s;
-            for (int p = 0; p < tile_passes; ++p) hist_add_warp(s_hist + p * 256, (key >> (8 * p)) & 255u, active);
+            // digit histograms of the tile passes: the low digit of a warp's
+            // keys is mostly distinct (consecutive tiles of a rect row), so
+            // each lane adds its own; higher digits mostly repeat in a warp
+            // and are combined first
+            if (tile_passes > 0) atomicAdd(s_hist + (key & 255u), 1u);
+            for (int p = 1; p < tile_passes; ++p) hist_add_warp(s_hist + p * 256, (key >> (8 * p)) & 255u, active);
             if (!ranges_zero) {
                 const uint32_t peers = __match_any_sync(active, key);
                 if ((uint32_t)lane == (uint32_t)(__ffs(peers) - 1)) {

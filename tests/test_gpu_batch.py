@@ -110,8 +110,10 @@ def test_local_ba_reduces_pose_error(torch):
     torch.cuda.synchronize()
     assert ba.check() == V.VG_OK
     after = pose_errors(ba.pose.cpu().numpy().astype(np.float64), T_true)
-    assert after[:, 0].mean() < 0.6 * before[:, 0].mean(), (before, after)
-    assert after[:, 1].mean() < 0.6 * before[:, 1].mean(), (before, after)
+    # poses only (the map fixed): 50 iterations take both errors below 30%
+    # (measured: rotation 0.61 -> 0.08 deg, translation 3.6 -> 0.2 cm)
+    assert after[:, 0].mean() < 0.3 * before[:, 0].mean(), (before, after)
+    assert after[:, 1].mean() < 0.3 * before[:, 1].mean(), (before, after)
 
 
 def test_local_ba_with_the_ssim_term(torch):
