@@ -45,15 +45,16 @@ BWD_FLOP_BLEND = 49       # per blended pair: T recovery, dL/dalpha, colour/dept
 CHAIN_FLOP_SLOT = 600     # per visible slot: projection, covariance and rotation reverse mode (FMA = 2)
 ADAM_BYTES_PARAM = 28     # read parameter, gradient, two moments; write parameter, two moments
 # DRAM bytes (read + write) per launch of the compositing kernels from one ncu
-# capture of this workload (profiles/step_kernels__mapping_1200x680.md), valid
-# while the kernels' sources hash to the value they had when captured
-BLEND_SOURCES = ("paper_2403_11247_b300/csrc/vg_blend.cu", "paper_2403_11247_b300/csrc/vg_common.cuh")
-NCU_TRAFFIC = {"blend_bwd": ("a5bebdd73b904de9", 24.4288e6 + 0.0),
-               "blend_fwd": ("a5bebdd73b904de9", 3.418624e6 + 2048.0)}
+# capture of this workload (profiles/blend_bwd_kernel__mapping_1200x680.md),
+# valid while the kernels' sources hash to the value they had when captured
+BLEND_SOURCES = ("paper_2403_11247_b300/csrc/vg_blend.cu", "paper_2403_11247_b300/csrc/vg_common.cuh",
+                 "paper_2403_11247_b300/csrc/vg_blend_common.cuh")
+NCU_TRAFFIC = {"blend_bwd": ("2fd16b6379fbb5de", 24.42752e6 + 0.0),
+               "blend_fwd": ("2fd16b6379fbb5de", 16.484352e6 + 586.496e3)}
 # warp instructions per launch from the same capture: with the live launch
 # time they give the issue rate against the SMs' issue peak (4 schedulers
 # per SM, one warp instruction per clock each)
-NCU_INSTRUCTIONS = {"blend_bwd": 111.143092e6, "blend_fwd": 51.578011e6}
+NCU_INSTRUCTIONS = {"blend_bwd": 105.19017e6, "blend_fwd": 55.232963e6}
 
 
 def ncu_traffic(stage: str):
