@@ -47,6 +47,13 @@ def gpu_forward(scene, cams, ctx=None, sh=None, **pkw):
     ctx = ctx or V.vg_ctx_create(0)
     params = V.default_params(**pkw)
     C_, D, S = V.render_with_retry(sh, cams, params, ctx)
+    if pkw.get("count_evals"):
+        # the work counters of exactly one forward (a retry -- a grown pair
+        # buffer, or the automatic sort form switching to the global sort
+        # after a long list -- would have added a discarded forward's)
+        V.vg_ctx_reset_counters(ctx)
+        C_, D, S = V.vg_render_fwd(sh, cams, params, ctx)
+        assert V.vg_check(ctx) == V.VG_OK
     return sh, ctx, params, C_.cpu().numpy(), D.cpu().numpy(), S.cpu().numpy()
 
 

@@ -53,3 +53,31 @@ def test_host_alloc_free_cycles_and_errors(torch):
         V.vg_host_alloc(0)
     t = V.host_empty((4, 5), torch.int32)
     assert t.shape == (4, 5) and t.dtype == torch.int32
+
+
+def test_workspace_growth_is_counted_and_grows_with_headroom(torch):
+    """A ctx used on a stream grows its buffers stream-ordered and by at
+    least a quarter: a render a little larger than the last one allocates
+    nothing new, a much larger one does; the results stay right."""
+    from paper_2403_11247_b300 import synth
+    sc = synth.room_scene(seed=1002, n_anchors=2500)
+    sh = V.vg_scene_upload(sc)
+    s = torch.cuda.Stream()
+    ctx = V.vg_ctx_create(1 << 20)
+    p = V.default_params()
+    with torch.cuda.stream(s):
+        ref = V.render_with_retry(sh, [synth.room_camera(320, 180, 160.0)], p, ctx, stream=s)
+        a0 = V.vg_workspace_allocs()
+        V.render_with_retry(sh, [synth.room_camera(330, 186, 165.0)], p, ctx, stream=s)   # grows, with headroom
+        a1 = V.vg_workspace_allocs()
+        V.render_with_retry(sh, [synth.room_camera(340, 190, 170.0)], p, ctx, stream=s)   # inside the headroom
+        a2 = V.vg_workspace_allocs()
+        big = V.render_with_retry(sh, [synth.room_camera(640, 360, 320.0)], p, ctx, stream=s)   # 4x the pixels
+        a3 = V.vg_workspace_allocs()
+        again = V.render_with_retry(sh, [synth.room_camera(320, 180, 160.0)], p, ctx, stream=s)
+    s.synchronize()
+    assert a1 > a0 and a2 == a1 and a3 > a2, (a0, a1, a2, a3)
+    assert V.vg_check(ctx, s) == V.VG_OK
+    for x, y in zip(ref, again):
+        assert torch.equal(x, y)
+    assert float(big[2].max()) > 0.0

@@ -43,7 +43,9 @@ def _scene_and_cams():
     return sc, cams
 
 
-def test_masked_forward_and_backward_match_the_oracle(torch):
+@pytest.mark.parametrize("split", [1, 6])
+def test_masked_forward_and_backward_match_the_oracle(torch, split):
+    """Sampled rays, lists composited whole (1) and split over 6 CTAs."""
     sc, cams = _scene_and_cams()
     o = O.Oracle(sc, cams)
     mask = sample_rays(o.n_pixels, 0.3, 11, 2)
@@ -52,13 +54,13 @@ def test_masked_forward_and_backward_match_the_oracle(torch):
     sh = V.vg_scene_upload(sc)
     ctx = V.vg_ctx_create(0)
     md = torch.from_numpy(mask).cuda()
-    params = V.default_params(pixel_mask=md)
+    params = V.default_params(pixel_mask=md, list_split=split)
     C_, D, S = V.render_with_retry(sh, cams, params, ctx)
     for g, name in ((S, "S"), (D, "D")):
         assert not g.cpu().numpy()[~mask.astype(bool)].any(), name   # unsampled pixels are not composited
     proj, _, _ = o.projection()
     check_images(C_.cpu().numpy(), D.cpu().numpy(), S.cpu().numpy(), f, cams, float(proj[proj[:, 10] == 1, 2].max()),
-                 "rays")
+                 f"rays-split{split}")
     dC, dD, dS = masked_upstream(17, f, cams)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
     g = to_np_grads(V.vg_render_bwd(sh, cams, params, ctx, t(dC), t(dD), t(dS)))

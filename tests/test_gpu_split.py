@@ -50,6 +50,18 @@ def test_split_deep_lists_match_oracle(cuda):
     backward_parity(sc, cams, "bwd-deep-auto")
 
 
+def test_split_views_of_different_sizes_match_oracle(cuda):
+    """Three views (64x48, 48x32, 40x24: 22 tiles) in one launch, split
+    automatically: images, counters, gradients and pose sums against the
+    oracle."""
+    sc = deep_scene()
+    c0 = synth.tiny_camera()
+    cams = [c0, synth.camera(38.0, 38.0, 24.0, 16.0, 48, 32, c0.T_cw, c0.near),
+            synth.camera(30.0, 30.0, 20.0, 12.0, 40, 24, c0.T_cw, c0.near)]
+    assert_forward_parity(sc, cams, "split-views")
+    backward_parity(sc, cams, "bwd-split-views")
+
+
 def _render(sh, cams, ctx, **kw):
     p = V.default_params(count_evals=1, **kw)
     out = [x.cpu().numpy() for x in V.render_with_retry(sh, cams, p, ctx)]
