@@ -621,6 +621,16 @@ def large_leg(torch, V, synth, steps=20):
     for _ in range(3):
         step()
     torch.cuda.synchronize()
+    # launch shape picked on this workload (the step's upstream gradients
+    # are in dC, dD now)
+    from paper_2403_11247_b300.autotune import autotune_launch, launch_params
+    tune = autotune_launch(sh, cams, ctx, dC, dD, None, grads, reps=3, sort_mode=V.VG_SORT_GLOBAL)
+    params = V.default_params(sort_mode=V.VG_SORT_GLOBAL, **launch_params(tune))
+    for g_ in grads.values():
+        g_.zero_()
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, capture_error_mode="thread_local"):
         step()
@@ -639,7 +649,7 @@ def large_leg(torch, V, synth, steps=20):
     tiles = 4 * ((cams[0].width + 15) // 16) * ((cams[0].height + 15) // 16)
     # stage times and work counters: a second capture carrying the stage
     # events, with the work counters on
-    params_c = V.default_params(sort_mode=V.VG_SORT_GLOBAL, count_evals=1)
+    params_c = V.default_params(sort_mode=V.VG_SORT_GLOBAL, count_evals=1, **launch_params(tune))
 
     def step_c():
         V.vg_render_fwd(sh, cams, params_c, ctx, C_, D, S)
@@ -675,7 +685,7 @@ def large_leg(torch, V, synth, steps=20):
     # the per-tile form (lists over 1,024 sorted by the long-list pass), same
     # step in a graph of its own
     ctx_t = V.vg_ctx_create(0)
-    params_t = V.default_params(sort_mode=V.VG_SORT_TILE)
+    params_t = V.default_params(sort_mode=V.VG_SORT_TILE, **launch_params(tune))
     V.render_with_retry(sh, cams, params_t, ctx_t)
     V.vg_ctx_reserve(ctx_t, int(st["pairs"] * 1.2) + 4096)
 
@@ -703,7 +713,7 @@ def large_leg(torch, V, synth, steps=20):
            "ms_per_step": ms, "iters_per_s": 1000.0 / ms, "mpix_per_s": 4 * P / ms / 1e3,
            "pairs": st["pairs"], "mean_list_per_tile": st["pairs"] / tiles, "visible_slots": st["visible"],
            "steps": steps, "stages_ms_per_step": {k: v[0] / Kp for k, v in prof.items() if v[1]},
-           "per_kernel_roofline": rows, "sort": "global (lists over 1,024 entries)",
+           "per_kernel_roofline": rows, "sort": "global (lists over 1,024 entries)", "autotune": tune,
            "per_tile_form_ms_per_step": statistics.median(t_times)}
     log(f"large scene: {ms:.2f} ms per 4-view fwd+bwd, {res['mean_list_per_tile']:.0f} Gaussians per tile")
     return res
