@@ -161,11 +161,12 @@ typedef struct {
  *   grouped by tile; the forward compositing kernel sorts each tile's list
  *   of up to VG_TILE_SORT_CAP entries by (depth bits, slot) in shared memory
  *   and writes it back for the backward, and a pass before it sorts the
- *   longer lists (up to VG_TILE_SORT_LONG_CAP entries, one CTA each).
+ *   longer lists (up to VG_TILE_SORT_LONG_CAP entries, one CTA each: a
+ *   shared-memory radix sort up to 4,096 entries, a bitonic network above).
  *   VG_SORT_AUTO (the default): VG_SORT_TILE without the long-list pass
  *   until a forward on this ctx meets a list over VG_TILE_SORT_CAP, and
  *   VG_SORT_GLOBAL from then on (for lists that long the global radix
- *   passes are faster than the long-list pass's comparison sort).  A forward
+ *   passes are faster than the scatter and the per-list sorts).  A forward
  *   that meets a list longer than its form takes leaves its outputs invalid
  *   and the next vg_check returns VG_ERR_CAPACITY (render again:
  *   vg.render_with_retry does).
