@@ -190,7 +190,8 @@ typedef struct {
  *   2..32 = S.  The images equal the unsplit ones up to FP32 rounding of
  *   the transmittance products (the same Gaussians are blended except where
  *   a product lands within rounding of t_min); the backward must use the
- *   forward's split, which the ctx keeps. */
+ *   forward's split, which the ctx keeps.  Workspace: 48 B per tile pixel
+ *   and segment (tiles x S x 256 x 48 B). */
 typedef struct {
     int32_t tile;
     int32_t batch;
