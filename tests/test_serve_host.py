@@ -91,3 +91,30 @@ def test_reset_clears_results():
     tr[0].done, tr[0].result = 1.0, (1, 2, 3)
     serve.reset(tr)
     assert tr[0].done == -1.0 and tr[0].result is None
+
+
+def test_summary_breaks_the_slowest_requests_down():
+    """p99 breakdown: queued (arrival to enqueue), enqueue host time, device
+    time, and the rest until the result is noticed, over the slowest 1%."""
+    tr = []
+    for i in range(200):
+        r = _req(i, "render", 0, 8, 8, t=0.001 * i)
+        slow = i == 7 or i == 11
+        r.launched = r.arrival + (0.020 if slow else 0.001)
+        r.launch_host_ms = 0.5
+        r.gpu_ms = 3.0 if slow else 1.0
+        r.done = r.launched + (0.5 + r.gpu_ms + 0.25) / 1e3
+        tr.append(r)
+    out = serve.summarize(tr, wall=1.0, launches=200)
+    b = out["p99_breakdown_ms"]
+    assert b["n"] == 2
+    assert abs(b["queued"] - 20.0) < 1e-6 and abs(b["gpu"] - 3.0) < 1e-6
+    assert abs(b["enqueue_host"] - 0.5) < 1e-9 and abs(b["after_gpu"] - 0.25) < 1e-6
+    lat = np.array([(r.done - r.arrival) * 1e3 for r in tr])
+    assert abs(out["p99_ms"] - np.percentile(lat, 99)) < 1e-9 and out["p99_ms"] < 23.75
+    assert out["enqueue_host_ms"]["max"] == 0.5 and out["gpu_ms"]["max"] == 3.0
+    # without launch records (requests never launched) there is no breakdown
+    serve.reset(tr)
+    for r in tr:
+        r.done = r.arrival + 0.001
+    assert "p99_breakdown_ms" not in serve.summarize(tr, wall=1.0, launches=0)
