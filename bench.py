@@ -49,8 +49,8 @@ ADAM_BYTES_PARAM = 28     # read parameter, gradient, two moments; write paramet
 # valid while the kernels' sources hash to the value they had when captured
 BLEND_SOURCES = ("paper_2403_11247_b300/csrc/vg_blend.cu", "paper_2403_11247_b300/csrc/vg_common.cuh",
                  "paper_2403_11247_b300/csrc/vg_blend_common.cuh")
-NCU_TRAFFIC = {"blend_bwd": ("2fd16b6379fbb5de", 24.42752e6 + 0.0),
-               "blend_fwd": ("2fd16b6379fbb5de", 16.484352e6 + 586.496e3)}
+NCU_TRAFFIC = {"blend_bwd": ("92663f7472549d3f", 24.42752e6 + 0.0),
+               "blend_fwd": ("92663f7472549d3f", 16.484352e6 + 586.496e3)}
 # warp instructions per launch from the same capture: with the live launch
 # time they give the issue rate against the SMs' issue peak (4 schedulers
 # per SM, one warp instruction per clock each)

@@ -328,6 +328,15 @@ __device__ __forceinline__ float fast_exp2(float x) {
     return y;
 }
 
+// add v to a word of shared memory without reading the result back (the
+// reduction form of the atomic add: the thread does not wait for it)
+__device__ __forceinline__ void red_add_shared(float* p, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_shared(uint32_t* p, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -11,6 +11,7 @@ namespace vgk {
 
 constexpr int CHAIN_THREADS = 256;
 
+
 __device__ __forceinline__ float block_sum_256(float x, float* s_tmp /*[8]*/) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -252,10 +253,15 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                     for (int st = 0; st < S.L[gi]; ++st) {
                         const int k = __ldg(S.idx[gi] + (int64_t)st * S.N + n);
                         const int j = (st * S.K[gi] + k) * d;
-                        float* dst = O.cb_in_smem ? s_cb + O.cb_off[gi] + j : O.cb[gi] + j;
+                        if (O.cb_in_smem) {
 #pragma unroll
-                        for (int c = 0; c < dmax; ++c)
-                            if (c < d) atomicAdd(dst + c, gval(gi, c));
+                            for (int c = 0; c < dmax; ++c)
+                                if (c < d) red_add_shared(s_cb + O.cb_off[gi] + j + c, gval(gi, c));
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < dmax; ++c)
+                                if (c < d) atomicAdd(O.cb[gi] + j + c, gval(gi, c));
+                        }
                     }
                 } else if (O.raw[gi]) {
 #pragma unroll
@@ -280,8 +286,10 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                 if (S.Lo > 0) {
                     for (int st = 0; st < S.Lo; ++st) {
                         const int j = (st * S.Ko + __ldg(S.idxo + (int64_t)st * S.N + n)) * 3;
-                        float* dst = O.cb_in_smem ? s_cb + O.cb_off[4] + j : O.d_off + j;
-                        for (int c = 0; c < 3; ++c) atomicAdd(dst + c, dmu[c] * la[c]);
+                        if (O.cb_in_smem)
+                            for (int c = 0; c < 3; ++c) red_add_shared(s_cb + O.cb_off[4] + j + c, dmu[c] * la[c]);
+                        else
+                            for (int c = 0; c < 3; ++c) atomicAdd(O.d_off + j + c, dmu[c] * la[c]);
                     }
                 } else {
                     for (int c = 0; c < 3; ++c) atomicAdd(O.d_off + n * 3 + c, dmu[c] * la[c]);
@@ -291,8 +299,10 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                 if (S.Ll > 0) {
                     for (int st = 0; st < S.Ll; ++st) {
                         const int j = (st * S.Kl + __ldg(S.idxl + (int64_t)st * S.n_anchors + a)) * 3;
-                        float* dst = O.cb_in_smem ? s_cb + O.cb_off[5] + j : O.d_l + j;
-                        for (int c = 0; c < 3; ++c) atomicAdd(dst + c, dmu[c] * oo[c]);
+                        if (O.cb_in_smem)
+                            for (int c = 0; c < 3; ++c) red_add_shared(s_cb + O.cb_off[5] + j + c, dmu[c] * oo[c]);
+                        else
+                            for (int c = 0; c < 3; ++c) atomicAdd(O.d_l + j + c, dmu[c] * oo[c]);
                     }
                 } else {
                     for (int c = 0; c < 3; ++c) atomicAdd(O.d_l + a * 3 + c, dmu[c] * oo[c]);

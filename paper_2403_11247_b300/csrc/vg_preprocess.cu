@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(SceneDev S, const __
             for (int pass = 0; pass < 4; ++pass) {
                 const uint32_t b = (key >> (8 * pass)) & 255u;
                 const uint32_t peers = __match_any_sync(vis_mask, b);
-                if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s_hist[pass * 256 + b], (uint32_t)__popc(peers));
+                if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) red_add_shared(&s_hist[pass * 256 + b], (uint32_t)__popc(peers));
             }
         }
     }

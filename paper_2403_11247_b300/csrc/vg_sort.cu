@@ -65,7 +65,7 @@ __device__ __forceinline__ uint32_t lookback_walk(const unsigned long long* lb, 
 // are combined first (one atomic per distinct bin)
 __device__ __forceinline__ void hist_add_warp(uint32_t* h, uint32_t b, uint32_t active) {
     const uint32_t peers = __match_any_sync(active, b);
-    if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicAdd(h + b, (uint32_t)__popc(peers));
+    if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) red_add_shared(h + b, (uint32_t)__popc(peers));
 }
 
 __global__ void __launch_bounds__(SORT_THREADS) onesweep_pass_kernel(
@@ -355,12 +355,12 @@ __global__ void __launch_bounds__(EMIT_CHUNK) emit_pairs_kernel(
             // keys is mostly distinct (consecutive tiles of a rect row), so
             // each lane adds its own; higher digits mostly repeat in a warp
             // and are combined first
-            if (tile_passes > 0) atomicAdd(s_hist + (key & 255u), 1u);
+            if (tile_passes > 0) red_add_shared(s_hist + (key & 255u), 1u);
             for (int p = 1; p < tile_passes; ++p) hist_add_warp(s_hist + p * 256, (key >> (8 * p)) & 255u, active);
             if (!ranges_zero) {
                 const uint32_t peers = __match_any_sync(active, key);
                 if ((uint32_t)lane == (uint32_t)(__ffs(peers) - 1)) {
-                    if (tiles_in_smem) atomicAdd(s_tiles + key, (uint32_t)__popc(peers));
+                    if (tiles_in_smem) red_add_shared(s_tiles + key, (uint32_t)__popc(peers));
                     else atomicAdd(tile_counts + key, (uint32_t)__popc(peers));
                 }
             }
