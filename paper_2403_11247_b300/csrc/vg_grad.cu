@@ -320,11 +320,11 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                     float x = pose[c];
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                    if (lane == 0) atomicAdd(s_pose + v0 * 6 + c, x);
+                    if (lane == 0) red_add_shared(s_pose + v0 * 6 + c, x);
                 }
             } else if (pv >= 0) {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) atomicAdd(s_pose + pv * 6 + c, pose[c]);
+                for (int c = 0; c < 6; ++c) red_add_shared(s_pose + pv * 6 + c, pose[c]);
             }
         }
     }

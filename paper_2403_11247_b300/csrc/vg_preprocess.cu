@@ -228,8 +228,8 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(SceneDev S, const __
             }
         }
     }
-    if (n_vis) atomicAdd(&s_cnt[0], n_vis);
-    if (n_pair) atomicAdd(&s_cnt[1], n_pair);
+    if (n_vis) red_add_shared(&s_cnt[0], n_vis);
+    if (n_pair) red_add_shared(&s_cnt[1], n_pair);
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
         uint32_t h = s_hist[i];

@@ -534,8 +534,8 @@ __global__ void __launch_bounds__(1024) ranges_kernel(uint32_t* __restrict__ cnt
             ns += __shfl_xor_sync(0xffffffffu, ns, o);
         }
         if (lane == 0) {
-            atomicAdd(&s_lf[0], c);
-            atomicAdd(&s_lf[1], ns);
+            red_add_shared(&s_lf[0], c);
+            red_add_shared(&s_lf[1], ns);
         }
     }
     uint32_t mymax = 0;
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(1024) ranges_kernel(uint32_t* __restrict__ cnt
     if (lane == 0) atomicMax(&s_max, mymax);
     __syncthreads();
     const uint32_t cmax = s_max;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_bin[order_bucket(cnt[i], cmax)], 1u);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) red_add_shared(&s_bin[order_bucket(cnt[i], cmax)], 1u);
     __syncthreads();
     if (warp == 0) {  // exclusive scan of the bucket sizes, 8 buckets per lane
         uint32_t v[ORDER_BUCKETS / 32], tot = 0;
