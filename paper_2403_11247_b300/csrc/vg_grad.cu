@@ -81,8 +81,14 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
 #pragma unroll
             for (int c = 0; c < 10; ++c) nz |= g[c] != 0.f;
             if (!nz) break;
-            float mu[3], ls[3], q[4], ol, rgb[3];
-            anchor_mean(S, n, mu);
+            // Eq. 7's offset and scaling factor, decoded once: the mean here,
+            // their own gradients at the end
+            const int64_t a = n / S.k;
+            float mu[3], ls[3], q[4], ol, rgb[3], oo[3], la[3];
+            scene_offset(S, n, oo);
+            scene_scale(S, a, la);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) mu[c] = __fadd_rn(__ldg(S.xyz + a * 3 + c), __fmul_rn(oo[c], la[c]));
             decode_attr<3>(S, 0, n, ls);
             decode_attr<4>(S, 1, n, q);
             decode_attr<1>(S, 2, n, &ol);
@@ -275,10 +281,6 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
             }
             // Eq. 7: d x_a = sum_i dmu_i, d O_i = dmu_i * l, d l = sum_i dmu_i * O_i;
             // coded O or l pass their gradient to the indexed codeword of every stage
-            const int64_t a = n / S.k;
-            float oo[3], la[3];
-            scene_offset(S, n, oo);
-            scene_scale(S, a, la);
 #pragma unroll
             for (int c = 0; c < 3; ++c)
                 if (O.d_xyz) atomicAdd(O.d_xyz + a * 3 + c, dmu[c]);
