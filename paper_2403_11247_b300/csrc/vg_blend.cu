@@ -19,9 +19,10 @@
 // against the Gaussian's alpha >= alpha_min bounding box (half extents from
 // the preprocess, widened for FP32 rounding) skips Gaussians that every
 // pixel of the warp would skip anyway; the per-pixel decisions are unchanged.
-// In the backward, lanes of a warp hold different pixels of the same
-// Gaussian: their ten partials are reduced with a fully transposing butterfly
-// (12 shuffles) and ten lanes issue the global atomics in one instruction.
+// In the backward, the walk (one pixel per lane) queues each visit's
+// per-pixel (dp, wt) in shared memory, and every 16 visits (8 at 4 pixels
+// per thread) the warp sums the queued Gaussians' ten gradient partials
+// with one Gaussian per lane pair (quad): no reduction across the warp.
 #include "vg_blend_common.cuh"
 
 namespace vgk {
@@ -279,6 +280,126 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_fwd_kernel(
     finish_items<PERSIST>(work);
 }
 
+// Backward gradient queue.  The walk keeps one pixel per lane (a pixel's
+// transmittance and its running sum B are sequential in the list), but the
+// ten per-Gaussian sums are taken with one Gaussian per lane group: each
+// visit stores its pixels' (dp, wt) = (x dL/dalpha, alpha T) in the warp's
+// queue column and the Gaussian's staged index, and every QN visits the
+// warp turns the queue around -- the LPE = 32/QN lanes of entry e each sum
+// its partials over PPL of the warp's pixels, 0-2 shuffle stages fold the
+// parts (each part keeps half of the remaining values), and every lane adds
+// its sums to the Gaussian's gradient row.  No sum crosses all 32 lanes.
+// Rows are padded by one float2, so both the column writes of the walk and
+// the row reads of the turn-around are free of bank conflicts.
+template <int PPT>
+struct BwdQueue {
+    static constexpr int NW = TILE_PIX / PPT / 32;  // warps per block
+    static constexpr int WP = 32 * PPT;             // pixels per warp
+    static constexpr int QN = PPT >= 4 ? 8 : 16;    // visits per turn-around
+    static constexpr int LPE = 32 / QN;             // lanes per queued Gaussian
+    static constexpr int PPL = WP / LPE;            // pixels each of them sums
+    static constexpr int QROW = QN + 1;             // float2 per pixel row
+    static constexpr int GROW = PPL + 1;            // float4 per part's pixel gradients
+    static constexpr size_t BYTES = (size_t)BLEND_BATCH * (3 * sizeof(float4) + sizeof(uint32_t)) +
+                                    (size_t)NW * LPE * GROW * sizeof(float4) +
+                                    (size_t)NW * WP * QROW * sizeof(float2) + (size_t)NW * QN * sizeof(uint32_t);
+};
+
+// The turn-around of one warp's queue (nq <= QN visits).  Sums, for the
+// Gaussian at mean (u, v) over the part's pixels (dx = u - px, dy = v - py),
+//   s0 = sum dp dx, s1 = sum dp dy, s2 = sum dp dx^2, s3 = sum dp dx dy,
+//   s4 = sum dp dy^2, s5 = sum dp, s6..s9 = sum wt (dC_r, dC_g, dC_b, dD);
+// then dL/du = -(a s0 + b s1), dL/dv = -(b s0 + c s1) for the natural-unit
+// inverse covariance (a, b, c), dL/d(a, b, c) = (-s2/2, -s3, -s4/2),
+// dL/do = s5 / o (dp = o e^power dL/dalpha) and the colour and depth
+// gradients s6..s9 (Eq. 16-18 in reverse).
+template <int PPT>
+__device__ __forceinline__ void bwd_turn_around(int nq, const float2* __restrict__ sq, const float4* __restrict__ sgp,
+                                                const uint32_t* __restrict__ sqi, const float4* __restrict__ s_xy,
+                                                const float4* __restrict__ s_co, const uint32_t* __restrict__ s_slot,
+                                                float X0, float Y0, float alpha_min, float* __restrict__ g2d) {
+    using Q = BwdQueue<PPT>;
+    using R = WarpRect<PPT>;
+    constexpr int ROWS = Q::PPL / R::W;
+    const int lane = threadIdx.x & 31;
+    const int e = lane % Q::QN, part = lane / Q::QN;
+    const bool valid = e < nq;
+    const uint32_t i = sqi[valid ? e : 0];
+    const float4 g = s_xy[i];
+    float dxs[R::W], dys[ROWS];
+#pragma unroll
+    for (int c = 0; c < R::W; ++c) dxs[c] = __fsub_rn(g.x, X0 + (float)c);
+    const float Yp = Y0 + (float)(part * ROWS);
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) dys[r] = __fsub_rn(g.y, Yp + (float)r);
+    const float2* q = sq + part * Q::PPL * Q::QROW + e;
+    const float4* gq = sgp + part * Q::GROW;
+    float s[10];
+#pragma unroll
+    for (int c = 0; c < 10; ++c) s[c] = 0.f;
+#pragma unroll
+    for (int jj = 0; jj < Q::PPL; ++jj) {
+        const float2 pw = q[jj * Q::QROW];
+        const float4 gp = gq[jj];
+        const float dx = dxs[jj % R::W], dy = dys[jj / R::W];
+        const float pdx = pw.x * dx, pdy = pw.x * dy;
+        s[0] += pdx;
+        s[1] += pdy;
+        s[2] = fmaf(pdx, dx, s[2]);
+        s[3] = fmaf(pdx, dy, s[3]);
+        s[4] = fmaf(pdy, dy, s[4]);
+        s[5] += pw.x;
+        s[6] = fmaf(pw.y, gp.x, s[6]);
+        s[7] = fmaf(pw.y, gp.y, s[7]);
+        s[8] = fmaf(pw.y, gp.z, s[8]);
+        s[9] = fmaf(pw.y, gp.w, s[9]);
+    }
+    // fold the parts: value v ends in the lane whose part bits select it
+    int first = 0;  // index of this lane's first kept value
+    int kept = 10;
+    if constexpr (Q::LPE >= 2) {
+        const bool h16 = (lane & 16) != 0;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const float send = h16 ? s[k] : s[k + 5];
+            const float keep = h16 ? s[k + 5] : s[k];
+            s[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+        first = h16 ? 5 : 0;
+        kept = 5;
+    }
+    if constexpr (Q::LPE >= 4) {
+        const bool h8 = (lane & 8) != 0;  // clear: values first..first+2, set: first+3, first+4
+        const float b0 = (h8 ? s[3] : s[0]) + __shfl_xor_sync(0xffffffffu, h8 ? s[0] : s[3], 8);
+        const float b1 = (h8 ? s[4] : s[1]) + __shfl_xor_sync(0xffffffffu, h8 ? s[1] : s[4], 8);
+        const float b2 = s[2] + __shfl_xor_sync(0xffffffffu, s[2], 8);  // (kept by the clear lane only)
+        s[0] = b0;
+        s[1] = b1;
+        s[2] = b2;
+        first += h8 ? 3 : 0;
+        kept = h8 ? 2 : 3;
+    }
+    if (!valid) return;
+    const float4 co = s_co[i];
+    float* row = g2d + (int64_t)s_slot[i] * G2D_STRIDE + first;
+    // natural-unit inverse covariance from the base-2 coefficients:
+    // a = -2 ln2 A2, b = -ln2 B2, c = -2 ln2 C2; 1/o = 2^thr / alpha_min
+    const float na = -2.f * LN2 * co.x, nb = -LN2 * co.y, nc = -2.f * LN2 * co.z;
+    const float inv_o = fast_exp2(co.w) / alpha_min;
+    constexpr int KMAX = Q::LPE == 1 ? 10 : Q::LPE == 2 ? 5 : 3;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        if (k < kept) {
+            const int v = first + k;
+            const float sc = (v == 2 || v == 4) ? -0.5f : v == 3 ? -1.f : v == 5 ? inv_o : 1.f;
+            float out = s[k] * sc;
+            if (k == 0 && v == 0) out = -(na * s[0] + nb * s[1]);
+            if (k == 1 && v == 1) out = -(nb * s[0] + nc * s[1]);
+            atomicAdd(row + k, out);
+        }
+    }
+}
+
 template <int PPT, bool PERSIST>
 __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     const __grid_constant__ Views V, Consts cs, uint32_t* work, const uint2* __restrict__ ranges,
@@ -288,15 +409,22 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     const float* __restrict__ Tfin, const uint32_t* __restrict__ ncontrib, const float* __restrict__ dC,
     const float* __restrict__ dD, const float* __restrict__ dS, float* __restrict__ g2d,
     unsigned long long* bwd_pairs, int count) {
-    constexpr int NT = TILE_PIX / PPT;
-    __shared__ float4 s_xy[BLEND_BATCH];
-    __shared__ float4 s_co[BLEND_BATCH];   // base-2 exponent coefficients and threshold
-    __shared__ float4 s_nat[BLEND_BATCH];  // inverse 2D covariance a, b, c and 1/opacity
-    __shared__ float4 s_cd[BLEND_BATCH];
-    __shared__ uint32_t s_slot[BLEND_BATCH];
+    using Q = BwdQueue<PPT>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4* s_xy = reinterpret_cast<float4*>(smem);
+    float4* s_co = s_xy + BLEND_BATCH;  // base-2 exponent coefficients and threshold
+    float4* s_cd = s_co + BLEND_BATCH;  // colour and depth
+    float4* s_gp = s_cd + BLEND_BATCH;  // per warp and part: the pixels' upstream colour and depth gradients
+    float2* s_q = reinterpret_cast<float2*>(s_gp + Q::NW * Q::LPE * Q::GROW);  // per warp: [pixel][visit]
+    uint32_t* s_slot = reinterpret_cast<uint32_t*>(s_q + Q::NW * Q::WP * Q::QROW);
+    uint32_t* s_qi = s_slot + BLEND_BATCH;  // per warp: staged index of each queued visit
     __shared__ uint32_t s_max;
     __shared__ uint32_t s_item;
     const uint32_t BB = (uint32_t)cs.blend_batch;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* const sgp = s_gp + warp * Q::LPE * Q::GROW;
+    float2* const sq = s_q + warp * Q::WP * Q::QROW;
+    uint32_t* const sqi = s_qi + warp * Q::QN;
 
     uint32_t ahead = (PERSIST && threadIdx.x == 0) ? atomicAdd(work, 1u) : 0u;
     for (uint32_t item = PERSIST ? 0u : blockIdx.x;
@@ -307,11 +435,9 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     const int t = gt - vi.tile_base;
     const int tx = t % vi.tiles_x, ty = t / vi.tiles_x;
     const int64_t HW = (int64_t)vi.W * vi.H, pb = vi.pix_base;
-    const int warp = threadIdx.x >> 5;
     float X0, X1, Y0, Y1;
     warp_rect<PPT>(tx, ty, warp, X0, X1, Y0, Y1);
 
-    int px[PPT], py[PPT];
     float fpx[PPT], fpy[PPT];
     uint32_t nc[PPT];
     float T[PPT], Bk[PPT], gp[PPT][5];
@@ -320,12 +446,11 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     for (int k = 0; k < PPT; ++k) {
         int lx, ly;
         pixel_of<PPT>(threadIdx.x, k, lx, ly);
-        px[k] = tx * TILE + lx;
-        py[k] = ty * TILE + ly;
-        fpx[k] = (float)px[k];
-        fpy[k] = (float)py[k];
-        const bool inside = px[k] < vi.W && py[k] < vi.H;
-        const int64_t i = (int64_t)py[k] * vi.W + px[k];
+        const int px = tx * TILE + lx, py = ty * TILE + ly;
+        fpx[k] = (float)px;
+        fpy[k] = (float)py;
+        const bool inside = px < vi.W && py < vi.H;
+        const int64_t i = (int64_t)py * vi.W + px;
         nc[k] = inside ? ncontrib[pb + i] : 0u;
         T[k] = inside ? Tfin[pb + i] : 1.f;
         Bk[k] = 0.f;
@@ -335,6 +460,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
         gp[k][3] = (inside && dD) ? dD[pb + i] : 0.f;
         gp[k][4] = (inside && dS) ? dS[pb + i] : 0.f;
         mymax = max(mymax, nc[k]);
+        const int j = lane + 32 * k;  // the pixel's row in the warp's queue
+        sgp[(j / Q::PPL) * Q::GROW + j % Q::PPL] = make_float4(gp[k][0], gp[k][1], gp[k][2], gp[k][3]);
     }
     if (count) {
         uint32_t walked = 0;
@@ -342,41 +469,31 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
         for (int k = 0; k < PPT; ++k) walked += nc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) walked += __shfl_xor_sync(0xffffffffu, walked, o);
-        if ((threadIdx.x & 31) == 0 && walked) atomicAdd(bwd_pairs, (unsigned long long)walked);
+        if (lane == 0 && walked) atomicAdd(bwd_pairs, (unsigned long long)walked);
     }
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(&s_max, mymax);
+    if (lane == 0) atomicMax(&s_max, mymax);
     __syncthreads();
     const uint2 rg = ranges[gt];
     const uint32_t end = rg.x + min(s_max, rg.y - rg.x);
     // largest list position this warp still needs
     const uint32_t warp_max = mymax;
-    // this lane's reduced value and its factor: dL/d(u, v) = -sum dp (conic d);
-    // dL/d(a, b, c) = -sum dp (dx^2/2, dx dy, dy^2/2); dL/do = sum e^power dA
-    // with e^power = x / o (the 1/o is the visited Gaussian's); the rest as summed
-    const int red_idx = reduce10_index(threadIdx.x & 31);
-    const float red_scale = (red_idx == 2 || red_idx == 4) ? -0.5f : (red_idx >= 0 && red_idx <= 3) ? -1.f : 1.f;
+    int qn = 0;  // visits in the warp's queue (warp-uniform)
 
     for (uint32_t bend = end; bend > rg.x;) {
         const uint32_t bstart = (bend - rg.x > BB) ? bend - BB : rg.x;
         __syncthreads();
-        for (int i = threadIdx.x; i < (int)(bend - bstart); i += NT) {
+        for (int i = threadIdx.x; i < (int)(bend - bstart); i += TILE_PIX / PPT) {
             const uint32_t s = pvals[bstart + i];
             s_slot[i] = s;
             s_xy[i] = xy[s];
-            const float4 co = conic_o[s];
-            s_co[i] = co;
-            // natural-unit conic and 1/opacity: a = -2 ln2 A2, b = -ln2 B2,
-            // c = -2 ln2 C2, 1/o = 2^thr / alpha_min
-            s_nat[i] = make_float4(-2.f * LN2 * co.x, -LN2 * co.y, -2.f * LN2 * co.z,
-                                   fast_exp2(co.w) / cs.alpha_min);
+            s_co[i] = conic_o[s];
             s_cd[i] = rgbd[s];
         }
         __syncthreads();
-        const int lane = threadIdx.x & 31;
         for (int c1 = (int)(bend - bstart); c1 > 0; c1 -= 32) {
             const int c0 = c1 > 32 ? c1 - 32 : 0;
             // each lane tests one Gaussian of the chunk; hits are then walked
@@ -392,19 +509,13 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
                 const uint32_t jl = bstart - rg.x + (uint32_t)i;
                 const float4 g = s_xy[i];
                 const float4 co = s_co[i];
-                const float4 nat = s_nat[i];
                 const float4 cd = s_cd[i];
-                float vals[10];
-#pragma unroll
-                for (int c = 0; c < 10; ++c) vals[c] = 0.f;
-                bool any = false;
+                float2* const qc = sq + lane * Q::QROW + qn;
                 // Branch-free per pixel: a pixel that does not blend this
                 // Gaussian (past its last contributor, positive exponent,
                 // alpha below alpha_min) gets alpha = x = 0 by select, which
-                // makes every update below an exact no-op; a pixel that
-                // blends takes exactly the arithmetic of the walk.  (Whole
-                // warps rarely skip a visited Gaussian, so branching around
-                // the update costs more in reconvergence than it saves.)
+                // makes every update an exact no-op and queues (0, 0); a
+                // pixel that blends takes exactly the arithmetic of the walk.
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     const float dx = __fsub_rn(g.x, fpx[k]), dy = __fsub_rn(g.y, fpy[k]);
@@ -420,33 +531,25 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
                     const float dA = T[k] * w - Bk[k] * inv;
                     const float wt = alpha * T[k];
                     Bk[k] = fmaf(w, wt, Bk[k]);
-                    vals[6] = fmaf(wt, gp[k][0], vals[6]);
-                    vals[7] = fmaf(wt, gp[k][1], vals[7]);
-                    vals[8] = fmaf(wt, gp[k][2], vals[8]);
-                    vals[9] = fmaf(wt, gp[k][3], vals[9]);
-                    // capped alpha is constant: no conic, mean or opacity terms.
-                    // The per-Gaussian factors (e^power = x / o, the signs and
-                    // halves of the conic terms) are applied once per visit below
-                    // (uncapped, x is alpha: dp = alpha dA = x dA, and the
-                    // opacity sum takes the same dp)
+                    // a capped alpha is constant: no conic, mean or opacity
+                    // terms; uncapped, alpha = x and dp = x dA feeds them all
                     const float xu = x <= cs.alpha_max ? x : 0.f;
-                    const float dp = xu * dA;
-                    const float pdx = dp * dx, pdy = dp * dy;
-                    vals[5] += dp;
-                    vals[0] = fmaf(nat.x, pdx, fmaf(nat.y, pdy, vals[0]));
-                    vals[1] = fmaf(nat.y, pdx, fmaf(nat.z, pdy, vals[1]));
-                    vals[2] = fmaf(pdx, dx, vals[2]);
-                    vals[3] = fmaf(pdx, dy, vals[3]);
-                    vals[4] = fmaf(pdy, dy, vals[4]);
-                    any |= live;
+                    qc[k * 32 * Q::QROW] = make_float2(xu * dA, wt);
                 }
-                if (__any_sync(0xffffffffu, any)) {
-                    const float sum = warp_reduce10(vals);
-                    if (red_idx >= 0)
-                        atomicAdd(g2d + (int64_t)s_slot[i] * G2D_STRIDE + red_idx,
-                                  sum * (red_idx == 5 ? nat.w : red_scale));
+                sqi[qn] = (uint32_t)i;
+                if (++qn == Q::QN) {
+                    __syncwarp();
+                    bwd_turn_around<PPT>(Q::QN, sq, sgp, sqi, s_xy, s_co, s_slot, X0, Y0, cs.alpha_min, g2d);
+                    qn = 0;
+                    __syncwarp();
                 }
             }
+        }
+        if (qn) {  // the queue refers to staged Gaussians: empty it before the next batch
+            __syncwarp();
+            bwd_turn_around<PPT>(qn, sq, sgp, sqi, s_xy, s_co, s_slot, X0, Y0, cs.alpha_min, g2d);
+            qn = 0;
+            __syncwarp();
         }
         bend = bstart;
     }
@@ -525,8 +628,12 @@ cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, int pers
     count_launches(1);
     const unsigned grid = blend_grid(V, persist, work);
 #define VG_BWD2(P, PE)                                                                                               \
-    blend_bwd_kernel<P, PE><<<grid, TILE_PIX / P, 0, st>>>(V, cs, work, ranges, order, pvals, xy, conic_o, rgbd, Tfin, \
-                                                           ncontrib, dC, dD, dS, g2d, bwd_pairs, count)
+    do {                                                                                                             \
+        const cudaError_t e = allow_dynamic_smem((const void*)blend_bwd_kernel<P, PE>, BwdQueue<P>::BYTES);          \
+        if (e != cudaSuccess) return e;                                                                              \
+        blend_bwd_kernel<P, PE><<<grid, TILE_PIX / P, BwdQueue<P>::BYTES, st>>>(                                     \
+            V, cs, work, ranges, order, pvals, xy, conic_o, rgbd, Tfin, ncontrib, dC, dD, dS, g2d, bwd_pairs, count); \
+    } while (0)
 #define VG_BWD(P)                                                                                                    \
     do {                                                                                                             \
         if (work) VG_BWD2(P, true); else VG_BWD2(P, false);                                                          \
