@@ -300,7 +300,9 @@ struct BwdQueue {
     static constexpr int PPL = WP / LPE;            // pixels each of them sums
     static constexpr int QROW = QN + 1;             // float2 per pixel row
     static constexpr int GROW = PPL + 1;            // float4 per part's pixel gradients
-    static constexpr size_t BYTES = (size_t)BLEND_BATCH * (3 * sizeof(float4) + sizeof(uint32_t)) +
+    static constexpr int STAGE = 128;               // Gaussians staged at a time (at most)
+    static constexpr int MINB = PPT == 1 ? 3 : PPT == 2 ? 4 : 2;  // blocks per SM the registers must allow
+    static constexpr size_t BYTES = (size_t)STAGE * (3 * sizeof(float4) + sizeof(uint32_t)) +
                                     (size_t)NW * LPE * GROW * sizeof(float4) +
                                     (size_t)NW * WP * QROW * sizeof(float2) + (size_t)NW * QN * sizeof(uint32_t);
 };
@@ -326,33 +328,40 @@ __device__ __forceinline__ void bwd_turn_around(int nq, const float2* __restrict
     const bool valid = e < nq;
     const uint32_t i = sqi[valid ? e : 0];
     const float4 g = s_xy[i];
-    float dxs[R::W], dys[ROWS];
+    float dxs[R::W];
 #pragma unroll
     for (int c = 0; c < R::W; ++c) dxs[c] = __fsub_rn(g.x, X0 + (float)c);
     const float Yp = Y0 + (float)(part * ROWS);
-#pragma unroll
-    for (int r = 0; r < ROWS; ++r) dys[r] = __fsub_rn(g.y, Yp + (float)r);
     const float2* q = sq + part * Q::PPL * Q::QROW + e;
     const float4* gq = sgp + part * Q::GROW;
     float s[10];
 #pragma unroll
     for (int c = 0; c < 10; ++c) s[c] = 0.f;
+    // a pixel row shares dy: per row, sum dp dx, dp dx^2 and dp, then fold
+    // in the dy factors once
+#pragma unroll 1
+    for (int r = 0; r < ROWS; ++r, q += R::W * Q::QROW, gq += R::W) {
+        float A = 0.f, B = 0.f, C = 0.f;
 #pragma unroll
-    for (int jj = 0; jj < Q::PPL; ++jj) {
-        const float2 pw = q[jj * Q::QROW];
-        const float4 gp = gq[jj];
-        const float dx = dxs[jj % R::W], dy = dys[jj / R::W];
-        const float pdx = pw.x * dx, pdy = pw.x * dy;
-        s[0] += pdx;
-        s[1] += pdy;
-        s[2] = fmaf(pdx, dx, s[2]);
-        s[3] = fmaf(pdx, dy, s[3]);
-        s[4] = fmaf(pdy, dy, s[4]);
-        s[5] += pw.x;
-        s[6] = fmaf(pw.y, gp.x, s[6]);
-        s[7] = fmaf(pw.y, gp.y, s[7]);
-        s[8] = fmaf(pw.y, gp.z, s[8]);
-        s[9] = fmaf(pw.y, gp.w, s[9]);
+        for (int c = 0; c < R::W; ++c) {
+            const float2 pw = q[c * Q::QROW];
+            const float4 gp = gq[c];
+            const float pdx = pw.x * dxs[c];
+            A += pdx;
+            B = fmaf(pdx, dxs[c], B);
+            C += pw.x;
+            s[6] = fmaf(pw.y, gp.x, s[6]);
+            s[7] = fmaf(pw.y, gp.y, s[7]);
+            s[8] = fmaf(pw.y, gp.z, s[8]);
+            s[9] = fmaf(pw.y, gp.w, s[9]);
+        }
+        const float dy = __fsub_rn(g.y, Yp + (float)r);
+        s[0] += A;
+        s[1] = fmaf(C, dy, s[1]);
+        s[2] += B;
+        s[3] = fmaf(A, dy, s[3]);
+        s[4] = fmaf(C * dy, dy, s[4]);
+        s[5] += C;
     }
     // fold the parts: value v ends in the lane whose part bits select it
     int first = 0;  // index of this lane's first kept value
@@ -401,7 +410,7 @@ __device__ __forceinline__ void bwd_turn_around(int nq, const float2* __restrict
 }
 
 template <int PPT, bool PERSIST>
-__global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
+__global__ void __launch_bounds__(TILE_PIX / PPT, BwdQueue<PPT>::MINB) blend_bwd_kernel(
     const __grid_constant__ Views V, Consts cs, uint32_t* work, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ order,
     const uint32_t* __restrict__ pvals,
@@ -412,15 +421,15 @@ __global__ void __launch_bounds__(TILE_PIX / PPT) blend_bwd_kernel(
     using Q = BwdQueue<PPT>;
     extern __shared__ __align__(16) unsigned char smem[];
     float4* s_xy = reinterpret_cast<float4*>(smem);
-    float4* s_co = s_xy + BLEND_BATCH;  // base-2 exponent coefficients and threshold
-    float4* s_cd = s_co + BLEND_BATCH;  // colour and depth
-    float4* s_gp = s_cd + BLEND_BATCH;  // per warp and part: the pixels' upstream colour and depth gradients
+    float4* s_co = s_xy + Q::STAGE;  // base-2 exponent coefficients and threshold
+    float4* s_cd = s_co + Q::STAGE;  // colour and depth
+    float4* s_gp = s_cd + Q::STAGE;  // per warp and part: the pixels' upstream colour and depth gradients
     float2* s_q = reinterpret_cast<float2*>(s_gp + Q::NW * Q::LPE * Q::GROW);  // per warp: [pixel][visit]
     uint32_t* s_slot = reinterpret_cast<uint32_t*>(s_q + Q::NW * Q::WP * Q::QROW);
-    uint32_t* s_qi = s_slot + BLEND_BATCH;  // per warp: staged index of each queued visit
+    uint32_t* s_qi = s_slot + Q::STAGE;  // per warp: staged index of each queued visit
     __shared__ uint32_t s_max;
     __shared__ uint32_t s_item;
-    const uint32_t BB = (uint32_t)cs.blend_batch;
+    const uint32_t BB = min((uint32_t)cs.blend_batch, (uint32_t)Q::STAGE);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* const sgp = s_gp + warp * Q::LPE * Q::GROW;
     float2* const sq = s_q + warp * Q::WP * Q::QROW;
