@@ -307,7 +307,8 @@ struct BwdQueue {
                                     (size_t)NW * WP * QROW * sizeof(float2) + (size_t)NW * QN * sizeof(uint32_t);
 };
 
-// The turn-around of one warp's queue (nq <= QN visits).  Sums, for the
+// The turn-around of one warp's queue (nq <= 32 / LPE visits, LPE lanes per
+// queued Gaussian).  Sums, for the
 // Gaussian at mean (u, v) over the part's pixels (dx = u - px, dy = v - py),
 //   s0 = sum dp dx, s1 = sum dp dy, s2 = sum dp dx^2, s3 = sum dp dx dy,
 //   s4 = sum dp dy^2, s5 = sum dp, s6..s9 = sum wt (dC_r, dC_g, dC_b, dD);
@@ -315,16 +316,19 @@ struct BwdQueue {
 // inverse covariance (a, b, c), dL/d(a, b, c) = (-s2/2, -s3, -s4/2),
 // dL/do = s5 / o (dp = o e^power dL/dalpha) and the colour and depth
 // gradients s6..s9 (Eq. 16-18 in reverse).
-template <int PPT>
+template <int PPT, int LPE>
 __device__ __forceinline__ void bwd_turn_around(int nq, const float2* __restrict__ sq, const float4* __restrict__ sgp,
                                                 const uint32_t* __restrict__ sqi, const float4* __restrict__ s_xy,
                                                 const float4* __restrict__ s_co, const uint32_t* __restrict__ s_slot,
                                                 float X0, float Y0, float alpha_min, float* __restrict__ g2d) {
     using Q = BwdQueue<PPT>;
     using R = WarpRect<PPT>;
-    constexpr int ROWS = Q::PPL / R::W;
+    constexpr int NE = 32 / LPE;     // entries this turn-around takes
+    constexpr int PPL = Q::WP / LPE;  // pixels each lane sums
+    constexpr int ROWS = PPL / R::W;
+    static_assert(LPE >= Q::LPE && LPE <= 4 && ROWS >= 1, "turn-around shape");
     const int lane = threadIdx.x & 31;
-    const int e = lane % Q::QN, part = lane / Q::QN;
+    const int e = lane % NE, part = lane / NE;
     const bool valid = e < nq;
     const uint32_t i = sqi[valid ? e : 0];
     const float4 g = s_xy[i];
@@ -332,8 +336,9 @@ __device__ __forceinline__ void bwd_turn_around(int nq, const float2* __restrict
 #pragma unroll
     for (int c = 0; c < R::W; ++c) dxs[c] = __fsub_rn(g.x, X0 + (float)c);
     const float Yp = Y0 + (float)(part * ROWS);
-    const float2* q = sq + part * Q::PPL * Q::QROW + e;
-    const float4* gq = sgp + part * Q::GROW;
+    const int j0 = part * PPL;  // the part's first pixel
+    const float2* q = sq + j0 * Q::QROW + e;
+    const float4* gq = sgp + (j0 / Q::PPL) * Q::GROW + j0 % Q::PPL;
     float s[10];
 #pragma unroll
     for (int c = 0; c < 10; ++c) s[c] = 0.f;
@@ -366,7 +371,7 @@ __device__ __forceinline__ void bwd_turn_around(int nq, const float2* __restrict
     // fold the parts: value v ends in the lane whose part bits select it
     int first = 0;  // index of this lane's first kept value
     int kept = 10;
-    if constexpr (Q::LPE >= 2) {
+    if constexpr (LPE >= 2) {
         const bool h16 = (lane & 16) != 0;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -377,7 +382,7 @@ __device__ __forceinline__ void bwd_turn_around(int nq, const float2* __restrict
         first = h16 ? 5 : 0;
         kept = 5;
     }
-    if constexpr (Q::LPE >= 4) {
+    if constexpr (LPE >= 4) {
         const bool h8 = (lane & 8) != 0;  // clear: values first..first+2, set: first+3, first+4
         const float b0 = (h8 ? s[3] : s[0]) + __shfl_xor_sync(0xffffffffu, h8 ? s[0] : s[3], 8);
         const float b1 = (h8 ? s[4] : s[1]) + __shfl_xor_sync(0xffffffffu, h8 ? s[1] : s[4], 8);
@@ -395,7 +400,7 @@ __device__ __forceinline__ void bwd_turn_around(int nq, const float2* __restrict
     // a = -2 ln2 A2, b = -ln2 B2, c = -2 ln2 C2; 1/o = 2^thr / alpha_min
     const float na = -2.f * LN2 * co.x, nb = -LN2 * co.y, nc = -2.f * LN2 * co.z;
     const float inv_o = fast_exp2(co.w) / alpha_min;
-    constexpr int KMAX = Q::LPE == 1 ? 10 : Q::LPE == 2 ? 5 : 3;
+    constexpr int KMAX = LPE == 1 ? 10 : LPE == 2 ? 5 : 3;
 #pragma unroll
     for (int k = 0; k < KMAX; ++k) {
         if (k < kept) {
@@ -447,7 +452,9 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, BwdQueue<PPT>::MINB) blend_bwd
     float X0, X1, Y0, Y1;
     warp_rect<PPT>(tx, ty, warp, X0, X1, Y0, Y1);
 
-    float fpx[PPT], fpy[PPT];
+    // a lane's pixels share their column (the warp rectangle's width divides 32)
+    static_assert(32 % WarpRect<PPT>::W == 0, "pixel columns per lane");
+    float fpx = 0.f, fpy[PPT];
     uint32_t nc[PPT];
     float T[PPT], Bk[PPT], gp[PPT][5];
     uint32_t mymax = 0;
@@ -456,7 +463,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, BwdQueue<PPT>::MINB) blend_bwd
         int lx, ly;
         pixel_of<PPT>(threadIdx.x, k, lx, ly);
         const int px = tx * TILE + lx, py = ty * TILE + ly;
-        fpx[k] = (float)px;
+        fpx = (float)px;
         fpy[k] = (float)py;
         const bool inside = px < vi.W && py < vi.H;
         const int64_t i = (int64_t)py * vi.W + px;
@@ -520,6 +527,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, BwdQueue<PPT>::MINB) blend_bwd
                 const float4 co = s_co[i];
                 const float4 cd = s_cd[i];
                 float2* const qc = sq + lane * Q::QROW + qn;
+                const float dx = __fsub_rn(g.x, fpx);
                 // Branch-free per pixel: a pixel that does not blend this
                 // Gaussian (past its last contributor, positive exponent,
                 // alpha below alpha_min) gets alpha = x = 0 by select, which
@@ -527,7 +535,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, BwdQueue<PPT>::MINB) blend_bwd
                 // pixel that blends takes exactly the arithmetic of the walk.
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    const float dx = __fsub_rn(g.x, fpx[k]), dy = __fsub_rn(g.y, fpy[k]);
+                    const float dy = __fsub_rn(g.y, fpy[k]);
                     const float p2 = gauss_p2(co.x, co.y, co.z, dx, dy);
                     const float q = __fsub_rn(p2, co.w);
                     const bool live = jl < nc[k] && !(p2 > 0.f) && !(q < 0.f);
@@ -536,7 +544,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, BwdQueue<PPT>::MINB) blend_bwd
                     const float alpha = fminf(cs.alpha_max, x);
                     const float inv = __fdividef(1.f, 1.f - alpha);  // hardware reciprocal, ~2 ulp
                     T[k] = live ? T[k] * inv : T[k];  // transmittance in front of this Gaussian
-                    const float w = gp[k][0] * cd.x + gp[k][1] * cd.y + gp[k][2] * cd.z + gp[k][3] * cd.w + gp[k][4];
+                    const float w =
+                        fmaf(gp[k][3], cd.w, fmaf(gp[k][2], cd.z, fmaf(gp[k][1], cd.y, fmaf(gp[k][0], cd.x, gp[k][4]))));
                     const float dA = T[k] * w - Bk[k] * inv;
                     const float wt = alpha * T[k];
                     Bk[k] = fmaf(w, wt, Bk[k]);
@@ -548,7 +557,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, BwdQueue<PPT>::MINB) blend_bwd
                 sqi[qn] = (uint32_t)i;
                 if (++qn == Q::QN) {
                     __syncwarp();
-                    bwd_turn_around<PPT>(Q::QN, sq, sgp, sqi, s_xy, s_co, s_slot, X0, Y0, cs.alpha_min, g2d);
+                    bwd_turn_around<PPT, Q::LPE>(Q::QN, sq, sgp, sqi, s_xy, s_co, s_slot, X0, Y0, cs.alpha_min, g2d);
                     qn = 0;
                     __syncwarp();
                 }
@@ -556,7 +565,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, BwdQueue<PPT>::MINB) blend_bwd
         }
         if (qn) {  // the queue refers to staged Gaussians: empty it before the next batch
             __syncwarp();
-            bwd_turn_around<PPT>(qn, sq, sgp, sqi, s_xy, s_co, s_slot, X0, Y0, cs.alpha_min, g2d);
+            bwd_turn_around<PPT, Q::LPE>(qn, sq, sgp, sqi, s_xy, s_co, s_slot, X0, Y0, cs.alpha_min, g2d);
             qn = 0;
             __syncwarp();
         }
