@@ -141,8 +141,8 @@ typedef struct {
  *   left (a persistent launch; the counter is back at zero after it, so a
  *   captured graph can replay it).  Same results either way.
  * ppt_fwd, ppt_bwd: pixels per thread in the forward / backward blend
- *   kernels, 1, 2 or 4 (0 = default: 1 forward, 4 backward); a 16x16 tile is
- *   one block of 256 / ppt threads.
+ *   kernels, 1, 2 or 4 (0 = default: 2); a 16x16 tile is one block of
+ *   256 / ppt threads.
  * pose_dev: optional DEVICE array [n_views][12] read instead of the
  *   cameras' T_cw (lets a captured CUDA graph follow poses updated on the
  *   device).  count_evals: accumulate evaluated (pixel, Gaussian) pairs into

@@ -500,7 +500,10 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, BwdQueue<PPT>::MINB) blend_bwd
     int qn = 0;  // visits in the warp's queue (warp-uniform)
 
     for (uint32_t bend = end; bend > rg.x;) {
-        const uint32_t bstart = (bend - rg.x > BB) ? bend - BB : rg.x;
+        // batches start at multiples of BB from the list start, and chunks
+        // at multiples of 32 from the batch start (the part-filled chunk is
+        // the first walked)
+        const uint32_t bstart = rg.x + ((bend - rg.x - 1) / BB) * BB;
         __syncthreads();
         for (int i = threadIdx.x; i < (int)(bend - bstart); i += TILE_PIX / PPT) {
             const uint32_t s = pvals[bstart + i];
@@ -510,8 +513,8 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, BwdQueue<PPT>::MINB) blend_bwd
             s_cd[i] = rgbd[s];
         }
         __syncthreads();
-        for (int c1 = (int)(bend - bstart); c1 > 0; c1 -= 32) {
-            const int c0 = c1 > 32 ? c1 - 32 : 0;
+        for (int c1 = (int)(bend - bstart); c1 > 0; c1 = (c1 - 1) & ~31) {
+            const int c0 = (c1 - 1) & ~31;
             // each lane tests one Gaussian of the chunk; hits are then walked
             // back to front (highest set bit first)
             const int il = c0 + lane;
@@ -627,8 +630,8 @@ cudaError_t launch_blend_fwd(const Views& V, const Consts& cs, int ppt, int pers
         }                                                                                                       \
     } while (0)
     if (ppt == 4) VG_FWD(4);
-    else if (ppt == 2) VG_FWD(2);
-    else VG_FWD(1);
+    else if (ppt == 1) VG_FWD(1);
+    else VG_FWD(2);
 #undef VG_FWD
 #undef VG_FWD3
 #undef VG_FWD4
@@ -657,8 +660,8 @@ cudaError_t launch_blend_bwd(const Views& V, const Consts& cs, int ppt, int pers
         if (work) VG_BWD2(P, true); else VG_BWD2(P, false);                                                          \
     } while (0)
     if (ppt == 1) VG_BWD(1);
-    else if (ppt == 2) VG_BWD(2);
-    else VG_BWD(4);
+    else if (ppt == 4) VG_BWD(4);
+    else VG_BWD(2);
 #undef VG_BWD
 #undef VG_BWD2
     return cudaGetLastError();
