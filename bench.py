@@ -114,8 +114,10 @@ def stage_rooflines(prof, K, stats, wl, hbm_gbs, alu_tflops):
                        "compaction: depth keys of every slot, 20 B per visible slot (+48 B gradient-row zeroing, "
                        "+4 B per pixel of target depth for the fused loss; global sort: 4 passes x 16 B per slot)"),
         "duplicate": (P * 8 + vis * 16 + (vis * 8 if glob else 0), "8 B per pair written, 16 B per visible slot read"),
-        "tile_sort": ((wl["tile_passes"] if glob else 1) * 16 * P + (12 * P if wl.get("long_pass") else 0),
-                      "16 B per pair per pass (scatter: one pass; long-list pass: 12 B more per pair)"),
+        "tile_sort": ((wl["tile_passes"] if glob else 1) * 16 * P + (12 * P if wl.get("long_pass") else 0) +
+                      (wl["tiles"] * 16 if not glob and not wl.get("long_pass") else 0),
+                      "16 B per pair per pass (per-tile form: one placement pass, which also writes the ranges and "
+                      "order, 16 B per tile; long-list pass: 12 B more per pair)"),
         "ranges": (wl["tiles"] * 16, "per tile count read, range and order written"),
         "loss": (wl["pixels"] * 52, "36 B read + 16 B written per pixel"),
         "pose": (4 * 6 * wl["views"] * 148, "per-block pose partials"),

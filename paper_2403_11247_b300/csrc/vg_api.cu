@@ -761,7 +761,7 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
     VG_TRY(ctx->part_total.ensure((size_t)ceil_div(slots, DUP_TILE) * 4, st, "pair partition totals"));
     VG_TRY(ctx->ranges.ensure((size_t)V.total_tiles * 8, st, "ranges"));
     VG_TRY(ctx->tile_order.ensure((size_t)V.total_tiles * 4, st, "tile order"));
-    const size_t scr_words = (size_t)(SCR_WORDS + V.total_tiles);
+    const size_t scr_words = (size_t)SCR_WORDS + 2 * (size_t)V.total_tiles;
     if (ctx->scratch.bytes < scr_words * 4) ctx->scratch_clean_words = 0;
     VG_TRY(ctx->scratch.ensure(scr_words * 4, st, "scratch"));
     VG_TRY(ctx->pose_part.ensure((size_t)n_views * 6 * 4, st, "pose sums"));
@@ -842,7 +842,14 @@ static vg_status render_forward(vg_scene* scene, const vg_camera* cams, int32_t 
                               scr, tile_sort ? 0 : tp, ctx->part_total.as<uint32_t>(), err, slots,
                               ctx->ranges.as<uint2>(), st));
     const int tgrid = sort_pass_grid(cap);
-    if (tile_sort) {
+    if (tile_sort && !long_pass && tile_place_fits(V.total_tiles)) {
+        // ranges, tile order and grouping by tile in one launch
+        VG_STAGE(VG_STAGE_TILE_SORT,
+                 launch_tile_place(ctx->pkey[0].as<uint32_t>(), ctx->pval[0].as<uint32_t>(), cap, scr,
+                                   V.total_tiles, ctx->ranges.as<uint2>(), ctx->tile_order.as<uint32_t>(), cs.lf_blk,
+                                   lf_grid, scr + SCR_LOSS_VALID, ctx->pkey[1].as<uint32_t>(),
+                                   ctx->pval[1].as<uint32_t>(), st));
+    } else if (tile_sort) {
         VG_STAGE(VG_STAGE_RANGES, launch_ranges(scr, V.total_tiles, ctx->ranges.as<uint2>(),
                                                ctx->tile_order.as<uint32_t>(), 0, cs.lf_blk, lf_grid,
                                                scr + SCR_LOSS_VALID,

@@ -278,9 +278,15 @@ __device__ __forceinline__ void scene_scale(const SceneDev& S, int64_t a, float 
     }
 }
 
+// anchor of Gaussian n (k Gaussians per anchor): a 32-bit division where n
+// fits, which costs a fraction of the 64-bit one
+__device__ __forceinline__ int64_t anchor_of(const SceneDev& S, int64_t n) {
+    return n <= 0x7fffffffll ? (int64_t)((uint32_t)n / (uint32_t)S.k) : n / S.k;
+}
+
 // Eq. 7 with the binning rounding: mu_c = xa_c + (O_c * l_c), no FMA
 __device__ __forceinline__ void anchor_mean(const SceneDev& S, int64_t n, float mu[3]) {
-    const int64_t a = n / S.k;
+    const int64_t a = anchor_of(S, n);
     float o[3], l[3];
     scene_offset(S, n, o);
     scene_scale(S, a, l);

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
             if (!nz) break;
             // Eq. 7's offset and scaling factor, decoded once: the mean here,
             // their own gradients at the end
-            const int64_t a = n / S.k;
+            const int64_t a = anchor_of(S, n);
             float mu[3], ls[3], q[4], ol, rgb[3], oo[3], la[3];
             scene_offset(S, n, oo);
             scene_scale(S, a, la);

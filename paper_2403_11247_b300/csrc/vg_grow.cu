@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) grow_stats_kernel(SceneDev S, const uint3
         if (oacc) {
             float ol;
             decode_attr<1>(S, 2, n, &ol);
-            const int64_t a = n / S.k;
+            const int64_t a = anchor_of(S, n);
             atomicAdd(oacc + a, 1.f / (1.f + expf(-ol)));
             atomicAdd(ocnt + a, 1u);
         }

@@ -18,8 +18,11 @@ constexpr int SCR_CNT_DUP = 1798;
 constexpr int SCR_CNT_TILE = 1799;     // 3 pass counters
 constexpr int SCR_LOSS_VALID = 1802;
 constexpr int SCR_N_LONG = 1804;       // tiles with lists over VG_TILE_SORT_CAP (ranges kernel)
+constexpr int SCR_PLACE_DONE = 1805;   // CTAs of the tile placement that have finished
 constexpr int SCR_WORDS = 1808;
-constexpr int SCR_TILE_COUNTS = SCR_WORDS;  // per-tile pair counts follow, [total_tiles]
+// per-tile pair counts follow, [total_tiles], then the tile placement's fill
+// counters, [total_tiles]
+constexpr int SCR_TILE_COUNTS = SCR_WORDS;
 
 // persistent state words
 constexpr int ST_EPOCH = 0;
@@ -134,6 +137,15 @@ cudaError_t launch_ranges(uint32_t* scratch, int n_tiles, uint2* ranges, uint32_
 cudaError_t launch_tile_sort_long(const uint2* ranges, const uint32_t* long_tiles, const uint32_t* n_long,
                                   uint32_t* pvals, const uint32_t* dkey, uint32_t* err, cudaStream_t st);
 cudaError_t launch_epoch_bump(uint32_t* state, uint32_t by, cudaStream_t st);
+// ranges, longest-first tile order and the grouping of the pairs by tile
+// (unordered within a tile) in one launch, from the per-tile pair counts at
+// scratch + SCR_TILE_COUNTS (which end at zero, as do the fill counters after
+// them); lf_blk / lf_counts as in launch_ranges.  For up to
+// tile_place_fits() tiles.
+bool tile_place_fits(int n_tiles);
+cudaError_t launch_tile_place(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t cap, uint32_t* scratch,
+                              int n_tiles, uint2* ranges, uint32_t* order, const uint32_t* lf_blk, int lf_grid,
+                              uint32_t* lf_counts, uint32_t* keys_out, uint32_t* vals_out, cudaStream_t st);
 // group the pairs by tile (unordered within a tile) into the ranges; counts
 // (the per-tile pair counts the ranges came from) end at zero
 cudaError_t launch_tile_scatter(const uint32_t* keys_in, const uint32_t* vals_in, const uint32_t* n_dev, uint32_t cap,

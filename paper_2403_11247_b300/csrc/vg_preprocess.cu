@@ -9,76 +9,63 @@
 
 namespace vgk {
 
-__global__ void __launch_bounds__(256, 5) preprocess_kernel(SceneDev S, const __grid_constant__ Views V, Consts cs,
-                                                         float4* __restrict__ xy, float4* __restrict__ conic_o,
-                                                         float4* __restrict__ rgbd, uint2* __restrict__ rect,
-                                                         uint32_t* __restrict__ ntiles, uint32_t* __restrict__ dkey,
-                                                         uint32_t* __restrict__ scratch, uint32_t* state,
-                                                         uint32_t* __restrict__ blk_count) {
+// One thread per Gaussian of a 256-Gaussian block in the first phase: the
+// anchor mean (Eq. 7), the mask, the near plane and a conservative reach test
+// (below) decide whether the Gaussian can touch a tile of any view; every
+// slot of a Gaussian that cannot is written culled at once.  The candidates
+// of the block are then compacted (in Gaussian order) and decoded and
+// projected by consecutive threads, so the warps that run the decode and the
+// projection are dense: with about a tenth of a scene in view, almost every
+// warp has a candidate lane, and without the compaction almost every warp
+// would run the whole path.
+constexpr int PRE_THREADS = 256;
+constexpr int LS_STAGES = 8;  // stages the log-scale bound covers
+
+__global__ void __launch_bounds__(PRE_THREADS, 4) preprocess_kernel(
+    SceneDev S, const __grid_constant__ Views V, Consts cs, float4* __restrict__ xy, float4* __restrict__ conic_o,
+    float4* __restrict__ rgbd, uint2* __restrict__ rect, uint32_t* __restrict__ ntiles, uint32_t* __restrict__ dkey,
+    uint32_t* __restrict__ scratch, uint32_t* state, uint32_t* __restrict__ blk_count) {
     __shared__ uint32_t s_hist[4 * 256];
     __shared__ uint32_t s_cnt[2];
-    constexpr int LS_STAGES = 8;            // stages the log-scale bound below covers
-    __shared__ float s_lsw[8][LS_STAGES];   // per warp, per stage: largest log-scale codebook entry
-    __shared__ float s_lsb;                 // bound on every decodable log-scale component
-    extern __shared__ float s_cb[];  // the coded groups' codebooks, group after group
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_hist[i] = 0;
-    if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0;
-    int cb_off[4];
-    {
-        int off = 0;
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            cb_off[g] = off;
-            if (S.L[g] > 0) {
-                const int sz = S.L[g] * S.K[g] * gdim(g);
-                for (int i = threadIdx.x; i < sz; i += blockDim.x) s_cb[off + i] = __ldg(S.cb[g] + i);
-                off += sz;
-            }
-        }
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) state[ST_EPOCH] += 16u;  // fresh lookback epochs for this forward
+    __shared__ uint32_t s_wn[PRE_THREADS / 32];
+    __shared__ float s_lsb;  // bound on every decodable log-scale component
+    __shared__ uint32_t s_list[PRE_THREADS];  // the block's candidates (Gaussian offsets in the block)
+    __shared__ float s_mu[PRE_THREADS * 3];   // and their means
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (cs.depth_hist)
+        for (int i = tid; i < 4 * 256; i += PRE_THREADS) s_hist[i] = 0;
+    if (tid < 2) s_cnt[tid] = 0;
+    if (blockIdx.x == 0 && tid == 0) state[ST_EPOCH] += 16u;  // fresh lookback epochs for this forward
     // the fused L1 loss's value (summed by the compositing) starts from zero
-    if (cs.lf_on && blockIdx.x == 0 && threadIdx.x == 0) *cs.lf_loss = 0.f;
-    __syncthreads();
+    if (cs.lf_on && blockIdx.x == 0 && tid == 0) *cs.lf_loss = 0.f;
     // A decoded log-scale component is a sum over stages of one codeword
     // entry each, so it is at most the sum of each stage's largest entry:
     // with that scale bound, a Gaussian whose 3-sigma box cannot reach any
     // tile of any view is culled before its attributes are decoded.  The box
     // bound uses |J|_F >= |J|_2, a 1% and 2-pixel margin covers FP32
-    // rounding, so no Gaussian the full test keeps is lost.
+    // rounding, so no Gaussian the full test keeps is lost.  (One warp
+    // computes it while the others start on their means.)
     const bool ls_bound = S.L[0] > 0 && S.L[0] <= LS_STAGES;
-    if (ls_bound) {
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, per = S.K[0] * 3;
+    if (ls_bound && warp == 0) {
+        const int per = S.K[0] * 3;
+        float tot = 0.f;
         for (int st = 0; st < S.L[0]; ++st) {
             float mx = -INFINITY;
-            for (int i = threadIdx.x; i < per; i += blockDim.x) mx = fmaxf(mx, s_cb[cb_off[0] + st * per + i]);
+            for (int i = lane; i < per; i += 32) mx = fmaxf(mx, __ldg(S.cb[0] + st * per + i));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if (lane == 0) s_lsw[w][st] = mx;
+            tot += mx;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float tot = 0.f;
-            for (int st = 0; st < S.L[0]; ++st) {
-                float mx = -INFINITY;
-                for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) mx = fmaxf(mx, s_lsw[ww][st]);
-                tot += mx;
-            }
-            s_lsb = tot;
-        }
-        __syncthreads();
+        if (lane == 0) s_lsb = tot;
     }
 
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = (int64_t)blockIdx.x * PRE_THREADS + tid;
     const bool live = n < S.N;
-    uint32_t n_vis = 0, n_pair = 0;
-    float mu[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, ol = 0.f, rgb[3] = {0, 0, 0};
-    bool active = false;
-    float RS[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // R diag(s): Sigma = RS RS^T
-    float opac = 0.f;
+    float mu[3] = {0, 0, 0};
+    bool cand = false;
     if (live) {
         anchor_mean(S, n, mu);
-        active = S.mask ? (__ldg(S.mask + n) > S.mask_thr) : true;
+        cand = S.mask ? (__ldg(S.mask + n) > S.mask_thr) : true;
         // a Gaussian behind the near plane of every view needs no attributes
         bool in_front = false;
         for (int v = 0; v < V.n && !in_front; ++v) {
@@ -87,155 +74,199 @@ __global__ void __launch_bounds__(256, 5) preprocess_kernel(SceneDev S, const __
             cam_point(T, mu, pc);
             in_front = pc[2] > V.v[v].near_plane;
         }
-        active = active && in_front;
-        if (active && ls_bound) {
-            const float smax = expf(s_lsb) * 1.001f;
-            bool reach = false;
-            for (int v = 0; v < V.n && !reach; ++v) {
-                const ViewInfo& vi = V.v[v];
-                float T[12], pc[3];
-                view_pose(V, v, T);
-                cam_point(T, mu, pc);
-                if (!(pc[2] > vi.near_plane)) continue;
-                const float iz = 1.f / pc[2];
-                float tx = pc[0] * iz, ty = pc[1] * iz;
-                const float u = vi.fx * tx + vi.cx, vv = vi.fy * ty + vi.cy;
-                if (cs.jacobian_clamp) {
-                    tx = fminf(fmaxf(tx, -vi.limx), vi.limx);
-                    ty = fminf(fmaxf(ty, -vi.limy), vi.limy);
-                }
-                const float fz = vi.fx * iz, gz = vi.fy * iz;
-                const float jf2 = fz * fz * (1.f + tx * tx) + gz * gz * (1.f + ty * ty);
-                const float r = cs.sigma_cull * sqrtf(jf2 * smax * smax + cs.dilation) * 1.01f + 2.f;
-                reach = u + r >= 0.f && u - r < (float)(vi.tiles_x * TILE) && vv + r >= 0.f &&
-                        vv - r < (float)(vi.tiles_y * TILE);
-            }
-            active = reach;
-        }
+        cand = cand && in_front;
     }
-    if (live && active) {
-        decode_attr_smem<3>(S, 0, n, s_cb + cb_off[0], ls);
-        decode_attr_smem<4>(S, 1, n, s_cb + cb_off[1], q);
-        decode_attr_smem<1>(S, 2, n, s_cb + cb_off[2], &ol);
-        decode_attr_smem<3>(S, 3, n, s_cb + cb_off[3], rgb);
-        float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-        active = active && (qq > 0.f);
-        if (active) {
-            float qn_inv = 1.f / sqrtf(qq);
-            float qn[4] = {q[0] * qn_inv, q[1] * qn_inv, q[2] * qn_inv, q[3] * qn_inv};
-            float R[3][3];
-            quat_rot(qn, R);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float sc = expf(ls[c]);
-#pragma unroll
-                for (int r = 0; r < 3; ++r) RS[r][c] = R[r][c] * sc;
-            }
-            opac = 1.f / (1.f + expf(-ol));
-        }
-    }
-    for (int v = 0; v < V.n; ++v) {
-        uint32_t key = 0xffffffffu;  // culled slots sort last
-        if (live) {
-            const int64_t slot = (int64_t)v * S.N + n;
+    __syncthreads();  // s_lsb
+    if (cand && ls_bound) {
+        const float smax = expf(s_lsb) * 1.001f;
+        bool reach = false;
+        for (int v = 0; v < V.n && !reach; ++v) {
             const ViewInfo& vi = V.v[v];
-            bool ok = active;
-            float p[3] = {0, 0, 1};
-            float u = 0, vv = 0;
-            uint32_t cnt = 0;
-            int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-            float a = 0, b = 0, c = 0, ex = -1.f, ey = -1.f;
-            if (ok) {
-                float T[12];
-                view_pose(V, v, T);
-                cam_point(T, mu, p);
-                const float z = p[2];
-                ok = z > vi.near_plane;
-                if (ok) {
-                    u = __fadd_rn(__fdiv_rn(__fmul_rn(vi.fx, p[0]), z), vi.cx);
-                    vv = __fadd_rn(__fdiv_rn(__fmul_rn(vi.fy, p[1]), z), vi.cy);
-                    float txz = p[0] / z, tyz = p[1] / z;
-                    if (cs.jacobian_clamp) {
-                        txz = fminf(fmaxf(txz, -vi.limx), vi.limx);
-                        tyz = fminf(fmaxf(tyz, -vi.limy), vi.limy);
-                    }
-                    const float J00 = vi.fx / z, J02 = -vi.fx * txz / z;
-                    const float J11 = vi.fy / z, J12 = -vi.fy * tyz / z;
-                    float A, B, C, det;
-                    cov2d(J00, J02, J11, J12, T, RS, cs.dilation, A, B, C, det);
-                    ok = det > 0.f;
-                    if (ok) {
-                        const float inv = 1.f / det;
-                        a = C * inv;
-                        b = -B * inv;
-                        c = A * inv;
-                        // half extents of the box holding every pixel with
-                        // o exp(-q/2) >= alpha_min, q = d^T conic d: the ellipse
-                        // q <= tau, tau = 2 ln(o / alpha_min), has half extents
-                        // sqrt(tau A), sqrt(tau C); widened so that FP32
-                        // rounding of a pixel's own test can never fall outside
-                        if (opac > cs.alpha_min) {
-                            const float tau = 2.f * logf(opac / cs.alpha_min) * 1.001f + 1e-3f;
-                            ex = sqrtf(tau * A) * 1.0001f + 1e-3f;
-                            ey = sqrtf(tau * C) * 1.0001f + 1e-3f;
-                        }
-                        // largest eigenvalue; mid^2 - det written as a sum of squares
-                        const float mid = 0.5f * (A + C), hd = 0.5f * (A - C);
-                        const float lam = mid + sqrtf(hd * hd + B * B);
-                        float rr = cs.sigma_cull * sqrtf(lam);
-                        int radius = (rr < (float)RADIUS_MAX) ? (int)ceilf(rr) : RADIUS_MAX;
-                        const float rf = (float)radius;
-                        const float fx0 = floorf(__fdiv_rn(__fsub_rn(u, rf), (float)TILE));
-                        const float fx1 = floorf(__fdiv_rn(__fadd_rn(u, rf), (float)TILE)) + 1.f;
-                        const float fy0 = floorf(__fdiv_rn(__fsub_rn(vv, rf), (float)TILE));
-                        const float fy1 = floorf(__fdiv_rn(__fadd_rn(vv, rf), (float)TILE)) + 1.f;
-                        x0 = (int)fminf(fmaxf(fx0, 0.f), (float)vi.tiles_x);
-                        x1 = (int)fminf(fmaxf(fx1, 0.f), (float)vi.tiles_x);
-                        y0 = (int)fminf(fmaxf(fy0, 0.f), (float)vi.tiles_y);
-                        y1 = (int)fminf(fmaxf(fy1, 0.f), (float)vi.tiles_y);
-                        ok = (x1 > x0) && (y1 > y0);
-                        cnt = ok ? (uint32_t)((x1 - x0) * (y1 - y0)) : 0u;
-                    }
-                }
+            float T[12], pc[3];
+            view_pose(V, v, T);
+            cam_point(T, mu, pc);
+            if (!(pc[2] > vi.near_plane)) continue;
+            const float iz = 1.f / pc[2];
+            float tx = pc[0] * iz, ty = pc[1] * iz;
+            const float u = vi.fx * tx + vi.cx, vv = vi.fy * ty + vi.cy;
+            if (cs.jacobian_clamp) {
+                tx = fminf(fmaxf(tx, -vi.limx), vi.limx);
+                ty = fminf(fmaxf(ty, -vi.limy), vi.limy);
             }
-            if (ok) {
-                xy[slot] = make_float4(u, vv, ex, ey);
-                // base-2 exponent coefficients and the opacity threshold
-                const float thr = opac > 0.f ? log2f(cs.alpha_min / opac) : 3.0e38f;
-                conic_o[slot] = make_float4(-0.5f * LOG2E * a, -LOG2E * b, -0.5f * LOG2E * c, thr);
-                rgbd[slot] = make_float4(rgb[0], rgb[1], rgb[2], p[2]);
-                rect[slot] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
-                ntiles[slot] = cnt;
-                key = __float_as_uint(p[2]);
-                dkey[slot] = key;
-                ++n_vis;
-                n_pair += cnt;
-                if (cs.seen) cs.seen[n] = 1u;
-            } else {
-                ntiles[slot] = 0u;
-                dkey[slot] = 0xffffffffu;
+            const float fz = vi.fx * iz, gz = vi.fy * iz;
+            const float jf2 = fz * fz * (1.f + tx * tx) + gz * gz * (1.f + ty * ty);
+            const float r = cs.sigma_cull * sqrtf(jf2 * smax * smax + cs.dilation) * 1.01f + 2.f;
+            reach = u + r >= 0.f && u - r < (float)(vi.tiles_x * TILE) && vv + r >= 0.f &&
+                    vv - r < (float)(vi.tiles_y * TILE);
+        }
+        cand = reach;
+    }
+    if (live && !cand)
+        for (int v = 0; v < V.n; ++v) {
+            const int64_t slot = (int64_t)v * S.N + n;
+            ntiles[slot] = 0u;
+            dkey[slot] = 0xffffffffu;  // culled slots sort last
+        }
+    // compaction of the candidates, in Gaussian order
+    const uint32_t bal = __ballot_sync(0xffffffffu, cand);
+    if (lane == 0) s_wn[warp] = (uint32_t)__popc(bal);
+    __syncthreads();
+    uint32_t pos = (uint32_t)__popc(bal & lanemask_lt()), n_cand = 0;
+#pragma unroll
+    for (int w = 0; w < PRE_THREADS / 32; ++w) {
+        const uint32_t c = s_wn[w];
+        pos += w < warp ? c : 0u;
+        n_cand += c;
+    }
+    if (cand) {
+        s_list[pos] = (uint32_t)tid;
+        s_mu[3 * pos] = mu[0];
+        s_mu[3 * pos + 1] = mu[1];
+        s_mu[3 * pos + 2] = mu[2];
+    }
+    __syncthreads();
+
+    uint32_t n_vis = 0, n_pair = 0;
+    // (a uniform loop: every lane of a warp takes part in its warp votes)
+    for (uint32_t j0 = 0; j0 < n_cand; j0 += PRE_THREADS) {
+        const uint32_t j = j0 + (uint32_t)tid;
+        const bool valid = j < n_cand;
+        const int64_t g = valid ? (int64_t)blockIdx.x * PRE_THREADS + s_list[j] : 0;
+        float gm[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, ol = 0.f, rgb[3] = {0, 0, 0};
+        float RS[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // R diag(s): Sigma = RS RS^T
+        float opac = 0.f;
+        bool active = valid;
+        if (valid) {
+            gm[0] = s_mu[3 * j];
+            gm[1] = s_mu[3 * j + 1];
+            gm[2] = s_mu[3 * j + 2];
+            decode_attr<3>(S, 0, g, ls);
+            decode_attr<4>(S, 1, g, q);
+            decode_attr<1>(S, 2, g, &ol);
+            decode_attr<3>(S, 3, g, rgb);
+            const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+            active = qq > 0.f;
+            if (active) {
+                const float qn_inv = 1.f / sqrtf(qq);
+                const float qn[4] = {q[0] * qn_inv, q[1] * qn_inv, q[2] * qn_inv, q[3] * qn_inv};
+                float R[3][3];
+                quat_rot(qn, R);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float sc = expf(ls[c]);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) RS[r][c] = R[r][c] * sc;
+                }
+                opac = 1.f / (1.f + expf(-ol));
             }
         }
-        // depth-key digit histograms of the visible slots; most lanes share
-        // the high digits
-        const uint32_t vis_mask = __ballot_sync(0xffffffffu, live && key != 0xffffffffu);
-        if (cs.depth_hist && live && key != 0xffffffffu) {
+        for (int v = 0; v < V.n; ++v) {
+            uint32_t key = 0xffffffffu;
+            if (valid) {
+                const int64_t slot = (int64_t)v * S.N + g;
+                const ViewInfo& vi = V.v[v];
+                bool ok = active;
+                float p[3] = {0, 0, 1};
+                float u = 0, vv = 0;
+                uint32_t cnt = 0;
+                int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+                float a = 0, b = 0, c = 0, ex = -1.f, ey = -1.f;
+                if (ok) {
+                    float T[12];
+                    view_pose(V, v, T);
+                    cam_point(T, gm, p);
+                    const float z = p[2];
+                    ok = z > vi.near_plane;
+                    if (ok) {
+                        u = __fadd_rn(__fdiv_rn(__fmul_rn(vi.fx, p[0]), z), vi.cx);
+                        vv = __fadd_rn(__fdiv_rn(__fmul_rn(vi.fy, p[1]), z), vi.cy);
+                        float txz = p[0] / z, tyz = p[1] / z;
+                        if (cs.jacobian_clamp) {
+                            txz = fminf(fmaxf(txz, -vi.limx), vi.limx);
+                            tyz = fminf(fmaxf(tyz, -vi.limy), vi.limy);
+                        }
+                        const float J00 = vi.fx / z, J02 = -vi.fx * txz / z;
+                        const float J11 = vi.fy / z, J12 = -vi.fy * tyz / z;
+                        float A, B, C, det;
+                        cov2d(J00, J02, J11, J12, T, RS, cs.dilation, A, B, C, det);
+                        ok = det > 0.f;
+                        if (ok) {
+                            const float inv = 1.f / det;
+                            a = C * inv;
+                            b = -B * inv;
+                            c = A * inv;
+                            // half extents of the box holding every pixel with
+                            // o exp(-q/2) >= alpha_min, q = d^T conic d: the
+                            // ellipse q <= tau, tau = 2 ln(o / alpha_min), has
+                            // half extents sqrt(tau A), sqrt(tau C); widened so
+                            // that FP32 rounding of a pixel's own test can never
+                            // fall outside
+                            if (opac > cs.alpha_min) {
+                                const float tau = 2.f * logf(opac / cs.alpha_min) * 1.001f + 1e-3f;
+                                ex = sqrtf(tau * A) * 1.0001f + 1e-3f;
+                                ey = sqrtf(tau * C) * 1.0001f + 1e-3f;
+                            }
+                            // largest eigenvalue; mid^2 - det written as a sum of squares
+                            const float mid = 0.5f * (A + C), hd = 0.5f * (A - C);
+                            const float lam = mid + sqrtf(hd * hd + B * B);
+                            const float rr = cs.sigma_cull * sqrtf(lam);
+                            const int radius = (rr < (float)RADIUS_MAX) ? (int)ceilf(rr) : RADIUS_MAX;
+                            const float rf = (float)radius;
+                            const float fx0 = floorf(__fdiv_rn(__fsub_rn(u, rf), (float)TILE));
+                            const float fx1 = floorf(__fdiv_rn(__fadd_rn(u, rf), (float)TILE)) + 1.f;
+                            const float fy0 = floorf(__fdiv_rn(__fsub_rn(vv, rf), (float)TILE));
+                            const float fy1 = floorf(__fdiv_rn(__fadd_rn(vv, rf), (float)TILE)) + 1.f;
+                            x0 = (int)fminf(fmaxf(fx0, 0.f), (float)vi.tiles_x);
+                            x1 = (int)fminf(fmaxf(fx1, 0.f), (float)vi.tiles_x);
+                            y0 = (int)fminf(fmaxf(fy0, 0.f), (float)vi.tiles_y);
+                            y1 = (int)fminf(fmaxf(fy1, 0.f), (float)vi.tiles_y);
+                            ok = (x1 > x0) && (y1 > y0);
+                            cnt = ok ? (uint32_t)((x1 - x0) * (y1 - y0)) : 0u;
+                        }
+                    }
+                }
+                if (ok) {
+                    xy[slot] = make_float4(u, vv, ex, ey);
+                    // base-2 exponent coefficients and the opacity threshold
+                    const float thr = opac > 0.f ? log2f(cs.alpha_min / opac) : 3.0e38f;
+                    conic_o[slot] = make_float4(-0.5f * LOG2E * a, -LOG2E * b, -0.5f * LOG2E * c, thr);
+                    rgbd[slot] = make_float4(rgb[0], rgb[1], rgb[2], p[2]);
+                    rect[slot] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+                    ntiles[slot] = cnt;
+                    key = __float_as_uint(p[2]);
+                    dkey[slot] = key;
+                    ++n_vis;
+                    n_pair += cnt;
+                    if (cs.seen) cs.seen[g] = 1u;
+                } else {
+                    ntiles[slot] = 0u;
+                    dkey[slot] = 0xffffffffu;
+                }
+            }
+            // depth-key digit histograms of the visible slots; most lanes share
+            // the high digits
+            if (cs.depth_hist) {
+                const uint32_t vis_mask = __ballot_sync(0xffffffffu, key != 0xffffffffu);
+                if (key != 0xffffffffu) {
 #pragma unroll
-            for (int pass = 0; pass < 4; ++pass) {
-                const uint32_t b = (key >> (8 * pass)) & 255u;
-                const uint32_t peers = __match_any_sync(vis_mask, b);
-                if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) red_add_shared(&s_hist[pass * 256 + b], (uint32_t)__popc(peers));
+                    for (int pass = 0; pass < 4; ++pass) {
+                        const uint32_t bk = (key >> (8 * pass)) & 255u;
+                        const uint32_t peers = __match_any_sync(vis_mask, bk);
+                        if (lane == __ffs(peers) - 1) red_add_shared(&s_hist[pass * 256 + bk], (uint32_t)__popc(peers));
+                    }
+                }
             }
         }
     }
     if (n_vis) red_add_shared(&s_cnt[0], n_vis);
     if (n_pair) red_add_shared(&s_cnt[1], n_pair);
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
-        uint32_t h = s_hist[i];
-        if (h) atomicAdd(scratch + SCR_DEPTH_HIST + i, h);
-    }
-    if (threadIdx.x == 0) {
+    if (cs.depth_hist)
+        for (int i = tid; i < 4 * 256; i += PRE_THREADS) {
+            const uint32_t h = s_hist[i];
+            if (h) atomicAdd(scratch + SCR_DEPTH_HIST + i, h);
+        }
+    if (tid == 0) {
         blk_count[blockIdx.x] = s_cnt[0];
         blk_count[gridDim.x + blockIdx.x] = s_cnt[1];  // the block's (slot, tile) pairs
     }
@@ -356,7 +387,7 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
     }
 }
 
-int preprocess_blocks(int64_t N) { return (int)ceil_div(N > 0 ? N : 1, 256); }
+int preprocess_blocks(int64_t N) { return (int)ceil_div(N > 0 ? N : 1, PRE_THREADS); }
 
 
 // with the fused loss the compaction grid counts its normalisers too: a
@@ -368,23 +399,13 @@ int compact_grid(int64_t N, const Consts& cs) {
 
 
 
-static size_t codebook_smem(const SceneDev& S) {
-    size_t n = 0;
-    for (int g = 0; g < 4; ++g)
-        if (S.L[g] > 0) n += (size_t)S.L[g] * S.K[g] * gdim(g);
-    return n * sizeof(float);
-}
-
 cudaError_t launch_preprocess(const SceneDev& S, const Views& V, const Consts& cs, float4* xy, float4* conic_o,
                               float4* rgbd, uint2* rect, uint32_t* ntiles, uint32_t* dkey, uint32_t* scratch,
                               uint32_t* state, uint32_t* blk_count, cudaStream_t st) {
     const int blocks = preprocess_blocks(S.N);
-    const size_t smem = codebook_smem(S);
-    cudaError_t e = allow_dynamic_smem((const void*)preprocess_kernel, smem);
-    if (e != cudaSuccess) return e;
     count_launches(1);
-    preprocess_kernel<<<(unsigned)blocks, 256, smem, st>>>(S, V, cs, xy, conic_o, rgbd, rect, ntiles, dkey, scratch,
-                                                           state, blk_count);
+    preprocess_kernel<<<(unsigned)blocks, PRE_THREADS, 0, st>>>(S, V, cs, xy, conic_o, rgbd, rect, ntiles, dkey,
+                                                                scratch, state, blk_count);
     return cudaGetLastError();
 }
 
