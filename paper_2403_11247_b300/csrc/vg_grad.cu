@@ -77,22 +77,26 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                 g[4] = r1.x; g[5] = r1.y; g[6] = r1.z; g[7] = r1.w;
                 g[8] = r2.x; g[9] = r2.y; g[10] = r2.z; g[11] = r2.w;
             }
-            bool nz = false;
-#pragma unroll
-            for (int c = 0; c < 10; ++c) nz |= g[c] != 0.f;
-            if (!nz) break;
             // Eq. 7's offset and scaling factor, decoded once: the mean here,
-            // their own gradients at the end
+            // their own gradients at the end.  Every load of the slot's
+            // attributes goes out before the row is tested, so that they
+            // overlap the row's round trip instead of following it; the codes
+            // stay in registers for the codebook gradients.
             const int64_t a = anchor_of(S, n);
             float mu[3], ls[3], q[4], ol, rgb[3], oo[3], la[3];
+            uint32_t kp[4][DECODE_STAGES / 4];
             scene_offset(S, n, oo);
             scene_scale(S, a, la);
 #pragma unroll
             for (int c = 0; c < 3; ++c) mu[c] = __fadd_rn(__ldg(S.xyz + a * 3 + c), __fmul_rn(oo[c], la[c]));
-            decode_attr<3>(S, 0, n, ls);
-            decode_attr<4>(S, 1, n, q);
-            decode_attr<1>(S, 2, n, &ol);
-            decode_attr<3>(S, 3, n, rgb);
+            decode_attr_codes<3>(S, 0, n, ls, kp[0]);
+            decode_attr_codes<4>(S, 1, n, q, kp[1]);
+            decode_attr_codes<1>(S, 2, n, &ol, kp[2]);
+            decode_attr_codes<3>(S, 3, n, rgb, kp[3]);
+            bool nz = false;
+#pragma unroll
+            for (int c = 0; c < 10; ++c) nz |= g[c] != 0.f;
+            if (!nz) break;
             const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
             if (!(qq > 0.f)) break;
             // one reciprocal per slot for every quotient by |q| and by z below;
@@ -256,8 +260,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                 const int d = gdim(gi);
                 if (S.L[gi] > 0) {
                     if (!O.cb[gi]) continue;
-                    for (int st = 0; st < S.L[gi]; ++st) {
-                        const int k = __ldg(S.idx[gi] + (int64_t)st * S.N + n);
+                    auto add_cw = [&](int st, int k) {
                         const int j = (st * S.K[gi] + k) * d;
                         if (O.cb_in_smem) {
 #pragma unroll
@@ -268,7 +271,12 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                             for (int c = 0; c < dmax; ++c)
                                 if (c < d) atomicAdd(O.cb[gi] + j + c, gval(gi, c));
                         }
-                    }
+                    };
+#pragma unroll
+                    for (int st = 0; st < DECODE_STAGES; ++st)
+                        if (st < S.L[gi]) add_cw(st, (int)code_at(kp[gi], st));
+                    for (int st = DECODE_STAGES; st < S.L[gi]; ++st)
+                        add_cw(st, __ldg(S.idx[gi] + (int64_t)st * S.N + n));
                 } else if (O.raw[gi]) {
 #pragma unroll
                     for (int c = 0; c < dmax; ++c)

@@ -21,14 +21,13 @@ namespace vgk {
 constexpr int PRE_THREADS = 256;
 constexpr int LS_STAGES = 8;  // stages the log-scale bound covers
 
-__global__ void __launch_bounds__(PRE_THREADS, 4) preprocess_kernel(
+__global__ void __launch_bounds__(PRE_THREADS, 5) preprocess_kernel(
     SceneDev S, const __grid_constant__ Views V, Consts cs, float4* __restrict__ xy, float4* __restrict__ conic_o,
     float4* __restrict__ rgbd, uint2* __restrict__ rect, uint32_t* __restrict__ ntiles, uint32_t* __restrict__ dkey,
     uint32_t* __restrict__ scratch, uint32_t* state, uint32_t* __restrict__ blk_count) {
     __shared__ uint32_t s_hist[4 * 256];
     __shared__ uint32_t s_cnt[2];
     __shared__ uint32_t s_wn[PRE_THREADS / 32];
-    __shared__ float s_lsb;  // bound on every decodable log-scale component
     __shared__ uint32_t s_list[PRE_THREADS];  // the block's candidates (Gaussian offsets in the block)
     __shared__ float s_mu[PRE_THREADS * 3];   // and their means
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -43,20 +42,28 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) preprocess_kernel(
     // with that scale bound, a Gaussian whose 3-sigma box cannot reach any
     // tile of any view is culled before its attributes are decoded.  The box
     // bound uses |J|_F >= |J|_2, a 1% and 2-pixel margin covers FP32
-    // rounding, so no Gaussian the full test keeps is lost.  (One warp
-    // computes it while the others start on their means.)
+    // rounding, so no Gaussian the full test keeps is lost.  Every warp
+    // computes the bound itself (its loads go out with the lanes' own), so
+    // that no warp waits for another before its reach test.
     const bool ls_bound = S.L[0] > 0 && S.L[0] <= LS_STAGES;
-    if (ls_bound && warp == 0) {
+    float lsb = 0.f;
+    if (ls_bound) {
         const int per = S.K[0] * 3;
-        float tot = 0.f;
-        for (int st = 0; st < S.L[0]; ++st) {
-            float mx = -INFINITY;
-            for (int i = lane; i < per; i += 32) mx = fmaxf(mx, __ldg(S.cb[0] + st * per + i));
+        float mx[LS_STAGES];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            tot += mx;
+        for (int st = 0; st < LS_STAGES; ++st) {
+            mx[st] = -INFINITY;
+            if (st < S.L[0])
+#pragma unroll 2
+                for (int i = lane; i < per; i += 32) mx[st] = fmaxf(mx[st], __ldg(S.cb[0] + st * per + i));
         }
-        if (lane == 0) s_lsb = tot;
+#pragma unroll
+        for (int st = 0; st < LS_STAGES; ++st)
+            if (st < S.L[0]) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mx[st] = fmaxf(mx[st], __shfl_xor_sync(0xffffffffu, mx[st], o));
+                lsb += mx[st];
+            }
     }
 
     const int64_t n = (int64_t)blockIdx.x * PRE_THREADS + tid;
@@ -65,27 +72,21 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) preprocess_kernel(
     bool cand = false;
     if (live) {
         anchor_mean(S, n, mu);
-        cand = S.mask ? (__ldg(S.mask + n) > S.mask_thr) : true;
-        // a Gaussian behind the near plane of every view needs no attributes
-        bool in_front = false;
-        for (int v = 0; v < V.n && !in_front; ++v) {
-            float T[12], pc[3];
-            view_pose(V, v, T);
-            cam_point(T, mu, pc);
-            in_front = pc[2] > V.v[v].near_plane;
-        }
-        cand = cand && in_front;
-    }
-    __syncthreads();  // s_lsb
-    if (cand && ls_bound) {
-        const float smax = expf(s_lsb) * 1.001f;
-        bool reach = false;
-        for (int v = 0; v < V.n && !reach; ++v) {
+        const bool on = S.mask ? (__ldg(S.mask + n) > S.mask_thr) : true;
+        // a candidate lies in front of the near plane of some view and (with
+        // the scale bound) its widest possible 3-sigma box reaches a tile of
+        // that view
+        const float smax = ls_bound ? expf(lsb) * 1.001f : 0.f;
+        for (int v = 0; v < V.n && on && !cand; ++v) {
             const ViewInfo& vi = V.v[v];
             float T[12], pc[3];
             view_pose(V, v, T);
             cam_point(T, mu, pc);
             if (!(pc[2] > vi.near_plane)) continue;
+            if (!ls_bound) {
+                cand = true;
+                break;
+            }
             const float iz = 1.f / pc[2];
             float tx = pc[0] * iz, ty = pc[1] * iz;
             const float u = vi.fx * tx + vi.cx, vv = vi.fy * ty + vi.cy;
@@ -96,10 +97,9 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) preprocess_kernel(
             const float fz = vi.fx * iz, gz = vi.fy * iz;
             const float jf2 = fz * fz * (1.f + tx * tx) + gz * gz * (1.f + ty * ty);
             const float r = cs.sigma_cull * sqrtf(jf2 * smax * smax + cs.dilation) * 1.01f + 2.f;
-            reach = u + r >= 0.f && u - r < (float)(vi.tiles_x * TILE) && vv + r >= 0.f &&
-                    vv - r < (float)(vi.tiles_y * TILE);
+            cand = u + r >= 0.f && u - r < (float)(vi.tiles_x * TILE) && vv + r >= 0.f &&
+                   vv - r < (float)(vi.tiles_y * TILE);
         }
-        cand = reach;
     }
     if (live && !cand)
         for (int v = 0; v < V.n; ++v) {

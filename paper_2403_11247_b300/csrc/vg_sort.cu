@@ -674,24 +674,22 @@ cudaError_t launch_tile_scatter(const uint32_t* keys_in, const uint32_t* vals_in
 // per-tile ranges, the longest-first tile order and the grouping of the pairs
 // by tile in one launch (per-tile sort without the long-list pass, up to
 // PLACE_SMEM_TILES tiles).  Every CTA scans the per-tile pair counts itself (a
-// few thousand words from L2) into a shared-memory copy of the tile starts;
-// CTA b writes the ranges and the order entries of its own stretch of tiles
-// [n b / G, n (b + 1) / G), placing each tile after the tiles of its
-// length bucket that lie in front of the stretch (every CTA counts those from
-// the same counts, so the stretches fill disjoint positions); then it places
-// its share of the pairs: a pair claims a free position of its tile's range
-// by counting the tile's fill counter up (one atomic per run of equal tiles
-// in a warp, several pairs per thread in flight).  The last CTA out puts the
-// counts, the fill counters and its exit counter back to zero for the next
-// forward.  The one-CTA scan launch and the separate scatter launch are gone.
+// few thousand words from L2) into a shared-memory copy of the tile starts.
+// CTA 0 then writes the ranges, the order (longest lists first: 256 buckets
+// of list length, descending, any order within a bucket) and the fused
+// loss's normalisers; the other CTAs place the pairs: a pair claims a free
+// position of its tile's range by counting the tile's fill counter up (one
+// atomic per run of equal tiles in a warp, several pairs per thread in
+// flight).  The last CTA out puts the counts, the fill counters and its exit
+// counter back to zero for the next forward.  This replaces a one-CTA scan
+// launch followed by a separate scatter launch.
 // ---------------------------------------------------------------------------
 constexpr int PLACE_THREADS = 512;
 constexpr int PLACE_ITEMS = 4;
 constexpr int PLACE_SMEM_TILES = 16384;
 
 // length bucket of a tile list: 0 for the longest, ORDER_BUCKETS - 1 for
-// empty ones (any monotone rule works; every CTA evaluates the same FP32
-// expression on the same inputs, so all CTAs agree)
+// empty ones
 __device__ __forceinline__ int place_bucket(uint32_t c, float scale) {
     return ORDER_BUCKETS - 1 - min(ORDER_BUCKETS - 1, (int)((float)c * scale));
 }
@@ -702,14 +700,17 @@ __global__ void __launch_bounds__(PLACE_THREADS) tile_place_kernel(
     uint32_t* __restrict__ lf_counts, uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out) {
     extern __shared__ uint32_t s_start[];  // [n + 1]: exclusive scan of the tile counts, the total last
     __shared__ uint32_t s_w[PLACE_THREADS / 32], s_w2[PLACE_THREADS / 32];
-    __shared__ uint32_t s_bin[ORDER_BUCKETS], s_cur[ORDER_BUCKETS];
+    __shared__ uint32_t s_bin[ORDER_BUCKETS];
     __shared__ uint32_t s_max, s_last;
     uint32_t* const cnt_g = scratch + SCR_TILE_COUNTS;
     uint32_t* const fill = cnt_g + n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool lead = blockIdx.x == 0;  // the CTA that writes ranges and order
     for (int i = tid; i < n; i += PLACE_THREADS) s_start[i] = cnt_g[i];
-    for (int i = tid; i < ORDER_BUCKETS; i += PLACE_THREADS) s_bin[i] = s_cur[i] = 0u;
-    if (tid == 0) s_max = 0u;
+    if (lead) {
+        for (int i = tid; i < ORDER_BUCKETS; i += PLACE_THREADS) s_bin[i] = 0u;
+        if (tid == 0) s_max = 0u;
+    }
     __syncthreads();
     // each thread scans a contiguous stretch of the counts
     const int per = (n + PLACE_THREADS - 1) / PLACE_THREADS;
@@ -725,10 +726,13 @@ __global__ void __launch_bounds__(PLACE_THREADS) tile_place_kernel(
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += y;
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
     if (lane == 31) s_w[warp] = inc;
-    if (lane == 0) atomicMax(&s_max, mx);
+    if (lead) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) atomicMax(&s_max, mx);
+    }
     __syncthreads();
     uint32_t run = inc - sum;
     for (int w = 0; w < warp; ++w) run += s_w[w];
@@ -739,98 +743,113 @@ __global__ void __launch_bounds__(PLACE_THREADS) tile_place_kernel(
     }
     if (tid == PLACE_THREADS - 1) s_start[n] = run;  // (the last stretch ends at n)
     __syncthreads();
-    // order: bucket sizes over all tiles, and over the tiles in front of
-    // this CTA's stretch
-    const uint32_t cmax = s_max;
-    const float scale = cmax > 0u ? (float)(ORDER_BUCKETS - 1) / (float)cmax : 0.f;
-    const int lo = (int)(((int64_t)n * blockIdx.x) / gridDim.x);
-    const int hi = (int)(((int64_t)n * (blockIdx.x + 1)) / gridDim.x);
-    for (int i = tid; i < n; i += PLACE_THREADS) {
-        const int b = place_bucket(s_start[i + 1] - s_start[i], scale);
-        red_add_shared(&s_bin[b], 1u);
-        if (i < lo) red_add_shared(&s_cur[b], 1u);
-    }
-    __syncthreads();
-    if (warp == 0) {  // s_cur[b] += start of bucket b (exclusive scan, 8 buckets per lane)
-        constexpr int BPL = ORDER_BUCKETS / 32;
-        uint32_t v[BPL], tot = 0u;
-#pragma unroll
-        for (int k = 0; k < BPL; ++k) {
-            v[k] = s_bin[lane * BPL + k];
-            tot += v[k];
-        }
-        uint32_t bi = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, bi, o);
-            if (lane >= o) bi += y;
-        }
-        uint32_t r = bi - tot;
-#pragma unroll
-        for (int k = 0; k < BPL; ++k) {
-            s_cur[lane * BPL + k] += r;
-            r += v[k];
-        }
-    }
-    __syncthreads();
-    for (int i = lo + tid; i < hi; i += PLACE_THREADS) {
-        const uint32_t s0 = s_start[i], s1 = s_start[i + 1];
-        ranges[i] = make_uint2(s0, s1);
-        order[atomicAdd(&s_cur[place_bucket(s1 - s0, scale)], 1u)] = (uint32_t)i;
-    }
-    if (lf_blk && blockIdx.x == 0) {  // the fused loss's normalisers from the compaction's per-block counts
-        uint32_t c = 0u, ns = 0u;
-        for (int i = tid; i < lf_grid; i += PLACE_THREADS) {
-            c += lf_blk[i];
-            ns += lf_blk[lf_grid + i];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            c += __shfl_xor_sync(0xffffffffu, c, o);
-            ns += __shfl_xor_sync(0xffffffffu, ns, o);
-        }
-        if (lane == 0) {
-            s_w[warp] = c;
-            s_w2[warp] = ns;
+
+    if (lead) {
+        const uint32_t cmax = s_max;
+        const float scale = cmax > 0u ? (float)(ORDER_BUCKETS - 1) / (float)cmax : 0.f;
+        // bucket sizes; the lanes of a warp that share a bucket add once
+        // (a uniform loop: every lane takes part in the vote)
+        for (int i0b = 0; i0b < n; i0b += PLACE_THREADS) {
+            const int i = i0b + tid;
+            const int b = i < n ? place_bucket(s_start[i + 1] - s_start[i], scale) : -1;
+            const uint32_t peers = __match_any_sync(0xffffffffu, b);
+            if (b >= 0 && lane == __ffs(peers) - 1) red_add_shared(&s_bin[b], (uint32_t)__popc(peers));
         }
         __syncthreads();
-        if (tid == 0) {
-            uint32_t a = 0u, b = 0u;
-            for (int w = 0; w < PLACE_THREADS / 32; ++w) {
-                a += s_w[w];
-                b += s_w2[w];
+        if (warp == 0) {  // exclusive scan of the bucket sizes, 8 buckets per lane
+            constexpr int BPL = ORDER_BUCKETS / 32;
+            uint32_t v[BPL], tot = 0u;
+#pragma unroll
+            for (int k = 0; k < BPL; ++k) {
+                v[k] = s_bin[lane * BPL + k];
+                tot += v[k];
             }
-            lf_counts[0] = a;
-            lf_counts[1] = b;
-        }
-    }
-    // the pairs: PLACE_ITEMS per thread per round, their claims in flight together
-    const uint32_t P = min(scratch[SCR_PAIRS], cap);
-    const uint32_t lt = lanemask_lt();
-    const uint32_t span = (uint32_t)PLACE_THREADS * PLACE_ITEMS;
-    for (uint32_t base = blockIdx.x * span; base < P; base += gridDim.x * span) {
-        uint32_t key[PLACE_ITEMS], val[PLACE_ITEMS], peers[PLACE_ITEMS], old[PLACE_ITEMS];
+            uint32_t bi = tot;
 #pragma unroll
-        for (int k = 0; k < PLACE_ITEMS; ++k) {
-            const uint32_t e = base + (uint32_t)(k * PLACE_THREADS + tid);
-            key[k] = e < P ? keys_in[e] : 0xffffffffu;
-            val[k] = e < P ? vals_in[e] : 0u;
-        }
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, bi, o);
+                if (lane >= o) bi += y;
+            }
+            uint32_t r = bi - tot;
 #pragma unroll
-        for (int k = 0; k < PLACE_ITEMS; ++k) {
-            peers[k] = __match_any_sync(0xffffffffu, key[k]);
-            old[k] = 0u;
-            if (key[k] < (uint32_t)n && lane == __ffs(peers[k]) - 1)
-                old[k] = atomicAdd(fill + key[k], (uint32_t)__popc(peers[k]));
+            for (int k = 0; k < BPL; ++k) {
+                s_bin[lane * BPL + k] = r;
+                r += v[k];
+            }
         }
+        __syncthreads();
+        for (int i0b = 0; i0b < n; i0b += PLACE_THREADS) {
+            const int i = i0b + tid;
+            uint32_t s0 = 0u, s1 = 0u;
+            int b = -1;
+            if (i < n) {
+                s0 = s_start[i];
+                s1 = s_start[i + 1];
+                ranges[i] = make_uint2(s0, s1);
+                b = place_bucket(s1 - s0, scale);
+            }
+            const uint32_t peers = __match_any_sync(0xffffffffu, b);
+            const int leader = __ffs(peers) - 1;
+            uint32_t at = 0u;
+            if (b >= 0 && lane == leader) at = atomicAdd(&s_bin[b], (uint32_t)__popc(peers));
+            at = __shfl_sync(0xffffffffu, at, leader);
+            if (b >= 0) order[at + (uint32_t)__popc(peers & lanemask_lt())] = (uint32_t)i;
+        }
+        if (lf_blk) {  // the fused loss's normalisers from the compaction's per-block counts
+            uint32_t c = 0u, ns = 0u;
+            for (int i = tid; i < lf_grid; i += PLACE_THREADS) {
+                c += lf_blk[i];
+                ns += lf_blk[lf_grid + i];
+            }
 #pragma unroll
-        for (int k = 0; k < PLACE_ITEMS; ++k) {
-            const uint32_t o = __shfl_sync(0xffffffffu, old[k], __ffs(peers[k]) - 1);
-            if (key[k] < (uint32_t)n) {
-                const uint32_t pos = s_start[key[k]] + o + (uint32_t)__popc(peers[k] & lt);
-                if (pos < cap) {
-                    keys_out[pos] = key[k];
-                    vals_out[pos] = val[k];
+            for (int o = 16; o > 0; o >>= 1) {
+                c += __shfl_xor_sync(0xffffffffu, c, o);
+                ns += __shfl_xor_sync(0xffffffffu, ns, o);
+            }
+            if (lane == 0) {
+                s_w[warp] = c;
+                s_w2[warp] = ns;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t a = 0u, b = 0u;
+                for (int w = 0; w < PLACE_THREADS / 32; ++w) {
+                    a += s_w[w];
+                    b += s_w2[w];
+                }
+                lf_counts[0] = a;
+                lf_counts[1] = b;
+            }
+        }
+    } else {
+        // the pairs: PLACE_ITEMS per thread per round, their claims in flight together
+        const uint32_t P = min(scratch[SCR_PAIRS], cap);
+        const uint32_t lt = lanemask_lt();
+        const uint32_t span = (uint32_t)PLACE_THREADS * PLACE_ITEMS;
+        for (uint32_t base = (blockIdx.x - 1) * span; base < P; base += (gridDim.x - 1) * span) {
+            uint32_t key[PLACE_ITEMS], val[PLACE_ITEMS], peers[PLACE_ITEMS], old[PLACE_ITEMS];
+#pragma unroll
+            for (int k = 0; k < PLACE_ITEMS; ++k) {
+                const uint32_t e = base + (uint32_t)(k * PLACE_THREADS + tid);
+                key[k] = e < P ? keys_in[e] : 0xffffffffu;
+                val[k] = e < P ? vals_in[e] : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < PLACE_ITEMS; ++k) {
+                peers[k] = __match_any_sync(0xffffffffu, key[k]);
+                old[k] = 0u;
+                if (key[k] < (uint32_t)n && lane == __ffs(peers[k]) - 1)
+                    old[k] = atomicAdd(fill + key[k], (uint32_t)__popc(peers[k]));
+            }
+#pragma unroll
+            for (int k = 0; k < PLACE_ITEMS; ++k) {
+                const uint32_t o = __shfl_sync(0xffffffffu, old[k], __ffs(peers[k]) - 1);
+                if (key[k] < (uint32_t)n) {
+                    const uint32_t pos = s_start[key[k]] + o + (uint32_t)__popc(peers[k] & lt);
+                    if (pos < cap) {
+                        keys_out[pos] = key[k];
+                        vals_out[pos] = val[k];
+                    }
                 }
             }
         }
@@ -861,9 +880,11 @@ cudaError_t launch_tile_place(const uint32_t* keys_in, const uint32_t* vals_in, 
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms < 1) sms = 148;
     }
+    // CTA 0 writes the ranges and the order, the others place the pairs
     int64_t grid = ceil_div((int64_t)cap, (int64_t)PLACE_THREADS * PLACE_ITEMS);
-    if (grid > (int64_t)sms * 2) grid = (int64_t)sms * 2;
+    if (grid > (int64_t)sms * 2 - 1) grid = (int64_t)sms * 2 - 1;
     if (grid < 1) grid = 1;
+    grid += 1;
     const size_t smem = (size_t)(n_tiles + 1) * 4;
     cudaError_t e = allow_dynamic_smem((const void*)tile_place_kernel, smem);
     if (e != cudaSuccess) return e;
