@@ -32,14 +32,20 @@ __device__ __forceinline__ void adam_update(float& p, float& m, float& v, float 
 // thread issues the loads of its chunk at once instead of walking the tensors
 // one after another (one DRAM round trip per launch, not one per tensor); a
 // chunk goes through float4 loads where its tensor's four arrays are 16-byte
-// aligned and it is whole.  The bias corrections are computed once per thread.
+// aligned and it is whole.
 __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamPack A, float lr, float b1, float b2,
                                                    float eps, const int32_t* step_dev, int32_t step_host) {
-    const int32_t step = step_dev ? step_dev[0] : step_host;
-    const float bc1 = 1.f - powf(b1, (float)step);
-    const float bc2 = 1.f - powf(b2, (float)step);
-    const float step_size = lr / bc1;
-    const float inv_sqrt_bc2 = rsqrtf(bc2);
+    // the bias corrections, once per block (the powers cost as many issue
+    // slots as a thread's whole update)
+    __shared__ float s_bc[2];
+    if (threadIdx.x == 0) {
+        const int32_t step = step_dev ? step_dev[0] : step_host;
+        s_bc[0] = 1.f - powf(b1, (float)step);
+        s_bc[1] = 1.f - powf(b2, (float)step);
+    }
+    __syncthreads();
+    const float step_size = lr / s_bc[0];
+    const float inv_sqrt_bc2 = rsqrtf(s_bc[1]);
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     const int64_t total = A.chunk_end[A.n - 1];
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += nthr) {

@@ -87,7 +87,9 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) preprocess_kernel(
                 cand = true;
                 break;
             }
-            const float iz = 1.f / pc[2];
+            // (hardware reciprocal and reciprocal square root: a few ulp,
+            // far inside the margins)
+            const float iz = __fdividef(1.f, pc[2]);
             float tx = pc[0] * iz, ty = pc[1] * iz;
             const float u = vi.fx * tx + vi.cx, vv = vi.fy * ty + vi.cy;
             if (cs.jacobian_clamp) {
@@ -96,7 +98,8 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) preprocess_kernel(
             }
             const float fz = vi.fx * iz, gz = vi.fy * iz;
             const float jf2 = fz * fz * (1.f + tx * tx) + gz * gz * (1.f + ty * ty);
-            const float r = cs.sigma_cull * sqrtf(jf2 * smax * smax + cs.dilation) * 1.01f + 2.f;
+            const float r2 = fmaxf(jf2 * smax * smax + cs.dilation, 1e-30f);
+            const float r = cs.sigma_cull * (r2 * rsqrtf(r2)) * 1.01f + 2.f;
             cand = u + r >= 0.f && u - r < (float)(vi.tiles_x * TILE) && vv + r >= 0.f &&
                    vv - r < (float)(vi.tiles_y * TILE);
         }
@@ -343,6 +346,7 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
     uint32_t off, poff = 0;
     {
         uint32_t a = 0, p = 0;
+#pragma unroll 4
         for (int j = threadIdx.x; j < b; j += 256) {
             a += cnt[j];
             if (pair_off) p += cnt[nb + j];

@@ -706,6 +706,33 @@ __global__ void __launch_bounds__(PLACE_THREADS) tile_place_kernel(
     uint32_t* const fill = cnt_g + n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool lead = blockIdx.x == 0;  // the CTA that writes ranges and order
+    // a placing CTA loads and claims its first round of pairs before the
+    // scan: the claims need only the fill counters, so their round trips
+    // overlap the scan, and only the positions wait for the tile starts
+    const uint32_t P = min(scratch[SCR_PAIRS], cap);
+    const uint32_t lt = lanemask_lt();
+    const uint32_t span = (uint32_t)PLACE_THREADS * PLACE_ITEMS;
+    uint32_t key[PLACE_ITEMS], val[PLACE_ITEMS], peers[PLACE_ITEMS], old[PLACE_ITEMS];
+    auto claim = [&](uint32_t base) {
+#pragma unroll
+        for (int k = 0; k < PLACE_ITEMS; ++k) {
+            const uint32_t e = base + (uint32_t)(k * PLACE_THREADS + tid);
+            key[k] = e < P ? keys_in[e] : 0xffffffffu;
+            val[k] = e < P ? vals_in[e] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < PLACE_ITEMS; ++k) {
+            peers[k] = __match_any_sync(0xffffffffu, key[k]);
+            old[k] = 0u;
+            if (key[k] < (uint32_t)n && lane == __ffs(peers[k]) - 1)
+                old[k] = atomicAdd(fill + key[k], (uint32_t)__popc(peers[k]));
+        }
+    };
+    uint32_t base = lead ? P : (blockIdx.x - 1) * span;
+    if (base < P) claim(base);
+    // (unrolled: the loads of a thread's counts go out together, not one L2
+    // round trip each)
+#pragma unroll 8
     for (int i = tid; i < n; i += PLACE_THREADS) s_start[i] = cnt_g[i];
     if (lead) {
         for (int i = tid; i < ORDER_BUCKETS; i += PLACE_THREADS) s_bin[i] = 0u;
@@ -797,6 +824,7 @@ __global__ void __launch_bounds__(PLACE_THREADS) tile_place_kernel(
         }
         if (lf_blk) {  // the fused loss's normalisers from the compaction's per-block counts
             uint32_t c = 0u, ns = 0u;
+#pragma unroll 4
             for (int i = tid; i < lf_grid; i += PLACE_THREADS) {
                 c += lf_blk[i];
                 ns += lf_blk[lf_grid + i];
@@ -823,24 +851,8 @@ __global__ void __launch_bounds__(PLACE_THREADS) tile_place_kernel(
         }
     } else {
         // the pairs: PLACE_ITEMS per thread per round, their claims in flight together
-        const uint32_t P = min(scratch[SCR_PAIRS], cap);
-        const uint32_t lt = lanemask_lt();
-        const uint32_t span = (uint32_t)PLACE_THREADS * PLACE_ITEMS;
-        for (uint32_t base = (blockIdx.x - 1) * span; base < P; base += (gridDim.x - 1) * span) {
-            uint32_t key[PLACE_ITEMS], val[PLACE_ITEMS], peers[PLACE_ITEMS], old[PLACE_ITEMS];
-#pragma unroll
-            for (int k = 0; k < PLACE_ITEMS; ++k) {
-                const uint32_t e = base + (uint32_t)(k * PLACE_THREADS + tid);
-                key[k] = e < P ? keys_in[e] : 0xffffffffu;
-                val[k] = e < P ? vals_in[e] : 0u;
-            }
-#pragma unroll
-            for (int k = 0; k < PLACE_ITEMS; ++k) {
-                peers[k] = __match_any_sync(0xffffffffu, key[k]);
-                old[k] = 0u;
-                if (key[k] < (uint32_t)n && lane == __ffs(peers[k]) - 1)
-                    old[k] = atomicAdd(fill + key[k], (uint32_t)__popc(peers[k]));
-            }
+        for (bool first = true; base < P; base += (gridDim.x - 1) * span, first = false) {
+            if (!first) claim(base);
 #pragma unroll
             for (int k = 0; k < PLACE_ITEMS; ++k) {
                 const uint32_t o = __shfl_sync(0xffffffffu, old[k], __ffs(peers[k]) - 1);
