@@ -423,6 +423,7 @@ __global__ void __launch_bounds__(TILE_PIX / PPT, BwdQueue<PPT>::MINB) blend_bwd
     const float* __restrict__ Tfin, const uint32_t* __restrict__ ncontrib, const float* __restrict__ dC,
     const float* __restrict__ dD, const float* __restrict__ dS, float* __restrict__ g2d,
     unsigned long long* bwd_pairs, int count) {
+    allow_dependents();  // the chain kernel's scene-only prefix may overlap this kernel's last CTAs
     using Q = BwdQueue<PPT>;
     extern __shared__ __align__(16) unsigned char smem[];
     float4* s_xy = reinterpret_cast<float4*>(smem);

@@ -327,6 +327,14 @@ __device__ __forceinline__ float gauss_p2(float A2, float B2, float C2, float dx
     return __fmaf_rn(dx, inner, __fmul_rn(__fmul_rn(C2, dy), dy));
 }
 
+// Overlapped launch of a dependent kernel (programmatic dependent launch):
+// the kernel in front lets its dependents be scheduled once each of its CTAs
+// has started (allow_dependents), and the dependent kernel runs its
+// scene-only prefix, then waits here until the kernel in front has completed
+// and its writes are visible.  Both are no-ops for a normal launch.
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // 2^x with the hardware base-2 exponential unit
 __device__ __forceinline__ float fast_exp2(float x) {
     float y;

@@ -48,6 +48,7 @@ __host__ __device__ inline float* chain_cb_dst(const ChainOut& O, int gi) {
 __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
     SceneDev S, const __grid_constant__ Views V, Consts cs, const float* __restrict__ g2d,
     const uint32_t* __restrict__ vis, const uint32_t* __restrict__ nvis_dev, uint32_t max_vis, ChainOut O) {
+    allow_dependents();  // the pose kernel that reads the sums may wait on the device
     extern __shared__ float s_dyn[];  // [V.n][6] pose sums, then the codebook-gradient accumulators
     float* s_pose = s_dyn;
     float* s_cb = s_dyn + V.n * 6;
@@ -69,18 +70,10 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
             const uint32_t slot = vis[e];
             const int v = slot_view(slot, (uint32_t)S.N, V.n);
             const int64_t n = (int64_t)slot - (int64_t)v * S.N;
-            float g[12];
-            {
-                const float4* row = reinterpret_cast<const float4*>(g2d + (int64_t)slot * G2D_STRIDE);
-                const float4 r0 = row[0], r1 = row[1], r2 = row[2];
-                g[0] = r0.x; g[1] = r0.y; g[2] = r0.z; g[3] = r0.w;
-                g[4] = r1.x; g[5] = r1.y; g[6] = r1.z; g[7] = r1.w;
-                g[8] = r2.x; g[9] = r2.y; g[10] = r2.z; g[11] = r2.w;
-            }
             // Eq. 7's offset and scaling factor, decoded once: the mean here,
-            // their own gradients at the end.  Every load of the slot's
-            // attributes goes out before the row is tested, so that they
-            // overlap the row's round trip instead of following it; the codes
+            // their own gradients at the end.  Everything up to the 2D
+            // covariance depends on the scene alone, so it runs before the
+            // wait for the backward compositing (overlapped launch); the codes
             // stay in registers for the codebook gradients.
             const int64_t a = anchor_of(S, n);
             float mu[3], ls[3], q[4], ol, rgb[3], oo[3], la[3];
@@ -93,10 +86,6 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
             decode_attr_codes<4>(S, 1, n, q, kp[1]);
             decode_attr_codes<1>(S, 2, n, &ol, kp[2]);
             decode_attr_codes<3>(S, 3, n, rgb, kp[3]);
-            bool nz = false;
-#pragma unroll
-            for (int c = 0; c < 10; ++c) nz |= g[c] != 0.f;
-            if (!nz) break;
             const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
             if (!(qq > 0.f)) break;
             // one reciprocal per slot for every quotient by |q| and by z below;
@@ -148,6 +137,20 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
 #pragma unroll
                     for (int c = 0; c < 3; ++c) RS[r][c] = R[r][c] * s[c];
                 cov2d(J00, J02, J11, J12, T, RS, cs.dilation, A, B, C, det);
+                // the slot's 2D gradient row, written by the backward compositing
+                grid_dependency_wait();
+                float g[12];
+                {
+                    const float4* row = reinterpret_cast<const float4*>(g2d + (int64_t)slot * G2D_STRIDE);
+                    const float4 r0 = row[0], r1 = row[1], r2 = row[2];
+                    g[0] = r0.x; g[1] = r0.y; g[2] = r0.z; g[3] = r0.w;
+                    g[4] = r1.x; g[5] = r1.y; g[6] = r1.z; g[7] = r1.w;
+                    g[8] = r2.x; g[9] = r2.y; g[10] = r2.z; g[11] = r2.w;
+                }
+                bool nz = false;
+#pragma unroll
+                for (int c = 0; c < 10; ++c) nz |= g[c] != 0.f;
+                if (!nz) break;
                 const float i2 = __fdividef(1.f, det * det);
                 const float da = g[2], db = g[3], dc = g[4];
                 // conic = inverse of [[A,B],[B,C]]
@@ -338,6 +341,7 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
             }
         }
     }
+    grid_dependency_wait();  // (threads without a slot too, before any global write)
     __syncthreads();
     for (int i = threadIdx.x; i < V.n * 6; i += blockDim.x)
         if (s_pose[i] != 0.f) atomicAdd(O.pose_sum + i, s_pose[i]);
@@ -417,9 +421,11 @@ cudaError_t launch_chain(const SceneDev& S, const Views& V, const Consts& cs, co
     const size_t smem = chain_smem(S, V, &O);
     cudaError_t e = allow_dynamic_smem((const void*)chain_kernel, smem);
     if (e != cudaSuccess) return e;
-    count_launches(1);
-    chain_kernel<<<blocks, CHAIN_THREADS, smem, st>>>(S, V, cs, g2d, vis, nvis_dev, max_vis, O);
-    return cudaGetLastError();
+    // overlapped with the backward compositing in front of it (same call):
+    // the chain's CTAs start their scene-only prefix as that kernel's last
+    // CTAs run
+    return launch_overlapped(chain_kernel, dim3((unsigned)blocks), dim3(CHAIN_THREADS), smem, st, S, V, cs, g2d, vis,
+                             nvis_dev, max_vis, O);
 }
 
 // ---------------------------------------------------------------------------
@@ -476,6 +482,7 @@ cudaError_t launch_icp(const SceneDev& S, const Views& V, const float* q, const 
 // dxi = the chain's pose sums (+ the ICP term's block partials, if any)
 __global__ void pose_final_kernel(const float* __restrict__ pose_sum, const float* __restrict__ icp_part, int nbi,
                                   float* __restrict__ dxi, float* __restrict__ icp_loss) {
+    grid_dependency_wait();  // (overlapped launch: nothing is read before the kernel in front completes)
     __shared__ float s_tmp[8];
     const int v = blockIdx.x;
     if (!icp_part) {
@@ -495,9 +502,10 @@ __global__ void pose_final_kernel(const float* __restrict__ pose_sum, const floa
 
 cudaError_t launch_pose_final(int n_views, const float* pose_sum, const float* icp_part, int nbi, float* dxi,
                               float* icp_loss, cudaStream_t st) {
-    count_launches(1);
-    pose_final_kernel<<<n_views, icp_part ? 256 : 32, 0, st>>>(pose_sum, icp_part, nbi, dxi, icp_loss);
-    return cudaGetLastError();
+    // overlapped: resident as the chain (or ICP) kernel in front runs, it
+    // waits on the device instead of being launched after it
+    return launch_overlapped(pose_final_kernel, dim3((unsigned)n_views), dim3(icp_part ? 256 : 32), 0, st, pose_sum,
+                             icp_part, nbi, dxi, icp_loss);
 }
 
 // ---------------------------------------------------------------------------

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "vg_common.cuh"
 
 namespace vgk {
@@ -67,6 +69,28 @@ __device__ __forceinline__ void mark_chunks(uint32_t* chunk_start, uint32_t j, u
 
 // kernels enqueued by this library in this process (host-side count)
 void count_launches(int n);
+// Launch kernel<<<grid, block, smem, st>>>(args...) with programmatic stream
+// serialization: its CTAs may be scheduled once every CTA of the kernel in
+// front of it has started (that kernel calls allow_dependents()), and the
+// kernel must call grid_dependency_wait() before it reads anything that
+// kernel writes or writes anything that kernel reads.  Used only where the
+// kernel in front is this library's own, enqueued by the same call.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_overlapped(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    count_launches(1);
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 // Raise a kernel's dynamic shared-memory limit when its static plus dynamic
 // shared memory passes the 48 KB that launches get without opting in.
 cudaError_t allow_dynamic_smem(const void* kernel, size_t dynamic_bytes);

@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamP
     __syncthreads();
     const float step_size = lr / s_bc[0];
     const float inv_sqrt_bc2 = rsqrtf(s_bc[1]);
+    allow_dependents();  // the step counter's increment may wait on the device
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     const int64_t total = A.chunk_end[A.n - 1];
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += nthr) {
@@ -89,7 +90,12 @@ __global__ void __launch_bounds__(256) adam_kernel(const __grid_constant__ AdamP
     }
 }
 
-__global__ void step_increment_kernel(int32_t* step_dev) { step_dev[0] += 1; }
+// (overlapped launch after the optimiser kernel of the same call: resident
+// while that kernel runs, it waits on the device for it)
+__global__ void step_increment_kernel(int32_t* step_dev) {
+    grid_dependency_wait();
+    step_dev[0] += 1;
+}
 
 cudaError_t launch_adam(int n, float* const* p, float* const* g, float* const* m, float* const* v,
                         const int64_t* size, uint32_t zero_mask, float lr, float b1, float b2, float eps,
@@ -115,11 +121,8 @@ cudaError_t launch_adam(int n, float* const* p, float* const* g, float* const* m
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (step_dev) {
-        count_launches(1);
-        step_increment_kernel<<<1, 1, 0, st>>>(step_dev);
-    }
-    return cudaGetLastError();
+    if (step_dev) return launch_overlapped(step_increment_kernel, dim3(1), dim3(1), 0, st, step_dev);
+    return cudaSuccess;
 }
 
 // SE(3) exponential of xi = (rho, phi): R = exp([phi]x) (Rodrigues),
@@ -160,6 +163,7 @@ __device__ void se3_exp(const float xi[6], float R[3][3], float t[3]) {
 __global__ void pose_step_kernel(int n_views, float* pose, const float* dxi, float* m, float* v, float lr_rot,
                                  float lr_trans, float b1, float b2, float eps, const int32_t* step_dev,
                                  int32_t step_host) {
+    allow_dependents();  // the step counter's increment may wait on the device
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= n_views) return;
     const int32_t step = step_dev ? step_dev[0] : step_host;
@@ -196,11 +200,8 @@ cudaError_t launch_pose_step(int n_views, float* pose, const float* dxi, float* 
                                                                       b2, eps, step_dev, step_host);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (step_dev) {
-        count_launches(1);
-        step_increment_kernel<<<1, 1, 0, st>>>(step_dev);
-    }
-    return cudaGetLastError();
+    if (step_dev) return launch_overlapped(step_increment_kernel, dim3(1), dim3(1), 0, st, step_dev);
+    return cudaSuccess;
 }
 
 }  // namespace vgk

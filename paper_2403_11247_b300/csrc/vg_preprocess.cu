@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) preprocess_kernel(
     __shared__ uint32_t s_wn[PRE_THREADS / 32];
     __shared__ uint32_t s_list[PRE_THREADS];  // the block's candidates (Gaussian offsets in the block)
     __shared__ float s_mu[PRE_THREADS * 3];   // and their means
+    allow_dependents();  // the compaction's loss normalisers may overlap this kernel's last CTAs
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (cs.depth_hist)
         for (int i = tid; i < 4 * 256; i += PRE_THREADS) s_hist[i] = 0;
@@ -300,8 +301,9 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
                                                       float* __restrict__ g2d_rows, float* __restrict__ pose_zero,
                                                       int n_pose, int nb, const Consts cs) {
     __shared__ uint32_t s_tmp[8];
-    if (blockIdx.x == 0)
-        for (int i = threadIdx.x; i < n_pose; i += 256) pose_zero[i] = 0.f;
+    // (overlapped launch: the loss normalisers read only the caller's target
+    // depths and pixel mask, so they are counted while the preprocess
+    // drains; everything after the wait reads the preprocess's outputs)
     if (cs.lf_on) {
         // the fused L1 loss's normalisers, counted before any pixel is
         // composited: valid target depths and sampled pixels, per block
@@ -337,6 +339,9 @@ __global__ void __launch_bounds__(256) compact_kernel(const __grid_constant__ Vi
             cs.lf_blk[gridDim.x + blockIdx.x] = nst;
         }
     }
+    grid_dependency_wait();
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < n_pose; i += 256) pose_zero[i] = 0.f;
     if ((int)blockIdx.x >= nb) return;
     const int64_t n = (int64_t)blockIdx.x * 256 + threadIdx.x;
     const int b = (int)blockIdx.x;
@@ -419,11 +424,11 @@ cudaError_t launch_compact(const Views& V, int64_t N, const uint32_t* dkey, cons
                            float* g2d_rows, float* pose_zero, int n_pose, const Consts& cs, cudaStream_t st) {
     const int blocks = preprocess_blocks(N);
     const int64_t grid = compact_grid(N, cs);
-    count_launches(1);
-    compact_kernel<<<(unsigned)grid, 256, 0, st>>>(V, N, dkey, blk_count, keys_out, vals_out, vals_copy, ntiles,
-                                                   pair_off, chunk_start, cap, scratch, err, g2d_rows, pose_zero,
-                                                   pose_zero ? n_pose : 0, blocks, cs);
-    return cudaGetLastError();
+    // overlapped with the preprocess in front of it (same call): the
+    // compaction's CTAs count the loss normalisers as the preprocess drains
+    return launch_overlapped(compact_kernel, dim3((unsigned)grid), dim3(256), 0, st, V, N, dkey, blk_count, keys_out,
+                             vals_out, vals_copy, ntiles, pair_off, chunk_start, cap, scratch, err, g2d_rows, pose_zero,
+                             pose_zero ? n_pose : 0, blocks, cs);
 }
 
 // ---------------------------------------------------------------------------
