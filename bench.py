@@ -33,10 +33,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd iters/s and Mpix/s at 1200x680, 300k Gaussians; served p50/p99 latency vs 1-at-a-time"
 WORKLOAD = ("mapping step fwd+bwd: 40,000 anchors x 8 = 320,000 Gaussians on a 0.05 m room grid (20% masked), "
-            "RVQ 4 groups x 3 stages x 64 codewords, 1200x680 fx=fy=600, L1 colour + 0.5 L1 depth vs a "
-            "jittered-camera render, Adam on anchors/offsets/l/codebooks/mask logits")
+            "RVQ 4 groups x 3 stages x 64 codewords, 1200x680 fx=fy=600, L1 colour + 0.5 L1 depth vs an "
+            "RGB-D frame (8-bit colour, 16-bit depth in mm) of a jittered-camera render, Adam on "
+            "anchors/offsets/l/codebooks/mask logits")
 W_IMG, H_IMG = 1200, 680
 FP32_PEAK_PER_SM_CLK = 128 * 2      # FP32 lanes x 2 FLOP (FMA) per SM per clock
+DEPTH_SCALE = 1000.0      # target depth frames in millimetres (16-bit)
 # algorithmic FP32 FLOPs per pair (FMA = 2), counted from the kernels' source
 FWD_FLOP_EVAL = 14        # offset, quadratic form, exp argument, opacity product, tests
 FWD_FLOP_BLEND = 12       # transmittance update, 4 FMA accumulations, silhouette
@@ -241,9 +243,15 @@ def build_workload(torch, V, synth):
     sh = V.vg_scene_upload(dscene, V.VG_SCENE_BORROW)
     ctx = V.vg_ctx_create(0)
     params = V.default_params()
-    # target frame: a render at a jittered camera (fixed during the run)
-    Ct, Dt, _ = V.render_with_retry(sh, [tcam], params, ctx)
-    Ct, Dt = Ct.clone(), Dt.clone()
+    # target frame: a render at a jittered camera (fixed during the run),
+    # held as a camera delivers it -- 8-bit RGB, 16-bit depth in millimetres
+    # -- and decoded on the device into the FP32 images the loss reads
+    Cr, Dr, _ = V.render_with_retry(sh, [tcam], params, ctx)
+    rgb_h = np.clip(np.rint(np.moveaxis(Cr.cpu().numpy().reshape(3, H_IMG, W_IMG), 0, -1) * 255.0), 0, 255)
+    rgb_h = np.ascontiguousarray(rgb_h.astype(np.uint8))
+    mm_h = np.clip(np.rint(Dr.cpu().numpy().reshape(H_IMG, W_IMG) * DEPTH_SCALE), 0, 65535).astype(np.uint16)
+    Ct, Dt = V.vg_frame_decode(torch.from_numpy(rgb_h.reshape(-1)).to(dev),
+                               torch.from_numpy(mm_h.reshape(-1).view(np.int16)).to(dev), W_IMG, H_IMG, DEPTH_SCALE)
     V.render_with_retry(sh, [cam], params, ctx)
     pairs = V.vg_ctx_stats(ctx)["pairs"]
     V.vg_ctx_reserve(ctx, int(pairs * 1.5) + 4096)
@@ -262,6 +270,7 @@ def build_workload(torch, V, synth):
     vs = [torch.zeros_like(p) for p in plist]
     step_dev = torch.ones(1, dtype=torch.int32, device=dev)
     return dict(scene=scene, cam=cam, tcam=tcam, sh=sh, ctx=ctx, params=params, bufs=bufs, grads=grads,
+                frame_rgb=rgb_h, frame_mm=mm_h,
                 plist=plist, glist=glist, ms=ms, vs=vs, step_dev=step_dev, P=P)
 
 
@@ -1192,10 +1201,21 @@ def run_ours(args):
     if True:
         b = w["bufs"]
         # staging buffers from the library's page-locked host allocator
-        Ct_h = V.host_empty(b["Ct"].numel())
-        V.vg_host_stage(Ct_h, b["Ct"].cpu())
-        Dt_h = V.host_empty(b["Dt"].numel())
-        V.vg_host_stage(Dt_h, b["Dt"].cpu())
+        # the frame as the camera delivers it (8-bit RGB, 16-bit depth), in
+        # page-locked memory; each step uploads it and decodes it on the
+        # device (copy stream) into that step's FP32 target images
+        rgb_h = V.host_empty(w["frame_rgb"].size, torch.uint8)
+        V.vg_host_stage(rgb_h, w["frame_rgb"].reshape(-1))
+        mm_h = V.host_empty(w["frame_mm"].size, torch.int16)
+        V.vg_host_stage(mm_h, w["frame_mm"].reshape(-1).view(np.int16))
+        raw = [(torch.empty(rgb_h.numel(), dtype=torch.uint8, device="cuda"),
+                torch.empty(mm_h.numel(), dtype=torch.int16, device="cuda")) for _ in range(2)]
+
+        def upload(j):
+            V.vg_memcpy_async(raw[j][0], rgb_h, copy_stream)
+            V.vg_memcpy_async(raw[j][1], mm_h, copy_stream)
+            V.vg_frame_decode(raw[j][0], raw[j][1], W_IMG, H_IMG, DEPTH_SCALE, tgts[j][0], tgts[j][1],
+                              stream=copy_stream)
         n_e2e = max(3, min(args.steps, 200))
         out_h = V.host_empty((n_e2e, 7))
         out2 = torch.empty_like(b["out"])
@@ -1222,16 +1242,14 @@ def run_ours(args):
             e.record(stream)
         t0 = time.perf_counter()
         with torch.cuda.stream(copy_stream):
-            V.vg_memcpy_async(tgts[0][0], Ct_h, copy_stream)
-            V.vg_memcpy_async(tgts[0][1], Dt_h, copy_stream)
+            upload(0)
             ready[0].record(copy_stream)
         for i in range(n_e2e):
             j = i & 1
             if i + 1 < n_e2e:
                 copy_stream.wait_event(free[1 - j])
                 with torch.cuda.stream(copy_stream):
-                    V.vg_memcpy_async(tgts[1 - j][0], Ct_h, copy_stream)
-                    V.vg_memcpy_async(tgts[1 - j][1], Dt_h, copy_stream)
+                    upload(1 - j)
                     ready[1 - j].record(copy_stream)
             stream.wait_event(ready[j])
             stream.wait_event(read[j])  # the readback of this buffer's previous step is done
@@ -1247,7 +1265,8 @@ def run_ours(args):
         dt = time.perf_counter() - t0
         if V.vg_check(w["ctx"]) != V.VG_OK or not bool(torch.isfinite(out_h).all()):
             raise RuntimeError("end-to-end steps: device status not OK or non-finite results")
-        e2e = {"value": world * n_e2e / dt, "unit": "iters/s", "h2d_bytes_per_step": Ct_h.numel() * 4 + Dt_h.numel() * 4,
+        e2e = {"value": world * n_e2e / dt, "unit": "iters/s", "h2d_bytes_per_step": rgb_h.numel() + mm_h.numel() * 2,
+               "frame": "8-bit RGB + 16-bit depth (mm) uploaded, decoded on the device (vg_frame_decode) every step",
                "d2h_bytes_per_step": 7 * 4, "steps": n_e2e,
                "pipelining": "upload of step i+1 and readback of step i-1 overlap step i (two target and result "
                              "buffers, copy and readback streams)",

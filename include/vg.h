@@ -434,6 +434,26 @@ vg_status vg_render_fwd_l1(vg_scene* scene, const vg_camera* cams, int32_t n_vie
 vg_status vg_pose_grad(vg_ctx* ctx, int32_t n_views, const float* icp_q, const float* icp_w,
                        float* dxi, float* icp_loss, vg_stream stream);
 
+/* RGB-D frame ingestion.  The method's input is a sequence of RGB-D frames
+ * {I_i, D_i} with known intrinsics (Sec. 3, opening paragraph); sensors
+ * deliver them as interleaved 8-bit colour and 16-bit depth, and uploading
+ * them in that form moves 5 bytes a pixel over the host link instead of the
+ * 16 of FP32 images.  This decodes n_views frames of width x height pixels,
+ * back to back, on the device:
+ *   rgb   uint8  [n_views][height][width][3]  (DEVICE, interleaved R, G, B)
+ *   depth uint16 [n_views][height][width]     (DEVICE, depth_scale units a
+ *                                              metre; 0 = no measurement)
+ *   C     float  [n_views][3][height][width]  (DEVICE, planar: rgb / 255)
+ *   D     float  [n_views][height][width]     (DEVICE: depth / depth_scale,
+ *                                              0 where there is none, which
+ *                                              the L1 losses treat as invalid)
+ * in the layout the renderer and the losses use (C, D as vg_render_fwd
+ * writes them).  Both quotients are IEEE FP32 divisions.  Enqueued on
+ * `stream`; no allocation.  VG_ERR_INVALID_ARG for a NULL pointer,
+ * n_views, width or height < 1, or depth_scale not finite and positive. */
+vg_status vg_frame_decode(int32_t n_views, int32_t width, int32_t height, const uint8_t* rgb, const uint16_t* depth,
+                          float depth_scale, float* C, float* D, vg_stream stream);
+
 /* Upstream gradients of L = mean|C - Ct| + w_depth * mean_{Dt>0}|D - Dt| over
  * n_views views of n_pix pixels each (C, Ct: [n_views][3][n_pix]; D, Dt, S:
  * [n_views][n_pix]); with gate >= 0 only pixels with S > gate contribute

@@ -1063,6 +1063,16 @@ vg_status vg_loss_l1(int32_t n_views, int64_t n_pix, const float* C, const float
     return vg_loss_l1_masked(n_views, n_pix, C, D, S, Ct, Dt, nullptr, w_depth, gate, dC, dD, dS, loss, ctx, stream);
 }
 
+vg_status vg_frame_decode(int32_t n_views, int32_t width, int32_t height, const uint8_t* rgb, const uint16_t* depth,
+                          float depth_scale, float* C, float* D, vg_stream stream) {
+    if (!rgb || !depth || !C || !D || n_views < 1 || width < 1 || height < 1)
+        return fail(VG_ERR_INVALID_ARG, "vg_frame_decode: null pointer or empty size");
+    if (!(depth_scale > 0.f) || !std::isfinite(depth_scale))
+        return fail(VG_ERR_INVALID_ARG, "vg_frame_decode: depth_scale must be finite and positive");
+    VG_CUDA(launch_frame_decode(n_views, (int64_t)width * height, rgb, depth, depth_scale, C, D, (cudaStream_t)stream));
+    return VG_OK;
+}
+
 vg_status vg_sample_rays(uint8_t* mask, int64_t n, double rate, uint64_t seed, const int32_t* round_dev,
                          int32_t round_host, vg_stream stream) {
     if (n < 0 || (n > 0 && !mask) || !(rate >= 0.0 && rate <= 1.0))

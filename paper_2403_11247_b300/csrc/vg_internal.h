@@ -97,6 +97,10 @@ cudaError_t allow_dynamic_smem(const void* kernel, size_t dynamic_bytes);
 // record the message returned by vg_last_error() and return s
 vg_status set_error(vg_status s, const char* msg);
 
+// frame.cu: RGB-D frames (interleaved uint8 RGB, uint16 depth) to planar FP32
+cudaError_t launch_frame_decode(int n_views, int64_t hw, const uint8_t* rgb, const uint16_t* depth, float depth_scale,
+                                float* C, float* D, cudaStream_t st);
+
 // preprocess.cu
 int preprocess_blocks(int64_t N);
 // the compaction's grid (preprocess_blocks, widened for the fused loss's

@@ -106,6 +106,7 @@ def lib():
             "vg_loss_l1": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P, P],
             "vg_loss_l1_masked": [I32, I64, P, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P, P],
             "vg_sample_rays": [P, I64, C.c_double, C.c_uint64, P, I32, P],
+            "vg_frame_decode": [I32, I32, I32, P, P, C.c_float, P, P, P],
             "vg_loss_l1_noalloc": [I32, I64, P, P, P, P, P, C.c_float, C.c_float, P, P, P, P, P],
             "vg_probe_peak": [I32, I32, P, I64, P, P],
             "vg_rvq_encode": [P, I64, P, P, P, P, P],
@@ -590,6 +591,22 @@ def vg_pose_grad(ctx: CtxHandle, n_views: int, icp_q=None, icp_w=None, dxi=None,
     return dxi, icp_loss
 
 
+def vg_frame_decode(rgb, depth, width: int, height: int, depth_scale: float, C_=None, D=None, stream=None):
+    """RGB-D frames as sensors deliver them -- rgb uint8 [views][H][W][3],
+    depth uint16 [views][H][W] (depth_scale units a metre), CUDA tensors --
+    decoded on the device into planar FP32 C [views*3*H*W] and D [views*H*W]."""
+    torch = _torch()
+    hw = int(width) * int(height)
+    n_views = rgb.numel() // (3 * hw) if hw > 0 else 0
+    if C_ is None:
+        C_ = torch.empty(3 * n_views * hw, dtype=torch.float32, device=rgb.device)
+    if D is None:
+        D = torch.empty(n_views * hw, dtype=torch.float32, device=rgb.device)
+    _check(lib().vg_frame_decode(int(n_views), int(width), int(height), _ptr(rgb), _ptr(depth), float(depth_scale),
+                                 _ptr(C_), _ptr(D), _stream(stream)), "vg_frame_decode")
+    return C_, D
+
+
 def vg_loss_l1(n_views: int, n_pix: int, C_, D, S, Ct, Dt, w_depth: float, gate: float, ctx: CtxHandle,
                dC=None, dD=None, dS=None, loss=None, stream=None):
     torch = _torch()
@@ -754,7 +771,7 @@ def exported_symbols():
             "vg_launch_count", "vg_probe_peak", "vg_rvq_encode", "vg_mask_loss", "vg_mask_prune", "vg_ssim_loss", "vg_icp_associate",
             "vg_grow_accumulate", "vg_anchor_grow", "vg_anchor_prune", "vg_host_alloc", "vg_host_free", "vg_memcpy_async", "vg_host_stage",
             "vg_loss_l1_masked", "vg_sample_rays", "vg_render_fwd_l1", "vg_ctx_set_spin_limit",
-            "vg_workspace_allocs"]
+            "vg_workspace_allocs", "vg_frame_decode"]
 
 
 PROBES = {"fma": (0, 20000, "TFLOP/s", 1e12), "ex2": (1, 2000, "G exp2/s", 1e9), "smem": (2, 5000, "TB/s", 1e12),

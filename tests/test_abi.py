@@ -95,6 +95,11 @@ def test_argument_errors_return_before_any_cuda_call(lib):
     g = V.vg_attr_group(3, 2, 300, None, None, None)
     assert lib.vg_rvq_decode(C.byref(g), 10, C.c_void_p(16), None) == V.VG_ERR_INVALID_ARG
     assert lib.vg_ctx_create(-1, C.byref(out)) == V.VG_ERR_INVALID_ARG
+    dev = C.c_void_p(256)  # never dereferenced: every call below fails its argument checks first
+    assert lib.vg_frame_decode(1, 4, 4, None, dev, C.c_float(1000.0), dev, dev, None) == V.VG_ERR_INVALID_ARG
+    assert lib.vg_frame_decode(0, 4, 4, dev, dev, C.c_float(1000.0), dev, dev, None) == V.VG_ERR_INVALID_ARG
+    assert lib.vg_frame_decode(1, 4, 4, dev, dev, C.c_float(0.0), dev, dev, None) == V.VG_ERR_INVALID_ARG
+    assert lib.vg_frame_decode(1, 4, 4, dev, dev, C.c_float(float("nan")), dev, dev, None) == V.VG_ERR_INVALID_ARG
     assert lib.vg_loss_l1(0, 10, *([None] * 5), 0.5, -1.0, *([None] * 6)) == V.VG_ERR_INVALID_ARG
 
 
