@@ -51,12 +51,12 @@ ADAM_BYTES_PARAM = 28     # read parameter, gradient, two moments; write paramet
 # valid while the kernels' sources hash to the value they had when captured
 BLEND_SOURCES = ("paper_2403_11247_b300/csrc/vg_blend.cu", "paper_2403_11247_b300/csrc/vg_common.cuh",
                  "paper_2403_11247_b300/csrc/vg_blend_common.cuh")
-NCU_TRAFFIC = {"blend_bwd": ("92663f7472549d3f", 24.42752e6 + 0.0),
-               "blend_fwd": ("92663f7472549d3f", 16.484352e6 + 586.496e3)}
+NCU_TRAFFIC = {"blend_bwd": ("af5d6e0d5e1685ec", 24.435712e6 + 0.0),
+               "blend_fwd": ("af5d6e0d5e1685ec", 16.483584e6 + 550.144e3)}
 # warp instructions per launch from the same capture: with the live launch
 # time they give the issue rate against the SMs' issue peak (4 schedulers
 # per SM, one warp instruction per clock each)
-NCU_INSTRUCTIONS = {"blend_bwd": 105.19017e6, "blend_fwd": 55.232963e6}
+NCU_INSTRUCTIONS = {"blend_bwd": 75.339315e6, "blend_fwd": 55.214048e6}
 
 
 def ncu_traffic(stage: str):

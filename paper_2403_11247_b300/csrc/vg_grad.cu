@@ -60,6 +60,10 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
     // warp-uniform trip count, so that the pose sums can use warp shuffles;
     // consecutive 32-slot chunks go to consecutive blocks, so that a visible
     // set smaller than the grid still spreads over every SM
+    // Only a thread's first slot waits for the backward compositing before
+    // loading its gradient row; later slots (scenes with more visible slots
+    // than threads) load the row together with the attributes.
+    bool waited = false;
     for (uint32_t base = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32u; base < nvis;
          base += gridDim.x * blockDim.x) {
         const uint32_t e = base + lane;
@@ -70,6 +74,16 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
             const uint32_t slot = vis[e];
             const int v = slot_view(slot, (uint32_t)S.N, V.n);
             const int64_t n = (int64_t)slot - (int64_t)v * S.N;
+            const float4* row = reinterpret_cast<const float4*>(g2d + (int64_t)slot * G2D_STRIDE);
+            float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+            if (waited) {  // a slot whose row is zero (seen, never blended) needs nothing else
+                r0 = row[0];
+                r1 = row[1];
+                r2 = row[2];
+                if (r0.x == 0.f && r0.y == 0.f && r0.z == 0.f && r0.w == 0.f && r1.x == 0.f && r1.y == 0.f &&
+                    r1.z == 0.f && r1.w == 0.f && r2.x == 0.f && r2.y == 0.f)
+                    break;
+            }
             // Eq. 7's offset and scaling factor, decoded once: the mean here,
             // their own gradients at the end.  Everything up to the 2D
             // covariance depends on the scene alone, so it runs before the
@@ -138,11 +152,15 @@ __global__ void __launch_bounds__(CHAIN_THREADS) chain_kernel(
                     for (int c = 0; c < 3; ++c) RS[r][c] = R[r][c] * s[c];
                 cov2d(J00, J02, J11, J12, T, RS, cs.dilation, A, B, C, det);
                 // the slot's 2D gradient row, written by the backward compositing
-                grid_dependency_wait();
+                if (!waited) {
+                    grid_dependency_wait();
+                    waited = true;
+                    r0 = row[0];
+                    r1 = row[1];
+                    r2 = row[2];
+                }
                 float g[12];
                 {
-                    const float4* row = reinterpret_cast<const float4*>(g2d + (int64_t)slot * G2D_STRIDE);
-                    const float4 r0 = row[0], r1 = row[1], r2 = row[2];
                     g[0] = r0.x; g[1] = r0.y; g[2] = r0.z; g[3] = r0.w;
                     g[4] = r1.x; g[5] = r1.y; g[6] = r1.z; g[7] = r1.w;
                     g[8] = r2.x; g[9] = r2.y; g[10] = r2.z; g[11] = r2.w;
