@@ -32,6 +32,7 @@ from . import synth
 from . import vg as V
 
 # device bytes a launch needs beyond the scene, for admission
+DEPTH_SCALE = 1000.0             # track frames: 16-bit depth in millimetres
 BYTES_PER_PIXEL = 4 * 16         # images, T_final / contributor counts, gradients, targets
 BYTES_PER_SLOT = 4 * 30          # per (view, Gaussian) records, depth-sort buffers, gradient rows
 BYTES_PER_PAIR = 4 * 4           # (tile|depth key, value) x 2 sort buffers
@@ -45,7 +46,7 @@ class Request:
     scene: int
     cam: object                  # synth.Camera-like
     arrival: float               # seconds from the start of the trace
-    target: Optional[tuple] = None   # (Ct [3HW], Dt [HW]) pinned host float32, for "track"
+    target: Optional[tuple] = None   # (rgb uint8 [H][W][3], depth int16 [H][W] in mm) pinned host, for "track"
     done: float = -1.0
     result: object = None
     launched: float = -1.0       # when its launch sequence was enqueued
@@ -75,7 +76,8 @@ class ServingWorkload:
     """Requests against resident scenes: render requests from cameras moved
     at random (up to 2 deg / 5 cm) from the reference camera; track requests
     carry the RGB-D frame rendered (once per scene and size, before serving)
-    at the reference camera and ask for the pose gradient at a pose
+    at the reference camera -- as a camera delivers it, 8-bit colour and
+    16-bit depth in millimetres -- and ask for the pose gradient at a pose
     perturbed from it by up to 1 deg / 2 cm."""
 
     def __init__(self, scenes: Dict[int, "V.SceneHandle"], sizes: Sequence[tuple], params=None):
@@ -87,20 +89,22 @@ class ServingWorkload:
             for w, h in self.sizes:
                 ref = synth.serving_camera(w, h)
                 C_, D, _ = V.render_with_retry(scenes[sid], [ref], params, ctx)
-                # the targets track requests upload: page-locked, huge-page backed
-                Ct = V.host_empty(C_.numel())
-                Dt = V.host_empty(D.numel())
-                V.vg_host_stage(Ct, C_.cpu())
-                V.vg_host_stage(Dt, D.cpu())
-                self.targets[(sid, w, h)] = (ref, Ct, Dt)
+                # the frames track requests upload: page-locked, huge-page backed
+                rgb = np.clip(np.rint(np.moveaxis(C_.cpu().numpy().reshape(3, h, w), 0, -1) * 255.0), 0, 255)
+                mm = np.clip(np.rint(D.cpu().numpy() * DEPTH_SCALE), 0, 65535).astype(np.uint16)
+                rgb_h = V.host_empty(3 * w * h, torch.uint8)
+                mm_h = V.host_empty(w * h, torch.int16)
+                V.vg_host_stage(rgb_h, np.ascontiguousarray(rgb.astype(np.uint8)).reshape(-1))
+                V.vg_host_stage(mm_h, mm.view(np.int16))
+                self.targets[(sid, w, h)] = (ref, rgb_h, mm_h)
         torch.cuda.synchronize()
 
     def request(self, kind, sid, w, h, rng):
         if kind == "render":
             return synth.serving_camera(w, h, pose_seed=int(rng.integers(1 << 30))), None
-        ref, Ct, Dt = self.targets[(sid, w, h)]
+        ref, rgb_h, mm_h = self.targets[(sid, w, h)]
         T = synth.perturb_pose(ref.T_cw, rng, 1.0, 0.02)
-        return synth.camera(ref.fx, ref.fy, ref.cx, ref.cy, w, h, T, ref.near), (Ct, Dt)
+        return synth.camera(ref.fx, ref.fy, ref.cx, ref.cy, w, h, T, ref.near), (rgb_h, mm_h)
 
     def trace(self, seed: int, rate: float, duration: float, p_track: float = 0.3) -> List[Request]:
         return poisson_trace(np.random.default_rng(seed), rate, duration, sorted(self.scenes), self.sizes,
@@ -257,10 +261,15 @@ class Server:
                 dC, dD = grad[:3 * P], grad[3 * P:]
                 res = torch.empty(7 * B, **f32)
                 dxi, loss = res[:6 * B].view(B, 6), res[6 * B:]
+                rgb_d = torch.empty(3 * P, dtype=torch.uint8, device=self.device)
+                mm_d = torch.empty(P, dtype=torch.int16, device=self.device)
                 for i, r in enumerate(batch):
-                    # staged targets (library host memory): copied through the library
-                    V.vg_memcpy_async(Ct[3 * n * i:3 * n * (i + 1)], r.target[0], lane.stream)
-                    V.vg_memcpy_async(Dt[n * i:n * (i + 1)], r.target[1], lane.stream)
+                    # staged frames (library host memory): copied through the library
+                    V.vg_memcpy_async(rgb_d[3 * n * i:3 * n * (i + 1)], r.target[0], lane.stream)
+                    V.vg_memcpy_async(mm_d[n * i:n * (i + 1)], r.target[1], lane.stream)
+                # decoded on the device into the planar FP32 targets of all B views
+                V.vg_frame_decode(rgb_d, mm_d, cams[0].width, cams[0].height, DEPTH_SCALE, Ct, Dt,
+                                  stream=lane.stream)
                 for i in range(B):
                     c3, c1 = slice(3 * n * i, 3 * n * (i + 1)), slice(n * i, n * (i + 1))
                     V.vg_loss_l1(1, n, C_[c3], D[c1], S[c1], Ct[c3], Dt[c1], self.w_depth, -1.0, lane.ctx,
@@ -269,7 +278,7 @@ class Server:
                 V.vg_pose_grad(lane.ctx, B, dxi=dxi, stream=lane.stream)
                 host = self._host(lane, 7 * B)
                 host.copy_(res, non_blocking=True)
-                lane.keep = [out, tgt, grad, res]
+                lane.keep = [out, tgt, grad, res, rgb_d, mm_d]
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(lane.stream)
         lane.event, lane.batch, lane.host, lane.t_start = ev, batch, host, t_start
