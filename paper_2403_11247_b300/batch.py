@@ -10,6 +10,10 @@ colour), backward to the map and to the B pose twists,
 Adam on the poses (the pose moves by exp(-step^) on the left) and Adam on the
 map.  Poses live in a device array read by the kernels, so a captured graph
 follows them as they change; the step counters live on the device too.
+With fixed_views = k the window's first k keyframes (its oldest, already
+adjusted ones) keep their poses: they fix the gauge, which a window whose
+poses and map are all free lacks (a common rigid motion of every pose and of
+the map leaves the loss unchanged).
 With ray_rate < 1 each iteration fits only a random subset of the keyframes'
 pixels (the BA's sampled rays), redrawn on the device every iteration.
 """
@@ -28,7 +32,7 @@ class LocalBA:
     def __init__(self, scene: SceneParams, cams: Sequence, Ct: torch.Tensor, Dt: torch.Tensor,
                  lr_rot: float = 2e-3, lr_trans: float = 2e-3, lr_map: float = 0.0, w_depth: float = 0.5,
                  ppt_fwd: int = 0, ppt_bwd: int = 0, pair_headroom: float = 2.0, w_ssim: float = 0.0,
-                 ray_rate: float = 1.0, ray_seed: int = 0):
+                 ray_rate: float = 1.0, ray_seed: int = 0, fixed_views: int = 0):
         self.scene = scene
         self.cams = list(cams)
         self.B = len(self.cams)
@@ -50,6 +54,9 @@ class LocalBA:
         self.w_depth = w_depth
         self.w_ssim = w_ssim
         self.lr_rot, self.lr_trans, self.lr_map = lr_rot, lr_trans, lr_map
+        if not 0 <= fixed_views < len(self.cams):
+            raise ValueError("fixed_views must leave at least one keyframe free")
+        self.fixed_views = int(fixed_views)
         self.ctx = V.vg_ctx_create(0)
         self.sh = scene.handle()
         B, P = self.B, self.P
@@ -113,7 +120,9 @@ class LocalBA:
                                self.w_ssim, dC=self.dC, loss=self.ssim_loss)
             V.vg_render_bwd(self.sh, self.cams, self.params, self.ctx, self.dC, self.dD, None, self.grads)
             V.vg_pose_grad(self.ctx, self.B, dxi=self.dxi)
-            V.vg_pose_step(self.pose, self.dxi, self.pm, self.pv, self.lr_rot, self.lr_trans, step_dev=self.pose_step)
+            k = self.fixed_views  # (the fixed keyframes' rows are left out of the step)
+            V.vg_pose_step(self.pose[k:], self.dxi[k:], self.pm[k:], self.pv[k:], self.lr_rot, self.lr_trans,
+                           step_dev=self.pose_step)
             if self.lr_map > 0:
                 V.vg_adam_step(self.map_params, self.map_grads, self.mm, self.mv, self.lr_map, step_dev=self.map_step)
 

@@ -116,6 +116,36 @@ def test_local_ba_reduces_pose_error(torch):
     assert after[:, 1].mean() < 0.3 * before[:, 1].mean(), (before, after)
 
 
+def test_local_ba_with_the_oldest_keyframe_fixed(torch):
+    """Map and poses adjusted together, the oldest keyframe held at its
+    (exact) pose: it keeps its pose bit for bit, and the gauge it fixes lets
+    the other poses converge although the map moves too."""
+    from paper_2403_11247_b300.autograd import SceneParams
+    from paper_2403_11247_b300.batch import LocalBA, pose_errors
+    sc = synth.tiny_scene()
+    truth = kf(perturbed=False, n=8)
+    scene = SceneParams.from_synth(sc, requires_grad=False)
+    ctx = V.vg_ctx_create(0)
+    Ct, Dt, _ = V.render_with_retry(scene.handle(), truth, V.default_params(), ctx)
+    start = [truth[0]] + list(kf(perturbed=True, n=8)[1:])
+    ba = LocalBA(scene, start, Ct.clone(), Dt.clone(), lr_map=1e-4, fixed_views=1)
+    T_true = np.stack([np.asarray(c.T_cw, np.float64) for c in truth])
+    pose0 = ba.pose.clone()
+    before = pose_errors(pose0[1:].cpu().numpy().astype(np.float64), T_true[1:])
+    ba.capture(50)
+    ba.replay()
+    torch.cuda.synchronize()
+    assert ba.check() == V.VG_OK
+    assert torch.equal(ba.pose[0], pose0[0])
+    after = pose_errors(ba.pose[1:].cpu().numpy().astype(np.float64), T_true[1:])
+    # measured: rotation 0.53 -> 0.27 deg, translation 3.5 -> 0.74 cm (with
+    # every pose free the translation error only reaches 1.1 cm)
+    assert after[:, 0].mean() < 0.6 * before[:, 0].mean(), (before, after)
+    assert after[:, 1].mean() < 0.6 * before[:, 1].mean(), (before, after)
+    with pytest.raises(ValueError):
+        LocalBA(scene, start, Ct.clone(), Dt.clone(), fixed_views=8)
+
+
 def test_local_ba_with_the_ssim_term(torch):
     from paper_2403_11247_b300.autograd import SceneParams
     from paper_2403_11247_b300.batch import LocalBA, pose_errors
