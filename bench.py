@@ -1080,6 +1080,29 @@ def run_ours(args):
         run()
     torch.cuda.synchronize()
 
+    # the same step as plain launches (no graph), same L2 flush between steps,
+    # taken before the first idle wait of the process: on some hosts, once
+    # the process has idled for about a second every CUDA host call runs
+    # several times slower for the rest of its life (an eager step's host
+    # time ~0.1 -> ~0.7 ms), which graph replay does not feel but eager
+    # launches do
+    eager = None
+    if graph is not None:
+        V.vg_ctx_profile(w["ctx"], False)
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(min(args.steps, 100))]
+        for i, (a, b_) in enumerate(ev2):
+            flush.fill_(float(i))
+            a.record(stream)
+            step()
+            b_.record(stream)
+        torch.cuda.synchronize()
+        if V.vg_check(w["ctx"]) != V.VG_OK:
+            raise RuntimeError("device status not OK in the plain-launch steps")
+        eager_ms = [a.elapsed_time(b_) for a, b_ in ev2]
+        eager = {"iters_per_s": world * len(eager_ms) / (sum(eager_ms) / 1000.0),
+                 "p50_step_ms": statistics.median(eager_ms), "steps": len(eager_ms)}
+
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -1188,24 +1211,6 @@ def run_ours(args):
     probes = V.probe_peaks()
     roof["probe_fp32_tflops"] = probes["fma"]["value"]
     roof["probe_frac"] = roof["achieved"] / probes["fma"]["value"] if roof["bound"] == "alu" else None
-
-    # the same step as plain launches (no graph), same L2 flush between steps
-    eager = None
-    if graph is not None:
-        V.vg_ctx_profile(w["ctx"], False)
-        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(min(args.steps, 100))]
-        for i, (a, b_) in enumerate(ev2):
-            flush.fill_(float(i))
-            a.record(stream)
-            step()
-            b_.record(stream)
-        torch.cuda.synchronize()
-        if V.vg_check(w["ctx"]) != V.VG_OK:
-            raise RuntimeError("device status not OK in the plain-launch steps")
-        eager_ms = [a.elapsed_time(b_) for a, b_ in ev2]
-        eager = {"iters_per_s": world * len(eager_ms) / (sum(eager_ms) / 1000.0),
-                 "p50_step_ms": statistics.median(eager_ms), "steps": len(eager_ms)}
 
     # end to end through the public API: every step's target frame goes up
     # from pinned host memory and its loss and pose gradient come back.  The
